@@ -1,0 +1,132 @@
+"""Trapezoidal companion models and nodal assembly (oracle; test infrastructure).
+
+The paper states the EMT network equation G v(t) = i_in(t) + i_his(t - dt)
+(Sec. II, Eq. 1) and says it comes from the nodal formulation discretised by
+numerical integration (it cites the EMTP book). The trapezoidal companion
+model of each element is written here from that rule:
+
+  series RL  v = R i + L di/dt     ->  i(t) = g v_e(t) + I_h,   g = 1/(R + 2L/dt),
+                                       I_h <- g [v_e + (2L/dt - R) i]
+  series RC  v = R i + v_C, C dv_C/dt = i
+                                   ->  i(t) = g v_e(t) + I_h,   g = 1/(R + dt/(2C)),
+                                       I_h <- -g [v_e + (dt/(2C) - R) i]
+  shunt C    i = C dv/dt           ->  i(t) = g v(t) + I_h,     g = 2C/dt,
+                                       I_h <- -(g v + i)
+  source     Thevenin e(t), R_s    ->  conductance 1/R_s to ground, injection e(t)/R_s
+  load       current sink A sin(w t + phi) leaving the bus
+
+Every history-carrying element is kept in one uniform form: endpoints (a, b)
+with b = -1 for ground, conductance g, and the update I_h <- alpha v_e + beta i.
+Current i_e flows from a to b, so its history term enters the right-hand side
+as -I_h at a and +I_h at b (the sign convention of Eq. 1's i_his).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+KIND_RL = 0
+KIND_RC = 1
+
+
+def elements(net: dict, dt: float) -> dict:
+    """History elements: series branches first (ids 0..nb-1), then one shunt
+    capacitor per bus. Returns endpoints, g, alpha, beta."""
+    nb = len(net["br_a"])
+    n = net["n_bus"]
+    a = np.concatenate([net["br_a"], np.arange(n)]).astype(np.int64)
+    b = np.concatenate([net["br_b"], -np.ones(n, np.int64)]).astype(np.int64)
+    g = np.zeros(nb + n)
+    alpha = np.zeros(nb + n)
+    beta = np.zeros(nb + n)
+    for e in range(nb):
+        R = float(net["R"][e])
+        if net["kind"][e] == KIND_RL:
+            x = 2.0 * float(net["L"][e]) / dt
+            g[e] = 1.0 / (R + x)
+            alpha[e] = g[e]
+            beta[e] = g[e] * (x - R)
+        else:
+            x = dt / (2.0 * float(net["C"][e]))
+            g[e] = 1.0 / (R + x)
+            alpha[e] = -g[e]
+            beta[e] = -g[e] * (x - R)
+    for n_ in range(n):
+        gc = 2.0 * float(net["shunt_C"][n_]) / dt
+        g[nb + n_] = gc
+        alpha[nb + n_] = -gc
+        beta[nb + n_] = -1.0
+    return dict(a=a, b=b, g=g, alpha=alpha, beta=beta, n_series=nb)
+
+
+def graph(net: dict, dt: float) -> dict:
+    """The conductance graph: every element and every source conductance as a
+    branch (to = -1 for ground). This is the list G is assembled from."""
+    el = elements(net, dt)
+    src_g = 1.0 / np.asarray(net["src_Rs"], float)
+    return dict(n_bus=net["n_bus"],
+                frm=np.concatenate([el["a"], np.asarray(net["src_bus"], np.int64)]),
+                to=np.concatenate([el["b"], -np.ones(len(src_g), np.int64)]),
+                g=np.concatenate([el["g"], src_g]),
+                n_series=el["n_series"])
+
+
+def assemble_dense(gr: dict) -> np.ndarray:
+    """G = sum over branches of g u u^T, u = e_a - e_b (or e_a to ground)."""
+    n = gr["n_bus"]
+    G = np.zeros((n, n))
+    for a, b, g in zip(gr["frm"], gr["to"], gr["g"]):
+        G[a, a] += g
+        if b >= 0:
+            G[b, b] += g
+            G[a, b] -= g
+            G[b, a] -= g
+    return G
+
+
+def assemble_sparse(gr: dict) -> sp.csc_matrix:
+    n = gr["n_bus"]
+    rows, cols, vals = [], [], []
+    for a, b, g in zip(gr["frm"], gr["to"], gr["g"]):
+        rows.append(a); cols.append(a); vals.append(g)
+        if b >= 0:
+            rows += [b, a, b]; cols += [b, b, a]; vals += [g, -g, -g]
+    return sp.csc_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def source_injection(net: dict, t: float, src_scale=None, load_scale=None) -> np.ndarray:
+    """i_in(t): Norton currents e(t)/R_s of the sources minus the load sinks."""
+    n = net["n_bus"]
+    w = 2.0 * np.pi * net["freq"]
+    i = np.zeros(n)
+    vm = np.asarray(net["src_Vm"], float) * (1.0 if src_scale is None else np.asarray(src_scale, float))
+    for k, bus in enumerate(net["src_bus"]):
+        i[bus] += vm[k] * np.sin(w * t + net["src_phi"][k]) / net["src_Rs"][k]
+    if len(net["load_bus"]):
+        am = np.asarray(net["load_amp"], float) * (1.0 if load_scale is None else np.asarray(load_scale, float))
+        for k, bus in enumerate(net["load_bus"]):
+            i[bus] -= am[k] * np.sin(w * t + net["load_phi"][k])
+    return i
+
+
+def history_injection(el: dict, Ih: np.ndarray, n_bus: int) -> np.ndarray:
+    """i_his: -I_h at the from-bus and +I_h at the to-bus of every element."""
+    i = np.zeros(n_bus)
+    for e in range(len(Ih)):
+        i[el["a"][e]] -= Ih[e]
+        if el["b"][e] >= 0:
+            i[el["b"][e]] += Ih[e]
+    return i
+
+
+def branch_voltage(el: dict, v: np.ndarray) -> np.ndarray:
+    vb = np.where(el["b"] >= 0, v[np.maximum(el["b"], 0)], 0.0)
+    return v[el["a"]] - vb
+
+
+def update_history(el: dict, v: np.ndarray, Ih: np.ndarray, active: np.ndarray):
+    """Element currents at t and the history sources for t + dt."""
+    ve = branch_voltage(el, v)
+    cur = np.where(active, el["g"] * ve + Ih, 0.0)
+    Ih_new = np.where(active, el["alpha"] * ve + el["beta"] * cur, 0.0)
+    return cur, Ih_new

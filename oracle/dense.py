@@ -1,0 +1,41 @@
+"""Exact network solve by dense factorisation (oracle; test infrastructure).
+
+The inverse-based rewrite v = G^{-1} i of Eq. 2 has a unique answer because G
+is symmetric positive definite (every bus has a shunt to ground). This module
+computes it the plain way: a dense Cholesky factorisation, refactored after
+every change of G ("explicit recomputation").
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+class DenseSolver:
+    def __init__(self, G: np.ndarray):
+        self.G = np.array(G, dtype=float)
+        self.cf = sla.cho_factor(self.G, lower=True)
+
+    def solve(self, rhs: np.ndarray) -> np.ndarray:
+        return sla.cho_solve(self.cf, rhs)
+
+    def inverse(self) -> np.ndarray:
+        return sla.cho_solve(self.cf, np.eye(self.G.shape[0]))
+
+
+def inverse(G: np.ndarray) -> np.ndarray:
+    return DenseSolver(G).inverse()
+
+
+def sherman_morrison(Ginv: np.ndarray, u: np.ndarray, delta: float) -> np.ndarray:
+    """(G + delta u u^T)^{-1} = G^{-1} - (delta/d) z z^T, z = G^{-1} u, d = 1 + delta u^T z."""
+    z = Ginv @ u
+    d = 1.0 + delta * float(u @ z)
+    return Ginv - (delta / d) * np.outer(z, z)
+
+
+def woodbury(Ginv: np.ndarray, U: np.ndarray, deltas: np.ndarray) -> np.ndarray:
+    """(G + U diag(delta) U^T)^{-1} by the Woodbury identity."""
+    Z = Ginv @ U
+    K = np.diag(1.0 / np.asarray(deltas, float)) + U.T @ Z
+    return Ginv - Z @ np.linalg.solve(K, Z.T)

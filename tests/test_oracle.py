@@ -1,0 +1,482 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics:
+closed forms, hand-worked fixtures, identities the paper states, brute force
+on small inputs. None of these re-types the oracle's own formula."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import netgen
+from oracle import companion as cm
+from oracle import dense
+from oracle import emt
+from oracle import hinv
+from oracle import modify
+from oracle import partition as pt
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+DT = 50e-6
+
+
+def _net(n_bus, seed, extra=None):
+    return netgen.small_network(n_bus, seed, extra=extra)
+
+
+# ---------------------------------------------------------------- companion models
+def _rc_circuit(R, C, V):
+    """One bus: a DC source V behind R (sine with f = 0, phase pi/2) and a shunt C."""
+    return dict(n_bus=1, br_a=np.zeros(0, np.int32), br_b=np.zeros(0, np.int32), kind=np.zeros(0, np.int32),
+                R=np.zeros(0), L=np.zeros(0), C=np.zeros(0), shunt_C=np.array([C]),
+                src_bus=np.array([0], np.int32), src_Vm=np.array([V]), src_phi=np.array([np.pi / 2]),
+                src_Rs=np.array([R]), load_bus=np.zeros(0, np.int32), load_amp=np.zeros(0),
+                load_phi=np.zeros(0), freq=0.0)
+
+
+def test_rc_charging_closed_form():
+    # Trapezoidal charging from rest with the source switched on between 0 and dt:
+    # v_n = V (1 - rho^(n-1) / (1 + a)),  rho = (1 - a)/(1 + a),  a = dt / (2RC)
+    # (derived by hand from the trapezoidal rule; tends to V (1 - exp(-t/RC))).
+    R, C, V, dt, n = 10.0, 20e-6, 1.7, 20e-6, 400
+    nw = emt.Network(_rc_circuit(R, C, V), dt, want_tree=False)
+    out, _ = emt.simulate(nw, n, solver="dense")
+    a = dt / (2 * R * C)
+    rho = (1 - a) / (1 + a)
+    k = np.arange(1, n + 1)
+    ref = V * (1 - rho ** (k - 1) / (1 + a))
+    assert np.max(np.abs(out[:, 0] - ref)) <= 1e-13 * V
+    analytic = V * (1 - np.exp(-k * dt / (R * C)))
+    assert np.max(np.abs(out[:, 0] - analytic)) <= 2.0 * a * V   # O(dt) start-up offset only
+
+
+def _phasor_check(kind):
+    # Sine source (Rs) -> series branch (RL or RC) -> bus 1 with shunt C. The
+    # trapezoidal steady state equals the phasor solution with s = j (2/dt) tan(w dt/2)
+    # (the bilinear transform), so after the transient the samples match exactly.
+    f, dt = 60.0, 50e-6
+    w = 2 * np.pi * f
+    Rs, R, L, Cs, Csh, V, phi = 1.0, 2.0, 10e-3, 50e-6, 100e-6, 1.3, 0.4
+    net = dict(n_bus=2, br_a=np.array([0], np.int32), br_b=np.array([1], np.int32),
+               kind=np.array([kind], np.int32), R=np.array([R]), L=np.array([L if kind == 0 else 0.0]),
+               C=np.array([Cs if kind == 1 else 0.0]), shunt_C=np.array([20e-6, Csh]),
+               src_bus=np.array([0], np.int32), src_Vm=np.array([V]), src_phi=np.array([phi]),
+               src_Rs=np.array([Rs]), load_bus=np.zeros(0, np.int32), load_amp=np.zeros(0),
+               load_phi=np.zeros(0), freq=f)
+    nw = emt.Network(net, dt, want_tree=False)
+    n = 8000
+    out, _ = emt.simulate(nw, n, solver="dense")
+    s = 1j * (2 / dt) * np.tan(w * dt / 2)
+    Zb = R + (s * L if kind == 0 else 1 / (s * Cs))
+    Y0 = 1 / Rs + s * 20e-6
+    Y1 = s * Csh
+    # nodal phasor equations
+    A = np.array([[Y0 + 1 / Zb, -1 / Zb], [-1 / Zb, Y1 + 1 / Zb]])
+    E = V * np.exp(1j * (phi - np.pi / 2)) / Rs     # sin(wt + phi) = Re(exp(j(wt + phi - pi/2)))
+    Vp = np.linalg.solve(A, np.array([E, 0]))
+    k = np.arange(n - 400, n + 1 - 1) + 1
+    ref = np.real(Vp[None, :] * np.exp(1j * w * k * dt)[:, None])
+    got = out[n - 400:]
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_rl_sine_steady_state_bilinear():
+    _phasor_check(0)
+
+
+def test_rc_series_sine_steady_state_bilinear():
+    _phasor_check(1)
+
+
+def test_kirchhoff_balance_every_step():
+    net = netgen.tile(1_000_000)
+    nw = emt.Network(net, DT, want_tree=False)
+    el = nw.el
+    n = net["n_bus"]
+    Ih = np.zeros(len(el["g"]))
+    active = np.ones(len(el["g"]), bool)
+    sol = dense.DenseSolver(nw.G)
+    w = 2 * np.pi * net["freq"]
+    for step in range(1, 60):
+        t = step * DT
+        rhs = cm.source_injection(net, t) + cm.history_injection(el, Ih, n)
+        v = sol.solve(rhs)
+        cur, Ih = cm.update_history(el, v, Ih, active)
+        # KCL: element currents leaving each bus + source currents (v - e)/Rs = 0
+        bal = np.zeros(n)
+        np.add.at(bal, el["a"], cur)
+        m = el["b"] >= 0
+        np.add.at(bal, el["b"][m], -cur[m])
+        e = net["src_Vm"] * np.sin(w * t + net["src_phi"])
+        np.add.at(bal, net["src_bus"], (v[net["src_bus"]] - e) / net["src_Rs"])
+        scale = np.max(np.abs(cur)) + 1e-300
+        assert np.max(np.abs(bal)) <= 1e-12 * max(scale, np.max(np.abs(net["src_Vm"] / net["src_Rs"])))
+
+
+def _energy(nw, v, cur, active):
+    net, el = nw.net, nw.el
+    nb = el["n_series"]
+    E = 0.5 * np.sum(net["shunt_C"] * v ** 2)
+    ve = cm.branch_voltage(el, v)[:nb]
+    for e in range(nb):
+        if not active[e]:
+            continue
+        if net["kind"][e] == cm.KIND_RL:
+            E += 0.5 * net["L"][e] * cur[e] ** 2
+        else:
+            vc = ve[e] - net["R"][e] * cur[e]
+            E += 0.5 * net["C"][e] * vc ** 2
+    return E
+
+
+def test_passivity_sources_off():
+    # With every source switched off, the trapezoidal energy never increases.
+    net = _net(24, 5)
+    nw = emt.Network(net, DT, want_tree=False)
+    _, st = emt.simulate(nw, 200, solver="dense")
+    off = dict(net)
+    off["src_Vm"] = np.zeros_like(net["src_Vm"])
+    nw2 = emt.Network(off, DT, want_tree=False)
+    el = nw2.el
+    Ih, active = st["Ih"].copy(), st["active"]
+    v, cur = st["v"], st["cur"]
+    sol = dense.DenseSolver(nw2.G)
+    E_prev = _energy(nw2, v, cur, active)
+    assert E_prev > 0
+    for step in range(300):
+        rhs = cm.history_injection(el, Ih, net["n_bus"])
+        v = sol.solve(rhs)
+        cur, Ih = cm.update_history(el, v, Ih, active)
+        E = _energy(nw2, v, cur, active)
+        assert E <= E_prev * (1 + 1e-12)
+        E_prev = E
+
+
+# ---------------------------------------------------------------- exact solve
+@pytest.mark.parametrize("n_bus", [2, 3, 5, 8, 13, 16])
+def test_dense_inverse_brute_force(n_bus):
+    nw = emt.Network(_net(n_bus, 100 + n_bus), DT, want_tree=False)
+    Gi = dense.inverse(nw.G)
+    assert np.allclose(Gi, np.linalg.inv(nw.G), rtol=1e-12, atol=0)
+    assert np.max(np.abs(nw.G @ Gi - np.eye(n_bus))) <= 1e-12
+    assert np.max(np.abs(Gi - Gi.T)) <= 1e-14 * np.max(np.abs(Gi))
+
+
+def test_dense_matches_sparse_lu():
+    # The paper's reference solver is LU based (Sec. V-C.1); SciPy's sparse LU agrees.
+    net = netgen.tile(1_000_000)
+    nw = emt.Network(net, DT, want_tree=False)
+    rhs = np.random.default_rng(0).standard_normal(net["n_bus"])
+    v1 = dense.DenseSolver(nw.G).solve(rhs)
+    v2 = spla.splu(cm.assemble_sparse(nw.gr)).solve(rhs)
+    assert np.max(np.abs(v1 - v2)) <= 1e-13 * np.max(np.abs(v1))
+
+
+def test_two_bus_golden():
+    gd = json.load(open(os.path.join(GOLD, "two_bus.json")))
+    g0, g = gd["g0"], gd["g"]
+    G = np.array([[g0 + g, -g], [-g, g0 + g]])
+    tree = pt.build_tree(2, np.array([0]), np.array([1]), levels=1)
+    gb = np.array([g])
+    ex = hinv.HInv(G, tree, gb, hinv.EXACT).dense()
+    pa = hinv.HInv(G, tree, gb, hinv.PAPER).dense()
+    assert np.allclose(ex, gd["exact_inverse"], rtol=1e-15, atol=1e-16)
+    assert np.allclose(pa, gd["paper_inverse"], rtol=1e-15, atol=1e-16)
+    assert np.allclose(dense.inverse(G), gd["exact_inverse"], rtol=1e-15, atol=1e-16)
+
+
+# ---------------------------------------------------------------- partition
+def _graph_path(n):
+    return np.arange(n - 1), np.arange(1, n)
+
+
+def _graph_cycle(n):
+    return np.arange(n), (np.arange(n) + 1) % n
+
+
+def _graph_barbell(m):
+    a, b = [], []
+    for off in (0, m):
+        for i in range(m):
+            for j in range(i + 1, m):
+                a.append(off + i); b.append(off + j)
+    a.append(m - 1); b.append(m)
+    return np.array(a), np.array(b)
+
+
+def _graph_ladder(m):
+    a, b = [], []
+    for i in range(m):
+        a.append(i); b.append(m + i)
+        if i + 1 < m:
+            a += [i, m + i]; b += [i + 1, m + i + 1]
+    return np.array(a), np.array(b)
+
+
+def _brute_min_bisection(n, a, b):
+    import itertools
+    best = None
+    nA = (n + 1) // 2
+    for S in itertools.combinations(range(n), nA):
+        S = set(S)
+        c = sum(1 for x, y in zip(a, b) if (x in S) != (y in S))
+        best = c if best is None else min(best, c)
+    return best
+
+
+@pytest.mark.parametrize("name,graph,n", [
+    ("path", _graph_path(11), 11), ("cycle", _graph_cycle(12), 12),
+    ("barbell", _graph_barbell(6), 12), ("ladder", _graph_ladder(6), 12)])
+def test_bisection_reaches_brute_force_minimum(name, graph, n):
+    a, b = graph
+    L, R = pt.bisect(np.arange(n), a, b)
+    assert sorted(np.concatenate([L, R]).tolist()) == list(range(n))
+    assert {len(L), len(R)} == {(n + 1) // 2, n // 2}
+    assert pt.cut_size(L, R, a, b) == _brute_min_bisection(n, a, b)
+
+
+def test_kl_never_worse_than_growth_and_small_brute_force():
+    for seed in range(6):
+        net = _net(12, 300 + seed, extra=6)
+        a, b = net["br_a"], net["br_b"]
+        L, R = pt.bisect(np.arange(12), a, b)
+        best = _brute_min_bisection(12, a, b)
+        assert pt.cut_size(L, R, a, b) >= best
+        assert pt.cut_size(L, R, a, b) <= best + 2
+
+
+def test_tree_invariants():
+    net = netgen.tiled(2, 4)
+    tr = pt.build_tree(net["n_bus"], net["br_a"], net["br_b"], levels=3)
+    n = net["n_bus"]
+    assert sorted(tr["perm"].tolist()) == list(range(n))
+    assert len(tr["leaves"]) == 8
+    assert [int(tr["hi"][j] - tr["lo"][j]) for j in tr["leaves"]] == [179] * 8
+    for p in range(len(tr["lo"])):
+        if tr["left"][p] >= 0:
+            l, r = tr["left"][p], tr["right"][p]
+            assert tr["lo"][l] == tr["lo"][p] and tr["hi"][l] == tr["lo"][r] and tr["hi"][r] == tr["hi"][p]
+            assert tr["perm"][tr["lo"][l]:tr["hi"][l]].min() < tr["perm"][tr["lo"][r]:tr["hi"][r]].min()
+            # the cut list is exactly the set of crossing branches
+            Ls = set(tr["perm"][tr["lo"][l]:tr["hi"][l]].tolist())
+            Rs = set(tr["perm"][tr["lo"][r]:tr["hi"][r]].tolist())
+            cross = sorted(e for e, (x, y) in enumerate(zip(net["br_a"], net["br_b"]))
+                           if (x in Ls and y in Rs) or (x in Rs and y in Ls))
+            got = sorted(tr["cut_e"][tr["cut_ptr"][p]:tr["cut_ptr"][p + 1]].tolist())
+            assert got == cross
+            for c in range(tr["cut_ptr"][p], tr["cut_ptr"][p + 1]):
+                assert tr["lo"][l] <= tr["cut_a"][c] < tr["hi"][l] <= tr["cut_b"][c] < tr["hi"][r]
+    # leaf-size threshold reading: leaf iff size <= d_th
+    tr2 = pt.build_tree(net["n_bus"], net["br_a"], net["br_b"], levels=0, d_th=100)
+    for p in range(len(tr2["lo"])):
+        size = tr2["hi"][p] - tr2["lo"][p]
+        assert (tr2["left"][p] < 0) == (size <= 100)
+
+
+def test_lca_brute_force():
+    net = netgen.tiled(2, 2)
+    tr = pt.build_tree(net["n_bus"], net["br_a"], net["br_b"], levels=0, d_th=20)
+    rng = np.random.default_rng(3)
+    leaves = tr["leaves"]
+    for _ in range(200):
+        u, v = rng.choice(leaves, 2)
+        c = pt.lca(tr, int(u), int(v))
+        # brute force: the deepest node whose range contains both leaves' ranges
+        cands = [p for p in range(len(tr["lo"])) if tr["lo"][p] <= min(tr["lo"][u], tr["lo"][v])
+                 and tr["hi"][p] >= max(tr["hi"][u], tr["hi"][v])]
+        assert c == max(cands, key=lambda p: tr["depth"][p])
+
+
+# ---------------------------------------------------------------- hierarchical inverse
+@pytest.fixture(scope="module")
+def tile_nw():
+    return emt.Network(netgen.tile(1_000_000), DT, levels=2)
+
+
+def test_exact_store_equals_dense_inverse(tile_nw):
+    Gi = dense.inverse(tile_nw.G)
+    H = hinv.HInv(tile_nw.G, tile_nw.tree, tile_nw.g_series, hinv.EXACT)
+    assert hinv.relative_error(H.dense(), Gi) <= 1e-13
+    x = np.random.default_rng(1).standard_normal(179)
+    assert np.max(np.abs(H.apply(x) - Gi @ x)) <= 1e-13 * np.max(np.abs(Gi @ x))
+
+
+@pytest.mark.parametrize("n_bus,levels", [(2, 1), (5, 2), (13, 3), (16, 2)])
+def test_exact_store_tiny_brute_force(n_bus, levels):
+    nw = emt.Network(_net(n_bus, 40 + n_bus), DT, levels=levels)
+    H = hinv.HInv(nw.G, nw.tree, nw.g_series, hinv.EXACT)
+    assert np.allclose(H.dense(), np.linalg.inv(nw.G), rtol=1e-11, atol=1e-14)
+
+
+def test_paper_store_equals_dense_algorithm1(tile_nw):
+    t = tile_nw.tree
+    Gp = tile_nw.G[np.ix_(t["perm"], t["perm"])]
+    A1 = hinv.algorithm1_dense(Gp, t)
+    H = hinv.HInv(tile_nw.G, t, tile_nw.g_series, hinv.PAPER)
+    assert np.max(np.abs(H.dense_node(0) - A1)) <= 1e-13 * np.max(np.abs(A1))
+
+
+def test_eq5_offdiagonal_blocks_vanish(tile_nw):
+    # Eq. 5 with M of Eq. 7: off-diagonal blocks 0, diagonal blocks I + M H^T and
+    # I + M^T H. Those printed blocks are the blocks of Ginv G (the product order
+    # is swapped in the text; G Ginv is its transpose, with blocks I + H M^T ...).
+    # Algorithm 1 applies Eq. 4-7 at every node with G1, G2 the matrices whose
+    # inverses the children hold (the true blocks when the children are leaves).
+    t = tile_nw.tree
+    H = hinv.HInv(tile_nw.G, t, tile_nw.g_series, hinv.PAPER)
+    Gp = H.Gp
+    checked_leaf_pair = False
+    for p in range(len(t["lo"])):
+        if t["left"][p] < 0:
+            continue
+        l, r = int(t["left"][p]), int(t["right"][p])
+        lo, hi = int(t["lo"][p]), int(t["hi"][p])
+        ml = int(t["hi"][l] - lo)
+        Gi = H.dense_node(p)
+        if t["left"][l] < 0 and t["left"][r] < 0:
+            G1, G2 = Gp[lo:lo + ml, lo:lo + ml], Gp[lo + ml:hi, lo + ml:hi]
+            checked_leaf_pair = True
+        else:
+            G1, G2 = np.linalg.inv(H.dense_node(l)), np.linalg.inv(H.dense_node(r))
+        Hm = Gp[lo:hi, lo:hi][:ml, ml:]
+        Gblk = np.block([[G1, Hm], [Hm.T, G2]])
+        prod = Gi @ Gblk
+        M = Gi[:ml, ml:]
+        scale = np.max(np.abs(prod))
+        assert np.max(np.abs(Gblk @ Gi - prod.T)) <= 1e-12 * scale
+        assert np.max(np.abs(prod[:ml, ml:])) <= 1e-12 * scale
+        assert np.max(np.abs(prod[ml:, :ml])) <= 1e-12 * scale
+        assert np.max(np.abs(prod[:ml, :ml] - (np.eye(ml) + M @ Hm.T))) <= 1e-12 * scale
+        assert np.max(np.abs(prod[ml:, ml:] - (np.eye(hi - lo - ml) + M.T @ Hm))) <= 1e-12 * scale
+    assert checked_leaf_pair
+
+
+def test_eq9_low_rank_form_equals_eq7(tile_nw):
+    t = tile_nw.tree
+    H = hinv.HInv(tile_nw.G, t, tile_nw.g_series, hinv.PAPER)
+    p = 0
+    l, r = int(t["left"][p]), int(t["right"][p])
+    A, B = H.dense_node(l), H.dense_node(r)
+    lo, hi = int(t["lo"][p]), int(t["hi"][p])
+    ml = int(t["hi"][l] - lo)
+    Hm = H.Gp[lo:hi, lo:hi][:ml, ml:]
+    M7 = -A @ Hm @ B
+    M9 = -(H.P[p]) @ H.Q[p].T
+    assert np.max(np.abs(M7 - M9)) <= 1e-14 * np.max(np.abs(M7))
+    hl, hr = H.cut_columns(p)
+    assert np.array_equal(hl @ hr.T, Hm)
+
+
+def test_no_coupling_paper_equals_exact():
+    # Two disconnected halves: H = 0, so the approximation is exact.
+    net = netgen.small_network(10, 9)
+    a, b = net["br_a"], net["br_b"]
+    keep = ~(((a < 5) & (b >= 5)) | ((a >= 5) & (b < 5)))
+    for k in ("br_a", "br_b", "kind", "R", "L", "C"):
+        net[k] = net[k][keep]
+    nw = emt.Network(net, DT, levels=1)
+    ex = hinv.HInv(nw.G, nw.tree, nw.g_series, hinv.EXACT).dense()
+    pa = hinv.HInv(nw.G, nw.tree, nw.g_series, hinv.PAPER).dense()
+    assert np.max(np.abs(ex - pa)) <= 1e-15 * np.max(np.abs(ex))
+
+
+def test_paper_error_falls_as_threshold_grows():
+    # Fig. 5: the approximation error drops as d_th grows, to zero at d_th = N.
+    nw = emt.Network(netgen.tile(1_000_000), DT, want_tree=False)
+    Gi = dense.inverse(nw.G)
+    errs = []
+    for d in (10, 45, 179):
+        tr = pt.build_tree(179, nw.series_frm, nw.series_to, 0, d)
+        errs.append(hinv.relative_error(hinv.HInv(nw.G, tr, nw.g_series, hinv.PAPER).dense(), Gi))
+    assert errs[0] >= errs[1] and errs[2] <= 1e-14
+
+
+# ---------------------------------------------------------------- modification
+def test_sherman_morrison_and_woodbury_closed_forms(tile_nw):
+    G = tile_nw.G
+    Gi = dense.inverse(G)
+    a, b = int(tile_nw.series_frm[7]), int(tile_nw.series_to[7])
+    g = float(tile_nw.g_series[7])
+    u = modify.u_vector(179, a, b)
+    G2 = modify.modified_G(G, a, b, -g)
+    assert np.max(np.abs(dense.sherman_morrison(Gi, u, -g) - np.linalg.inv(G2))) <= 1e-12 * np.max(np.abs(Gi))
+    a2, b2 = int(tile_nw.series_frm[50]), int(tile_nw.series_to[50])
+    g2 = float(tile_nw.g_series[50])
+    U = np.stack([u, modify.u_vector(179, a2, b2)], axis=1)
+    G3 = modify.modified_G(G2, a2, b2, -g2)
+    assert np.max(np.abs(dense.woodbury(Gi, U, [-g, -g2]) - np.linalg.inv(G3))) <= 1e-12 * np.max(np.abs(Gi))
+
+
+def _cross_and_inner_branches(nw):
+    t = nw.tree
+    cross = int(t["cut_e"][t["cut_ptr"][0]])
+    inner = None
+    for e in range(len(nw.series_frm)):
+        la = pt.leaf_of(t, int(t["pos"][nw.series_frm[e]]))
+        lb = pt.leaf_of(t, int(t["pos"][nw.series_to[e]]))
+        if la == lb:
+            inner = e
+            break
+    return cross, inner
+
+
+def test_exact_rebuild_after_trip_equals_dense(tile_nw):
+    H = hinv.HInv(tile_nw.G, tile_nw.tree, tile_nw.g_series, hinv.EXACT)
+    for e in _cross_and_inner_branches(tile_nw):
+        a, b, g = int(tile_nw.series_frm[e]), int(tile_nw.series_to[e]), float(tile_nw.g_series[e])
+        H2 = modify.rebuild(H, tile_nw.series_frm, tile_nw.series_to, a, b, -g)
+        ref = np.linalg.inv(modify.modified_G(tile_nw.G, a, b, -g))
+        assert hinv.relative_error(H2.dense(), ref) <= 1e-13
+
+
+def test_algorithm2_to_root_equals_rebuild(tile_nw):
+    H = hinv.HInv(tile_nw.G, tile_nw.tree, tile_nw.g_series, hinv.PAPER)
+    for e in _cross_and_inner_branches(tile_nw):
+        a, b, g = int(tile_nw.series_frm[e]), int(tile_nw.series_to[e]), float(tile_nw.g_series[e])
+        A = modify.algorithm2(H, tile_nw.series_frm, tile_nw.series_to, a, b, -g, to_root=True)
+        R = modify.rebuild(H, tile_nw.series_frm, tile_nw.series_to, a, b, -g)
+        assert np.array_equal(A.dense(), R.dense())
+
+
+def test_algorithm2_literal_touches_only_local_blocks(tile_nw):
+    # Fault to ground inside one leaf: the LCA is the leaf itself, so only that
+    # leaf's inverse changes (Sec. IV-A, best case), and it is the direct inverse
+    # of the modified leaf block.
+    t = tile_nw.tree
+    H = hinv.HInv(tile_nw.G, t, tile_nw.g_series, hinv.PAPER)
+    bus = int(t["perm"][3])
+    A = modify.algorithm2(H, tile_nw.series_frm, tile_nw.series_to, bus, -1, 0.1)
+    j = pt.leaf_of(t, 3)
+    lo, hi = int(t["lo"][j]), int(t["hi"][j])
+    blk = modify.modified_G(tile_nw.G, bus, -1, 0.1)[np.ix_(t["perm"][lo:hi], t["perm"][lo:hi])]
+    assert np.allclose(A.leaf_inv[j], np.linalg.inv(blk), rtol=1e-12, atol=1e-15)
+    for p in A.P:
+        assert np.array_equal(A.P[p], H.P[p]) and np.array_equal(A.Q[p], H.Q[p])
+    for q in A.leaf_inv:
+        if q != j:
+            assert np.array_equal(A.leaf_inv[q], H.leaf_inv[q])
+    # with the LCA at the root, the literal algorithm is a full rebuild
+    e = int(t["cut_e"][t["cut_ptr"][0]])
+    a, b, g = int(tile_nw.series_frm[e]), int(tile_nw.series_to[e]), float(tile_nw.g_series[e])
+    L = modify.algorithm2(H, tile_nw.series_frm, tile_nw.series_to, a, b, -g)
+    R = modify.rebuild(H, tile_nw.series_frm, tile_nw.series_to, a, b, -g)
+    assert np.array_equal(L.dense(), R.dense())
+
+
+def test_modification_saving_golden():
+    gd = json.load(open(os.path.join(GOLD, "paper_numbers.json")))["modification_saving"]
+    assert round(100 * modify.leaf_inversion_saving(gd["d_th"], gd["n"]), 1) == gd["printed_percent"]
+
+
+# ---------------------------------------------------------------- stepping
+def test_stepping_solvers_agree_with_trip_and_fault():
+    net = netgen.tile(1_000_000)
+    nw = emt.Network(net, DT, levels=2)
+    e = netgen.pick_branch(net)
+    ev = [(30, emt.TRIP, e, 0.0), (40, emt.FAULT_ON, 17, 10.0), (55, emt.FAULT_OFF, 17, 0.0)]
+    d, sd = emt.simulate(nw, 80, ev, solver="dense")
+    x, sx = emt.simulate(nw, 80, ev, solver="exact")
+    assert np.max(np.abs(d - x)) <= 1e-11 * np.max(np.abs(d))
+    assert sd["cur"][e] == 0.0 and sd["Ih"][e] == 0.0
+    p, _ = emt.simulate(nw, 80, ev, solver="paper")
+    assert np.all(np.isfinite(p))
