@@ -1,0 +1,191 @@
+/*
+ * emt.h -- C ABI of the GB300 hierarchical-inverse EMT network solver.
+ *
+ * The library solves the per-step EMT network equation G v(t) = i_in(t) + i_his(t - dt)
+ * (Sec. II, Eq. 1) as the matrix-vector product v = G^{-1} i (Eq. 2), where G^{-1} is held
+ * as the hierarchical store of Sec. III: dense inverses of the leaf sub-networks plus, per
+ * internal tree node, the low-rank factors P = G_l^{-1} h_l, Q = G_r^{-1} h_r of Eq. 9 and a
+ * small core matrix. It updates that store locally when a branch or a fault changes G (Sec. IV).
+ *
+ * Conventions for every call:
+ *   - Calls return emt_status and never throw or abort; emt_last_error() gives a
+ *     thread-local message for the last failing call on the calling thread.
+ *   - Host arrays passed in are read during the call only and copied; the caller keeps
+ *     ownership. Device pointers (suffix _dev) are caller-owned CUDA device memory.
+ *   - Bus indices are 0-based in the caller's original bus order; vectors passed to and
+ *     from the library are in that order (the library applies its internal ordering).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is enqueued on it
+ *     and is asynchronous unless the call says it synchronises. Device-side failures
+ *     (a non-positive modification denominator, a bounded wait that ran out) are recorded
+ *     in a device status word and returned by the next synchronising call.
+ *   - Handles are not thread-safe: use one handle from one host thread and one stream.
+ *   - The library allocates its own device memory (cudaMalloc) for the stored inverse,
+ *     its scratch and simulation state; emt_*_destroy frees it.
+ */
+#ifndef EMT_H
+#define EMT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EMT_OK = 0,
+  EMT_ERR_INVALID = 1,     /* bad argument or inconsistent input                     */
+  EMT_ERR_NOMEM = 2,       /* device or host allocation failed                       */
+  EMT_ERR_SINGULAR = 3,    /* modification would make G singular / indefinite        */
+  EMT_ERR_CUDA = 4,        /* CUDA runtime error (message has the CUDA error string) */
+  EMT_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out                     */
+  EMT_ERR_STATE = 6,       /* call not valid in the handle's current state           */
+  EMT_ERR_UNSUPPORTED = 7  /* valid request outside what this build implements       */
+} emt_status;
+
+/* Store variants (Sec. III): EXACT uses the Woodbury core S^{-1} at each node and holds the
+ * exact inverse; PAPER uses the core [[0, I], [I, 0]], i.e. M = -P Q^T of Eq. 9 (Algorithm 1),
+ * the paper's approximate inverse. */
+enum { EMT_MODE_EXACT = 0, EMT_MODE_PAPER = 1 };
+
+/* Arithmetic of the hot apply. FP64: double storage and arithmetic. FF64: float-float
+ * pairs (8 bytes per element, ~48-bit significand) with compensated FP32 arithmetic.
+ * FP32: float storage and arithmetic; emt_apply refines against the FP64 residual. */
+enum { EMT_PREC_FP64 = 0, EMT_PREC_FF64 = 1, EMT_PREC_FP32 = 2 };
+
+typedef struct emt_tree emt_tree;
+typedef struct emt_hinv emt_hinv;
+typedef struct emt_sim emt_sim;
+
+/* Conductance graph (Sec. II): G = sum over branches of g_e u_e u_e^T with u_e = e_from - e_to,
+ * or u_e = e_from for a branch to ground (to = -1). g_e > 0. Bus-to-bus branches are the edges
+ * the partition sees; their index in this list is their branch id. */
+typedef struct {
+  int32_t n_bus;
+  int32_t n_branch;
+  const int32_t* from;     /* [n_branch] bus index                    */
+  const int32_t* to;       /* [n_branch] bus index, or -1 for ground  */
+  const double* g;         /* [n_branch] conductance in siemens       */
+} emt_graph;
+
+/* Build options. levels > 0: bisect to depth `levels` (2^levels leaves when sizes allow);
+ * levels == 0: bisect while a set has more than d_th buses (a leaf holds at most d_th buses,
+ * the node threshold of Sec. III-B). */
+typedef struct {
+  int32_t levels;
+  int32_t d_th;
+  int32_t mode;            /* EMT_MODE_*  */
+  int32_t precision;       /* EMT_PREC_*  */
+} emt_hinv_opts;
+
+const char* emt_last_error(void);
+const char* emt_version(void);
+
+/* ---- partition tree (host only; no GPU needed) ------------------------------------------
+ * Recursive bisection minimising the number of cut branches (Sec. III-B, Fig. 2-3): BFS
+ * growth from a pseudo-peripheral bus, Kernighan-Lin refinement, deterministic integer
+ * tie-breaking. Nodes are numbered breadth first (root 0); leaves read left to right give
+ * the nested ordering perm (new position -> bus), so every node is a range [lo, hi). */
+emt_status emt_tree_build(const emt_graph* graph, const emt_hinv_opts* opts, emt_tree** out);
+/* Sizes of the arrays emt_tree_arrays fills. */
+emt_status emt_tree_sizes(const emt_tree* t, int32_t* n_node, int32_t* n_leaf, int32_t* n_cut);
+/* Copy the tree out. perm: [n_bus]; lo, hi, parent (-1 at the root), left, right (-1 at
+ * leaves), depth: [n_node]; cut_ptr: [n_node + 1]; cut_a, cut_b (positions in perm, a in the
+ * left child, b in the right), cut_branch (branch id): [n_cut]. Any pointer may be NULL. */
+emt_status emt_tree_arrays(const emt_tree* t, int32_t* perm, int32_t* lo, int32_t* hi,
+                           int32_t* parent, int32_t* left, int32_t* right, int32_t* depth,
+                           int32_t* cut_ptr, int32_t* cut_a, int32_t* cut_b, int32_t* cut_branch);
+void emt_tree_destroy(emt_tree* t);
+
+/* ---- hierarchical inverse ---------------------------------------------------------------
+ * Algorithm 1 (Sec. III-B): partition, invert every leaf block directly (Cholesky, FP64),
+ * then bottom-up form P, Q (Eq. 9) by applying the children's stores to the cut columns,
+ * and the node cores. Synchronises `stream` before returning. */
+emt_status emt_build_hinv(const emt_graph* graph, const emt_hinv_opts* opts, void* stream,
+                          emt_hinv** out);
+/* The handle's tree (owned by the handle). */
+const emt_tree* emt_hinv_tree(const emt_hinv* h);
+
+/* v = G^{-1} i (Eq. 2) for nrhs column vectors. i_dev, v_dev: device, column-major
+ * n_bus x nrhs with leading dimension ld >= n_bus (doubles), bus order. For EMT_PREC_FP32 the
+ * result is refined up to max_refine times against the FP64 residual r = i - G v until
+ * ||c||_inf <= tol ||v||_inf. Asynchronous on `stream`. nrhs >= 1; nrhs == 1 takes the fused
+ * single-vector kernels. */
+emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld,
+                     int32_t max_refine, double tol, void* stream);
+
+/* G' = G + delta_g u u^T with u = e_a - e_b (bus_b >= 0: conductance change of the lowest-id
+ * branch joining a and b; delta_g = -g_e trips branch e) or u = e_a (bus_b == -1: a shunt to
+ * ground, e.g. a fault resistance 1/R_f). Sec. IV. EXACT stores get an exact local update
+ * (Sherman-Morrison at every node on the paths from the touched leaves to the root, FP64
+ * denominators); PAPER stores get Algorithm 2 (re-invert touched leaves, recompute the
+ * factors on the paths to the lowest common ancestor). If a denominator is not positive the
+ * store is left unchanged and EMT_ERR_SINGULAR is returned. Synchronises `stream`. */
+emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double delta_g,
+                             void* stream);
+
+/* Wait for the handle's work on `stream` and return its device status. */
+emt_status emt_hinv_sync(emt_hinv* h, void* stream);
+void emt_hinv_destroy(emt_hinv* h);
+
+/* ---- EMT simulation ---------------------------------------------------------------------
+ * Element data of one network. Series branches are RL (kind 0: R, L) or RC (kind 1: R, C);
+ * every bus may carry a shunt capacitor; sources are Thevenin sines Vm sin(2 pi f t + phi)
+ * behind Rs; loads are sine current sinks amp sin(2 pi f t + phi). Trapezoidal companion
+ * models (Sec. II) give g = 1/(R + 2L/dt), 1/(R + dt/2C), 2C/dt and 1/Rs. */
+enum { EMT_KIND_RL = 0, EMT_KIND_RC = 1 };
+typedef struct {
+  int32_t n_bus;
+  int32_t n_branch;
+  const int32_t* from;
+  const int32_t* to;
+  const int32_t* kind;
+  const double* R;
+  const double* L;
+  const double* C;
+  const double* shunt_C;   /* [n_bus] (F) or NULL */
+  int32_t n_src;
+  const int32_t* src_bus;
+  const double* src_Vm;
+  const double* src_phi;
+  const double* src_Rs;
+  int32_t n_load;
+  const int32_t* load_bus;
+  const double* load_amp;
+  const double* load_phi;
+  double freq;
+} emt_network;
+
+/* Event kinds for emt_sim_schedule. TRIP: target = branch id (opens before the step is
+ * solved; current and history zeroed). FAULT_ON: target = bus, value = R_f (ohm). FAULT_OFF:
+ * target = bus (restores the pre-fault store). */
+enum { EMT_EVENT_TRIP = 0, EMT_EVENT_FAULT_ON = 1, EMT_EVENT_FAULT_OFF = 2 };
+
+/* Create a simulation of `net` at time step dt with nrhs independent columns (nrhs = 1 for
+ * the single-network workload). src_scale [nrhs x n_src] and load_scale [nrhs x n_load]
+ * (row per column, may be NULL) scale source and load amplitudes per column. Builds the
+ * hierarchical inverse; state starts at zero (sources first evaluated at t = dt). */
+emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, double dt,
+                          int32_t nrhs, const double* src_scale, const double* load_scale,
+                          void* stream, emt_sim** out);
+/* Schedule an event at a 1-based step (before that step is solved). column = -1: every
+ * column (the shared store is modified); column >= 0: that column only (multi-column runs
+ * apply it as a per-column Sherman-Morrison correction; TRIP only). */
+emt_status emt_sim_schedule(emt_sim* s, int32_t step, int32_t kind, int32_t target,
+                            double value, int32_t column);
+/* Buses whose voltages emt_step records each step (default: none). */
+emt_status emt_sim_monitor(emt_sim* s, int32_t n_mon, const int32_t* buses);
+/* Advance n_steps steps. record_dev (device, may be NULL): [n_steps][nrhs][n_mon] doubles of
+ * monitored voltages. Asynchronous on `stream`. */
+emt_status emt_step(emt_sim* s, int32_t n_steps, double* record_dev, void* stream);
+/* Synchronise and copy out state. what: 0 = bus voltages [nrhs][n_bus] (bus order),
+ * 1 = current step number (one double). Returns the device status. */
+emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out);
+/* Tuning knob for the fused single-column kernels: rows of the leaf blocks per CTA
+ * (0 = automatic). Takes effect on the next emt_step. */
+emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
+void emt_sim_destroy(emt_sim* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

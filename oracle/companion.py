@@ -100,22 +100,19 @@ def source_injection(net: dict, t: float, src_scale=None, load_scale=None) -> np
     w = 2.0 * np.pi * net["freq"]
     i = np.zeros(n)
     vm = np.asarray(net["src_Vm"], float) * (1.0 if src_scale is None else np.asarray(src_scale, float))
-    for k, bus in enumerate(net["src_bus"]):
-        i[bus] += vm[k] * np.sin(w * t + net["src_phi"][k]) / net["src_Rs"][k]
+    np.add.at(i, np.asarray(net["src_bus"]), vm * np.sin(w * t + np.asarray(net["src_phi"])) / np.asarray(net["src_Rs"]))
     if len(net["load_bus"]):
         am = np.asarray(net["load_amp"], float) * (1.0 if load_scale is None else np.asarray(load_scale, float))
-        for k, bus in enumerate(net["load_bus"]):
-            i[bus] -= am[k] * np.sin(w * t + net["load_phi"][k])
+        np.add.at(i, np.asarray(net["load_bus"]), -am * np.sin(w * t + np.asarray(net["load_phi"])))
     return i
 
 
 def history_injection(el: dict, Ih: np.ndarray, n_bus: int) -> np.ndarray:
     """i_his: -I_h at the from-bus and +I_h at the to-bus of every element."""
     i = np.zeros(n_bus)
-    for e in range(len(Ih)):
-        i[el["a"][e]] -= Ih[e]
-        if el["b"][e] >= 0:
-            i[el["b"][e]] += Ih[e]
+    np.add.at(i, el["a"], -Ih)
+    m = el["b"] >= 0
+    np.add.at(i, el["b"][m], Ih[m])
     return i
 
 

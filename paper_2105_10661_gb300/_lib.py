@@ -1,0 +1,283 @@
+"""ctypes binding of libemt_hinv.so (argument marshalling only).
+
+Every function mirrors one entry point of include/emt.h under the same name.
+Host arrays are NumPy; device buffers are passed as raw pointers (ints) or as
+objects with a ``data_ptr()`` method (torch tensors). Nothing here computes any
+part of the method: if the shared library is missing, importing this module
+raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libemt_hinv.so")
+
+EMT_OK = 0
+EMT_ERR_INVALID = 1
+EMT_ERR_NOMEM = 2
+EMT_ERR_SINGULAR = 3
+EMT_ERR_CUDA = 4
+EMT_ERR_TIMEOUT = 5
+EMT_ERR_STATE = 6
+EMT_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "EMT_OK", 1: "EMT_ERR_INVALID", 2: "EMT_ERR_NOMEM", 3: "EMT_ERR_SINGULAR", 4: "EMT_ERR_CUDA",
+                5: "EMT_ERR_TIMEOUT", 6: "EMT_ERR_STATE", 7: "EMT_ERR_UNSUPPORTED"}
+
+EMT_MODE_EXACT = 0
+EMT_MODE_PAPER = 1
+EMT_PREC_FP64 = 0
+EMT_PREC_FF64 = 1
+EMT_PREC_FP32 = 2
+EMT_KIND_RL = 0
+EMT_KIND_RC = 1
+EMT_EVENT_TRIP = 0
+EMT_EVENT_FAULT_ON = 1
+EMT_EVENT_FAULT_OFF = 2
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+
+
+class EmtGraph(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", _i32p), ("to", _i32p), ("g", _f64p)]
+
+
+class EmtHinvOpts(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("d_th", C.c_int32), ("mode", C.c_int32), ("precision", C.c_int32)]
+
+
+class EmtNetwork(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("from_", _i32p), ("to", _i32p), ("kind", _i32p),
+                ("R", _f64p), ("L", _f64p), ("C", _f64p), ("shunt_C", _f64p),
+                ("n_src", C.c_int32), ("src_bus", _i32p), ("src_Vm", _f64p), ("src_phi", _f64p), ("src_Rs", _f64p),
+                ("n_load", C.c_int32), ("load_bus", _i32p), ("load_amp", _f64p), ("load_phi", _f64p),
+                ("freq", C.c_double)]
+
+
+class EmtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"native library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    sigs = {
+        "emt_last_error": (C.c_char_p, []),
+        "emt_version": (C.c_char_p, []),
+        "emt_tree_build": (C.c_int, [C.POINTER(EmtGraph), C.POINTER(EmtHinvOpts), C.POINTER(vp)]),
+        "emt_tree_sizes": (C.c_int, [vp, _i32p, _i32p, _i32p]),
+        "emt_tree_arrays": (C.c_int, [vp] + [_i32p] * 11),
+        "emt_tree_destroy": (None, [vp]),
+        "emt_build_hinv": (C.c_int, [C.POINTER(EmtGraph), C.POINTER(EmtHinvOpts), vp, C.POINTER(vp)]),
+        "emt_hinv_tree": (vp, [vp]),
+        "emt_apply": (C.c_int, [vp, vp, vp, C.c_int32, C.c_int64, C.c_int32, C.c_double, vp]),
+        "emt_modify_branch": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, vp]),
+        "emt_hinv_sync": (C.c_int, [vp, vp]),
+        "emt_hinv_destroy": (None, [vp]),
+        "emt_sim_create": (C.c_int, [C.POINTER(EmtNetwork), C.POINTER(EmtHinvOpts), C.c_double, C.c_int32, _f64p,
+                                     _f64p, vp, C.POINTER(vp)]),
+        "emt_sim_schedule": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32]),
+        "emt_sim_monitor": (C.c_int, [vp, C.c_int32, _i32p]),
+        "emt_step": (C.c_int, [vp, C.c_int32, vp, vp]),
+        "emt_sim_read": (C.c_int, [vp, C.c_int32, _f64p]),
+        "emt_sim_set_rows_per_cta": (C.c_int, [vp, C.c_int32]),
+        "emt_sim_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes", "emt_tree_arrays", "emt_tree_destroy",
+            "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
+            "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
+            "emt_sim_set_rows_per_cta", "emt_sim_destroy")
+
+
+def _check(code):
+    if code != EMT_OK:
+        raise EmtError(code, lib.emt_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("expected a device pointer or an object with data_ptr()")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream   # torch.cuda.Stream
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None and a.size else None
+
+
+def make_graph(n_bus, frm, to, g):
+    keep = [_i32(frm), _i32(to), _f64(g)]
+    gr = EmtGraph(int(n_bus), len(keep[0]), _p(keep[0], _i32p), _p(keep[1], _i32p), _p(keep[2], _f64p))
+    return gr, keep
+
+
+def make_opts(levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64):
+    return EmtHinvOpts(int(levels), int(d_th), int(mode), int(precision))
+
+
+def make_network(net: dict):
+    """emt_network from the raw element dict of the synthetic generator."""
+    k = dict(frm=_i32(net["br_a"]), to=_i32(net["br_b"]), kind=_i32(net["kind"]), R=_f64(net["R"]),
+             L=_f64(net["L"]), C=_f64(net["C"]), shunt=_f64(net["shunt_C"]), sb=_i32(net["src_bus"]),
+             sv=_f64(net["src_Vm"]), sp=_f64(net["src_phi"]), sr=_f64(net["src_Rs"]), lb=_i32(net["load_bus"]),
+             la=_f64(net["load_amp"]), lp=_f64(net["load_phi"]))
+    nw = EmtNetwork(int(net["n_bus"]), len(k["frm"]), _p(k["frm"], _i32p), _p(k["to"], _i32p), _p(k["kind"], _i32p),
+                    _p(k["R"], _f64p), _p(k["L"], _f64p), _p(k["C"], _f64p), _p(k["shunt"], _f64p),
+                    len(k["sb"]), _p(k["sb"], _i32p), _p(k["sv"], _f64p), _p(k["sp"], _f64p), _p(k["sr"], _f64p),
+                    len(k["lb"]), _p(k["lb"], _i32p), _p(k["la"], _f64p), _p(k["lp"], _f64p),
+                    float(net["freq"]))
+    return nw, k
+
+
+# ------------------------------------------------------------------ entry points (same names)
+def emt_version():
+    return lib.emt_version().decode()
+
+
+def emt_tree_build(n_bus, frm, to, g=None, levels=0, d_th=0):
+    if g is None:
+        g = np.ones(len(frm))
+    gr, keep = make_graph(n_bus, frm, to, g)
+    o = make_opts(levels, d_th)
+    h = C.c_void_p()
+    _check(lib.emt_tree_build(C.byref(gr), C.byref(o), C.byref(h)))
+    try:
+        return tree_arrays(h.value, n_bus)
+    finally:
+        lib.emt_tree_destroy(h)
+
+
+def tree_arrays(handle, n_bus):
+    nn, nl, nc = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.emt_tree_sizes(handle, C.byref(nn), C.byref(nl), C.byref(nc)))
+    nn, nl, nc = nn.value, nl.value, nc.value
+    out = {k: np.zeros(s, np.int32) for k, s in
+           (("perm", n_bus), ("lo", nn), ("hi", nn), ("parent", nn), ("left", nn), ("right", nn), ("depth", nn),
+            ("cut_ptr", nn + 1), ("cut_a", nc), ("cut_b", nc), ("cut_e", nc))}
+    _check(lib.emt_tree_arrays(handle, *[_p(out[k], _i32p) if out[k].size else None for k in
+                                         ("perm", "lo", "hi", "parent", "left", "right", "depth", "cut_ptr", "cut_a",
+                                          "cut_b", "cut_e")]))
+    return out
+
+
+class HInv:
+    """Owning wrapper of an emt_hinv handle."""
+
+    def __init__(self, handle, n_bus):
+        self.h = handle
+        self.n = n_bus
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.emt_hinv_destroy(self.h)
+            self.h = None
+
+    def tree(self):
+        return tree_arrays(lib.emt_hinv_tree(self.h), self.n)
+
+
+def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64, stream=None):
+    gr, keep = make_graph(n_bus, frm, to, g)
+    o = make_opts(levels, d_th, mode, precision)
+    h = C.c_void_p()
+    _check(lib.emt_build_hinv(C.byref(gr), C.byref(o), _stream(stream), C.byref(h)))
+    return HInv(h.value, n_bus)
+
+
+def emt_apply(h: HInv, i_dev, v_dev, nrhs=1, ld=None, max_refine=0, tol=0.0, stream=None):
+    _check(lib.emt_apply(h.h, _ptr(i_dev), _ptr(v_dev), int(nrhs), int(ld if ld is not None else h.n),
+                         int(max_refine), float(tol), _stream(stream)))
+
+
+def emt_modify_branch(h: HInv, bus_a, bus_b, delta_g, stream=None):
+    _check(lib.emt_modify_branch(h.h, int(bus_a), int(bus_b), float(delta_g), _stream(stream)))
+
+
+def emt_hinv_sync(h: HInv, stream=None):
+    _check(lib.emt_hinv_sync(h.h, _stream(stream)))
+
+
+class Sim:
+    """Owning wrapper of an emt_sim handle."""
+
+    def __init__(self, handle, n_bus, nrhs):
+        self.h = handle
+        self.n = n_bus
+        self.nrhs = nrhs
+        self.n_mon = 0
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.emt_sim_destroy(self.h)
+            self.h = None
+
+
+def emt_sim_create(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FF64, nrhs=1,
+                   src_scale=None, load_scale=None, stream=None):
+    nw, keep = make_network(net)
+    o = make_opts(levels, d_th, mode, precision)
+    ss = _f64(src_scale) if src_scale is not None else None
+    ls = _f64(load_scale) if load_scale is not None else None
+    h = C.c_void_p()
+    _check(lib.emt_sim_create(C.byref(nw), C.byref(o), float(dt), int(nrhs), _p(ss, _f64p), _p(ls, _f64p),
+                              _stream(stream), C.byref(h)))
+    return Sim(h.value, int(net["n_bus"]), nrhs)
+
+
+def emt_sim_schedule(s: Sim, step, kind, target, value=0.0, column=-1):
+    _check(lib.emt_sim_schedule(s.h, int(step), int(kind), int(target), float(value), int(column)))
+
+
+def emt_sim_monitor(s: Sim, buses):
+    b = _i32(buses)
+    _check(lib.emt_sim_monitor(s.h, len(b), _p(b, _i32p)))
+    s.n_mon = len(b)
+
+
+def emt_step(s: Sim, n_steps, record_dev=None, stream=None):
+    _check(lib.emt_step(s.h, int(n_steps), _ptr(record_dev), _stream(stream)))
+
+
+def emt_sim_read(s: Sim, what=0):
+    out = np.zeros(s.n * s.nrhs if what == 0 else 1)
+    _check(lib.emt_sim_read(s.h, int(what), _p(out, _f64p)))
+    return out
+
+
+def emt_sim_set_rows_per_cta(s: Sim, rows):
+    _check(lib.emt_sim_set_rows_per_cta(s.h, int(rows)))

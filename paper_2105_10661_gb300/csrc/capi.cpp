@@ -1,0 +1,234 @@
+// The extern "C" boundary: argument checks, exception-to-status translation, handle ownership.
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "plan.h"
+#include "sim.h"
+
+namespace emt {
+thread_local std::string g_last_error;
+void set_last_error(const std::string& m) { g_last_error = m; }
+void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>& rpos, const double* i_dev,
+                   double* v_dev, int nrhs, int64_t ld, int max_refine, cudaStream_t s);
+}  // namespace emt
+
+struct emt_tree {
+  emt::Tree t;
+};
+
+struct emt_hinv {
+  std::unique_ptr<emt::Store> st;
+  emt::FusedPlan plan;
+  bool has_plan = false;
+  emt::DevBuf<double> vpos, rpos;
+  emt_tree tree;
+};
+
+struct emt_sim {
+  std::unique_ptr<emt::Sim> sim;
+};
+
+namespace {
+
+template <typename F>
+emt_status guard(F&& f) {
+  try {
+    f();
+    emt::g_last_error.clear();
+    return EMT_OK;
+  } catch (const emt::Error& e) {
+    emt::g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    emt::g_last_error = "host allocation failed";
+    return EMT_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    emt::g_last_error = e.what();
+    return EMT_ERR_INVALID;
+  } catch (...) {
+    emt::g_last_error = "unknown error";
+    return EMT_ERR_INVALID;
+  }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+emt_status status_from_device(int dev) {
+  if (dev == emt::DEV_OK) return EMT_OK;
+  if (dev == emt::DEV_SINGULAR) {
+    emt::g_last_error = "device reported a singular or indefinite matrix";
+    return EMT_ERR_SINGULAR;
+  }
+  if (dev == emt::DEV_TIMEOUT) {
+    emt::g_last_error = "a bounded device wait ran out";
+    return EMT_ERR_TIMEOUT;
+  }
+  emt::g_last_error = "unknown device status";
+  return EMT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* emt_last_error(void) { return emt::g_last_error.c_str(); }
+const char* emt_version(void) { return "emt-hinv 0.1 (sm_103a)"; }
+
+emt_status emt_tree_build(const emt_graph* graph, const emt_hinv_opts* opts, emt_tree** out) {
+  return guard([&] {
+    EMT_REQUIRE(graph && opts && out, EMT_ERR_INVALID, "null argument");
+    EMT_REQUIRE(graph->n_branch == 0 || (graph->from && graph->to), EMT_ERR_INVALID, "null branch arrays");
+    std::unique_ptr<emt_tree> t(new emt_tree);
+    t->t = emt::build_tree(graph->n_bus, graph->n_branch, graph->from, graph->to, opts->levels, opts->d_th);
+    *out = t.release();
+  });
+}
+
+emt_status emt_tree_sizes(const emt_tree* t, int32_t* n_node, int32_t* n_leaf, int32_t* n_cut) {
+  return guard([&] {
+    EMT_REQUIRE(t, EMT_ERR_INVALID, "null tree");
+    if (n_node) *n_node = t->t.n_node();
+    if (n_leaf) *n_leaf = (int32_t)t->t.leaves.size();
+    if (n_cut) *n_cut = (int32_t)t->t.cut_a.size();
+  });
+}
+
+emt_status emt_tree_arrays(const emt_tree* t, int32_t* perm, int32_t* lo, int32_t* hi, int32_t* parent,
+                           int32_t* left, int32_t* right, int32_t* depth, int32_t* cut_ptr, int32_t* cut_a,
+                           int32_t* cut_b, int32_t* cut_branch) {
+  return guard([&] {
+    EMT_REQUIRE(t, EMT_ERR_INVALID, "null tree");
+    const emt::Tree& x = t->t;
+    auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+      if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
+    };
+    cp(perm, x.perm);
+    cp(lo, x.lo);
+    cp(hi, x.hi);
+    cp(parent, x.parent);
+    cp(left, x.left);
+    cp(right, x.right);
+    cp(depth, x.depth);
+    cp(cut_ptr, x.cut_ptr);
+    cp(cut_a, x.cut_a);
+    cp(cut_b, x.cut_b);
+    cp(cut_branch, x.cut_e);
+  });
+}
+
+void emt_tree_destroy(emt_tree* t) { delete t; }
+
+emt_status emt_build_hinv(const emt_graph* graph, const emt_hinv_opts* opts, void* stream, emt_hinv** out) {
+  return guard([&] {
+    EMT_REQUIRE(out, EMT_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    cudaStream_t s = as_stream(stream);
+    std::unique_ptr<emt_hinv> h(new emt_hinv);
+    h->st.reset(new emt::Store(graph, opts, s));
+    h->st->build(s);
+    const int dev = h->st->device_status(s);
+    if (dev != emt::DEV_OK) throw emt::Error(EMT_ERR_SINGULAR, "G is not positive definite (a leaf or core is singular)");
+    h->tree.t = h->st->tree;
+    *out = h.release();
+  });
+}
+
+const emt_tree* emt_hinv_tree(const emt_hinv* h) { return h ? &h->tree : nullptr; }
+
+emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld, int32_t max_refine,
+                     double tol, void* stream) {
+  (void)tol;
+  return guard([&] {
+    EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
+    EMT_REQUIRE(i_dev && v_dev, EMT_ERR_INVALID, "null vectors");
+    EMT_REQUIRE(nrhs >= 1 && ld >= h->st->n, EMT_ERR_INVALID, "bad nrhs or leading dimension");
+    EMT_REQUIRE(max_refine >= 0 && max_refine <= 16, EMT_ERR_INVALID, "max_refine out of range");
+    cudaStream_t s = as_stream(stream);
+    if (!h->has_plan) {
+      emt::make_plan(*h->st, 0, h->plan, s);
+      h->has_plan = true;
+    }
+    emt::apply_vectors(*h->st, h->plan, h->vpos, h->rpos, i_dev, v_dev, nrhs, ld, max_refine, s);
+  });
+}
+
+emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double delta_g, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
+    cudaStream_t s = as_stream(stream);
+    h->st->modify(bus_a, bus_b, delta_g, s);
+    if (h->has_plan) emt::refresh_plan_values(*h->st, h->plan, s);
+    EMT_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+emt_status emt_hinv_sync(emt_hinv* h, void* stream) {
+  emt_status r = guard([&] { EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle"); });
+  if (r != EMT_OK) return r;
+  int dev = 0;
+  r = guard([&] { dev = h->st->device_status(as_stream(stream)); });
+  if (r != EMT_OK) return r;
+  return status_from_device(dev);
+}
+
+void emt_hinv_destroy(emt_hinv* h) { delete h; }
+
+emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, double dt, int32_t nrhs,
+                          const double* src_scale, const double* load_scale, void* stream, emt_sim** out) {
+  return guard([&] {
+    EMT_REQUIRE(out, EMT_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    std::unique_ptr<emt_sim> h(new emt_sim);
+    h->sim.reset(new emt::Sim(net, opts, dt, nrhs, src_scale, load_scale, as_stream(stream)));
+    *out = h.release();
+  });
+}
+
+emt_status emt_sim_schedule(emt_sim* s, int32_t step, int32_t kind, int32_t target, double value, int32_t column) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    s->sim->schedule(step, kind, target, value, column);
+  });
+}
+
+emt_status emt_sim_monitor(emt_sim* s, int32_t n_mon, const int32_t* buses) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    s->sim->set_monitor(n_mon, buses, nullptr);
+  });
+}
+
+emt_status emt_step(emt_sim* s, int32_t n_steps, double* record_dev, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    s->sim->step(n_steps, record_dev, as_stream(stream));
+  });
+}
+
+emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out) {
+  emt_status r = guard([&] {
+    EMT_REQUIRE(s && s->sim && host_out, EMT_ERR_INVALID, "null argument");
+    s->sim->read(what, host_out, nullptr);
+  });
+  if (r != EMT_OK) return r;
+  int dev = 0;
+  r = guard([&] {
+    EMT_CUDA(cudaDeviceSynchronize());
+    dev = s->sim->store->device_status(nullptr);
+  });
+  if (r != EMT_OK) return r;
+  return status_from_device(dev);
+}
+
+emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
+    s->sim->set_rows_per_cta(rows_per_cta, nullptr);
+  });
+}
+
+void emt_sim_destroy(emt_sim* s) { delete s; }
+
+}  // extern "C"

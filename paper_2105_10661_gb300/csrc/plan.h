@@ -1,0 +1,40 @@
+// Launch plan of the fused single-vector kernels for one store: which rows each CTA owns,
+// the distinct cut endpoints of the boundary sweep, and the per-CTA partial buffer.
+#pragma once
+#include <vector>
+
+#include "fused.cuh"
+
+namespace emt {
+
+struct FusedPlan {
+  int rows_per_cta = 0;
+  int n_cta = 0;
+  int pld = 0;
+  int max_rows = 0;
+  int s_total = 0;
+  size_t smem_partial = 0;
+  size_t smem_sweep = 0;
+  DevBuf<int> cta_leaf, cta_r0, cta_r1, leaf_cta0, leaf_ncta;
+  DevBuf<int> item_pos, item_crow, item_sidx, item_cut, item_lvl, crow_pos;
+  DevBuf<double> part;       // n_cta x pld entries of 8 bytes (double or float2); FP32 uses half
+  DevBuf<double> cut_gn64;   // -g_e per cut, per precision
+  DevBuf<float2> cut_gnff;
+  DevBuf<float> cut_gn32;
+  CtaMapD cmap() const;
+  CutRowsD crows() const;
+};
+
+// Build a plan (rows_per_cta <= 0 picks a default from the store size).
+void make_plan(const Store& st, int rows_per_cta, FusedPlan& plan, cudaStream_t s);
+// Refresh the -g_e copies after a modification.
+void refresh_plan_values(const Store& st, FusedPlan& plan, cudaStream_t s);
+int default_rows_per_cta(const Store& st);
+
+// One single-vector application in the store's precision.
+//   src: bus-ordered input (src_pos == false) or position-ordered (true)
+//   v_pos: position-ordered result (accumulate: +=); v_bus: optional bus-ordered copy
+void fused_apply(const Store& st, FusedPlan& plan, const double* src, bool src_pos, double* v_pos, double* v_bus,
+                 bool accumulate, cudaStream_t s);
+
+}  // namespace emt

@@ -1,0 +1,482 @@
+// EMT time stepping on the GPU: per step, the history update of every element and the source
+// injections form i(t) = i_in(t) + i_his(t - dt) (Sec. II, Eq. 1), the hierarchical apply gives
+// v(t) = Ginv i(t) (Eq. 2), and the next step's history follows from v(t).
+//
+// Each step is the fused pair of kernels of the single-vector apply with the EMT work folded in:
+//   partial  per owned row: update the history source of every incident element from v(t - dt)
+//            (trapezoidal companion models; the state of a bus-to-bus element is kept at both of its
+//            ends and both copies evolve identically), add the source/load injection, then stream
+//            the owned rows of the leaf inverse;
+//   sweep    boundary sweep and expansion -> v(t), monitored voltages recorded.
+// FP32 stores add one refinement pass per step (residual against the FP64 G, second apply).
+// Steps are launched as CUDA graphs of a fixed chunk length (the step number lives in device
+// memory, so one instantiated graph serves every chunk); events split the chunks.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+
+#include "plan.h"
+#include "sim.h"
+
+namespace emt {
+
+namespace {
+
+__device__ __forceinline__ double element_history(double vi, double vo, int sgn, double g, double alpha, double beta,
+                                                  double& Ih) {
+  // element current a -> b: i = g v_e + I_h, v_e = v_a - v_b; history for the next step
+  const double ve = sgn > 0 ? vi - vo : vo - vi;
+  const double cur = g * ve + Ih;
+  const double Ihn = alpha * ve + beta * cur;
+  Ih = Ihn;
+  return sgn > 0 ? -Ihn : Ihn;   // contribution to i_his at this end
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kFusedThreads) k_step_partial(DStore st, CtaMapD cm, SimD sim, int s_in_chunk,
+                                                                int pass, typename Acc<PREC>::X* __restrict__ part) {
+  using A = Acc<PREC>;
+  using X = typename A::X;
+  if (*st.status != DEV_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  X* xs = reinterpret_cast<X*>(smem_raw);
+  X* red = xs + ((cm.max_rows + 1) & ~1);
+  const int c = blockIdx.x;
+  const int j = cm.cta_leaf[c];
+  const int r0 = cm.cta_r0[c], r1 = cm.cta_r1[c];
+  const int lo = st.lo[st.leaf_node[j]];
+  const int step = sim.dyn->step_base + s_in_chunk + 1;
+  for (int r = threadIdx.x; r < r1 - r0; r += blockDim.x) {
+    const int pos = lo + r0 + r;
+    double x;
+    if (pass == 0) {
+      const double t = step * sim.dt;
+      double hist = 0.0;
+      const double vi = sim.v_pos[pos];
+      for (int m = sim.inc_ptr[pos]; m < sim.inc_ptr[pos + 1]; ++m) {
+        const int o = sim.inc_other[m];
+        const double vo = o >= 0 ? sim.v_pos[o] : 0.0;
+        double Ih = sim.Ih[m];
+        hist += element_history(vi, vo, sim.inc_sgn[m], sim.inc_g[m], sim.inc_alpha[m], sim.inc_beta[m], Ih);
+        sim.Ih[m] = Ih;
+      }
+      double inj = 0.0;
+      for (int m = sim.src_ptr[pos]; m < sim.src_ptr[pos + 1]; ++m)
+        inj += sim.src_coef[m] * sin(sim.omega * t + sim.src_phi[m]);
+      x = inj + hist;
+      if (sim.x_pos) sim.x_pos[pos] = x;
+    } else {
+      // refinement: r = x - G v with the FP64 conductance matrix
+      double acc = sim.x_pos[pos];
+      for (int t = sim.csr_ptr[pos]; t < sim.csr_ptr[pos + 1]; ++t) acc -= sim.csr_val[t] * sim.v_pos[sim.csr_col[t]];
+      x = acc;
+    }
+    xs[r] = A::prep(x);
+  }
+  __syncthreads();
+  leaf_partial_core<PREC>(st, j, r0, r1, xs, part + (int64_t)c * cm.pld, red);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kFusedThreads) k_step_sweep(DStore st, CtaMapD cm, CutRowsD cr, SimD sim,
+                                                              int s_in_chunk, int accumulate, int record,
+                                                              const typename Acc<PREC>::X* __restrict__ part,
+                                                              const typename Acc<PREC>::T* __restrict__ cut_gn) {
+  using A = Acc<PREC>;
+  using X = typename A::X;
+  if (*st.status != DEV_OK) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  X* ycut = reinterpret_cast<X*>(smem_raw);
+  X* t = ycut + cr.n_crow;
+  X* s = t + cr.s_total;
+  boundary_sweep<PREC>(st, cm, cr, part, ycut, t, s, cut_gn);
+  const int c = blockIdx.x;
+  const int j = cm.cta_leaf[c];
+  const int leaf_node = st.leaf_node[j];
+  const int lo = st.lo[leaf_node];
+  const int r0 = cm.cta_r0[c], r1 = cm.cta_r1[c];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int step = sim.dyn->step_base + s_in_chunk + 1;
+  double* rec = sim.dyn->rec;
+  for (int r = r0 + warp; r < r1; r += nw) {
+    const int pos = lo + r;
+    const X y = leaf_y<PREC>(st, cm, part, pos);
+    const X v = expand_row<PREC>(st, leaf_node, pos, y, s);
+    if ((threadIdx.x & 31) == 0) {
+      double out = A::todbl(v);
+      if (accumulate) out += sim.v_pos[pos];
+      sim.v_pos[pos] = out;
+      if (record && rec) {
+        const int mi = sim.mon_idx[pos];
+        if (mi >= 0) rec[(int64_t)(step - sim.dyn->rec_first) * sim.n_mon + mi] = out;
+      }
+    }
+  }
+}
+
+__global__ void k_advance(SimDyn* dyn, int n) { dyn->step_base += n; }
+__global__ void k_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec) {
+  dyn->step_base = step_base;
+  dyn->rec_first = rec_first;
+  dyn->rec = rec;
+}
+// Trip: the element leaves G; its parameters and both history copies are zeroed.
+__global__ void k_open_element(double* g, double* alpha, double* beta, double* Ih, int m0, int m1) {
+  for (int m : {m0, m1})
+    if (m >= 0) {
+      g[m] = 0.0;
+      alpha[m] = 0.0;
+      beta[m] = 0.0;
+      Ih[m] = 0.0;
+    }
+}
+
+template <int PREC>
+void launch_steps(Sim& sm, int n, cudaStream_t s) {
+  using X = typename Acc<PREC>::X;
+  using T = typename Acc<PREC>::T;
+  const Store& st = *sm.store;
+  const FusedPlan& p = sm.plan;
+  const DStore v = st.view();
+  const CtaMapD cm = p.cmap();
+  const CutRowsD cr = p.crows();
+  const SimD sd = sm.view();
+  X* part = reinterpret_cast<X*>(p.part.p);
+  const T* gn = PREC == EMT_PREC_FP64 ? reinterpret_cast<const T*>(p.cut_gn64.p)
+                : PREC == EMT_PREC_FF64 ? reinterpret_cast<const T*>(p.cut_gnff.p)
+                                        : reinterpret_cast<const T*>(p.cut_gn32.p);
+  static bool attr = false;
+  if (!attr) {
+    EMT_CUDA(cudaFuncSetAttribute(k_step_partial<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    EMT_CUDA(cudaFuncSetAttribute(k_step_sweep<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  const bool refine = PREC == EMT_PREC_FP32;
+  for (int i = 0; i < n; ++i) {
+    k_step_partial<PREC><<<p.n_cta, kFusedThreads, p.smem_partial, s>>>(v, cm, sd, i, 0, part);
+    k_step_sweep<PREC><<<p.n_cta, kFusedThreads, p.smem_sweep, s>>>(v, cm, cr, sd, i, 0, refine ? 0 : 1, part, gn);
+    if (refine) {
+      k_step_partial<PREC><<<p.n_cta, kFusedThreads, p.smem_partial, s>>>(v, cm, sd, i, 1, part);
+      k_step_sweep<PREC><<<p.n_cta, kFusedThreads, p.smem_sweep, s>>>(v, cm, cr, sd, i, 1, 1, part, gn);
+    }
+  }
+  k_advance<<<1, 1, 0, s>>>(sm.d_dyn.p, n);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
+  switch (sm.store->precision) {
+    case EMT_PREC_FP64: launch_steps<EMT_PREC_FP64>(sm, n, s); break;
+    case EMT_PREC_FF64: launch_steps<EMT_PREC_FF64>(sm, n, s); break;
+    default: launch_steps<EMT_PREC_FP32>(sm, n, s); break;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+SimD Sim::view() const {
+  SimD d;
+  d.n = n;
+  d.inc_ptr = inc_ptr.p;
+  d.inc_other = inc_other.p;
+  d.inc_sgn = inc_sgn.p;
+  d.inc_g = inc_g.p;
+  d.inc_alpha = inc_alpha.p;
+  d.inc_beta = inc_beta.p;
+  d.Ih = Ih.p;
+  d.src_ptr = src_ptr.p;
+  d.src_coef = src_coef.p;
+  d.src_phi = src_phi.p;
+  d.omega = omega;
+  d.dt = dt;
+  d.v_pos = v_pos.p;
+  d.x_pos = store->precision == EMT_PREC_FP32 ? x_pos.p : nullptr;
+  d.mon_idx = mon_idx.p;
+  d.n_mon = n_mon;
+  d.dyn = d_dyn.p;
+  d.csr_ptr = store->d_csr_ptr.p;
+  d.csr_col = store->d_csr_col.p;
+  d.csr_val = store->d_csr_val.p;
+  return d;
+}
+
+Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs_, const double* src_scale,
+         const double* load_scale, cudaStream_t s) {
+  EMT_REQUIRE(net && opts, EMT_ERR_INVALID, "null network or options");
+  EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
+  EMT_REQUIRE(nrhs_ == 1, EMT_ERR_UNSUPPORTED, "this build steps one column per simulation");
+  (void)src_scale;
+  (void)load_scale;
+  n = net->n_bus;
+  nrhs = nrhs_;
+  dt = dt_;
+  omega = 2.0 * M_PI * net->freq;
+  const int nb = net->n_branch;
+  EMT_REQUIRE(n >= 1 && nb >= 0, EMT_ERR_INVALID, "bad network sizes");
+  // trapezoidal companion models (Sec. II): elements = series branches, then shunt capacitors
+  el_a.clear();
+  for (int e = 0; e < nb; ++e) {
+    const int a = net->from[e], b = net->to[e];
+    EMT_REQUIRE(a >= 0 && a < n && b >= 0 && b < n && a != b, EMT_ERR_INVALID, "series branch endpoints");
+    const double R = net->R[e];
+    double g, al, be;
+    if (net->kind[e] == EMT_KIND_RL) {
+      const double x = 2.0 * net->L[e] / dt;
+      g = 1.0 / (R + x);
+      al = g;
+      be = g * (x - R);
+    } else {
+      EMT_REQUIRE(net->kind[e] == EMT_KIND_RC && net->C[e] > 0, EMT_ERR_INVALID, "bad RC branch");
+      const double x = dt / (2.0 * net->C[e]);
+      g = 1.0 / (R + x);
+      al = -g;
+      be = -g * (x - R);
+    }
+    EMT_REQUIRE(std::isfinite(g) && g > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
+    el_a.push_back(a);
+    el_b.push_back(b);
+    el_g.push_back(g);
+    el_alpha.push_back(al);
+    el_beta.push_back(be);
+  }
+  n_series = nb;
+  if (net->shunt_C)
+    for (int i = 0; i < n; ++i) {
+      const double C = net->shunt_C[i];
+      if (!(C > 0)) continue;
+      const double g = 2.0 * C / dt;
+      el_a.push_back(i);
+      el_b.push_back(-1);
+      el_g.push_back(g);
+      el_alpha.push_back(-g);
+      el_beta.push_back(-1.0);
+    }
+  // conductance graph for the store: elements + source conductances
+  std::vector<int32_t> gf(el_a.begin(), el_a.end()), gt(el_b.begin(), el_b.end());
+  std::vector<double> gv(el_g.begin(), el_g.end());
+  for (int k = 0; k < net->n_src; ++k) {
+    EMT_REQUIRE(net->src_bus[k] >= 0 && net->src_bus[k] < n && net->src_Rs[k] > 0, EMT_ERR_INVALID, "bad source");
+    gf.push_back(net->src_bus[k]);
+    gt.push_back(-1);
+    gv.push_back(1.0 / net->src_Rs[k]);
+  }
+  emt_graph gr{n, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
+  // the partition sees bus-to-bus branches only; series branch ids are their element ids
+  store.reset(new Store(&gr, opts, s));
+  store->build(s);
+  const Tree& t = store->tree;
+  // incidences by position (element order inside a position)
+  std::vector<std::vector<int>> at(n);
+  for (size_t e = 0; e < el_a.size(); ++e) {
+    at[t.pos[el_a[e]]].push_back((int)e);
+    if (el_b[e] >= 0) at[t.pos[el_b[e]]].push_back((int)e);
+  }
+  std::vector<int> iptr(n + 1, 0), iother, isgn;
+  std::vector<double> ig, ial, ibe;
+  el_inc.assign(el_a.size(), {-1, -1});
+  for (int p = 0; p < n; ++p) {
+    for (int e : at[p]) {
+      const int m = (int)iother.size();
+      const bool is_a = t.pos[el_a[e]] == p;
+      iother.push_back(is_a ? (el_b[e] >= 0 ? t.pos[el_b[e]] : -1) : t.pos[el_a[e]]);
+      isgn.push_back(is_a ? 1 : -1);
+      ig.push_back(el_g[e]);
+      ial.push_back(el_alpha[e]);
+      ibe.push_back(el_beta[e]);
+      (is_a ? el_inc[e].first : el_inc[e].second) = m;
+    }
+    iptr[p + 1] = (int)iother.size();
+  }
+  inc_ptr.upload(iptr, s);
+  inc_other.upload(iother, s);
+  inc_sgn.upload(isgn, s);
+  inc_g.upload(ig, s);
+  inc_alpha.upload(ial, s);
+  inc_beta.upload(ibe, s);
+  Ih.alloc(std::max<size_t>(iother.size(), 1));
+  Ih.zero(s);
+  // sources and loads per position
+  std::vector<std::vector<std::pair<double, double>>> terms(n);
+  for (int k = 0; k < net->n_src; ++k)
+    terms[t.pos[net->src_bus[k]]].push_back({net->src_Vm[k] / net->src_Rs[k], net->src_phi[k]});
+  for (int k = 0; k < net->n_load; ++k) {
+    EMT_REQUIRE(net->load_bus[k] >= 0 && net->load_bus[k] < n, EMT_ERR_INVALID, "bad load bus");
+    terms[t.pos[net->load_bus[k]]].push_back({-net->load_amp[k], net->load_phi[k]});
+  }
+  std::vector<int> sp(n + 1, 0);
+  std::vector<double> sc, sph;
+  for (int p = 0; p < n; ++p) {
+    for (auto& tm : terms[p]) {
+      sc.push_back(tm.first);
+      sph.push_back(tm.second);
+    }
+    sp[p + 1] = (int)sc.size();
+  }
+  src_ptr.upload(sp, s);
+  src_coef.upload(sc, s);
+  src_phi.upload(sph, s);
+  v_pos.alloc(n);
+  v_pos.zero(s);
+  x_pos.alloc(n);
+  x_pos.zero(s);
+  std::vector<int> mi(n, -1);
+  mon_idx.upload(mi, s);
+  n_mon = 0;
+  d_dyn.alloc(1);
+  EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
+  make_plan(*store, 0, plan, s);
+  EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  EMT_CUDA(cudaStreamSynchronize(s));
+  EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
+}
+
+Sim::~Sim() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+void Sim::drop_graphs() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+}
+
+void Sim::set_rows_per_cta(int rpc, cudaStream_t s) {
+  EMT_CUDA(cudaDeviceSynchronize());
+  drop_graphs();
+  make_plan(*store, rpc, plan, s);
+  EMT_CUDA(cudaDeviceSynchronize());
+}
+
+void Sim::set_monitor(int nm, const int32_t* buses, cudaStream_t s) {
+  EMT_REQUIRE(nm >= 0 && (nm == 0 || buses), EMT_ERR_INVALID, "bad monitor list");
+  std::vector<int> mi(n, -1);
+  for (int k = 0; k < nm; ++k) {
+    EMT_REQUIRE(buses[k] >= 0 && buses[k] < n, EMT_ERR_INVALID, "monitor bus out of range");
+    EMT_REQUIRE(mi[store->tree.pos[buses[k]]] < 0, EMT_ERR_INVALID, "duplicate monitor bus");
+    mi[store->tree.pos[buses[k]]] = k;
+  }
+  EMT_CUDA(cudaDeviceSynchronize());
+  mon_idx.upload(mi, s);
+  n_mon = nm;
+  drop_graphs();
+  EMT_CUDA(cudaDeviceSynchronize());
+}
+
+void Sim::schedule(int step, int kind, int target, double value, int column) {
+  EMT_REQUIRE(step >= 1, EMT_ERR_INVALID, "event step must be >= 1");
+  EMT_REQUIRE(step > cur_step, EMT_ERR_STATE, "event step already simulated");
+  EMT_REQUIRE(column == -1 || (column >= 0 && column < nrhs), EMT_ERR_INVALID, "bad column");
+  EMT_REQUIRE(column == -1, EMT_ERR_UNSUPPORTED, "per-column events need a multi-column simulation");
+  if (kind == EMT_EVENT_TRIP) EMT_REQUIRE(target >= 0 && target < n_series, EMT_ERR_INVALID, "trip target must be a series branch");
+  else if (kind == EMT_EVENT_FAULT_ON) EMT_REQUIRE(target >= 0 && target < n && value > 0, EMT_ERR_INVALID, "bad fault");
+  else if (kind == EMT_EVENT_FAULT_OFF) EMT_REQUIRE(target >= 0 && target < n, EMT_ERR_INVALID, "bad fault bus");
+  else throw Error(EMT_ERR_INVALID, "unknown event kind");
+  events.push_back({step, kind, target, value, column});
+  std::stable_sort(events.begin(), events.end(), [](const Event& a, const Event& b) { return a.step < b.step; });
+}
+
+void Sim::apply_event(const Event& ev, cudaStream_t s) {
+  Store& st = *store;
+  if (ev.kind == EMT_EVENT_TRIP) {
+    const int e = ev.target;
+    if (el_g[e] == 0.0) return;   // already open
+    const double g = el_g[e];
+    st.modify_async(el_a[e], el_b[e], -g, s);
+    k_open_element<<<1, 1, 0, s>>>(inc_g.p, inc_alpha.p, inc_beta.p, Ih.p, el_inc[e].first, el_inc[e].second);
+    el_g[e] = 0.0;
+  } else if (ev.kind == EMT_EVENT_FAULT_ON) {
+    Snapshot& sn = snapshots[ev.target];
+    sn.save(st, s);
+    st.modify_async(ev.target, -1, 1.0 / ev.value, s);
+  } else {
+    auto it = snapshots.find(ev.target);
+    EMT_REQUIRE(it != snapshots.end(), EMT_ERR_STATE, "FAULT_OFF without FAULT_ON");
+    it->second.restore(st, s);
+    snapshots.erase(it);
+  }
+  refresh_plan_values(st, plan, s);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void Snapshot::save(const Store& st, cudaStream_t s) {
+  L.alloc(st.L64.n);
+  F.alloc(std::max<size_t>(st.F64.n, 1));
+  C.alloc(std::max<size_t>(st.C64.n, 1));
+  cg.alloc(std::max<size_t>(st.d_cut_g.n, 1));
+  cv.alloc(std::max<size_t>(st.d_csr_val.n, 1));
+  EMT_CUDA(cudaMemcpyAsync(L.p, st.L64.p, st.L64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.F64.n) EMT_CUDA(cudaMemcpyAsync(F.p, st.F64.p, st.F64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.C64.n) EMT_CUDA(cudaMemcpyAsync(C.p, st.C64.p, st.C64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.d_cut_g.n) EMT_CUDA(cudaMemcpyAsync(cg.p, st.d_cut_g.p, st.d_cut_g.n * 8, cudaMemcpyDeviceToDevice, s));
+  EMT_CUDA(cudaMemcpyAsync(cv.p, st.d_csr_val.p, st.d_csr_val.n * 8, cudaMemcpyDeviceToDevice, s));
+  g_val = st.g_val;
+  csr_val = st.csr_val;
+  cut_g = st.cut_g_h;
+}
+
+void Snapshot::restore(Store& st, cudaStream_t s) {
+  EMT_CUDA(cudaMemcpyAsync(st.L64.p, L.p, st.L64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.F64.n) EMT_CUDA(cudaMemcpyAsync(st.F64.p, F.p, st.F64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.C64.n) EMT_CUDA(cudaMemcpyAsync(st.C64.p, C.p, st.C64.n * 8, cudaMemcpyDeviceToDevice, s));
+  if (st.d_cut_g.n) EMT_CUDA(cudaMemcpyAsync(st.d_cut_g.p, cg.p, st.d_cut_g.n * 8, cudaMemcpyDeviceToDevice, s));
+  EMT_CUDA(cudaMemcpyAsync(st.d_csr_val.p, cv.p, st.d_csr_val.n * 8, cudaMemcpyDeviceToDevice, s));
+  st.g_val = g_val;
+  st.csr_val = csr_val;
+  st.cut_g_h = cut_g;
+  st.pack(s);
+}
+
+void Sim::run(int n_steps, cudaStream_t s) {
+  int done = 0;
+  while (done < n_steps) {
+    const int next = cur_step + 1;
+    while (ev_cursor < events.size() && events[ev_cursor].step < next) ++ev_cursor;
+    while (ev_cursor < events.size() && events[ev_cursor].step == next) apply_event(events[ev_cursor++], s);
+    int stretch = n_steps - done;
+    if (ev_cursor < events.size()) stretch = std::min(stretch, events[ev_cursor].step - next);
+    stretch = std::max(stretch, 1);
+    int left = stretch;
+    while (left >= kChunk) {
+      auto it = graphs.find(kChunk);
+      if (it == graphs.end()) {
+        cudaGraph_t g;
+        EMT_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+        launch_steps_any(*this, kChunk, cap_stream);
+        EMT_CUDA(cudaStreamEndCapture(cap_stream, &g));
+        cudaGraphExec_t ge;
+        EMT_CUDA(cudaGraphInstantiate(&ge, g, 0));
+        cudaGraphDestroy(g);
+        it = graphs.emplace(kChunk, ge).first;
+      }
+      EMT_CUDA(cudaGraphLaunch(it->second, s));
+      left -= kChunk;
+    }
+    if (left > 0) launch_steps_any(*this, left, s);
+    cur_step += stretch;
+    done += stretch;
+  }
+}
+
+void Sim::step(int n_steps, double* record_dev, cudaStream_t s) {
+  EMT_REQUIRE(n_steps >= 0, EMT_ERR_INVALID, "n_steps must be >= 0");
+  if (n_steps == 0) return;
+  k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
+  EMT_CUDA(cudaGetLastError());
+  run(n_steps, s);
+}
+
+void Sim::read(int what, double* host_out, cudaStream_t s) {
+  if (what == 1) {
+    host_out[0] = (double)cur_step;
+    return;
+  }
+  EMT_REQUIRE(what == 0, EMT_ERR_INVALID, "unknown read selector");
+  std::vector<double> vp(n);
+  EMT_CUDA(cudaDeviceSynchronize());
+  EMT_CUDA(cudaMemcpy(vp.data(), v_pos.p, n * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int p = 0; p < n; ++p) host_out[store->tree.perm[p]] = vp[p];
+}
+
+}  // namespace emt

@@ -1,0 +1,91 @@
+// EMT simulation object (host) and its device view.
+#pragma once
+#include <map>
+#include <memory>
+#include <utility>
+#include <vector>
+
+#include "plan.h"
+
+namespace emt {
+
+struct SimDyn {
+  int step_base;   // steps completed before the current launch sequence
+  int rec_first;   // step number stored at record row 0
+  double* rec;     // record buffer of the current emt_step call (may be null)
+};
+
+struct SimD {
+  int n;
+  const int* inc_ptr;      // incidences per position
+  const int* inc_other;    // position of the element's other end (-1: ground)
+  const int* inc_sgn;      // +1 at the element's from-bus, -1 at its to-bus
+  const double* inc_g;
+  const double* inc_alpha;
+  const double* inc_beta;
+  double* Ih;              // history source, one copy per incidence
+  const int* src_ptr;
+  const double* src_coef;  // Vm/Rs for sources, -amp for loads
+  const double* src_phi;
+  double omega, dt;
+  double* v_pos;
+  double* x_pos;           // right-hand side kept for the refinement residual (FP32 only)
+  const int* mon_idx;
+  int n_mon;
+  SimDyn* dyn;
+  const int* csr_ptr;
+  const int* csr_col;
+  const double* csr_val;
+};
+
+struct Event {
+  int step, kind, target;
+  double value;
+  int column;
+};
+
+// Copy of the FP64 store taken when a fault switches in; switching it out restores it.
+struct Snapshot {
+  DevBuf<double> L, F, C, cg, cv;
+  std::vector<double> g_val, csr_val, cut_g;
+  void save(const Store& st, cudaStream_t s);
+  void restore(Store& st, cudaStream_t s);
+};
+
+class Sim {
+ public:
+  Sim(const emt_network* net, const emt_hinv_opts* opts, double dt, int nrhs, const double* src_scale,
+      const double* load_scale, cudaStream_t s);
+  ~Sim();
+  void schedule(int step, int kind, int target, double value, int column);
+  void set_monitor(int n_mon, const int32_t* buses, cudaStream_t s);
+  void set_rows_per_cta(int rpc, cudaStream_t s);
+  void step(int n_steps, double* record_dev, cudaStream_t s);
+  void read(int what, double* host_out, cudaStream_t s);
+  SimD view() const;
+
+  static constexpr int kChunk = 64;
+  std::unique_ptr<Store> store;
+  FusedPlan plan;
+  int n = 0, nrhs = 1, n_series = 0, n_mon = 0;
+  double dt = 0, omega = 0;
+  int cur_step = 0;
+  std::vector<int> el_a, el_b;
+  std::vector<double> el_g, el_alpha, el_beta;
+  std::vector<std::pair<int, int>> el_inc;
+  DevBuf<int> inc_ptr, inc_other, inc_sgn, src_ptr, mon_idx;
+  DevBuf<double> inc_g, inc_alpha, inc_beta, Ih, src_coef, src_phi, v_pos, x_pos;
+  DevBuf<SimDyn> d_dyn;
+  std::vector<Event> events;
+  size_t ev_cursor = 0;
+  std::map<int, Snapshot> snapshots;
+  std::map<int, cudaGraphExec_t> graphs;
+  cudaStream_t cap_stream = nullptr;
+
+ private:
+  void run(int n_steps, cudaStream_t s);
+  void apply_event(const Event& ev, cudaStream_t s);
+  void drop_graphs();
+};
+
+}  // namespace emt

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs. Tolerances: 1e-10 for FP64 / float-float, 1e-8 for FP32
+after refinement (relative to the max-norm of the reference)."""
+import numpy as np
+import pytest
+
+import netgen
+from oracle import dense as odense
+from oracle import emt as oemt
+from oracle import hinv as ohinv
+from oracle import modify as omod
+from tests.gpu_util import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = 50e-6
+TOL = {0: 1e-10, 1: 1e-10, 2: 1e-8}
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2105_10661_gb300 import buildlib
+    buildlib.build()
+    import paper_2105_10661_gb300._lib as lib
+    assert torch.cuda.is_available()
+    return lib
+
+
+def _store_inputs(net):
+    nw = oemt.Network(net, DT, want_tree=False)
+    gr = nw.gr
+    return nw, gr
+
+
+def _apply(L, h, X):
+    n, m = X.shape
+    i_dev = torch.tensor(X.T.copy(), dtype=torch.float64, device="cuda")
+    v_dev = torch.zeros_like(i_dev)
+    L.emt_apply(h, i_dev, v_dev, nrhs=m, ld=n, max_refine=2 if h_prec(h) == 2 else 0)
+    torch.cuda.synchronize()
+    return v_dev.cpu().numpy().T
+
+
+_PREC = {}
+
+
+def h_prec(h):
+    return _PREC.get(id(h), 0)
+
+
+def _build(L, net_nw, levels=0, d_th=0, mode=0, prec=0):
+    nw, gr = net_nw
+    h = L.emt_build_hinv(gr["n_bus"], gr["frm"], gr["to"], gr["g"], levels=levels, d_th=d_th, mode=mode, precision=prec)
+    _PREC[id(h)] = prec
+    return h
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("which,levels,d_th", [("tile", 2, 0), ("tiles8", 3, 0), ("small5", 2, 0), ("small37", 0, 7),
+                                               ("small2", 1, 0), ("tile", 0, 20)])
+def test_exact_apply_matches_dense_solve(L, prec, which, levels, d_th):
+    if which == "tile":
+        net = netgen.tile(1_000_000)
+    elif which == "tiles8":
+        net = netgen.tiled(2, 4)
+    else:
+        net = netgen.small_network(int(which[5:]), 91)
+    ni = _store_inputs(net)
+    h = _build(L, ni, levels, d_th, 0, prec)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((net["n_bus"], 3))
+    got = _apply(L, h, X)
+    ref = odense.DenseSolver(ni[0].G).solve(X)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_paper_apply_matches_algorithm1(L, prec):
+    net = netgen.tiled(2, 4)
+    ni = _store_inputs(net)
+    tree = __import__("oracle.partition", fromlist=["x"]).build_tree(net["n_bus"], net["br_a"], net["br_b"], 3)
+    H = ohinv.HInv(ni[0].G, tree, ni[0].g_series, ohinv.PAPER)
+    h = _build(L, ni, 3, 0, 1, prec)
+    X = np.random.default_rng(6).standard_normal((net["n_bus"], 2))
+    got = _apply(L, h, X)
+    ref = H.apply(X)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+def _branch_cases(nw, tree):
+    from oracle import partition as op
+    cross = int(tree["cut_e"][tree["cut_ptr"][0]])
+    inner = None
+    for e in range(len(nw.series_frm)):
+        if op.leaf_of(tree, int(tree["pos"][nw.series_frm[e]])) == op.leaf_of(tree, int(tree["pos"][nw.series_to[e]])):
+            inner = e
+            break
+    deep = None
+    for p in range(1, len(tree["lo"])):
+        if tree["left"][p] >= 0 and tree["cut_ptr"][p + 1] > tree["cut_ptr"][p]:
+            deep = int(tree["cut_e"][tree["cut_ptr"][p]])
+            break
+    return [cross, inner, deep]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_modify_matches_recomputation(L, prec):
+    net = netgen.tiled(2, 4)
+    ni = _store_inputs(net)
+    nw = ni[0]
+    from oracle import partition as op
+    tree = op.build_tree(net["n_bus"], net["br_a"], net["br_b"], 3)
+    h = _build(L, ni, 3, 0, 0, prec)
+    G = nw.G.copy()
+    X = np.random.default_rng(7).standard_normal((net["n_bus"], 2))
+    for e in _branch_cases(nw, tree):
+        a, b, g = int(nw.series_frm[e]), int(nw.series_to[e]), float(nw.g_series[e])
+        L.emt_modify_branch(h, a, b, -g)
+        G = omod.modified_G(G, a, b, -g)
+        assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
+    # fault to ground and its removal
+    L.emt_modify_branch(h, 11, -1, 0.1)
+    G = omod.modified_G(G, 11, -1, 0.1)
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
+
+
+def test_exact_modify_singular_rejected_and_store_unchanged(L):
+    net = netgen.tile(1_000_000)
+    ni = _store_inputs(net)
+    h = _build(L, ni, 2, 0, 0, 0)
+    X = np.random.default_rng(8).standard_normal((net["n_bus"], 1))
+    before = _apply(L, h, X)
+    a = int(ni[0].series_frm[3])
+    with pytest.raises(L.EmtError) as e:
+        L.emt_modify_branch(h, a, -1, -10.0 * ni[0].G[a, a])   # makes G indefinite
+    assert e.value.code == L.EMT_ERR_SINGULAR
+    after = _apply(L, h, X)
+    assert np.array_equal(before, after)
+
+
+def test_paper_modify_matches_algorithm2(L):
+    net = netgen.tiled(2, 4)
+    ni = _store_inputs(net)
+    nw = ni[0]
+    from oracle import partition as op
+    tree = op.build_tree(net["n_bus"], net["br_a"], net["br_b"], 3)
+    H = ohinv.HInv(nw.G, tree, nw.g_series, ohinv.PAPER)
+    h = _build(L, ni, 3, 0, 1, 0)
+    X = np.random.default_rng(9).standard_normal((net["n_bus"], 2))
+    for e in _branch_cases(nw, tree):
+        a, b, g = int(nw.series_frm[e]), int(nw.series_to[e]), float(nw.g_series[e])
+        L.emt_modify_branch(h, a, b, -g)
+        H = omod.algorithm2(H, nw.series_frm, nw.series_to, a, b, -g)
+        assert rel_err(_apply(L, h, X), H.apply(X)) <= 1e-10
+
+
+def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rpc=0):
+    nw = oemt.Network(net, DT, levels=levels)
+    oev = []
+    for (st, kind, tgt, val) in events:
+        oev.append((st, kind, tgt, val))
+    ref, _ = oemt.simulate(nw, steps, oev, solver=solver)
+    sim = L.emt_sim_create(net, DT, levels=levels, mode=mode, precision=prec)
+    if rpc:
+        L.emt_sim_set_rows_per_cta(sim, rpc)
+    L.emt_sim_monitor(sim, np.arange(net["n_bus"]))
+    for (st, kind, tgt, val) in events:
+        L.emt_sim_schedule(sim, st, kind, tgt, val)
+    rec = torch.zeros(steps, net["n_bus"], dtype=torch.float64, device="cuda")
+    # two calls to exercise the step counter across emt_step calls
+    h1 = steps // 2
+    L.emt_step(sim, h1, rec[:h1])
+    L.emt_step(sim, steps - h1, rec[h1:])
+    torch.cuda.synchronize()
+    final = L.emt_sim_read(sim, 0)
+    got = rec.cpu().numpy()
+    assert np.array_equal(final, got[-1])
+    return rel_err(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_sim_179_bus_trip_matches_oracle(L, prec):
+    net = netgen.tile(1_000_000)
+    e = netgen.pick_branch(net)
+    err = _sim_compare(L, net, 2, 150, [(70, 0, e, 0.0)], prec)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("rpc", [0, 7, 64, 179])
+def test_sim_fault_on_off_and_cta_shapes(L, rpc):
+    net = netgen.tile(1_000_000)
+    ev = [(30, 1, 17, 10.0), (90, 2, 17, 0.0), (100, 0, netgen.pick_branch(net), 0.0)]
+    err = _sim_compare(L, net, 2, 140, ev, 1, rpc=rpc)
+    assert err <= 1e-10, err
+
+
+def test_sim_paper_mode_matches_oracle_paper_stepping(L):
+    net = netgen.tile(1_000_000)
+    e = netgen.pick_branch(net)
+    err = _sim_compare(L, net, 2, 120, [(60, 0, e, 0.0)], 1, mode=1, solver="paper")
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_sim_1432_bus_matches_oracle(L, prec):
+    net = netgen.tiled(2, 4)
+    e = netgen.pick_branch(net)
+    err = _sim_compare(L, net, 3, 200, [(100, 0, e, 0.0)], prec)
+    assert err <= TOL[prec], err
+
+
+def test_sim_ragged_small_network(L):
+    net = netgen.small_network(37, 5)
+    err = _sim_compare(L, net, 3, 90, [(40, 0, 3, 0.0)], 1)
+    assert err <= 1e-10, err

@@ -1,0 +1,66 @@
+"""Host-side checks of the native library (no GPU): it loads, exports every
+entry point of include/emt.h, and its partition tree is bit-exact with the
+oracle's independent implementation."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import netgen
+from oracle import partition as opart
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2105_10661_gb300 import buildlib
+    buildlib.build()
+    import paper_2105_10661_gb300._lib as lib
+    return lib
+
+
+def test_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "emt.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(emt_[a-z_0-9]+)\s*\(", hdr))
+    assert len(declared) >= 19
+    for name in declared:
+        assert hasattr(L.lib, name), name
+    assert set(L.EXPORTED) == declared
+
+
+KEYS = ["perm", "lo", "hi", "parent", "left", "right", "depth", "cut_ptr", "cut_a", "cut_b", "cut_e"]
+
+
+@pytest.mark.parametrize("which,levels,d_th", [
+    ("tile", 2, 0), ("tile", 0, 74), ("tile", 0, 10), ("tile", 0, 2), ("tiles8", 3, 0), ("tiles8", 0, 100),
+    ("small5", 2, 0), ("small13", 3, 0), ("small37", 0, 7), ("small2", 1, 0)])
+def test_partition_bit_exact_with_oracle(L, which, levels, d_th):
+    if which == "tile":
+        net = netgen.tile(1_000_000)
+    elif which == "tiles8":
+        net = netgen.tiled(2, 4)
+    else:
+        net = netgen.small_network(int(which[5:]), 77)
+    got = L.emt_tree_build(net["n_bus"], net["br_a"], net["br_b"], levels=levels, d_th=d_th)
+    ref = opart.build_tree(net["n_bus"], net["br_a"], net["br_b"], levels=levels, d_th=d_th)
+    for k in KEYS:
+        assert np.array_equal(got[k], np.asarray(ref[k])), k
+
+
+def test_partition_bit_exact_64_tiles(L):
+    net = netgen.config_network(4)
+    got = L.emt_tree_build(net["n_bus"], net["br_a"], net["br_b"], levels=4)
+    ref = opart.build_tree(net["n_bus"], net["br_a"], net["br_b"], levels=4)
+    for k in KEYS:
+        assert np.array_equal(got[k], np.asarray(ref[k])), k
+
+
+def test_partition_rejects_bad_input(L):
+    with pytest.raises(L.EmtError) as e:
+        L.emt_tree_build(4, [0, 1], [1, 7], levels=1)
+    assert e.value.code == L.EMT_ERR_INVALID
+    with pytest.raises(L.EmtError):
+        L.emt_tree_build(4, [0], [1], levels=0, d_th=0)
