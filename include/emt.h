@@ -183,6 +183,20 @@ emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out);
 /* Tuning knob for the fused single-column kernels: rows of the leaf blocks per CTA
  * (0 = automatic). Takes effect on the next emt_step. */
 emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
+/* Return the simulation to its state right after emt_sim_create: stored inverse restored
+ * (every modification undone), voltages and history zeroed, step counter 0; scheduled events
+ * and the monitor list are kept. Asynchronous on `stream`. */
+emt_status emt_sim_reset(emt_sim* s, void* stream);
+/* Sizes of the simulation, for byte/FLOP accounting. out[0..n): n_bus, n_leaf, leaf elements
+ * (sum b_j^2), factor elements (sum n_q k_q), core elements (sum (2k_q)^2), CTAs of the fused
+ * kernels, element incidences, distinct cut rows, boundary-vector length (sum 2k_q), kernels
+ * launched by emt_step/emt_sim_reset since creation, series branches, elements. */
+emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
+/* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
+ * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the
+ * sweep/expansion kernel. Leaves the simulation state undefined: call emt_sim_reset
+ * afterwards. Asynchronous on `stream`. */
+emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream);
 void emt_sim_destroy(emt_sim* s);
 
 #ifdef __cplusplus

@@ -90,6 +90,9 @@ def _load():
         "emt_sim_read": (C.c_int, [vp, C.c_int32, _f64p]),
         "emt_sim_set_rows_per_cta": (C.c_int, [vp, C.c_int32]),
         "emt_sim_destroy": (None, [vp]),
+        "emt_sim_reset": (C.c_int, [vp, vp]),
+        "emt_sim_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int32]),
+        "emt_sim_bench_kernel": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -102,7 +105,8 @@ lib = _load()
 EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes", "emt_tree_arrays", "emt_tree_destroy",
             "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
-            "emt_sim_set_rows_per_cta", "emt_sim_destroy")
+            "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
+            "emt_sim_bench_kernel")
 
 
 def _check(code):
@@ -281,3 +285,21 @@ def emt_sim_read(s: Sim, what=0):
 
 def emt_sim_set_rows_per_cta(s: Sim, rows):
     _check(lib.emt_sim_set_rows_per_cta(s.h, int(rows)))
+
+
+def emt_sim_reset(s: Sim, stream=None):
+    _check(lib.emt_sim_reset(s.h, _stream(stream)))
+
+
+STAT_KEYS = ("n_bus", "n_leaf", "leaf_elems", "factor_elems", "core_elems", "n_cta", "n_incidence", "n_cut_rows",
+             "s_total", "launches", "n_series", "n_elements")
+
+
+def emt_sim_stats(s: Sim):
+    out = (C.c_int64 * len(STAT_KEYS))()
+    _check(lib.emt_sim_stats(s.h, out, len(STAT_KEYS)))
+    return dict(zip(STAT_KEYS, [int(x) for x in out]))
+
+
+def emt_sim_bench_kernel(s: Sim, which, reps, stream=None):
+    _check(lib.emt_sim_bench_kernel(s.h, int(which), int(reps), _stream(stream)))

@@ -229,6 +229,27 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
   });
 }
 
+emt_status emt_sim_reset(emt_sim* s, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    s->sim->reset(as_stream(stream));
+  });
+}
+
+emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim && out && n >= 0, EMT_ERR_INVALID, "null argument");
+    s->sim->stats(out, n);
+  });
+}
+
+emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    s->sim->bench_kernel(which, reps, as_stream(stream));
+  });
+}
+
 void emt_sim_destroy(emt_sim* s) { delete s; }
 
 }  // extern "C"

@@ -165,11 +165,40 @@ void launch_steps(Sim& sm, int n, cudaStream_t s) {
   EMT_CUDA(cudaGetLastError());
 }
 
+template <int PREC>
+void launch_bench(Sim& sm, int which, int reps, cudaStream_t s) {
+  using X = typename Acc<PREC>::X;
+  using T = typename Acc<PREC>::T;
+  const Store& st = *sm.store;
+  const FusedPlan& p = sm.plan;
+  const DStore v = st.view();
+  const CtaMapD cm = p.cmap();
+  const CutRowsD cr = p.crows();
+  const SimD sd = sm.view();
+  X* part = reinterpret_cast<X*>(p.part.p);
+  const T* gn = PREC == EMT_PREC_FP64 ? reinterpret_cast<const T*>(p.cut_gn64.p)
+                : PREC == EMT_PREC_FF64 ? reinterpret_cast<const T*>(p.cut_gnff.p)
+                                        : reinterpret_cast<const T*>(p.cut_gn32.p);
+  for (int i = 0; i < reps; ++i) {
+    if (which == 0) k_step_partial<PREC><<<p.n_cta, kFusedThreads, p.smem_partial, s>>>(v, cm, sd, 0, 0, part);
+    else k_step_sweep<PREC><<<p.n_cta, kFusedThreads, p.smem_sweep, s>>>(v, cm, cr, sd, 0, 0, 0, part, gn);
+  }
+  EMT_CUDA(cudaGetLastError());
+}
+
 void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
   switch (sm.store->precision) {
     case EMT_PREC_FP64: launch_steps<EMT_PREC_FP64>(sm, n, s); break;
     case EMT_PREC_FF64: launch_steps<EMT_PREC_FF64>(sm, n, s); break;
     default: launch_steps<EMT_PREC_FP32>(sm, n, s); break;
+  }
+}
+
+void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
+  switch (sm.store->precision) {
+    case EMT_PREC_FP64: launch_bench<EMT_PREC_FP64>(sm, which, reps, s); break;
+    case EMT_PREC_FF64: launch_bench<EMT_PREC_FF64>(sm, which, reps, s); break;
+    default: launch_bench<EMT_PREC_FP32>(sm, which, reps, s); break;
   }
 }
 
@@ -327,6 +356,12 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
   d_dyn.alloc(1);
   EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
   make_plan(*store, 0, plan, s);
+  base.save(*store, s);
+  inc_g0.upload(ig, s);
+  inc_alpha0.upload(ial, s);
+  inc_beta0.upload(ibe, s);
+  el_g0 = el_g;
+  launches_per_step = store->precision == EMT_PREC_FP32 ? 4 : 2;
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   EMT_CUDA(cudaStreamSynchronize(s));
   EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
@@ -334,6 +369,7 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
 
 Sim::~Sim() {
   for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second);
   if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 
@@ -451,9 +487,13 @@ void Sim::run(int n_steps, cudaStream_t s) {
         it = graphs.emplace(kChunk, ge).first;
       }
       EMT_CUDA(cudaGraphLaunch(it->second, s));
+      launches += (int64_t)kChunk * launches_per_step + 1;
       left -= kChunk;
     }
-    if (left > 0) launch_steps_any(*this, left, s);
+    if (left > 0) {
+      launch_steps_any(*this, left, s);
+      launches += (int64_t)left * launches_per_step + 1;
+    }
     cur_step += stretch;
     done += stretch;
   }
@@ -464,7 +504,64 @@ void Sim::step(int n_steps, double* record_dev, cudaStream_t s) {
   if (n_steps == 0) return;
   k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
   EMT_CUDA(cudaGetLastError());
+  launches += 1;
   run(n_steps, s);
+}
+
+void Sim::reset(cudaStream_t s) {
+  base.restore(*store, s);
+  refresh_plan_values(*store, plan, s);
+  const size_t ni = inc_g.n;
+  EMT_CUDA(cudaMemcpyAsync(inc_g.p, inc_g0.p, ni * 8, cudaMemcpyDeviceToDevice, s));
+  EMT_CUDA(cudaMemcpyAsync(inc_alpha.p, inc_alpha0.p, ni * 8, cudaMemcpyDeviceToDevice, s));
+  EMT_CUDA(cudaMemcpyAsync(inc_beta.p, inc_beta0.p, ni * 8, cudaMemcpyDeviceToDevice, s));
+  Ih.zero(s);
+  v_pos.zero(s);
+  x_pos.zero(s);
+  EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
+  el_g = el_g0;
+  snapshots.clear();
+  cur_step = 0;
+  ev_cursor = 0;
+  launches += 4;   // pack (3) + -g refresh
+}
+
+void Sim::stats(int64_t* out, int n_out) const {
+  const Store& st = *store;
+  int64_t leaf = 0, fac = 0, core = 0;
+  for (int j = 0; j < st.n_leaf; ++j) {
+    const int nd = st.leaf_nodes_h[j];
+    const int64_t b = st.tree.hi[nd] - st.tree.lo[nd];
+    leaf += b * b;
+  }
+  for (int q : st.lvl_nodes_h) {
+    const int64_t k = st.node_k_h[q];
+    fac += (int64_t)(st.tree.hi[q] - st.tree.lo[q]) * k;
+    core += 4 * k * k;
+  }
+  const int64_t v[] = {n, st.n_leaf, leaf, fac, core, plan.n_cta, (int64_t)inc_g.n,
+                       (int64_t)st.cut_rows.crow_pos.size(), st.s_total, launches, n_series,
+                       (int64_t)el_a.size()};
+  for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
+}
+
+void Sim::bench_kernel(int which, int reps, cudaStream_t s) {
+  EMT_REQUIRE(which == 0 || which == 1, EMT_ERR_INVALID, "which must be 0 or 1");
+  EMT_REQUIRE(reps >= 1 && reps <= 100000, EMT_ERR_INVALID, "reps out of range");
+  const int key = which * 1000000 + reps;
+  auto it = bench_graphs.find(key);
+  if (it == bench_graphs.end()) {
+    cudaGraph_t g;
+    EMT_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    launch_bench_any(*this, which, reps, cap_stream);
+    EMT_CUDA(cudaStreamEndCapture(cap_stream, &g));
+    cudaGraphExec_t ge;
+    EMT_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    it = bench_graphs.emplace(key, ge).first;
+  }
+  k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, nullptr);
+  EMT_CUDA(cudaGraphLaunch(it->second, s));
 }
 
 void Sim::read(int what, double* host_out, cudaStream_t s) {

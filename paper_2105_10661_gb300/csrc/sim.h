@@ -62,6 +62,9 @@ class Sim {
   void set_rows_per_cta(int rpc, cudaStream_t s);
   void step(int n_steps, double* record_dev, cudaStream_t s);
   void read(int what, double* host_out, cudaStream_t s);
+  void reset(cudaStream_t s);
+  void stats(int64_t* out, int n) const;
+  void bench_kernel(int which, int reps, cudaStream_t s);
   SimD view() const;
 
   static constexpr int kChunk = 64;
@@ -80,7 +83,13 @@ class Sim {
   size_t ev_cursor = 0;
   std::map<int, Snapshot> snapshots;
   std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraphExec_t> bench_graphs;
   cudaStream_t cap_stream = nullptr;
+  Snapshot base;                               // store right after construction
+  DevBuf<double> inc_g0, inc_alpha0, inc_beta0;
+  std::vector<double> el_g0;
+  int64_t launches = 0;                        // kernels enqueued by step/reset
+  int launches_per_step = 2;
 
  private:
   void run(int n_steps, cudaStream_t s);
