@@ -123,6 +123,26 @@ emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nr
 emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double delta_g,
                              void* stream);
 
+/* Scratch reserved by emt_apply_noalloc on every GPU that loads this library, for the
+ * life of the process. */
+#define EMT_APPLY_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* v = G^{-1} i for one vector, like emt_apply with nrhs = 1 and no refinement, but the call
+ * allocates no memory at all (no cudaMalloc, no host allocation). It is for callers that cannot
+ * allocate once they are running, such as a real-time simulator loop that reserves all its memory
+ * at start-up. The paper has no counterpart; it is a deployment convenience. The handle must come
+ * from emt_build_hinv (which does allocate, once). The kernels keep their scratch, the per-CTA
+ * partial sums of the leaf stage, in one fixed device array of EMT_APPLY_NOALLOC_SCRATCH_BYTES
+ * (4 MiB). A store that would need more than that (n_leaf * ceil(max_leaf / 32) * max_leaf * 8
+ * bytes) is rejected with EMT_ERR_UNSUPPORTED and a message; use emt_apply for it. FP32 stores
+ * return the unrefined FP32 result. i_dev, v_dev: device, n_bus doubles each, bus order.
+ * The first call on each device looks up the array's device address and sets kernel attributes.
+ * Make that first call before any stream capture on that device. All calls share the array.
+ * Calls that overlap on the GPU race on it: serialise calls across streams and handles. Each
+ * call rewrites every scratch entry it reads, so nothing has to be cleared between calls.
+ * Asynchronous on `stream`. */
+emt_status emt_apply_noalloc(const emt_hinv* h, const double* i_dev, double* v_dev, void* stream);
+
 /* Wait for the handle's work on `stream` and return its device status. */
 emt_status emt_hinv_sync(emt_hinv* h, void* stream);
 void emt_hinv_destroy(emt_hinv* h);

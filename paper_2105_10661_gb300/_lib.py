@@ -93,6 +93,7 @@ def _load():
         "emt_sim_reset": (C.c_int, [vp, vp]),
         "emt_sim_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int32]),
         "emt_sim_bench_kernel": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
+        "emt_apply_noalloc": (C.c_int, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -106,7 +107,7 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
-            "emt_sim_bench_kernel")
+            "emt_sim_bench_kernel", "emt_apply_noalloc")
 
 
 def _check(code):
@@ -226,6 +227,11 @@ def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, pre
 def emt_apply(h: HInv, i_dev, v_dev, nrhs=1, ld=None, max_refine=0, tol=0.0, stream=None):
     _check(lib.emt_apply(h.h, _ptr(i_dev), _ptr(v_dev), int(nrhs), int(ld if ld is not None else h.n),
                          int(max_refine), float(tol), _stream(stream)))
+
+
+def emt_apply_noalloc(h: HInv, i_dev, v_dev, stream=None):
+    """Single-vector apply that allocates nothing (scratch in a fixed device array)."""
+    _check(lib.emt_apply_noalloc(h.h, _ptr(i_dev), _ptr(v_dev), _stream(stream)))
 
 
 def emt_modify_branch(h: HInv, bus_a, bus_b, delta_g, stream=None):

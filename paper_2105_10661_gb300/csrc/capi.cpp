@@ -11,6 +11,7 @@ thread_local std::string g_last_error;
 void set_last_error(const std::string& m) { g_last_error = m; }
 void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>& rpos, const double* i_dev,
                    double* v_dev, int nrhs, int64_t ld, int max_refine, cudaStream_t s);
+void apply_noalloc(const Store& st, const double* i_dev, double* v_dev, cudaStream_t s);
 }  // namespace emt
 
 struct emt_tree {
@@ -150,6 +151,14 @@ emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nr
       h->has_plan = true;
     }
     emt::apply_vectors(*h->st, h->plan, h->vpos, h->rpos, i_dev, v_dev, nrhs, ld, max_refine, s);
+  });
+}
+
+emt_status emt_apply_noalloc(const emt_hinv* h, const double* i_dev, double* v_dev, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
+    EMT_REQUIRE(i_dev && v_dev, EMT_ERR_INVALID, "null vectors");
+    emt::apply_noalloc(*h->st, i_dev, v_dev, as_stream(stream));
   });
 }
 
