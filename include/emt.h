@@ -203,6 +203,17 @@ emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out);
 /* Tuning knob for the fused single-column kernels: rows of the leaf blocks per CTA
  * (0 = automatic). Takes effect on the next emt_step. */
 emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
+/* Launch-shape tuning of the single-column step kernels: rows of a leaf per CTA (0 = automatic)
+ * and the kernel generation (1 = first generation; 2 = programmatic-dependent-launch kernels with
+ * a TMA-staged sweep image, used when the network fits their shared-memory limits, else 1).
+ * Synchronises the device; takes effect on the next emt_step. */
+emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
+/* Autotuner: time each candidate (rows per CTA in {4..48}, kernel generation 2 then 1) on
+ * probe_steps steps of this simulation, keep the fastest and remember it for every later
+ * simulation of the same network shape in this process (emt_sim_create applies it). Resets the
+ * simulation. Synchronises `stream`. best_rpc / best_kernels (may be NULL) receive the choice. */
+emt_status emt_sim_autotune(emt_sim* s, int32_t probe_steps, int32_t* best_rpc, int32_t* best_kernels,
+                            void* stream);
 /* Return the simulation to its state right after emt_sim_create: stored inverse restored
  * (every modification undone), voltages and history zeroed, step counter 0; scheduled events
  * and the monitor list are kept. Asynchronous on `stream`. */

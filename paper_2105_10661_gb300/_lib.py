@@ -94,6 +94,8 @@ def _load():
         "emt_sim_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.c_int32]),
         "emt_sim_bench_kernel": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
         "emt_apply_noalloc": (C.c_int, [vp, vp, vp, vp]),
+        "emt_sim_tune": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "emt_sim_autotune": (C.c_int, [vp, C.c_int32, _i32p, _i32p, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -107,7 +109,7 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
-            "emt_sim_bench_kernel", "emt_apply_noalloc")
+            "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune")
 
 
 def _check(code):
@@ -309,3 +311,13 @@ def emt_sim_stats(s: Sim):
 
 def emt_sim_bench_kernel(s: Sim, which, reps, stream=None):
     _check(lib.emt_sim_bench_kernel(s.h, int(which), int(reps), _stream(stream)))
+
+
+def emt_sim_tune(s: Sim, rows_per_cta=0, kernels=2):
+    _check(lib.emt_sim_tune(s.h, int(rows_per_cta), int(kernels)))
+
+
+def emt_sim_autotune(s: Sim, probe_steps=256, stream=None):
+    r, k = C.c_int32(), C.c_int32()
+    _check(lib.emt_sim_autotune(s.h, int(probe_steps), C.byref(r), C.byref(k), _stream(stream)))
+    return r.value, k.value

@@ -174,6 +174,11 @@ void make_plan(const Store& st, int rows_per_cta, FusedPlan& p, cudaStream_t s) 
   p.max_rows = 0;
   for (int c = 0; c < p.n_cta; ++c) p.max_rows = std::max(p.max_rows, c1v[c] - c0v[c]);
   p.pld = (maxb + 3) / 4 * 4;
+  p.h_cta_leaf = cl;
+  p.h_cta_r0 = c0v;
+  p.h_cta_r1 = c1v;
+  p.h_leaf_cta0 = lc0;
+  p.h_leaf_ncta = lnc;
   p.cta_leaf.upload(cl, s);
   p.cta_r0.upload(c0v, s);
   p.cta_r1.upload(c1v, s);

@@ -4,6 +4,7 @@
 #include <string>
 
 #include "plan.h"
+#include "multi.h"
 #include "sim.h"
 
 namespace emt {
@@ -27,7 +28,9 @@ struct emt_hinv {
 };
 
 struct emt_sim {
-  std::unique_ptr<emt::Sim> sim;
+  std::unique_ptr<emt::Sim> sim;     // one column
+  std::unique_ptr<emt::MSim> msim;   // several columns
+  bool ok() const { return sim || msim; }
 };
 
 namespace {
@@ -189,42 +192,47 @@ emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, dou
     EMT_REQUIRE(out, EMT_ERR_INVALID, "null output handle");
     *out = nullptr;
     std::unique_ptr<emt_sim> h(new emt_sim);
-    h->sim.reset(new emt::Sim(net, opts, dt, nrhs, src_scale, load_scale, as_stream(stream)));
+    if (nrhs > 1) h->msim.reset(new emt::MSim(net, opts, dt, nrhs, src_scale, load_scale, as_stream(stream)));
+    else h->sim.reset(new emt::Sim(net, opts, dt, nrhs, src_scale, load_scale, as_stream(stream)));
     *out = h.release();
   });
 }
 
 emt_status emt_sim_schedule(emt_sim* s, int32_t step, int32_t kind, int32_t target, double value, int32_t column) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
-    s->sim->schedule(step, kind, target, value, column);
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    if (s->msim) s->msim->schedule(step, kind, target, value, column);
+    else s->sim->schedule(step, kind, target, value, column);
   });
 }
 
 emt_status emt_sim_monitor(emt_sim* s, int32_t n_mon, const int32_t* buses) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
-    s->sim->set_monitor(n_mon, buses, nullptr);
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    if (s->msim) s->msim->set_monitor(n_mon, buses);
+    else s->sim->set_monitor(n_mon, buses, nullptr);
   });
 }
 
 emt_status emt_step(emt_sim* s, int32_t n_steps, double* record_dev, void* stream) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
-    s->sim->step(n_steps, record_dev, as_stream(stream));
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    if (s->msim) s->msim->step(n_steps, record_dev, as_stream(stream));
+    else s->sim->step(n_steps, record_dev, as_stream(stream));
   });
 }
 
 emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out) {
   emt_status r = guard([&] {
-    EMT_REQUIRE(s && s->sim && host_out, EMT_ERR_INVALID, "null argument");
-    s->sim->read(what, host_out, nullptr);
+    EMT_REQUIRE(s && s->ok() && host_out, EMT_ERR_INVALID, "null argument");
+    if (s->msim) s->msim->read(what, host_out);
+    else s->sim->read(what, host_out, nullptr);
   });
   if (r != EMT_OK) return r;
   int dev = 0;
   r = guard([&] {
     EMT_CUDA(cudaDeviceSynchronize());
-    dev = s->sim->store->device_status(nullptr);
+    dev = s->msim ? s->msim->store->device_status(nullptr) : s->sim->store->device_status(nullptr);
   });
   if (r != EMT_OK) return r;
   return status_from_device(dev);
@@ -238,17 +246,38 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
   });
 }
 
-emt_status emt_sim_reset(emt_sim* s, void* stream) {
+emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
   return guard([&] {
     EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
-    s->sim->reset(as_stream(stream));
+    EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
+    s->sim->tune(rows_per_cta, kernels, nullptr);
+  });
+}
+
+emt_status emt_sim_autotune(emt_sim* s, int32_t probe_steps, int32_t* best_rpc, int32_t* best_kernels,
+                            void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    int r = 0, k = 0;
+    s->sim->autotune(probe_steps, &r, &k, as_stream(stream));
+    if (best_rpc) *best_rpc = r;
+    if (best_kernels) *best_kernels = k;
+  });
+}
+
+emt_status emt_sim_reset(emt_sim* s, void* stream) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    if (s->msim) s->msim->reset(as_stream(stream));
+    else s->sim->reset(as_stream(stream));
   });
 }
 
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim && out && n >= 0, EMT_ERR_INVALID, "null argument");
-    s->sim->stats(out, n);
+    EMT_REQUIRE(s && s->ok() && out && n >= 0, EMT_ERR_INVALID, "null argument");
+    if (s->msim) s->msim->stats(out, n);
+    else s->sim->stats(out, n);
   });
 }
 

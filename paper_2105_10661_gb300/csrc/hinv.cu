@@ -621,7 +621,7 @@ void Store::setup_layout(cudaStream_t s) {
       EMT_REQUIRE(2 * k <= kMaxCoreDim, EMT_ERR_UNSUPPORTED,
                   "a tree node cuts more than 80 branches; use more levels or a smaller d_th");
       node_k_h[p] = k;
-      node_kld_h[p] = (k + 1) / 2 * 2;
+      node_kld_h[p] = (k + 3) / 4 * 4;   // 16-byte rows in every precision
       node_foff_h[p] = foff;
       foff += (int64_t)(t.hi[p] - t.lo[p]) * node_kld_h[p];
       node_coff_h[p] = coff;

@@ -1,0 +1,810 @@
+// Multi-column EMT stepping (see multi.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+
+#include "multi.h"
+
+namespace emt {
+
+namespace {
+
+// ------------------------------------------------------------------ float-float helpers
+__device__ __forceinline__ float2 ff_n(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+__device__ __forceinline__ float2 ff_addx(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return ff_n(s, __fadd_rn(err, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 ff_mulx(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  return ff_n(p, e);
+}
+__device__ __forceinline__ float2 ff_negx(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_subx(float2 a, float2 b) { return ff_addx(a, ff_negx(b)); }
+__device__ __forceinline__ float2 ff_f(float x) { return make_float2(x, 0.f); }
+
+float2 host_ff(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// sweep metadata header (ints)
+enum {
+  M_NCROW = 0, M_NITEMS, M_STOTAL, M_MAXD, M_NCORE, M_OFF_CROW, M_OFF_LVL_ITEM, M_OFF_ITEM, M_OFF_SEG,
+  M_OFF_LVL_CORE, M_OFF_CORE, M_HEADER = 16
+};
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_mc_trig(float2* trig, int first_step, int n, double omega, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s, c;
+  sincos(omega * ((double)(first_step + i) * dt), &s, &c);
+  const float sh = (float)s, ch = (float)c;
+  trig[2 * i] = make_float2(sh, (float)(s - (double)sh));
+  trig[2 * i + 1] = make_float2(ch, (float)(c - (double)ch));
+}
+
+// history update of every element end and injection, one (position, column) per thread
+__global__ void __launch_bounds__(128) k_mc_inject(MSimD m, int s_in_chunk, int* status) {
+  const int pos = blockIdx.x;
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= m.R || *status != DEV_OK) return;
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  const bool trip = m.trip_step[c] > 0 && step >= m.trip_step[c];
+  const int te = m.trip_elem[c];
+  const int64_t R = m.R;
+  const float2 vi = m.V[pos * R + c];
+  float2 hist = ff_f(0.f);
+  for (int k = m.inc_ptr[pos]; k < m.inc_ptr[pos + 1]; ++k) {
+    const MRec rec = m.inc[k];
+    if (trip && rec.elem == te) {
+      m.Ih[k * R + c] = ff_f(0.f);
+      continue;
+    }
+    const float2 vo = rec.other >= 0 ? m.V[(int64_t)rec.other * R + c] : ff_f(0.f);
+    const float2 ve = rec.sgn > 0 ? ff_subx(vi, vo) : ff_subx(vo, vi);
+    const float2 cur = ff_addx(ff_mulx(rec.g, ve), m.Ih[k * R + c]);
+    const float2 Ihn = ff_addx(ff_mulx(rec.alpha, ve), ff_mulx(rec.beta, cur));
+    m.Ih[k * R + c] = Ihn;
+    hist = rec.sgn > 0 ? ff_subx(hist, Ihn) : ff_addx(hist, Ihn);
+  }
+  const int ti = step - m.dyn->trig_first;
+  const float2 sw = m.trig[2 * ti], cw = m.trig[2 * ti + 1];
+  float2 inj = ff_f(0.f);
+  for (int t = m.term_ptr[pos]; t < m.term_ptr[pos + 1]; ++t)
+    inj = ff_addx(inj, ff_addx(ff_mulx(m.term_cs[t * R + c], sw), ff_mulx(m.term_sn[t * R + c], cw)));
+  const float2 x = ff_addx(inj, hist);
+  m.X[pos * R + c] = x;
+  m.Xf[pos * R + c] = x.x;
+}
+
+// Leaf stage as a GEMM over the columns: Y[leaf rows] = L_j (FP32) * Xf[leaf rows].
+// Tile 64 x 128, K step 16, 256 threads with an 8 x 4 register tile.
+constexpr int GBM = 64, GBN = 128, GBK = 16;
+__global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restrict__ tiles,
+                                                 const float* __restrict__ Xf, float* __restrict__ Y, int R,
+                                                 const int* status) {
+  __shared__ __align__(16) float As[GBK][GBM + 4];
+  __shared__ __align__(16) float Bs[GBK][GBN + 4];
+  if (*status != DEV_OK) return;
+  const int4 tl = tiles[blockIdx.x];
+  const int j = tl.x, m0 = tl.y, n0 = tl.z;
+  const int node = st.leaf_node[j];
+  const int lo = st.lo[node], b = st.hi[node] - lo, ld = st.leaf_ld[j];
+  const float* L = st.L32 + st.leaf_off[j];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 5, tx = tid & 31;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
+  for (int k0 = 0; k0 < b; k0 += GBK) {
+    {
+      const int row = tid >> 2, kq = (tid & 3) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m0 + row < b && k0 + kq < ld) v = __ldg(reinterpret_cast<const float4*>(L + (int64_t)(m0 + row) * ld + k0 + kq));
+      As[kq + 0][row] = v.x;
+      As[kq + 1][row] = v.y;
+      As[kq + 2][row] = v.z;
+      As[kq + 3][row] = v.w;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int kk = (tid >> 5) + 8 * h, nn = (tid & 31) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k0 + kk < b) {
+        const float* src = Xf + (int64_t)(lo + k0 + kk) * R + n0 + nn;
+        if ((R & 3) == 0 && n0 + nn + 3 < R) v = *reinterpret_cast<const float4*>(src);
+        else {
+          if (n0 + nn + 0 < R) v.x = src[0];
+          if (n0 + nn + 1 < R) v.y = src[1];
+          if (n0 + nn + 2 < R) v.z = src[2];
+          if (n0 + nn + 3 < R) v.w = src[3];
+        }
+      }
+      *reinterpret_cast<float4*>(&Bs[kk][nn]) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      float a[8], bv[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      bv[0] = b4.x;
+      bv[1] = b4.y;
+      bv[2] = b4.z;
+      bv[3] = b4.w;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], bv[q], acc[i][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + ty * 8 + i;
+    if (r >= b) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int cc = n0 + tx * 4 + q;
+      if (cc < R) Y[(int64_t)(lo + r) * R + cc] = acc[i][q];
+    }
+  }
+}
+
+// Corrected leaf-stage value at one position for one column (ancestors strictly below depth d
+// when d >= 0, all ancestors when d < 0), from the S computed so far (shared memory, CB columns).
+__device__ __forceinline__ float corrected(const DStore& st, const float* Y, int64_t R, int pos, int c, int cl,
+                                           const float* s_sh, int cb, int d) {
+  float v = Y[pos * R + c];
+  for (int q = st.parent[st.leaf_node[st.pos_leaf[pos]]]; q >= 0 && st.depth[q] > d; q = st.parent[q]) {
+    const int k = st.node_k[q];
+    const int half = pos < st.hi[st.left[q]] ? 0 : k;
+    const float* Fr = st.F32 + st.node_foff[q] + (int64_t)(pos - st.lo[q]) * st.node_kld[q];
+    const int si = st.node_soff[q] + half;
+    for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], s_sh[(si + e) * cb + cl], v);
+  }
+  return v;
+}
+
+// Boundary sweep for a block of columns; writes S (and the N-1 factors when n1 is set).
+__global__ void __launch_bounds__(256) k_mc_sweep(DStore st, MSimD m, int cb, int n1, int s_in_chunk,
+                                                  const int* status) {
+  extern __shared__ __align__(16) float sh[];
+  if (*status != DEV_OK) return;
+  const int c0 = blockIdx.x * cb;
+  const int ncol = min(cb, m.R - c0);
+  const int* M = m.meta;
+  const int n_crow = M[M_NCROW], s_total = M[M_STOTAL], maxd = M[M_MAXD];
+  float* ycut = sh;                         // [n_crow][cb]
+  float* t = ycut + (size_t)n_crow * cb;     // [s_total][cb]
+  float* s = t + (size_t)s_total * cb;       // [s_total][cb]
+  const int64_t R = m.R;
+  const int tid = threadIdx.x;
+  const int* crow_pos = M + M[M_OFF_CROW];
+  for (int w = tid; w < n_crow * cb; w += blockDim.x) {
+    const int k = w / cb, cl = w % cb;
+    ycut[w] = cl < ncol ? m.Y[(int64_t)crow_pos[k] * R + c0 + cl] : 0.f;
+  }
+  __syncthreads();
+  const int* lvl_item = M + M[M_OFF_LVL_ITEM];
+  const int* item = M + M[M_OFF_ITEM];
+  const int* seg = M + M[M_OFF_SEG];
+  const int* lvl_core = M + M[M_OFF_LVL_CORE];
+  const int* core = M + M[M_OFF_CORE];
+  for (int d = maxd - 1; d >= 0; --d) {
+    const int i0 = lvl_item[d], i1 = lvl_item[d + 1];
+    for (int w = i0 * cb + tid; w < i1 * cb; w += blockDim.x) {
+      const int it = w / cb, cl = w % cb;
+      const int* rec = item + 5 * it;
+      float v = ycut[rec[0] * cb + cl];
+      for (int sg = rec[3]; sg < rec[3] + rec[4]; ++sg) {
+        const int si = seg[3 * sg], k = seg[3 * sg + 1];
+        const float* Fr = st.F32 + seg[3 * sg + 2];
+        for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], s[(si + e) * cb + cl], v);
+      }
+      if (rec[2] >= 0) v *= (float)(-st.cut_g[rec[2]]);
+      t[rec[1] * cb + cl] = v;
+    }
+    __syncthreads();
+    const int j0 = lvl_core[d], j1 = lvl_core[d + 1];
+    for (int w = j0 * cb + tid; w < j1 * cb; w += blockDim.x) {
+      const int cr = w / cb, cl = w % cb;
+      const int* rec = core + 4 * cr;
+      const float* Cr = st.C32 + rec[3];
+      float v = 0.f;
+      for (int e = 0; e < rec[2]; ++e) v = fmaf(Cr[e], t[(rec[1] + e) * cb + cl], v);
+      s[rec[0] * cb + cl] = v;
+    }
+    __syncthreads();
+  }
+  for (int w = tid; w < s_total * cb; w += blockDim.x) {
+    const int r = w / cb, cl = w % cb;
+    if (cl < ncol) m.S[(int64_t)r * R + c0 + cl] = s[w];
+  }
+  if (n1) {
+    const int step = m.dyn->step_base + s_in_chunk + 1;
+    for (int cl = tid; cl < ncol; cl += blockDim.x) {
+      const int c = c0 + cl;
+      float f = 0.f;
+      if (m.trip_step[c] > 0 && step >= m.trip_step[c]) {
+        const float ya = corrected(st, m.Y, R, m.trip_a[c], c, cl, s, cb, -1);
+        const float yb = m.trip_b[c] >= 0 ? corrected(st, m.Y, R, m.trip_b[c], c, cl, s, cb, -1) : 0.f;
+        f = (float)m.trip_coef[c] * (ya - yb);
+      }
+      m.fcol[c] = f;
+    }
+  }
+}
+
+// Expansion (+ N-1 correction): V (pass 0: =, pass 1: +=) and monitored record.
+__global__ void __launch_bounds__(128) k_mc_expand(DStore st, MSimD m, int pass, int n1, int record, int s_in_chunk,
+                                                   const int* status) {
+  const int pos = blockIdx.x;
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= m.R || *status != DEV_OK) return;
+  const int64_t R = m.R;
+  float v = m.Y[pos * R + c];
+  for (int q = st.parent[st.leaf_node[st.pos_leaf[pos]]]; q >= 0; q = st.parent[q]) {
+    const int k = st.node_k[q];
+    const int half = pos < st.hi[st.left[q]] ? 0 : k;
+    const float* Fr = st.F32 + st.node_foff[q] + (int64_t)(pos - st.lo[q]) * st.node_kld[q];
+    const float* Sq = m.S + (int64_t)(st.node_soff[q] + half) * R + c;
+    for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], Sq[e * R], v);
+  }
+  if (n1) {
+    const float f = m.fcol[c];
+    if (f != 0.f) v = fmaf(-f, m.Z[pos * R + c].x, v);
+  }
+  float2 out = pass == 0 ? ff_f(v) : ff_addx(m.V[pos * R + c], ff_f(v));
+  m.V[pos * R + c] = out;
+  if (record && m.dyn->rec) {
+    const int mi = m.mon_idx[pos];
+    if (mi >= 0) {
+      const int step = m.dyn->step_base + s_in_chunk + 1;
+      m.dyn->rec[((int64_t)(step - m.dyn->rec_first) * R + c) * m.n_mon + mi] = (double)out.x + (double)out.y;
+    }
+  }
+}
+
+// r = x - G' v (float-float), stored as the FP32 input of the correction apply.
+__global__ void __launch_bounds__(128) k_mc_residual(MSimD m, int n1, int s_in_chunk, const int* status) {
+  const int pos = blockIdx.x;
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= m.R || *status != DEV_OK) return;
+  const int64_t R = m.R;
+  float2 r = m.X[pos * R + c];
+  for (int t = m.csr_ptr[pos]; t < m.csr_ptr[pos + 1]; ++t)
+    r = ff_subx(r, ff_mulx(m.csr_ff[t], m.V[(int64_t)m.csr_col[t] * R + c]));
+  if (n1) {
+    const int step = m.dyn->step_base + s_in_chunk + 1;
+    if (m.trip_step[c] > 0 && step >= m.trip_step[c]) {
+      const int a = m.trip_a[c], b = m.trip_b[c];
+      if (pos == a || pos == b) {
+        // (G' v)_i = (G v)_i + delta u_i (v_a - v_b)
+        float2 du = m.V[(int64_t)a * R + c];
+        if (b >= 0) du = ff_subx(du, m.V[(int64_t)b * R + c]);
+        const float2 dl = ff_mulx(m.trip_delta_ff[c], du);
+        r = pos == a ? ff_subx(r, dl) : ff_addx(r, dl);
+      }
+    }
+  }
+  m.Xf[pos * R + c] = r.x;
+}
+
+// d_c = 1 + delta_c u_c^T z_c (FP64) and the Sherman-Morrison factor delta_c / d_c
+__global__ void k_mc_trip_coef(MSimD m, double* coef, int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.R) return;
+  if (m.trip_step[c] <= 0) {
+    coef[c] = 0.0;
+    return;
+  }
+  const int64_t R = m.R;
+  const float2 za = m.Z[(int64_t)m.trip_a[c] * R + c];
+  double ut = (double)za.x + (double)za.y;
+  if (m.trip_b[c] >= 0) {
+    const float2 zb = m.Z[(int64_t)m.trip_b[c] * R + c];
+    ut -= (double)zb.x + (double)zb.y;
+  }
+  const double d = 1.0 + m.trip_delta[c] * ut;
+  if (!(d > 1e-12)) atomicExch(status, DEV_SINGULAR);
+  coef[c] = m.trip_delta[c] / d;
+}
+
+__global__ void k_mc_unit(MSimD m, float2* X, float* Xf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.R || m.trip_step[c] <= 0) return;
+  const int64_t R = m.R;
+  X[(int64_t)m.trip_a[c] * R + c] = ff_f(1.f);
+  Xf[(int64_t)m.trip_a[c] * R + c] = 1.f;
+  if (m.trip_b[c] >= 0) {
+    X[(int64_t)m.trip_b[c] * R + c] = ff_f(-1.f);
+    Xf[(int64_t)m.trip_b[c] * R + c] = -1.f;
+  }
+}
+
+__global__ void k_mc_advance(SimDyn* dyn, int n) { dyn->step_base += n; }
+__global__ void k_mc_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec) {
+  dyn->step_base = step_base;
+  dyn->rec_first = rec_first;
+  dyn->rec = rec;
+  dyn->trig_first = rec_first;
+}
+
+}  // namespace
+
+// ====================================================================== host side
+MSimD MSim::view() const {
+  MSimD d{};
+  d.n = n;
+  d.R = R;
+  d.s_total = store->s_total;
+  d.n_crow = n_crow;
+  d.max_depth = store->tree.max_depth;
+  d.inc = inc.p;
+  d.inc_ptr = inc_ptr.p;
+  d.Ih = Ih.p;
+  d.V = V.p;
+  d.X = X.p;
+  d.Xf = Xf.p;
+  d.Y = Y.p;
+  d.S = S.p;
+  d.fcol = fcol.p;
+  d.term_ptr = term_ptr.p;
+  d.term_cs = term_cs.p;
+  d.term_sn = term_sn.p;
+  d.trig = trig.p;
+  d.trip_step = trip_step.p;
+  d.trip_elem = trip_elem.p;
+  d.trip_a = trip_a.p;
+  d.trip_b = trip_b.p;
+  d.trip_delta = trip_delta.p;
+  d.trip_delta_ff = trip_dff.p;
+  d.trip_coef = trip_coef.p;
+  d.Z = Z.p;
+  d.csr_ptr = store->d_csr_ptr.p;
+  d.csr_col = store->d_csr_col.p;
+  d.csr_ff = csr_ff.p;
+  d.mon_idx = mon_idx.p;
+  d.n_mon = n_mon;
+  d.dyn = d_dyn.p;
+  d.meta = meta.p;
+  return d;
+}
+
+MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_, const double* src_scale,
+           const double* load_scale, cudaStream_t s) {
+  EMT_REQUIRE(net && opts, EMT_ERR_INVALID, "null network or options");
+  EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
+  EMT_REQUIRE(R_ >= 2 && R_ <= 65536, EMT_ERR_INVALID, "nrhs out of range");
+  n = net->n_bus;
+  R = R_;
+  dt = dt_;
+  omega = 2.0 * M_PI * net->freq;
+  const int nb = net->n_branch;
+  std::vector<double> el_al, el_be;
+  for (int e = 0; e < nb; ++e) {
+    const int a = net->from[e], b = net->to[e];
+    EMT_REQUIRE(a >= 0 && a < n && b >= 0 && b < n && a != b, EMT_ERR_INVALID, "series branch endpoints");
+    const double Rr = net->R[e];
+    double g, al, be;
+    if (net->kind[e] == EMT_KIND_RL) {
+      const double x = 2.0 * net->L[e] / dt;
+      g = 1.0 / (Rr + x);
+      al = g;
+      be = g * (x - Rr);
+    } else {
+      EMT_REQUIRE(net->kind[e] == EMT_KIND_RC && net->C[e] > 0, EMT_ERR_INVALID, "bad RC branch");
+      const double x = dt / (2.0 * net->C[e]);
+      g = 1.0 / (Rr + x);
+      al = -g;
+      be = -g * (x - Rr);
+    }
+    EMT_REQUIRE(std::isfinite(g) && g > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
+    el_a.push_back(a);
+    el_b.push_back(b);
+    el_g.push_back(g);
+    el_al.push_back(al);
+    el_be.push_back(be);
+  }
+  n_series = nb;
+  if (net->shunt_C)
+    for (int i = 0; i < n; ++i) {
+      const double C = net->shunt_C[i];
+      if (!(C > 0)) continue;
+      const double g = 2.0 * C / dt;
+      el_a.push_back(i);
+      el_b.push_back(-1);
+      el_g.push_back(g);
+      el_al.push_back(-g);
+      el_be.push_back(-1.0);
+    }
+  std::vector<int32_t> gf(el_a.begin(), el_a.end()), gt(el_b.begin(), el_b.end());
+  std::vector<double> gv(el_g.begin(), el_g.end());
+  for (int k = 0; k < net->n_src; ++k) {
+    EMT_REQUIRE(net->src_bus[k] >= 0 && net->src_bus[k] < n && net->src_Rs[k] > 0, EMT_ERR_INVALID, "bad source");
+    gf.push_back(net->src_bus[k]);
+    gt.push_back(-1);
+    gv.push_back(1.0 / net->src_Rs[k]);
+  }
+  emt_graph gr{n, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
+  emt_hinv_opts o = *opts;
+  o.precision = EMT_PREC_FP32;
+  store.reset(new Store(&gr, &o, s));
+  store->build(s);
+  const Tree& t = store->tree;
+  // element ends by position
+  std::vector<std::vector<int>> at(n);
+  for (size_t e = 0; e < el_a.size(); ++e) {
+    at[t.pos[el_a[e]]].push_back((int)e);
+    if (el_b[e] >= 0) at[t.pos[el_b[e]]].push_back((int)e);
+  }
+  std::vector<int> iptr(n + 1, 0);
+  std::vector<MRec> recs;
+  for (int p = 0; p < n; ++p) {
+    for (int e : at[p]) {
+      MRec r{};
+      const bool is_a = t.pos[el_a[e]] == p;
+      r.self = p;
+      r.other = is_a ? (el_b[e] >= 0 ? t.pos[el_b[e]] : -1) : t.pos[el_a[e]];
+      r.sgn = is_a ? 1 : -1;
+      r.elem = (int)e;
+      r.g = host_ff(el_g[e]);
+      r.alpha = host_ff(el_al[e]);
+      r.beta = host_ff(el_be[e]);
+      recs.push_back(r);
+    }
+    iptr[p + 1] = (int)recs.size();
+  }
+  n_inc = (int)recs.size();
+  inc.upload(recs, s);
+  inc_ptr.upload(iptr, s);
+  // source and load terms with per-column scales
+  struct Term {
+    int pos;
+    double coef, phi;
+    int kind, idx;   // kind 0 source (idx into src arrays), 1 load
+  };
+  std::vector<std::vector<Term>> terms(n);
+  for (int k = 0; k < net->n_src; ++k)
+    terms[t.pos[net->src_bus[k]]].push_back({0, net->src_Vm[k] / net->src_Rs[k], net->src_phi[k], 0, k});
+  for (int k = 0; k < net->n_load; ++k) {
+    EMT_REQUIRE(net->load_bus[k] >= 0 && net->load_bus[k] < n, EMT_ERR_INVALID, "bad load bus");
+    terms[t.pos[net->load_bus[k]]].push_back({0, -net->load_amp[k], net->load_phi[k], 1, k});
+  }
+  std::vector<int> tptr(n + 1, 0);
+  std::vector<float2> tcs, tsn;
+  for (int p = 0; p < n; ++p) {
+    for (auto& tm : terms[p]) {
+      for (int c = 0; c < R; ++c) {
+        double sc = 1.0;
+        if (tm.kind == 0 && src_scale) sc = src_scale[(size_t)c * net->n_src + tm.idx];
+        if (tm.kind == 1 && load_scale) sc = load_scale[(size_t)c * net->n_load + tm.idx];
+        tcs.push_back(host_ff(tm.coef * sc * std::cos(tm.phi)));
+        tsn.push_back(host_ff(tm.coef * sc * std::sin(tm.phi)));
+      }
+    }
+    tptr[p + 1] = tptr[p] + (int)terms[p].size();
+  }
+  if (tcs.empty()) {
+    tcs.push_back(make_float2(0, 0));
+    tsn.push_back(make_float2(0, 0));
+  }
+  term_ptr.upload(tptr, s);
+  term_cs.upload(tcs, s);
+  term_sn.upload(tsn, s);
+  std::vector<float2> cff(store->csr_val.size());
+  for (size_t k = 0; k < cff.size(); ++k) cff[k] = host_ff(store->csr_val[k]);
+  csr_ff.upload(cff, s);
+  // state
+  const size_t nR = (size_t)n * R;
+  Ih.alloc((size_t)n_inc * R);
+  V.alloc(nR);
+  X.alloc(nR);
+  Xf.alloc(nR);
+  Y.alloc(nR);
+  Z.alloc(nR);
+  S.alloc((size_t)std::max(store->s_total, 1) * R);
+  fcol.alloc(R);
+  h_trip_step.assign(R, 0);
+  h_trip_elem.assign(R, -1);
+  trip_step.upload(h_trip_step, s);
+  trip_elem.upload(h_trip_elem, s);
+  trip_a.upload(std::vector<int>(R, 0), s);
+  trip_b.upload(std::vector<int>(R, -1), s);
+  trip_delta.upload(std::vector<double>(R, 0.0), s);
+  trip_dff.upload(std::vector<float2>(R, make_float2(0.f, 0.f)), s);
+  trip_coef.upload(std::vector<double>(R, 0.0), s);
+  mon_idx.upload(std::vector<int>(n, -1), s);
+  d_dyn.alloc(1);
+  EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
+  build_meta(s);
+  reset(s);
+  EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  EMT_CUDA(cudaStreamSynchronize(s));
+  EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
+}
+
+MSim::~MSim() {
+  drop_graphs();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+void MSim::drop_graphs() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+}
+
+void MSim::build_meta(cudaStream_t s) {
+  const Store& st = *store;
+  const Tree& t = st.tree;
+  const CutRows& cr = st.cut_rows;
+  std::vector<int> M(M_HEADER, 0);
+  n_crow = (int)cr.crow_pos.size();
+  M[M_NCROW] = n_crow;
+  M[M_NITEMS] = cr.n_items;
+  M[M_STOTAL] = st.s_total;
+  M[M_MAXD] = t.max_depth;
+  M[M_OFF_CROW] = (int)M.size();
+  for (int p : cr.crow_pos) M.push_back(p);
+  std::vector<int> order(cr.n_items);
+  for (int i = 0; i < cr.n_items; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return t.depth[cr.item_node[x]] < t.depth[cr.item_node[y]]; });
+  M[M_OFF_LVL_ITEM] = (int)M.size();
+  {
+    std::vector<int> lvl(t.max_depth + 2, 0);
+    for (int i = 0; i < cr.n_items; ++i) lvl[t.depth[cr.item_node[i]] + 1]++;
+    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
+    for (int v : lvl) M.push_back(v);
+  }
+  M[M_OFF_ITEM] = (int)M.size();
+  const size_t item_base = M.size();
+  M.resize(M.size() + 5 * (size_t)cr.n_items);
+  std::vector<int> segs;
+  for (int w = 0; w < cr.n_items; ++w) {
+    const int it = order[w];
+    const int q = cr.item_node[it];
+    const int d = t.depth[q];
+    const int ps = cr.item_pos[it];
+    const int k = st.node_k_h[q];
+    const int slot = cr.item_sidx[it] - st.node_soff_h[q];
+    int* rec = &M[item_base + 5 * w];
+    rec[0] = cr.item_crow[it];
+    rec[1] = cr.item_sidx[it];
+    rec[2] = slot < k ? t.cut_ptr[q] + slot : -1;
+    rec[3] = (int)segs.size() / 3;
+    int nseg = 0;
+    for (int a = t.parent[st.leaf_nodes_h[leaf_index_of_pos(st, ps)]]; a >= 0 && t.depth[a] > d; a = t.parent[a]) {
+      const int ka = st.node_k_h[a];
+      if (ka == 0) continue;
+      segs.push_back(st.node_soff_h[a] + (ps < t.hi[t.left[a]] ? 0 : ka));
+      segs.push_back(ka);
+      segs.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * st.node_kld_h[a]));
+      ++nseg;
+    }
+    rec[4] = nseg;
+  }
+  M[M_OFF_SEG] = (int)M.size();
+  for (int v : segs) M.push_back(v);
+  M[M_OFF_LVL_CORE] = (int)M.size();
+  {
+    std::vector<int> lvl(t.max_depth + 2, 0);
+    for (int q : st.lvl_nodes_h) lvl[t.depth[q] + 1] += 2 * st.node_k_h[q];
+    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
+    for (int v : lvl) M.push_back(v);
+  }
+  M[M_OFF_CORE] = (int)M.size();
+  for (int q : st.lvl_nodes_h) {
+    const int m2 = 2 * st.node_k_h[q];
+    for (int r = 0; r < m2; ++r) {
+      M.push_back(st.node_soff_h[q] + r);
+      M.push_back(st.node_soff_h[q]);
+      M.push_back(m2);
+      M.push_back((int)(st.node_coff_h[q] + (int64_t)r * m2));
+    }
+  }
+  meta.upload(M, s);
+  // GEMM tiles over (leaf, row block, column block)
+  std::vector<int4> tiles;
+  for (int j = 0; j < st.n_leaf; ++j) {
+    const int b = t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]];
+    for (int m0 = 0; m0 < b; m0 += GBM)
+      for (int n0 = 0; n0 < R; n0 += GBN) tiles.push_back(make_int4(j, m0, n0, 0));
+  }
+  n_tiles = (int)tiles.size();
+  gemm_tiles.alloc(tiles.size() * 4);
+  EMT_CUDA(cudaMemcpyAsync(gemm_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  // column block of the sweep: as many columns as shared memory allows (<= 32)
+  sweep_cb = 32;
+  while (sweep_cb > 1 && (size_t)(n_crow + 2 * st.s_total) * sweep_cb * 4 > 200 * 1024) sweep_cb /= 2;
+  sweep_smem = (size_t)(n_crow + 2 * st.s_total) * sweep_cb * 4 + 64;
+}
+
+void MSim::schedule(int step, int kind, int target, double value, int column) {
+  (void)value;
+  EMT_REQUIRE(step >= 1, EMT_ERR_INVALID, "event step must be >= 1");
+  EMT_REQUIRE(cur_step == 0 && !z_ready, EMT_ERR_STATE, "multi-column events must be scheduled before stepping");
+  EMT_REQUIRE(kind == EMT_EVENT_TRIP && column >= 0 && column < R, EMT_ERR_UNSUPPORTED,
+              "multi-column simulations take per-column trips only");
+  EMT_REQUIRE(target >= 0 && target < n_series, EMT_ERR_INVALID, "trip target must be a series branch");
+  EMT_REQUIRE(h_trip_step[column] == 0, EMT_ERR_INVALID, "one trip per column");
+  h_trip_step[column] = step;
+  h_trip_elem[column] = target;
+}
+
+void MSim::prepare_trips(cudaStream_t s) {
+  // upload the per-column trips and compute z_c = Ginv u_c (two refined passes) and d_c
+  const Tree& t = store->tree;
+  std::vector<int> ta(R, 0), tb(R, -1);
+  std::vector<double> td(R, 0.0);
+  bool any = false;
+  for (int c = 0; c < R; ++c) {
+    if (h_trip_step[c] <= 0) continue;
+    any = true;
+    const int e = h_trip_elem[c];
+    ta[c] = t.pos[el_a[e]];
+    tb[c] = t.pos[el_b[e]];
+    td[c] = -el_g[e];
+  }
+  trip_step.upload(h_trip_step, s);
+  trip_elem.upload(h_trip_elem, s);
+  trip_a.upload(ta, s);
+  trip_b.upload(tb, s);
+  trip_delta.upload(td, s);
+  {
+    std::vector<float2> tdf(R);
+    for (int c = 0; c < R; ++c) tdf[c] = host_ff(td[c]);
+    trip_dff.upload(tdf, s);
+  }
+  z_ready = true;
+  if (!any) return;
+  const size_t nR = (size_t)n * R;
+  X.zero(s);
+  Xf.zero(s);
+  MSimD d = view();
+  k_mc_unit<<<(R + 127) / 128, 128, 0, s>>>(d, X.p, Xf.p);
+  apply_pass(0, 0, 0, 0, s);
+  const dim3 grid(n, (R + 127) / 128);
+  k_mc_residual<<<grid, 128, 0, s>>>(d, 0, 0, store->d_status.p);
+  apply_pass(1, 0, 0, 0, s);
+  EMT_CUDA(cudaMemcpyAsync(Z.p, V.p, nR * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  k_mc_trip_coef<<<(R + 127) / 128, 128, 0, s>>>(d, trip_coef.p, store->d_status.p);
+  EMT_CUDA(cudaGetLastError());
+  // back to the initial state
+  V.zero(s);
+  X.zero(s);
+  Xf.zero(s);
+}
+
+void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s) {
+  const DStore st = store->view();
+  const MSimD d = view();
+  k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p);
+  static bool attr = false;
+  if (!attr) {
+    EMT_CUDA(cudaFuncSetAttribute(k_mc_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  k_mc_sweep<<<(R + sweep_cb - 1) / sweep_cb, 256, sweep_smem, s>>>(st, d, sweep_cb, n1, s_in_chunk,
+                                                                    store->d_status.p);
+  k_mc_expand<<<dim3(n, (R + 127) / 128), 128, 0, s>>>(st, d, pass, n1, record, s_in_chunk, store->d_status.p);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void MSim::launch_steps(int nst, cudaStream_t s) {
+  const MSimD d = view();
+  const dim3 grid(n, (R + 127) / 128);
+  for (int i = 0; i < nst; ++i) {
+    k_mc_inject<<<grid, 128, 0, s>>>(d, i, store->d_status.p);
+    apply_pass(0, 1, 0, i, s);
+    k_mc_residual<<<grid, 128, 0, s>>>(d, 1, i, store->d_status.p);
+    apply_pass(1, 1, 1, i, s);
+  }
+  k_mc_advance<<<1, 1, 0, s>>>(d_dyn.p, nst);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void MSim::step(int n_steps, double* record_dev, cudaStream_t s) {
+  EMT_REQUIRE(n_steps >= 0, EMT_ERR_INVALID, "n_steps must be >= 0");
+  if (n_steps == 0) return;
+  if (!z_ready) prepare_trips(s);
+  k_mc_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
+  if ((size_t)2 * n_steps > trig.n) trig.alloc((size_t)2 * std::max(n_steps, 1024));
+  k_mc_trig<<<(n_steps + 255) / 256, 256, 0, s>>>(trig.p, cur_step + 1, n_steps, omega, dt);
+  EMT_CUDA(cudaGetLastError());
+  launches += 2;
+  int left = n_steps;
+  while (left >= kChunk) {
+    auto it = graphs.find(kChunk);
+    if (it == graphs.end()) {
+      cudaGraph_t g;
+      EMT_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+      launch_steps(kChunk, cap_stream);
+      EMT_CUDA(cudaStreamEndCapture(cap_stream, &g));
+      cudaGraphExec_t ge;
+      EMT_CUDA(cudaGraphInstantiate(&ge, g, 0));
+      cudaGraphDestroy(g);
+      it = graphs.emplace(kChunk, ge).first;
+    }
+    EMT_CUDA(cudaGraphLaunch(it->second, s));
+    launches += (int64_t)kChunk * 8 + 1;
+    left -= kChunk;
+  }
+  if (left > 0) {
+    launch_steps(left, s);
+    launches += (int64_t)left * 8 + 1;
+  }
+  cur_step += n_steps;
+}
+
+void MSim::reset(cudaStream_t s) {
+  Ih.zero(s);
+  V.zero(s);
+  X.zero(s);
+  Xf.zero(s);
+  EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
+  cur_step = 0;
+}
+
+void MSim::set_monitor(int nm, const int32_t* buses) {
+  EMT_REQUIRE(nm >= 0 && (nm == 0 || buses), EMT_ERR_INVALID, "bad monitor list");
+  std::vector<int> mi(n, -1);
+  for (int k = 0; k < nm; ++k) {
+    EMT_REQUIRE(buses[k] >= 0 && buses[k] < n, EMT_ERR_INVALID, "monitor bus out of range");
+    EMT_REQUIRE(mi[store->tree.pos[buses[k]]] < 0, EMT_ERR_INVALID, "duplicate monitor bus");
+    mi[store->tree.pos[buses[k]]] = k;
+  }
+  EMT_CUDA(cudaDeviceSynchronize());
+  mon_idx.upload(mi, nullptr);
+  n_mon = nm;
+  drop_graphs();
+  EMT_CUDA(cudaDeviceSynchronize());
+}
+
+void MSim::read(int what, double* host_out) {
+  if (what == 1) {
+    host_out[0] = (double)cur_step;
+    return;
+  }
+  EMT_REQUIRE(what == 0, EMT_ERR_INVALID, "unknown read selector");
+  std::vector<float2> vp((size_t)n * R);
+  EMT_CUDA(cudaDeviceSynchronize());
+  EMT_CUDA(cudaMemcpy(vp.data(), V.p, vp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+  for (int p = 0; p < n; ++p)
+    for (int c = 0; c < R; ++c)
+      host_out[(size_t)c * n + store->tree.perm[p]] = (double)vp[(size_t)p * R + c].x + (double)vp[(size_t)p * R + c].y;
+}
+
+void MSim::stats(int64_t* out, int n_out) const {
+  const Store& st = *store;
+  int64_t leaf = 0, fac = 0, core = 0;
+  for (int j = 0; j < st.n_leaf; ++j) {
+    const int nd = st.leaf_nodes_h[j];
+    const int64_t b = st.tree.hi[nd] - st.tree.lo[nd];
+    leaf += b * b;
+  }
+  for (int q : st.lvl_nodes_h) {
+    const int64_t k = st.node_k_h[q];
+    fac += (int64_t)(st.tree.hi[q] - st.tree.lo[q]) * k;
+    core += 4 * k * k;
+  }
+  const int64_t v[] = {n, st.n_leaf, leaf, fac, core, n_tiles, n_inc, n_crow, st.s_total, launches, n_series,
+                       (int64_t)el_a.size()};
+  for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
+}
+
+}  // namespace emt

@@ -1,0 +1,105 @@
+// Multi-column EMT stepping: R independent columns (N-1 contingencies or load/source scenarios)
+// share one stored inverse and step together.
+//
+// Per step, for all columns at once:
+//   inject    element histories and source/load injections (float-float arithmetic)
+//   apply     leaf stage Y = blkdiag(L_j) X as a GEMM over the R columns (FP32 operands, FP32
+//             accumulation), boundary sweep per column block, expansion V = Y - sum F_q S_q;
+//             a column whose branch has tripped adds the Sherman-Morrison term of its own
+//             change, v_c -= (delta_c / d_c) z_c u_c^T y_c with z_c = Ginv u_c and the FP64
+//             denominator d_c = 1 + delta_c u_c^T z_c
+//   refine    residual r = x - G' v in float-float arithmetic (G' includes each column's trip),
+//             a second apply of r, v += c
+// The result is float-float (about 48 significant bits); one refinement pass brings the FP32
+// apply to the accuracy of the FP64 oracle. Per-column trips switch on by step number inside
+// the kernels, so a whole run is a chain of CUDA graphs with no host work between steps.
+#pragma once
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "sim.h"
+
+namespace emt {
+
+struct MRec {
+  int self, other, sgn, elem;
+  float2 g, alpha, beta;   // float-float
+};
+static_assert(sizeof(MRec) == 40, "MRec must be 40 bytes");
+
+struct MSimD {
+  int n, R, s_total, n_crow, max_depth;
+  const MRec* inc;
+  const int* inc_ptr;
+  float2* Ih;           // [n_inc][R]
+  float2* V;            // [n][R]
+  float2* X;            // [n][R]
+  float* Xf;            // [n][R] GEMM input
+  float* Y;             // [n][R] leaf-stage result
+  float* S;             // [s_total][R]
+  float* fcol;          // [R]
+  const int* term_ptr;  // [n + 1]
+  const float2* term_cs;   // [n_terms][R]
+  const float2* term_sn;   // [n_terms][R]
+  const float2* trig;   // [2 * steps] sin, cos (float-float)
+  const int* trip_step; // [R], 0 = none
+  const int* trip_elem; // [R]
+  const int* trip_a;    // [R] positions
+  const int* trip_b;
+  const double* trip_delta;   // [R]
+  const float2* trip_delta_ff;   // [R] the same as float-float
+  const double* trip_coef;    // [R] delta / d
+  const float2* Z;      // [n][R]
+  const int* csr_ptr;
+  const int* csr_col;
+  const float2* csr_ff;
+  const int* mon_idx;
+  int n_mon;
+  SimDyn* dyn;
+  const int* meta;      // sweep metadata (see multi.cu)
+};
+
+class MSim {
+ public:
+  MSim(const emt_network* net, const emt_hinv_opts* opts, double dt, int R, const double* src_scale,
+       const double* load_scale, cudaStream_t s);
+  ~MSim();
+  void schedule(int step, int kind, int target, double value, int column);
+  void set_monitor(int n_mon, const int32_t* buses);
+  void step(int n_steps, double* record_dev, cudaStream_t s);
+  void read(int what, double* host_out);
+  void reset(cudaStream_t s);
+  void stats(int64_t* out, int n) const;
+  MSimD view() const;
+
+  static constexpr int kChunk = 32;
+  std::unique_ptr<Store> store;
+  int n = 0, R = 0, n_series = 0, n_mon = 0, cur_step = 0;
+  double dt = 0, omega = 0;
+  int64_t launches = 0;
+  std::vector<int> el_a, el_b;
+  std::vector<double> el_g;
+  // device
+  DevBuf<MRec> inc;
+  DevBuf<int> inc_ptr, term_ptr, trip_step, trip_elem, trip_a, trip_b, mon_idx, meta, gemm_tiles;
+  DevBuf<float2> Ih, V, X, term_cs, term_sn, trig, Z, csr_ff, trip_dff;
+  DevBuf<float> Xf, Y, S, fcol;
+  DevBuf<double> trip_delta, trip_coef;
+  DevBuf<SimDyn> d_dyn;
+  int n_inc = 0, n_tiles = 0, n_crow = 0, sweep_cb = 32;
+  size_t sweep_smem = 0;
+  std::vector<int> h_trip_step, h_trip_elem;
+  bool z_ready = false;
+  std::map<int, cudaGraphExec_t> graphs;
+  cudaStream_t cap_stream = nullptr;
+
+ private:
+  void build_meta(cudaStream_t s);
+  void prepare_trips(cudaStream_t s);
+  void launch_steps(int n, cudaStream_t s);
+  void apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s);
+  void drop_graphs();
+};
+
+}  // namespace emt

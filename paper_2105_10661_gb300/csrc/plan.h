@@ -16,6 +16,7 @@ struct FusedPlan {
   size_t smem_partial = 0;
   size_t smem_sweep = 0;
   DevBuf<int> cta_leaf, cta_r0, cta_r1, leaf_cta0, leaf_ncta;
+  std::vector<int> h_cta_leaf, h_cta_r0, h_cta_r1, h_leaf_cta0, h_leaf_ncta;   // host copies
   DevBuf<int> item_pos, item_crow, item_sidx, item_cut, item_lvl, crow_pos;
   DevBuf<double> part;       // n_cta x pld entries of 8 bytes (double or float2); FP32 uses half
   DevBuf<double> cut_gn64;   // -g_e per cut, per precision

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 
 #include "plan.h"
 #include "sim.h"
@@ -120,6 +122,7 @@ __global__ void k_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec
   dyn->step_base = step_base;
   dyn->rec_first = rec_first;
   dyn->rec = rec;
+  dyn->trig_first = rec_first;
 }
 // Trip: the element leaves G; its parameters and both history copies are zeroed.
 __global__ void k_open_element(double* g, double* alpha, double* beta, double* Ih, int m0, int m1) {
@@ -187,6 +190,12 @@ void launch_bench(Sim& sm, int which, int reps, cudaStream_t s) {
 }
 
 void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
+  if (sm.use_v2()) {
+    step2_launch_any(sm, n, s);
+    k_advance<<<1, 1, 0, s>>>(sm.d_dyn.p, n);
+    EMT_CUDA(cudaGetLastError());
+    return;
+  }
   switch (sm.store->precision) {
     case EMT_PREC_FP64: launch_steps<EMT_PREC_FP64>(sm, n, s); break;
     case EMT_PREC_FF64: launch_steps<EMT_PREC_FF64>(sm, n, s); break;
@@ -195,6 +204,10 @@ void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
 }
 
 void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
+  if (sm.use_v2()) {
+    step2_bench(sm, which, reps, s);
+    return;
+  }
   switch (sm.store->precision) {
     case EMT_PREC_FP64: launch_bench<EMT_PREC_FP64>(sm, which, reps, s); break;
     case EMT_PREC_FF64: launch_bench<EMT_PREC_FF64>(sm, which, reps, s); break;
@@ -334,6 +347,7 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
     EMT_REQUIRE(net->load_bus[k] >= 0 && net->load_bus[k] < n, EMT_ERR_INVALID, "bad load bus");
     terms[t.pos[net->load_bus[k]]].push_back({-net->load_amp[k], net->load_phi[k]});
   }
+  src_terms = terms;
   std::vector<int> sp(n + 1, 0);
   std::vector<double> sc, sph;
   for (int p = 0; p < n; ++p) {
@@ -362,7 +376,9 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
   inc_beta0.upload(ibe, s);
   el_g0 = el_g;
   launches_per_step = store->precision == EMT_PREC_FP32 ? 4 : 2;
+  s2.build(*this, s);
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  apply_cached_tuning(s);
   EMT_CUDA(cudaStreamSynchronize(s));
   EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
 }
@@ -378,11 +394,91 @@ void Sim::drop_graphs() {
   graphs.clear();
 }
 
-void Sim::set_rows_per_cta(int rpc, cudaStream_t s) {
+void Sim::set_rows_per_cta(int rpc, cudaStream_t s) { tune(rpc, kernels, s); }
+
+void Sim::tune(int rpc, int kern, cudaStream_t s) {
+  EMT_REQUIRE(kern == 1 || kern == 2, EMT_ERR_INVALID, "kernels must be 1 or 2");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
+  for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second);
+  bench_graphs.clear();
   make_plan(*store, rpc, plan, s);
+  s2.ready = false;
+  s2.build(*this, s);
+  kernels = kern;
   EMT_CUDA(cudaDeviceSynchronize());
+}
+
+namespace {
+// Tuned launch shapes per network shape, shared by every simulation of this process.
+struct TuneKey {
+  int n, n_leaf, max_depth, prec, sms;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, n_leaf, max_depth, prec, sms) < std::tie(o.n, o.n_leaf, o.max_depth, o.prec, o.sms);
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mutex;
+TuneKey tune_key(const Sim& sm) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return {sm.n, sm.store->n_leaf, sm.store->tree.max_depth, sm.store->precision, sms};
+}
+}  // namespace
+
+// Time every candidate launch shape on `probe_steps` steps of this simulation and keep the
+// fastest; the choice is cached per network shape for later simulations in this process.
+// The simulation is reset afterwards.
+void Sim::autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream_t s) {
+  EMT_REQUIRE(probe_steps >= 1 && probe_steps <= 100000, EMT_ERR_INVALID, "probe_steps out of range");
+  const int cands[] = {4, 6, 8, 10, 12, 16, 20, 24, 32, 48};
+  cudaEvent_t e0, e1;
+  EMT_CUDA(cudaEventCreate(&e0));
+  EMT_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int brpc = 0, bk = 1;
+  for (int k : {2, 1}) {
+    for (int rpc : cands) {
+      tune(rpc, k, s);
+      if (k == 2 && !s2.ready) continue;
+      reset(s);
+      step(8, nullptr, s);
+      EMT_CUDA(cudaEventRecord(e0, s));
+      step(probe_steps, nullptr, s);
+      EMT_CUDA(cudaEventRecord(e1, s));
+      EMT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      EMT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        brpc = rpc;
+        bk = k;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tune(brpc, bk, s);
+  reset(s);
+  EMT_CUDA(cudaStreamSynchronize(s));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tune_cache[tune_key(*this)] = {brpc, bk};
+  }
+  if (best_rpc) *best_rpc = brpc;
+  if (best_kernels) *best_kernels = bk;
+}
+
+void Sim::apply_cached_tuning(cudaStream_t s) {
+  std::pair<int, int> v;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune_cache.find(tune_key(*this));
+    if (it == g_tune_cache.end()) return;
+    v = it->second;
+  }
+  tune(v.first, v.second, s);
 }
 
 void Sim::set_monitor(int nm, const int32_t* buses, cudaStream_t s) {
@@ -421,6 +517,7 @@ void Sim::apply_event(const Event& ev, cudaStream_t s) {
     const double g = el_g[e];
     st.modify_async(el_a[e], el_b[e], -g, s);
     k_open_element<<<1, 1, 0, s>>>(inc_g.p, inc_alpha.p, inc_beta.p, Ih.p, el_inc[e].first, el_inc[e].second);
+    if (s2.ready) s2.open_element(el_inc[e].first, el_inc[e].second, s);
     el_g[e] = 0.0;
   } else if (ev.kind == EMT_EVENT_FAULT_ON) {
     Snapshot& sn = snapshots[ev.target];
@@ -433,6 +530,7 @@ void Sim::apply_event(const Event& ev, cudaStream_t s) {
     snapshots.erase(it);
   }
   refresh_plan_values(st, plan, s);
+  if (s2.ready) s2.refresh(*this, s);
   EMT_CUDA(cudaGetLastError());
 }
 
@@ -505,6 +603,10 @@ void Sim::step(int n_steps, double* record_dev, cudaStream_t s) {
   k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
   EMT_CUDA(cudaGetLastError());
   launches += 1;
+  if (s2.ready) {
+    s2.fill_trig(*this, cur_step + 1, n_steps, s);
+    launches += 1;
+  }
   run(n_steps, s);
 }
 
@@ -520,6 +622,10 @@ void Sim::reset(cudaStream_t s) {
   x_pos.zero(s);
   EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
   el_g = el_g0;
+  if (s2.ready) {
+    s2.reset_state(s);
+    s2.refresh(*this, s);
+  }
   snapshots.clear();
   cur_step = 0;
   ev_cursor = 0;
@@ -561,6 +667,7 @@ void Sim::bench_kernel(int which, int reps, cudaStream_t s) {
     it = bench_graphs.emplace(key, ge).first;
   }
   k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, nullptr);
+  if (s2.ready) s2.fill_trig(*this, cur_step + 1, 1, s);
   EMT_CUDA(cudaGraphLaunch(it->second, s));
 }
 

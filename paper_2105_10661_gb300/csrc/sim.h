@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "plan.h"
+#include "step2.cuh"
 
 namespace emt {
 
@@ -13,6 +14,8 @@ struct SimDyn {
   int step_base;   // steps completed before the current launch sequence
   int rec_first;   // step number stored at record row 0
   double* rec;     // record buffer of the current emt_step call (may be null)
+  int trig_first;  // step number of row 0 of the sin/cos table
+  int pad;
 };
 
 struct SimD {
@@ -52,6 +55,37 @@ struct Snapshot {
   void restore(Store& st, cudaStream_t s);
 };
 
+class Sim;
+
+// Plan and device data of the second-generation step kernels (step2.cu).
+struct Step2 {
+  bool ready = false;
+  int prec = 0;
+  int max_inc = 0;
+  int max_lnc = 0;
+  int core_bytes = 0;
+  int n_seg_copy = 0;
+  size_t smem_static = 0, smem_sweep = 0, smem_partial = 0;
+  ImgHeader header{};
+  std::vector<IncRec> inc0;
+  DevBuf<IncRec> inc;
+  DevBuf<SrcRec> d_src;
+  DevBuf<double2> d_src_sum;
+  DevBuf<int> d_src_ptr;
+  DevBuf<double> trig;
+  DevBuf<double> img;
+  DevBuf<int> seg_src_d, seg_dst_d, seg_len_d;
+  DevBuf<OwnCopy> own_d;
+  bool build(const Sim& sm, cudaStream_t s);
+  void refresh(const Sim& sm, cudaStream_t s);
+  void reset_state(cudaStream_t s);
+  void fill_trig(const Sim& sm, int first_step, int n, cudaStream_t s);
+  void open_element(int m0, int m1, cudaStream_t s);
+  Step2D view(const Sim& sm) const;
+};
+void step2_launch_any(Sim& sm, int n, cudaStream_t s);
+void step2_bench(Sim& sm, int which, int reps, cudaStream_t s);
+
 class Sim {
  public:
   Sim(const emt_network* net, const emt_hinv_opts* opts, double dt, int nrhs, const double* src_scale,
@@ -60,6 +94,9 @@ class Sim {
   void schedule(int step, int kind, int target, double value, int column);
   void set_monitor(int n_mon, const int32_t* buses, cudaStream_t s);
   void set_rows_per_cta(int rpc, cudaStream_t s);
+  void tune(int rpc, int kernels, cudaStream_t s);
+  void autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream_t s);
+  void apply_cached_tuning(cudaStream_t s);
   void step(int n_steps, double* record_dev, cudaStream_t s);
   void read(int what, double* host_out, cudaStream_t s);
   void reset(cudaStream_t s);
@@ -90,6 +127,10 @@ class Sim {
   std::vector<double> el_g0;
   int64_t launches = 0;                        // kernels enqueued by step/reset
   int launches_per_step = 2;
+  std::vector<std::vector<std::pair<double, double>>> src_terms;   // per position: (coef, phi)
+  Step2 s2;
+  int kernels = 2;                             // 1: first-generation step kernels, 2: step2
+  bool use_v2() const { return kernels == 2 && s2.ready; }
 
  private:
   void run(int n_steps, cudaStream_t s);

@@ -155,15 +155,15 @@ def test_paper_modify_matches_algorithm2(L):
         assert rel_err(_apply(L, h, X), H.apply(X)) <= 1e-10
 
 
-def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rpc=0):
+def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rpc=0, kernels=2):
     nw = oemt.Network(net, DT, levels=levels)
     oev = []
     for (st, kind, tgt, val) in events:
         oev.append((st, kind, tgt, val))
     ref, _ = oemt.simulate(nw, steps, oev, solver=solver)
     sim = L.emt_sim_create(net, DT, levels=levels, mode=mode, precision=prec)
-    if rpc:
-        L.emt_sim_set_rows_per_cta(sim, rpc)
+    if rpc or kernels != 2:
+        L.emt_sim_tune(sim, rpc, kernels)
     L.emt_sim_monitor(sim, np.arange(net["n_bus"]))
     for (st, kind, tgt, val) in events:
         L.emt_sim_schedule(sim, st, kind, tgt, val)
@@ -179,19 +179,21 @@ def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rp
     return rel_err(got, ref)
 
 
+@pytest.mark.parametrize("kernels", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1, 2])
-def test_sim_179_bus_trip_matches_oracle(L, prec):
+def test_sim_179_bus_trip_matches_oracle(L, prec, kernels):
     net = netgen.tile(1_000_000)
     e = netgen.pick_branch(net)
-    err = _sim_compare(L, net, 2, 150, [(70, 0, e, 0.0)], prec)
+    err = _sim_compare(L, net, 2, 150, [(70, 0, e, 0.0)], prec, kernels=kernels)
     assert err <= TOL[prec], err
 
 
-@pytest.mark.parametrize("rpc", [0, 7, 64, 179])
-def test_sim_fault_on_off_and_cta_shapes(L, rpc):
+@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("rpc", [0, 7, 16, 64, 179])
+def test_sim_fault_on_off_and_cta_shapes(L, rpc, kernels):
     net = netgen.tile(1_000_000)
     ev = [(30, 1, 17, 10.0), (90, 2, 17, 0.0), (100, 0, netgen.pick_branch(net), 0.0)]
-    err = _sim_compare(L, net, 2, 140, ev, 1, rpc=rpc)
+    err = _sim_compare(L, net, 2, 140, ev, 1, rpc=rpc, kernels=kernels)
     assert err <= 1e-10, err
 
 
@@ -202,15 +204,95 @@ def test_sim_paper_mode_matches_oracle_paper_stepping(L):
     assert err <= 1e-10, err
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_sim_1432_bus_matches_oracle(L, prec):
+@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_sim_1432_bus_matches_oracle(L, prec, kernels):
     net = netgen.tiled(2, 4)
     e = netgen.pick_branch(net)
-    err = _sim_compare(L, net, 3, 200, [(100, 0, e, 0.0)], prec)
+    err = _sim_compare(L, net, 3, 200, [(100, 0, e, 0.0)], prec, kernels=kernels)
     assert err <= TOL[prec], err
+
+
+def test_sim_reset_reproduces_run_bit_for_bit(L):
+    net = netgen.tiled(2, 4)
+    e = netgen.pick_branch(net)
+    sim = L.emt_sim_create(net, DT, levels=3, precision=L.EMT_PREC_FF64)
+    L.emt_sim_schedule(sim, 50, 0, e)
+    L.emt_sim_monitor(sim, np.arange(16))
+    a = torch.zeros(100, 16, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    L.emt_step(sim, 100, a)
+    L.emt_sim_reset(sim)
+    L.emt_step(sim, 100, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
 
 
 def test_sim_ragged_small_network(L):
     net = netgen.small_network(37, 5)
     err = _sim_compare(L, net, 3, 90, [(40, 0, 3, 0.0)], 1)
     assert err <= 1e-10, err
+
+
+# ---------------------------------------------------------------- multi-column (N-1, scenarios)
+def _msim_run(L, net, levels, steps, R, trips=None, src_scale=None, load_scale=None):
+    sim = L.emt_sim_create(net, DT, levels=levels, nrhs=R, src_scale=src_scale, load_scale=load_scale)
+    if trips:
+        for c, (st, e) in trips.items():
+            L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+    L.emt_sim_monitor(sim, np.arange(net["n_bus"]))
+    rec = torch.zeros(steps, R, net["n_bus"], dtype=torch.float64, device="cuda")
+    h1 = steps // 3
+    L.emt_step(sim, h1, rec[:h1])
+    L.emt_step(sim, steps - h1, rec[h1:])
+    torch.cuda.synchronize()
+    final = L.emt_sim_read(sim, 0).reshape(R, net["n_bus"])
+    got = rec.cpu().numpy()
+    assert np.array_equal(final, got[-1])
+    return got
+
+
+@pytest.mark.parametrize("which,levels,R,steps", [("tile", 2, 8, 90), ("tiles8", 3, 12, 70)])
+def test_multi_column_n1_trips_match_oracle(L, which, levels, R, steps):
+    net = netgen.tile(1_000_000) if which == "tile" else netgen.tiled(2, 4)
+    branches = netgen.pick_branches(net, R - 1, seed=11)
+    trips = {c: (steps // 2 + (c % 3), int(branches[c])) for c in range(R - 1)}   # last column: no trip
+    got = _msim_run(L, net, levels, steps, R, trips=trips)
+    nw = oemt.Network(net, DT, levels=levels)
+    worst = 0.0
+    for c in range(R):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense")
+        worst = max(worst, rel_err(got[:, c, :], ref))
+    assert worst <= 1e-8, worst
+
+
+def test_multi_column_scenarios_match_oracle(L):
+    net = netgen.add_loads(netgen.tiled(2, 2), seed=13)
+    R = 6
+    ss, ls = netgen.scenario_scales(net, R, seed=13)
+    got = _msim_run(L, net, 2, 60, R, src_scale=ss, load_scale=ls)
+    nw = oemt.Network(net, DT, levels=2)
+    worst = 0.0
+    for c in range(R):
+        ref, _ = oemt.simulate(nw, 60, [], solver="dense", src_scale=ss[c], load_scale=ls[c])
+        worst = max(worst, rel_err(got[:, c, :], ref))
+    assert worst <= 1e-8, worst
+
+
+def test_multi_column_reset_and_unaligned_columns(L):
+    net = netgen.tile(1_000_000)
+    R = 5   # not a multiple of 4: scalar loads in the GEMM tail
+    sim = L.emt_sim_create(net, DT, levels=2, nrhs=R)
+    L.emt_sim_schedule(sim, 20, 0, 3, 0.0, 1)
+    L.emt_sim_monitor(sim, np.arange(10))
+    a = torch.zeros(40, R, 10, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    L.emt_step(sim, 40, a)
+    L.emt_sim_reset(sim)
+    L.emt_step(sim, 40, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    nw = oemt.Network(net, DT, levels=2)
+    ref, _ = oemt.simulate(nw, 40, [(20, oemt.TRIP, 3, 0.0)], solver="dense", monitor=np.arange(10))
+    assert rel_err(a[:, 1, :].cpu().numpy(), ref) <= 1e-8
