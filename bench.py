@@ -406,7 +406,7 @@ def multi_arm(args):
     traj = rec.cpu().numpy()
     st = L.emt_sim_stats(sim)
     # accuracy on sampled columns over a bounded number of steps (oracle, single thread)
-    acc_cols = [0, R // 2, R - 1]
+    acc_cols = [0, R - 1] if args.config == 4 else [0, R // 2, R - 1]
     acc_steps = T if args.config == 3 else 100
     errs = {}
     cpu_sec = 0.0

@@ -203,10 +203,12 @@ emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out);
 /* Tuning knob for the fused single-column kernels: rows of the leaf blocks per CTA
  * (0 = automatic). Takes effect on the next emt_step. */
 emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
-/* Launch-shape tuning of the single-column step kernels: rows of a leaf per CTA (0 = automatic)
- * and the kernel generation (1 = first generation; 2 = programmatic-dependent-launch kernels with
- * a TMA-staged sweep image, used when the network fits their shared-memory limits, else 1).
- * Synchronises the device; takes effect on the next emt_step. */
+/* Launch-shape tuning. Single-column simulations: rows of a leaf per CTA (0 = automatic) and the
+ * kernel generation (1 = first generation; 2 = programmatic-dependent-launch kernels with a
+ * TMA-staged sweep image, used when the network fits their shared-memory limits, else 1).
+ * Multi-column simulations: `kernels` selects the leaf-stage GEMM (1 = FP32 CUDA cores,
+ * 2 = tcgen05 tensor cores with BF16 splits, used when nrhs is a multiple of 4 and >= 32);
+ * rows_per_cta is ignored. Synchronises the device; takes effect on the next emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
 /* Autotuner: time each candidate (rows per CTA in {4..48}, kernel generation 2 then 1) on
  * probe_steps steps of this simulation, keep the fastest and remember it for every later

@@ -248,9 +248,10 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
 
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
     EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
-    s->sim->tune(rows_per_cta, kernels, nullptr);
+    if (s->msim) s->msim->set_gemm(kernels, nullptr);
+    else s->sim->tune(rows_per_cta, kernels, nullptr);
   });
 }
 

@@ -532,6 +532,7 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   d_dyn.alloc(1);
   EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
   build_meta(s);
+  if ((R & 3) == 0 && R >= 32) umma.build(*store, R, s);
   reset(s);
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   EMT_CUDA(cudaStreamSynchronize(s));
@@ -693,7 +694,8 @@ void MSim::prepare_trips(cudaStream_t s) {
 void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s) {
   const DStore st = store->view();
   const MSimD d = view();
-  k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p);
+  if (gemm_kind == 2 && umma.ready) umma.launch(*store, Xf.p, Y.p, s);
+  else k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p);
   static bool attr = false;
   if (!attr) {
     EMT_CUDA(cudaFuncSetAttribute(k_mc_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -749,6 +751,14 @@ void MSim::step(int n_steps, double* record_dev, cudaStream_t s) {
     launches += (int64_t)left * 8 + 1;
   }
   cur_step += n_steps;
+}
+
+void MSim::set_gemm(int kind, cudaStream_t s) {
+  EMT_REQUIRE(kind == 1 || kind == 2, EMT_ERR_INVALID, "kernels must be 1 or 2");
+  EMT_CUDA(cudaDeviceSynchronize());
+  drop_graphs();
+  gemm_kind = kind;
+  (void)s;
 }
 
 void MSim::reset(cudaStream_t s) {

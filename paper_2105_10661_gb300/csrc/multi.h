@@ -60,6 +60,16 @@ struct MSimD {
   const int* meta;      // sweep metadata (see multi.cu)
 };
 
+// tcgen05 leaf stage (umma.cu)
+struct Umma {
+  bool ready = false;
+  int R = 0, TN = 0, n_blocks = 0, n_tiles = 0;
+  DevBuf<uint16_t> a_blocks;
+  DevBuf<int4> d_tiles;
+  void build(const Store& st, int R, cudaStream_t s);
+  void launch(const Store& st, const float* Xf, float* Y, cudaStream_t s);
+};
+
 class MSim {
  public:
   MSim(const emt_network* net, const emt_hinv_opts* opts, double dt, int R, const double* src_scale,
@@ -71,7 +81,10 @@ class MSim {
   void read(int what, double* host_out);
   void reset(cudaStream_t s);
   void stats(int64_t* out, int n) const;
+  void set_gemm(int kind, cudaStream_t s);   // 1 SIMT FP32, 2 tcgen05 BF16x3
   MSimD view() const;
+  Umma umma;
+  int gemm_kind = 2;
 
   static constexpr int kChunk = 32;
   std::unique_ptr<Store> store;

@@ -296,3 +296,29 @@ def test_multi_column_reset_and_unaligned_columns(L):
     nw = oemt.Network(net, DT, levels=2)
     ref, _ = oemt.simulate(nw, 40, [(20, oemt.TRIP, 3, 0.0)], solver="dense", monitor=np.arange(10))
     assert rel_err(a[:, 1, :].cpu().numpy(), ref) <= 1e-8
+
+
+@pytest.mark.parametrize("gemm", [1, 2])
+@pytest.mark.parametrize("which,levels,R,steps", [("tile", 2, 64, 50), ("tiles8", 3, 128, 40)])
+def test_multi_column_gemm_kinds_match_oracle(L, gemm, which, levels, R, steps):
+    # gemm 1: FP32 CUDA-core leaf GEMM; gemm 2: tcgen05 BF16x3 leaf GEMM (FP32 accumulate in TMEM)
+    net = netgen.tile(1_000_000) if which == "tile" else netgen.tiled(2, 4)
+    branches = netgen.pick_branches(net, 3, seed=5)
+    trips = {0: (steps // 2, int(branches[0])), R // 2: (steps // 3, int(branches[1])), R - 1: (5, int(branches[2]))}
+    sim = L.emt_sim_create(net, DT, levels=levels, nrhs=R)
+    L.emt_sim_tune(sim, 0, gemm)
+    for c, (st, e) in trips.items():
+        L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+    mon = np.arange(0, net["n_bus"], 7)
+    L.emt_sim_monitor(sim, mon)
+    rec = torch.zeros(steps, R, len(mon), dtype=torch.float64, device="cuda")
+    L.emt_step(sim, steps, rec)
+    torch.cuda.synchronize()
+    got = rec.cpu().numpy()
+    nw = oemt.Network(net, DT, levels=levels)
+    worst = 0.0
+    for c in (0, 1, R // 2, R - 1):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
+        worst = max(worst, rel_err(got[:, c, :], ref))
+    assert worst <= 1e-8, worst
