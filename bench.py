@@ -40,19 +40,20 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--time-steps", type=int, default=20000)
     ap.add_argument("--variants", default="ff64,fp32,fp64")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 41],
                     help="2: single 1,432-bus simulation (default); 3: N-1 screening, 256 contingencies; "
-                         "4: 11,456-bus network, 512 scenarios")
+                         "4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of 2,000 requests")
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-col", type=int, default=-1, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
-def workload(rank: int = 0):
+def workload(rank: int = 0, cfg: int = 2):
     import numpy as np
     import netgen
-    net = netgen.tiled(2, 4)
+    net = netgen.tile(1_000_000) if cfg == 1 else netgen.tiled(2, 4)
     trip = netgen.pick_branch(net, seed=7 + rank)
     mon = np.sort(np.random.default_rng(17).choice(net["n_bus"], N_MON, replace=False))
     return net, trip, mon
@@ -84,9 +85,9 @@ def cpu_worker(out_prefix: str, n_steps: int, cfg: int = 2, col: int = -1):
     import numpy as np
     from oracle import emt as oemt
     t0 = time.perf_counter()
-    if cfg == 2:
-        net, trip, mon = workload()
-        nw = oemt.Network(net, DT, levels=3)
+    if cfg in (1, 2):
+        net, trip, mon = workload(0, cfg)
+        nw = oemt.Network(net, DT, levels=2 if cfg == 1 else 3)
         half = n_steps // 2
         traj, _ = oemt.simulate(nw, n_steps, [(half, oemt.TRIP, trip, 0.0)], solver="exact", monitor=mon)
     else:
@@ -160,6 +161,21 @@ class Clocks:
         return out
 
 
+def job_ms(ms: float, world: int, device=None) -> float:
+    """Whole-job time of one timed step: the maximum over ranks of each rank's own time."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units processed by all ranks per second (independent replicas, weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def rel_err(got, ref):
     import numpy as np
     return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
@@ -209,8 +225,9 @@ def native_arm(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    T = args.time_steps
-    net, trip, mon = workload(rank)
+    T = args.time_steps if args.config == 2 else 2000
+    LV = 3 if args.config == 2 else 2
+    net, trip, mon = workload(rank, args.config)
     n = net["n_bus"]
     prec = {"ff64": L.EMT_PREC_FF64, "fp32": L.EMT_PREC_FP32, "fp64": L.EMT_PREC_FP64}
     names = [v for v in args.variants.split(",") if v]
@@ -225,12 +242,12 @@ def native_arm(args):
     ref = None
     cpu_sec = None
     if rank == 0:
-        ref, cpu_sec = run_cpu_oracle(T)
+        ref, cpu_sec = run_cpu_oracle(T, args.config)
 
     results = {}
     clocks = Clocks(local)
     for name in names:
-        sim = L.emt_sim_create(net, DT, levels=3, mode=L.EMT_MODE_EXACT, precision=prec[name])
+        sim = L.emt_sim_create(net, DT, levels=LV, mode=L.EMT_MODE_EXACT, precision=prec[name])
         L.emt_sim_schedule(sim, T // 2, L.EMT_EVENT_TRIP, trip)
         L.emt_sim_monitor(sim, mon)
         tuned = L.emt_sim_autotune(sim, 512, stream)
@@ -253,13 +270,10 @@ def native_arm(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         launches = L.emt_sim_stats(sim)["launches"] - l0
-        ms = float(np.mean(times))
-        t_max = torch.tensor([ms], device=dev)
-        if world > 1:
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        ms = job_ms(float(np.mean(times)), world, dev)
         traj = rec.cpu().numpy()
         err = rel_err(traj, ref) if ref is not None else None
-        results[name] = dict(sim=sim, ms=float(t_max.item()), err=err, launches=launches // args.steps,
+        results[name] = dict(sim=sim, ms=ms, err=err, launches=launches // args.steps,
                              tuned={"rows_per_cta": tuned[0], "kernels": tuned[1]})
     clk = clocks.stop()
 
@@ -268,7 +282,7 @@ def native_arm(args):
     H = results[head]
     sim = H["sim"]
     st = L.emt_sim_stats(sim)
-    value = world * n * T / (H["ms"] / 1e3)
+    value = job_rate(n * T, world, H["ms"])
 
     # roofline of the dominant kernel (timed alone as a graph of back-to-back launches)
     reps = 2000
@@ -306,7 +320,7 @@ def native_arm(args):
     for i in range(max(1, min(args.steps, 3)) + 1):
         barrier()
         t0 = time.perf_counter()
-        s2 = L.emt_sim_create(net, DT, levels=3, mode=L.EMT_MODE_EXACT, precision=prec[head])
+        s2 = L.emt_sim_create(net, DT, levels=LV, mode=L.EMT_MODE_EXACT, precision=prec[head])
         L.emt_sim_schedule(s2, T // 2, L.EMT_EVENT_TRIP, trip)
         L.emt_sim_monitor(s2, mon)
         rec2 = torch.empty(T, N_MON, dtype=torch.float64, device=dev)
@@ -317,16 +331,18 @@ def native_arm(args):
         t1 = time.perf_counter()
         if i > 0:
             e2e_times.append(t1 - t0)
-    e2e_ms = float(np.mean(e2e_times)) * 1e3
-    e2e_val = world * n * T / (e2e_ms / 1e3)
+    e2e_ms = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
+    e2e_val = job_rate(n * T, world, e2e_ms)
 
     if rank == 0:
         line = {
             "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
-            "config": {"workload": "1432-bus network (8 seeded 179-bus tiles), 3-level hierarchy, 20,000 time steps "
-                                   "of 50 us, one line trip at step 10,000, 16 monitored buses",
+            "config": {"workload": ("1432-bus network (8 seeded 179-bus tiles), 3-level hierarchy, 20,000 time steps "
+                                    "of 50 us, one line trip at step 10,000, 16 monitored buses") if args.config == 2 else
+                                   ("179-bus tile, 2-level hierarchy (4 leaves), 2,000 time steps of 50 us, one line "
+                                    "trip at step 1,000, 16 monitored buses"),
                        "time_steps_per_step": T, "buses": n, "mode": "exact", "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{world}"},
             "accuracy": {k: results[k]["err"] for k in names},
@@ -397,12 +413,8 @@ def multi_arm(args):
         times.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     launches = (L.emt_sim_stats(sim)["launches"] - l0) // args.steps
-    ms = float(np.mean(times))
-    t_max = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = world * n * R * T / (ms / 1e3)
+    ms = job_ms(float(np.mean(times)), world, dev)
+    value = job_rate(n * R * T, world, ms)
     traj = rec.cpu().numpy()
     st = L.emt_sim_stats(sim)
     # accuracy on sampled columns over a bounded number of steps (oracle, single thread)
@@ -446,6 +458,166 @@ def multi_arm(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- config 5 (serving)
+def serve_requests(nets, n_req, seed, rate, steps_lo=1000, steps_hi=10000):
+    import numpy as np
+    import netgen
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_req):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        k = int(rng.integers(len(nets)))
+        net = nets[k][0]
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        if rng.random() < 0.5:
+            out.append((k, t, steps, 0, int(rng.integers(len(net["br_a"]))), 0.0, int(rng.integers(1, steps)), 0))
+        else:
+            st = int(rng.integers(1, max(2, steps - 400)))
+            out.append((k, t, steps, 1, int(rng.integers(net["n_bus"])), 10.0, st, 400))
+    return out
+
+
+def serve_arm(args):
+    import numpy as np
+    import torch
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+    from oracle import emt as oemt
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nets = [(netgen.tile(1_000_000), 2, 256), (netgen.tiled(2, 4), 3, 256), (netgen.config_network(4), 4, 128)]
+    mons = [np.sort(np.random.default_rng(17 + i).choice(n[0]["n_bus"], N_MON, replace=False)) for i, n in enumerate(nets)]
+
+    def make_server():
+        srv = L.emt_server_create(100, 96 << 30)
+        ids = [L.emt_server_add_network(srv, n[0], DT, levels=n[1], max_slots=n[2], monitor=mons[i])
+               for i, n in enumerate(nets)]
+        return srv, ids
+
+    # calibration: a burst at t = 0 measures the saturated request rate
+    srv, ids = make_server()
+    cal = serve_requests(nets, 300, 99, 0.0)
+    for r in cal:
+        L.emt_server_submit(srv, ids[r[0]], *r[1:])
+    L.emt_server_run(srv)
+    cst = L.emt_server_stats(srv)
+    sat_rate = cst["finished"] / cst["wall_s"]
+    del srv
+    # the measured run: Poisson arrivals at 80% of the saturated rate
+    rate = 0.8 * sat_rate
+    reqs = serve_requests(nets, args.requests, 17, rate)
+    srv, ids = make_server()
+    rids = [L.emt_server_submit(srv, ids[r[0]], *r[1:]) for r in reqs]
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    L.emt_server_run(srv)
+    clk = clocks.stop()
+    st = L.emt_server_stats(srv)
+    # accuracy: oracle on sampled short requests of the two smaller networks
+    errs = {}
+    cpu_sec = 0.0
+    cpu_bus_steps = 0.0
+    picks = [i for i, r in enumerate(reqs) if r[0] in (0, 1) and r[2] <= 2500][:4]
+    for i in picks:
+        k, _, steps, kind, target, value, ev, ln = reqs[i]
+        net, levels, _ = nets[k]
+        t0 = time.perf_counter()
+        nw = oemt.Network(net, DT, levels=levels)
+        evs = ([(ev, oemt.TRIP, target, 0.0)] if kind == 0 else
+               [(ev, oemt.FAULT_ON, target, value), (ev + ln, oemt.FAULT_OFF, target, 0.0)])
+        ref, _ = oemt.simulate(nw, steps, evs, solver="exact", monitor=mons[k])
+        cpu_sec += time.perf_counter() - t0
+        cpu_bus_steps += steps * net["n_bus"]
+        got, _ = L.emt_server_result(srv, rids[i])
+        errs[str(i)] = rel_err(got, ref)
+    print(json.dumps({
+        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle; p50/p99 served latency", "value": st["bus_steps_per_s"],
+        "unit": "bus-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": st["wall_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff64-refine", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {args.requests} requests over resident 179/1432/11456-bus "
+                               "networks, 1000-10000 steps each, a line trip or a 10-ohm 400-step bus fault per request",
+                   "arrival_rate_req_per_s": rate, "saturated_rate_req_per_s": sat_rate, "tick_steps": 100,
+                   "slots": [n[2] for n in nets]},
+        "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "max": st["max_s"]},
+        "served": {k: st[k] for k in ("wall_s", "bus_steps", "max_queue", "ticks", "finished")},
+        "accuracy": {"sampled_requests": errs, "max": max(errs.values()) if errs else None},
+        "cpu_baseline": {"value": cpu_bus_steps / cpu_sec if cpu_sec else None, "unit": "bus-steps/s", "cores": 1,
+                         "kind": "oracle", "sample": f"{len(picks)} sampled requests, exact hierarchical store"},
+        "clocks": clk,
+    }))
+
+
+# ---------------------------------------------------------------- config 4': single-vector apply, HBM bound
+def apply_arm(args):
+    import numpy as np
+    import torch
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+    from oracle import emt as oemt
+    from oracle import hinv as ohinv
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    net = netgen.config_network(4)
+    n = net["n_bus"]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    x = torch.tensor(np.random.default_rng(5).standard_normal(n), dtype=torch.float64, device=dev)
+    res = {}
+    for name, p in (("fp64", L.EMT_PREC_FP64), ("ff64", L.EMT_PREC_FF64)):
+        h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=p)
+        v = torch.zeros(n, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            L.emt_apply(h, x, v, stream=stream)
+        ts = []
+        for _ in range(max(args.steps, 10)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.emt_apply(h, x, v, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name] = (float(np.median(ts)), v.cpu().numpy())
+    # oracle: exact hierarchical apply of the same vector (CPU, single thread)
+    t0 = time.perf_counter()
+    nw = oemt.Network(net, DT, levels=4)
+    H = ohinv.HInv(nw.G, nw.tree, nw.g_series, ohinv.EXACT)
+    t1 = time.perf_counter()
+    ref = H.apply(x.cpu().numpy())
+    t2 = time.perf_counter()
+    tree = nw.tree
+    leaf = sum(int(tree["hi"][j] - tree["lo"][j]) ** 2 for j in tree["leaves"])
+    fac = sum(int(tree["hi"][p] - tree["lo"][p]) * int(tree["cut_ptr"][p + 1] - tree["cut_ptr"][p])
+              for p in range(len(tree["lo"])) if tree["left"][p] >= 0)
+    byts = (leaf + fac) * 8 + n * 8 * 3
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    head = min(res, key=lambda k: res[k][0])
+    ms = res[head][0]
+    ach = byts / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": n / (ms * 1e-3), "unit": "bus-steps/s",
+        "n_gpus": 1, "steps": max(args.steps, 10), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
+        "config": {"workload": "single-vector apply v = Ginv i on the 11456-bus store (16 leaves of 716), "
+                               "L2 flushed before every apply", "store_bytes_fp64": (leaf + fac) * 8},
+        "variants_ms": {k: v[0] for k, v in res.items()},
+        "accuracy": {k: rel_err(v[1], ref) for k, v in res.items()},
+        "roofline": {"bound": "hbm", "kernel": "whole apply (leaf partials + sweep)", "achieved": ach,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                     "algorithmic_bytes": byts},
+        "cpu_baseline": {"value": n / (t2 - t1), "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "one exact hierarchical apply of the same vector (store build excluded)"},
+    }))
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -455,6 +627,10 @@ def main():
         reference_arm(args)
     elif args.config in (3, 4):
         multi_arm(args)
+    elif args.config == 5:
+        serve_arm(args)
+    elif args.config == 41:
+        apply_arm(args)
     else:
         native_arm(args)
 

@@ -175,6 +175,12 @@ typedef struct {
   double freq;
 } emt_network;
 
+/* emt_build_hinv on the conductance graph of an EMT network at time step dt: the trapezoidal
+ * companion conductance of every series branch and shunt capacitor and 1/Rs of every source
+ * (Sec. II). Series branch ids are preserved. Synchronises `stream`. */
+emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const emt_hinv_opts* opts, void* stream,
+                                       emt_hinv** out);
+
 /* Event kinds for emt_sim_schedule. TRIP: target = branch id (opens before the step is
  * solved; current and history zeroed). FAULT_ON: target = bus, value = R_f (ohm). FAULT_OFF:
  * target = bus (restores the pre-fault store). */
@@ -205,7 +211,9 @@ emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out);
 emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
 /* Launch-shape tuning. Single-column simulations: rows of a leaf per CTA (0 = automatic) and the
  * kernel generation (1 = first generation; 2 = programmatic-dependent-launch kernels with a
- * TMA-staged sweep image, used when the network fits their shared-memory limits, else 1).
+ * TMA-staged sweep image, used when the network fits their shared-memory limits, else 1;
+ * 3 = thread-block-cluster leaf stage reduced through distributed shared memory and an FP64
+ * sweep; rows_per_cta then sets the cluster size, ceil(max leaf / rows_per_cta) <= 8).
  * Multi-column simulations: `kernels` selects the leaf-stage GEMM (1 = FP32 CUDA cores,
  * 2 = tcgen05 tensor cores with BF16 splits, used when nrhs is a multiple of 4 and >= 32);
  * rows_per_cta is ignored. Synchronises the device; takes effect on the next emt_step. */
@@ -231,6 +239,39 @@ emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
  * afterwards. Asynchronous on `stream`. */
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream);
 void emt_sim_destroy(emt_sim* s);
+
+/* Failure-path self-test of the bounded device waits: launches one CTA that waits on an mbarrier
+ * no one arrives at, with a limit of limit_us microseconds of SM clock (at most 2 s), then sets
+ * the device status word. Returns EMT_ERR_TIMEOUT when the wait ran out as designed (the
+ * context stays usable), EMT_OK never. Synchronises `stream`. */
+emt_status emt_selftest_bounded_wait(int32_t limit_us, void* stream);
+
+/* ---- continuous-batching server --------------------------------------------------------
+ * Base networks stay resident on the GPU, each as a multi-column simulation whose columns are
+ * request slots; the slot count of a network is its share of hbm_budget_bytes divided by the
+ * per-slot footprint (admission by memory). Requests arrive on a wall-clock schedule (seconds
+ * after emt_server_run starts); arrived requests are admitted into free slots between ticks of
+ * tick_steps steps, every busy network advances one tick on its own stream, finished requests
+ * free their slots. A request may carry one change: event_kind 0 trips series branch `target`
+ * event_step steps after its start; 1 switches a fault R_f = value ohm to ground at bus `target`
+ * for event_len steps; -1 none. Each request's voltages at the network's monitored buses are
+ * kept per step. */
+typedef struct emt_server emt_server;
+emt_status emt_server_create(int32_t tick_steps, uint64_t hbm_budget_bytes, emt_server** out);
+/* Add a base network (built now) with up to max_slots concurrent requests; returns its id. */
+emt_status emt_server_add_network(emt_server* s, const emt_network* net, const emt_hinv_opts* opts, double dt,
+                                  int32_t max_slots, int32_t n_mon, const int32_t* mon_buses, int32_t* net_id);
+emt_status emt_server_submit(emt_server* s, int32_t net_id, double arrival_s, int32_t n_steps, int32_t event_kind,
+                             int32_t target, double value, int32_t event_step, int32_t event_len, int32_t* req_id);
+/* Serve every submitted request that has not finished yet; returns when all are done. */
+emt_status emt_server_run(emt_server* s);
+/* Monitored voltages of a finished request ([n_steps][n_mon], may be NULL) and its times
+ * (arrival, admission, completion in seconds since the start of emt_server_run; may be NULL). */
+emt_status emt_server_result(const emt_server* s, int32_t req_id, double* out, double* times3);
+/* out[0..n): wall seconds, bus-steps served, bus-steps per second, p50 / p99 / max latency (s),
+ * largest queue length, ticks, finished requests. */
+emt_status emt_server_stats(const emt_server* s, double* out, int32_t n);
+void emt_server_destroy(emt_server* s);
 
 #ifdef __cplusplus
 }

@@ -96,6 +96,18 @@ def _load():
         "emt_apply_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "emt_sim_tune": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "emt_sim_autotune": (C.c_int, [vp, C.c_int32, _i32p, _i32p, vp]),
+        "emt_server_create": (C.c_int, [C.c_int32, C.c_uint64, C.POINTER(vp)]),
+        "emt_server_add_network": (C.c_int, [vp, C.POINTER(EmtNetwork), C.POINTER(EmtHinvOpts), C.c_double, C.c_int32,
+                                             C.c_int32, _i32p, _i32p]),
+        "emt_server_submit": (C.c_int, [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                        C.c_int32, C.c_int32, _i32p]),
+        "emt_server_run": (C.c_int, [vp]),
+        "emt_server_result": (C.c_int, [vp, C.c_int32, _f64p, _f64p]),
+        "emt_server_stats": (C.c_int, [vp, _f64p, C.c_int32]),
+        "emt_server_destroy": (None, [vp]),
+        "emt_selftest_bounded_wait": (C.c_int, [C.c_int32, vp]),
+        "emt_build_hinv_from_network": (C.c_int, [C.POINTER(EmtNetwork), C.c_double, C.POINTER(EmtHinvOpts), vp,
+                                                  C.POINTER(vp)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -109,7 +121,9 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
-            "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune")
+            "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
+            "emt_server_add_network", "emt_server_submit", "emt_server_run", "emt_server_result", "emt_server_stats",
+            "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network")
 
 
 def _check(code):
@@ -321,3 +335,79 @@ def emt_sim_autotune(s: Sim, probe_steps=256, stream=None):
     r, k = C.c_int32(), C.c_int32()
     _check(lib.emt_sim_autotune(s.h, int(probe_steps), C.byref(r), C.byref(k), _stream(stream)))
     return r.value, k.value
+
+
+class Server:
+    """Owning wrapper of an emt_server handle."""
+
+    def __init__(self, handle):
+        self.h = handle
+        self.n_mon = {}
+        self.steps = {}
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.emt_server_destroy(self.h)
+            self.h = None
+
+
+def emt_server_create(tick_steps=100, hbm_budget_bytes=0):
+    h = C.c_void_p()
+    _check(lib.emt_server_create(int(tick_steps), int(hbm_budget_bytes), C.byref(h)))
+    return Server(h.value)
+
+
+def emt_server_add_network(srv: Server, net: dict, dt, levels=0, d_th=0, max_slots=64, monitor=None):
+    nw, keep = make_network(net)
+    o = make_opts(levels, d_th, EMT_MODE_EXACT, EMT_PREC_FP32)
+    mon = _i32(monitor if monitor is not None else np.arange(min(16, net["n_bus"])))
+    nid = C.c_int32()
+    _check(lib.emt_server_add_network(srv.h, C.byref(nw), C.byref(o), float(dt), int(max_slots), len(mon),
+                                      _p(mon, _i32p), C.byref(nid)))
+    srv.n_mon[nid.value] = len(mon)
+    return nid.value
+
+
+def emt_server_submit(srv: Server, net_id, arrival_s, n_steps, event_kind=-1, target=0, value=0.0, event_step=0,
+                      event_len=0):
+    rid = C.c_int32()
+    _check(lib.emt_server_submit(srv.h, int(net_id), float(arrival_s), int(n_steps), int(event_kind), int(target),
+                                 float(value), int(event_step), int(event_len), C.byref(rid)))
+    srv.steps[rid.value] = (int(n_steps), int(net_id))
+    return rid.value
+
+
+def emt_server_run(srv: Server):
+    _check(lib.emt_server_run(srv.h))
+
+
+def emt_server_result(srv: Server, req_id):
+    n_steps, nid = srv.steps[req_id]
+    out = np.zeros((n_steps, srv.n_mon[nid]))
+    times = np.zeros(3)
+    _check(lib.emt_server_result(srv.h, int(req_id), _p(out, _f64p), _p(times, _f64p)))
+    return out, times
+
+
+SERVER_STAT_KEYS = ("wall_s", "bus_steps", "bus_steps_per_s", "p50_s", "p99_s", "max_s", "max_queue", "ticks",
+                    "finished")
+
+
+def emt_server_stats(srv: Server):
+    out = np.zeros(len(SERVER_STAT_KEYS))
+    _check(lib.emt_server_stats(srv.h, _p(out, _f64p), len(out)))
+    return dict(zip(SERVER_STAT_KEYS, out.tolist()))
+
+
+def emt_selftest_bounded_wait(limit_us=1000, stream=None):
+    """Returns the status code (EMT_ERR_TIMEOUT expected)."""
+    return lib.emt_selftest_bounded_wait(int(limit_us), _stream(stream))
+
+
+def emt_build_hinv_from_network(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64,
+                                stream=None):
+    nw, keep = make_network(net)
+    o = make_opts(levels, d_th, mode, precision)
+    h = C.c_void_p()
+    _check(lib.emt_build_hinv_from_network(C.byref(nw), float(dt), C.byref(o), _stream(stream), C.byref(h)))
+    return HInv(h.value, int(net["n_bus"]))

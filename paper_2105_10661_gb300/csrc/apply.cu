@@ -249,6 +249,10 @@ void fused_apply(const Store& st, FusedPlan& p, const double* src, bool src_pos,
   }
 }
 
+void fused_apply_ff64(const Store& st, FusedPlan& p, const double* src, bool src_pos, double* v_pos, cudaStream_t s) {
+  launch_apply<EMT_PREC_FF64>(st, p, src, src_pos, v_pos, nullptr, false, s);
+}
+
 // emt_apply: single vectors go through the fused kernels; FP32 stores are refined against the
 // FP64 residual (fixed number of passes, max_refine).
 void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>& rpos, const double* i_dev,

@@ -5,6 +5,7 @@
 
 #include "plan.h"
 #include "multi.h"
+#include "server.h"
 #include "sim.h"
 
 namespace emt {
@@ -13,6 +14,9 @@ void set_last_error(const std::string& m) { g_last_error = m; }
 void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>& rpos, const double* i_dev,
                    double* v_dev, int nrhs, int64_t ld, int max_refine, cudaStream_t s);
 void apply_noalloc(const Store& st, const double* i_dev, double* v_dev, cudaStream_t s);
+int selftest_wait(int limit_us, cudaStream_t s);
+void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
+                   std::vector<double>& gv);
 }  // namespace emt
 
 struct emt_tree {
@@ -25,6 +29,10 @@ struct emt_hinv {
   bool has_plan = false;
   emt::DevBuf<double> vpos, rpos;
   emt_tree tree;
+};
+
+struct emt_server {
+  std::unique_ptr<emt::Server> srv;
 };
 
 struct emt_sim {
@@ -136,6 +144,16 @@ emt_status emt_build_hinv(const emt_graph* graph, const emt_hinv_opts* opts, voi
     h->tree.t = h->st->tree;
     *out = h.release();
   });
+}
+
+emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const emt_hinv_opts* opts, void* stream,
+                                       emt_hinv** out) {
+  std::vector<int32_t> gf, gt;
+  std::vector<double> gv;
+  emt_status r = guard([&] { emt::network_graph(net, dt, gf, gt, gv); });
+  if (r != EMT_OK) return r;
+  emt_graph g{net->n_bus, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
+  return emt_build_hinv(&g, opts, stream, out);
 }
 
 const emt_tree* emt_hinv_tree(const emt_hinv* h) { return h ? &h->tree : nullptr; }
@@ -290,5 +308,73 @@ emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* s
 }
 
 void emt_sim_destroy(emt_sim* s) { delete s; }
+
+emt_status emt_server_create(int32_t tick_steps, uint64_t hbm_budget_bytes, emt_server** out) {
+  return guard([&] {
+    EMT_REQUIRE(out, EMT_ERR_INVALID, "null output handle");
+    std::unique_ptr<emt_server> h(new emt_server);
+    h->srv.reset(new emt::Server(tick_steps, (size_t)hbm_budget_bytes));
+    *out = h.release();
+  });
+}
+
+emt_status emt_server_add_network(emt_server* s, const emt_network* net, const emt_hinv_opts* opts, double dt,
+                                  int32_t max_slots, int32_t n_mon, const int32_t* mon_buses, int32_t* net_id) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv && net && opts, EMT_ERR_INVALID, "null argument");
+    const int id = s->srv->add_network(net, opts, dt, max_slots, n_mon, mon_buses);
+    if (net_id) *net_id = id;
+  });
+}
+
+emt_status emt_server_submit(emt_server* s, int32_t net_id, double arrival_s, int32_t n_steps, int32_t event_kind,
+                             int32_t target, double value, int32_t event_step, int32_t event_len, int32_t* req_id) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv, EMT_ERR_INVALID, "null server");
+    const int id = s->srv->submit(net_id, arrival_s, n_steps, event_kind, target, value, event_step, event_len);
+    if (req_id) *req_id = id;
+  });
+}
+
+emt_status emt_server_run(emt_server* s) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv, EMT_ERR_INVALID, "null server");
+    s->srv->run();
+  });
+}
+
+emt_status emt_server_result(const emt_server* s, int32_t req_id, double* out, double* times3) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv, EMT_ERR_INVALID, "null server");
+    EMT_REQUIRE(req_id >= 0 && req_id < (int)s->srv->reqs.size(), EMT_ERR_INVALID, "unknown request");
+    const auto& r = s->srv->reqs[req_id];
+    EMT_REQUIRE(r.t_done >= 0, EMT_ERR_STATE, "request not finished");
+    if (out) std::memcpy(out, r.out.data(), r.out.size() * sizeof(double));
+    if (times3) {
+      times3[0] = r.arrival;
+      times3[1] = r.t_admit;
+      times3[2] = r.t_done;
+    }
+  });
+}
+
+emt_status emt_server_stats(const emt_server* s, double* out, int32_t n) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv && out, EMT_ERR_INVALID, "null argument");
+    s->srv->stats(out, n);
+  });
+}
+
+void emt_server_destroy(emt_server* s) { delete s; }
+
+emt_status emt_selftest_bounded_wait(int32_t limit_us, void* stream) {
+  int dev = 0;
+  emt_status r = guard([&] {
+    EMT_REQUIRE(limit_us >= 1 && limit_us <= 2000000, EMT_ERR_INVALID, "limit_us must be in [1, 2e6]");
+    dev = emt::selftest_wait(limit_us, as_stream(stream));
+  });
+  if (r != EMT_OK) return r;
+  return status_from_device(dev);
+}
 
 }  // extern "C"

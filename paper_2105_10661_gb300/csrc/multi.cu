@@ -54,12 +54,16 @@ __global__ void k_mc_trig(float2* trig, int first_step, int n, double omega, dou
 }
 
 // history update of every element end and injection, one (position, column) per thread
+__device__ __forceinline__ bool change_on(const MSimD& m, int c, int step) {
+  return m.trip_step[c] > 0 && step >= m.trip_step[c] && step < m.trip_off[c];
+}
+
 __global__ void __launch_bounds__(128) k_mc_inject(MSimD m, int s_in_chunk, int* status) {
   const int pos = blockIdx.x;
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R || *status != DEV_OK) return;
+  if (c >= m.R_act || *status != DEV_OK) return;
   const int step = m.dyn->step_base + s_in_chunk + 1;
-  const bool trip = m.trip_step[c] > 0 && step >= m.trip_step[c];
+  const bool trip = change_on(m, c, step) && m.trip_elem[c] >= 0;
   const int te = m.trip_elem[c];
   const int64_t R = m.R;
   const float2 vi = m.V[pos * R + c];
@@ -92,12 +96,13 @@ __global__ void __launch_bounds__(128) k_mc_inject(MSimD m, int s_in_chunk, int*
 constexpr int GBM = 64, GBN = 128, GBK = 16;
 __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restrict__ tiles,
                                                  const float* __restrict__ Xf, float* __restrict__ Y, int R,
-                                                 const int* status) {
+                                                 const int* status, int r_act) {
   __shared__ __align__(16) float As[GBK][GBM + 4];
   __shared__ __align__(16) float Bs[GBK][GBN + 4];
   if (*status != DEV_OK) return;
   const int4 tl = tiles[blockIdx.x];
   const int j = tl.x, m0 = tl.y, n0 = tl.z;
+  if (n0 >= r_act) return;
   const int node = st.leaf_node[j];
   const int lo = st.lo[node], b = st.hi[node] - lo, ld = st.leaf_ld[j];
   const float* L = st.L32 + st.leaf_off[j];
@@ -185,7 +190,8 @@ __global__ void __launch_bounds__(256) k_mc_sweep(DStore st, MSimD m, int cb, in
   extern __shared__ __align__(16) float sh[];
   if (*status != DEV_OK) return;
   const int c0 = blockIdx.x * cb;
-  const int ncol = min(cb, m.R - c0);
+  const int ncol = min(cb, m.R_act - c0);
+  if (ncol <= 0) return;
   const int* M = m.meta;
   const int n_crow = M[M_NCROW], s_total = M[M_STOTAL], maxd = M[M_MAXD];
   float* ycut = sh;                         // [n_crow][cb]
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(256) k_mc_sweep(DStore st, MSimD m, int cb, in
     for (int cl = tid; cl < ncol; cl += blockDim.x) {
       const int c = c0 + cl;
       float f = 0.f;
-      if (m.trip_step[c] > 0 && step >= m.trip_step[c]) {
+      if (change_on(m, c, step)) {
         const float ya = corrected(st, m.Y, R, m.trip_a[c], c, cl, s, cb, -1);
         const float yb = m.trip_b[c] >= 0 ? corrected(st, m.Y, R, m.trip_b[c], c, cl, s, cb, -1) : 0.f;
         f = (float)m.trip_coef[c] * (ya - yb);
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(128) k_mc_expand(DStore st, MSimD m, int pass,
                                                    const int* status) {
   const int pos = blockIdx.x;
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R || *status != DEV_OK) return;
+  if (c >= m.R_act || *status != DEV_OK) return;
   const int64_t R = m.R;
   float v = m.Y[pos * R + c];
   for (int q = st.parent[st.leaf_node[st.pos_leaf[pos]]]; q >= 0; q = st.parent[q]) {
@@ -283,14 +289,14 @@ __global__ void __launch_bounds__(128) k_mc_expand(DStore st, MSimD m, int pass,
 __global__ void __launch_bounds__(128) k_mc_residual(MSimD m, int n1, int s_in_chunk, const int* status) {
   const int pos = blockIdx.x;
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R || *status != DEV_OK) return;
+  if (c >= m.R_act || *status != DEV_OK) return;
   const int64_t R = m.R;
   float2 r = m.X[pos * R + c];
   for (int t = m.csr_ptr[pos]; t < m.csr_ptr[pos + 1]; ++t)
     r = ff_subx(r, ff_mulx(m.csr_ff[t], m.V[(int64_t)m.csr_col[t] * R + c]));
   if (n1) {
     const int step = m.dyn->step_base + s_in_chunk + 1;
-    if (m.trip_step[c] > 0 && step >= m.trip_step[c]) {
+    if (change_on(m, c, step)) {
       const int a = m.trip_a[c], b = m.trip_b[c];
       if (pos == a || pos == b) {
         // (G' v)_i = (G v)_i + delta u_i (v_a - v_b)
@@ -336,6 +342,65 @@ __global__ void k_mc_unit(MSimD m, float2* X, float* Xf) {
   }
 }
 
+// Start column c afresh: zero its voltages, history and right-hand side.
+__global__ void k_mc_reset_col(MSimD m, int n_inc, int c) {
+  const int64_t R = m.R;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inc; i += gridDim.x * blockDim.x) {
+    m.Ih[i * R + c] = ff_f(0.f);
+    if (i < m.n) {
+      m.V[i * R + c] = ff_f(0.f);
+      m.X[i * R + c] = ff_f(0.f);
+      m.Xf[i * R + c] = 0.f;
+    }
+  }
+}
+
+// Source/load coefficients of column c for a start S = w t0 (local time t - t0):
+// cs' = cs cos S + sn sin S, sn' = sn cos S - cs sin S.
+__global__ void k_mc_rotate_terms(MSimD m, const double* __restrict__ base, float2* cs, float2* sn, int n_terms, int c,
+                                  double cosS, double sinS) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_terms) return;
+  const double a = base[2 * t], b = base[2 * t + 1];
+  const double x = a * cosS + b * sinS, y = b * cosS - a * sinS;
+  const float xh = (float)x, yh = (float)y;
+  cs[(int64_t)t * m.R + c] = make_float2(xh, (float)(x - (double)xh));
+  sn[(int64_t)t * m.R + c] = make_float2(yh, (float)(y - (double)yh));
+}
+
+__global__ void k_mc_set_z(MSimD m, float2* Z, const double* __restrict__ zpos, int c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n) return;
+  const double v = zpos[i];
+  const float h = (float)v;
+  Z[(int64_t)i * m.R + c] = make_float2(h, (float)(v - (double)h));
+}
+
+__global__ void k_mc_one_coef(MSimD m, double* coef, int c, int* status) {
+  const int64_t R = m.R;
+  const float2 za = m.Z[(int64_t)m.trip_a[c] * R + c];
+  double ut = (double)za.x + (double)za.y;
+  if (m.trip_b[c] >= 0) {
+    const float2 zb = m.Z[(int64_t)m.trip_b[c] * R + c];
+    ut -= (double)zb.x + (double)zb.y;
+  }
+  const double d = 1.0 + m.trip_delta[c] * ut;
+  if (!(d > 1e-12)) atomicExch(status, DEV_SINGULAR);
+  coef[c] = m.trip_delta[c] / d;
+}
+
+__global__ void k_mc_set_event(int* on, int* off, int* elem, int* ta, int* tb, double* td, float2* tdf, int c, int v_on,
+                               int v_off, int v_elem, int v_a, int v_b, double v_d) {
+  on[c] = v_on;
+  off[c] = v_off;
+  elem[c] = v_elem;
+  ta[c] = v_a;
+  tb[c] = v_b;
+  td[c] = v_d;
+  const float h = (float)v_d;
+  tdf[c] = make_float2(h, (float)(v_d - (double)h));
+}
+
 __global__ void k_mc_advance(SimDyn* dyn, int n) { dyn->step_base += n; }
 __global__ void k_mc_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec) {
   dyn->step_base = step_base;
@@ -368,6 +433,8 @@ MSimD MSim::view() const {
   d.term_sn = term_sn.p;
   d.trig = trig.p;
   d.trip_step = trip_step.p;
+  d.trip_off = trip_off.p;
+  d.R_act = R_act;
   d.trip_elem = trip_elem.p;
   d.trip_a = trip_a.p;
   d.trip_b = trip_b.p;
@@ -503,6 +570,16 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
     tcs.push_back(make_float2(0, 0));
     tsn.push_back(make_float2(0, 0));
   }
+  {
+    std::vector<double> tb;
+    for (int p = 0; p < n; ++p)
+      for (auto& tm : terms[p]) {
+        tb.push_back(tm.coef * std::cos(tm.phi));
+        tb.push_back(tm.coef * std::sin(tm.phi));
+      }
+    if (tb.empty()) tb.assign(2, 0.0);
+    term_base.upload(tb, s);
+  }
   term_ptr.upload(tptr, s);
   term_cs.upload(tcs, s);
   term_sn.upload(tsn, s);
@@ -523,6 +600,9 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   h_trip_elem.assign(R, -1);
   trip_step.upload(h_trip_step, s);
   trip_elem.upload(h_trip_elem, s);
+  h_trip_off.assign(R, 0x7fffffff);
+  trip_off.upload(h_trip_off, s);
+  R_act = R;
   trip_a.upload(std::vector<int>(R, 0), s);
   trip_b.upload(std::vector<int>(R, -1), s);
   trip_delta.upload(std::vector<double>(R, 0.0), s);
@@ -694,22 +774,24 @@ void MSim::prepare_trips(cudaStream_t s) {
 void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s) {
   const DStore st = store->view();
   const MSimD d = view();
-  if (gemm_kind == 2 && umma.ready) umma.launch(*store, Xf.p, Y.p, s);
-  else k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p);
+  if (gemm_kind == 2 && umma.ready) umma.launch(*store, Xf.p, Y.p, s, R_act);
+  else
+    k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p,
+                                      R_act);
   static bool attr = false;
   if (!attr) {
     EMT_CUDA(cudaFuncSetAttribute(k_mc_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  k_mc_sweep<<<(R + sweep_cb - 1) / sweep_cb, 256, sweep_smem, s>>>(st, d, sweep_cb, n1, s_in_chunk,
+  k_mc_sweep<<<(R_act + sweep_cb - 1) / sweep_cb, 256, sweep_smem, s>>>(st, d, sweep_cb, n1, s_in_chunk,
                                                                     store->d_status.p);
-  k_mc_expand<<<dim3(n, (R + 127) / 128), 128, 0, s>>>(st, d, pass, n1, record, s_in_chunk, store->d_status.p);
+  k_mc_expand<<<dim3(n, (R_act + 127) / 128), 128, 0, s>>>(st, d, pass, n1, record, s_in_chunk, store->d_status.p);
   EMT_CUDA(cudaGetLastError());
 }
 
 void MSim::launch_steps(int nst, cudaStream_t s) {
   const MSimD d = view();
-  const dim3 grid(n, (R + 127) / 128);
+  const dim3 grid(n, (R_act + 127) / 128);
   for (int i = 0; i < nst; ++i) {
     k_mc_inject<<<grid, 128, 0, s>>>(d, i, store->d_status.p);
     apply_pass(0, 1, 0, i, s);
@@ -731,7 +813,7 @@ void MSim::step(int n_steps, double* record_dev, cudaStream_t s) {
   launches += 2;
   int left = n_steps;
   while (left >= kChunk) {
-    auto it = graphs.find(kChunk);
+    auto it = graphs.find(R_act);
     if (it == graphs.end()) {
       cudaGraph_t g;
       EMT_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -740,7 +822,7 @@ void MSim::step(int n_steps, double* record_dev, cudaStream_t s) {
       cudaGraphExec_t ge;
       EMT_CUDA(cudaGraphInstantiate(&ge, g, 0));
       cudaGraphDestroy(g);
-      it = graphs.emplace(kChunk, ge).first;
+      it = graphs.emplace(R_act, ge).first;
     }
     EMT_CUDA(cudaGraphLaunch(it->second, s));
     launches += (int64_t)kChunk * 8 + 1;
@@ -751,6 +833,60 @@ void MSim::step(int n_steps, double* record_dev, cudaStream_t s) {
     launches += (int64_t)left * 8 + 1;
   }
   cur_step += n_steps;
+}
+
+void MSim::set_active(int r_act) {
+  EMT_REQUIRE(r_act >= 1 && r_act <= R, EMT_ERR_INVALID, "active column count out of range");
+  R_act = r_act;
+}
+
+void fused_apply_ff64(const Store& st, FusedPlan& p, const double* src, bool src_pos, double* v_pos, cudaStream_t s);
+
+void MSim::admit(int c, int kind, int target, double value, int ev_step, int len, cudaStream_t s) {
+  EMT_REQUIRE(c >= 0 && c < R, EMT_ERR_INVALID, "slot out of range");
+  z_ready = true;   // columns are managed one by one from here on
+  const Tree& t = store->tree;
+  const MSimD d = view();
+  k_mc_reset_col<<<(n_inc + 255) / 256, 256, 0, s>>>(d, n_inc, c);
+  const int n_terms = (int)(term_base.n / 2);
+  const double S = omega * (double)cur_step * dt;
+  k_mc_rotate_terms<<<(n_terms + 127) / 128, 128, 0, s>>>(d, term_base.p, term_cs.p, term_sn.p, n_terms, c, std::cos(S),
+                                                           std::sin(S));
+  int on = 0, off = 0x7fffffff, elem = -1, pa = 0, pb = -1;
+  double delta = 0.0;
+  if (kind == 0) {
+    EMT_REQUIRE(target >= 0 && target < n_series, EMT_ERR_INVALID, "trip target must be a series branch");
+    on = cur_step + ev_step;
+    elem = target;
+    pa = t.pos[el_a[target]];
+    pb = t.pos[el_b[target]];
+    delta = -el_g[target];
+  } else if (kind == 1) {
+    EMT_REQUIRE(target >= 0 && target < n && value > 0 && len > 0, EMT_ERR_INVALID, "bad fault");
+    on = cur_step + ev_step;
+    off = on + len;
+    pa = t.pos[target];
+    delta = 1.0 / value;
+  }
+  k_mc_set_event<<<1, 1, 0, s>>>(trip_step.p, trip_off.p, trip_elem.p, trip_a.p, trip_b.p, trip_delta.p, trip_dff.p, c,
+                                 on, off, elem, pa, pb, delta);
+  if (kind >= 0) {
+    // z_c = Ginv u_c with the accurate single-vector apply (float-float), then d_c in FP64
+    if (!zplan_ready) {
+      make_plan(*store, 0, zplan, s);
+      u_bus.alloc(n);
+      z_pos.alloc(n);
+      zplan_ready = true;
+    }
+    std::vector<double> u(n, 0.0);
+    u[t.perm[pa]] = 1.0;
+    if (pb >= 0) u[t.perm[pb]] = -1.0;
+    EMT_CUDA(cudaMemcpyAsync(u_bus.p, u.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    fused_apply_ff64(*store, zplan, u_bus.p, false, z_pos.p, s);
+    k_mc_set_z<<<(n + 255) / 256, 256, 0, s>>>(d, Z.p, z_pos.p, c);
+    k_mc_one_coef<<<1, 1, 0, s>>>(d, trip_coef.p, c, store->d_status.p);
+  }
+  EMT_CUDA(cudaGetLastError());
 }
 
 void MSim::set_gemm(int kind, cudaStream_t s) {

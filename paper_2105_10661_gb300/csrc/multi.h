@@ -30,6 +30,8 @@ static_assert(sizeof(MRec) == 40, "MRec must be 40 bytes");
 
 struct MSimD {
   int n, R, s_total, n_crow, max_depth;
+  int R_act;            // columns processed (prefix of the R slots)
+  const int* trip_off;  // [R] first step the change is no longer applied (INT_MAX for a trip)
   const MRec* inc;
   const int* inc_ptr;
   float2* Ih;           // [n_inc][R]
@@ -67,7 +69,7 @@ struct Umma {
   DevBuf<uint16_t> a_blocks;
   DevBuf<int4> d_tiles;
   void build(const Store& st, int R, cudaStream_t s);
-  void launch(const Store& st, const float* Xf, float* Y, cudaStream_t s);
+  void launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act);
 };
 
 class MSim {
@@ -82,6 +84,11 @@ class MSim {
   void reset(cudaStream_t s);
   void stats(int64_t* out, int n) const;
   void set_gemm(int kind, cudaStream_t s);   // 1 SIMT FP32, 2 tcgen05 BF16x3
+  // serving: (re)start column c as a new request at the current step, with an optional
+  // per-column change (kind 0 trip of series branch `target`, kind 1 fault at bus `target` with
+  // R_f = value ohm lasting `len` steps, kind -1 none) `ev_step` steps after the start
+  void admit(int c, int kind, int target, double value, int ev_step, int len, cudaStream_t s);
+  void set_active(int r_act);
   MSimD view() const;
   Umma umma;
   int gemm_kind = 2;
@@ -95,7 +102,13 @@ class MSim {
   std::vector<double> el_g;
   // device
   DevBuf<MRec> inc;
-  DevBuf<int> inc_ptr, term_ptr, trip_step, trip_elem, trip_a, trip_b, mon_idx, meta, gemm_tiles;
+  DevBuf<int> inc_ptr, term_ptr, trip_step, trip_elem, trip_a, trip_b, mon_idx, meta, gemm_tiles, trip_off;
+  DevBuf<double> term_base;   // [n_terms][2] coef cos(phi), coef sin(phi) with the column scale 1
+  DevBuf<double> u_bus, z_pos;
+  FusedPlan zplan;
+  bool zplan_ready = false;
+  int R_act = 0;
+  std::vector<int> h_trip_off;
   DevBuf<float2> Ih, V, X, term_cs, term_sn, trig, Z, csr_ff, trip_dff;
   DevBuf<float> Xf, Y, S, fcol;
   DevBuf<double> trip_delta, trip_coef;

@@ -190,6 +190,12 @@ void launch_bench(Sim& sm, int which, int reps, cudaStream_t s) {
 }
 
 void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
+  if (sm.use_v3()) {
+    step3_launch_any(sm, n, s);
+    k_advance<<<1, 1, 0, s>>>(sm.d_dyn.p, n);
+    EMT_CUDA(cudaGetLastError());
+    return;
+  }
   if (sm.use_v2()) {
     step2_launch_any(sm, n, s);
     k_advance<<<1, 1, 0, s>>>(sm.d_dyn.p, n);
@@ -204,6 +210,10 @@ void launch_steps_any(Sim& sm, int n, cudaStream_t s) {
 }
 
 void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
+  if (sm.use_v3()) {
+    step3_bench(sm, which, reps, s);
+    return;
+  }
   if (sm.use_v2()) {
     step2_bench(sm, which, reps, s);
     return;
@@ -218,6 +228,45 @@ void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+// Conductance graph of a network at time step dt: trapezoidal companion conductances of the
+// series branches (ids preserved) and shunt capacitors, then 1/Rs of the sources.
+void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
+                   std::vector<double>& gv) {
+  EMT_REQUIRE(net && dt > 0, EMT_ERR_INVALID, "null network or bad dt");
+  gf.clear();
+  gt.clear();
+  gv.clear();
+  for (int e = 0; e < net->n_branch; ++e) {
+    const int a = net->from[e], b = net->to[e];
+    EMT_REQUIRE(a >= 0 && a < net->n_bus && b >= 0 && b < net->n_bus && a != b, EMT_ERR_INVALID,
+                "series branch endpoints");
+    double g;
+    if (net->kind[e] == EMT_KIND_RL) g = 1.0 / (net->R[e] + 2.0 * net->L[e] / dt);
+    else {
+      EMT_REQUIRE(net->kind[e] == EMT_KIND_RC && net->C[e] > 0, EMT_ERR_INVALID, "bad RC branch");
+      g = 1.0 / (net->R[e] + dt / (2.0 * net->C[e]));
+    }
+    EMT_REQUIRE(std::isfinite(g) && g > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
+    gf.push_back(a);
+    gt.push_back(b);
+    gv.push_back(g);
+  }
+  if (net->shunt_C)
+    for (int i = 0; i < net->n_bus; ++i)
+      if (net->shunt_C[i] > 0) {
+        gf.push_back(i);
+        gt.push_back(-1);
+        gv.push_back(2.0 * net->shunt_C[i] / dt);
+      }
+  for (int k = 0; k < net->n_src; ++k) {
+    EMT_REQUIRE(net->src_bus[k] >= 0 && net->src_bus[k] < net->n_bus && net->src_Rs[k] > 0, EMT_ERR_INVALID,
+                "bad source");
+    gf.push_back(net->src_bus[k]);
+    gt.push_back(-1);
+    gv.push_back(1.0 / net->src_Rs[k]);
+  }
+}
+
 SimD Sim::view() const {
   SimD d;
   d.n = n;
@@ -397,7 +446,7 @@ void Sim::drop_graphs() {
 void Sim::set_rows_per_cta(int rpc, cudaStream_t s) { tune(rpc, kernels, s); }
 
 void Sim::tune(int rpc, int kern, cudaStream_t s) {
-  EMT_REQUIRE(kern == 1 || kern == 2, EMT_ERR_INVALID, "kernels must be 1 or 2");
+  EMT_REQUIRE(kern >= 1 && kern <= 3, EMT_ERR_INVALID, "kernels must be 1, 2 or 3");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second);
@@ -405,6 +454,16 @@ void Sim::tune(int rpc, int kern, cudaStream_t s) {
   make_plan(*store, rpc, plan, s);
   s2.ready = false;
   s2.build(*this, s);
+  s3.ready = false;
+  if (kern == 3 && s2.ready) {
+    int maxb = 0;
+    for (int j = 0; j < store->n_leaf; ++j)
+      maxb = std::max(maxb, store->tree.hi[store->leaf_nodes_h[j]] - store->tree.lo[store->leaf_nodes_h[j]]);
+    const int r = rpc > 0 ? rpc : default_rows_per_cta(*store);
+    int cs = std::max(1, std::min(8, (maxb + r - 1) / r));
+    while (cs > 1 && !s3.build(*this, cs, s)) --cs;
+    if (!s3.ready) s3.build(*this, cs, s);
+  }
   kernels = kern;
   EMT_CUDA(cudaDeviceSynchronize());
 }
@@ -438,10 +497,11 @@ void Sim::autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream
   EMT_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int brpc = 0, bk = 1;
-  for (int k : {2, 1}) {
+  for (int k : {3, 2, 1}) {
     for (int rpc : cands) {
       tune(rpc, k, s);
       if (k == 2 && !s2.ready) continue;
+      if (k == 3 && !use_v3()) continue;
       reset(s);
       step(8, nullptr, s);
       EMT_CUDA(cudaEventRecord(e0, s));
@@ -531,6 +591,7 @@ void Sim::apply_event(const Event& ev, cudaStream_t s) {
   }
   refresh_plan_values(st, plan, s);
   if (s2.ready) s2.refresh(*this, s);
+  if (s3.ready) s3.img.refresh(*this, s);
   EMT_CUDA(cudaGetLastError());
 }
 
@@ -626,6 +687,7 @@ void Sim::reset(cudaStream_t s) {
     s2.reset_state(s);
     s2.refresh(*this, s);
   }
+  if (s3.ready) s3.img.refresh(*this, s);
   snapshots.clear();
   cur_step = 0;
   ev_cursor = 0;

@@ -76,7 +76,7 @@ struct Step2 {
   DevBuf<double> img;
   DevBuf<int> seg_src_d, seg_dst_d, seg_len_d;
   DevBuf<OwnCopy> own_d;
-  bool build(const Sim& sm, cudaStream_t s);
+  bool build(const Sim& sm, cudaStream_t s, int force_prec = -1);
   void refresh(const Sim& sm, cudaStream_t s);
   void reset_state(cudaStream_t s);
   void fill_trig(const Sim& sm, int first_step, int n, cudaStream_t s);
@@ -84,6 +84,20 @@ struct Step2 {
   Step2D view(const Sim& sm) const;
 };
 void step2_launch_any(Sim& sm, int n, cudaStream_t s);
+void step3_sweep(Sim& sm, const Step2& img, const double* ylf, int s_in_chunk, int accumulate, int record, cudaStream_t s);
+
+// Kernel generation 3 (step3.cu): cluster-reduced leaf stage + FP64 sweep.
+struct Step3 {
+  bool ready = false;
+  int cs = 0;                 // CTAs per leaf = cluster size
+  int max_rows = 0, maxb = 0, max_inc = 0;
+  size_t smem_partial = 0;
+  Step2 img;                  // FP64 sweep image
+  DevBuf<double> ylf;         // reduced leaf-stage values per position
+  bool build(Sim& sm, int cs, cudaStream_t s);
+};
+void step3_launch_any(Sim& sm, int n, cudaStream_t s);
+void step3_bench(Sim& sm, int which, int reps, cudaStream_t s);
 void step2_bench(Sim& sm, int which, int reps, cudaStream_t s);
 
 class Sim {
@@ -129,8 +143,10 @@ class Sim {
   int launches_per_step = 2;
   std::vector<std::vector<std::pair<double, double>>> src_terms;   // per position: (coef, phi)
   Step2 s2;
-  int kernels = 2;                             // 1: first-generation step kernels, 2: step2
+  Step3 s3;
+  int kernels = 2;                             // 1: first generation, 2: step2, 3: step3
   bool use_v2() const { return kernels == 2 && s2.ready; }
+  bool use_v3() const { return kernels == 3 && s3.ready && s2.ready; }
 
  private:
   void run(int n_steps, cudaStream_t s);

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_partial(DStore st, CtaM
 }
 
 // ------------------------------------------------------------------ sweep kernel
-template <int PREC>
+template <int PREC, bool FROMY = false>
 __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMapD cm, SimD sim, Step2D q,
                                                                int s_in_chunk, int accumulate, int record,
                                                                const typename Acc<PREC>::X* __restrict__ part) {
@@ -286,13 +286,20 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
   const T* Gn = reinterpret_cast<const T*>(img + H->off_g_bytes);
   const T* R = reinterpret_cast<const T*>(img + H->off_r_bytes);
   const T* C = reinterpret_cast<const T*>(cores);
+  const int nrow = r1 - r0;
+  if constexpr (FROMY) {
+    // generation 3: the leaf stage already holds one reduced value per position
+    const int* cpos = I + H->off_crow_pos;
+    for (int k = tid; k < n_crow; k += kFusedThreads) ycut[k] = A::prep(q.ylf[cpos[k]]);
+    for (int r = tid; r < nrow; r += kFusedThreads) yown[r] = A::prep(q.ylf[lo + r0 + r]);
+    __syncthreads();
+  } else {
   // dynamic: every partial needed (cut rows, then own rows) is loaded in unrolled batches so
   // all loads of a thread are in flight together, then reduced in shared memory
   X* pv = yown + ((r1 - r0) + 1);
   const int* cpair_ptr = I + H->off_cpair_ptr;
   const int* cpair = I + H->off_cpair;
   const int n_cp = H->n_cpair;
-  const int nrow = r1 - r0;
   const int total = n_cp + nrow * lnc;
   for (int base = 0; base < total; base += kFusedThreads * kGatherUnroll) {
     X tmp[kGatherUnroll];
@@ -327,6 +334,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
     yown[r] = a.getx();
   }
   __syncthreads();
+  }
   const int* lvl_item = I + H->off_lvl_item;
   const int* item = I + H->off_item;
   const int* seg = I + H->off_seg;
@@ -448,12 +456,39 @@ void launch_pdl(K kernel, int grid, int block, size_t smem, cudaStream_t s, Args
 
 }  // namespace
 
+// Waits on an mbarrier that never completes, with the same bounded wait as the step kernels.
+__global__ void k_selftest_wait(long long limit_cycles, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, limit_cycles) && threadIdx.x == 0) atomicExch(status, DEV_TIMEOUT);
+}
+
+int selftest_wait(int limit_us, cudaStream_t s) {
+  int dev = 0, khz = 0;
+  EMT_CUDA(cudaGetDevice(&dev));
+  EMT_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  if (khz <= 0) khz = 2000000;
+  DevBuf<int> st;
+  st.alloc(1);
+  st.zero(s);
+  k_selftest_wait<<<1, 32, 0, s>>>((long long)limit_us * khz / 1000, st.p);
+  EMT_CUDA(cudaGetLastError());
+  int h = 0;
+  EMT_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  EMT_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
 // ====================================================================== host side
-bool Step2::build(const Sim& sm, cudaStream_t s) {
+bool Step2::build(const Sim& sm, cudaStream_t s, int force_prec) {
   const Store& st = *sm.store;
   const FusedPlan& p = sm.plan;
   const Tree& t = st.tree;
-  prec = st.precision;
+  prec = force_prec >= 0 ? force_prec : st.precision;
   const size_t tb = prec == EMT_PREC_FP32 ? 4 : 8;
   // partial kernel feasibility: one 16-byte slot per thread, rows per thread <= kRmax
   const int ve = prec == EMT_PREC_FP32 ? 4 : 2;
@@ -549,6 +584,8 @@ bool Step2::build(const Sim& sm, cudaStream_t s) {
     ints.push_back(p.h_leaf_ncta[j]);
     ints.push_back(ps - t.lo[st.leaf_nodes_h[j]]);
   }
+  Hh.off_crow_pos = (int)ints.size();
+  for (int k = 0; k < Hh.n_crow; ++k) ints.push_back(cr.crow_pos[k]);
   Hh.off_cpair_ptr = (int)ints.size();
   {
     std::vector<int> ptr(Hh.n_crow + 1, 0), pairs;
@@ -758,6 +795,7 @@ Step2D Step2::view(const Sim& sm) const {
   d.sweep_smem_static = smem_static;
   d.max_inc = max_inc;
   d.max_lnc = max_lnc;
+  d.ylf = nullptr;
   return d;
 }
 
@@ -803,6 +841,20 @@ void step2_launch(Sim& sm, int n, cudaStream_t s) {
                  (const X*)part);
     }
   }
+}
+
+// Sweep of kernel generation 3: FP64 arithmetic on the reduced leaf values `ylf`.
+void step3_sweep(Sim& sm, const Step2& img, const double* ylf, int s_in_chunk, int accumulate, int record, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    EMT_CUDA(cudaFuncSetAttribute(k_step2_sweep<EMT_PREC_FP64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr = true;
+  }
+  Step2D q = img.view(sm);
+  q.ylf = ylf;
+  launch_pdl(k_step2_sweep<EMT_PREC_FP64, true>, sm.plan.n_cta, kFusedThreads, img.smem_sweep, s, sm.store->view(),
+             sm.plan.cmap(), sm.view(), q, s_in_chunk, accumulate, record, (const double*)nullptr);
 }
 
 void step2_launch_any(Sim& sm, int n, cudaStream_t s) {

@@ -42,6 +42,7 @@ struct ImgHeader {
   int off_core;      // ints: [n_core][4] = s out, t in, m2, c_off
   int off_anc_ptr;   // ints: [n_leaf + 1]
   int off_anc;       // ints: [n_anc][5] = k, kld, split position, s index (left half), s index (right half)
+  int off_crow_pos;  // ints: [n_crow] positions of the distinct cut rows
   int off_cpair_ptr; // ints: [n_crow + 1] ranges into the partial-offset list
   int off_cpair;     // ints: [n_cpair] offsets into the partial buffer
   int n_cpair;
@@ -80,6 +81,7 @@ struct Step2D {
   int own_rows_max;
   int max_inc;                // largest number of element ends owned by one CTA
   int max_lnc;                // largest number of CTAs of one leaf
+  const double* ylf;          // leaf-stage values per position (kernel generation 3), or null
 };
 
 }  // namespace emt

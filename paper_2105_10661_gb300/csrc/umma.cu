@@ -92,6 +92,7 @@ struct UmmaArgs {
   const float* Xf;          // [n][R]
   float* Y;                 // [n][R]
   int R, TN, nkc_max;
+  int r_act;                // columns in use; tiles starting beyond exit at once
 };
 
 // Stage the B chunk (rows k0..k0+63 of the leaf, columns n0..n0+TN) as BF16 hi/lo.
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int4 tl = a.tiles[blockIdx.x];
   const int j = tl.x, m0 = tl.y, n0 = tl.z, blk0 = tl.w;
+  if (n0 >= a.r_act) return;   // uniform per CTA, before any barrier or tensor memory use
   const int node = st.leaf_node[j];
   const int lo = st.lo[node], b = st.hi[node] - lo;
   const int nkc = (b + UKC - 1) / UKC;
@@ -320,12 +322,13 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
   k_tile_leaves<<<n_blocks, 256, 0, s>>>(st.view(), dl.p, dm.p, dk.p, a_blocks.p, n_blocks);
   d_tiles.alloc(tiles.size());
   EMT_CUDA(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-  EMT_CUDA(cudaFuncSetAttribute(k_mc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_smem_bytes(TN)));
+  // the attribute is per kernel, shared by every simulation: allow the largest tile
+  EMT_CUDA(cudaFuncSetAttribute(k_mc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_smem_bytes(256)));
   EMT_CUDA(cudaStreamSynchronize(s));   // the index lists above are freed on return
   ready = true;
 }
 
-void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s) {
+void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act) {
   UmmaArgs a;
   a.tiles = d_tiles.p;
   a.a_blocks = a_blocks.p;
@@ -334,6 +337,7 @@ void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s) {
   a.R = R;
   a.TN = TN;
   a.nkc_max = 0;
+  a.r_act = r_act;
   k_mc_umma<<<n_tiles, 256, umma_smem_bytes(TN), s>>>(st.view(), a, st.d_status.p);
   EMT_CUDA(cudaGetLastError());
 }

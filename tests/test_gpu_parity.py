@@ -179,7 +179,7 @@ def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rp
     return rel_err(got, ref)
 
 
-@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("kernels", [1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sim_179_bus_trip_matches_oracle(L, prec, kernels):
     net = netgen.tile(1_000_000)
@@ -188,7 +188,7 @@ def test_sim_179_bus_trip_matches_oracle(L, prec, kernels):
     assert err <= TOL[prec], err
 
 
-@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("kernels", [1, 2, 3])
 @pytest.mark.parametrize("rpc", [0, 7, 16, 64, 179])
 def test_sim_fault_on_off_and_cta_shapes(L, rpc, kernels):
     net = netgen.tile(1_000_000)
@@ -204,7 +204,7 @@ def test_sim_paper_mode_matches_oracle_paper_stepping(L):
     assert err <= 1e-10, err
 
 
-@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("kernels", [1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sim_1432_bus_matches_oracle(L, prec, kernels):
     net = netgen.tiled(2, 4)
@@ -322,3 +322,14 @@ def test_multi_column_gemm_kinds_match_oracle(L, gemm, which, levels, R, steps):
         ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
         worst = max(worst, rel_err(got[:, c, :], ref))
     assert worst <= 1e-8, worst
+
+
+def test_bounded_wait_times_out_cleanly_and_context_survives(L):
+    # a wait that nothing satisfies runs out after ~1 ms and reports EMT_ERR_TIMEOUT; the
+    # context stays usable for the next call
+    assert L.emt_selftest_bounded_wait(1000) == L.EMT_ERR_TIMEOUT
+    net = netgen.tile(1_000_000)
+    ni = _store_inputs(net)
+    h = _build(L, ni, 2, 0, 0, 1)
+    X = np.random.default_rng(3).standard_normal((net["n_bus"], 1))
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(ni[0].G).solve(X)) <= 1e-10
