@@ -213,12 +213,16 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
  * kernel generation (1 = first generation; 2 = programmatic-dependent-launch kernels with a
  * TMA-staged sweep image, used when the network fits their shared-memory limits, else 1;
  * 3 = thread-block-cluster leaf stage reduced through distributed shared memory and an FP64
- * sweep; rows_per_cta then sets the cluster size, ceil(max leaf / rows_per_cta) <= 8).
+ * sweep; rows_per_cta then sets the cluster size, ceil(max leaf / rows_per_cta) <= 8;
+ * 4 = the whole time loop in one persistent thread-block cluster whose shared memory holds the
+ * store; rows_per_cta then is the cluster size (1, 2, 4, 8 or 16 CTAs), FP64 and FF64 stores
+ * only; EMT_ERR_UNSUPPORTED, with generation 2 selected instead, when the store does not fit).
  * Multi-column simulations: `kernels` selects the leaf-stage GEMM (1 = FP32 CUDA cores,
  * 2 = tcgen05 tensor cores with BF16 splits, used when nrhs is a multiple of 4 and >= 32);
  * rows_per_cta is ignored. Synchronises the device; takes effect on the next emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
-/* Autotuner: time each candidate (rows per CTA in {4..48}, kernel generation 2 then 1) on
+/* Autotuner: time each candidate (cluster sizes 1..16 of generation 4, rows per CTA in {4..48}
+ * of generations 3, 2 and 1) on
  * probe_steps steps of this simulation, keep the fastest and remember it for every later
  * simulation of the same network shape in this process (emt_sim_create applies it). Resets the
  * simulation. Synchronises `stream`. best_rpc / best_kernels (may be NULL) receive the choice. */
@@ -235,8 +239,9 @@ emt_status emt_sim_reset(emt_sim* s, void* stream);
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
 /* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
  * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the
- * sweep/expansion kernel. Leaves the simulation state undefined: call emt_sim_reset
- * afterwards. Asynchronous on `stream`. */
+ * sweep/expansion kernel. With kernel generation 4 it enqueues one launch of the persistent
+ * kernel running `reps` time steps (either `which`). Leaves the simulation state undefined: call
+ * emt_sim_reset afterwards. Asynchronous on `stream`. */
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream);
 void emt_sim_destroy(emt_sim* s);
 

@@ -268,8 +268,16 @@ emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
     EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
-    if (s->msim) s->msim->set_gemm(kernels, nullptr);
-    else s->sim->tune(rows_per_cta, kernels, nullptr);
+    if (s->msim) {
+      s->msim->set_gemm(kernels, nullptr);
+    } else {
+      s->sim->tune(rows_per_cta, kernels, nullptr);
+      if (kernels == 4 && !s->sim->use_v4()) {
+        s->sim->tune(0, 2, nullptr);
+        throw emt::Error(EMT_ERR_UNSUPPORTED,
+                         "kernel generation 4 needs an FP64 or FF64 store that fits one cluster of that size");
+      }
+    }
   });
 }
 

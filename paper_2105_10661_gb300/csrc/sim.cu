@@ -446,7 +446,7 @@ void Sim::drop_graphs() {
 void Sim::set_rows_per_cta(int rpc, cudaStream_t s) { tune(rpc, kernels, s); }
 
 void Sim::tune(int rpc, int kern, cudaStream_t s) {
-  EMT_REQUIRE(kern >= 1 && kern <= 3, EMT_ERR_INVALID, "kernels must be 1, 2 or 3");
+  EMT_REQUIRE(kern >= 1 && kern <= 4, EMT_ERR_INVALID, "kernels must be 1, 2, 3 or 4");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second);
@@ -464,6 +464,8 @@ void Sim::tune(int rpc, int kern, cudaStream_t s) {
     while (cs > 1 && !s3.build(*this, cs, s)) --cs;
     if (!s3.ready) s3.build(*this, cs, s);
   }
+  s4.ready = false;
+  if (kern == 4 && s2.ready) s4.build(*this, rpc > 0 ? rpc : 1, s);
   kernels = kern;
   EMT_CUDA(cudaDeviceSynchronize());
 }
@@ -497,11 +499,16 @@ void Sim::autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream
   EMT_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int brpc = 0, bk = 1;
-  for (int k : {3, 2, 1}) {
-    for (int rpc : cands) {
+  const int cands4[] = {1, 2, 4, 8, 16};
+  for (int k : {4, 3, 2, 1}) {
+    const int* cb = k == 4 ? cands4 : cands;
+    const int nc = k == 4 ? 5 : (int)(sizeof(cands) / sizeof(cands[0]));
+    for (int ci = 0; ci < nc; ++ci) {
+      const int rpc = cb[ci];
       tune(rpc, k, s);
       if (k == 2 && !s2.ready) continue;
       if (k == 3 && !use_v3()) continue;
+      if (k == 4 && !use_v4()) continue;
       reset(s);
       step(8, nullptr, s);
       EMT_CUDA(cudaEventRecord(e0, s));
@@ -592,6 +599,7 @@ void Sim::apply_event(const Event& ev, cudaStream_t s) {
   refresh_plan_values(st, plan, s);
   if (s2.ready) s2.refresh(*this, s);
   if (s3.ready) s3.img.refresh(*this, s);
+  if (s4.ready) s4.refresh(*this, s);
   EMT_CUDA(cudaGetLastError());
 }
 
@@ -633,6 +641,14 @@ void Sim::run(int n_steps, cudaStream_t s) {
     if (ev_cursor < events.size()) stretch = std::min(stretch, events[ev_cursor].step - next);
     stretch = std::max(stretch, 1);
     int left = stretch;
+    if (use_v4()) {
+      // one persistent launch for the whole stretch between events
+      step4_launch(*this, stretch, s);
+      k_advance<<<1, 1, 0, s>>>(d_dyn.p, stretch);
+      EMT_CUDA(cudaGetLastError());
+      launches += (cur_rec && n_mon > 0 && store->precision == EMT_PREC_FF64) ? 3 : 2;
+      left = 0;
+    }
     while (left >= kChunk) {
       auto it = graphs.find(kChunk);
       if (it == graphs.end()) {
@@ -664,6 +680,7 @@ void Sim::step(int n_steps, double* record_dev, cudaStream_t s) {
   k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
   EMT_CUDA(cudaGetLastError());
   launches += 1;
+  cur_rec = record_dev;
   if (s2.ready) {
     s2.fill_trig(*this, cur_step + 1, n_steps, s);
     launches += 1;
@@ -688,6 +705,7 @@ void Sim::reset(cudaStream_t s) {
     s2.refresh(*this, s);
   }
   if (s3.ready) s3.img.refresh(*this, s);
+  if (s4.ready) s4.refresh(*this, s);
   snapshots.clear();
   cur_step = 0;
   ev_cursor = 0;
@@ -716,6 +734,15 @@ void Sim::stats(int64_t* out, int n_out) const {
 void Sim::bench_kernel(int which, int reps, cudaStream_t s) {
   EMT_REQUIRE(which == 0 || which == 1, EMT_ERR_INVALID, "which must be 0 or 1");
   EMT_REQUIRE(reps >= 1 && reps <= 100000, EMT_ERR_INVALID, "reps out of range");
+  if (use_v4()) {
+    // the persistent kernel runs `reps` time steps in one launch
+    k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, nullptr);
+    s2.fill_trig(*this, cur_step + 1, reps, s);
+    cur_rec = nullptr;
+    step4_launch(*this, reps, s);
+    EMT_CUDA(cudaGetLastError());
+    return;
+  }
   const int key = which * 1000000 + reps;
   auto it = bench_graphs.find(key);
   if (it == bench_graphs.end()) {

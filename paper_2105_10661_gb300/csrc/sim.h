@@ -73,6 +73,7 @@ struct Step2 {
   DevBuf<double2> d_src_sum;
   DevBuf<int> d_src_ptr;
   DevBuf<double> trig;
+  DevBuf<float4> trigff;
   DevBuf<double> img;
   DevBuf<int> seg_src_d, seg_dst_d, seg_len_d;
   DevBuf<OwnCopy> own_d;
@@ -97,6 +98,32 @@ struct Step3 {
   bool build(Sim& sm, int cs, cudaStream_t s);
 };
 void step3_launch_any(Sim& sm, int n, cudaStream_t s);
+
+// Kernel generation 4 (step4.cu): the whole time loop in one persistent thread-block cluster.
+struct Step4D {
+  int C, P;         // CTAs in the cluster; most CTAs sharing one leaf
+  int o_x, o_part, o_ycp, o_ycut, o_yvp, o_s, o_v, o_contrib, o_row, o_vrow, o_out, o_push, o_img, o_K, o_L, o_F;
+  int max_vrows, img_int_bytes, ldk, n_crow;
+  const int* hdr;   // [C][24] per-CTA header
+  const int* tab;   // per-CTA tables
+  const double* K;  // [s_total][ldk] matrix of the boundary sweep (8-byte elements)
+  float2* rec_ff;   // float-float record of this launch ([n_steps][n_mon]), or null
+};
+struct Step4 {
+  bool ready = false;
+  int C = 0, P = 1;
+  size_t smem = 0;
+  size_t o_x = 0, o_part = 0, o_ycp = 0, o_ycut = 0, o_yvp = 0, o_s = 0, o_v = 0, o_contrib = 0, o_row = 0,
+         o_vrow = 0, o_out = 0, o_push = 0, o_img = 0, o_K = 0, o_L = 0, o_F = 0;
+  int max_vrows = 0, img_int_bytes = 0, ldk = 0, n_crow = 0, s_total = 0;
+  DevBuf<int> hdr, tab;
+  DevBuf<double> K;        // s = K y_cut (FP64 or float-float pairs)
+  DevBuf<float2> rec_ff;   // float-float record of one launch, converted to FP64 afterwards
+  bool build(Sim& sm, int n_cta, cudaStream_t s);
+  void refresh(const Sim& sm, cudaStream_t s);
+  Step4D view() const;
+};
+void step4_launch(Sim& sm, int n, cudaStream_t s);
 void step3_bench(Sim& sm, int which, int reps, cudaStream_t s);
 void step2_bench(Sim& sm, int which, int reps, cudaStream_t s);
 
@@ -140,13 +167,16 @@ class Sim {
   DevBuf<double> inc_g0, inc_alpha0, inc_beta0;
   std::vector<double> el_g0;
   int64_t launches = 0;                        // kernels enqueued by step/reset
+  double* cur_rec = nullptr;                   // record buffer of the current emt_step call
   int launches_per_step = 2;
   std::vector<std::vector<std::pair<double, double>>> src_terms;   // per position: (coef, phi)
   Step2 s2;
   Step3 s3;
-  int kernels = 2;                             // 1: first generation, 2: step2, 3: step3
+  Step4 s4;
+  int kernels = 2;                             // 1: first generation, 2: step2, 3: step3, 4: step4
   bool use_v2() const { return kernels == 2 && s2.ready; }
   bool use_v3() const { return kernels == 3 && s3.ready && s2.ready; }
+  bool use_v4() const { return kernels == 4 && s4.ready && s2.ready; }
 
  private:
   void run(int n_steps, cudaStream_t s);

@@ -89,13 +89,15 @@ __global__ void k_img_refresh(DStore st, unsigned char* img, int off_g, int n_cu
   }
 }
 
-__global__ void k_trig(double* trig, int first_step, int n, double omega, double dt) {
+__global__ void k_trig(double* trig, float4* trigff, int first_step, int n, double omega, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s, c;
   sincos(omega * ((double)(first_step + i) * dt), &s, &c);
   trig[2 * i] = s;
   trig[2 * i + 1] = c;
+  const float2 fs = ff_from(s), fc = ff_from(c);
+  trigff[i] = make_float4(fs.x, fs.y, fc.x, fc.y);
 }
 
 // ------------------------------------------------------------------ partial kernel
@@ -283,9 +285,6 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
   X* t = ycut + n_crow;
   X* s = t + s_total;
   X* yown = s + s_total;
-  const T* Gn = reinterpret_cast<const T*>(img + H->off_g_bytes);
-  const T* R = reinterpret_cast<const T*>(img + H->off_r_bytes);
-  const T* C = reinterpret_cast<const T*>(cores);
   const int nrow = r1 - r0;
   if constexpr (FROMY) {
     // generation 3: the leaf stage already holds one reduced value per position
@@ -335,70 +334,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
   }
   __syncthreads();
   }
-  const int* lvl_item = I + H->off_lvl_item;
-  const int* item = I + H->off_item;
-  const int* seg = I + H->off_seg;
-  const int* lvl_core = I + H->off_lvl_core;
-  const int* core = I + H->off_core;
-  // Dot products are split over groups of kGroup threads (shuffle-reduced) so that no thread
-  // runs a long dependent float-float chain; the loops are warp-uniform for the shuffles.
-  const int grp = tid / kGroup, gl = tid % kGroup;
-  constexpr int kGroups = kFusedThreads / kGroup;
-  for (int d = H->max_depth - 1; d >= 0; --d) {
-    const int i0 = lvl_item[d], i1 = lvl_item[d + 1];
-    for (int base = i0; base < i1; base += kGroups) {
-      const int it = base + grp;
-      A a;
-      const int* rec = item + 6 * (it < i1 ? it : i0);
-      if (it < i1) {
-        if (gl == 0) a.add(ycut[rec[0]]);
-        const T* rv = R + rec[3];
-        for (int sg = rec[4]; sg < rec[4] + rec[5]; ++sg) {
-          const int si = seg[2 * sg], k = seg[2 * sg + 1];
-          for (int e = gl; e < k; e += kGroup) a.fma(rv[e], neg(s[si + e]));
-          rv += k;
-        }
-      }
-      X val = a.getx();
-#pragma unroll
-      for (int o = kGroup / 2; o > 0; o >>= 1) {
-        A tt;
-        tt.add(val);
-        tt.add(a.shfl_xor(val, o));
-        val = tt.getx();
-      }
-      if (it < i1 && gl == 0) {
-        if (rec[2] >= 0) {
-          A m;
-          m.fma(Gn[rec[2]], val);
-          val = m.getx();
-        }
-        t[rec[1]] = val;
-      }
-    }
-    __syncthreads();
-    const int j0 = lvl_core[d], j1 = lvl_core[d + 1];
-    for (int base = j0; base < j1; base += kGroups) {
-      const int w = base + grp;
-      A a;
-      const int* rec = core + 4 * (w < j1 ? w : j0);
-      if (w < j1) {
-        const T* Cr = C + rec[3];
-        const X* tq = t + rec[1];
-        for (int e = gl; e < rec[2]; e += kGroup) a.fma(Cr[e], tq[e]);
-      }
-      X val = a.getx();
-#pragma unroll
-      for (int o = kGroup / 2; o > 0; o >>= 1) {
-        A tt;
-        tt.add(val);
-        tt.add(a.shfl_xor(val, o));
-        val = tt.getx();
-      }
-      if (w < j1 && gl == 0) s[rec[0]] = val;
-    }
-    __syncthreads();
-  }
+  sweep_levels<PREC, kGroup>(img, cores, ycut, t, s);
   // expansion of the own rows: warp per row
   const int* anc_ptr = I + H->off_anc_ptr;
   const int* anc = I + H->off_anc;
@@ -659,8 +595,6 @@ bool Step2::build(const Sim& sm, cudaStream_t s, int force_prec) {
   Hh.off_core = (int)ints.size();
   {
     // core rows in increasing depth order (lvl_nodes_h is grouped by increasing depth)
-    int64_t cbase = 0;   // core image holds the store's C array as is
-    (void)cbase;
     for (int q : st.lvl_nodes_h) {
       const int m2 = 2 * st.node_k_h[q];
       for (int r = 0; r < m2; ++r) {
@@ -768,8 +702,11 @@ void Step2::reset_state(cudaStream_t s) {
 }
 
 void Step2::fill_trig(const Sim& sm, int first_step, int n, cudaStream_t s) {
-  if ((size_t)2 * n > trig.n) trig.alloc((size_t)2 * std::max(n, 1024));
-  k_trig<<<(n + 255) / 256, 256, 0, s>>>(trig.p, first_step, n, sm.omega, sm.dt);
+  if ((size_t)2 * n > trig.n) {
+    trig.alloc((size_t)2 * std::max(n, 1024));
+    trigff.alloc((size_t)std::max(n, 1024));
+  }
+  k_trig<<<(n + 255) / 256, 256, 0, s>>>(trig.p, trigff.p, first_step, n, sm.omega, sm.dt);
   EMT_CUDA(cudaGetLastError());
 }
 
@@ -782,6 +719,7 @@ Step2D Step2::view(const Sim& sm) const {
   d.src = d_src.p;
   d.src_ptr = d_src_ptr.p;
   d.trig = trig.p;
+  d.trigff = trigff.p;
   d.img = reinterpret_cast<const unsigned char*>(img.p);
   d.img_bytes = header.img_bytes;
   d.cores = prec == EMT_PREC_FP64 ? reinterpret_cast<const unsigned char*>(st.C64.p)

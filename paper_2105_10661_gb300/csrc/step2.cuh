@@ -70,6 +70,7 @@ struct Step2D {
   const SrcRec* src;
   const int* src_ptr;
   const double* trig;      // [2 * n] sin, cos of w t per step (indexed from trig_first)
+  const float4* trigff;    // [n] the same as float-float pairs: sin hi, lo, cos hi, lo
   // sweep kernel
   const unsigned char* img;
   int img_bytes;
@@ -83,5 +84,90 @@ struct Step2D {
   int max_lnc;                // largest number of CTAs of one leaf
   const double* ylf;          // leaf-stage values per position (kernel generation 3), or null
 };
+
+// Boundary sweep of every tree node, bottom-up, from the shared-memory image: at each depth,
+// t = (-g) y_cut - sum over deeper ancestors of (factor row . s) for every cut endpoint (the
+// gather form of t_p = [h_l^T y_l; h_r^T y_r], Eq. 9 factors), then s = C t per node. ycut holds
+// the leaf-stage value of every distinct cut row. Dot products are split over groups of kGroup
+// threads (shuffle-reduced) so that no thread runs a long dependent chain; loops are
+// warp-uniform for the shuffles. Uses every thread of the block; ends with __syncthreads.
+template <int PREC, int kGroup>
+__device__ __forceinline__ void sweep_levels(const unsigned char* img, const unsigned char* cores,
+                                             const typename Acc<PREC>::X* ycut, typename Acc<PREC>::X* t,
+                                             typename Acc<PREC>::X* s) {
+  using A = Acc<PREC>;
+  using X = typename A::X;
+  using T = typename A::T;
+  const ImgHeader* H = reinterpret_cast<const ImgHeader*>(img);
+  const int* I = reinterpret_cast<const int*>(img);
+  const T* Gn = reinterpret_cast<const T*>(img + H->off_g_bytes);
+  const T* R = reinterpret_cast<const T*>(img + H->off_r_bytes);
+  const T* C = reinterpret_cast<const T*>(cores);
+  const int* lvl_item = I + H->off_lvl_item;
+  const int* item = I + H->off_item;
+  const int* seg = I + H->off_seg;
+  const int* lvl_core = I + H->off_lvl_core;
+  const int* core = I + H->off_core;
+  const int grp = threadIdx.x / kGroup, gl = threadIdx.x % kGroup;
+  const int n_groups = blockDim.x / kGroup;
+  const int g_warp = (threadIdx.x >> 5) * (32 / kGroup);   // first group of this warp
+  for (int d = H->max_depth - 1; d >= 0; --d) {
+    const int i0 = lvl_item[d], i1 = lvl_item[d + 1];
+    for (int base = i0; base < i1; base += n_groups) {
+      if (base + g_warp >= i1) break;   // the whole warp is idle for the rest of this phase
+      const int it = base + grp;
+      A a;
+      const int* rec = item + 6 * (it < i1 ? it : i0);
+      if (it < i1) {
+        if (gl == 0) a.add(ycut[rec[0]]);
+        const T* rv = R + rec[3];
+        for (int sg = rec[4]; sg < rec[4] + rec[5]; ++sg) {
+          const int si = seg[2 * sg], k = seg[2 * sg + 1];
+          for (int e = gl; e < k; e += kGroup) a.fma(rv[e], neg(s[si + e]));
+          rv += k;
+        }
+      }
+      X val = a.getx();
+#pragma unroll
+      for (int o = kGroup / 2; o > 0; o >>= 1) {
+        A tt;
+        tt.add(val);
+        tt.add(a.shfl_xor(val, o));
+        val = tt.getx();
+      }
+      if (it < i1 && gl == 0) {
+        if (rec[2] >= 0) {
+          A m;
+          m.fma(Gn[rec[2]], val);
+          val = m.getx();
+        }
+        t[rec[1]] = val;
+      }
+    }
+    __syncthreads();
+    const int j0 = lvl_core[d], j1 = lvl_core[d + 1];
+    for (int base = j0; base < j1; base += n_groups) {
+      if (base + g_warp >= j1) break;
+      const int w = base + grp;
+      A a;
+      const int* rec = core + 4 * (w < j1 ? w : j0);
+      if (w < j1) {
+        const T* Cr = C + rec[3];
+        const X* tq = t + rec[1];
+        for (int e = gl; e < rec[2]; e += kGroup) a.fma(Cr[e], tq[e]);
+      }
+      X val = a.getx();
+#pragma unroll
+      for (int o = kGroup / 2; o > 0; o >>= 1) {
+        A tt;
+        tt.add(val);
+        tt.add(a.shfl_xor(val, o));
+        val = tt.getx();
+      }
+      if (w < j1 && gl == 0) s[rec[0]] = val;
+    }
+    __syncthreads();
+  }
+}
 
 }  // namespace emt

@@ -197,6 +197,43 @@ def test_sim_fault_on_off_and_cta_shapes(L, rpc, kernels):
     assert err <= 1e-10, err
 
 
+@pytest.mark.parametrize("cs", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sim_persistent_cluster_179_bus_events(L, prec, cs):
+    # one cluster of cs CTAs runs the time loop; cs < 4 groups whole leaves, cs > 4 splits them
+    net = netgen.tile(1_000_000)
+    ev = [(30, 1, 17, 10.0), (90, 2, 17, 0.0), (100, 0, netgen.pick_branch(net), 0.0)]
+    err = _sim_compare(L, net, 2, 140, ev, prec, rpc=cs, kernels=4)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sim_persistent_cluster_1432_bus(L, prec):
+    net = netgen.tiled(2, 4)
+    e = netgen.pick_branch(net)
+    err = _sim_compare(L, net, 3, 200, [(100, 0, e, 0.0)], prec, rpc=16, kernels=4)
+    assert err <= TOL[prec], err
+
+
+def test_sim_persistent_cluster_rejects_what_does_not_fit(L):
+    # eight CTAs would each hold a whole 179-row leaf (258 KB): more than one CTA's shared memory
+    sim = L.emt_sim_create(netgen.tiled(2, 4), DT, levels=3, precision=L.EMT_PREC_FF64)
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_sim_tune(sim, 8, 4)
+    assert ex.value.code == L.EMT_ERR_UNSUPPORTED
+    sim32 = L.emt_sim_create(netgen.tile(1_000_000), DT, levels=2, precision=L.EMT_PREC_FP32)
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_sim_tune(sim32, 1, 4)
+    assert ex.value.code == L.EMT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cs", [1, 4, 16])
+def test_sim_persistent_cluster_ragged_network(L, cs):
+    net = netgen.small_network(37, 5)
+    err = _sim_compare(L, net, 3, 90, [(40, 0, 3, 0.0)], 1, rpc=cs, kernels=4)
+    assert err <= 1e-10, err
+
+
 def test_sim_paper_mode_matches_oracle_paper_stepping(L):
     net = netgen.tile(1_000_000)
     e = netgen.pick_branch(net)
