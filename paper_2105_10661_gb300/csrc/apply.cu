@@ -234,6 +234,7 @@ void make_plan(const Store& st, int rows_per_cta, FusedPlan& p, cudaStream_t s) 
 }
 
 void refresh_plan_values(const Store& st, FusedPlan& p, cudaStream_t s) {
+  if (p.sa) p.sa->refresh(st, s);
   const int nc = (int)st.cut_g_h.size();
   if (nc == 0) return;
   k_neg_g<<<(nc + 255) / 256, 256, 0, s>>>(nc, st.d_cut_g.p, p.cut_gn64.p, p.cut_gnff.p, p.cut_gn32.p);
@@ -242,6 +243,10 @@ void refresh_plan_values(const Store& st, FusedPlan& p, cudaStream_t s) {
 
 void fused_apply(const Store& st, FusedPlan& p, const double* src, bool src_pos, double* v_pos, double* v_bus,
                  bool accumulate, cudaStream_t s) {
+  if (p.sa && p.sa->ready) {
+    stream_apply(st, *p.sa, src, src_pos, v_pos, v_bus, accumulate, s);
+    return;
+  }
   switch (st.precision) {
     case EMT_PREC_FP64: launch_apply<EMT_PREC_FP64>(st, p, src, src_pos, v_pos, v_bus, accumulate, s); break;
     case EMT_PREC_FF64: launch_apply<EMT_PREC_FF64>(st, p, src, src_pos, v_pos, v_bus, accumulate, s); break;
@@ -259,6 +264,10 @@ void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>
                    double* v_dev, int nrhs, int64_t ld, int max_refine, cudaStream_t s) {
   if (vpos.n < (size_t)st.n) vpos.alloc(st.n);
   if (rpos.n < (size_t)st.n) rpos.alloc(st.n);
+  if (!p.sa && stream_apply_wanted(st)) {
+    auto sa = std::make_shared<StreamApply>();
+    if (sa->build(st, s)) p.sa = sa;
+  }
   const bool refine = st.precision == EMT_PREC_FP32 && max_refine > 0;
   for (int c = 0; c < nrhs; ++c) {
     const double* src = i_dev + (int64_t)c * ld;

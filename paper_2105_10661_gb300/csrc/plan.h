@@ -1,11 +1,35 @@
 // Launch plan of the fused single-vector kernels for one store: which rows each CTA owns,
 // the distinct cut endpoints of the boundary sweep, and the per-CTA partial buffer.
 #pragma once
+#include <memory>
 #include <vector>
 
-#include "fused.cuh"
+#include "step2.cuh"
 
 namespace emt {
+
+// Ancestor record of a leaf for the streaming expansion: F offset of the leaf's first row at
+// that ancestor, its row stride, k, and the index of the half of s the leaf's rows use.
+struct StreamAnc {
+  long long foff;
+  int kld, k, sidx, pad;
+};
+
+// Streaming apply for stores larger than the caches (stream.cu): row ranges of the persistent
+// leaf-stream CTAs, the sweep image and matrix K (s = K y_cut), ancestor records for the
+// expansion, and the intermediate vectors.
+struct StreamApply {
+  bool ready = false;
+  int prec = 0, n_cta = 0, stage_elems = 0, n_crow = 0, s_total = 0, ldk = 0, n_seg = 0, max_stages = 0, n_anc = 0;
+  size_t smem = 0, smem_ldg = 0;
+  bool ldg = false;                  // leaf stage: plain 16-byte loads instead of the TMA ring
+  ImgHeader hdr{};
+  DevBuf<double> img, K, y, ycut, sv;   // 8-byte elements (FP64 or float-float pairs)
+  DevBuf<int> seg_src, seg_dst, seg_len, row0, crow_of, anc_ptr;
+  DevBuf<StreamAnc> anc;             // ancestor records, grouped per leaf (anc_ptr)
+  bool build(const Store& st, cudaStream_t s);
+  void refresh(const Store& st, cudaStream_t s);   // after a modification of the store
+};
 
 struct FusedPlan {
   int rows_per_cta = 0;
@@ -22,6 +46,7 @@ struct FusedPlan {
   DevBuf<double> cut_gn64;   // -g_e per cut, per precision
   DevBuf<float2> cut_gnff;
   DevBuf<float> cut_gn32;
+  std::shared_ptr<StreamApply> sa;   // built on first use for large stores (emt_apply)
   CtaMapD cmap() const;
   CutRowsD crows() const;
 };
@@ -31,6 +56,9 @@ void make_plan(const Store& st, int rows_per_cta, FusedPlan& plan, cudaStream_t 
 // Refresh the -g_e copies after a modification.
 void refresh_plan_values(const Store& st, FusedPlan& plan, cudaStream_t s);
 int default_rows_per_cta(const Store& st);
+bool stream_apply_wanted(const Store& st);
+void stream_apply(const Store& st, StreamApply& sa, const double* src, bool src_pos, double* v_pos, double* v_bus,
+                  bool accumulate, cudaStream_t s);
 
 // One single-vector application in the store's precision.
 //   src: bus-ordered input (src_pos == false) or position-ordered (true)

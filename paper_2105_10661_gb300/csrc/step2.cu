@@ -420,6 +420,157 @@ int selftest_wait(int limit_us, cudaStream_t s) {
 }
 
 // ====================================================================== host side
+// Boundary-sweep image of a store: header, integer tables (distinct cut rows, sweep items by
+// depth, factor segments, core rows, ancestor lists per leaf), -g per cut and the factor rows
+// every item needs. With a plan, the cut rows also carry the CTAs whose partial sums hold them.
+void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader& hdr, DevBuf<double>& img,
+                       DevBuf<int>& seg_src, DevBuf<int>& seg_dst, DevBuf<int>& seg_len, int& n_seg, cudaStream_t s) {
+  const Tree& t = st.tree;
+  const size_t tb = prec == EMT_PREC_FP32 ? 4 : 8;
+  const CutRows& cr = st.cut_rows;
+  std::vector<int> ints;
+  ImgHeader Hh{};
+  auto align_ints = [&]() {
+    while ((ints.size() * 4) % 16) ints.push_back(0);
+  };
+  ints.resize((sizeof(ImgHeader) + 15) / 16 * 4, 0);
+  Hh.n_crow = (int)cr.crow_pos.size();
+  Hh.n_items = cr.n_items;
+  Hh.s_total = st.s_total;
+  Hh.max_depth = t.max_depth;
+  Hh.n_leaf = st.n_leaf;
+  Hh.n_cut = (int)st.cut_g_h.size();
+  Hh.off_crow = (int)ints.size();
+  for (int k = 0; k < Hh.n_crow; ++k) {
+    const int ps = cr.crow_pos[k];
+    const int j = leaf_index_of_pos(st, ps);
+    ints.push_back(p ? p->h_leaf_cta0[j] : 0);
+    ints.push_back(p ? p->h_leaf_ncta[j] : 0);
+    ints.push_back(ps - t.lo[st.leaf_nodes_h[j]]);
+  }
+  Hh.off_crow_pos = (int)ints.size();
+  for (int k = 0; k < Hh.n_crow; ++k) ints.push_back(cr.crow_pos[k]);
+  Hh.off_cpair_ptr = (int)ints.size();
+  {
+    std::vector<int> ptr(Hh.n_crow + 1, 0), pairs;
+    for (int k = 0; k < Hh.n_crow; ++k) {
+      const int ps = cr.crow_pos[k];
+      const int j = leaf_index_of_pos(st, ps);
+      const int loc = ps - t.lo[st.leaf_nodes_h[j]];
+      if (p)
+        for (int u = 0; u < p->h_leaf_ncta[j]; ++u) pairs.push_back((p->h_leaf_cta0[j] + u) * p->pld + loc);
+      ptr[k + 1] = (int)pairs.size();
+    }
+    for (int v : ptr) ints.push_back(v);
+    Hh.off_cpair = (int)ints.size();
+    Hh.n_cpair = (int)pairs.size();
+    for (int v : pairs) ints.push_back(v);
+  }
+  // items by increasing depth
+  std::vector<int> order(cr.n_items);
+  for (int i = 0; i < cr.n_items; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return t.depth[cr.item_node[x]] < t.depth[cr.item_node[y]]; });
+  Hh.off_lvl_item = (int)ints.size();
+  {
+    std::vector<int> lvl(t.max_depth + 2, 0);
+    for (int i = 0; i < cr.n_items; ++i) lvl[t.depth[cr.item_node[i]] + 1]++;
+    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
+    for (int v : lvl) ints.push_back(v);
+  }
+  Hh.off_item = (int)ints.size();
+  ints.resize(ints.size() + 6 * (size_t)cr.n_items);
+  std::vector<int> segs;               // pairs
+  std::vector<int> seg_src_h, seg_dst_h, seg_len_h;
+  int r_elems = 0;
+  for (int w = 0; w < cr.n_items; ++w) {
+    const int it = order[w];
+    const int q = cr.item_node[it];
+    const int d = t.depth[q];
+    const int ps = cr.item_pos[it];
+    const int k = st.node_k_h[q];
+    const int slot = cr.item_sidx[it] - st.node_soff_h[q];
+    int* rec = &ints[Hh.off_item + 6 * w];
+    rec[0] = cr.item_crow[it];
+    rec[1] = cr.item_sidx[it];
+    rec[2] = slot < k ? t.cut_ptr[q] + slot : -1;
+    rec[3] = r_elems;
+    rec[4] = (int)segs.size() / 2;
+    int nseg = 0;
+    for (int a = t.parent[st.leaf_nodes_h[leaf_index_of_pos(st, ps)]]; a >= 0 && t.depth[a] > d; a = t.parent[a]) {
+      const int ka = st.node_k_h[a];
+      if (ka == 0) continue;
+      const int half = ps < t.hi[t.left[a]] ? 0 : ka;
+      segs.push_back(st.node_soff_h[a] + half);
+      segs.push_back(ka);
+      seg_src_h.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * st.node_kld_h[a]));
+      seg_dst_h.push_back(r_elems);
+      seg_len_h.push_back(ka);
+      r_elems += ka;
+      ++nseg;
+    }
+    rec[5] = nseg;
+  }
+  Hh.off_seg = (int)ints.size();
+  Hh.n_seg = (int)segs.size() / 2;
+  for (int v : segs) ints.push_back(v);
+  Hh.off_lvl_core = (int)ints.size();
+  {
+    std::vector<int> lvl(t.max_depth + 2, 0);
+    for (int q : st.lvl_nodes_h) lvl[t.depth[q] + 1] += 2 * st.node_k_h[q];
+    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
+    for (int v : lvl) ints.push_back(v);
+  }
+  Hh.off_core = (int)ints.size();
+  {
+    // core rows in increasing depth order (lvl_nodes_h is grouped by increasing depth)
+    for (int q : st.lvl_nodes_h) {
+      const int m2 = 2 * st.node_k_h[q];
+      for (int r = 0; r < m2; ++r) {
+        ints.push_back(st.node_soff_h[q] + r);
+        ints.push_back(st.node_soff_h[q]);
+        ints.push_back(m2);
+        ints.push_back((int)(st.node_coff_h[q] + (int64_t)r * m2));
+      }
+    }
+    Hh.n_core = (int)((ints.size() - Hh.off_core) / 4);
+  }
+  Hh.off_anc_ptr = (int)ints.size();
+  std::vector<int> anc_list;
+  std::vector<int> anc_ptr(st.n_leaf + 1, 0);
+  for (int j = 0; j < st.n_leaf; ++j) {
+    for (int a = t.parent[st.leaf_nodes_h[j]]; a >= 0; a = t.parent[a]) {
+      anc_list.push_back(st.node_k_h[a]);
+      anc_list.push_back(st.node_kld_h[a]);
+      anc_list.push_back(t.hi[t.left[a]]);
+      anc_list.push_back(st.node_soff_h[a]);
+      anc_list.push_back(st.node_soff_h[a] + st.node_k_h[a]);
+      anc_ptr[j + 1]++;
+    }
+    anc_ptr[j + 1] += anc_ptr[j];
+  }
+  for (int v : anc_ptr) ints.push_back(v);
+  Hh.off_anc = (int)ints.size();
+  for (int v : anc_list) ints.push_back(v);
+  align_ints();
+  Hh.int_words = (int)ints.size();
+  Hh.off_g_bytes = Hh.int_words * 4;
+  const size_t g_bytes = (Hh.n_cut * tb + 15) / 16 * 16;
+  Hh.off_r_bytes = (int)(Hh.off_g_bytes + g_bytes);
+  const size_t r_bytes = ((size_t)r_elems * tb + 15) / 16 * 16;
+  Hh.img_bytes = (int)(Hh.off_r_bytes + std::max<size_t>(r_bytes, 16));
+  std::memcpy(ints.data(), &Hh, sizeof(ImgHeader));
+  img.alloc((Hh.img_bytes + 7) / 8);
+  EMT_CUDA(cudaMemsetAsync(img.p, 0, Hh.img_bytes, s));
+  EMT_CUDA(cudaMemcpyAsync(img.p, ints.data(), ints.size() * 4, cudaMemcpyHostToDevice, s));
+  hdr = Hh;
+  seg_src.upload(seg_src_h.empty() ? std::vector<int>{0} : seg_src_h, s);
+  seg_dst.upload(seg_dst_h.empty() ? std::vector<int>{0} : seg_dst_h, s);
+  seg_len.upload(seg_len_h.empty() ? std::vector<int>{0} : seg_len_h, s);
+  n_seg = (int)seg_src_h.size();
+  refresh_sweep_image(st, prec, hdr, img, seg_src, seg_dst, seg_len, n_seg, s);
+}
+
 bool Step2::build(const Sim& sm, cudaStream_t s, int force_prec) {
   const Store& st = *sm.store;
   const FusedPlan& p = sm.plan;
@@ -498,147 +649,8 @@ bool Step2::build(const Sim& sm, cudaStream_t s, int force_prec) {
     d_src_sum.upload(ssum, s);
   }
   d_src_ptr.upload(sptr, s);
-  // ---- sweep image
-  const CutRows& cr = st.cut_rows;
-  std::vector<int> ints;
-  ImgHeader Hh{};
-  auto align_ints = [&]() {
-    while ((ints.size() * 4) % 16) ints.push_back(0);
-  };
-  ints.resize((sizeof(ImgHeader) + 15) / 16 * 4, 0);
-  Hh.n_crow = (int)cr.crow_pos.size();
-  Hh.n_items = cr.n_items;
-  Hh.s_total = st.s_total;
-  Hh.max_depth = t.max_depth;
-  Hh.n_leaf = st.n_leaf;
-  Hh.n_cut = (int)st.cut_g_h.size();
-  Hh.off_crow = (int)ints.size();
-  for (int k = 0; k < Hh.n_crow; ++k) {
-    const int ps = cr.crow_pos[k];
-    const int j = leaf_index_of_pos(st, ps);
-    ints.push_back(p.h_leaf_cta0[j]);
-    ints.push_back(p.h_leaf_ncta[j]);
-    ints.push_back(ps - t.lo[st.leaf_nodes_h[j]]);
-  }
-  Hh.off_crow_pos = (int)ints.size();
-  for (int k = 0; k < Hh.n_crow; ++k) ints.push_back(cr.crow_pos[k]);
-  Hh.off_cpair_ptr = (int)ints.size();
-  {
-    std::vector<int> ptr(Hh.n_crow + 1, 0), pairs;
-    for (int k = 0; k < Hh.n_crow; ++k) {
-      const int ps = cr.crow_pos[k];
-      const int j = leaf_index_of_pos(st, ps);
-      const int loc = ps - t.lo[st.leaf_nodes_h[j]];
-      for (int u = 0; u < p.h_leaf_ncta[j]; ++u) pairs.push_back((p.h_leaf_cta0[j] + u) * p.pld + loc);
-      ptr[k + 1] = (int)pairs.size();
-    }
-    for (int v : ptr) ints.push_back(v);
-    Hh.off_cpair = (int)ints.size();
-    Hh.n_cpair = (int)pairs.size();
-    for (int v : pairs) ints.push_back(v);
-  }
-  // items by increasing depth
-  std::vector<int> order(cr.n_items);
-  for (int i = 0; i < cr.n_items; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return t.depth[cr.item_node[x]] < t.depth[cr.item_node[y]]; });
-  Hh.off_lvl_item = (int)ints.size();
-  {
-    std::vector<int> lvl(t.max_depth + 2, 0);
-    for (int i = 0; i < cr.n_items; ++i) lvl[t.depth[cr.item_node[i]] + 1]++;
-    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
-    for (int v : lvl) ints.push_back(v);
-  }
-  Hh.off_item = (int)ints.size();
-  ints.resize(ints.size() + 6 * (size_t)cr.n_items);
-  std::vector<int> segs;               // pairs
-  std::vector<int> seg_src, seg_dst, seg_len;
-  int r_elems = 0;
-  for (int w = 0; w < cr.n_items; ++w) {
-    const int it = order[w];
-    const int q = cr.item_node[it];
-    const int d = t.depth[q];
-    const int ps = cr.item_pos[it];
-    const int k = st.node_k_h[q];
-    const int slot = cr.item_sidx[it] - st.node_soff_h[q];
-    int* rec = &ints[Hh.off_item + 6 * w];
-    rec[0] = cr.item_crow[it];
-    rec[1] = cr.item_sidx[it];
-    rec[2] = slot < k ? t.cut_ptr[q] + slot : -1;
-    rec[3] = r_elems;
-    rec[4] = (int)segs.size() / 2;
-    int nseg = 0;
-    for (int a = t.parent[st.leaf_nodes_h[leaf_index_of_pos(st, ps)]]; a >= 0 && t.depth[a] > d; a = t.parent[a]) {
-      const int ka = st.node_k_h[a];
-      if (ka == 0) continue;
-      const int half = ps < t.hi[t.left[a]] ? 0 : ka;
-      segs.push_back(st.node_soff_h[a] + half);
-      segs.push_back(ka);
-      seg_src.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * st.node_kld_h[a]));
-      seg_dst.push_back(r_elems);
-      seg_len.push_back(ka);
-      r_elems += ka;
-      ++nseg;
-    }
-    rec[5] = nseg;
-  }
-  Hh.off_seg = (int)ints.size();
-  Hh.n_seg = (int)segs.size() / 2;
-  for (int v : segs) ints.push_back(v);
-  Hh.off_lvl_core = (int)ints.size();
-  {
-    std::vector<int> lvl(t.max_depth + 2, 0);
-    for (int q : st.lvl_nodes_h) lvl[t.depth[q] + 1] += 2 * st.node_k_h[q];
-    for (int d = 0; d <= t.max_depth; ++d) lvl[d + 1] += lvl[d];
-    for (int v : lvl) ints.push_back(v);
-  }
-  Hh.off_core = (int)ints.size();
-  {
-    // core rows in increasing depth order (lvl_nodes_h is grouped by increasing depth)
-    for (int q : st.lvl_nodes_h) {
-      const int m2 = 2 * st.node_k_h[q];
-      for (int r = 0; r < m2; ++r) {
-        ints.push_back(st.node_soff_h[q] + r);
-        ints.push_back(st.node_soff_h[q]);
-        ints.push_back(m2);
-        ints.push_back((int)(st.node_coff_h[q] + (int64_t)r * m2));
-      }
-    }
-    Hh.n_core = (int)((ints.size() - Hh.off_core) / 4);
-  }
-  Hh.off_anc_ptr = (int)ints.size();
-  std::vector<int> anc_list;
-  std::vector<int> anc_ptr(st.n_leaf + 1, 0);
-  for (int j = 0; j < st.n_leaf; ++j) {
-    for (int a = t.parent[st.leaf_nodes_h[j]]; a >= 0; a = t.parent[a]) {
-      anc_list.push_back(st.node_k_h[a]);
-      anc_list.push_back(st.node_kld_h[a]);
-      anc_list.push_back(t.hi[t.left[a]]);
-      anc_list.push_back(st.node_soff_h[a]);
-      anc_list.push_back(st.node_soff_h[a] + st.node_k_h[a]);
-      anc_ptr[j + 1]++;
-    }
-    anc_ptr[j + 1] += anc_ptr[j];
-  }
-  for (int v : anc_ptr) ints.push_back(v);
-  Hh.off_anc = (int)ints.size();
-  for (int v : anc_list) ints.push_back(v);
-  align_ints();
-  Hh.int_words = (int)ints.size();
-  Hh.off_g_bytes = Hh.int_words * 4;
-  const size_t g_bytes = (Hh.n_cut * tb + 15) / 16 * 16;
-  Hh.off_r_bytes = (int)(Hh.off_g_bytes + g_bytes);
-  const size_t r_bytes = ((size_t)r_elems * tb + 15) / 16 * 16;
-  Hh.img_bytes = (int)(Hh.off_r_bytes + std::max<size_t>(r_bytes, 16));
-  std::memcpy(ints.data(), &Hh, sizeof(ImgHeader));
-  img.alloc((Hh.img_bytes + 7) / 8);
-  EMT_CUDA(cudaMemsetAsync(img.p, 0, Hh.img_bytes, s));
-  EMT_CUDA(cudaMemcpyAsync(img.p, ints.data(), ints.size() * 4, cudaMemcpyHostToDevice, s));
-  header = Hh;
-  seg_src_d.upload(seg_src.empty() ? std::vector<int>{0} : seg_src, s);
-  seg_dst_d.upload(seg_dst.empty() ? std::vector<int>{0} : seg_dst, s);
-  seg_len_d.upload(seg_len.empty() ? std::vector<int>{0} : seg_len, s);
-  n_seg_copy = (int)seg_src.size();
+  build_sweep_image(st, &p, prec, header, img, seg_src_d, seg_dst_d, seg_len_d, n_seg_copy, s);
+  const ImgHeader& Hh = header;
   core_bytes = (int)(st.C_elems * tb);
   // own factor rows per CTA
   std::vector<OwnCopy> own(p.n_cta);
@@ -674,8 +686,9 @@ bool Step2::build(const Sim& sm, cudaStream_t s, int force_prec) {
   return true;
 }
 
-void Step2::refresh(const Sim& sm, cudaStream_t s) {
-  const Store& st = *sm.store;
+void refresh_sweep_image(const Store& st, int prec, const ImgHeader& header, DevBuf<double>& img,
+                         const DevBuf<int>& seg_src_d, const DevBuf<int>& seg_dst_d, const DevBuf<int>& seg_len_d,
+                         int n_seg_copy, cudaStream_t s) {
   const DStore v = st.view();
   const int nth = 256;
   const int work = std::max(header.n_cut, n_seg_copy);
@@ -695,6 +708,69 @@ void Step2::refresh(const Sim& sm, cudaStream_t s) {
                                                         seg_src_d.p, seg_dst_d.p, seg_len_d.p, n_seg_copy);
   }
   EMT_CUDA(cudaGetLastError());
+}
+
+// K[:, c] = s for y_cut = e_c: the boundary sweep (every tree node, bottom-up) is linear in the
+// cut-row values, so one sweep per unit vector gives the matrix of the whole sweep. One CTA per
+// column; rows of K have leading dimension ldk (zero beyond n_crow). The image and cores are
+// staged in shared memory when they fit, else read from global memory (L2).
+template <int PREC>
+__global__ void k_build_K(const unsigned char* __restrict__ img, int img_bytes, const unsigned char* __restrict__ cores,
+                          int core_bytes, int staged, int n_crow, int s_total, int ldk,
+                          typename Acc<PREC>::T* __restrict__ K) {
+  using A = Acc<PREC>;
+  using X = typename A::X;
+  extern __shared__ __align__(16) unsigned char smk[];
+  const unsigned char* im = img;
+  const unsigned char* co = cores;
+  unsigned char* vec = smk;
+  if (staged) {
+    for (int i = threadIdx.x; i < img_bytes / 16; i += blockDim.x)
+      reinterpret_cast<int4*>(smk)[i] = reinterpret_cast<const int4*>(img)[i];
+    for (int i = threadIdx.x; i < core_bytes / 16; i += blockDim.x)
+      reinterpret_cast<int4*>(smk + img_bytes)[i] = reinterpret_cast<const int4*>(cores)[i];
+    im = smk;
+    co = smk + img_bytes;
+    vec = smk + img_bytes + core_bytes;
+  }
+  X* ycut = reinterpret_cast<X*>(vec);
+  X* t = ycut + n_crow;
+  X* sv = t + s_total;
+  const int c = blockIdx.x;
+  for (int i = threadIdx.x; i < n_crow; i += blockDim.x) ycut[i] = A::prep(i == c ? 1.0 : 0.0);
+  __syncthreads();
+  sweep_levels<PREC, 8>(im, co, ycut, t, sv);
+  for (int r = threadIdx.x; r < s_total; r += blockDim.x) K[(int64_t)r * ldk + c] = sv[r];
+}
+
+void build_sweep_matrix(int prec, const unsigned char* img, int img_bytes, const unsigned char* cores, int core_bytes,
+                        int n_crow, int s_total, int ldk, void* K, cudaStream_t s) {
+  if (n_crow == 0 || s_total == 0) return;
+  const size_t vec = (size_t)(n_crow + 2 * s_total) * 8;
+  int dev = 0, optin = 0;
+  EMT_CUDA(cudaGetDevice(&dev));
+  EMT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int staged = (size_t)img_bytes + (size_t)core_bytes + vec <= (size_t)optin ? 1 : 0;
+  const size_t smem_k = vec + (staged ? (size_t)img_bytes + (size_t)core_bytes : 0);
+  EMT_REQUIRE(smem_k <= (size_t)optin, EMT_ERR_UNSUPPORTED, "sweep vectors too large for one CTA");
+  if (prec == EMT_PREC_FF64) {
+    EMT_CUDA(cudaFuncSetAttribute(k_build_K<EMT_PREC_FF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+    k_build_K<EMT_PREC_FF64><<<n_crow, 256, smem_k, s>>>(img, img_bytes, cores, core_bytes, staged, n_crow, s_total, ldk,
+                                                         reinterpret_cast<float2*>(K));
+  } else if (prec == EMT_PREC_FP64) {
+    EMT_CUDA(cudaFuncSetAttribute(k_build_K<EMT_PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+    k_build_K<EMT_PREC_FP64><<<n_crow, 256, smem_k, s>>>(img, img_bytes, cores, core_bytes, staged, n_crow, s_total, ldk,
+                                                         reinterpret_cast<double*>(K));
+  } else {
+    EMT_CUDA(cudaFuncSetAttribute(k_build_K<EMT_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+    k_build_K<EMT_PREC_FP32><<<n_crow, 256, smem_k, s>>>(img, img_bytes, cores, core_bytes, staged, n_crow, s_total, ldk,
+                                                         reinterpret_cast<float*>(K));
+  }
+  EMT_CUDA(cudaGetLastError());
+}
+
+void Step2::refresh(const Sim& sm, cudaStream_t s) {
+  refresh_sweep_image(*sm.store, prec, header, img, seg_src_d, seg_dst_d, seg_len_d, n_seg_copy, s);
 }
 
 void Step2::reset_state(cudaStream_t s) {

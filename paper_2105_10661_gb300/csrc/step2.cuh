@@ -16,6 +16,8 @@
 
 namespace emt {
 
+struct FusedPlan;
+
 // One element end: the history source of a bus-to-bus element lives at both ends and both copies
 // evolve identically (same operands, same instruction sequence).
 struct IncRec {
@@ -84,6 +86,17 @@ struct Step2D {
   int max_lnc;                // largest number of CTAs of one leaf
   const double* ylf;          // leaf-stage values per position (kernel generation 3), or null
 };
+
+// Build / refresh the sweep image of a store (a plan, when given, adds the CTAs holding each cut
+// row's partial sums), and the matrix form of the sweep: K ([s_total][ldk] elements of the
+// precision) with s = K y_cut.
+void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader& hdr, DevBuf<double>& img,
+                       DevBuf<int>& seg_src, DevBuf<int>& seg_dst, DevBuf<int>& seg_len, int& n_seg, cudaStream_t s);
+void refresh_sweep_image(const Store& st, int prec, const ImgHeader& hdr, DevBuf<double>& img,
+                         const DevBuf<int>& seg_src, const DevBuf<int>& seg_dst, const DevBuf<int>& seg_len,
+                         int n_seg, cudaStream_t s);
+void build_sweep_matrix(int prec, const unsigned char* img, int img_bytes, const unsigned char* cores, int core_bytes,
+                        int n_crow, int s_total, int ldk, void* K, cudaStream_t s);
 
 // Boundary sweep of every tree node, bottom-up, from the shared-memory image: at each depth,
 // t = (-g) y_cut - sum over deeper ancestors of (factor row . s) for every cut endpoint (the

@@ -449,31 +449,6 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   }
 }
 
-// K[:, c] = s for y_cut = e_c: the boundary sweep (every tree node, bottom-up) is linear in the
-// cut-row values, so one sweep per unit vector gives the matrix of the whole sweep. One CTA per
-// column; rows of K have leading dimension ldk (zero beyond n_crow).
-template <int PREC>
-__global__ void k_build_K(const unsigned char* __restrict__ img, int img_bytes, const unsigned char* __restrict__ cores,
-                          int core_bytes, int n_crow, int s_total, int ldk, typename Acc<PREC>::T* __restrict__ K) {
-  using A = Acc<PREC>;
-  using X = typename A::X;
-  extern __shared__ __align__(16) unsigned char smk[];
-  unsigned char* im = smk;
-  unsigned char* co = smk + img_bytes;
-  X* ycut = reinterpret_cast<X*>(co + core_bytes);
-  X* t = ycut + n_crow;
-  X* sv = t + s_total;
-  const int c = blockIdx.x;
-  for (int i = threadIdx.x; i < img_bytes / 16; i += blockDim.x)
-    reinterpret_cast<int4*>(im)[i] = reinterpret_cast<const int4*>(img)[i];
-  for (int i = threadIdx.x; i < core_bytes / 16; i += blockDim.x)
-    reinterpret_cast<int4*>(co)[i] = reinterpret_cast<const int4*>(cores)[i];
-  for (int i = threadIdx.x; i < n_crow; i += blockDim.x) ycut[i] = A::prep(i == c ? 1.0 : 0.0);
-  __syncthreads();
-  sweep_levels<PREC, 8>(im, co, ycut, t, sv);
-  for (int r = threadIdx.x; r < s_total; r += blockDim.x) K[(int64_t)r * ldk + c] = sv[r];
-}
-
 // FP64 record rows of one launch from its float-float staging record (before the step counter
 // advances past the launch)
 __global__ void k_rec_ff(const float2* __restrict__ rec_ff, int n, const SimDyn* dyn, int n_mon) {
@@ -585,19 +560,9 @@ Step4D Step4::view() const {
 
 // K from the current sweep image (after a build, a modification or a reset).
 void Step4::refresh(const Sim& sm, cudaStream_t s) {
-  if (!ready || n_crow == 0 || s_total == 0) return;
+  if (!ready) return;
   const Step2D q = sm.s2.view(sm);
-  const size_t smem_k = (size_t)q.img_bytes + (size_t)q.core_bytes + (size_t)(n_crow + 2 * s_total) * 8;
-  if (sm.store->precision == EMT_PREC_FF64) {
-    EMT_CUDA(cudaFuncSetAttribute(k_build_K<EMT_PREC_FF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-    k_build_K<EMT_PREC_FF64><<<n_crow, 256, smem_k, s>>>(q.img, q.img_bytes, q.cores, q.core_bytes, n_crow, s_total,
-                                                         ldk, reinterpret_cast<float2*>(K.p));
-  } else {
-    EMT_CUDA(cudaFuncSetAttribute(k_build_K<EMT_PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-    k_build_K<EMT_PREC_FP64><<<n_crow, 256, smem_k, s>>>(q.img, q.img_bytes, q.cores, q.core_bytes, n_crow, s_total,
-                                                         ldk, K.p);
-  }
-  EMT_CUDA(cudaGetLastError());
+  build_sweep_matrix(sm.store->precision, q.img, q.img_bytes, q.cores, q.core_bytes, n_crow, s_total, ldk, K.p, s);
 }
 
 // Host plan: positions per CTA, halos, leaf-stage outputs and their push destinations, copy
