@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_partial(DStore st, CtaM
 template <int PREC, bool FROMY = false>
 __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMapD cm, SimD sim, Step2D q,
                                                                int s_in_chunk, int accumulate, int record,
-                                                               const typename Acc<PREC>::X* __restrict__ part) {
+                                                               const typename Acc<PREC>::X* part) {
   using A = Acc<PREC>;
   using X = typename A::X;
   using T = typename A::T;
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
   if constexpr (FROMY) {
     // generation 3: the leaf stage already holds one reduced value per position
     const int* cpos = I + H->off_crow_pos;
-    for (int k = tid; k < n_crow; k += kFusedThreads) ycut[k] = A::prep(q.ylf[cpos[k]]);
-    for (int r = tid; r < nrow; r += kFusedThreads) yown[r] = A::prep(q.ylf[lo + r0 + r]);
+    for (int k = tid; k < n_crow; k += kFusedThreads) ycut[k] = A::prep(__ldcg(q.ylf + cpos[k]));
+    for (int r = tid; r < nrow; r += kFusedThreads) yown[r] = A::prep(__ldcg(q.ylf + lo + r0 + r));
     __syncthreads();
   } else {
   // dynamic: every partial needed (cut rows, then own rows) is loaded in unrolled batches so
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMap
           const int w = i - n_cp;
           off = (int64_t)(lc0 + w % lnc) * cm.pld + r0 + w / lnc;
         }
-        tmp[u] = part[off];
+        tmp[u] = __ldcg(part + off);   // written by the preceding grid: read through L2, never hoisted
       }
     }
 #pragma unroll

@@ -74,6 +74,12 @@ __device__ __forceinline__ void ld2(const double* p, double (&e)[2]) {
   e[1] = v.y;
 }
 
+// Buffers written by an earlier grid of the same stream are read through L2 (ld.global.cg): with
+// programmatic dependent launch a grid starts before its predecessor ends, so no read of such a
+// buffer may go through the non-coherent or L1 path.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+
 template <int PREC>
 __device__ __forceinline__ typename Acc<PREC>::X warp_sum(const Acc<PREC>& a, int lanes) {
   using A = Acc<PREC>;
@@ -105,7 +111,7 @@ struct StageRec {
 // the stream.
 template <int PREC>
 __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __restrict__ row0,
-                                                        const int* __restrict__ crow_of, const double* __restrict__ src,
+                                                        const int* __restrict__ crow_of, const double* src,
                                                         int src_pos, typename Acc<PREC>::X* __restrict__ y,
                                                         typename Acc<PREC>::X* __restrict__ ycut, int stage_elems,
                                                         int max_stages) {
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
       }
       double val[kG];
 #pragma unroll
-      for (int u = 0; u < kG; ++u) val[u] = idx[u] >= 0 ? src[idx[u]] : 0.0;
+      for (int u = 0; u < kG; ++u) val[u] = idx[u] >= 0 ? ldcg(src + idx[u]) : 0.0;
 #pragma unroll
       for (int u = 0; u < kG; ++u) {
         const int p = base + u * kST;
@@ -260,7 +266,7 @@ constexpr int kLT = 768;
 constexpr int kLdgChunk = 12;   // 16-byte loads per lane per pass (rows up to 768 elements)
 template <int PREC>
 __global__ void __launch_bounds__(kLT, 1) k_leaf_ldg(DStore st, const int* __restrict__ row0,
-                                                     const int* __restrict__ crow_of, const double* __restrict__ src,
+                                                     const int* __restrict__ crow_of, const double* src,
                                                      int src_pos, typename Acc<PREC>::X* __restrict__ y,
                                                      typename Acc<PREC>::X* __restrict__ ycut) {
   using A = Acc<PREC>;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kLT, 1) k_leaf_ldg(DStore st, const int* __res
       }
       double val[kG];
 #pragma unroll
-      for (int u = 0; u < kG; ++u) val[u] = idx[u] >= 0 ? src[idx[u]] : 0.0;
+      for (int u = 0; u < kG; ++u) val[u] = idx[u] >= 0 ? ldcg(src + idx[u]) : 0.0;
 #pragma unroll
       for (int u = 0; u < kG; ++u) {
         const int p = base + u * kLT;
@@ -336,8 +342,8 @@ __global__ void __launch_bounds__(kLT, 1) k_leaf_ldg(DStore st, const int* __res
 
 // s = K y_cut: y_cut staged in shared memory, one warp per row of K
 template <int PREC>
-__global__ void __launch_bounds__(256) k_sweep_matrix(const typename Acc<PREC>::T* __restrict__ K, int s_total, int ldk,
-                                                      int n_crow, const typename Acc<PREC>::X* __restrict__ ycut_g,
+__global__ void __launch_bounds__(128) k_sweep_matrix(const typename Acc<PREC>::T* __restrict__ K, int s_total, int ldk,
+                                                      int n_crow, const typename Acc<PREC>::X* ycut_g,
                                                       typename Acc<PREC>::X* __restrict__ s) {
   using A = Acc<PREC>;
   using X = typename A::X;
@@ -349,11 +355,11 @@ __global__ void __launch_bounds__(256) k_sweep_matrix(const typename Acc<PREC>::
   const int lane = threadIdx.x & 31;
   const T* Kr = K + (int64_t)(row < s_total ? row : 0) * ldk;
   pdl_wait_s();
-  for (int k = threadIdx.x; k < n_crow; k += blockDim.x) yc[k] = ycut_g[k];
+  for (int k = threadIdx.x; k < n_crow; k += blockDim.x) yc[k] = ldcg(ycut_g + k);
   __syncthreads();
   if (row >= s_total) return;
   A a, a2;
-  constexpr int kU = 8;   // loads in flight per lane
+  constexpr int kU = 18;   // loads in flight per lane (one pass for up to 576 cut rows)
   for (int base = 0; base < n_crow; base += 32 * kU) {
     T kv[kU];
 #pragma unroll
@@ -378,15 +384,15 @@ __global__ void __launch_bounds__(256) k_sweep_matrix(const typename Acc<PREC>::
 // v = y - sum over ancestors of F row . s(half); 16 lanes per position, two positions per warp.
 // s and the ancestor records sit in shared memory. A lane takes elements lane + 16 m (m < 4) of
 // every ancestor's factor row (k <= 64 per pass; longer rows take further passes), and the loads
-// of up to kMaxAnc ancestors are all issued before the first product, so a position costs about
-// one DRAM round trip.
-constexpr int kMaxAnc = 6;
+// of up to kMaxAnc ancestors (deeper paths take further rounds) are all issued before the first
+// product, so a position costs about one DRAM round trip per round.
+constexpr int kMaxAnc = 4;
 constexpr int kEL = 16;   // lanes per position
 template <int PREC>
-__global__ void __launch_bounds__(256) k_expand_stream(DStore st, const StreamAnc* __restrict__ anc,
+__global__ void __launch_bounds__(256, 4) k_expand_stream(DStore st, const StreamAnc* __restrict__ anc,
                                                        const int* __restrict__ anc_ptr, int n_anc, int s_total,
-                                                       const typename Acc<PREC>::X* __restrict__ y,
-                                                       const typename Acc<PREC>::X* __restrict__ s_g, double* __restrict__ v_pos,
+                                                       const typename Acc<PREC>::X* y,
+                                                       const typename Acc<PREC>::X* s_g, double* __restrict__ v_pos,
                                                        double* __restrict__ v_bus, int accumulate) {
   using A = Acc<PREC>;
   using X = typename A::X;
@@ -404,7 +410,8 @@ __global__ void __launch_bounds__(256) k_expand_stream(DStore st, const StreamAn
   const int lo = st.lo[st.leaf_node[j]];
   const int x0 = anc_ptr[j], x1 = valid ? anc_ptr[j + 1] : anc_ptr[j];
   pdl_wait_s();
-  for (int i = threadIdx.x; i < s_total; i += blockDim.x) ss[i] = s_g[i];
+  const X yp = ldcg(y + pp);   // in flight with the loads below
+  for (int i = threadIdx.x; i < s_total; i += blockDim.x) ss[i] = ldcg(s_g + i);
   __syncthreads();
   const T* F = Elem<PREC>::F(st);
   A a, a2;
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(256) k_expand_stream(DStore st, const StreamAn
   const X w = warp_sum<PREC>(a, kEL);
   if (valid && gl == 0) {
     A f;
-    f.add(y[pp]);
+    f.add(yp);
     f.add(w);
     double out = A::todbl(f.getx());
     if (accumulate) out += v_pos[pp];
@@ -487,7 +494,7 @@ void launch_stream(const Store& st, StreamApply& sa, const double* src, bool src
     launch_pdl_s(k_leaf_stream<PREC>, sa.n_cta, kST, sa.smem, s, v, (const int*)sa.row0.p, (const int*)sa.crow_of.p,
                  src, src_pos ? 1 : 0, y, yc, sa.stage_elems, sa.max_stages);
   if (sa.s_total > 0 && sa.n_crow > 0) {
-    const int wpb = 8;
+    const int wpb = 4;
     launch_pdl_s(k_sweep_matrix<PREC>, (sa.s_total + wpb - 1) / wpb, wpb * 32, (size_t)sa.n_crow * 8, s,
                  (const T*)sa.K.p, sa.s_total, sa.ldk, sa.n_crow, (const X*)yc, sv);
   }
