@@ -15,6 +15,14 @@ struct StreamAnc {
   int kld, k, sidx, pad;
 };
 
+// Stage of the leaf stream: element offset of its first row in the store, the row stride (the
+// leaf's ld), rows (1 or 2, one leaf), the x-window offset of the leaf, the leaf size, the cut-row
+// indices of the rows (-1: none) and the position of the first row.
+struct StreamStage {
+  long long off;
+  int ld, nr, xo, b, crow0, crow1, p, pad;
+};
+
 // Streaming apply for stores larger than the caches (stream.cu): row ranges of the persistent
 // leaf-stream CTAs, the sweep image and matrix K (s = K y_cut), ancestor records for the
 // expansion, and the intermediate vectors.
@@ -25,7 +33,9 @@ struct StreamApply {
   bool ldg = false;                  // leaf stage: plain 16-byte loads instead of the TMA ring
   ImgHeader hdr{};
   DevBuf<double> img, K, y, ycut, sv;   // 8-byte elements (FP64 or float-float pairs)
-  DevBuf<int> seg_src, seg_dst, seg_len, row0, crow_of, anc_ptr;
+  DevBuf<int> seg_src, seg_dst, seg_len, row0, crow_of, anc_ptr, st0;
+  DevBuf<StreamStage> stages;        // leaf-stream stages, grouped per CTA (st0)
+  DevBuf<int2> win;                  // per CTA: x window [x, y)
   DevBuf<StreamAnc> anc;             // ancestor records, grouped per leaf (anc_ptr)
   bool build(const Store& st, cudaStream_t s);
   void refresh(const Store& st, cudaStream_t s);   // after a modification of the store

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
     const int warp = tid >> 5, lane = tid & 31;
     for (int u = warp; u < hd[H_NFC]; u += kT4 / 32) {
       const int so = fc[3 * u], dst = fc[3 * u + 1], len = fc[3 * u + 2];
-      for (int e = lane; e < len; e += 32) Fs[dst + e] = Fg[so + e];
+      for (int e = lane; e < len; e += 32) Fs[dst + (int64_t)e * d.fstride] = Fg[so + e];
     }
     for (int i = tid; i < ns * ldk; i += kT4) Ks[i] = Kg[(int64_t)s0 * ldk + i];
     // partial slots a CTA never receives (leaves split into fewer than P parts) stay zero
@@ -415,14 +415,17 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       const int* vr = vrow + kVR * (i < nv ? i : 0);
       if (i < nv) {
         const int pos = vr[0], j = vr[2];
-        const T* Fr = Fs + vr[1];
+        // factor rows are stored element-major (element e of row i at e * fstride + i), so the
+        // lanes of a warp, which take consecutive rows, read consecutive words
+        const T* Fr = Fs + i;
+        const int fs = d.fstride;
         for (int x = anc_ptr[j]; x < anc_ptr[j + 1]; ++x) {
           const int* an = anc + 5 * x;
           const int k = an[0];
           const int si = pos < an[2] ? an[3] : an[4];
 #pragma unroll 4
-          for (int e = gl_e; e < k; e += le) a.fma(Fr[e], neg(ss[si + e]));
-          Fr += an[1];
+          for (int e = gl_e; e < k; e += le) a.fma(Fr[(int64_t)e * fs], neg(ss[si + e]));
+          Fr += (int64_t)an[1] * fs;
         }
       }
       const X w = group_sum<PREC>(a, le);
@@ -547,6 +550,7 @@ Step4D Step4::view() const {
   v.o_K = (int)o_K;
   v.o_L = (int)o_L;
   v.o_F = (int)o_F;
+  v.fstride = fstride;
   v.max_vrows = max_vrows;
   v.img_int_bytes = img_int_bytes;
   v.ldk = ldk;
@@ -668,6 +672,7 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
   std::vector<int> n_out(n_cta, 0), lpv(n_cta, 1), n_push(n_cta, 0);
   int max_rows = 0, max_ends = 0, max_out = 0, max_push = 0, max_part = 0;
   int64_t maxL = 0, maxF = 0;
+  int max_packed = 0;   // longest packed factor row (sum of kld over a path)
   max_vrows = 0;
   for (int c = 0; c < n_cta; ++c) {
     const int nr = cp1[c] - cp0[c];
@@ -682,6 +687,8 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     for (int ps : halo[c]) Fe += frow(ps);
     maxL = std::max(maxL, Le);
     maxF = std::max(maxF, Fe);
+    for (int ps = cp0[c]; ps < cp1[c]; ++ps) max_packed = std::max(max_packed, (int)frow(ps));
+    for (int ps : halo[c]) max_packed = std::max(max_packed, (int)frow(ps));
     for (int j = cj0[c]; j < cj1[c]; ++j) {
       n_out[c] += lb[j];
       for (int r = 0; r < lb[j]; ++r) {
@@ -716,7 +723,11 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
   o_img = off;       off = align16(off + (size_t)img_int_bytes);
   o_K = off;         off = align16(off + (size_t)max_slice * ldk * tb);
   o_L = off;         off = align16(off + (size_t)maxL * tb);
-  o_F = off;         off = align16(off + (size_t)maxF * tb);
+  // element-major factor rows: stride = 8 (mod 16) elements, so two 8-byte columns of one warp
+  // fall in different halves of the banks
+  fstride = max_vrows + ((8 - max_vrows % 16) + 16) % 16;
+  (void)maxF;
+  o_F = off;         off = align16(off + (size_t)max_packed * fstride * tb);
   smem = off;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -755,19 +766,19 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     for (int ps = cp0[c]; ps < cp1[c]; ++ps) vpos.push_back(ps);
     for (int ps : halo[c]) vpos.push_back(ps);
     std::vector<int> vr, fc;
-    int64_t fdst = 0;
     for (size_t i = 0; i < vpos.size(); ++i) {
       const int ps = vpos[i];
+      int64_t fdst = 0;   // element offset within the row's packed sequence
       const int j = leaf_of(ps);
       vr.push_back(ps);
-      vr.push_back((int)fdst);
+      vr.push_back((int)i);
       vr.push_back(j);
       vr.push_back(i < (size_t)nr ? (int)i : -1);
       for (int a = t.parent[st.leaf_nodes_h[j]]; a >= 0; a = t.parent[a]) {
         const int kld = st.node_kld_h[a];
         if (kld > 0) {
           fc.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * kld));
-          fc.push_back((int)fdst);
+          fc.push_back((int)(fdst * fstride + (int64_t)i));
           fc.push_back(kld);
         }
         fdst += kld;

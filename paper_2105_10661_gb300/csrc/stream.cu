@@ -80,6 +80,26 @@ __device__ __forceinline__ void ld2(const double* p, double (&e)[2]) {
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 
+// Copy n vector entries written by the preceding grid into shared memory, all loads of a thread
+// in flight together (one DRAM round trip for up to 8 entries per thread).
+template <typename X>
+__device__ __forceinline__ void stage_vec(X* dst, const X* src, int n) {
+  constexpr int kU = 8;
+  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
+    X v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < n) v[u] = ldcg(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < n) dst[i] = v[u];
+    }
+  }
+}
+
 template <int PREC>
 __device__ __forceinline__ typename Acc<PREC>::X warp_sum(const Acc<PREC>& a, int lanes) {
   using A = Acc<PREC>;
@@ -96,23 +116,15 @@ __device__ __forceinline__ typename Acc<PREC>::X warp_sum(const Acc<PREC>& a, in
 __device__ __forceinline__ void pdl_wait_s() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_go_s() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Per-stage copy record of the leaf stream: element offset of the stage's first row in the store,
-// the row stride (the leaf's ld), the number of rows (1 or 2, same leaf), the x-window offset of
-// the leaf, the leaf size, the cut-row indices of the rows (-1: not a cut row) and the position of
-// the first row.
-struct StageRec {
-  long long off;
-  int ld, nr, xo, b, crow0, crow1, p, pad;   // p: position of the first row
-};
-
-// rows [row0[c], row0[c + 1]) of CTA c (row = position); y in position order, vector type.
-// y_cut (the distinct cut rows, in their order) is written as well. The x window is gathered and
-// the stage table built before the first copy is issued, so the gather does not queue behind
-// the stream.
+// Stages [st0[c], st0[c + 1]) of CTA c: a contiguous range of leaf rows (rows = positions), one or
+// two rows of one leaf per stage; y in position order, vector type. y_cut (the distinct cut rows,
+// in their order) is written as well. The x window [win[c].x, win[c].y) is gathered before the
+// first copy is issued, so the gather does not queue behind the stream.
 template <int PREC>
-__global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __restrict__ row0,
-                                                        const int* __restrict__ crow_of, const double* src,
-                                                        int src_pos, typename Acc<PREC>::X* __restrict__ y,
+__global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const StreamStage* __restrict__ stages,
+                                                        const int* __restrict__ st0, const int2* __restrict__ win,
+                                                        const double* src, int src_pos,
+                                                        typename Acc<PREC>::X* __restrict__ y,
                                                         typename Acc<PREC>::X* __restrict__ ycut, int stage_elems,
                                                         int max_stages) {
   using A = Acc<PREC>;
@@ -121,17 +133,17 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
   extern __shared__ __align__(128) unsigned char sml[];
   uint64_t* full = reinterpret_cast<uint64_t*>(sml);
   uint64_t* empty = full + kStages;
-  int* misc = reinterpret_cast<int*>(empty + kStages);   // [0] abort flag, [1] number of stages
+  int* misc = reinterpret_cast<int*>(empty + kStages);   // [0] abort flag
   T* stage = reinterpret_cast<T*>(sml + 16 * kStages + 16);
-  StageRec* sr = reinterpret_cast<StageRec*>(stage + (size_t)kStages * stage_elems);
+  StreamStage* sr = reinterpret_cast<StreamStage*>(stage + (size_t)kStages * stage_elems);
   X* xw = reinterpret_cast<X*>(sr + max_stages);
   const int c = blockIdx.x;
-  const int r0 = row0[c], r1 = row0[c + 1];
+  const int u0 = st0[c], nst = st0[c + 1] - u0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pdl_go_s();
-  if (r1 <= r0) return;
-  const int j0 = st.pos_leaf[r0], j1 = st.pos_leaf[r1 - 1];
-  const int wlo = st.lo[st.leaf_node[j0]], whi = st.hi[st.leaf_node[j1]];
+  if (nst <= 0) return;
+  const int2 w = win[c];
+  const int wlo = w.x, whi = w.y;
   const T* L = Elem<PREC>::L(st);
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -141,41 +153,8 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
     misc[0] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // stage table: stage u holds rows 2u and 2u+1 of the CTA when both belong to one leaf. Rows are
-  // paired within each leaf from its first row in this CTA, so a leaf boundary starts a new pair.
-  // Thread i handles row i; the rows that start a stage write its record.
-  for (int i = tid; i < r1 - r0; i += kST) {
-    const int p = r0 + i;
-    const int j = st.pos_leaf[p];
-    const int node = st.leaf_node[j];
-    const int lo = st.lo[node];
-    const int first = max(lo, r0);   // first row of this leaf in the CTA
-    const int k = p - first;
-    if ((k & 1) == 0) {
-      // stages before this leaf's first row in the CTA: ceil(rows / 2) per earlier leaf
-      int u = 0;
-      for (int q = r0; q < first;) {
-        const int jq = st.pos_leaf[q];
-        const int hq = min(st.hi[st.leaf_node[jq]], r1);
-        u += (hq - q + 1) / 2;
-        q = hq;
-      }
-      u += k / 2;
-      const int hi = min(st.hi[node], r1);
-      StageRec q;
-      q.ld = st.leaf_ld[j];
-      q.off = st.leaf_off[j] + (int64_t)(p - lo) * q.ld;
-      q.nr = p + 1 < hi ? 2 : 1;
-      q.xo = lo - wlo;
-      q.b = st.hi[node] - lo;
-      q.crow0 = crow_of[p];
-      q.crow1 = q.nr == 2 ? crow_of[p + 1] : -1;
-      q.p = p;
-      q.pad = 0;
-      sr[u] = q;
-      if (p + q.nr == r1) misc[1] = u + 1;
-    }
-  }
+  // stage table (built on the host; static per store)
+  for (int u = tid; u < nst; u += kST) sr[u] = stages[u0 + u];
   pdl_wait_s();
   {
     // gather in batches: all index loads of a thread, then all value loads (two round trips)
@@ -198,7 +177,6 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
     }
   }
   __syncthreads();
-  const int nst = misc[1];
   if (warp == 0) {
     // producer: one stage (1-2 rows) per slot; a slot is refilled after its consumer released it
     if (lane == 0) {
@@ -208,7 +186,7 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
         const int s = u % kStages;
         if (u >= kStages) ok = mb_wait(&empty[s], (uint32_t)(((u / kStages) - 1) & 1), kWaitS);
         if (!ok) break;
-        const StageRec q = sr[u];
+        const StreamStage q = sr[u];
         const uint32_t bytes = (uint32_t)(q.ld * q.nr) * (uint32_t)sizeof(T);
         mb_expect(&full[s], bytes);
         bulk_row(stage + (size_t)s * stage_elems, L + q.off, bytes, &full[s]);
@@ -231,7 +209,7 @@ __global__ void __launch_bounds__(kST, 1) k_leaf_stream(DStore st, const int* __
         if (lane == 0) atomicExch(st.status, DEV_TIMEOUT);
         break;
       }
-      const StageRec q = sr[u];
+      const StreamStage q = sr[u];
       const X* xr = xw + q.xo;
       const int p0 = q.p;
       for (int rr = 0; rr < q.nr; ++rr) {
@@ -355,7 +333,7 @@ __global__ void __launch_bounds__(128) k_sweep_matrix(const typename Acc<PREC>::
   const int lane = threadIdx.x & 31;
   const T* Kr = K + (int64_t)(row < s_total ? row : 0) * ldk;
   pdl_wait_s();
-  for (int k = threadIdx.x; k < n_crow; k += blockDim.x) yc[k] = ldcg(ycut_g + k);
+  stage_vec(yc, ycut_g, n_crow);
   __syncthreads();
   if (row >= s_total) return;
   A a, a2;
@@ -411,7 +389,7 @@ __global__ void __launch_bounds__(256, 4) k_expand_stream(DStore st, const Strea
   const int x0 = anc_ptr[j], x1 = valid ? anc_ptr[j + 1] : anc_ptr[j];
   pdl_wait_s();
   const X yp = ldcg(y + pp);   // in flight with the loads below
-  for (int i = threadIdx.x; i < s_total; i += blockDim.x) ss[i] = ldcg(s_g + i);
+  stage_vec(ss, s_g, s_total);
   __syncthreads();
   const T* F = Elem<PREC>::F(st);
   A a, a2;
@@ -491,8 +469,9 @@ void launch_stream(const Store& st, StreamApply& sa, const double* src, bool src
     launch_pdl_s(k_leaf_ldg<PREC>, sa.n_cta, kLT, sa.smem_ldg, s, v, (const int*)sa.row0.p, (const int*)sa.crow_of.p,
                  src, src_pos ? 1 : 0, y, yc);
   else
-    launch_pdl_s(k_leaf_stream<PREC>, sa.n_cta, kST, sa.smem, s, v, (const int*)sa.row0.p, (const int*)sa.crow_of.p,
-                 src, src_pos ? 1 : 0, y, yc, sa.stage_elems, sa.max_stages);
+    launch_pdl_s(k_leaf_stream<PREC>, sa.n_cta, kST, sa.smem, s, v, (const StreamStage*)sa.stages.p,
+                 (const int*)sa.st0.p, (const int2*)sa.win.p, src, src_pos ? 1 : 0, y, yc, sa.stage_elems,
+                 sa.max_stages);
   if (sa.s_total > 0 && sa.n_crow > 0) {
     const int wpb = 4;
     launch_pdl_s(k_sweep_matrix<PREC>, (sa.s_total + wpb - 1) / wpb, wpb * 32, (size_t)sa.n_crow * 8, s,
@@ -546,22 +525,49 @@ bool StreamApply::build(const Store& st, cudaStream_t s) {
     const int j0 = leaf_index_of_pos(st, r0[c]), j1 = leaf_index_of_pos(st, r0[c + 1] - 1);
     max_win = std::max(max_win, (size_t)(t.hi[st.leaf_nodes_h[j1]] - t.lo[st.leaf_nodes_h[j0]]));
   }
+  // stage table: per CTA, rows paired within each leaf (a leaf boundary starts a new pair)
+  std::vector<int> cro(n, -1);
+  for (size_t k = 0; k < st.cut_rows.crow_pos.size(); ++k) cro[st.cut_rows.crow_pos[k]] = (int)k;
+  std::vector<StreamStage> stg;
+  std::vector<int> s0v(n_cta + 1, 0);
+  std::vector<int2> wv(n_cta, make_int2(0, 0));
   max_stages = 0;
   for (int c = 0; c < n_cta; ++c) {
-    // stages = sum over the leaves of the CTA's rows of ceil(rows in that leaf / 2)
-    int u = 0;
-    for (int q = r0[c]; q < r0[c + 1];) {
-      const int hq = std::min(t.hi[st.leaf_nodes_h[leaf_index_of_pos(st, q)]], r0[c + 1]);
-      u += (hq - q + 1) / 2;
-      q = hq;
+    s0v[c] = (int)stg.size();
+    if (r0[c + 1] > r0[c]) {
+      const int jf = leaf_index_of_pos(st, r0[c]), jl = leaf_index_of_pos(st, r0[c + 1] - 1);
+      const int wlo = t.lo[st.leaf_nodes_h[jf]];
+      wv[c] = make_int2(wlo, t.hi[st.leaf_nodes_h[jl]]);
+      for (int q = r0[c]; q < r0[c + 1];) {
+        const int j = leaf_index_of_pos(st, q);
+        const int lo = t.lo[st.leaf_nodes_h[j]];
+        const int hq = std::min(t.hi[st.leaf_nodes_h[j]], r0[c + 1]);
+        for (int p = q; p < hq; p += 2) {
+          StreamStage g{};
+          g.ld = st.leaf_ld_h[j];
+          g.off = st.leaf_off_h[j] + (int64_t)(p - lo) * g.ld;
+          g.nr = p + 1 < hq ? 2 : 1;
+          g.xo = lo - wlo;
+          g.b = t.hi[st.leaf_nodes_h[j]] - lo;
+          g.crow0 = cro[p];
+          g.crow1 = g.nr == 2 ? cro[p + 1] : -1;
+          g.p = p;
+          stg.push_back(g);
+        }
+        q = hq;
+      }
     }
-    max_stages = std::max(max_stages, u);
+    max_stages = std::max(max_stages, (int)stg.size() - s0v[c]);
   }
-  smem = 16 * kStages + 16 + (size_t)kStages * stage_elems * 8 + (size_t)max_stages * sizeof(StageRec) +
+  s0v[n_cta] = (int)stg.size();
+  smem = 16 * kStages + 16 + (size_t)kStages * stage_elems * 8 + (size_t)max_stages * sizeof(StreamStage) +
          (max_win + 2) * 8;
   if (smem + 1024 > (size_t)optin) return false;
   smem_ldg = (max_win + 2) * 8;
   row0.upload(r0, s);
+  stages.upload(stg.empty() ? std::vector<StreamStage>{StreamStage{}} : stg, s);
+  st0.upload(s0v, s);
+  win.upload(wv, s);
   // sweep matrix
   build_sweep_image(st, nullptr, prec, hdr, img, seg_src, seg_dst, seg_len, n_seg, s);
   n_crow = hdr.n_crow;
