@@ -169,98 +169,82 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
   }
 }
 
-// Corrected leaf-stage value at one position for one column (ancestors strictly below depth d
-// when d >= 0, all ancestors when d < 0), from the S computed so far (shared memory, CB columns).
-__device__ __forceinline__ float corrected(const DStore& st, const float* Y, int64_t R, int pos, int c, int cl,
-                                           const float* s_sh, int cb, int d) {
-  float v = Y[pos * R + c];
-  for (int q = st.parent[st.leaf_node[st.pos_leaf[pos]]]; q >= 0 && st.depth[q] > d; q = st.parent[q]) {
-    const int k = st.node_k[q];
-    const int half = pos < st.hi[st.left[q]] ? 0 : k;
-    const float* Fr = st.F32 + st.node_foff[q] + (int64_t)(pos - st.lo[q]) * st.node_kld[q];
-    const int si = st.node_soff[q] + half;
-    for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], s_sh[(si + e) * cb + cl], v);
-  }
-  return v;
-}
-
-// Boundary sweep for a block of columns; writes S (and the N-1 factors when n1 is set).
-__global__ void __launch_bounds__(256) k_mc_sweep(DStore st, MSimD m, int cb, int n1, int s_in_chunk,
-                                                  const int* status) {
-  extern __shared__ __align__(16) float sh[];
+// Boundary sweep of all columns as one product: S = K Y_cut, K = the matrix of the sweep
+// (s_total x ldk, FP32, built on the device from the sweep image), Y_cut = the leaf-stage rows at
+// the distinct cut rows. Tiles of 32 rows of S x 64 columns, 32-deep chunks of K: 128 threads each
+// form a 4 x 4 block of outputs from 16-byte shared-memory reads; the next chunk is loaded into
+// registers while the current one is multiplied.
+constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128;
+__global__ void __launch_bounds__(SBT) k_mc_sweep_gemm(MSimD m, const float* __restrict__ K, int ldk,
+                                                       const int* status) {
+  __shared__ __align__(16) float Ks[SBK][SBM];
+  __shared__ __align__(16) float Ys[SBK][SBN];
   if (*status != DEV_OK) return;
-  const int c0 = blockIdx.x * cb;
-  const int ncol = min(cb, m.R_act - c0);
-  if (ncol <= 0) return;
   const int* M = m.meta;
-  const int n_crow = M[M_NCROW], s_total = M[M_STOTAL], maxd = M[M_MAXD];
-  float* ycut = sh;                         // [n_crow][cb]
-  float* t = ycut + (size_t)n_crow * cb;     // [s_total][cb]
-  float* s = t + (size_t)s_total * cb;       // [s_total][cb]
-  const int64_t R = m.R;
-  const int tid = threadIdx.x;
+  const int n_crow = M[M_NCROW], s_total = M[M_STOTAL];
   const int* crow_pos = M + M[M_OFF_CROW];
-  for (int w = tid; w < n_crow * cb; w += blockDim.x) {
-    const int k = w / cb, cl = w % cb;
-    ycut[w] = cl < ncol ? m.Y[(int64_t)crow_pos[k] * R + c0 + cl] : 0.f;
-  }
-  __syncthreads();
-  const int* lvl_item = M + M[M_OFF_LVL_ITEM];
-  const int* item = M + M[M_OFF_ITEM];
-  const int* seg = M + M[M_OFF_SEG];
-  const int* lvl_core = M + M[M_OFF_LVL_CORE];
-  const int* core = M + M[M_OFF_CORE];
-  for (int d = maxd - 1; d >= 0; --d) {
-    const int i0 = lvl_item[d], i1 = lvl_item[d + 1];
-    for (int w = i0 * cb + tid; w < i1 * cb; w += blockDim.x) {
-      const int it = w / cb, cl = w % cb;
-      const int* rec = item + 5 * it;
-      float v = ycut[rec[0] * cb + cl];
-      for (int sg = rec[3]; sg < rec[3] + rec[4]; ++sg) {
-        const int si = seg[3 * sg], k = seg[3 * sg + 1];
-        const float* Fr = st.F32 + seg[3 * sg + 2];
-        for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], s[(si + e) * cb + cl], v);
-      }
-      if (rec[2] >= 0) v *= (float)(-st.cut_g[rec[2]]);
-      t[rec[1] * cb + cl] = v;
+  const int r0 = blockIdx.x * SBM, c0 = blockIdx.y * SBN;
+  if (c0 >= m.R_act) return;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;   // rows ty*4.., columns tx*4..
+  const int64_t R = m.R;
+  constexpr int KL = SBK * SBM / SBT, YL = SBK * SBN / SBT;   // 8 and 16 loads per thread
+  float kr[KL], yr[YL];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < KL; ++u) {
+      const int w = tid + u * SBT, kk = w % SBK, rr = w / SBK;
+      const int r = r0 + rr, k = k0 + kk;
+      kr[u] = (r < s_total && k < n_crow) ? K[(int64_t)r * ldk + k] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < YL; ++u) {
+      const int w = tid + u * SBT, kk = w / SBN, cc = w % SBN;
+      const int k = k0 + kk, c = c0 + cc;
+      yr[u] = (k < n_crow && c < m.R_act) ? m.Y[(int64_t)crow_pos[k] * R + c] : 0.f;
+    }
+  };
+  float acc[4][4] = {};
+  load(0);
+  for (int k0 = 0; k0 < n_crow; k0 += SBK) {
+#pragma unroll
+    for (int u = 0; u < KL; ++u) {
+      const int w = tid + u * SBT;
+      Ks[w % SBK][w / SBK] = kr[u];
+    }
+#pragma unroll
+    for (int u = 0; u < YL; ++u) {
+      const int w = tid + u * SBT;
+      Ys[w / SBN][w % SBN] = yr[u];
     }
     __syncthreads();
-    const int j0 = lvl_core[d], j1 = lvl_core[d + 1];
-    for (int w = j0 * cb + tid; w < j1 * cb; w += blockDim.x) {
-      const int cr = w / cb, cl = w % cb;
-      const int* rec = core + 4 * cr;
-      const float* Cr = st.C32 + rec[3];
-      float v = 0.f;
-      for (int e = 0; e < rec[2]; ++e) v = fmaf(Cr[e], t[(rec[1] + e) * cb + cl], v);
-      s[rec[0] * cb + cl] = v;
+    if (k0 + SBK < n_crow) load(k0 + SBK);   // in flight during the products below
+#pragma unroll 8
+    for (int kk = 0; kk < SBK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&Ks[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Ys[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
     }
     __syncthreads();
   }
-  for (int w = tid; w < s_total * cb; w += blockDim.x) {
-    const int r = w / cb, cl = w % cb;
-    if (cl < ncol) m.S[(int64_t)r * R + c0 + cl] = s[w];
-  }
-  if (n1) {
-    const int step = m.dyn->step_base + s_in_chunk + 1;
-    for (int cl = tid; cl < ncol; cl += blockDim.x) {
-      const int c = c0 + cl;
-      float f = 0.f;
-      if (change_on(m, c, step)) {
-        const float ya = corrected(st, m.Y, R, m.trip_a[c], c, cl, s, cb, -1);
-        const float yb = m.trip_b[c] >= 0 ? corrected(st, m.Y, R, m.trip_b[c], c, cl, s, cb, -1) : 0.f;
-        f = (float)m.trip_coef[c] * (ya - yb);
-      }
-      m.fcol[c] = f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= s_total) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + tx * 4 + q;
+      if (c < m.R_act) m.S[(int64_t)r * R + c] = acc[i][q];
     }
   }
 }
 
-// Expansion (+ N-1 correction): V (pass 0: =, pass 1: +=) and monitored record.
-__global__ void __launch_bounds__(128) k_mc_expand(DStore st, MSimD m, int pass, int n1, int record, int s_in_chunk,
-                                                   const int* status) {
-  const int pos = blockIdx.x;
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R_act || *status != DEV_OK) return;
+// Corrected leaf-stage value v = y - sum over ancestors of F row . S(half) at one position and
+// column, with S in global memory.
+__device__ __forceinline__ float corrected_g(const DStore& st, const MSimD& m, int pos, int c) {
   const int64_t R = m.R;
   float v = m.Y[pos * R + c];
   for (int q = st.parent[st.leaf_node[st.pos_leaf[pos]]]; q >= 0; q = st.parent[q]) {
@@ -270,17 +254,115 @@ __global__ void __launch_bounds__(128) k_mc_expand(DStore st, MSimD m, int pass,
     const float* Sq = m.S + (int64_t)(st.node_soff[q] + half) * R + c;
     for (int e = 0; e < k; ++e) v = fmaf(-Fr[e], Sq[e * R], v);
   }
-  if (n1) {
-    const float f = m.fcol[c];
-    if (f != 0.f) v = fmaf(-f, m.Z[pos * R + c].x, v);
+  return v;
+}
+
+// N-1 factor of each column whose change is switched on: f_c = (delta_c / d_c) (v_a - v_b) from
+// the FP32 apply before the column's own Sherman-Morrison term (zero for the others).
+__global__ void k_mc_fcol(DStore st, MSimD m, int s_in_chunk, const int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.R_act || *status != DEV_OK) return;
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  float f = 0.f;
+  if (change_on(m, c, step)) {
+    const float ya = corrected_g(st, m, m.trip_a[c], c);
+    const float yb = m.trip_b[c] >= 0 ? corrected_g(st, m, m.trip_b[c], c) : 0.f;
+    f = (float)m.trip_coef[c] * (ya - yb);
   }
-  float2 out = pass == 0 ? ff_f(v) : ff_addx(m.V[pos * R + c], ff_f(v));
-  m.V[pos * R + c] = out;
-  if (record && m.dyn->rec) {
-    const int mi = m.mon_idx[pos];
-    if (mi >= 0) {
-      const int step = m.dyn->step_base + s_in_chunk + 1;
-      m.dyn->rec[((int64_t)(step - m.dyn->rec_first) * R + c) * m.n_mon + mi] = (double)out.x + (double)out.y;
+  m.fcol[c] = f;
+}
+
+// Expansion (+ N-1 correction) as a tiled product per leaf: for a tile of up to 32 positions of
+// one leaf and 128 columns, V = Y - F_path S_path, where F_path holds the tile's factor rows of all
+// its ancestors (the same ancestors and halves for every position of a leaf) and S_path the
+// matching rows of S. Path elements are taken in chunks of 16: the S chunk (16 x 128) and the F
+// chunk (16 x 32, element-major) go to shared memory, and each of 256 threads forms a 4 x 4 block
+// of outputs (4 positions x 4 columns) from 16-byte reads; the next chunk is loaded into registers
+// while the current one is multiplied. pass 0: V = result; pass 1: V += result and the monitored
+// record.
+constexpr int XP = 32, XC = 128, XE = 16, XT = 256;
+__global__ void __launch_bounds__(XT) k_mc_expand_tiled(DStore st, MSimD m, const int4* __restrict__ tiles,
+                                                        const int* __restrict__ path_ptr,
+                                                        const int* __restrict__ path_srow,
+                                                        const long long* __restrict__ path_fbase,
+                                                        const int* __restrict__ path_kld, int pass, int n1, int record,
+                                                        int s_in_chunk, const int* status) {
+  __shared__ __align__(16) float Ss[XE][XC];
+  __shared__ __align__(16) float Fs[XE][XP];
+  if (*status != DEV_OK) return;
+  const int4 tl = tiles[blockIdx.x];   // leaf, first position, positions, unused
+  const int j = tl.x, p0 = tl.y, cnt = tl.z;
+  const int c0 = blockIdx.y * XC;
+  if (c0 >= m.R_act) return;
+  const int tid = threadIdx.x, ty = tid / 32, tx = tid % 32;   // positions ty*4.., columns tx*4..
+  const int64_t R = m.R;
+  const int e0 = path_ptr[j], ne = path_ptr[j + 1] - e0;
+  constexpr int SL = XE * XC / XT, FL = XE * XP / XT;   // 8 and 2 loads per thread
+  float sr[SL], fr[FL];
+  auto load = [&](int eb) {
+#pragma unroll
+    for (int u = 0; u < SL; ++u) {
+      const int w = tid + u * XT, e = w / XC, cc = w % XC;
+      sr[u] = (eb + e < ne && c0 + cc < m.R_act) ? m.S[(int64_t)path_srow[e0 + eb + e] * R + c0 + cc] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < FL; ++u) {
+      const int w = tid + u * XT, e = w / XP, p = w % XP;
+      float f = 0.f;
+      if (p < cnt && eb + e < ne) {
+        const int ix = e0 + eb + e;
+        f = st.F32[path_fbase[ix] + (int64_t)(p0 + p) * path_kld[ix]];
+      }
+      fr[u] = f;
+    }
+  };
+  float acc[4][4] = {};
+  if (ne > 0) load(0);
+  for (int eb = 0; eb < ne; eb += XE) {
+#pragma unroll
+    for (int u = 0; u < SL; ++u) {
+      const int w = tid + u * XT;
+      Ss[w / XC][w % XC] = sr[u];
+    }
+#pragma unroll
+    for (int u = 0; u < FL; ++u) {
+      const int w = tid + u * XT;
+      Fs[w / XP][w % XP] = fr[u];
+    }
+    __syncthreads();
+    if (eb + XE < ne) load(eb + XE);   // in flight during the products below
+#pragma unroll
+    for (int e = 0; e < XE; ++e) {
+      const float4 f = *reinterpret_cast<const float4*>(&Fs[e][ty * 4]);
+      const float4 sv = *reinterpret_cast<const float4*>(&Ss[e][tx * 4]);
+      const float fv[4] = {f.x, f.y, f.z, f.w}, svv[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(fv[i], svv[q], acc[i][q]);
+    }
+    __syncthreads();
+  }
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = c0 + tx * 4 + q;
+    if (c >= m.R_act) continue;
+    const float fc = n1 ? m.fcol[c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = ty * 4 + i;
+      if (p >= cnt) continue;
+      const int pos = p0 + p;
+      float v = m.Y[pos * R + c] - acc[i][q];
+      if (fc != 0.f) v = fmaf(-fc, m.Z[pos * R + c].x, v);
+      const float2 out = pass == 0 ? ff_f(v) : ff_addx(m.V[pos * R + c], ff_f(v));
+      m.V[pos * R + c] = out;
+      if (record && m.dyn->rec) {
+        const int mi = m.mon_idx[pos];
+        if (mi >= 0)
+          m.dyn->rec[((int64_t)(step - m.dyn->rec_first) * R + c) * m.n_mon + mi] = (double)out.x + (double)out.y;
+      }
     }
   }
 }
@@ -710,9 +792,54 @@ void MSim::build_meta(cudaStream_t s) {
   gemm_tiles.alloc(tiles.size() * 4);
   EMT_CUDA(cudaMemcpyAsync(gemm_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   // column block of the sweep: as many columns as shared memory allows (<= 32)
-  sweep_cb = 32;
-  while (sweep_cb > 1 && (size_t)(n_crow + 2 * st.s_total) * sweep_cb * 4 > 200 * 1024) sweep_cb /= 2;
-  sweep_smem = (size_t)(n_crow + 2 * st.s_total) * sweep_cb * 4 + 64;
+  // matrix of the sweep (FP32): S = K Y_cut
+  {
+    ImgHeader hdr{};
+    DevBuf<double> img;
+    DevBuf<int> sg_src, sg_dst, sg_len;
+    int n_sg = 0;
+    build_sweep_image(st, nullptr, EMT_PREC_FP32, hdr, img, sg_src, sg_dst, sg_len, n_sg, s);
+    ldk = (n_crow + 1) / 2 * 2;
+    Kmat.alloc(std::max<size_t>((size_t)st.s_total * ldk, 1));
+    EMT_CUDA(cudaMemsetAsync(Kmat.p, 0, Kmat.n * sizeof(float), s));
+    build_sweep_matrix(EMT_PREC_FP32, reinterpret_cast<const unsigned char*>(img.p), hdr.img_bytes,
+                       reinterpret_cast<const unsigned char*>(st.C32.p), (int)(st.C_elems * 4), n_crow, st.s_total,
+                       ldk, Kmat.p, s);
+    EMT_CUDA(cudaStreamSynchronize(s));
+  }
+  // expansion tiles (up to 32 positions of one leaf) and per-leaf path tables: for every element
+  // of the concatenated ancestor rows, the row of S and the factor offset (minus position x kld)
+  {
+    std::vector<int4> tl;
+    std::vector<int> pp(st.n_leaf + 1, 0), srow, kld;
+    std::vector<long long> fb;
+    for (int j = 0; j < st.n_leaf; ++j) {
+      const int leaf = st.leaf_nodes_h[j];
+      const int lo = t.lo[leaf], hi = t.hi[leaf];
+      for (int p = lo; p < hi; p += 32) tl.push_back(make_int4(j, p, std::min(32, hi - p), 0));
+      for (int a = t.parent[leaf]; a >= 0; a = t.parent[a]) {
+        const int k = st.node_k_h[a];
+        const int half = lo < t.hi[t.left[a]] ? 0 : k;
+        for (int e = 0; e < k; ++e) {
+          srow.push_back(st.node_soff_h[a] + half + e);
+          fb.push_back((long long)st.node_foff_h[a] - (long long)t.lo[a] * st.node_kld_h[a] + e);
+          kld.push_back(st.node_kld_h[a]);
+        }
+      }
+      pp[j + 1] = (int)srow.size();
+    }
+    if (srow.empty()) {
+      srow.push_back(0);
+      fb.push_back(0);
+      kld.push_back(0);
+    }
+    n_xtiles = (int)tl.size();
+    xtiles.upload(tl, s);
+    path_ptr.upload(pp, s);
+    path_srow.upload(srow, s);
+    path_fbase.upload(fb, s);
+    path_kld.upload(kld, s);
+  }
 }
 
 void MSim::schedule(int step, int kind, int target, double value, int column) {
@@ -778,14 +905,13 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
   else
     k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p,
                                       R_act);
-  static bool attr = false;
-  if (!attr) {
-    EMT_CUDA(cudaFuncSetAttribute(k_mc_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
-  k_mc_sweep<<<(R_act + sweep_cb - 1) / sweep_cb, 256, sweep_smem, s>>>(st, d, sweep_cb, n1, s_in_chunk,
-                                                                    store->d_status.p);
-  k_mc_expand<<<dim3(n, (R_act + 127) / 128), 128, 0, s>>>(st, d, pass, n1, record, s_in_chunk, store->d_status.p);
+  if (store->s_total > 0 && n_crow > 0)
+    k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN), SBT, 0, s>>>(
+        d, reinterpret_cast<const float*>(Kmat.p), ldk, store->d_status.p);
+  if (n1) k_mc_fcol<<<(R_act + 127) / 128, 128, 0, s>>>(st, d, s_in_chunk, store->d_status.p);
+  k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
+      st, d, xtiles.p, path_ptr.p, path_srow.p, path_fbase.p, path_kld.p, pass, n1,
+      record, s_in_chunk, store->d_status.p);
   EMT_CUDA(cudaGetLastError());
 }
 

@@ -113,8 +113,11 @@ class MSim {
   DevBuf<float> Xf, Y, S, fcol;
   DevBuf<double> trip_delta, trip_coef;
   DevBuf<SimDyn> d_dyn;
-  int n_inc = 0, n_tiles = 0, n_crow = 0, sweep_cb = 32;
-  size_t sweep_smem = 0;
+  int n_inc = 0, n_tiles = 0, n_crow = 0, ldk = 0, n_xtiles = 0;
+  DevBuf<float> Kmat;                       // matrix of the sweep (FP32), S = K Y_cut
+  DevBuf<int4> xtiles;                      // expansion tiles: leaf, first position, positions
+  DevBuf<int> path_ptr, path_srow, path_kld;   // per-leaf path tables of the expansion
+  DevBuf<long long> path_fbase;
   std::vector<int> h_trip_step, h_trip_elem;
   bool z_ready = false;
   std::map<int, cudaGraphExec_t> graphs;
