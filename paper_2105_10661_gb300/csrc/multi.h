@@ -65,9 +65,10 @@ struct MSimD {
 // tcgen05 leaf stage (umma.cu)
 struct Umma {
   bool ready = false;
-  int R = 0, TN = 0, n_blocks = 0, n_tiles = 0;
-  DevBuf<uint16_t> a_blocks;
-  DevBuf<int4> d_tiles;
+  int R = 0, TN = 0, n_blocks = 0, n_tiles = 0, n_bblocks = 0;
+  DevBuf<uint16_t> a_blocks, b_blocks;   // pre-tiled BF16 splits of the leaves and of the right-hand sides
+  DevBuf<int4> d_tiles, b_desc;
+  DevBuf<int> tile_b;
   void build(const Store& st, int R, cudaStream_t s);
   void launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act);
 };

@@ -5,17 +5,16 @@
 // The dropped L_lo X_lo term and the split residuals leave a relative error of about 2^-16;
 // the multi-column step's float-float residual refinement removes it.
 //
-// One CTA computes a 128-row x TN-column tile of one leaf. K runs in chunks of 64, double
-// buffered in shared memory:
-//   A (L_hi | L_lo)   pre-tiled in global memory in the canonical K-major core-matrix layout
-//                     (8 rows x 16 bytes per core matrix), one 32 KB cp.async.bulk per chunk;
-//   B (X_hi, X_lo)    split from the FP32 right-hand sides by all threads and stored K-major
-//                     with an N-group stride of 1040 bytes (1024 + 16 rotates the banks, so
-//                     the 32 threads of a warp store to 32 different banks).
-// One elected thread issues tcgen05.mma (M = 128, N = TN, K = 16, kind::f16 with BF16 inputs)
-// three times per K step and commits them to an mbarrier; the epilogue reads the accumulator
-// with tcgen05.ld. Every mbarrier wait is bounded by clock64 and reports a timeout in the
-// device status word; tensor memory is always released.
+// Both operands are pre-tiled in global memory in the canonical K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix, no swizzle): A (the leaf blocks, split once per store) per
+// (leaf, 128-row tile, 64-deep K chunk), B (the right-hand sides, split once per pass by
+// k_split_b) per (leaf, TN-column tile, K chunk). One CTA computes a 128-row x TN-column tile of
+// one leaf as a two-stage pipeline: one thread issues one cp.async.bulk per operand and chunk into
+// a stage (full mbarrier), one thread issues tcgen05.mma (M = 128, N = TN, K = 16, kind::f16 with
+// BF16 inputs) three times per K step and commits them to the stage's empty mbarrier, and the
+// epilogue reads the accumulator with tcgen05.ld. Each mbarrier has a single waiter that waits
+// for its phases in order; every wait is bounded by clock64 and reports a timeout in the device
+// status word; tensor memory is always released.
 #include <algorithm>
 #include <cstdint>
 
@@ -31,7 +30,7 @@ constexpr int UM = 128;            // MMA M (tile rows)
 constexpr int UKC = 64;            // K chunk
 constexpr uint32_t A_CHUNK = UM * UKC * 2;          // 16 KB per split
 constexpr uint32_t A_SBO = 1024, A_LBO = 128;       // M-group stride, K-core stride
-constexpr uint32_t B_SBO = 1040, B_LBO = 128;       // N-group stride (padded), K-core stride
+constexpr uint32_t B_SBO = 1024, B_LBO = 128;       // N-group stride, K-core stride
 constexpr long long kSpin = 4000000000LL;           // ~2 s of SM clocks
 
 __device__ __forceinline__ uint32_t su(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -88,71 +87,74 @@ __global__ void k_tile_leaves(DStore st, const int* __restrict__ blk_leaf, const
 
 struct UmmaArgs {
   const int4* tiles;        // (leaf, m0, n0, first A block of this leaf-M-tile)
+  const int* tile_b;        // first B block of the tile's (leaf, N tile)
   const uint16_t* a_blocks; // pre-tiled leaf blocks
-  const float* Xf;          // [n][R]
+  const uint16_t* b_blocks; // pre-tiled right-hand sides
   float* Y;                 // [n][R]
-  int R, TN, nkc_max;
+  int R, TN;
   int r_act;                // columns in use; tiles starting beyond exit at once
 };
 
-// Stage the B chunk (rows k0..k0+63 of the leaf, columns n0..n0+TN) as BF16 hi/lo.
-__device__ __forceinline__ void stage_b(const UmmaArgs& a, int lo_pos, int b, int k0, int n0, unsigned char* Bh,
-                                        unsigned char* Bl) {
-  // item -> (k pair kp, 4-column group n4); the 32 lanes of a warp take 4 k pairs x 8 column
-  // groups, which with the 1040-byte N-group stride puts their 32-bit stores in 32 banks
-  const int TN = a.TN;
-  const int nb4 = TN / 32;                // blocks of 8 column groups
-  const int total = (UKC / 2) * (TN / 4);
-  for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int lane = w & 31, wi = w >> 5;
-    const int kp = (wi / nb4) * 4 + (lane & 3);
-    const int n4 = (wi % nb4) * 8 + (lane >> 2);
-    const int k = 2 * kp;
-    const int n = 4 * n4;
-    float x0[4] = {0.f, 0.f, 0.f, 0.f}, x1[4] = {0.f, 0.f, 0.f, 0.f};
-    const int gk0 = k0 + k, gk1 = k0 + k + 1;
-    if (n0 + n < a.R) {   // R is a multiple of 4, so the 4 columns are all valid and aligned
-      if (gk0 < b) {
-        const float4 v = *reinterpret_cast<const float4*>(a.Xf + (int64_t)(lo_pos + gk0) * a.R + n0 + n);
-        x0[0] = v.x; x0[1] = v.y; x0[2] = v.z; x0[3] = v.w;
-      }
-      if (gk1 < b) {
-        const float4 v = *reinterpret_cast<const float4*>(a.Xf + (int64_t)(lo_pos + gk1) * a.R + n0 + n);
-        x1[0] = v.x; x1[1] = v.y; x1[2] = v.z; x1[3] = v.w;
-      }
-    }
+// B blocks: per (leaf j, N tile, K chunk) [hi | lo], each TN x 64 BF16 in the canonical K-major
+// layout (N-group stride 1024 bytes, K-core stride 128 bytes). Thread item = one column and 8
+// consecutive k: one 16-byte core row per split.
+__global__ void k_split_b(DStore st, const int4* __restrict__ bdesc, const float* __restrict__ Xf,
+                          uint16_t* __restrict__ out, int R, int TN, int n_blk) {
+  const int blk = blockIdx.x;
+  if (blk >= n_blk) return;
+  const int4 d = bdesc[blk];   // leaf, N tile first column, K chunk, unused
+  const int node = st.leaf_node[d.x];
+  const int lo = st.lo[node], b = st.hi[node] - lo;
+  unsigned char* hi = reinterpret_cast<unsigned char*>(out) + (size_t)blk * 4 * TN * UKC;
+  unsigned char* lob = hi + (size_t)2 * TN * UKC;
+  for (int w = threadIdx.x; w < TN * (UKC / 8); w += blockDim.x) {
+    const int n = w % TN, kg = w / TN;
+    const int col = d.y + n;
+    uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int nn = n + q;
-      const uint16_t h0 = bf16_bits(x0[q]), h1 = bf16_bits(x1[q]);
-      const uint16_t l0 = bf16_bits(x0[q] - bf16_val(h0)), l1 = bf16_bits(x1[q] - bf16_val(h1));
-      const uint32_t off = (nn / 8) * B_SBO + (k / 8) * B_LBO + ((nn % 8) * 8 + (k % 8)) * 2;
-      *reinterpret_cast<uint32_t*>(Bh + off) = (uint32_t)h0 | ((uint32_t)h1 << 16);
-      *reinterpret_cast<uint32_t*>(Bl + off) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+      float x[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = d.z * UKC + kg * 8 + 2 * q + u;
+        x[u] = (k < b && col < R) ? Xf[(int64_t)(lo + k) * R + col] : 0.f;
+      }
+      const uint16_t h0 = bf16_bits(x[0]), h1 = bf16_bits(x[1]);
+      const uint16_t l0 = bf16_bits(x[0] - bf16_val(h0)), l1 = bf16_bits(x[1] - bf16_val(h1));
+      h[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      l[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
     }
+    const uint32_t off = (n / 8) * B_SBO + kg * B_LBO + (n % 8) * 16;
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lob + off) = make_uint4(l[0], l[1], l[2], l[3]);
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s_u(unsigned char* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su(dst)),
+               "l"(src), "r"(bytes), "r"(su(bar))
+               : "memory");
 }
 
 __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
-  const uint32_t b_bytes = (uint32_t)(TN / 8) * B_SBO;
-  unsigned char* Abuf[2] = {sm, sm + 2 * A_CHUNK};
-  unsigned char* Bh[2] = {sm + 4 * A_CHUNK, sm + 4 * A_CHUNK + 2 * b_bytes};
-  unsigned char* Bl[2] = {Bh[0] + b_bytes, Bh[1] + b_bytes};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 4 * A_CHUNK + 4 * b_bytes);   // a0, a1, m0, m1
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
-  int* flag = reinterpret_cast<int*>(bars + 5);
+  const uint32_t b_split = (uint32_t)TN * UKC * 2;              // bytes of one B split
+  const uint32_t stage_bytes = 2 * A_CHUNK + 2 * b_split;
+  unsigned char* stg[2] = {sm, sm + stage_bytes};
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);   // full0, full1, empty0, empty1, done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
+  int* flag = reinterpret_cast<int*>(bars + 6);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int4 tl = a.tiles[blockIdx.x];
   const int j = tl.x, m0 = tl.y, n0 = tl.z, blk0 = tl.w;
+  const int bblk0 = a.tile_b[blockIdx.x];
   if (n0 >= a.r_act) return;   // uniform per CTA, before any barrier or tensor memory use
   const int node = st.leaf_node[j];
   const int lo = st.lo[node], b = st.hi[node] - lo;
   const int nkc = (b + UKC - 1) / UKC;
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(bars + i)) : "memory");
+    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(bars + i)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *flag = 0;
   }
@@ -166,86 +168,80 @@ __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
-  auto issue_a = [&](int kc) {
-    const int s = kc & 1;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su(bars + s)), "r"(2 * A_CHUNK)
-                 : "memory");
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(a.a_blocks) + (size_t)(blk0 + kc) * 2 * A_CHUNK;
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     su(Abuf[s])),
-                 "l"(src), "r"(2 * A_CHUNK), "r"(su(bars + s))
-                 : "memory");
-  };
-  bool ok = true;
-  int last_a = 0, last_mma = -1;   // chunk indices of the last bulk copy and MMA batch issued (thread 0)
-  if (tid == 0) issue_a(0);
-  stage_b(a, lo, b, 0, n0, Bh[0], Bl[0]);
-  for (int kc = 0; kc < nkc; ++kc) {
-    const int s = kc & 1;
-    __syncthreads();
-    if (*flag) break;
-    if (tid == 0) {
+  __shared__ int cnt_sh[2];        // [0] chunks copied (producer), [1] chunks multiplied (issuer)
+  int issued = 0, committed = 0;
+  if (tid == 0) {
+    // producer: stage s = kc % 2 is refilled once the MMAs of chunk kc - 2 released it
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc & 1;
+      if (kc >= 2 && !bar_wait(bars + 2 + s, ((kc >> 1) - 1) & 1)) {
+        atomicExch(status, DEV_TIMEOUT);
+        atomicExch(flag, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(flag)) break;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su(bars + s)), "r"(stage_bytes)
+                   : "memory");
+      bulk_g2s_u(stg[s], reinterpret_cast<const unsigned char*>(a.a_blocks) + (size_t)(blk0 + kc) * 2 * A_CHUNK,
+                 2 * A_CHUNK, bars + s);
+      bulk_g2s_u(stg[s] + 2 * A_CHUNK, reinterpret_cast<const unsigned char*>(a.b_blocks) + (size_t)(bblk0 + kc) * 2 * b_split,
+                 2 * b_split, bars + s);
+      ++issued;
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc & 1;
       if (!bar_wait(bars + s, (kc >> 1) & 1)) {
         atomicExch(status, DEV_TIMEOUT);
-        *flag = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_hi = su(Abuf[s]), a_lo = a_hi + A_CHUNK;
-        const uint32_t b_hi = su(Bh[s]), b_lo = su(Bl[s]);
+        atomicExch(flag, 1);
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_hi = su(stg[s]), a_lo = a_hi + A_CHUNK;
+      const uint32_t b_hi = a_hi + 2 * A_CHUNK, b_lo = b_hi + b_split;
 #pragma unroll
-        for (int ks = 0; ks < UKC / 16; ++ks) {
-          const uint32_t ko = ks * 2 * 128;
-          const uint64_t dah = umma_desc(a_hi + ko, A_LBO, A_SBO), dal = umma_desc(a_lo + ko, A_LBO, A_SBO);
-          const uint64_t dbh = umma_desc(b_hi + ko, B_LBO, B_SBO), dbl = umma_desc(b_lo + ko, B_LBO, B_SBO);
-          const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                       "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0)
-                       : "memory");
-          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                       "l"(dah), "l"(dbl), "r"(idesc), "r"(1u)
-                       : "memory");
-          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                       "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
-                       : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bars + 2 + s))
+      for (int ks = 0; ks < UKC / 16; ++ks) {
+        const uint32_t ko = ks * 2 * 128;
+        const uint64_t dah = umma_desc(a_hi + ko, A_LBO, A_SBO), dal = umma_desc(a_lo + ko, A_LBO, A_SBO);
+        const uint64_t dbh = umma_desc(b_hi + ko, B_LBO, B_SBO), dbl = umma_desc(b_lo + ko, B_LBO, B_SBO);
+        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0)
                      : "memory");
-        last_mma = kc;
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dah), "l"(dbl), "r"(idesc), "r"(1u)
+                     : "memory");
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
+                     : "memory");
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bars + 2 + s))
+                   : "memory");
+      ++committed;
     }
-    if (kc + 1 < nkc) {
-      const int s2 = (kc + 1) & 1;
-      if (kc + 1 >= 2) {
-        // the MMAs of chunk kc - 1 read buffer s2: wait before overwriting it
-        if (!bar_wait(bars + 2 + s2, ((kc - 1) >> 1) & 1)) {
-          if (tid == 0) atomicExch(status, DEV_TIMEOUT);
-          *flag = 1;
-        }
-      }
-      __syncthreads();
-      if (*flag) break;
-      if (tid == 0) {
-        issue_a(kc + 1);
-        last_a = kc + 1;
-      }
-      stage_b(a, lo, b, (kc + 1) * UKC, n0, Bh[s2], Bl[s2]);
-    }
+    // all MMAs issued so far complete -> done
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bars + 4))
+                 : "memory");
+  }
+  if (tid == 0) cnt_sh[0] = issued;
+  if (tid == 32) cnt_sh[1] = committed;
+  __syncthreads();
+  // the issuer's last commit covers every MMA it issued
+  __shared__ int ok_sh;
+  if (tid == 32) {
+    const bool ok = bar_wait(bars + 4, 0);
+    if (!ok) atomicExch(status, DEV_TIMEOUT);
+    ok_sh = ok && !*reinterpret_cast<volatile int*>(flag) && cnt_sh[1] == nkc;
+  }
+  if (tid == 0 && cnt_sh[0] > cnt_sh[1]) {
+    // error path only: copies issued to stages the issuer never consumed; each is the latest use
+    // of its stage (at most one per stage), so its phase parity is unambiguous
+    for (int kc = cnt_sh[1]; kc < cnt_sh[0]; ++kc) bar_wait(bars + (kc & 1), (kc >> 1) & 1);
   }
   __syncthreads();
-  ok = (*flag == 0);
-  if (!ok && tid == 0) {
-    // give the copy and the MMAs still in flight a bounded chance to land before tensor memory
-    // and shared memory are released
-    bar_wait(bars + (last_a & 1), (last_a >> 1) & 1);
-    if (last_mma >= 0) bar_wait(bars + 2 + (last_mma & 1), (last_mma >> 1) & 1);
-  }
-  if (ok) {
-    const int last = nkc - 1;
-    if (!bar_wait(bars + 2 + (last & 1), (last >> 1) & 1)) {
-      if (tid == 0) atomicExch(status, DEV_TIMEOUT);
-      ok = false;
-    }
-  }
+  const bool ok = ok_sh != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     // epilogue: warp w reads lanes 32 (w % 4) .. +31; warps 0-3 and 4-7 split the columns
@@ -291,17 +287,22 @@ __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* 
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-size_t umma_smem_bytes(int TN) { return 4 * (size_t)A_CHUNK + 4 * (size_t)(TN / 8) * B_SBO + 64; }
+size_t umma_smem_bytes(int TN) { return 2 * (2 * (size_t)A_CHUNK + 2 * (size_t)TN * UKC * 2) + 64; }
 
 void Umma::build(const Store& st, int R_, cudaStream_t s) {
   R = R_;
   TN = R >= 256 ? 256 : (R > 64 ? 128 : 64);
   const Tree& t = st.tree;
-  std::vector<int> bl, bm, bk;
-  std::vector<int4> tiles;
+  std::vector<int> bl, bm, bk, tb;
+  std::vector<int4> tiles, bdesc;
   for (int j = 0; j < st.n_leaf; ++j) {
     const int b = t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]];
     const int nmt = (b + UM - 1) / UM, nkc = (b + UKC - 1) / UKC;
+    std::vector<int> bfirst;   // first B block of each N tile of this leaf
+    for (int n0 = 0; n0 < R; n0 += TN) {
+      bfirst.push_back((int)bdesc.size());
+      for (int kc = 0; kc < nkc; ++kc) bdesc.push_back(make_int4(j, n0, kc, 0));
+    }
     for (int mt = 0; mt < nmt; ++mt) {
       const int first = (int)bl.size();
       for (int kc = 0; kc < nkc; ++kc) {
@@ -309,17 +310,25 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
         bm.push_back(mt);
         bk.push_back(kc);
       }
-      for (int n0 = 0; n0 < R; n0 += TN) tiles.push_back(make_int4(j, mt * UM, n0, first));
+      int nt = 0;
+      for (int n0 = 0; n0 < R; n0 += TN, ++nt) {
+        tiles.push_back(make_int4(j, mt * UM, n0, first));
+        tb.push_back(bfirst[nt]);
+      }
     }
   }
   n_blocks = (int)bl.size();
   n_tiles = (int)tiles.size();
+  n_bblocks = (int)bdesc.size();
   DevBuf<int> dl, dm, dk;
   dl.upload(bl, s);
   dm.upload(bm, s);
   dk.upload(bk, s);
   a_blocks.alloc((size_t)n_blocks * A_CHUNK);   // uint16 count: 2 splits x A_CHUNK bytes / 2
   k_tile_leaves<<<n_blocks, 256, 0, s>>>(st.view(), dl.p, dm.p, dk.p, a_blocks.p, n_blocks);
+  b_blocks.alloc((size_t)n_bblocks * 2 * TN * UKC);   // uint16 count: 2 splits x TN x 64
+  b_desc.upload(bdesc, s);
+  tile_b.upload(tb, s);
   d_tiles.alloc(tiles.size());
   EMT_CUDA(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   // the attribute is per kernel, shared by every simulation: allow the largest tile
@@ -329,14 +338,15 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
 }
 
 void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act) {
+  k_split_b<<<n_bblocks, 256, 0, s>>>(st.view(), b_desc.p, Xf, b_blocks.p, R, TN, n_bblocks);
   UmmaArgs a;
   a.tiles = d_tiles.p;
+  a.tile_b = tile_b.p;
   a.a_blocks = a_blocks.p;
-  a.Xf = Xf;
+  a.b_blocks = b_blocks.p;
   a.Y = Y;
   a.R = R;
   a.TN = TN;
-  a.nkc_max = 0;
   a.r_act = r_act;
   k_mc_umma<<<n_tiles, 256, umma_smem_bytes(TN), s>>>(st.view(), a, st.d_status.p);
   EMT_CUDA(cudaGetLastError());
