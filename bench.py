@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--time-steps", type=int, default=20000)
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="time steps per bench step (default: the workload's own; smaller values are for "
+                         "profiling captures, not bench lines)")
     ap.add_argument("--variants", default="ff64,fp32,fp64")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 41],
                     help="2: single 1,432-bus simulation (default); 3: N-1 screening, 256 contingencies; "
@@ -227,7 +229,7 @@ def native_arm(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    T = args.time_steps if args.config == 2 else 2000
+    T = (args.time_steps or 20000) if args.config == 2 else (args.time_steps or 2000)
     LV = 3 if args.config == 2 else 2
     net, trip, mon = workload(rank, args.config)
     n = net["n_bus"]
@@ -401,6 +403,7 @@ def multi_arm(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     net, trips, ss, ls, mon, R, T, levels = multi_workload(args.config)
+    T = args.time_steps or T
     n = net["n_bus"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -438,9 +441,49 @@ def multi_arm(args):
     value = job_rate(n * R * T, world, ms)
     traj = rec.cpu().numpy()
     st = L.emt_sim_stats(sim)
+
+    # the kernels of one apply pass (each launched twice per time step), timed alone on the operands
+    # of the last pass: 0 leaf GEMM, 1 BF16 split of its right-hand sides, 2 sweep GEMM, 3 expansion
+    reps = 200
+    kus = {}
+    for which in (0, 1, 2, 3):
+        L.emt_sim_bench_kernel(sim, which, reps, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.emt_sim_bench_kernel(sim, which, reps, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kus[which] = e0.elapsed_time(e1) / reps * 1e3
+    L.emt_sim_reset(sim, stream)
+    us_gemm = kus[0]
+
+    # end to end through the C ABI from host arrays: build, schedule, step, record read back
+    e2e_times = []
+    rec_host = torch.empty(T, R, N_MON, dtype=torch.float64, pin_memory=True)
+    h2d = sum(int(np.asarray(net[k]).nbytes) for k in ("br_a", "br_b", "kind", "R", "L", "C", "shunt_C", "src_bus",
+                                                          "src_Vm", "src_phi", "src_Rs"))
+    h2d += (0 if ss is None else np.asarray(ss).nbytes) + (0 if ls is None else np.asarray(ls).nbytes)
+    for i in range(max(1, min(args.steps, 2)) + 1):
+        barrier()
+        t0 = time.perf_counter()
+        s2 = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=R, src_scale=ss, load_scale=ls)
+        for c, (stp, e) in trips.items():
+            L.emt_sim_schedule(s2, stp, L.EMT_EVENT_TRIP, e, 0.0, c)
+        L.emt_sim_monitor(s2, mon)
+        L.emt_step(s2, T, rec, stream)
+        rec_host.copy_(rec, non_blocking=True)
+        torch.cuda.synchronize()
+        del s2
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_times.append(t1 - t0)
+    e2e_ms = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
+    e2e_val = job_rate(n * R * T, world, e2e_ms)
     # accuracy on sampled columns over a bounded number of steps (oracle, single thread)
     acc_cols = [0, R - 1] if args.config == 4 else [0, R // 2, R - 1]
-    acc_steps = T if args.config == 3 else 100
+    acc_steps = T if args.config == 3 else min(100, T)
     errs = {}
     cpu_sec = 0.0
     if rank == 0:
@@ -449,12 +492,30 @@ def multi_arm(args):
             cpu_sec += sec
             errs[c] = rel_err(traj[:acc_steps, c, :], ref)
     cpu_rate = n * acc_steps * len(acc_cols) / cpu_sec if cpu_sec else None
-    # algorithmic bytes and flops per time step: leaf GEMM twice (apply + refinement)
-    flops_step = 2 * 2 * st["leaf_elems"] * R + 2 * 2 * st["factor_elems"] * R
+    # leaf GEMM: 2 sum(b_j^2) R algorithmic flops per launch (FP32-grade products, each formed as
+    # three BF16 tensor-core products hi*hi + hi*lo + lo*hi)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    fp32_peak = 69.4   # TFLOP/s FP32 FMA, measured by the probe on this GB300 (2 flops per FMA)
-    achieved_tf = flops_step * T / (ms / 1e3) / 1e12
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    flops_gemm = 2 * st["leaf_elems"] * R
+    peak_tf = peaks["bf16_tflops"] / 3.0
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp32_peak = 69.4   # TFLOP/s FP32 FMA (2 flops per FMA), measured by the probe on this GB300
+    # algorithmic work per launch: flops of the products; bytes of the streaming parts (split:
+    # read FP32, write BF16 hi + lo; expansion epilogue: read Y, read and write float-float V)
+    per = {
+        "k_mc_umma<leaf> (tcgen05 BF16x3)": (kus[0], "tensor", flops_gemm / 1e12, peak_tf, "TFLOP/s"),
+        "k_split_b (BF16 hi/lo split)": (kus[1], "hbm", n * R * 8 / 1e9, hbm, "GB/s"),
+        "k_mc_sweep_gemm (FP32 SIMT, cluster split-K)": (kus[2], "alu", 2 * st["s_total"] * st["n_cut_rows"] * R
+                                                         / 1e12, fp32_peak, "TFLOP/s"),
+        "k_mc_umma<expand> (tcgen05 BF16x3 + float-float epilogue)": (kus[3], "hbm", n * R * 20 / 1e9, hbm, "GB/s"),
+    }
+    kernels = {}
+    for name, (us, bound, work, peak, unit) in per.items():
+        ach = work / (us * 1e-6)
+        kernels[name] = {"us_per_launch": us, "launches_per_time_step": 2, "bound": bound, "achieved": ach,
+                         "peak": peak, "unit": unit, "frac": ach / peak,
+                         "share_of_step": 2 * us * T / 1e3 / ms}
+    dom = max(kernels, key=lambda k: kernels[k]["us_per_launch"])
     if rank == 0:
         name = ("N-1 screening: 256 contingencies on the 1432-bus network, each trips a different branch at step "
                 "1000, 5000 steps" if args.config == 3 else
@@ -467,10 +528,15 @@ def multi_arm(args):
                        "l2": "flushed between timed steps"},
             "accuracy": {"sampled_columns": {str(k): v for k, v in errs.items()}, "sampled_steps": acc_steps,
                          "max": max(errs.values()) if errs else None},
-            "roofline": {"bound": "alu", "kernel": "whole step (FP32 SIMT leaf GEMM dominant)",
-                         "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tf / fp32_peak, "traffic": None,
-                         "peak_source": "FP32 FMA rate measured by the probe (no MEASURED_PEAKS entry for FP32)"},
+            "roofline": dict(kernels[dom], kernel=dom, traffic=None,
+                             peak_source=("measured" if "when" in peaks else "fallback")
+                             + " (tensor: bf16 burst / 3, three BF16 products per FP32-grade product; hbm: copy; "
+                               "alu: FP32 FMA rate of the probe)",
+                             kernels=kernels),
+            "e2e": {"value": e2e_val, "unit": "bus-steps/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": T * R * N_MON * 8,
+                    "includes": "emt_sim_create from host arrays (partition, GPU build), trip scheduling, emt_step, "
+                                "D2H of the record"},
             "cpu_baseline": {"value": cpu_rate, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"columns {acc_cols}, {acc_steps} steps each, exact hierarchical store"},
             "gpu_launches": int(launches), "clocks": clk,

@@ -240,8 +240,13 @@ emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
 /* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
  * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the
  * sweep/expansion kernel. With kernel generation 4 it enqueues one launch of the persistent
- * kernel running `reps` time steps (either `which`). Leaves the simulation state undefined: call
- * emt_sim_reset afterwards. Asynchronous on `stream`. */
+ * kernel running `reps` time steps (either `which`). For a simulation of several columns it
+ * enqueues `reps` launches, on the operands of the last pass (step at least once first), of:
+ * which = 0 the leaf-product GEMM; 1 the kernel splitting the right-hand sides into BF16 blocks
+ * for the tensor-core GEMM (EMT_ERR_UNSUPPORTED with the SIMT GEMM); 2 the boundary-sweep GEMM
+ * S = K Y_cut; 3 the expansion of a correction pass (with its BF16 split on the tensor-core
+ * path). Leaves the simulation state undefined: call emt_sim_reset afterwards. Asynchronous on
+ * `stream`. */
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream);
 void emt_sim_destroy(emt_sim* s);
 

@@ -310,8 +310,9 @@ emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n) {
 
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
-    s->sim->bench_kernel(which, reps, as_stream(stream));
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    if (s->msim) s->msim->bench_kernel(which, reps, as_stream(stream));
+    else s->sim->bench_kernel(which, reps, as_stream(stream));
   });
 }
 

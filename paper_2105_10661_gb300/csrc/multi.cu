@@ -58,37 +58,81 @@ __device__ __forceinline__ bool change_on(const MSimD& m, int c, int step) {
   return m.trip_step[c] > 0 && step >= m.trip_step[c] && step < m.trip_off[c];
 }
 
-__global__ void __launch_bounds__(128) k_mc_inject(MSimD m, int s_in_chunk, int* status) {
-  const int pos = blockIdx.x;
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R_act || *status != DEV_OK) return;
-  const int step = m.dyn->step_base + s_in_chunk + 1;
-  const bool trip = change_on(m, c, step) && m.trip_elem[c] >= 0;
-  const int te = m.trip_elem[c];
-  const int64_t R = m.R;
-  const float2 vi = m.V[pos * R + c];
-  float2 hist = ff_f(0.f);
-  for (int k = m.inc_ptr[pos]; k < m.inc_ptr[pos + 1]; ++k) {
-    const MRec rec = m.inc[k];
-    if (trip && rec.elem == te) {
-      m.Ih[k * R + c] = ff_f(0.f);
-      continue;
-    }
-    const float2 vo = rec.other >= 0 ? m.V[(int64_t)rec.other * R + c] : ff_f(0.f);
-    const float2 ve = rec.sgn > 0 ? ff_subx(vi, vo) : ff_subx(vo, vi);
-    const float2 cur = ff_addx(ff_mulx(rec.g, ve), m.Ih[k * R + c]);
-    const float2 Ihn = ff_addx(ff_mulx(rec.alpha, ve), ff_mulx(rec.beta, cur));
-    m.Ih[k * R + c] = Ihn;
-    hist = rec.sgn > 0 ? ff_subx(hist, Ihn) : ff_addx(hist, Ihn);
+// History update of every element and injection. A CTA takes `ipp` consecutive positions (1, 2,
+// 4 or 8) and 256 columns, one per thread. The element-end records and row pointers of its
+// positions are staged in shared memory first, so that each position then costs one round trip to
+// memory: its voltage, the other ends' voltages, the old histories (up to IKB ends) and the source
+// terms (up to ITB) are all loaded before any arithmetic.
+constexpr int IPP_MAX = 8, ITH = 256, IKB = 6, ITB = 2;
+__global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in_chunk, int* status) {
+  extern __shared__ __align__(16) unsigned char ism[];
+  MRec* srec = reinterpret_cast<MRec*>(ism);
+  __shared__ int sptr[IPP_MAX + 1], tptr[IPP_MAX + 1];
+  if (*status != DEV_OK) return;   // uniform, before any barrier
+  const int p0 = blockIdx.x * ipp, np = min(ipp, m.n - p0);
+  const int tid = threadIdx.x, c = blockIdx.y * ITH + tid;
+  if (tid <= np) {
+    sptr[tid] = m.inc_ptr[p0 + tid];
+    tptr[tid] = m.term_ptr[p0 + tid];
   }
+  __syncthreads();
+  const int r0 = sptr[0];
+  for (int i = tid; i < sptr[np] - r0; i += ITH) srec[i] = m.inc[r0 + i];
+  __syncthreads();
+  if (c >= m.R_act) return;
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  const int64_t R = m.R;
+  const float2* Ih_rd = m.Ih + (int64_t)((step - 1) & 1) * m.n_el * R;
+  float2* Ih_wr = m.Ih + (int64_t)(step & 1) * m.n_el * R;
+  const int te = change_on(m, c, step) ? m.trip_elem[c] : -1;   // tripped element of this column
   const int ti = step - m.dyn->trig_first;
   const float2 sw = m.trig[2 * ti], cw = m.trig[2 * ti + 1];
-  float2 inj = ff_f(0.f);
-  for (int t = m.term_ptr[pos]; t < m.term_ptr[pos + 1]; ++t)
-    inj = ff_addx(inj, ff_addx(ff_mulx(m.term_cs[t * R + c], sw), ff_mulx(m.term_sn[t * R + c], cw)));
-  const float2 x = ff_addx(inj, hist);
-  m.X[pos * R + c] = x;
-  m.Xf[pos * R + c] = x.x;
+  for (int pi = 0; pi < np; ++pi) {
+    const int pos = p0 + pi;
+    const int k1 = sptr[pi + 1] - r0, t1 = tptr[pi + 1];
+    int kb = sptr[pi] - r0, tb = tptr[pi];
+    const float2 vi = m.V[pos * R + c];
+    float2 hist = ff_f(0.f), inj = ff_f(0.f);
+    do {
+      float2 vo[IKB], ih[IKB], tc[ITB], ts[ITB];
+#pragma unroll
+      for (int q = 0; q < IKB; ++q) {
+        if (kb + q < k1) {
+          const MRec& r = srec[kb + q];
+          vo[q] = r.other >= 0 ? m.V[(int64_t)r.other * R + c] : ff_f(0.f);
+          ih[q] = Ih_rd[(int64_t)r.elem * R + c];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < ITB; ++q) {
+        if (tb + q < t1) {
+          tc[q] = m.term_cs[(int64_t)(tb + q) * R + c];
+          ts[q] = m.term_sn[(int64_t)(tb + q) * R + c];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < IKB; ++q) {
+        if (kb + q >= k1) break;
+        const MRec& r = srec[kb + q];
+        // v_e = v_from - v_to, formed identically at both ends
+        const float2 ve = r.sgn > 0 ? ff_subx(vi, vo[q]) : ff_subx(vo[q], vi);
+        float2 ihn = ff_addx(ff_mulx(r.a1, ve), ff_mulx(r.beta, ih[q]));
+        if (r.elem == te) ihn = ff_f(0.f);   // the tripped element carries no current
+        hist = r.sgn > 0 ? ff_subx(hist, ihn) : ff_addx(hist, ihn);
+        if (r.sgn > 0) Ih_wr[(int64_t)r.elem * R + c] = ihn;
+      }
+#pragma unroll
+      for (int q = 0; q < ITB; ++q) {
+        if (tb + q >= t1) break;
+        inj = ff_addx(inj, ff_addx(ff_mulx(tc[q], sw), ff_mulx(ts[q], cw)));
+      }
+      kb += IKB;
+      tb += ITB;
+    } while (kb < k1 || tb < t1);
+    const float2 x = ff_addx(inj, hist);
+    m.X[pos * R + c] = x;
+    m.Xf[pos * R + c] = x.x;
+  }
 }
 
 // Leaf stage as a GEMM over the columns: Y[leaf rows] = L_j (FP32) * Xf[leaf rows].
@@ -171,75 +215,134 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
 
 // Boundary sweep of all columns as one product: S = K Y_cut, K = the matrix of the sweep
 // (s_total x ldk, FP32, built on the device from the sweep image), Y_cut = the leaf-stage rows at
-// the distinct cut rows. Tiles of 32 rows of S x 64 columns, 32-deep chunks of K: 128 threads each
-// form a 4 x 4 block of outputs from 16-byte shared-memory reads; the next chunk is loaded into
-// registers while the current one is multiplied.
-constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128;
-__global__ void __launch_bounds__(SBT) k_mc_sweep_gemm(MSimD m, const float* __restrict__ K, int ldk,
-                                                       const int* status) {
+// the distinct cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows
+// inside its subtree, so each 32-row tile of S runs over the column range of K holding its
+// nonzeros (krange, found once after K is built). That range is split among the SKS CTAs of a
+// thread-block cluster. Each CTA forms a 32 x 64 partial in 32-deep chunks (128 threads, a 4 x 4
+// block of outputs each, from 16-byte shared-memory reads; the next chunk is loaded into
+// registers while the current one is multiplied) and keeps it in shared memory; after a cluster
+// barrier, CTA z sums rows [8z, 8z + 8) of the SKS partials in rank order through distributed
+// shared memory, so the result does not depend on timing.
+constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128, SKS = 4;
+__global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
+    k_mc_sweep_gemm(MSimD m, const float* __restrict__ K, int ldk, const int2* __restrict__ krange,
+                    const int* status) {
   __shared__ __align__(16) float Ks[SBK][SBM];
   __shared__ __align__(16) float Ys[SBK][SBN];
-  if (*status != DEV_OK) return;
+  __shared__ __align__(16) float Ps[SBM][SBN];
   const int* M = m.meta;
-  const int n_crow = M[M_NCROW], s_total = M[M_STOTAL];
+  const int s_total = M[M_STOTAL];
   const int* crow_pos = M + M[M_OFF_CROW];
   const int r0 = blockIdx.x * SBM, c0 = blockIdx.y * SBN;
-  if (c0 >= m.R_act) return;
+  uint32_t z;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(z));
+  // no early exit: every CTA of the cluster reaches both cluster barriers
+  const bool live = c0 < m.R_act && *status == DEV_OK;
+  const int2 kr = krange[blockIdx.x];
+  const int per = (kr.y - kr.x + SKS - 1) / SKS;
+  const int kb = kr.x + (int)z * per, ke = min(kr.y, kb + per);
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;   // rows ty*4.., columns tx*4..
   const int64_t R = m.R;
   constexpr int KL = SBK * SBM / SBT, YL = SBK * SBN / SBT;   // 8 and 16 loads per thread
-  float kr[KL], yr[YL];
+  float kreg[KL], yreg[YL];
   auto load = [&](int k0) {
 #pragma unroll
     for (int u = 0; u < KL; ++u) {
       const int w = tid + u * SBT, kk = w % SBK, rr = w / SBK;
       const int r = r0 + rr, k = k0 + kk;
-      kr[u] = (r < s_total && k < n_crow) ? K[(int64_t)r * ldk + k] : 0.f;
+      kreg[u] = (r < s_total && k < ke) ? K[(int64_t)r * ldk + k] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < YL; ++u) {
       const int w = tid + u * SBT, kk = w / SBN, cc = w % SBN;
       const int k = k0 + kk, c = c0 + cc;
-      yr[u] = (k < n_crow && c < m.R_act) ? m.Y[(int64_t)crow_pos[k] * R + c] : 0.f;
+      yreg[u] = (k < ke && c < m.R_act) ? m.Y[(int64_t)crow_pos[k] * R + c] : 0.f;
     }
   };
   float acc[4][4] = {};
-  load(0);
-  for (int k0 = 0; k0 < n_crow; k0 += SBK) {
+  if (live && kb < ke) {
+    load(kb);
+    for (int k0 = kb; k0 < ke; k0 += SBK) {
 #pragma unroll
-    for (int u = 0; u < KL; ++u) {
-      const int w = tid + u * SBT;
-      Ks[w % SBK][w / SBK] = kr[u];
-    }
+      for (int u = 0; u < KL; ++u) {
+        const int w = tid + u * SBT;
+        Ks[w % SBK][w / SBK] = kreg[u];
+      }
 #pragma unroll
-    for (int u = 0; u < YL; ++u) {
-      const int w = tid + u * SBT;
-      Ys[w / SBN][w % SBN] = yr[u];
-    }
-    __syncthreads();
-    if (k0 + SBK < n_crow) load(k0 + SBK);   // in flight during the products below
+      for (int u = 0; u < YL; ++u) {
+        const int w = tid + u * SBT;
+        Ys[w / SBN][w % SBN] = yreg[u];
+      }
+      __syncthreads();
+      if (k0 + SBK < ke) load(k0 + SBK);   // in flight during the products below
 #pragma unroll 8
-    for (int kk = 0; kk < SBK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&Ks[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Ys[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      for (int kk = 0; kk < SBK; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&Ks[kk][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Ys[kk][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty * 4 + i;
-    if (r >= s_total) continue;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = c0 + tx * 4 + q;
-      if (c < m.R_act) m.S[(int64_t)r * R + c] = acc[i][q];
+          for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
+      }
+      __syncthreads();
     }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(&Ps[ty * 4 + i][tx * 4]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (live) {
+    constexpr int RPC = SBM / SKS;           // rows reduced by one CTA
+    constexpr int NV = RPC * SBN / SBT;      // values per thread
+    // every remote load is issued before the first sum, then the partials are added in rank order
+    float x[NV][SKS];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int v = tid + u * SBT, rr = (int)z * RPC + v / SBN, cc = v % SBN;
+      const uint32_t local = (uint32_t)__cvta_generic_to_shared(&Ps[rr][cc]);
+#pragma unroll
+      for (int q = 0; q < SKS; ++q) {
+        uint32_t remote;
+        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(q));
+        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x[u][q]) : "r"(remote));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int v = tid + u * SBT, rr = (int)z * RPC + v / SBN, cc = v % SBN;
+      float sum = 0.f;
+#pragma unroll
+      for (int q = 0; q < SKS; ++q) sum += x[u][q];
+      const int r = r0 + rr, c = c0 + cc;
+      if (r < s_total && c < m.R_act) m.S[(int64_t)r * R + c] = sum;
+    }
+  }
+  // keep every partial alive until all CTAs of the cluster have read it
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Column range [first, last + 1) of the nonzeros of K in each 32-row tile ((0, 0) if none).
+__global__ void k_mc_krange(const float* __restrict__ K, int ldk, int s_total, int n_crow, int2* out) {
+  __shared__ int lo_s, hi_s;
+  if (threadIdx.x == 0) {
+    lo_s = n_crow;
+    hi_s = 0;
+  }
+  __syncthreads();
+  const int r0 = blockIdx.x * SBM;
+  int lo = n_crow, hi = 0;
+  for (int idx = threadIdx.x; idx < SBM * n_crow; idx += blockDim.x) {
+    const int r = r0 + idx / n_crow, k = idx % n_crow;
+    if (r < s_total && K[(int64_t)r * ldk + k] != 0.f) {
+      lo = min(lo, k);
+      hi = max(hi, k + 1);
+    }
+  }
+  atomicMin(&lo_s, lo);
+  atomicMax(&hi_s, hi);
+  __syncthreads();
+  if (threadIdx.x == 0) out[blockIdx.x] = lo_s < hi_s ? make_int2(lo_s, hi_s) : make_int2(0, 0);
 }
 
 // Corrected leaf-stage value v = y - sum over ancestors of F row . S(half) at one position and
@@ -367,18 +470,48 @@ __global__ void __launch_bounds__(XT) k_mc_expand_tiled(DStore st, MSimD m, cons
   }
 }
 
-// r = x - G' v (float-float), stored as the FP32 input of the correction apply.
-__global__ void __launch_bounds__(128) k_mc_residual(MSimD m, int n1, int s_in_chunk, const int* status) {
-  const int pos = blockIdx.x;
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= m.R_act || *status != DEV_OK) return;
+// r = x - G' v (float-float), stored as the FP32 input of the correction apply. Same shape as the
+// injection: `ipp` positions x 256 columns per CTA, the CSR rows of its positions staged in shared
+// memory, then one round trip per position (up to RKB entries per batch).
+constexpr int RKB = 8;
+__global__ void __launch_bounds__(ITH) k_mc_residual(MSimD m, int ipp, int n1, int s_in_chunk, const int* status) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  __shared__ int sptr[IPP_MAX + 1];
+  if (*status != DEV_OK) return;   // uniform, before any barrier
+  const int p0 = blockIdx.x * ipp, np = min(ipp, m.n - p0);
+  const int tid = threadIdx.x, c = blockIdx.y * ITH + tid;
+  if (tid <= np) sptr[tid] = m.csr_ptr[p0 + tid];
+  __syncthreads();
+  const int r0 = sptr[0], nnz = sptr[np] - r0;
+  float2* sval = reinterpret_cast<float2*>(rsm);
+  int* scol = reinterpret_cast<int*>(rsm + (size_t)nnz * sizeof(float2));
+  for (int i = tid; i < nnz; i += ITH) {
+    sval[i] = m.csr_ff[r0 + i];
+    scol[i] = m.csr_col[r0 + i];
+  }
+  __syncthreads();
+  if (c >= m.R_act) return;
   const int64_t R = m.R;
-  float2 r = m.X[pos * R + c];
-  for (int t = m.csr_ptr[pos]; t < m.csr_ptr[pos + 1]; ++t)
-    r = ff_subx(r, ff_mulx(m.csr_ff[t], m.V[(int64_t)m.csr_col[t] * R + c]));
-  if (n1) {
-    const int step = m.dyn->step_base + s_in_chunk + 1;
-    if (change_on(m, c, step)) {
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  const bool on = n1 && change_on(m, c, step);
+  for (int pi = 0; pi < np; ++pi) {
+    const int pos = p0 + pi;
+    const int k1 = sptr[pi + 1] - r0;
+    int kb = sptr[pi] - r0;
+    float2 r = m.X[pos * R + c];
+    while (kb < k1) {
+      float2 v[RKB];
+#pragma unroll
+      for (int q = 0; q < RKB; ++q)
+        if (kb + q < k1) v[q] = m.V[(int64_t)scol[kb + q] * R + c];
+#pragma unroll
+      for (int q = 0; q < RKB; ++q) {
+        if (kb + q >= k1) break;
+        r = ff_subx(r, ff_mulx(sval[kb + q], v[q]));
+      }
+      kb += RKB;
+    }
+    if (on) {
       const int a = m.trip_a[c], b = m.trip_b[c];
       if (pos == a || pos == b) {
         // (G' v)_i = (G v)_i + delta u_i (v_a - v_b)
@@ -388,8 +521,8 @@ __global__ void __launch_bounds__(128) k_mc_residual(MSimD m, int n1, int s_in_c
         r = pos == a ? ff_subx(r, dl) : ff_addx(r, dl);
       }
     }
+    m.Xf[pos * R + c] = r.x;
   }
-  m.Xf[pos * R + c] = r.x;
 }
 
 // d_c = 1 + delta_c u_c^T z_c (FP64) and the Sherman-Morrison factor delta_c / d_c
@@ -425,10 +558,10 @@ __global__ void k_mc_unit(MSimD m, float2* X, float* Xf) {
 }
 
 // Start column c afresh: zero its voltages, history and right-hand side.
-__global__ void k_mc_reset_col(MSimD m, int n_inc, int c) {
+__global__ void k_mc_reset_col(MSimD m, int n_rows, int c) {
   const int64_t R = m.R;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inc; i += gridDim.x * blockDim.x) {
-    m.Ih[i * R + c] = ff_f(0.f);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_rows; i += gridDim.x * blockDim.x) {
+    if (i < 2 * m.n_el) m.Ih[i * R + c] = ff_f(0.f);
     if (i < m.n) {
       m.V[i * R + c] = ff_f(0.f);
       m.X[i * R + c] = ff_f(0.f);
@@ -504,6 +637,7 @@ MSimD MSim::view() const {
   d.inc = inc.p;
   d.inc_ptr = inc_ptr.p;
   d.Ih = Ih.p;
+  d.n_el = n_el_h;
   d.V = V.p;
   d.X = X.p;
   d.Xf = Xf.p;
@@ -607,18 +741,40 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
     for (int e : at[p]) {
       MRec r{};
       const bool is_a = t.pos[el_a[e]] == p;
-      r.self = p;
       r.other = is_a ? (el_b[e] >= 0 ? t.pos[el_b[e]] : -1) : t.pos[el_a[e]];
       r.sgn = is_a ? 1 : -1;
       r.elem = (int)e;
-      r.g = host_ff(el_g[e]);
-      r.alpha = host_ff(el_al[e]);
+      // Ih' = alpha v + beta (g v + Ih) = (alpha + beta g) v + beta Ih
+      r.a1 = host_ff(el_al[e] + el_be[e] * el_g[e]);
       r.beta = host_ff(el_be[e]);
       recs.push_back(r);
     }
     iptr[p + 1] = (int)recs.size();
   }
   n_inc = (int)recs.size();
+  n_el_h = (int)el_a.size();
+  {
+    // shared memory of the injection / residual CTAs: the most records (CSR entries) of any
+    // aligned window of IPP_MAX positions (windows of 1, 2, 4 positions nest inside them)
+    const auto& cp = store->csr_ptr;
+    int mi = 0, mc = 0;
+    for (int p = 0; p < n; p += IPP_MAX) {
+      const int q = std::min(n, p + IPP_MAX);
+      mi = std::max(mi, iptr[q] - iptr[p]);
+      mc = std::max(mc, cp[q] - cp[p]);
+    }
+    inj_smem = (size_t)mi * sizeof(MRec);
+    res_smem = (size_t)mc * (sizeof(float2) + sizeof(int));
+    EMT_REQUIRE(inj_smem <= 160 * 1024 && res_smem <= 160 * 1024, EMT_ERR_UNSUPPORTED,
+                "too many element ends on 8 consecutive buses");
+    if (inj_smem > 48 * 1024)
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+    if (res_smem > 48 * 1024)
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
+    int dev = 0;
+    EMT_CUDA(cudaGetDevice(&dev));
+    EMT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   inc.upload(recs, s);
   inc_ptr.upload(iptr, s);
   // source and load terms with per-column scales
@@ -670,7 +826,7 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   csr_ff.upload(cff, s);
   // state
   const size_t nR = (size_t)n * R;
-  Ih.alloc((size_t)n_inc * R);
+  Ih.alloc((size_t)2 * std::max(n_el_h, 1) * R);
   V.alloc(nR);
   X.alloc(nR);
   Xf.alloc(nR);
@@ -694,7 +850,10 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   d_dyn.alloc(1);
   EMT_CUDA(cudaMemsetAsync(d_dyn.p, 0, sizeof(SimDyn), s));
   build_meta(s);
-  if ((R & 3) == 0 && R >= 32) umma.build(*store, R, s);
+  if ((R & 3) == 0 && R >= 32) {
+    umma.build(*store, R, s);
+    umma.build_expand(*store, path_ptr_h, path_ptr.p, path_fbase.p, path_kld.p, s);
+  }
   reset(s);
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   EMT_CUDA(cudaStreamSynchronize(s));
@@ -805,6 +964,11 @@ void MSim::build_meta(cudaStream_t s) {
     build_sweep_matrix(EMT_PREC_FP32, reinterpret_cast<const unsigned char*>(img.p), hdr.img_bytes,
                        reinterpret_cast<const unsigned char*>(st.C32.p), (int)(st.C_elems * 4), n_crow, st.s_total,
                        ldk, Kmat.p, s);
+    const int n_rt = std::max(1, (st.s_total + SBM - 1) / SBM);
+    krange.alloc(n_rt);
+    EMT_CUDA(cudaMemsetAsync(krange.p, 0, n_rt * sizeof(int2), s));
+    if (st.s_total > 0 && n_crow > 0) k_mc_krange<<<n_rt, 256, 0, s>>>(Kmat.p, ldk, st.s_total, n_crow, krange.p);
+    EMT_CUDA(cudaGetLastError());
     EMT_CUDA(cudaStreamSynchronize(s));
   }
   // expansion tiles (up to 32 positions of one leaf) and per-leaf path tables: for every element
@@ -836,6 +1000,7 @@ void MSim::build_meta(cudaStream_t s) {
     n_xtiles = (int)tl.size();
     xtiles.upload(tl, s);
     path_ptr.upload(pp, s);
+    path_ptr_h = pp;
     path_srow.upload(srow, s);
     path_fbase.upload(fb, s);
     path_kld.upload(kld, s);
@@ -886,8 +1051,7 @@ void MSim::prepare_trips(cudaStream_t s) {
   MSimD d = view();
   k_mc_unit<<<(R + 127) / 128, 128, 0, s>>>(d, X.p, Xf.p);
   apply_pass(0, 0, 0, 0, s);
-  const dim3 grid(n, (R + 127) / 128);
-  k_mc_residual<<<grid, 128, 0, s>>>(d, 0, 0, store->d_status.p);
+  launch_residual(0, 0, s);
   apply_pass(1, 0, 0, 0, s);
   EMT_CUDA(cudaMemcpyAsync(Z.p, V.p, nR * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   k_mc_trip_coef<<<(R + 127) / 128, 128, 0, s>>>(d, trip_coef.p, store->d_status.p);
@@ -906,22 +1070,72 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
     k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p,
                                       R_act);
   if (store->s_total > 0 && n_crow > 0)
-    k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN), SBT, 0, s>>>(
-        d, reinterpret_cast<const float*>(Kmat.p), ldk, store->d_status.p);
+    k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
+        d, reinterpret_cast<const float*>(Kmat.p), ldk, krange.p, store->d_status.p);
   if (n1) k_mc_fcol<<<(R_act + 127) / 128, 128, 0, s>>>(st, d, s_in_chunk, store->d_status.p);
-  k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
-      st, d, xtiles.p, path_ptr.p, path_srow.p, path_fbase.p, path_kld.p, pass, n1,
-      record, s_in_chunk, store->d_status.p);
+  if (gemm_kind == 2 && umma.exp_ready)
+    umma.expand(*store, d, path_ptr.p, path_srow.p, pass, n1, record, s_in_chunk, s);
+  else
+    k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
+        st, d, xtiles.p, path_ptr.p, path_srow.p, path_fbase.p, path_kld.p, pass, n1,
+        record, s_in_chunk, store->d_status.p);
   EMT_CUDA(cudaGetLastError());
+}
+
+void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
+  EMT_REQUIRE(which >= 0 && which <= 3, EMT_ERR_INVALID, "which must be 0..3");
+  EMT_REQUIRE(reps >= 1 && reps <= 100000, EMT_ERR_INVALID, "reps out of range");
+  const bool tc = gemm_kind == 2 && umma.ready;
+  EMT_REQUIRE(tc || which != 1, EMT_ERR_UNSUPPORTED, "the SIMT leaf GEMM has no split kernel");
+  const MSimD d = view();
+  for (int i = 0; i < reps; ++i) {
+    if (which == 1) {
+      umma.split(*store, Xf.p, s);
+    } else if (which == 0) {
+      if (tc) umma.mma(*store, Y.p, s, R_act);
+      else
+        k_mc_gemm<<<n_tiles, 256, 0, s>>>(store->view(), reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R,
+                                          store->d_status.p, R_act);
+    } else if (which == 2) {
+      if (store->s_total > 0 && n_crow > 0)
+        k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
+            d, reinterpret_cast<const float*>(Kmat.p), ldk, krange.p, store->d_status.p);
+    } else {
+      // expansion of the correction pass with the N-1 terms, without the record
+      if (gemm_kind == 2 && umma.exp_ready)
+        umma.expand(*store, d, path_ptr.p, path_srow.p, 1, 1, 0, 0, s);
+      else
+        k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
+            store->view(), d, xtiles.p, path_ptr.p, path_srow.p, path_fbase.p, path_kld.p, 1, 1, 0, 0,
+            store->d_status.p);
+    }
+  }
+  EMT_CUDA(cudaGetLastError());
+}
+
+// positions per CTA of the injection and residual kernels: enough CTAs for about four per SM
+int MSim::positions_per_cta() const {
+  const int64_t col_blocks = (R_act + ITH - 1) / ITH;
+  int ipp = IPP_MAX;
+  while (ipp > 1 && (int64_t)((n + ipp - 1) / ipp) * col_blocks < 4LL * n_sm) ipp /= 2;
+  return ipp;
+}
+
+void MSim::launch_residual(int n1, int s_in_chunk, cudaStream_t s) {
+  const MSimD d = view();
+  const int ipp = positions_per_cta();
+  k_mc_residual<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, res_smem, s>>>(d, ipp, n1, s_in_chunk,
+                                                                                        store->d_status.p);
 }
 
 void MSim::launch_steps(int nst, cudaStream_t s) {
   const MSimD d = view();
-  const dim3 grid(n, (R_act + 127) / 128);
+  const int ipp = positions_per_cta();
   for (int i = 0; i < nst; ++i) {
-    k_mc_inject<<<grid, 128, 0, s>>>(d, i, store->d_status.p);
+    k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, i,
+                                                                                        store->d_status.p);
     apply_pass(0, 1, 0, i, s);
-    k_mc_residual<<<grid, 128, 0, s>>>(d, 1, i, store->d_status.p);
+    launch_residual(1, i, s);
     apply_pass(1, 1, 1, i, s);
   }
   k_mc_advance<<<1, 1, 0, s>>>(d_dyn.p, nst);
@@ -973,7 +1187,8 @@ void MSim::admit(int c, int kind, int target, double value, int ev_step, int len
   z_ready = true;   // columns are managed one by one from here on
   const Tree& t = store->tree;
   const MSimD d = view();
-  k_mc_reset_col<<<(n_inc + 255) / 256, 256, 0, s>>>(d, n_inc, c);
+  const int n_rows = std::max(2 * n_el_h, n);
+  k_mc_reset_col<<<(n_rows + 255) / 256, 256, 0, s>>>(d, n_rows, c);
   const int n_terms = (int)(term_base.n / 2);
   const double S = omega * (double)cur_step * dt;
   k_mc_rotate_terms<<<(n_terms + 127) / 128, 128, 0, s>>>(d, term_base.p, term_cs.p, term_sn.p, n_terms, c, std::cos(S),

@@ -22,11 +22,13 @@
 
 namespace emt {
 
+// One element end: the element's history is kept once (per element, two buffers by step parity);
+// both ends evaluate the same update from the same operands, the from-end stores it.
 struct MRec {
-  int self, other, sgn, elem;
-  float2 g, alpha, beta;   // float-float
+  int other, sgn, elem, pad;   // other end's position (-1 ground), +1 at the from-end, element index
+  float2 a1, beta;             // float-float alpha + beta g and beta: Ih' = a1 v_e + beta Ih
 };
-static_assert(sizeof(MRec) == 40, "MRec must be 40 bytes");
+static_assert(sizeof(MRec) == 32, "MRec must be 32 bytes");
 
 struct MSimD {
   int n, R, s_total, n_crow, max_depth;
@@ -34,7 +36,8 @@ struct MSimD {
   const int* trip_off;  // [R] first step the change is no longer applied (INT_MAX for a trip)
   const MRec* inc;
   const int* inc_ptr;
-  float2* Ih;           // [n_inc][R]
+  float2* Ih;           // [2][n_el][R] element histories; step s reads buffer (s - 1) & 1, writes s & 1
+  int n_el;
   float2* V;            // [n][R]
   float2* X;            // [n][R]
   float* Xf;            // [n][R] GEMM input
@@ -68,9 +71,21 @@ struct Umma {
   int R = 0, TN = 0, n_blocks = 0, n_tiles = 0, n_bblocks = 0;
   DevBuf<uint16_t> a_blocks, b_blocks;   // pre-tiled BF16 splits of the leaves and of the right-hand sides
   DevBuf<int4> d_tiles, b_desc;
-  DevBuf<int> tile_b;
+  DevBuf<int2> tile_b;                   // (first B block, K chunks) per tile
+  // expansion V = Y - F_path S_path (every leaf has ancestor rows)
+  bool exp_ready = false;
+  int xTN = 64, x_blocks = 0, x_tiles = 0, x_bblocks = 0;
+  DevBuf<uint16_t> xa_blocks, xb_blocks; // factor paths (per store) and gathered S rows (per pass)
+  DevBuf<int4> x_tiles_d, x_bdesc;
+  DevBuf<int2> x_tile_b;
   void build(const Store& st, int R, cudaStream_t s);
+  void build_expand(const Store& st, const std::vector<int>& path_ptr_h, const int* path_ptr,
+                    const long long* path_fbase, const int* path_kld, cudaStream_t s);
+  void expand(const Store& st, const MSimD& m, const int* path_ptr, const int* path_srow, int pass, int n1,
+              int record, int s_in_chunk, cudaStream_t s);
   void launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act);
+  void split(const Store& st, const float* Xf, cudaStream_t s);       // right-hand sides -> BF16 blocks
+  void mma(const Store& st, float* Y, cudaStream_t s, int r_act);     // leaf products from the blocks
 };
 
 class MSim {
@@ -114,8 +129,11 @@ class MSim {
   DevBuf<float> Xf, Y, S, fcol;
   DevBuf<double> trip_delta, trip_coef;
   DevBuf<SimDyn> d_dyn;
-  int n_inc = 0, n_tiles = 0, n_crow = 0, ldk = 0, n_xtiles = 0;
+  int n_inc = 0, n_el_h = 0, n_tiles = 0, n_crow = 0, ldk = 0, n_xtiles = 0, n_sm = 1;
+  size_t inj_smem = 0, res_smem = 0;   // dynamic shared memory of the injection / residual CTAs
   DevBuf<float> Kmat;                       // matrix of the sweep (FP32), S = K Y_cut
+  DevBuf<int2> krange;                      // per 32-row tile of K: column range of its nonzeros
+  std::vector<int> path_ptr_h;              // host copy of path_ptr
   DevBuf<int4> xtiles;                      // expansion tiles: leaf, first position, positions
   DevBuf<int> path_ptr, path_srow, path_kld;   // per-leaf path tables of the expansion
   DevBuf<long long> path_fbase;
@@ -129,6 +147,10 @@ class MSim {
   void prepare_trips(cudaStream_t s);
   void launch_steps(int n, cudaStream_t s);
   void apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s);
+  void launch_residual(int n1, int s_in_chunk, cudaStream_t s);
+  int positions_per_cta() const;
+ public:
+  void bench_kernel(int which, int reps, cudaStream_t s);
   void drop_graphs();
 };
 

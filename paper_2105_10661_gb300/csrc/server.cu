@@ -44,11 +44,11 @@ Server::~Server() {
 int Server::add_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int max_slots, int n_mon,
                         const int32_t* mon) {
   EMT_REQUIRE(max_slots >= 4 && n_mon >= 1 && mon, EMT_ERR_INVALID, "need >= 4 slots and a monitor list");
-  // per-slot footprint: V, X (float-float), Xf, Y (FP32), Z (float-float), history per element end,
-  // boundary vectors, source coefficients
+  // per-slot footprint: V, X (float-float), Xf, Y (FP32), Z (float-float), two history buffers per
+  // element (series branches and one shunt per bus), boundary vectors, source coefficients
   const int64_t n = net->n_bus;
-  const int64_t n_inc_est = 2 * (int64_t)net->n_branch + n;
-  const int64_t per_slot = n * (8 + 8 + 4 + 4 + 8) + n_inc_est * 8 + 4 * 64 + (int64_t)(net->n_src + net->n_load) * 16;
+  const int64_t n_hist_est = 2 * ((int64_t)net->n_branch + n);
+  const int64_t per_slot = n * (8 + 8 + 4 + 4 + 8) + n_hist_est * 8 + 4 * 64 + (int64_t)(net->n_src + net->n_load) * 16;
   int slots = max_slots;
   if (budget > 0) {
     const int64_t share = (int64_t)(budget - used) / 2;   // leave room for later networks

@@ -1,20 +1,23 @@
-// Leaf stage of the multi-column apply on the 5th-generation tensor cores (tcgen05).
+// Dense products of the multi-column apply on the 5th-generation tensor cores (tcgen05).
 //
-//   Y[leaf rows, columns] = L_j * X_j,  L_j = L_hi + L_lo,  X = X_hi + X_lo  (BF16 splits)
-//   Y ~= L_hi X_hi + L_hi X_lo + L_lo X_hi   (FP32 accumulation in tensor memory)
-// The dropped L_lo X_lo term and the split residuals leave a relative error of about 2^-16;
-// the multi-column step's float-float residual refinement removes it.
+// Leaf stage:  Y[leaf rows, columns] = L_j X_j
+// Expansion:   V[leaf rows, columns] = Y - F_path S_path   (F_path = the leaf's rows of the factors
+//              of all its ancestors, concatenated; S_path = the matching rows of S, Eq. 9 factors)
+// Each product A B is formed from BF16 splits A = A_hi + A_lo, B = B_hi + B_lo as
+//   A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi   (FP32 accumulation in tensor memory);
+// the dropped A_lo B_lo term and the split residuals leave a relative error of about 2^-16, which
+// the multi-column step's float-float residual refinement removes.
 //
 // Both operands are pre-tiled in global memory in the canonical K-major core-matrix layout
-// (8 rows x 16 bytes per core matrix, no swizzle): A (the leaf blocks, split once per store) per
-// (leaf, 128-row tile, 64-deep K chunk), B (the right-hand sides, split once per pass by
-// k_split_b) per (leaf, TN-column tile, K chunk). One CTA computes a 128-row x TN-column tile of
-// one leaf as a two-stage pipeline: one thread issues one cp.async.bulk per operand and chunk into
-// a stage (full mbarrier), one thread issues tcgen05.mma (M = 128, N = TN, K = 16, kind::f16 with
-// BF16 inputs) three times per K step and commits them to the stage's empty mbarrier, and the
-// epilogue reads the accumulator with tcgen05.ld. Each mbarrier has a single waiter that waits
-// for its phases in order; every wait is bounded by clock64 and reports a timeout in the device
-// status word; tensor memory is always released.
+// (8 rows x 16 bytes per core matrix, no swizzle): A (leaf blocks or factor paths, split once per
+// store) per (leaf, 128-row tile, 64-deep K chunk), B (right-hand sides or gathered S rows, split
+// once per pass) per (leaf, TN-column tile, K chunk). One CTA computes a 128-row x TN-column tile
+// of one leaf as a two-stage pipeline: one thread issues one cp.async.bulk per operand and chunk
+// into a stage (full mbarrier), one thread issues tcgen05.mma (M = 128, N = TN, K = 16,
+// kind::f16 with BF16 inputs) three times per K step and commits them to the stage's empty
+// mbarrier, and the epilogue reads the accumulator with tcgen05.ld. Each mbarrier has a single
+// waiter that waits for its phases in order; every wait is bounded by clock64 and reports a
+// timeout in the device status word; tensor memory is always released.
 #include <algorithm>
 #include <cstdint>
 
@@ -87,28 +90,68 @@ __global__ void k_tile_leaves(DStore st, const int* __restrict__ blk_leaf, const
 
 struct UmmaArgs {
   const int4* tiles;        // (leaf, m0, n0, first A block of this leaf-M-tile)
-  const int* tile_b;        // first B block of the tile's (leaf, N tile)
-  const uint16_t* a_blocks; // pre-tiled leaf blocks
-  const uint16_t* b_blocks; // pre-tiled right-hand sides
-  float* Y;                 // [n][R]
+  const int2* tile_b;       // (first B block of the tile's (leaf, N tile), K chunks)
+  const uint16_t* a_blocks; // pre-tiled A operand
+  const uint16_t* b_blocks; // pre-tiled B operand
+  float* Y;                 // [n][R] leaf stage: written; expansion: read
   int R, TN;
   int r_act;                // columns in use; tiles starting beyond exit at once
 };
 
+// Expansion epilogue arguments.
+struct ExpArgs {
+  MSimD m;
+  int pass, n1, record, s_in_chunk;
+};
+
+enum { UMMA_LEAF = 0, UMMA_EXPAND = 1 };
+
+// A blocks of the expansion: per (leaf, M tile, K chunk) [hi | lo] of the leaf's factor path,
+// element (row r, path element e) = F[path_fbase[e0 + e] + position(r) * path_kld[e0 + e]].
+__global__ void k_tile_paths(DStore st, const int* __restrict__ blk_leaf, const int* __restrict__ blk_mt,
+                             const int* __restrict__ blk_kc, const int* __restrict__ path_ptr,
+                             const long long* __restrict__ path_fbase, const int* __restrict__ path_kld,
+                             uint16_t* __restrict__ out, int n_blk) {
+  const int blk = blockIdx.x;
+  if (blk >= n_blk) return;
+  const int j = blk_leaf[blk], mt = blk_mt[blk], kc = blk_kc[blk];
+  const int node = st.leaf_node[j];
+  const int lo = st.lo[node], b = st.hi[node] - lo;
+  const int e0 = path_ptr[j], ne = path_ptr[j + 1] - e0;
+  uint16_t* hi = out + (size_t)blk * (A_CHUNK);
+  uint16_t* lw = hi + A_CHUNK / 2;
+  for (int w = threadIdx.x; w < UM * UKC; w += blockDim.x) {
+    const int rr = w / UKC, kk = w % UKC;
+    const int r = mt * UM + rr, e = kc * UKC + kk;
+    const double v = (r < b && e < ne) ? st.F64[path_fbase[e0 + e] + (int64_t)(lo + r) * path_kld[e0 + e]] : 0.0;
+    const uint16_t h = bf16_bits((float)v);
+    const uint16_t l = bf16_bits((float)(v - (double)bf16_val(h)));
+    const uint32_t off = (rr / 8) * A_SBO + (kk / 8) * A_LBO + ((rr % 8) * 8 + (kk % 8)) * 2;
+    hi[off / 2] = h;
+    lw[off / 2] = l;
+  }
+}
+
 // B blocks: per (leaf j, N tile, K chunk) [hi | lo], each TN x 64 BF16 in the canonical K-major
-// layout (N-group stride 1024 bytes, K-core stride 128 bytes). Thread item = one column and 8
-// consecutive k: one 16-byte core row per split.
+// layout (N-group stride 1024 bytes, K-core stride 128 bytes). Grid (blocks, TN / 32) x 256
+// threads; thread = one column and 8 consecutive k: one 16-byte core row per split.
+// With path_ptr null the rows of chunk k are the leaf's positions (leaf stage, source Xf);
+// otherwise they are the rows path_srow[path_ptr[leaf] + k] of the source (expansion, source S).
 __global__ void k_split_b(DStore st, const int4* __restrict__ bdesc, const float* __restrict__ Xf,
-                          uint16_t* __restrict__ out, int R, int TN, int n_blk) {
+                          uint16_t* __restrict__ out, int R, int TN, int n_blk, const int* __restrict__ path_ptr,
+                          const int* __restrict__ path_srow) {
   const int blk = blockIdx.x;
   if (blk >= n_blk) return;
   const int4 d = bdesc[blk];   // leaf, N tile first column, K chunk, unused
   const int node = st.leaf_node[d.x];
-  const int lo = st.lo[node], b = st.hi[node] - lo;
+  const int lo = path_ptr ? path_ptr[d.x] : st.lo[node];
+  const int b = path_ptr ? path_ptr[d.x + 1] - lo : st.hi[node] - lo;
   unsigned char* hi = reinterpret_cast<unsigned char*>(out) + (size_t)blk * 4 * TN * UKC;
   unsigned char* lob = hi + (size_t)2 * TN * UKC;
-  for (int w = threadIdx.x; w < TN * (UKC / 8); w += blockDim.x) {
-    const int n = w % TN, kg = w / TN;
+  // CTA y covers columns [32 y, 32 y + 32) of the tile: thread = one column and one group of 8 k
+  {
+    const int n = blockIdx.y * 32 + (threadIdx.x & 31), kg = threadIdx.x >> 5;
+    if (n >= TN || kg >= UKC / 8) return;
     const int col = d.y + n;
     uint32_t h[4], l[4];
 #pragma unroll
@@ -117,7 +160,8 @@ __global__ void k_split_b(DStore st, const int4* __restrict__ bdesc, const float
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int k = d.z * UKC + kg * 8 + 2 * q + u;
-        x[u] = (k < b && col < R) ? Xf[(int64_t)(lo + k) * R + col] : 0.f;
+        const int row = k < b ? (path_srow ? path_srow[lo + k] : lo + k) : 0;
+        x[u] = (k < b && col < R) ? Xf[(int64_t)row * R + col] : 0.f;
       }
       const uint16_t h0 = bf16_bits(x[0]), h1 = bf16_bits(x[1]);
       const uint16_t l0 = bf16_bits(x[0] - bf16_val(h0)), l1 = bf16_bits(x[1] - bf16_val(h1));
@@ -136,7 +180,120 @@ __device__ __forceinline__ void bulk_g2s_u(unsigned char* dst, const void* src, 
                : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* status) {
+// Expansion epilogue: the accumulator (128 x TN, FP32) goes through shared memory (row stride
+// TN + 1 words: conflict-free both ways) so that each warp then handles one position's TN columns
+// with coalesced accesses: v = Y - acc (- f_c z for a column whose change is on), V = v (pass 0) or
+// V + v in float-float (pass 1), and the monitored record. The pipeline stages are free here (every
+// MMA reading them has completed).
+__device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs& x, uint32_t tmem, unsigned char* sm,
+                                                int lo, int b, int m0, int n0) {
+  const int TN = a.TN, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* T = reinterpret_cast<float*>(sm);
+  const int ldt = TN + 1;
+  {
+    const int lane_base = 32 * (warp & 3);
+    const int nchunks = TN / 32;
+    const int half = nchunks / 2 > 0 ? nchunks / 2 : 1;
+    const int c_begin = (warp >> 2) * half, c_end = min(nchunks, c_begin + half);
+    for (int ch = c_begin; ch < c_end; ++ch) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float* trow = T + (lane_base + lane) * ldt + ch * 32;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) trow[q] = __uint_as_float(r[q]);
+    }
+  }
+  __syncthreads();
+  const MSimD& m = x.m;
+  const int64_t R = m.R;
+  const int step = m.dyn->step_base + x.s_in_chunk + 1;
+  double* rec = x.record ? m.dyn->rec : nullptr;
+  const int rec_first = m.dyn->rec_first;
+  // lane: columns c, c + 1 of every row of this warp (TN = 64); four rows' loads in flight at once
+  const int cc = 2 * lane, c = n0 + cc;
+  const int nv = cc < TN ? max(0, min(2, m.R_act - c)) : 0;   // valid columns of this lane
+  float fc0 = 0.f, fc1 = 0.f;
+  if (x.n1 && nv > 0) {
+    fc0 = m.fcol[c];
+    if (nv > 1) fc1 = m.fcol[c + 1];
+  }
+  const int rows = min(UM, b - m0);
+  constexpr int RB = 4;
+  for (int r0 = warp; r0 < rows; r0 += 8 * RB) {
+    float2 y[RB];
+    float4 vo[RB];
+    int mi[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int rr = r0 + 8 * u;
+      const int64_t at = (int64_t)(lo + m0 + rr) * R + c;
+      y[u] = make_float2(0.f, 0.f);
+      vo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      mi[u] = -1;
+      if (rr < rows && nv > 0) {
+        if (nv == 2) {
+          y[u] = *reinterpret_cast<const float2*>(m.Y + at);
+          if (x.pass) vo[u] = *reinterpret_cast<const float4*>(m.V + at);
+        } else {
+          y[u].x = m.Y[at];
+          if (x.pass) {
+            const float2 o = m.V[at];
+            vo[u].x = o.x;
+            vo[u].y = o.y;
+          }
+        }
+        if (rec) mi[u] = m.mon_idx[lo + m0 + rr];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int rr = r0 + 8 * u;
+      if (rr >= rows || nv == 0) continue;
+      const int pos = lo + m0 + rr;
+      const int64_t at = (int64_t)pos * R + c;
+      float v[2] = {y[u].x - T[rr * ldt + cc], y[u].y - T[rr * ldt + cc + 1]};
+      if (fc0 != 0.f) v[0] = fmaf(-fc0, m.Z[at].x, v[0]);
+      if (fc1 != 0.f) v[1] = fmaf(-fc1, m.Z[at + 1].x, v[1]);
+      const float ox[2] = {vo[u].x, vo[u].z}, oy[2] = {vo[u].y, vo[u].w};
+      float2 out[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (x.pass == 0) {
+          out[q] = make_float2(v[q], 0.f);
+        } else {
+          // float-float V + v (TwoSum, then renormalisation)
+          const float s1 = __fadd_rn(ox[q], v[q]);
+          const float bb = __fsub_rn(s1, ox[q]);
+          const float err = __fadd_rn(__fsub_rn(ox[q], __fsub_rn(s1, bb)), __fsub_rn(v[q], bb));
+          const float lo2 = __fadd_rn(err, oy[q]);
+          const float hi2 = __fadd_rn(s1, lo2);
+          out[q] = make_float2(hi2, __fsub_rn(lo2, __fsub_rn(hi2, s1)));
+        }
+      }
+      if (nv == 2)
+        *reinterpret_cast<float4*>(m.V + at) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+      else
+        m.V[at] = out[0];
+      if (mi[u] >= 0) {
+        double* rp = rec + ((int64_t)(step - rec_first) * R + c) * m.n_mon + mi[u];
+        rp[0] = (double)out[0].x + (double)out[0].y;
+        if (nv == 2) rp[m.n_mon] = (double)out[1].x + (double)out[1].y;
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
   const uint32_t b_split = (uint32_t)TN * UKC * 2;              // bytes of one B split
@@ -148,11 +305,11 @@ __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int4 tl = a.tiles[blockIdx.x];
   const int j = tl.x, m0 = tl.y, n0 = tl.z, blk0 = tl.w;
-  const int bblk0 = a.tile_b[blockIdx.x];
+  const int2 tb = a.tile_b[blockIdx.x];
+  const int bblk0 = tb.x, nkc = tb.y;   // nkc >= 1
   if (n0 >= a.r_act) return;   // uniform per CTA, before any barrier or tensor memory use
   const int node = st.leaf_node[j];
   const int lo = st.lo[node], b = st.hi[node] - lo;
-  const int nkc = (b + UKC - 1) / UKC;
   if (tid == 0) {
     for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(bars + i)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,7 +400,9 @@ __global__ void __launch_bounds__(256, 1) k_mc_umma(DStore st, UmmaArgs a, int* 
   __syncthreads();
   const bool ok = ok_sh != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
+  if (MODE == UMMA_EXPAND) {
+    if (ok) expand_epilogue(a, x, tmem, sm, lo, b, m0, n0);
+  } else if (ok) {
     // epilogue: warp w reads lanes 32 (w % 4) .. +31; warps 0-3 and 4-7 split the columns
     const int lane_base = 32 * (warp & 3);
     const int row = m0 + lane_base + (tid & 31);
@@ -293,8 +452,9 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
   R = R_;
   TN = R >= 256 ? 256 : (R > 64 ? 128 : 64);
   const Tree& t = st.tree;
-  std::vector<int> bl, bm, bk, tb;
+  std::vector<int> bl, bm, bk;
   std::vector<int4> tiles, bdesc;
+  std::vector<int2> tb;
   for (int j = 0; j < st.n_leaf; ++j) {
     const int b = t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]];
     const int nmt = (b + UM - 1) / UM, nkc = (b + UKC - 1) / UKC;
@@ -313,7 +473,7 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
       int nt = 0;
       for (int n0 = 0; n0 < R; n0 += TN, ++nt) {
         tiles.push_back(make_int4(j, mt * UM, n0, first));
-        tb.push_back(bfirst[nt]);
+        tb.push_back(make_int2(bfirst[nt], nkc));
       }
     }
   }
@@ -329,16 +489,78 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
   b_blocks.alloc((size_t)n_bblocks * 2 * TN * UKC);   // uint16 count: 2 splits x TN x 64
   b_desc.upload(bdesc, s);
   tile_b.upload(tb, s);
-  d_tiles.alloc(tiles.size());
-  EMT_CUDA(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  d_tiles.upload(tiles, s);
   // the attribute is per kernel, shared by every simulation: allow the largest tile
-  EMT_CUDA(cudaFuncSetAttribute(k_mc_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)umma_smem_bytes(256)));
+  EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_LEAF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)umma_smem_bytes(256)));
   EMT_CUDA(cudaStreamSynchronize(s));   // the index lists above are freed on return
   ready = true;
 }
 
+void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* path_ptr,
+                        const long long* path_fbase, const int* path_kld, cudaStream_t s) {
+  const Tree& t = st.tree;
+  for (int j = 0; j < st.n_leaf; ++j)
+    if (pp[j + 1] == pp[j]) return;   // a leaf without ancestor rows: the SIMT expansion serves it
+  std::vector<int> bl, bm, bk;
+  std::vector<int4> tiles, bdesc;
+  std::vector<int2> tb;
+  for (int j = 0; j < st.n_leaf; ++j) {
+    const int b = t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]];
+    const int ne = pp[j + 1] - pp[j];
+    const int nmt = (b + UM - 1) / UM, nkc = (ne + UKC - 1) / UKC;
+    std::vector<int> bfirst;
+    for (int n0 = 0; n0 < R; n0 += xTN) {
+      bfirst.push_back((int)bdesc.size());
+      for (int kc = 0; kc < nkc; ++kc) bdesc.push_back(make_int4(j, n0, kc, 0));
+    }
+    for (int mt = 0; mt < nmt; ++mt) {
+      const int first = (int)bl.size();
+      for (int kc = 0; kc < nkc; ++kc) {
+        bl.push_back(j);
+        bm.push_back(mt);
+        bk.push_back(kc);
+      }
+      int nt = 0;
+      for (int n0 = 0; n0 < R; n0 += xTN, ++nt) {
+        tiles.push_back(make_int4(j, mt * UM, n0, first));
+        tb.push_back(make_int2(bfirst[nt], nkc));
+      }
+    }
+  }
+  x_blocks = (int)bl.size();
+  x_tiles = (int)tiles.size();
+  x_bblocks = (int)bdesc.size();
+  DevBuf<int> dl, dm, dk;
+  dl.upload(bl, s);
+  dm.upload(bm, s);
+  dk.upload(bk, s);
+  xa_blocks.alloc((size_t)x_blocks * A_CHUNK);
+  k_tile_paths<<<x_blocks, 256, 0, s>>>(st.view(), dl.p, dm.p, dk.p, path_ptr, path_fbase, path_kld, xa_blocks.p,
+                                        x_blocks);
+  EMT_CUDA(cudaGetLastError());
+  xb_blocks.alloc((size_t)x_bblocks * 2 * xTN * UKC);
+  x_bdesc.upload(bdesc, s);
+  x_tile_b.upload(tb, s);
+  x_tiles_d.upload(tiles, s);
+  EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)umma_smem_bytes(xTN)));
+  EMT_CUDA(cudaStreamSynchronize(s));
+  exp_ready = true;
+}
+
 void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, int r_act) {
-  k_split_b<<<n_bblocks, 256, 0, s>>>(st.view(), b_desc.p, Xf, b_blocks.p, R, TN, n_bblocks);
+  split(st, Xf, s);
+  mma(st, Y, s, r_act);
+}
+
+void Umma::split(const Store& st, const float* Xf, cudaStream_t s) {
+  k_split_b<<<dim3(n_bblocks, TN / 32), 256, 0, s>>>(st.view(), b_desc.p, Xf, b_blocks.p, R, TN, n_bblocks, nullptr,
+                                                     nullptr);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void Umma::mma(const Store& st, float* Y, cudaStream_t s, int r_act) {
   UmmaArgs a;
   a.tiles = d_tiles.p;
   a.tile_b = tile_b.p;
@@ -348,7 +570,31 @@ void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, in
   a.R = R;
   a.TN = TN;
   a.r_act = r_act;
-  k_mc_umma<<<n_tiles, 256, umma_smem_bytes(TN), s>>>(st.view(), a, st.d_status.p);
+  ExpArgs x{};
+  k_mc_umma<UMMA_LEAF><<<n_tiles, 256, umma_smem_bytes(TN), s>>>(st.view(), a, x, st.d_status.p);
+  EMT_CUDA(cudaGetLastError());
+}
+
+void Umma::expand(const Store& st, const MSimD& m, const int* path_ptr, const int* path_srow, int pass, int n1,
+                  int record, int s_in_chunk, cudaStream_t s) {
+  k_split_b<<<dim3(x_bblocks, xTN / 32), 256, 0, s>>>(st.view(), x_bdesc.p, m.S, xb_blocks.p, R, xTN, x_bblocks, path_ptr,
+                                      path_srow);
+  UmmaArgs a;
+  a.tiles = x_tiles_d.p;
+  a.tile_b = x_tile_b.p;
+  a.a_blocks = xa_blocks.p;
+  a.b_blocks = xb_blocks.p;
+  a.Y = m.Y;
+  a.R = R;
+  a.TN = xTN;
+  a.r_act = m.R_act;
+  ExpArgs x;
+  x.m = m;
+  x.pass = pass;
+  x.n1 = n1;
+  x.record = record;
+  x.s_in_chunk = s_in_chunk;
+  k_mc_umma<UMMA_EXPAND><<<x_tiles, 256, umma_smem_bytes(xTN), s>>>(st.view(), a, x, st.d_status.p);
   EMT_CUDA(cudaGetLastError());
 }
 
