@@ -412,7 +412,10 @@ def multi_arm(args):
         if world > 1:
             dist.barrier()
 
+    tune = [int(x) for x in args.tune.split(",")] if args.tune else None
     sim = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=R, src_scale=ss, load_scale=ls)
+    if tune:
+        L.emt_sim_tune(sim, *tune)
     for c, (st, e) in trips.items():
         L.emt_sim_schedule(sim, st, L.EMT_EVENT_TRIP, e, 0.0, c)
     L.emt_sim_monitor(sim, mon)
@@ -469,6 +472,8 @@ def multi_arm(args):
         barrier()
         t0 = time.perf_counter()
         s2 = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=R, src_scale=ss, load_scale=ls)
+        if tune:
+            L.emt_sim_tune(s2, *tune)
         for c, (stp, e) in trips.items():
             L.emt_sim_schedule(s2, stp, L.EMT_EVENT_TRIP, e, 0.0, c)
         L.emt_sim_monitor(s2, mon)

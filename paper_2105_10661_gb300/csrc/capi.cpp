@@ -269,7 +269,7 @@ emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
     EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
     if (s->msim) {
-      s->msim->set_gemm(kernels, nullptr);
+      s->msim->set_gemm(kernels, rows_per_cta, nullptr);
     } else {
       s->sim->tune(rows_per_cta, kernels, nullptr);
       if (kernels == 4 && !s->sim->use_v4()) {

@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
 }
 
 // Boundary sweep of all columns as one product: S = K Y_cut, K = the matrix of the sweep
-// (s_total x ldk, FP32, built on the device from the sweep image), Y_cut = the leaf-stage rows at
-// the distinct cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows
+// (s_total x n_crow, FP32, built on the device from the sweep image and kept transposed so that a
+// chunk is read and staged without bank conflicts), Y_cut = the leaf-stage rows at the distinct
+// cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows
 // inside its subtree, so each 32-row tile of S runs over the column range of K holding its
 // nonzeros (krange, found once after K is built). That range is split among the SKS CTAs of a
 // thread-block cluster. Each CTA forms a 32 x 64 partial in 32-deep chunks (128 threads, a 4 x 4
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
 // shared memory, so the result does not depend on timing.
 constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128, SKS = 4;
 __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
-    k_mc_sweep_gemm(MSimD m, const float* __restrict__ K, int ldk, const int2* __restrict__ krange,
+    k_mc_sweep_gemm(MSimD m, const float* __restrict__ Kt, int ldt, const int2* __restrict__ krange,
                     const int* status) {
   __shared__ __align__(16) float Ks[SBK][SBM];
   __shared__ __align__(16) float Ys[SBK][SBN];
@@ -248,9 +249,9 @@ __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
   auto load = [&](int k0) {
 #pragma unroll
     for (int u = 0; u < KL; ++u) {
-      const int w = tid + u * SBT, kk = w % SBK, rr = w / SBK;
+      const int w = tid + u * SBT, rr = w % SBM, kk = w / SBM;   // a warp reads 32 rows of one column
       const int r = r0 + rr, k = k0 + kk;
-      kreg[u] = (r < s_total && k < ke) ? K[(int64_t)r * ldk + k] : 0.f;
+      kreg[u] = (r < s_total && k < ke) ? Kt[(int64_t)k * ldt + r] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < YL; ++u) {
@@ -266,7 +267,7 @@ __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
 #pragma unroll
       for (int u = 0; u < KL; ++u) {
         const int w = tid + u * SBT;
-        Ks[w % SBK][w / SBK] = kreg[u];
+        Ks[w / SBM][w % SBM] = kreg[u];
       }
 #pragma unroll
       for (int u = 0; u < YL; ++u) {
@@ -320,6 +321,14 @@ __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
   }
   // keep every partial alive until all CTAs of the cluster have read it
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Kt[k][r] = K[r][k]
+__global__ void k_mc_transpose(const float* __restrict__ K, int ldk, int s_total, int n_crow, float* Kt, int ldt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s_total * n_crow) return;
+  const int k = i / s_total, r = i % s_total;
+  Kt[(int64_t)k * ldt + r] = K[(int64_t)r * ldk + k];
 }
 
 // Column range [first, last + 1) of the nonzeros of K in each 32-row tile ((0, 0) if none).
@@ -968,6 +977,11 @@ void MSim::build_meta(cudaStream_t s) {
     krange.alloc(n_rt);
     EMT_CUDA(cudaMemsetAsync(krange.p, 0, n_rt * sizeof(int2), s));
     if (st.s_total > 0 && n_crow > 0) k_mc_krange<<<n_rt, 256, 0, s>>>(Kmat.p, ldk, st.s_total, n_crow, krange.p);
+    ldt = (st.s_total + 3) / 4 * 4;
+    Kt.alloc(std::max<size_t>((size_t)n_crow * ldt, 1));
+    EMT_CUDA(cudaMemsetAsync(Kt.p, 0, Kt.n * sizeof(float), s));
+    if (st.s_total > 0 && n_crow > 0)
+      k_mc_transpose<<<(st.s_total * n_crow + 255) / 256, 256, 0, s>>>(Kmat.p, ldk, st.s_total, n_crow, Kt.p, ldt);
     EMT_CUDA(cudaGetLastError());
     EMT_CUDA(cudaStreamSynchronize(s));
   }
@@ -1071,7 +1085,7 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
                                       R_act);
   if (store->s_total > 0 && n_crow > 0)
     k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
-        d, reinterpret_cast<const float*>(Kmat.p), ldk, krange.p, store->d_status.p);
+        d, Kt.p, ldt, krange.p, store->d_status.p);
   if (n1) k_mc_fcol<<<(R_act + 127) / 128, 128, 0, s>>>(st, d, s_in_chunk, store->d_status.p);
   if (gemm_kind == 2 && umma.exp_ready)
     umma.expand(*store, d, path_ptr.p, path_srow.p, pass, n1, record, s_in_chunk, s);
@@ -1099,7 +1113,7 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
     } else if (which == 2) {
       if (store->s_total > 0 && n_crow > 0)
         k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
-            d, reinterpret_cast<const float*>(Kmat.p), ldk, krange.p, store->d_status.p);
+            d, Kt.p, ldt, krange.p, store->d_status.p);
     } else {
       // expansion of the correction pass with the N-1 terms, without the record
       if (gemm_kind == 2 && umma.exp_ready)
@@ -1230,12 +1244,14 @@ void MSim::admit(int c, int kind, int target, double value, int ev_step, int len
   EMT_CUDA(cudaGetLastError());
 }
 
-void MSim::set_gemm(int kind, cudaStream_t s) {
+void MSim::set_gemm(int kind, int tn, cudaStream_t s) {
   EMT_REQUIRE(kind == 1 || kind == 2, EMT_ERR_INVALID, "kernels must be 1 or 2");
+  EMT_REQUIRE(tn == 0 || tn == 64 || tn == 128 || tn == 256, EMT_ERR_INVALID, "tile width must be 0, 64, 128 or 256");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   gemm_kind = kind;
-  (void)s;
+  if (kind == 2 && umma.ready && tn != 0 && tn != umma.TN) umma.build(*store, R, s, tn);
+  EMT_CUDA(cudaStreamSynchronize(s));
 }
 
 void MSim::reset(cudaStream_t s) {

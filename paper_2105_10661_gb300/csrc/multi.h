@@ -78,7 +78,7 @@ struct Umma {
   DevBuf<uint16_t> xa_blocks, xb_blocks; // factor paths (per store) and gathered S rows (per pass)
   DevBuf<int4> x_tiles_d, x_bdesc;
   DevBuf<int2> x_tile_b;
-  void build(const Store& st, int R, cudaStream_t s);
+  void build(const Store& st, int R, cudaStream_t s, int tn = 0);
   void build_expand(const Store& st, const std::vector<int>& path_ptr_h, const int* path_ptr,
                     const long long* path_fbase, const int* path_kld, cudaStream_t s);
   void expand(const Store& st, const MSimD& m, const int* path_ptr, const int* path_srow, int pass, int n1,
@@ -99,7 +99,8 @@ class MSim {
   void read(int what, double* host_out);
   void reset(cudaStream_t s);
   void stats(int64_t* out, int n) const;
-  void set_gemm(int kind, cudaStream_t s);   // 1 SIMT FP32, 2 tcgen05 BF16x3
+  // 1 SIMT FP32, 2 tcgen05 BF16x3 with leaf-GEMM tiles tn columns wide (0: by the column count)
+  void set_gemm(int kind, int tn, cudaStream_t s);
   // serving: (re)start column c as a new request at the current step, with an optional
   // per-column change (kind 0 trip of series branch `target`, kind 1 fault at bus `target` with
   // R_f = value ohm lasting `len` steps, kind -1 none) `ev_step` steps after the start
@@ -133,6 +134,8 @@ class MSim {
   size_t inj_smem = 0, res_smem = 0;   // dynamic shared memory of the injection / residual CTAs
   DevBuf<float> Kmat;                       // matrix of the sweep (FP32), S = K Y_cut
   DevBuf<int2> krange;                      // per 32-row tile of K: column range of its nonzeros
+  DevBuf<float> Kt;                         // K transposed ([n_crow][ldt])
+  int ldt = 0;
   std::vector<int> path_ptr_h;              // host copy of path_ptr
   DevBuf<int4> xtiles;                      // expansion tiles: leaf, first position, positions
   DevBuf<int> path_ptr, path_srow, path_kld;   // per-leaf path tables of the expansion

@@ -10,9 +10,9 @@
 //
 // Both operands are pre-tiled in global memory in the canonical K-major core-matrix layout
 // (8 rows x 16 bytes per core matrix, no swizzle): A (leaf blocks or factor paths, split once per
-// store) per (leaf, 128-row tile, 64-deep K chunk), B (right-hand sides or gathered S rows, split
+// store) per (leaf, 128-row tile, 32-deep K chunk), B (right-hand sides or gathered S rows, split
 // once per pass) per (leaf, TN-column tile, K chunk). One CTA computes a 128-row x TN-column tile
-// of one leaf as a two-stage pipeline: one thread issues one cp.async.bulk per operand and chunk
+// of one leaf as a pipeline of 2-4 stages (96 KB, two CTAs per SM): one thread issues one cp.async.bulk per operand and chunk
 // into a stage (full mbarrier), one thread issues tcgen05.mma (M = 128, N = TN, K = 16,
 // kind::f16 with BF16 inputs) three times per K step and commits them to the stage's empty
 // mbarrier, and the epilogue reads the accumulator with tcgen05.ld. Each mbarrier has a single
@@ -30,10 +30,11 @@ namespace emt {
 namespace {
 
 constexpr int UM = 128;            // MMA M (tile rows)
-constexpr int UKC = 64;            // K chunk
-constexpr uint32_t A_CHUNK = UM * UKC * 2;          // 16 KB per split
-constexpr uint32_t A_SBO = 1024, A_LBO = 128;       // M-group stride, K-core stride
-constexpr uint32_t B_SBO = 1024, B_LBO = 128;       // N-group stride, K-core stride
+constexpr int UKC = 32;            // K chunk
+constexpr uint32_t A_CHUNK = UM * UKC * 2;          // 8 KB per split
+constexpr uint32_t A_SBO = UKC / 8 * 128, A_LBO = 128;   // M-group stride (8 rows x UKC), K-core stride
+constexpr uint32_t B_SBO = UKC / 8 * 128, B_LBO = 128;   // N-group stride, K-core stride
+constexpr uint32_t kStageBudget = 96 * 1024;        // pipeline shared memory per CTA: two CTAs per SM
 constexpr long long kSpin = 4000000000LL;           // ~2 s of SM clocks
 
 __device__ __forceinline__ uint32_t su(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -63,7 +64,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
-// A blocks: per (leaf, M tile, K chunk) 32 KB = [hi 16 KB | lo 16 KB], canonical layout.
+// A blocks: per (leaf, M tile, K chunk) [hi | lo], A_CHUNK bytes each, canonical layout.
 __global__ void k_tile_leaves(DStore st, const int* __restrict__ blk_leaf, const int* __restrict__ blk_mt,
                               const int* __restrict__ blk_kc, uint16_t* __restrict__ out, int n_blk) {
   const int blk = blockIdx.x;
@@ -95,6 +96,7 @@ struct UmmaArgs {
   const uint16_t* b_blocks; // pre-tiled B operand
   float* Y;                 // [n][R] leaf stage: written; expansion: read
   int R, TN;
+  int ns;                   // pipeline stages
   int r_act;                // columns in use; tiles starting beyond exit at once
 };
 
@@ -133,7 +135,7 @@ __global__ void k_tile_paths(DStore st, const int* __restrict__ blk_leaf, const 
 }
 
 // B blocks: per (leaf j, N tile, K chunk) [hi | lo], each TN x 64 BF16 in the canonical K-major
-// layout (N-group stride 1024 bytes, K-core stride 128 bytes). Grid (blocks, TN / 32) x 256
+// layout (N-group stride B_SBO, K-core stride 128 bytes). Grid (blocks, TN / 32) x 32 (UKC / 8)
 // threads; thread = one column and 8 consecutive k: one 16-byte core row per split.
 // With path_ptr null the rows of chunk k are the leaf's positions (leaf stage, source Xf);
 // otherwise they are the rows path_srow[path_ptr[leaf] + k] of the source (expansion, source S).
@@ -293,15 +295,18 @@ __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
+__global__ void __launch_bounds__(256, 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
   const uint32_t b_split = (uint32_t)TN * UKC * 2;              // bytes of one B split
   const uint32_t stage_bytes = 2 * A_CHUNK + 2 * b_split;
-  unsigned char* stg[2] = {sm, sm + stage_bytes};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage_bytes);   // full0, full1, empty0, empty1, done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
-  int* flag = reinterpret_cast<int*>(bars + 6);
+  const int ns = a.ns;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + ns * stage_bytes);   // full[ns], empty[ns], done
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ns;
+  uint64_t* done = bars + 2 * ns;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * ns + 1);
+  int* flag = reinterpret_cast<int*>(bars + 2 * ns + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int4 tl = a.tiles[blockIdx.x];
   const int j = tl.x, m0 = tl.y, n0 = tl.z, blk0 = tl.w;
@@ -311,7 +316,8 @@ __global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DS
   const int node = st.leaf_node[j];
   const int lo = st.lo[node], b = st.hi[node] - lo;
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(bars + i)) : "memory");
+    for (int i = 0; i <= 2 * ns; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(bars + i)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *flag = 0;
   }
@@ -328,35 +334,36 @@ __global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DS
   __shared__ int cnt_sh[2];        // [0] chunks copied (producer), [1] chunks multiplied (issuer)
   int issued = 0, committed = 0;
   if (tid == 0) {
-    // producer: stage s = kc % 2 is refilled once the MMAs of chunk kc - 2 released it
+    // producer: stage s = kc % ns is refilled once the MMAs of chunk kc - ns released it
     for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc & 1;
-      if (kc >= 2 && !bar_wait(bars + 2 + s, ((kc >> 1) - 1) & 1)) {
+      const int s = kc % ns, u = kc / ns;
+      unsigned char* stg = sm + s * stage_bytes;
+      if (kc >= ns && !bar_wait(empty + s, (u - 1) & 1)) {
         atomicExch(status, DEV_TIMEOUT);
         atomicExch(flag, 1);
         break;
       }
       if (*reinterpret_cast<volatile int*>(flag)) break;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su(bars + s)), "r"(stage_bytes)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su(full + s)), "r"(stage_bytes)
                    : "memory");
-      bulk_g2s_u(stg[s], reinterpret_cast<const unsigned char*>(a.a_blocks) + (size_t)(blk0 + kc) * 2 * A_CHUNK,
-                 2 * A_CHUNK, bars + s);
-      bulk_g2s_u(stg[s] + 2 * A_CHUNK, reinterpret_cast<const unsigned char*>(a.b_blocks) + (size_t)(bblk0 + kc) * 2 * b_split,
-                 2 * b_split, bars + s);
+      bulk_g2s_u(stg, reinterpret_cast<const unsigned char*>(a.a_blocks) + (size_t)(blk0 + kc) * 2 * A_CHUNK,
+                 2 * A_CHUNK, full + s);
+      bulk_g2s_u(stg + 2 * A_CHUNK, reinterpret_cast<const unsigned char*>(a.b_blocks) + (size_t)(bblk0 + kc) * 2 * b_split,
+                 2 * b_split, full + s);
       ++issued;
     }
   } else if (tid == 32) {
     // MMA issuer
     for (int kc = 0; kc < nkc; ++kc) {
-      const int s = kc & 1;
-      if (!bar_wait(bars + s, (kc >> 1) & 1)) {
+      const int s = kc % ns, u = kc / ns;
+      if (!bar_wait(full + s, u & 1)) {
         atomicExch(status, DEV_TIMEOUT);
         atomicExch(flag, 1);
         break;
       }
       if (*reinterpret_cast<volatile int*>(flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = su(stg[s]), a_lo = a_hi + A_CHUNK;
+      const uint32_t a_hi = su(sm + s * stage_bytes), a_lo = a_hi + A_CHUNK;
       const uint32_t b_hi = a_hi + 2 * A_CHUNK, b_lo = b_hi + b_split;
 #pragma unroll
       for (int ks = 0; ks < UKC / 16; ++ks) {
@@ -374,13 +381,29 @@ __global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DS
                      "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
                      : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bars + 2 + s))
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(empty + s))
                    : "memory");
       ++committed;
     }
     // all MMAs issued so far complete -> done
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bars + 4))
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(done))
                  : "memory");
+  } else if (MODE == UMMA_EXPAND && warp >= 2) {
+    // the epilogue's inputs do not depend on the product: bring its Y rows (and, in the
+    // correction pass, its V rows) into L2 while the MMAs run; one 128-byte line per request
+    const MSimD& m = x.m;
+    const int rows = min(UM, b - m0);
+    const int ncol = min(TN, m.R_act - n0);
+    if (ncol > 0) {
+      const int ly = (ncol * 4 + 127) / 128, lv = x.pass ? (ncol * 8 + 127) / 128 : 0;
+      for (int w = tid - 64; w < rows * (ly + lv); w += 192) {
+        const int rr = w / (ly + lv), l = w % (ly + lv);
+        const int64_t at = (int64_t)(lo + m0 + rr) * m.R + n0;
+        const void* p = l < ly ? (const void*)(reinterpret_cast<const char*>(m.Y + at) + 128 * l)
+                               : (const void*)(reinterpret_cast<const char*>(m.V + at) + 128 * (l - ly));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+      }
+    }
   }
   if (tid == 0) cnt_sh[0] = issued;
   if (tid == 32) cnt_sh[1] = committed;
@@ -388,14 +411,14 @@ __global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DS
   // the issuer's last commit covers every MMA it issued
   __shared__ int ok_sh;
   if (tid == 32) {
-    const bool ok = bar_wait(bars + 4, 0);
+    const bool ok = bar_wait(done, 0);
     if (!ok) atomicExch(status, DEV_TIMEOUT);
     ok_sh = ok && !*reinterpret_cast<volatile int*>(flag) && cnt_sh[1] == nkc;
   }
   if (tid == 0 && cnt_sh[0] > cnt_sh[1]) {
     // error path only: copies issued to stages the issuer never consumed; each is the latest use
     // of its stage (at most one per stage), so its phase parity is unambiguous
-    for (int kc = cnt_sh[1]; kc < cnt_sh[0]; ++kc) bar_wait(bars + (kc & 1), (kc >> 1) & 1);
+    for (int kc = cnt_sh[1]; kc < cnt_sh[0]; ++kc) bar_wait(full + kc % ns, (kc / ns) & 1);
   }
   __syncthreads();
   const bool ok = ok_sh != 0;
@@ -446,12 +469,36 @@ __global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 2 : 1) k_mc_umma(DS
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-size_t umma_smem_bytes(int TN) { return 2 * (2 * (size_t)A_CHUNK + 2 * (size_t)TN * UKC * 2) + 64; }
+// pipeline stages for a tile width: as many as fit the budget, 2..4
+int umma_stages(int TN) {
+  const uint32_t stage = 2 * A_CHUNK + 2 * (uint32_t)TN * UKC * 2;
+  return std::max(2, std::min(4, (int)(kStageBudget / stage)));
+}
+// stages + barriers (2 ns + 1) + tensor-memory slot + flag
+size_t umma_smem_bytes(int TN) {
+  return (size_t)umma_stages(TN) * (2 * (size_t)A_CHUNK + 2 * (size_t)TN * UKC * 2) + 128;
+}
 
-void Umma::build(const Store& st, int R_, cudaStream_t s) {
+void Umma::build(const Store& st, int R_, cudaStream_t s, int tn) {
   R = R_;
-  TN = R >= 256 ? 256 : (R > 64 ? 128 : 64);
   const Tree& t = st.tree;
+  if (tn == 0) {
+    // the widest tile that still gives every SM a tile (fewer, wider tiles re-read the leaf blocks
+    // less), else the narrowest
+    int dev = 0, n_sm = 1;
+    EMT_CUDA(cudaGetDevice(&dev));
+    EMT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    int64_t mtiles = 0;
+    for (int j = 0; j < st.n_leaf; ++j)
+      mtiles += (t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]] + UM - 1) / UM;
+    tn = 64;
+    for (int w : {256, 128})
+      if (w <= std::max(R, 64) && mtiles * ((R + w - 1) / w) >= n_sm) {
+        tn = w;
+        break;
+      }
+  }
+  TN = tn;
   std::vector<int> bl, bm, bk;
   std::vector<int4> tiles, bdesc;
   std::vector<int2> tb;
@@ -492,7 +539,7 @@ void Umma::build(const Store& st, int R_, cudaStream_t s) {
   d_tiles.upload(tiles, s);
   // the attribute is per kernel, shared by every simulation: allow the largest tile
   EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_LEAF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)umma_smem_bytes(256)));
+                                (int)std::max(umma_smem_bytes(256), std::max(umma_smem_bytes(128), umma_smem_bytes(64)))));
   EMT_CUDA(cudaStreamSynchronize(s));   // the index lists above are freed on return
   ready = true;
 }
@@ -555,7 +602,7 @@ void Umma::launch(const Store& st, const float* Xf, float* Y, cudaStream_t s, in
 }
 
 void Umma::split(const Store& st, const float* Xf, cudaStream_t s) {
-  k_split_b<<<dim3(n_bblocks, TN / 32), 256, 0, s>>>(st.view(), b_desc.p, Xf, b_blocks.p, R, TN, n_bblocks, nullptr,
+  k_split_b<<<dim3(n_bblocks, TN / 32), 32 * (UKC / 8), 0, s>>>(st.view(), b_desc.p, Xf, b_blocks.p, R, TN, n_bblocks, nullptr,
                                                      nullptr);
   EMT_CUDA(cudaGetLastError());
 }
@@ -569,6 +616,7 @@ void Umma::mma(const Store& st, float* Y, cudaStream_t s, int r_act) {
   a.Y = Y;
   a.R = R;
   a.TN = TN;
+  a.ns = umma_stages(TN);
   a.r_act = r_act;
   ExpArgs x{};
   k_mc_umma<UMMA_LEAF><<<n_tiles, 256, umma_smem_bytes(TN), s>>>(st.view(), a, x, st.d_status.p);
@@ -577,7 +625,7 @@ void Umma::mma(const Store& st, float* Y, cudaStream_t s, int r_act) {
 
 void Umma::expand(const Store& st, const MSimD& m, const int* path_ptr, const int* path_srow, int pass, int n1,
                   int record, int s_in_chunk, cudaStream_t s) {
-  k_split_b<<<dim3(x_bblocks, xTN / 32), 256, 0, s>>>(st.view(), x_bdesc.p, m.S, xb_blocks.p, R, xTN, x_bblocks, path_ptr,
+  k_split_b<<<dim3(x_bblocks, xTN / 32), 32 * (UKC / 8), 0, s>>>(st.view(), x_bdesc.p, m.S, xb_blocks.p, R, xTN, x_bblocks, path_ptr,
                                       path_srow);
   UmmaArgs a;
   a.tiles = x_tiles_d.p;
@@ -587,6 +635,7 @@ void Umma::expand(const Store& st, const MSimD& m, const int* path_ptr, const in
   a.Y = m.Y;
   a.R = R;
   a.TN = xTN;
+  a.ns = umma_stages(xTN);
   a.r_act = m.R_act;
   ExpArgs x;
   x.m = m;
