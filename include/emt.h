@@ -217,10 +217,12 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
  * 4 = the whole time loop in one persistent thread-block cluster whose shared memory holds the
  * store; rows_per_cta then is the cluster size (1, 2, 4, 8 or 16 CTAs), FP64 and FF64 stores
  * only; EMT_ERR_UNSUPPORTED, with generation 2 selected instead, when the store does not fit).
- * Multi-column simulations: `kernels` selects the products of the apply (1 = FP32 CUDA cores,
- * 2 = tcgen05 tensor cores with BF16 splits, used when nrhs is a multiple of 4 and >= 32);
- * with kernels 2, rows_per_cta (0, 64, 128 or 256) is the column width of a leaf-GEMM tile
- * (0 = chosen from nrhs). Synchronises the device; takes effect on the next emt_step. */
+ * Multi-column simulations: `kernels` selects the products of the apply (1 = FP32 CUDA cores;
+ * 2 = tcgen05 tensor cores with BF16 splits for the leaf stage, and for the expansion when it has
+ * a tile for every SM; 3 = tcgen05 for both; 2 and 3 need nrhs a multiple of 4 and >= 32, 2 is
+ * the default then); with kernels 2 or 3, rows_per_cta (0, 64, 128 or 256) is the column width of
+ * a leaf-GEMM tile (0 = chosen from nrhs). Synchronises the device; takes effect on the next
+ * emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
 /* Autotuner: time each candidate (cluster sizes 1..16 of generation 4, rows per CTA in {4..48}
  * of generations 3, 2 and 1) on

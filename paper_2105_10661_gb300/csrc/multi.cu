@@ -31,6 +31,29 @@ __device__ __forceinline__ float2 ff_negx(float2 a) { return make_float2(-a.x, -
 __device__ __forceinline__ float2 ff_subx(float2 a, float2 b) { return ff_addx(a, ff_negx(b)); }
 __device__ __forceinline__ float2 ff_f(float x) { return make_float2(x, 0.f); }
 
+// Compensated accumulation (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005: Sum2 / Dot2) on float-float operands: the running value is (s, c) with s the
+// FP32 sum of the leading parts and c the FP32 sum of every rounding error and trailing part;
+// TwoSum and FMA-based TwoProduct make each step's error exact, and (s, c) is renormalised once
+// when the value is stored. For the few terms summed here its error matches float-float's.
+struct Acc2 {
+  float s, c;
+  __device__ __forceinline__ void add(float p, float e) {   // += p + e, p leading, e small
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)), e));
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float2 a, float2 b) {   // += a b
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+    add(p, e);
+  }
+  __device__ __forceinline__ float2 get() const { return ff_n(s, c); }
+};
+__device__ __forceinline__ Acc2 acc2(float2 x) { return Acc2{x.x, x.y}; }
+
 float2 host_ff(double x) {
   const float h = (float)x;
   return make_float2(h, (float)(x - (double)h));
@@ -92,7 +115,7 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
     const int k1 = sptr[pi + 1] - r0, t1 = tptr[pi + 1];
     int kb = sptr[pi] - r0, tb = tptr[pi];
     const float2 vi = m.V[pos * R + c];
-    float2 hist = ff_f(0.f), inj = ff_f(0.f);
+    Acc2 hist{0.f, 0.f}, inj{0.f, 0.f};
     do {
       float2 vo[IKB], ih[IKB], tc[ITB], ts[ITB];
 #pragma unroll
@@ -114,22 +137,35 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
       for (int q = 0; q < IKB; ++q) {
         if (kb + q >= k1) break;
         const MRec& r = srec[kb + q];
-        // v_e = v_from - v_to, formed identically at both ends
-        const float2 ve = r.sgn > 0 ? ff_subx(vi, vo[q]) : ff_subx(vo[q], vi);
-        float2 ihn = ff_addx(ff_mulx(r.a1, ve), ff_mulx(r.beta, ih[q]));
+        // v_e = v_from - v_to (TwoSum of the leading parts), formed identically at both ends
+        const float2 vf = r.sgn > 0 ? vi : vo[q], vt = r.sgn > 0 ? vo[q] : vi;
+        Acc2 de = acc2(vf);
+        de.add(-vt.x, -vt.y);
+        const float2 ve = make_float2(de.s, de.c);
+        // Ih' = a1 v_e + beta Ih, renormalised once (it is state)
+        Acc2 h{0.f, 0.f};
+        h.add_prod(r.a1, ve);
+        h.add_prod(r.beta, ih[q]);
+        float2 ihn = h.get();
         if (r.elem == te) ihn = ff_f(0.f);   // the tripped element carries no current
-        hist = r.sgn > 0 ? ff_subx(hist, ihn) : ff_addx(hist, ihn);
-        if (r.sgn > 0) Ih_wr[(int64_t)r.elem * R + c] = ihn;
+        if (r.sgn > 0) {
+          hist.add(-ihn.x, -ihn.y);
+          Ih_wr[(int64_t)r.elem * R + c] = ihn;
+        } else {
+          hist.add(ihn.x, ihn.y);
+        }
       }
 #pragma unroll
       for (int q = 0; q < ITB; ++q) {
         if (tb + q >= t1) break;
-        inj = ff_addx(inj, ff_addx(ff_mulx(tc[q], sw), ff_mulx(ts[q], cw)));
+        inj.add_prod(tc[q], sw);
+        inj.add_prod(ts[q], cw);
       }
       kb += IKB;
       tb += ITB;
     } while (kb < k1 || tb < t1);
-    const float2 x = ff_addx(inj, hist);
+    inj.add(hist.s, hist.c);
+    const float2 x = inj.get();
     m.X[pos * R + c] = x;
     m.Xf[pos * R + c] = x.x;
   }
@@ -507,7 +543,7 @@ __global__ void __launch_bounds__(ITH) k_mc_residual(MSimD m, int ipp, int n1, i
     const int pos = p0 + pi;
     const int k1 = sptr[pi + 1] - r0;
     int kb = sptr[pi] - r0;
-    float2 r = m.X[pos * R + c];
+    Acc2 ra = acc2(m.X[pos * R + c]);
     while (kb < k1) {
       float2 v[RKB];
 #pragma unroll
@@ -516,10 +552,11 @@ __global__ void __launch_bounds__(ITH) k_mc_residual(MSimD m, int ipp, int n1, i
 #pragma unroll
       for (int q = 0; q < RKB; ++q) {
         if (kb + q >= k1) break;
-        r = ff_subx(r, ff_mulx(sval[kb + q], v[q]));
+        ra.add_prod(ff_negx(sval[kb + q]), v[q]);
       }
       kb += RKB;
     }
+    float2 r = ra.get();
     if (on) {
       const int a = m.trip_a[c], b = m.trip_b[c];
       if (pos == a || pos == b) {
@@ -1079,7 +1116,7 @@ void MSim::prepare_trips(cudaStream_t s) {
 void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s) {
   const DStore st = store->view();
   const MSimD d = view();
-  if (gemm_kind == 2 && umma.ready) umma.launch(*store, Xf.p, Y.p, s, R_act);
+  if (gemm_kind >= 2 && umma.ready) umma.launch(*store, Xf.p, Y.p, s, R_act);
   else
     k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p,
                                       R_act);
@@ -1087,7 +1124,7 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
     k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
         d, Kt.p, ldt, krange.p, store->d_status.p);
   if (n1) k_mc_fcol<<<(R_act + 127) / 128, 128, 0, s>>>(st, d, s_in_chunk, store->d_status.p);
-  if (gemm_kind == 2 && umma.exp_ready)
+  if (tensor_expand())
     umma.expand(*store, d, path_ptr.p, path_srow.p, pass, n1, record, s_in_chunk, s);
   else
     k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
@@ -1099,7 +1136,7 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
 void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
   EMT_REQUIRE(which >= 0 && which <= 3, EMT_ERR_INVALID, "which must be 0..3");
   EMT_REQUIRE(reps >= 1 && reps <= 100000, EMT_ERR_INVALID, "reps out of range");
-  const bool tc = gemm_kind == 2 && umma.ready;
+  const bool tc = gemm_kind >= 2 && umma.ready;
   EMT_REQUIRE(tc || which != 1, EMT_ERR_UNSUPPORTED, "the SIMT leaf GEMM has no split kernel");
   const MSimD d = view();
   for (int i = 0; i < reps; ++i) {
@@ -1116,7 +1153,7 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
             d, Kt.p, ldt, krange.p, store->d_status.p);
     } else {
       // expansion of the correction pass with the N-1 terms, without the record
-      if (gemm_kind == 2 && umma.exp_ready)
+      if (tensor_expand())
         umma.expand(*store, d, path_ptr.p, path_srow.p, 1, 1, 0, 0, s);
       else
         k_mc_expand_tiled<<<dim3(n_xtiles, (R_act + XC - 1) / XC), XT, 0, s>>>(
@@ -1244,13 +1281,19 @@ void MSim::admit(int c, int kind, int target, double value, int ev_step, int len
   EMT_CUDA(cudaGetLastError());
 }
 
+// tcgen05 expansion: with kernels 3, or with kernels 2 when it has a tile for every SM (smaller
+// problems run the SIMT expansion faster)
+bool MSim::tensor_expand() const {
+  return umma.exp_ready && (gemm_kind == 3 || (gemm_kind == 2 && umma.x_tiles >= n_sm));
+}
+
 void MSim::set_gemm(int kind, int tn, cudaStream_t s) {
-  EMT_REQUIRE(kind == 1 || kind == 2, EMT_ERR_INVALID, "kernels must be 1 or 2");
+  EMT_REQUIRE(kind >= 1 && kind <= 3, EMT_ERR_INVALID, "kernels must be 1, 2 or 3");
   EMT_REQUIRE(tn == 0 || tn == 64 || tn == 128 || tn == 256, EMT_ERR_INVALID, "tile width must be 0, 64, 128 or 256");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   gemm_kind = kind;
-  if (kind == 2 && umma.ready && tn != 0 && tn != umma.TN) umma.build(*store, R, s, tn);
+  if (kind >= 2 && umma.ready && tn != 0 && tn != umma.TN) umma.build(*store, R, s, tn);
   EMT_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -99,7 +99,8 @@ class MSim {
   void read(int what, double* host_out);
   void reset(cudaStream_t s);
   void stats(int64_t* out, int n) const;
-  // 1 SIMT FP32, 2 tcgen05 BF16x3 with leaf-GEMM tiles tn columns wide (0: by the column count)
+  // 1 SIMT FP32, 2 tcgen05 BF16x3 (expansion on tcgen05 when it fills the SMs), 3 tcgen05 for both
+  // products; leaf-GEMM tiles tn columns wide (0: by the column count)
   void set_gemm(int kind, int tn, cudaStream_t s);
   // serving: (re)start column c as a new request at the current step, with an optional
   // per-column change (kind 0 trip of series branch `target`, kind 1 fault at bus `target` with
@@ -152,6 +153,7 @@ class MSim {
   void apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s);
   void launch_residual(int n1, int s_in_chunk, cudaStream_t s);
   int positions_per_cta() const;
+  bool tensor_expand() const;
  public:
   void bench_kernel(int which, int reps, cudaStream_t s);
   void drop_graphs();

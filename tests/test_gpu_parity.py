@@ -335,13 +335,14 @@ def test_multi_column_reset_and_unaligned_columns(L):
     assert rel_err(a[:, 1, :].cpu().numpy(), ref) <= 1e-8
 
 
-@pytest.mark.parametrize("gemm", [1, 2])
+@pytest.mark.parametrize("gemm", [1, 2, 3])
 @pytest.mark.parametrize("which,levels,R,steps", [("tile", 2, 64, 50), ("tiles8", 3, 128, 40), ("tiles8", 3, 36, 30),
                                                    ("tiles8", 4, 100, 30)])
 def test_multi_column_gemm_kinds_match_oracle(L, gemm, which, levels, R, steps):
-    # gemm 1: FP32 CUDA-core products; gemm 2: tcgen05 BF16x3 leaf GEMM and expansion (FP32
-    # accumulate in TMEM). 36 and 100 columns leave a ragged last 64-column tile; four levels give
-    # ancestor paths longer than one 64-deep K chunk.
+    # gemm 1: FP32 CUDA-core products; 2: tcgen05 BF16x3 leaf GEMM (FP32 accumulate in TMEM), the
+    # expansion by size (SIMT at these sizes); 3: tcgen05 leaf GEMM and expansion. 36 and 100
+    # columns leave a ragged last 64-column tile; four levels give ancestor paths longer than one
+    # 32-deep K chunk.
     net = netgen.tile(1_000_000) if which == "tile" else netgen.tiled(2, 4)
     branches = netgen.pick_branches(net, 3, seed=5)
     trips = {0: (steps // 2, int(branches[0])), R // 2: (steps // 3, int(branches[1])), R - 1: (5, int(branches[2]))}
