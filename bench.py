@@ -42,9 +42,11 @@ def parse():
                     help="time steps per bench step (default: the workload's own; smaller values are for "
                          "profiling captures, not bench lines)")
     ap.add_argument("--variants", default="ff64,fp32,fp64")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 41],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 41],
                     help="2: single 1,432-bus simulation (default); 3: N-1 screening, 256 contingencies; "
-                         "4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of 2,000 requests")
+                         "4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of 2,000 requests; "
+                         "6: PAPER-mode d_th sweep (approximation error, build and modification cost); "
+                         "41: single apply on the 11,456-bus store")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--tune", default="", help="rows_per_cta,kernels: fixed launch shape instead of the autotuner "
                                                "(with kernels 4, rows_per_cta is the cluster size)")
@@ -711,6 +713,106 @@ def apply_arm(args):
     }))
 
 
+# ---------------------------------------------------------------- config 6 (d_th sweep)
+def dth_arm(args):
+    """PAPER-mode store (Algorithm 1) on tiled arrays of 1..12 tiles, leaves of at most d_th buses.
+
+    Per (network, d_th): the approximation error of the PAPER inverse against the exact one (Fig. 5,
+    from identity applies of a PAPER and an EXACT store), the GPU build time (Algorithm 1), and the
+    time of Algorithm 2 for a 10-ohm bus fault against rebuilding the store of the faulted network
+    (Theorem 1, Sec. V-C.2); with the element saving 1 - (b / N)^2 of inverting one b-bus leaf
+    instead of the whole matrix."""
+    import numpy as np
+    import torch
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    shapes = [(1, 1), (1, 2), (2, 2), (2, 4), (3, 4)]
+    dths = [22, 45, 90, 179]
+    fault_ohm = 10.0
+    rows = []
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    def inverse(h, n):
+        eye = torch.eye(n, dtype=torch.float64, device=dev)
+        out = torch.empty_like(eye)
+        L.emt_apply(h, eye, out, nrhs=n, stream=stream)
+        torch.cuda.synchronize()
+        return out
+
+    for (r, c) in shapes:
+        net = netgen.tile(1_000_000) if r * c == 1 else netgen.tiled(r, c)
+        n = net["n_bus"]
+        # the fault as a zero-volt source behind 10 ohm: G' = G + (1/10) e_a e_a^T
+        bus = n // 3
+        netf = dict(net)
+        for k, v in (("src_bus", bus), ("src_Vm", 0.0), ("src_phi", 0.0), ("src_Rs", fault_ohm)):
+            netf[k] = np.concatenate([np.asarray(net[k]), np.asarray([v], dtype=np.asarray(net[k]).dtype)])
+        he = L.emt_build_hinv_from_network(net, DT, d_th=max(dths))   # exact store (single leaf up to 179)
+        Gi = inverse(he, n)
+        for d in dths:
+            if d > n and d != dths[0]:
+                continue
+            L.emt_build_hinv_from_network(net, DT, d_th=d, mode=L.EMT_MODE_PAPER)   # warm (allocator, kernels)
+            h, build_ms = timed(lambda: L.emt_build_hinv_from_network(net, DT, d_th=d, mode=L.EMT_MODE_PAPER))
+            Gp = inverse(h, n)
+            err = float(torch.linalg.norm(Gp - Gi) / torch.linalg.norm(Gi))
+            tr = h.tree()
+            leaves = [j for j in range(len(tr["lo"])) if tr["left"][j] < 0]
+            bmax = max(int(tr["hi"][j] - tr["lo"][j]) for j in leaves)
+            _, mod_ms = timed(lambda: L.emt_modify_branch(h, bus, -1, 1.0 / fault_ohm, stream=stream))
+            hf, rebuild_ms = timed(lambda: L.emt_build_hinv_from_network(netf, DT, d_th=d, mode=L.EMT_MODE_PAPER))
+            # literal Algorithm 2 stops at the lowest common ancestor; a rebuild also changes the
+            # ancestors' factors: their gap
+            Gm, Gf = inverse(h, n), inverse(hf, n)
+            gap = float(torch.linalg.norm(Gm - Gf) / torch.linalg.norm(Gf))
+            rows.append({"n_bus": n, "d_th": d, "n_leaf": len(leaves), "max_leaf": bmax,
+                         "paper_rel_err_vs_exact": err, "build_ms": build_ms, "modify_ms": mod_ms,
+                         "rebuild_ms": rebuild_ms, "time_saved": 1.0 - mod_ms / rebuild_ms,
+                         "algorithm2_vs_rebuild_rel_diff": gap,
+                         "element_saving": 1.0 - (bmax / n) ** 2})
+    # scaling of the build time with N at each d_th (least-squares slope of log t vs log N)
+    slopes = {}
+    for d in dths:
+        pts = [(x["n_bus"], x["build_ms"]) for x in rows if x["d_th"] == d]
+        if len(pts) >= 3:
+            lx, ly = np.log([p[0] for p in pts]), np.log([p[1] for p in pts])
+            slopes[str(d)] = float(np.polyfit(lx, ly, 1)[0])
+    head = [x for x in rows if x["n_bus"] == max(y["n_bus"] for y in rows) and x["d_th"] == 45][0]
+    # the oracle's Algorithm 2 on the same fault, 179-bus tile, d_th 45 (one core)
+    from oracle import emt as oemt, hinv as ohinv, modify as omod, partition as opart
+    t_net = netgen.tile(1_000_000)
+    nw = oemt.Network(t_net, DT, want_tree=False)
+    tree = opart.build_tree(t_net["n_bus"], nw.series_frm, nw.series_to, 0, 45)
+    H = ohinv.HInv(nw.G, tree, nw.g_series, ohinv.PAPER)
+    t0 = time.perf_counter()
+    omod.algorithm2(H, nw.series_frm, nw.series_to, t_net["n_bus"] // 3, -1, 1.0 / fault_ohm)
+    cpu_ms = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({
+        "metric": "share of rebuild time saved by Algorithm 2 (10-ohm bus fault, PAPER store)",
+        "value": head["time_saved"], "unit": "fraction", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": head["modify_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "PAPER-mode d_th sweep on seeded tiled arrays (179..2148 buses), d_th in "
+                               f"{dths}, 10-ohm fault at bus N/3", "headline": "2148 buses, d_th 45"},
+        "table": rows, "build_time_exponent_vs_N": slopes,
+        "cpu_baseline": {"value": cpu_ms, "unit": "ms per Algorithm 2", "cores": 1, "kind": "oracle",
+                         "sample": "179-bus tile, d_th 45, the same fault"},
+        "gpu_launches": None,
+    }))
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -724,6 +826,8 @@ def main():
         serve_arm(args)
     elif args.config == 41:
         apply_arm(args)
+    elif args.config == 6:
+        dth_arm(args)
     else:
         native_arm(args)
 

@@ -88,6 +88,28 @@ def test_paper_apply_matches_algorithm1(L, prec):
     assert rel_err(got, ref) <= TOL[prec]
 
 
+def test_paper_dth_sweep_matches_algorithm1_and_fig5_trend(L):
+    # PAPER stores with leaves of at most d_th buses (levels 0): each equals the oracle's Algorithm 1
+    # on the same tree, and the approximation error against the exact inverse falls as d_th grows,
+    # to rounding at d_th = N (one leaf: the direct inverse), as in Fig. 5.
+    net = netgen.tile(1_000_000)
+    ni = _store_inputs(net)
+    nw = ni[0]
+    from oracle import partition as op
+    X = np.random.default_rng(12).standard_normal((net["n_bus"], 3))
+    exact = odense.DenseSolver(nw.G).solve(X)
+    errs = []
+    for d in (10, 45, 179):
+        tree = op.build_tree(net["n_bus"], net["br_a"], net["br_b"], 0, d)
+        H = ohinv.HInv(nw.G, tree, nw.g_series, ohinv.PAPER)
+        h = _build(L, ni, 0, d, 1, 0)
+        got = _apply(L, h, X)
+        assert rel_err(got, H.apply(X)) <= 1e-10
+        errs.append(rel_err(got, exact))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] <= 1e-12
+
+
 def _branch_cases(nw, tree):
     from oracle import partition as op
     cross = int(tree["cut_e"][tree["cut_ptr"][0]])
