@@ -554,7 +554,10 @@ def multi_arm(args):
 
 
 # ---------------------------------------------------------------- config 5 (serving)
-def serve_requests(nets, n_req, seed, rate, steps_lo=1000, steps_hi=10000):
+PRIV_BASE = 100   # request network index >= PRIV_BASE: private network PRIV_BASE + j of the pool
+
+
+def serve_requests(nets, n_req, seed, rate, steps_lo=1000, steps_hi=10000, priv=None, priv_frac=0.0):
     import numpy as np
     import netgen
     rng = np.random.default_rng(seed)
@@ -562,8 +565,12 @@ def serve_requests(nets, n_req, seed, rate, steps_lo=1000, steps_hi=10000):
     out = []
     for _ in range(n_req):
         t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
-        k = int(rng.integers(len(nets)))
-        net = nets[k][0]
+        if priv and rng.random() < priv_frac:
+            j = int(rng.integers(len(priv)))
+            k, net = PRIV_BASE + j, priv[j]
+        else:
+            k = int(rng.integers(len(nets)))
+            net = nets[k][0]
         steps = int(rng.integers(steps_lo, steps_hi + 1))
         if rng.random() < 0.5:
             out.append((k, t, steps, 0, int(rng.integers(len(net["br_a"]))), 0.0, int(rng.integers(1, steps)), 0))
@@ -585,6 +592,11 @@ def serve_arm(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     nets = [(netgen.tile(1_000_000), 2, 256), (netgen.tiled(2, 4), 3, 256), (netgen.config_network(4), 4, 128)]
     mons = [np.sort(np.random.default_rng(17 + i).choice(n[0]["n_bus"], N_MON, replace=False)) for i, n in enumerate(nets)]
+    # private networks: a pool of seeded 179-bus tiles that requests bring with them (10 % of the
+    # requests); each is built on its first arrival and then served from the resident copy
+    priv = [netgen.tile(3_000_000 + j) for j in range(16)]
+    priv_mon = np.arange(0, 179, 12)[:N_MON]
+    priv_frac = 0.1
 
     def make_server():
         srv = L.emt_server_create(100, 96 << 30)
@@ -592,20 +604,25 @@ def serve_arm(args):
                for i, n in enumerate(nets)]
         return srv, ids
 
+    def submit(srv, ids, r):
+        if r[0] >= PRIV_BASE:
+            return L.emt_server_submit_network(srv, priv[r[0] - PRIV_BASE], DT, *r[1:], levels=2, monitor=priv_mon)
+        return L.emt_server_submit(srv, ids[r[0]], *r[1:])
+
     # calibration: a burst at t = 0 measures the saturated request rate
     srv, ids = make_server()
-    cal = serve_requests(nets, 300, 99, 0.0)
+    cal = serve_requests(nets, 300, 99, 0.0, priv=priv, priv_frac=priv_frac)
     for r in cal:
-        L.emt_server_submit(srv, ids[r[0]], *r[1:])
+        submit(srv, ids, r)
     L.emt_server_run(srv)
     cst = L.emt_server_stats(srv)
     sat_rate = cst["finished"] / cst["wall_s"]
     del srv
     # the measured run: Poisson arrivals at 80% of the saturated rate
     rate = 0.8 * sat_rate
-    reqs = serve_requests(nets, args.requests, 17, rate)
+    reqs = serve_requests(nets, args.requests, 17, rate, priv=priv, priv_frac=priv_frac)
     srv, ids = make_server()
-    rids = [L.emt_server_submit(srv, ids[r[0]], *r[1:]) for r in reqs]
+    rids = [submit(srv, ids, r) for r in reqs]
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     L.emt_server_run(srv)
     clk = clocks.stop()
@@ -615,14 +632,16 @@ def serve_arm(args):
     cpu_sec = 0.0
     cpu_bus_steps = 0.0
     picks = [i for i, r in enumerate(reqs) if r[0] in (0, 1) and r[2] <= 2500][:4]
+    picks += [i for i, r in enumerate(reqs) if r[0] >= PRIV_BASE and r[2] <= 2500][:2]
     for i in picks:
         k, _, steps, kind, target, value, ev, ln = reqs[i]
-        net, levels, _ = nets[k]
+        net, levels = (priv[k - PRIV_BASE], 2) if k >= PRIV_BASE else nets[k][:2]
+        mon = priv_mon if k >= PRIV_BASE else mons[k]
         t0 = time.perf_counter()
         nw = oemt.Network(net, DT, levels=levels)
         evs = ([(ev, oemt.TRIP, target, 0.0)] if kind == 0 else
                [(ev, oemt.FAULT_ON, target, value), (ev + ln, oemt.FAULT_OFF, target, 0.0)])
-        ref, _ = oemt.simulate(nw, steps, evs, solver="exact", monitor=mons[k])
+        ref, _ = oemt.simulate(nw, steps, evs, solver="exact", monitor=mon)
         cpu_sec += time.perf_counter() - t0
         cpu_bus_steps += steps * net["n_bus"]
         got, _ = L.emt_server_result(srv, rids[i])
@@ -632,11 +651,15 @@ def serve_arm(args):
         "unit": "bus-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": st["wall_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff64-refine", "data": "synthetic",
         "config": {"workload": f"serving: Poisson stream of {args.requests} requests over resident 179/1432/11456-bus "
-                               "networks, 1000-10000 steps each, a line trip or a 10-ohm 400-step bus fault per request",
+                               "networks (10% bring one of 16 private 179-bus networks, built on first arrival), "
+                               "1000-10000 steps each, a line trip or a 10-ohm 400-step bus fault per request",
                    "arrival_rate_req_per_s": rate, "saturated_rate_req_per_s": sat_rate, "tick_steps": 100,
                    "slots": [n[2] for n in nets]},
         "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "max": st["max_s"]},
         "served": {k: st[k] for k in ("wall_s", "bus_steps", "max_queue", "ticks", "finished")},
+        "private_networks": {"requests": sum(1 for r in reqs if r[0] >= PRIV_BASE), "pool": len(priv),
+                             "builds": st["builds"], "cache_hits": st["cache_hits"], "build_s": st["build_s"],
+                             "evictions": st["evictions"]},
         "accuracy": {"sampled_requests": errs, "max": max(errs.values()) if errs else None},
         "cpu_baseline": {"value": cpu_bus_steps / cpu_sec if cpu_sec else None, "unit": "bus-steps/s", "cores": 1,
                          "kind": "oracle", "sample": f"{len(picks)} sampled requests, exact hierarchical store"},

@@ -276,13 +276,25 @@ emt_status emt_server_add_network(emt_server* s, const emt_network* net, const e
                                   int32_t max_slots, int32_t n_mon, const int32_t* mon_buses, int32_t* net_id);
 emt_status emt_server_submit(emt_server* s, int32_t net_id, double arrival_s, int32_t n_steps, int32_t event_kind,
                              int32_t target, double value, int32_t event_step, int32_t event_len, int32_t* req_id);
+/* A request on its own (private) network: the network, store options, time step and monitor
+ * list are copied now and keyed by their content. When the request arrives, a resident network
+ * with the same key serves it (cache hit); otherwise the server builds its store and a simulation
+ * of 4 request slots in the admission path (cache miss), so the build is part of this request's
+ * latency. Private networks with no active or queued request are evicted, least recently used
+ * first, when a new one would exceed the HBM budget; a request whose network cannot be placed yet
+ * waits. The event fields are those of emt_server_submit. Host arrays only. */
+emt_status emt_server_submit_network(emt_server* s, const emt_network* net, const emt_hinv_opts* opts, double dt,
+                                     int32_t n_mon, const int32_t* mon_buses, double arrival_s, int32_t n_steps,
+                                     int32_t event_kind, int32_t target, double value, int32_t event_step,
+                                     int32_t event_len, int32_t* req_id);
 /* Serve every submitted request that has not finished yet; returns when all are done. */
 emt_status emt_server_run(emt_server* s);
 /* Monitored voltages of a finished request ([n_steps][n_mon], may be NULL) and its times
  * (arrival, admission, completion in seconds since the start of emt_server_run; may be NULL). */
 emt_status emt_server_result(const emt_server* s, int32_t req_id, double* out, double* times3);
 /* out[0..n): wall seconds, bus-steps served, bus-steps per second, p50 / p99 / max latency (s),
- * largest queue length, ticks, finished requests. */
+ * largest queue length, ticks, finished requests, private-network builds, private-network cache
+ * hits, seconds spent building, evictions. */
 emt_status emt_server_stats(const emt_server* s, double* out, int32_t n);
 void emt_server_destroy(emt_server* s);
 

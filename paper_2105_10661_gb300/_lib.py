@@ -101,6 +101,9 @@ def _load():
                                              C.c_int32, _i32p, _i32p]),
         "emt_server_submit": (C.c_int, [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                         C.c_int32, C.c_int32, _i32p]),
+        "emt_server_submit_network": (C.c_int, [vp, C.POINTER(EmtNetwork), C.POINTER(EmtHinvOpts), C.c_double,
+                                                C.c_int32, _i32p, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                                                C.c_double, C.c_int32, C.c_int32, _i32p]),
         "emt_server_run": (C.c_int, [vp]),
         "emt_server_result": (C.c_int, [vp, C.c_int32, _f64p, _f64p]),
         "emt_server_stats": (C.c_int, [vp, _f64p, C.c_int32]),
@@ -122,7 +125,8 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
             "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
-            "emt_server_add_network", "emt_server_submit", "emt_server_run", "emt_server_result", "emt_server_stats",
+            "emt_server_add_network", "emt_server_submit", "emt_server_submit_network", "emt_server_run",
+            "emt_server_result", "emt_server_stats",
             "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network")
 
 
@@ -377,20 +381,34 @@ def emt_server_submit(srv: Server, net_id, arrival_s, n_steps, event_kind=-1, ta
     return rid.value
 
 
+def emt_server_submit_network(srv: Server, net: dict, dt, arrival_s, n_steps, event_kind=-1, target=0, value=0.0,
+                              event_step=0, event_len=0, levels=0, d_th=0, monitor=None):
+    nw, keep = make_network(net)
+    o = make_opts(levels, d_th, EMT_MODE_EXACT, EMT_PREC_FP32)
+    mon = _i32(monitor if monitor is not None else np.arange(min(16, net["n_bus"])))
+    rid = C.c_int32()
+    _check(lib.emt_server_submit_network(srv.h, C.byref(nw), C.byref(o), float(dt), len(mon), _p(mon, _i32p),
+                                         float(arrival_s), int(n_steps), int(event_kind), int(target), float(value),
+                                         int(event_step), int(event_len), C.byref(rid)))
+    srv.steps[rid.value] = (int(n_steps), ("req", len(mon)))
+    return rid.value
+
+
 def emt_server_run(srv: Server):
     _check(lib.emt_server_run(srv.h))
 
 
 def emt_server_result(srv: Server, req_id):
     n_steps, nid = srv.steps[req_id]
-    out = np.zeros((n_steps, srv.n_mon[nid]))
+    n_mon = nid[1] if isinstance(nid, tuple) else srv.n_mon[nid]
+    out = np.zeros((n_steps, n_mon))
     times = np.zeros(3)
     _check(lib.emt_server_result(srv.h, int(req_id), _p(out, _f64p), _p(times, _f64p)))
     return out, times
 
 
 SERVER_STAT_KEYS = ("wall_s", "bus_steps", "bus_steps_per_s", "p50_s", "p99_s", "max_s", "max_queue", "ticks",
-                    "finished")
+                    "finished", "builds", "cache_hits", "build_s", "evictions")
 
 
 def emt_server_stats(srv: Server):

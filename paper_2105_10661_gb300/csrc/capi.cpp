@@ -1,4 +1,5 @@
 // The extern "C" boundary: argument checks, exception-to-status translation, handle ownership.
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -341,6 +342,19 @@ emt_status emt_server_submit(emt_server* s, int32_t net_id, double arrival_s, in
   return guard([&] {
     EMT_REQUIRE(s && s->srv, EMT_ERR_INVALID, "null server");
     const int id = s->srv->submit(net_id, arrival_s, n_steps, event_kind, target, value, event_step, event_len);
+    if (req_id) *req_id = id;
+  });
+}
+
+emt_status emt_server_submit_network(emt_server* s, const emt_network* net, const emt_hinv_opts* opts, double dt,
+                                     int32_t n_mon, const int32_t* mon_buses, double arrival_s, int32_t n_steps,
+                                     int32_t event_kind, int32_t target, double value, int32_t event_step,
+                                     int32_t event_len, int32_t* req_id) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->srv, EMT_ERR_INVALID, "null server");
+    EMT_REQUIRE(dt > 0 && std::isfinite(dt), EMT_ERR_INVALID, "dt must be > 0");
+    const int id = s->srv->submit_network(net, opts, dt, n_mon, mon_buses, arrival_s, n_steps, event_kind, target, value,
+                                          event_step, event_len);
     if (req_id) *req_id = id;
   });
 }

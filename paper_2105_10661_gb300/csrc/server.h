@@ -1,6 +1,8 @@
 // Continuous-batching simulation server (see server.cu).
 #pragma once
+#include <cstdint>
 #include <memory>
+#include <unordered_map>
 #include <vector>
 
 #include "multi.h"
@@ -14,11 +16,25 @@ class Server {
   int add_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int max_slots, int n_mon,
                   const int32_t* mon);
   int submit(int net, double arrival, int n_steps, int kind, int target, double value, int ev_step, int len);
+  // a request on its own network (copied now; built, or found resident, when it arrives)
+  int submit_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int n_mon, const int32_t* mon,
+                     double arrival, int n_steps, int kind, int target, double value, int ev_step, int len);
   void run();
   void stats(double* out, int n) const;
 
+  // host copy of a private network, keyed by its content
+  struct NetDesc {
+    int32_t n_bus = 0;
+    std::vector<int32_t> from, to, kind, src_bus, load_bus, mon;
+    std::vector<double> R, L, C, shunt_C, src_Vm, src_phi, src_Rs, load_amp, load_phi;
+    double freq = 0, dt = 0;
+    emt_hinv_opts opts{};
+    uint64_t key = 0;
+    emt_network view() const;
+  };
   struct Req {
     int net = 0, n_steps = 0, kind = -1, target = 0, ev_step = 0, len = 0, slot = -1, done_steps = 0;
+    int priv = -1, n_mon = 0;   // private network description (-1: a base network)
     double value = 0, arrival = 0, t_admit = -1, t_done = -1;
     std::vector<double> out;
   };
@@ -31,17 +47,26 @@ class Server {
     double* host_rec = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    bool priv = false;          // built for private-network requests (evictable)
+    uint64_t key = 0;
+    double last_used = 0;
   };
+  static constexpr int kPrivSlots = 4;
   int K;
   size_t budget, used = 0;
   std::vector<Net> nets;
   std::vector<Req> reqs;
-  double wall = 0, bus_steps = 0;
-  int max_queue = 0;
+  std::vector<NetDesc> descs;
+  std::unordered_map<uint64_t, int> cache;   // content key -> resident network
+  double wall = 0, bus_steps = 0, build_s = 0;
+  int max_queue = 0, builds = 0, hits = 0, evictions = 0;
   int64_t ticks = 0;
 
  private:
   bool device_ok();
+  static int64_t per_slot_bytes(const emt_network* net);
+  int place_private(int req, double t, std::vector<int>& idle_since);
+  void evict(int ni);
 };
 
 }  // namespace emt

@@ -94,3 +94,63 @@ def test_server_queues_when_slots_are_full(L):
         got, times = L.emt_server_result(srv, rid)
         assert times[0] <= times[1] <= times[2]
         assert rel_err(got, ref[:60 + 5 * k]) <= 1e-8
+
+
+def _oracle_run(net, levels, steps, kind, target, value, ev, ln, mon):
+    nw = oemt.Network(net, DT, levels=levels)
+    events = []
+    if kind == 0:
+        events = [(ev, oemt.TRIP, target, 0.0)]
+    elif kind == 1:
+        events = [(ev, oemt.FAULT_ON, target, value), (ev + ln, oemt.FAULT_OFF, target, 0.0)]
+    ref, _ = oemt.simulate(nw, steps, events, solver="dense", monitor=mon)
+    return ref
+
+
+def test_server_private_networks_build_on_miss_and_hit_the_cache(L):
+    # requests that bring their own networks: the first request of each network builds its store in
+    # the admission path, a later request with the same content is served by the resident one
+    base = netgen.tile(1_000_000)
+    p1 = netgen.tile(1_000_007)
+    p2 = netgen.tiled(1, 2, seed0=1_000_020)
+    e1 = netgen.pick_branches(p1, 1, seed=5)
+    mon1, mon2 = np.arange(0, p1["n_bus"], 13), np.arange(0, p2["n_bus"], 17)
+    srv = L.emt_server_create(30, 0)
+    nid = L.emt_server_add_network(srv, base, DT, levels=2, max_slots=8, monitor=np.arange(6))
+    cases = [
+        (p1, mon1, (0.00, 120, 0, int(e1[0]), 0.0, 50, 0)),
+        (p1, mon1, (0.01, 90, 1, 9, 10.0, 20, 30)),
+        (p2, mon2, (0.02, 100, -1, 0, 0.0, 0, 0)),
+    ]
+    rids = [L.emt_server_submit_network(srv, net, DT, *args, levels=2, monitor=mon) for net, mon, args in cases]
+    rb = L.emt_server_submit(srv, nid, 0.0, 80)
+    L.emt_server_run(srv)
+    st = L.emt_server_stats(srv)
+    assert st["finished"] == 4 and st["builds"] == 2 and st["cache_hits"] == 1 and st["evictions"] == 0
+    assert st["build_s"] > 0
+    for (net, mon, args), rid in zip(cases, rids):
+        got, times = L.emt_server_result(srv, rid)
+        assert times[0] <= times[1] <= times[2]
+        ref = _oracle_run(net, 2, args[1], *args[2:], mon)
+        assert rel_err(got, ref) <= 1e-8, rel_err(got, ref)
+    got, _ = L.emt_server_result(srv, rb)
+    assert rel_err(got, _oracle_run(base, 2, 80, -1, 0, 0.0, 0, 0, np.arange(6))) <= 1e-8
+
+
+def test_server_evicts_idle_private_networks_under_the_budget(L):
+    # a budget that holds one private network at a time: each arrival of the other network evicts
+    # the idle one (least recently used) and builds its own
+    p1 = netgen.tile(1_000_007)
+    p2 = netgen.tiled(1, 2, seed0=1_000_020)
+    mon1, mon2 = np.arange(5), np.arange(7)
+    srv = L.emt_server_create(30, 120_000)
+    r = [L.emt_server_submit_network(srv, p1, DT, 0.0, 60, levels=2, monitor=mon1),
+         L.emt_server_submit_network(srv, p2, DT, 1.0, 60, levels=2, monitor=mon2),
+         L.emt_server_submit_network(srv, p1, DT, 2.0, 60, levels=2, monitor=mon1)]
+    L.emt_server_run(srv)
+    st = L.emt_server_stats(srv)
+    assert st["finished"] == 3 and st["builds"] == 3 and st["evictions"] == 2 and st["cache_hits"] == 0
+    ref1 = _oracle_run(p1, 2, 60, -1, 0, 0.0, 0, 0, mon1)
+    assert rel_err(L.emt_server_result(srv, r[0])[0], ref1) <= 1e-8
+    assert rel_err(L.emt_server_result(srv, r[2])[0], ref1) <= 1e-8
+    assert rel_err(L.emt_server_result(srv, r[1])[0], _oracle_run(p2, 2, 60, -1, 0, 0.0, 0, 0, mon2)) <= 1e-8
