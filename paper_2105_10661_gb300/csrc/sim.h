@@ -103,7 +103,7 @@ void step3_launch_any(Sim& sm, int n, cudaStream_t s);
 struct Step4D {
   int C, P;         // CTAs in the cluster; most CTAs sharing one leaf
   int o_x, o_part, o_ycp, o_ycut, o_yvp, o_s, o_v, o_contrib, o_row, o_vrow, o_out, o_push, o_img, o_K, o_L, o_F;
-  int max_vrows, img_int_bytes, ldk, n_crow, fstride;
+  int max_vrows, img_int_bytes, ldk, n_crow, fstride, s_total;
   const int* hdr;   // [C][24] per-CTA header
   const int* tab;   // per-CTA tables
   const double* K;  // [s_total][ldk] matrix of the boundary sweep (8-byte elements)

@@ -74,6 +74,18 @@ __device__ __forceinline__ void st_remote(uint32_t a, float2 v) {
 __device__ __forceinline__ void st_remote(uint32_t a, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
+// asynchronous remote store whose completion is counted (in bytes) on the destination CTA's
+// mbarrier `mbar` (a shared::cluster address in the destination CTA)
+__device__ __forceinline__ void st_async(uint32_t a, float2 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(a),
+               "f"(v.x), "f"(v.y), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, double v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(a), "d"(v),
+               "r"(mbar)
+               : "memory");
+}
 __device__ __forceinline__ int ld_remote_i32(uint32_t a) {
   int v;
   asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
@@ -92,14 +104,14 @@ __device__ __forceinline__ void bulk4(void* dst, const void* src, uint32_t bytes
       "l"(src), "r"(bytes), "r"(sa4(bar))
       : "memory");
 }
-// Non-blocking polls of phase 0 until `limit` SM clock cycles have passed.
-__device__ __forceinline__ bool mbar_wait4(uint64_t* bar, long long limit) {
+// Non-blocking polls of the phase with the given parity until `limit` SM clock cycles have passed.
+__device__ __forceinline__ bool mbar_wait4(uint64_t* bar, long long limit, uint32_t parity = 0) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok)
-                 : "r"(sa4(bar))
+                 : "r"(sa4(bar)), "r"(parity)
                  : "memory");
     if (ok) return true;
     if (clock64() - t0 > limit) return false;
@@ -163,8 +175,9 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   using X = typename A::X;
   using T = typename A::T;
   extern __shared__ __align__(128) unsigned char sm4[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm4);
-  int* flag = reinterpret_cast<int*>(sm4 + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm4);        // prologue copies
+  uint64_t* sbar = reinterpret_cast<uint64_t*>(sm4 + 8);    // slices of s arriving from the other CTAs
+  int* flag = reinterpret_cast<int*>(sm4 + 16);             // [0] own ok, [1] cluster ok, [2] s wait failed
   const int tid = threadIdx.x;
   const int C = d.C, P = d.P;
   const int rank = C > 1 ? (int)cta_rank4() : 0;
@@ -200,6 +213,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   //      sweep image (ancestor lists) ...
   if (tid < 32) {
     if (tid == 0) {
+      mbar_init4(sbar);
       mbar_init4(bar);
       mbar_expect4(bar, (uint32_t)hd[H_LBYTES] + (uint32_t)d.img_int_bytes);
       bulk4(sm4 + d.o_img, q.img, (uint32_t)d.img_int_bytes, bar);
@@ -271,6 +285,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       mbar_wait4(bar, kWait4);   // give copies in flight a second bounded chance
     }
     flag[0] = (ok && *reinterpret_cast<volatile int*>(st.status) == DEV_OK) ? 1 : 0;
+    flag[2] = 0;
   }
   if (C > 1) cluster_barrier(); else __syncthreads();
   if (tid == 0) {
@@ -374,7 +389,12 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       else st_remote(mapa4(sa4(sm4) + off, (uint32_t)pr[1]), y);
     }
     if (C > 1) cluster_barrier(); else __syncthreads();
-    // 3. cut-row values, then this CTA's slice of s = K y_cut, pushed to every CTA
+    // 3. cut-row values, then this CTA's slice of s = K y_cut, sent to every other CTA by
+    //    asynchronous remote stores that count on the receiver's mbarrier: each CTA waits for its
+    //    own (s_total - ns) values only, instead of a cluster barrier. The next step's first
+    //    cluster barrier keeps a sender from overwriting s while a receiver still reads it, and a
+    //    CTA holding every slice knows every CTA has read its cut-row partials.
+    if (C > 1 && tid == 0) mbar_expect4(sbar, (uint32_t)((d.s_total - ns) * (int)sizeof(X)));
     for (int k = tid; k < n_crow; k += kT4) {
       A a;
       for (int p = 0; p < P; ++p) a.add(ycp[k * P + p]);
@@ -402,10 +422,15 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       if (i < ns)
         for (int c = gl_k; c < C; c += lk) {
           if (c == rank) ss[s0 + i] = sv;
-          else st_remote(mapa4(sa4(&ss[s0 + i]), (uint32_t)c), sv);
+          else st_async(mapa4(sa4(&ss[s0 + i]), (uint32_t)c), sv, mapa4(sa4(sbar), (uint32_t)c));
         }
     }
-    if (C > 1) cluster_barrier(); else __syncthreads();
+    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(sbar, kWait4, (uint32_t)par)) {
+      // a slice never arrived: report it and stop waiting (the results are void)
+      atomicExch(st.status, DEV_TIMEOUT);
+      flag[2] = 1;
+    }
+    __syncthreads();
     // 4. expansion of own and halo rows: v = y - sum over ancestors of F row . s(half)
     const X* yv = yvp + par * yv_half;
     for (int base = 0; base < nv; base += ng_e) {
@@ -540,6 +565,7 @@ Step4D Step4::view() const {
   v.o_ycut = (int)o_ycut;
   v.o_yvp = (int)o_yvp;
   v.o_s = (int)o_s;
+  v.s_total = s_total;
   v.o_v = (int)o_v;
   v.o_contrib = (int)o_contrib;
   v.o_row = (int)o_row;
