@@ -48,7 +48,7 @@ constexpr long long kWait4 = 4000000000LL;   // ~2 s of SM clock
 
 // header fields
 enum { H_P0, H_P1, H_NHALO, H_M0, H_M1, H_LBYTES, H_OLROW, H_NFC, H_OFC, H_OROW, H_OVROW, H_NOUT, H_OOUT, H_NPUSH,
-       H_OPUSH, H_OENDL, H_S0, H_S1, H_LP };
+       H_OPUSH, H_OENDL, H_S0, H_S1, H_LP, H_YIN };   // H_YIN: partials this CTA receives per step
 // own-row record fields (injection)
 enum { R_ELO, R_EHI, R_MON };
 // push kinds: partial of an expansion row (double-buffered by step parity) or of a cut row
@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   using T = typename A::T;
   extern __shared__ __align__(128) unsigned char sm4[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm4);        // prologue copies
-  uint64_t* sbar = reinterpret_cast<uint64_t*>(sm4 + 8);    // slices of s arriving from the other CTAs
-  int* flag = reinterpret_cast<int*>(sm4 + 16);             // [0] own ok, [1] cluster ok, [2] s wait failed
+  uint64_t* sbar = reinterpret_cast<uint64_t*>(sm4 + 8);    // [2] by step parity: slices of s from the other CTAs
+  uint64_t* ybar = reinterpret_cast<uint64_t*>(sm4 + 24);   // [2] by step parity: leaf-stage partials pushed here
+  int* flag = reinterpret_cast<int*>(sm4 + 40);             // [0] own ok, [1] cluster ok, [2] a data wait failed
   const int tid = threadIdx.x;
   const int C = d.C, P = d.P;
   const int rank = C > 1 ? (int)cta_rank4() : 0;
@@ -214,6 +215,9 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   if (tid < 32) {
     if (tid == 0) {
       mbar_init4(sbar);
+      mbar_init4(sbar + 1);
+      mbar_init4(ybar);
+      mbar_init4(ybar + 1);
       mbar_init4(bar);
       mbar_expect4(bar, (uint32_t)hd[H_LBYTES] + (uint32_t)d.img_int_bytes);
       bulk4(sm4 + d.o_img, q.img, (uint32_t)d.img_int_bytes, bar);
@@ -315,9 +319,22 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   X sx = A::zero(), cx = A::zero();
   if (tid < nrow && n_steps > 0) trig_x(q, step0 + 1 - trig_first, sx, cx);
 
+  // Within the step loop no cluster barrier is used. Every remote write is an asynchronous store
+  // counted on the receiver's mbarrier for that step parity, and each CTA waits (bounded) for the
+  // bytes it expects: the leaf-stage partials pushed to it, then the slices of s. Reuse is safe
+  // because every CTA sends its slice of s to every CTA: a CTA that holds all slices of step t
+  // knows every CTA has finished step t - 1's expansion (the double-buffered partials and s of
+  // that parity) and step t's cut-row reads, and the phases of one parity never overlap.
+  const uint32_t y_bytes = (uint32_t)hd[H_YIN] * (uint32_t)sizeof(X);
+  const uint32_t s_bytes = (uint32_t)((d.s_total - ns) * (int)sizeof(X));
   for (int it = 0; it < n_steps; ++it) {
     const int step = step0 + it + 1;
     const int par = it & 1;
+    X* ssp = ss + par * d.s_total;
+    if (C > 1 && tid == 0) {
+      mbar_expect4(ybar + par, y_bytes);
+      mbar_expect4(sbar + par, s_bytes);
+    }
     // 1. element histories from the previous step's voltages (both ends of an element run the
     //    same operations on the same operands, so the two copies stay identical)
 #pragma unroll
@@ -386,15 +403,14 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       const X y = a.getx();
       const uint32_t off = (uint32_t)pr[2] + (pr[3] == P_YV ? (uint32_t)(par * yv_half * (int)sizeof(X)) : 0u);
       if (pr[1] == rank) *reinterpret_cast<X*>(sm4 + off) = y;
-      else st_remote(mapa4(sa4(sm4) + off, (uint32_t)pr[1]), y);
+      else st_async(mapa4(sa4(sm4) + off, (uint32_t)pr[1]), y, mapa4(sa4(ybar + par), (uint32_t)pr[1]));
     }
-    if (C > 1) cluster_barrier(); else __syncthreads();
-    // 3. cut-row values, then this CTA's slice of s = K y_cut, sent to every other CTA by
-    //    asynchronous remote stores that count on the receiver's mbarrier: each CTA waits for its
-    //    own (s_total - ns) values only, instead of a cluster barrier. The next step's first
-    //    cluster barrier keeps a sender from overwriting s while a receiver still reads it, and a
-    //    CTA holding every slice knows every CTA has read its cut-row partials.
-    if (C > 1 && tid == 0) mbar_expect4(sbar, (uint32_t)((d.s_total - ns) * (int)sizeof(X)));
+    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(ybar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
+      atomicExch(st.status, DEV_TIMEOUT);   // partials never arrived: report and stop waiting
+      flag[2] = 1;
+    }
+    __syncthreads();
+    // 3. cut-row values, then this CTA's slice of s = K y_cut, sent to every other CTA
     for (int k = tid; k < n_crow; k += kT4) {
       A a;
       for (int p = 0; p < P; ++p) a.add(ycp[k * P + p]);
@@ -421,11 +437,11 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       const X sv = group_sum<PREC>(a, lk);
       if (i < ns)
         for (int c = gl_k; c < C; c += lk) {
-          if (c == rank) ss[s0 + i] = sv;
-          else st_async(mapa4(sa4(&ss[s0 + i]), (uint32_t)c), sv, mapa4(sa4(sbar), (uint32_t)c));
+          if (c == rank) ssp[s0 + i] = sv;
+          else st_async(mapa4(sa4(&ssp[s0 + i]), (uint32_t)c), sv, mapa4(sa4(sbar + par), (uint32_t)c));
         }
     }
-    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(sbar, kWait4, (uint32_t)par)) {
+    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(sbar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
       // a slice never arrived: report it and stop waiting (the results are void)
       atomicExch(st.status, DEV_TIMEOUT);
       flag[2] = 1;
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
           const int k = an[0];
           const int si = pos < an[2] ? an[3] : an[4];
 #pragma unroll 4
-          for (int e = gl_e; e < k; e += le) a.fma(Fr[(int64_t)e * fs], neg(ss[si + e]));
+          for (int e = gl_e; e < k; e += le) a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
           Fr += (int64_t)an[1] * fs;
         }
       }
@@ -468,6 +484,8 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
     }
     __syncthreads();
   }
+  // no CTA leaves while another may still write into its shared memory
+  if (C > 1) cluster_barrier();
   // write the state back for the next launch and for readers
   for (int r = tid; r < nrow; r += kT4) sim.v_pos[p0 + r] = A::todbl(vloc[r]);
 #pragma unroll
@@ -733,13 +751,13 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
   const size_t tb = 8;   // FP64 or float-float element
   const ImgHeader& Hh = s2.header;
   img_int_bytes = Hh.int_words * 4;
-  size_t off = 32;
+  size_t off = 64;   // mbarriers (prologue, s x 2, partials x 2) and flags
   o_x = off;         off = align16(off + (size_t)std::max(max_rows, 1) * tb);
   o_part = off;      off = align16(off + (size_t)max_part * tb);
   o_ycp = off;       off = align16(off + (size_t)std::max(n_crow * P, 1) * tb);
   o_ycut = off;      off = align16(off + (size_t)std::max(ldk, 2) * tb);
   o_yvp = off;       off = align16(off + (size_t)2 * max_vrows * P * tb);
-  o_s = off;         off = align16(off + (size_t)std::max(s_total, 1) * tb);
+  o_s = off;         off = align16(off + (size_t)2 * std::max(s_total, 1) * tb);   // two step parities
   o_v = off;         off = align16(off + (size_t)max_vrows * tb);
   o_contrib = off;   off = align16(off + (size_t)std::max(max_ends, 1) * tb);
   o_row = off;       off = align16(off + (size_t)max_rows * kRI * 4);
@@ -859,6 +877,8 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     h[H_OOUT] = (int)TB.size();
     TB.insert(TB.end(), outs.begin(), outs.end());
     h[H_NPUSH] = (int)pushes.size() / kPR;
+    for (size_t u = 0; u < pushes.size(); u += kPR)
+      if (pushes[u + 1] != c) H[(size_t)pushes[u + 1] * kHdr + H_YIN]++;
     h[H_OPUSH] = (int)TB.size();
     TB.insert(TB.end(), pushes.begin(), pushes.end());
     // element ends: local indices of the two voltages
