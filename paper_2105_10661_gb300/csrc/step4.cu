@@ -707,6 +707,29 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     cs1[c] = (int)((int64_t)s_total * (c + 1) / n_cta);
     max_slice = std::max(max_slice, cs1[c] - cs0[c]);
   }
+  // K is block-sparse: the rows of s of node q depend only on the cut rows inside q's subtree
+  // (the entries of K outside are exactly zero), so a cut row's partial goes only to the CTAs
+  // whose slice of s holds a node containing it; the slots of the others stay zero.
+  std::vector<std::vector<std::pair<int, int>>> need(n_cta);   // position ranges per CTA
+  {
+    std::vector<int> s_node(std::max(s_total, 1), -1);
+    for (int q = 0; q < (int)t.lo.size(); ++q)
+      if (t.left[q] >= 0)
+        for (int r = 0; r < 2 * st.node_k_h[q]; ++r) s_node[st.node_soff_h[q] + r] = q;
+    for (int c = 0; c < n_cta; ++c) {
+      int last = -2;
+      for (int r = cs0[c]; r < cs1[c]; ++r) {
+        const int q = s_node[r];
+        if (q >= 0 && q != last) need[c].push_back({t.lo[q], t.hi[q]});
+        last = q;
+      }
+    }
+  }
+  auto needs = [&](int c, int ps) {
+    for (auto& rg : need[c])
+      if (ps >= rg.first && ps < rg.second) return true;
+    return false;
+  };
   // ---- sizes
   auto frow = [&](int ps) {
     int64_t e = 0;
@@ -737,7 +760,9 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
       n_out[c] += lb[j];
       for (int r = 0; r < lb[j]; ++r) {
         const int ps = llo[j] + r;
-        n_push[c] += 1 + (int)readers[ps].size() + (crow_of[ps] >= 0 ? n_cta : 0);
+        n_push[c] += 1 + (int)readers[ps].size();
+        if (crow_of[ps] >= 0)
+          for (int cc = 0; cc < n_cta; ++cc) n_push[c] += needs(cc, ps) ? 1 : 0;
       }
     }
     const int pad = (n_out[c] + 31) / 32 * 32;
@@ -866,6 +891,7 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
         }
         if (crow_of[ps] >= 0)
           for (int cc = 0; cc < n_cta; ++cc) {
+            if (!needs(cc, ps)) continue;
             pushes.push_back(o);
             pushes.push_back(cc);
             pushes.push_back((int)(o_ycp + ((size_t)crow_of[ps] * P + cpart[c]) * tb));
