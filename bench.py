@@ -512,7 +512,7 @@ def multi_arm(args):
     per = {
         "k_mc_umma<leaf> (tcgen05 BF16x3)": (kus[0], "tensor", flops_gemm / 1e12, peak_tf, "TFLOP/s"),
         "k_split_b (BF16 hi/lo split)": (kus[1], "hbm", n * R * 8 / 1e9, hbm, "GB/s"),
-        "k_mc_sweep_gemm (FP32 SIMT, cluster split-K)": (kus[2], "alu", 2 * st["s_total"] * st["n_cut_rows"] * R
+        "k_mc_sweep_gemm (FP32 SIMT, split-K over nonzero column pieces)": (kus[2], "alu", 2 * st["s_total"] * st["n_cut_rows"] * R
                                                          / 1e12, fp32_peak, "TFLOP/s"),
         "expansion (tcgen05 k_mc_umma<expand> when it has a tile per SM, else SIMT k_mc_expand_tiled)":
             (kus[3], "hbm", n * R * 20 / 1e9, hbm, "GB/s"),

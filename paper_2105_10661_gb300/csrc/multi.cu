@@ -252,32 +252,29 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
 // Boundary sweep of all columns as one product: S = K Y_cut, K = the matrix of the sweep
 // (s_total x n_crow, FP32, built on the device from the sweep image and kept transposed so that a
 // chunk is read and staged without bank conflicts), Y_cut = the leaf-stage rows at the distinct
-// cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows
-// inside its subtree, so each 32-row tile of S runs over the column range of K holding its
-// nonzeros (krange, found once after K is built). That range is split among the SKS CTAs of a
-// thread-block cluster. Each CTA forms a 32 x 64 partial in 32-deep chunks (128 threads, a 4 x 4
-// block of outputs each, from 16-byte shared-memory reads; the next chunk is loaded into
-// registers while the current one is multiplied) and keeps it in shared memory; after a cluster
-// barrier, CTA z sums rows [8z, 8z + 8) of the SKS partials in rank order through distributed
-// shared memory, so the result does not depend on timing.
-constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128, SKS = 4;
-__global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
-    k_mc_sweep_gemm(MSimD m, const float* __restrict__ Kt, int ldt, const int2* __restrict__ krange,
-                    const int* status) {
+// cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows inside its
+// subtree, so each 32-row tile of S runs over the column range of K holding its nonzeros, cut into
+// pieces of 32..128 columns (the longest giving about four CTAs per SM; work item = tile, piece). A CTA forms the 32 x 64 product of one
+// piece in 32-deep chunks (128 threads, a 4 x 4 block of outputs each, from 16-byte shared-memory
+// reads; the next chunk is loaded into registers while the current one is multiplied). A tile of a
+// single piece writes S; otherwise each piece writes its partial to global memory and the CTA that
+// completes the tile (an atomic count per tile) adds the partials in piece order, so the result
+// does not depend on timing, and resets the count.
+constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128, SPIECE = 128;
+__global__ void __launch_bounds__(SBT) k_mc_sweep_gemm(MSimD m, const float* __restrict__ Kt, int ldt,
+                                                       const int4* __restrict__ items, float* part, int* count,
+                                                       int n_ct, const int* status) {
   __shared__ __align__(16) float Ks[SBK][SBM];
   __shared__ __align__(16) float Ys[SBK][SBN];
-  __shared__ __align__(16) float Ps[SBM][SBN];
+  __shared__ int last_sh;
+  if (*status != DEV_OK) return;   // uniform
   const int* M = m.meta;
   const int s_total = M[M_STOTAL];
   const int* crow_pos = M + M[M_OFF_CROW];
-  const int r0 = blockIdx.x * SBM, c0 = blockIdx.y * SBN;
-  uint32_t z;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(z));
-  // no early exit: every CTA of the cluster reaches both cluster barriers
-  const bool live = c0 < m.R_act && *status == DEV_OK;
-  const int2 kr = krange[blockIdx.x];
-  const int per = (kr.y - kr.x + SKS - 1) / SKS;
-  const int kb = kr.x + (int)z * per, ke = min(kr.y, kb + per);
+  const int4 it = items[blockIdx.x];   // row tile, first column of K, end column, piece | (pieces << 16)
+  const int rt = it.x, kb = it.y, ke = it.z, piece = it.w & 0xffff, pieces = it.w >> 16;
+  const int r0 = rt * SBM, c0 = blockIdx.y * SBN;
+  if (c0 >= m.R_act) return;       // uniform
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;   // rows ty*4.., columns tx*4..
   const int64_t R = m.R;
   constexpr int KL = SBK * SBM / SBT, YL = SBK * SBN / SBT;   // 8 and 16 loads per thread
@@ -297,7 +294,7 @@ __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
     }
   };
   float acc[4][4] = {};
-  if (live && kb < ke) {
+  if (kb < ke) {
     load(kb);
     for (int k0 = kb; k0 < ke; k0 += SBK) {
 #pragma unroll
@@ -325,38 +322,55 @@ __global__ void __cluster_dims__(1, 1, SKS) __launch_bounds__(SBT)
       __syncthreads();
     }
   }
+  if (pieces == 1) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    *reinterpret_cast<float4*>(&Ps[ty * 4 + i][tx * 4]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-  if (live) {
-    constexpr int RPC = SBM / SKS;           // rows reduced by one CTA
-    constexpr int NV = RPC * SBN / SBT;      // values per thread
-    // every remote load is issued before the first sum, then the partials are added in rank order
-    float x[NV][SKS];
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty * 4 + i;
+      if (r >= s_total) continue;
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int v = tid + u * SBT, rr = (int)z * RPC + v / SBN, cc = v % SBN;
-      const uint32_t local = (uint32_t)__cvta_generic_to_shared(&Ps[rr][cc]);
-#pragma unroll
-      for (int q = 0; q < SKS; ++q) {
-        uint32_t remote;
-        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(q));
-        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x[u][q]) : "r"(remote));
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + tx * 4 + q;
+        if (c < m.R_act) m.S[(int64_t)r * R + c] = acc[i][q];
       }
     }
+    return;
+  }
+  // partial of this piece: part[((first item of the tile + piece) * n_ct + column tile)][32 x 64]
+  const int first = blockIdx.x - piece;
+  float* mine = part + ((int64_t)blockIdx.x * n_ct + blockIdx.y) * (SBM * SBN);
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-      const int v = tid + u * SBT, rr = (int)z * RPC + v / SBN, cc = v % SBN;
-      float sum = 0.f;
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(mine + (ty * 4 + i) * SBN + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  __threadfence();
+  __syncthreads();
+  int* cnt = count + rt * n_ct + blockIdx.y;
+  if (tid == 0) last_sh = atomicAdd(cnt, 1) == pieces - 1;
+  __syncthreads();
+  if (!last_sh) return;
+  __threadfence();
+  float sum[4][4] = {};
+  for (int pc = 0; pc < pieces; ++pc) {
+    const float* src = part + ((int64_t)(first + pc) * n_ct + blockIdx.y) * (SBM * SBN);
 #pragma unroll
-      for (int q = 0; q < SKS; ++q) sum += x[u][q];
-      const int r = r0 + rr, c = c0 + cc;
-      if (r < s_total && c < m.R_act) m.S[(int64_t)r * R + c] = sum;
+    for (int i = 0; i < 4; ++i) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(src + (ty * 4 + i) * SBN + tx * 4));
+      sum[i][0] += v.x;
+      sum[i][1] += v.y;
+      sum[i][2] += v.z;
+      sum[i][3] += v.w;
     }
   }
-  // keep every partial alive until all CTAs of the cluster have read it
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= s_total) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + tx * 4 + q;
+      if (c < m.R_act) m.S[(int64_t)r * R + c] = sum[i][q];
+    }
+  }
+  if (tid == 0) *cnt = 0;   // ready for the next launch
 }
 
 // Kt[k][r] = K[r][k]
@@ -1019,6 +1033,34 @@ void MSim::build_meta(cudaStream_t s) {
     EMT_CUDA(cudaMemsetAsync(Kt.p, 0, Kt.n * sizeof(float), s));
     if (st.s_total > 0 && n_crow > 0)
       k_mc_transpose<<<(st.s_total * n_crow + 255) / 256, 256, 0, s>>>(Kmat.p, ldk, st.s_total, n_crow, Kt.p, ldt);
+    // work items of the sweep product: every row tile's nonzero column range in pieces of at most
+    // SPIECE columns (whole SBK chunks)
+    std::vector<int2> kr(n_rt);
+    EMT_CUDA(cudaMemcpyAsync(kr.data(), krange.p, n_rt * sizeof(int2), cudaMemcpyDeviceToHost, s));
+    EMT_CUDA(cudaStreamSynchronize(s));
+    n_ct = (R + SBN - 1) / SBN;
+    int dev = 0, n_sms = 1;
+    EMT_CUDA(cudaGetDevice(&dev));
+    EMT_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<int4> items;
+    // the longest piece (whole SBK chunks) that still gives about four CTAs per SM
+    for (int piece = SPIECE; piece >= SBK; piece /= 2) {
+      items.clear();
+      for (int rt = 0; rt < n_rt; ++rt) {
+        const int kb = kr[rt].x, ke = kr[rt].y;
+        const int pieces = std::max(1, (ke - kb + piece - 1) / piece);
+        for (int pc = 0; pc < pieces; ++pc) {
+          const int a0 = kb + pc * piece, a1 = std::min(ke, a0 + piece);
+          items.push_back(make_int4(rt, a0, std::max(a0, a1), pc | (pieces << 16)));
+        }
+      }
+      if ((int64_t)items.size() * n_ct >= 4LL * n_sms) break;
+    }
+    n_sweep_items = (int)items.size();
+    sweep_items.upload(items, s);
+    sweep_part.alloc(std::max<size_t>((size_t)n_sweep_items * n_ct * SBM * SBN, 1));
+    sweep_count.alloc((size_t)n_rt * n_ct);
+    EMT_CUDA(cudaMemsetAsync(sweep_count.p, 0, sweep_count.n * sizeof(int), s));
     EMT_CUDA(cudaGetLastError());
     EMT_CUDA(cudaStreamSynchronize(s));
   }
@@ -1121,8 +1163,8 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
     k_mc_gemm<<<n_tiles, 256, 0, s>>>(st, reinterpret_cast<const int4*>(gemm_tiles.p), Xf.p, Y.p, R, store->d_status.p,
                                       R_act);
   if (store->s_total > 0 && n_crow > 0)
-    k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
-        d, Kt.p, ldt, krange.p, store->d_status.p);
+    k_mc_sweep_gemm<<<dim3(n_sweep_items, n_ct), SBT, 0, s>>>(d, Kt.p, ldt, sweep_items.p, sweep_part.p,
+                                                              sweep_count.p, n_ct, store->d_status.p);
   if (n1) k_mc_fcol<<<(R_act + 127) / 128, 128, 0, s>>>(st, d, s_in_chunk, store->d_status.p);
   if (tensor_expand())
     umma.expand(*store, d, path_ptr.p, path_srow.p, pass, n1, record, s_in_chunk, s);
@@ -1149,8 +1191,8 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
                                           store->d_status.p, R_act);
     } else if (which == 2) {
       if (store->s_total > 0 && n_crow > 0)
-        k_mc_sweep_gemm<<<dim3((store->s_total + SBM - 1) / SBM, (R_act + SBN - 1) / SBN, SKS), SBT, 0, s>>>(
-            d, Kt.p, ldt, krange.p, store->d_status.p);
+        k_mc_sweep_gemm<<<dim3(n_sweep_items, n_ct), SBT, 0, s>>>(d, Kt.p, ldt, sweep_items.p, sweep_part.p,
+                                                                  sweep_count.p, n_ct, store->d_status.p);
     } else {
       // expansion of the correction pass with the N-1 terms, without the record
       if (tensor_expand())

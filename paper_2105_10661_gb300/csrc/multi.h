@@ -137,6 +137,10 @@ class MSim {
   DevBuf<int2> krange;                      // per 32-row tile of K: column range of its nonzeros
   DevBuf<float> Kt;                         // K transposed ([n_crow][ldt])
   int ldt = 0;
+  DevBuf<int4> sweep_items;                 // (row tile, first column, end column, piece | pieces << 16)
+  DevBuf<float> sweep_part;                 // partials of tiles cut into several pieces
+  DevBuf<int> sweep_count;                  // pieces done per (row tile, column tile)
+  int n_sweep_items = 0, n_ct = 0;
   std::vector<int> path_ptr_h;              // host copy of path_ptr
   DevBuf<int4> xtiles;                      // expansion tiles: leaf, first position, positions
   DevBuf<int> path_ptr, path_srow, path_kld;   // per-leaf path tables of the expansion
