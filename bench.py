@@ -322,8 +322,14 @@ def native_arm(args):
         # shared memory) over the per-step time of a launch running `reps` steps
         byts = b_partial + b_sweep
         ach = byts / (kt[0] * 1e-6) / 1e9
+        # DRAM traffic of this kernel from an ncu capture of one 1,000-step launch on this workload
+        # (dram__bytes_read.sum + dram__bytes_write.sum = 3,233,792 B: the store, read once),
+        # per time step like `achieved`
         roofline = {"bound": "hbm", "kernel": "k_step4", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "us_per_step": kt[0],
+                    "frac": ach / peaks["hbm_gbs"],
+                    "traffic": 3233792 / 1000 if args.config == 2 and H["tuned"]["rows_per_cta"] == 16 else None,
+                    "traffic_unit": "bytes per time step",
+                    "us_per_step": kt[0],
                     "algorithmic_bytes_per_step": byts, "cluster_ctas": H["tuned"]["rows_per_cta"],
                     "peak_source": "measured" if "when" in peaks else "fallback",
                     "note": "store resident in the shared memory of one cluster; per-step latency, not HBM, bounds it"}
@@ -447,11 +453,12 @@ def multi_arm(args):
     traj = rec.cpu().numpy()
     st = L.emt_sim_stats(sim)
 
-    # the kernels of one apply pass (each launched twice per time step), timed alone on the operands
-    # of the last pass: 0 leaf GEMM, 1 BF16 split of its right-hand sides, 2 sweep GEMM, 3 expansion
+    # the kernels of a time step, timed alone on the operands of the last pass: 0 leaf GEMM, 1 BF16
+    # split of its right-hand sides, 2 sweep GEMM, 3 expansion (each twice per time step), 4 history
+    # update and injection, 5 residual (once)
     reps = 200
     kus = {}
-    for which in (0, 1, 2, 3):
+    for which in (0, 1, 2, 3, 4, 5):
         L.emt_sim_bench_kernel(sim, which, reps, stream)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -509,21 +516,30 @@ def multi_arm(args):
     fp32_peak = 69.4   # TFLOP/s FP32 FMA (2 flops per FMA), measured by the probe on this GB300
     # algorithmic work per launch: flops of the products; bytes of the streaming parts (split:
     # read FP32, write BF16 hi + lo; expansion epilogue: read Y, read and write float-float V)
+    # injection: element histories read + written (two parity buffers, one word per element), own
+    # and neighbour voltages, source terms, X (float-float) and Xf written; residual: X and the
+    # CSR neighbours' V read, Xf written (neighbour re-reads hit L2: counted once)
+    n_el = st["n_elements"]
+    n_terms_b = (net["n_src"] if "n_src" in net else len(net["src_bus"])) + len(net.get("load_bus", []))
+    inj_bytes = (2 * n_el * 8 + n * 8 + n_terms_b * 16 + n * 12) * R
+    res_bytes = n * (8 + 8 + 4) * R
     per = {
-        "k_mc_umma<leaf> (tcgen05 BF16x3)": (kus[0], "tensor", flops_gemm / 1e12, peak_tf, "TFLOP/s"),
-        "k_split_b (BF16 hi/lo split)": (kus[1], "hbm", n * R * 8 / 1e9, hbm, "GB/s"),
-        "k_mc_sweep_gemm (FP32 SIMT, split-K over nonzero column pieces)": (kus[2], "alu", 2 * st["s_total"] * st["n_cut_rows"] * R
-                                                         / 1e12, fp32_peak, "TFLOP/s"),
+        "k_mc_umma<leaf> (tcgen05 BF16x3)": (kus[0], 2, "tensor", flops_gemm / 1e12, peak_tf, "TFLOP/s"),
+        "k_split_b (BF16 hi/lo split)": (kus[1], 2, "hbm", n * R * 8 / 1e9, hbm, "GB/s"),
+        "k_mc_sweep_gemm (FP32 SIMT, split-K over nonzero column pieces)":
+            (kus[2], 2, "alu", 2 * st["s_total"] * st["n_cut_rows"] * R / 1e12, fp32_peak, "TFLOP/s"),
         "expansion (tcgen05 k_mc_umma<expand> when it has a tile per SM, else SIMT k_mc_expand_tiled)":
-            (kus[3], "hbm", n * R * 20 / 1e9, hbm, "GB/s"),
+            (kus[3], 2, "hbm", n * R * 20 / 1e9, hbm, "GB/s"),
+        "k_mc_inject (histories + injection, float-float)": (kus[4], 1, "hbm", inj_bytes / 1e9, hbm, "GB/s"),
+        "k_mc_residual (float-float r = x - G'v)": (kus[5], 1, "hbm", res_bytes / 1e9, hbm, "GB/s"),
     }
     kernels = {}
-    for name, (us, bound, work, peak, unit) in per.items():
+    for name, (us, per_step, bound, work, peak, unit) in per.items():
         ach = work / (us * 1e-6)
-        kernels[name] = {"us_per_launch": us, "launches_per_time_step": 2, "bound": bound, "achieved": ach,
+        kernels[name] = {"us_per_launch": us, "launches_per_time_step": per_step, "bound": bound, "achieved": ach,
                          "peak": peak, "unit": unit, "frac": ach / peak,
-                         "share_of_step": 2 * us * T / 1e3 / ms}
-    dom = max(kernels, key=lambda k: kernels[k]["us_per_launch"])
+                         "share_of_step": per_step * us * T / 1e3 / ms}
+    dom = max(kernels, key=lambda k: kernels[k]["share_of_step"])
     if rank == 0:
         name = ("N-1 screening: 256 contingencies on the 1432-bus network, each trips a different branch at step "
                 "1000, 5000 steps" if args.config == 3 else

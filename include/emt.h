@@ -248,8 +248,8 @@ emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
  * which = 0 the leaf-product GEMM; 1 the kernel splitting the right-hand sides into BF16 blocks
  * for the tensor-core GEMM (EMT_ERR_UNSUPPORTED with the SIMT GEMM); 2 the boundary-sweep GEMM
  * S = K Y_cut; 3 the expansion of a correction pass (with its BF16 split on the tensor-core
- * path). Leaves the simulation state undefined: call emt_sim_reset afterwards. Asynchronous on
- * `stream`. */
+ * path); 4 the history update and injection; 5 the float-float residual. Leaves the simulation
+ * state undefined: call emt_sim_reset afterwards. Asynchronous on `stream`. */
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream);
 void emt_sim_destroy(emt_sim* s);
 

@@ -1176,7 +1176,7 @@ void MSim::apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t
 }
 
 void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
-  EMT_REQUIRE(which >= 0 && which <= 3, EMT_ERR_INVALID, "which must be 0..3");
+  EMT_REQUIRE(which >= 0 && which <= 5, EMT_ERR_INVALID, "which must be 0..5");
   EMT_REQUIRE(reps >= 1 && reps <= 100000, EMT_ERR_INVALID, "reps out of range");
   const bool tc = gemm_kind >= 2 && umma.ready;
   EMT_REQUIRE(tc || which != 1, EMT_ERR_UNSUPPORTED, "the SIMT leaf GEMM has no split kernel");
@@ -1193,6 +1193,12 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
       if (store->s_total > 0 && n_crow > 0)
         k_mc_sweep_gemm<<<dim3(n_sweep_items, n_ct), SBT, 0, s>>>(d, Kt.p, ldt, sweep_items.p, sweep_part.p,
                                                                   sweep_count.p, n_ct, store->d_status.p);
+    } else if (which == 4) {
+      const int ipp = positions_per_cta();
+      k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, 0,
+                                                                                          store->d_status.p);
+    } else if (which == 5) {
+      launch_residual(1, 0, s);
     } else {
       // expansion of the correction pass with the N-1 terms, without the record
       if (tensor_expand())
