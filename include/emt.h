@@ -220,7 +220,7 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
  * Multi-column simulations: `kernels` selects the products of the apply (1 = FP32 CUDA cores;
  * 2 = tcgen05 tensor cores with BF16 splits for the leaf stage, and for the expansion when it has
  * a tile for every SM; 3 = tcgen05 for both; 2 and 3 need nrhs a multiple of 4 and >= 32, 2 is
- * the default then); with kernels 2 or 3, rows_per_cta (0, 64, 128 or 256) is the column width of
+ * the default then); with kernels 2 or 3, rows_per_cta (0, 64, 128, 192 or 256) is the column width of
  * a leaf-GEMM tile (0 = chosen from nrhs). Synchronises the device; takes effect on the next
  * emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);

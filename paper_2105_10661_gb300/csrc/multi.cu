@@ -1337,7 +1337,8 @@ bool MSim::tensor_expand() const {
 
 void MSim::set_gemm(int kind, int tn, cudaStream_t s) {
   EMT_REQUIRE(kind >= 1 && kind <= 3, EMT_ERR_INVALID, "kernels must be 1, 2 or 3");
-  EMT_REQUIRE(tn == 0 || tn == 64 || tn == 128 || tn == 256, EMT_ERR_INVALID, "tile width must be 0, 64, 128 or 256");
+  EMT_REQUIRE(tn == 0 || tn == 64 || tn == 128 || tn == 192 || tn == 256, EMT_ERR_INVALID,
+              "tile width must be 0, 64, 128, 192 or 256");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   gemm_kind = kind;

@@ -298,6 +298,8 @@ template <int MODE>
 __global__ void __launch_bounds__(256, 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
+  // tensor-memory columns: a power of two >= 32 holding the TN accumulator columns
+  const uint32_t tcols = TN <= 32 ? 32u : (TN <= 64 ? 64u : (TN <= 128 ? 128u : 256u));
   const uint32_t b_split = (uint32_t)TN * UKC * 2;              // bytes of one B split
   const uint32_t stage_bytes = 2 * A_CHUNK + 2 * b_split;
   const int ns = a.ns;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(256, 2) k_mc_umma(DStore st, UmmaArgs a, ExpAr
     *flag = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su(tslot)), "r"(TN)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su(tslot)), "r"(tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(256, 2) k_mc_umma(DStore st, UmmaArgs a, ExpAr
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
 }  // namespace
@@ -483,20 +485,23 @@ void Umma::build(const Store& st, int R_, cudaStream_t s, int tn) {
   R = R_;
   const Tree& t = st.tree;
   if (tn == 0) {
-    // the widest tile that still gives every SM a tile (fewer, wider tiles re-read the leaf blocks
-    // less), else the narrowest
+    // The busiest SM runs ceil(tiles / SMs) tiles of TN columns each: take the width with the
+    // smallest such makespan, the widest among equals (wider tiles re-read the leaf blocks less).
     int dev = 0, n_sm = 1;
     EMT_CUDA(cudaGetDevice(&dev));
     EMT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     int64_t mtiles = 0;
     for (int j = 0; j < st.n_leaf; ++j)
       mtiles += (t.hi[st.leaf_nodes_h[j]] - t.lo[st.leaf_nodes_h[j]] + UM - 1) / UM;
-    tn = 64;
-    for (int w : {256, 128})
-      if (w <= std::max(R, 64) && mtiles * ((R + w - 1) / w) >= n_sm) {
+    int64_t best = -1;
+    for (int w : {256, 192, 128, 64}) {
+      const int64_t tiles = mtiles * ((R + w - 1) / w);
+      const int64_t span = (tiles + n_sm - 1) / n_sm * w;
+      if (best < 0 || span < best) {
+        best = span;
         tn = w;
-        break;
       }
+    }
   }
   TN = tn;
   std::vector<int> bl, bm, bk;

@@ -396,3 +396,28 @@ def test_bounded_wait_times_out_cleanly_and_context_survives(L):
     h = _build(L, ni, 2, 0, 0, 1)
     X = np.random.default_rng(3).standard_normal((net["n_bus"], 1))
     assert rel_err(_apply(L, h, X), odense.DenseSolver(ni[0].G).solve(X)) <= 1e-10
+
+
+@pytest.mark.parametrize("tile,R", [(192, 200), (256, 128), (192, 64)])
+def test_multi_column_leaf_tile_widths_match_oracle(L, tile, R):
+    # leaf-GEMM tiles 192 or 256 columns wide (tensor memory rounded up to a power of two), with a
+    # ragged or padded last column tile; tensor-core expansion on
+    net = netgen.tiled(2, 4)
+    steps = 30
+    branches = netgen.pick_branches(net, 2, seed=9)
+    trips = {1: (12, int(branches[0])), R - 1: (20, int(branches[1]))}
+    sim = L.emt_sim_create(net, DT, levels=3, nrhs=R)
+    L.emt_sim_tune(sim, tile, 3)
+    for c, (st, e) in trips.items():
+        L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+    mon = np.arange(0, net["n_bus"], 9)
+    L.emt_sim_monitor(sim, mon)
+    rec = torch.zeros(steps, R, len(mon), dtype=torch.float64, device="cuda")
+    L.emt_step(sim, steps, rec)
+    torch.cuda.synchronize()
+    got = rec.cpu().numpy()
+    nw = oemt.Network(net, DT, levels=3)
+    for c in (0, 1, R // 2, R - 1):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
+        assert rel_err(got[:, c, :], ref) <= 1e-8, (c, rel_err(got[:, c, :], ref))
