@@ -220,75 +220,78 @@ __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs
   const int step = m.dyn->step_base + x.s_in_chunk + 1;
   double* rec = x.record ? m.dyn->rec : nullptr;
   const int rec_first = m.dyn->rec_first;
-  // lane: columns c, c + 1 of every row of this warp (TN = 64); four rows' loads in flight at once
-  const int cc = 2 * lane, c = n0 + cc;
-  const int nv = cc < TN ? max(0, min(2, m.R_act - c)) : 0;   // valid columns of this lane
-  float fc0 = 0.f, fc1 = 0.f;
-  if (x.n1 && nv > 0) {
-    fc0 = m.fcol[c];
-    if (nv > 1) fc1 = m.fcol[c + 1];
-  }
-  const int rows = min(UM, b - m0);
-  constexpr int RB = 4;
-  for (int r0 = warp; r0 < rows; r0 += 8 * RB) {
-    float2 y[RB];
-    float4 vo[RB];
-    int mi[RB];
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const int rr = r0 + 8 * u;
-      const int64_t at = (int64_t)(lo + m0 + rr) * R + c;
-      y[u] = make_float2(0.f, 0.f);
-      vo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      mi[u] = -1;
-      if (rr < rows && nv > 0) {
-        if (nv == 2) {
-          y[u] = *reinterpret_cast<const float2*>(m.Y + at);
-          if (x.pass) vo[u] = *reinterpret_cast<const float4*>(m.V + at);
-        } else {
-          y[u].x = m.Y[at];
-          if (x.pass) {
-            const float2 o = m.V[at];
-            vo[u].x = o.x;
-            vo[u].y = o.y;
+  // per 64-column group, lane: columns c, c + 1 of every row of this warp; four rows' loads in
+  // flight at once
+  for (int cg = 0; cg < TN; cg += 64) {
+    const int cc = cg + 2 * lane, c = n0 + cc;
+    const int nv = cc < TN ? max(0, min(2, m.R_act - c)) : 0;   // valid columns of this lane
+    float fc0 = 0.f, fc1 = 0.f;
+    if (x.n1 && nv > 0) {
+      fc0 = m.fcol[c];
+      if (nv > 1) fc1 = m.fcol[c + 1];
+    }
+    const int rows = min(UM, b - m0);
+    constexpr int RB = 4;
+    for (int r0 = warp; r0 < rows; r0 += 8 * RB) {
+      float2 y[RB];
+      float4 vo[RB];
+      int mi[RB];
+  #pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int rr = r0 + 8 * u;
+        const int64_t at = (int64_t)(lo + m0 + rr) * R + c;
+        y[u] = make_float2(0.f, 0.f);
+        vo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mi[u] = -1;
+        if (rr < rows && nv > 0) {
+          if (nv == 2) {
+            y[u] = *reinterpret_cast<const float2*>(m.Y + at);
+            if (x.pass) vo[u] = *reinterpret_cast<const float4*>(m.V + at);
+          } else {
+            y[u].x = m.Y[at];
+            if (x.pass) {
+              const float2 o = m.V[at];
+              vo[u].x = o.x;
+              vo[u].y = o.y;
+            }
+          }
+          if (rec) mi[u] = m.mon_idx[lo + m0 + rr];
+        }
+      }
+  #pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int rr = r0 + 8 * u;
+        if (rr >= rows || nv == 0) continue;
+        const int pos = lo + m0 + rr;
+        const int64_t at = (int64_t)pos * R + c;
+        float v[2] = {y[u].x - T[rr * ldt + cc], y[u].y - T[rr * ldt + cc + 1]};
+        if (fc0 != 0.f) v[0] = fmaf(-fc0, m.Z[at].x, v[0]);
+        if (fc1 != 0.f) v[1] = fmaf(-fc1, m.Z[at + 1].x, v[1]);
+        const float ox[2] = {vo[u].x, vo[u].z}, oy[2] = {vo[u].y, vo[u].w};
+        float2 out[2];
+  #pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (x.pass == 0) {
+            out[q] = make_float2(v[q], 0.f);
+          } else {
+            // float-float V + v (TwoSum, then renormalisation)
+            const float s1 = __fadd_rn(ox[q], v[q]);
+            const float bb = __fsub_rn(s1, ox[q]);
+            const float err = __fadd_rn(__fsub_rn(ox[q], __fsub_rn(s1, bb)), __fsub_rn(v[q], bb));
+            const float lo2 = __fadd_rn(err, oy[q]);
+            const float hi2 = __fadd_rn(s1, lo2);
+            out[q] = make_float2(hi2, __fsub_rn(lo2, __fsub_rn(hi2, s1)));
           }
         }
-        if (rec) mi[u] = m.mon_idx[lo + m0 + rr];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const int rr = r0 + 8 * u;
-      if (rr >= rows || nv == 0) continue;
-      const int pos = lo + m0 + rr;
-      const int64_t at = (int64_t)pos * R + c;
-      float v[2] = {y[u].x - T[rr * ldt + cc], y[u].y - T[rr * ldt + cc + 1]};
-      if (fc0 != 0.f) v[0] = fmaf(-fc0, m.Z[at].x, v[0]);
-      if (fc1 != 0.f) v[1] = fmaf(-fc1, m.Z[at + 1].x, v[1]);
-      const float ox[2] = {vo[u].x, vo[u].z}, oy[2] = {vo[u].y, vo[u].w};
-      float2 out[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (x.pass == 0) {
-          out[q] = make_float2(v[q], 0.f);
-        } else {
-          // float-float V + v (TwoSum, then renormalisation)
-          const float s1 = __fadd_rn(ox[q], v[q]);
-          const float bb = __fsub_rn(s1, ox[q]);
-          const float err = __fadd_rn(__fsub_rn(ox[q], __fsub_rn(s1, bb)), __fsub_rn(v[q], bb));
-          const float lo2 = __fadd_rn(err, oy[q]);
-          const float hi2 = __fadd_rn(s1, lo2);
-          out[q] = make_float2(hi2, __fsub_rn(lo2, __fsub_rn(hi2, s1)));
+        if (nv == 2)
+          *reinterpret_cast<float4*>(m.V + at) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+        else
+          m.V[at] = out[0];
+        if (mi[u] >= 0) {
+          double* rp = rec + ((int64_t)(step - rec_first) * R + c) * m.n_mon + mi[u];
+          rp[0] = (double)out[0].x + (double)out[0].y;
+          if (nv == 2) rp[m.n_mon] = (double)out[1].x + (double)out[1].y;
         }
-      }
-      if (nv == 2)
-        *reinterpret_cast<float4*>(m.V + at) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
-      else
-        m.V[at] = out[0];
-      if (mi[u] >= 0) {
-        double* rp = rec + ((int64_t)(step - rec_first) * R + c) * m.n_mon + mi[u];
-        rp[0] = (double)out[0].x + (double)out[0].y;
-        if (nv == 2) rp[m.n_mon] = (double)out[1].x + (double)out[1].y;
       }
     }
   }
@@ -554,6 +557,9 @@ void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* 
   const Tree& t = st.tree;
   for (int j = 0; j < st.n_leaf; ++j)
     if (pp[j + 1] == pp[j]) return;   // a leaf without ancestor rows: the SIMT expansion serves it
+  // 64-column tiles: the epilogue is bound by its loads and needs the CTAs (128-column tiles, a
+  // quarter of the CTAs fewer setups, measured slower on the 11,456-bus network: 49 against 39 us)
+  xTN = 64;
   std::vector<int> bl, bm, bk;
   std::vector<int4> tiles, bdesc;
   std::vector<int2> tb;
