@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <deque>
 #include <map>
+#include <set>
 #include <tuple>
 
 #include "internal.h"
@@ -103,11 +104,16 @@ std::vector<int> growth_order(const Local& g, int start) {
   return order;
 }
 
+// The choices are those of the plain O(n) scans (a = largest D over unlocked A, b = largest
+// D(b) - 2 w(a, b) over unlocked B, smallest id on ties), found in O(log n): the unlocked vertices
+// of each side sit in an ordered set keyed by (-D, id), whose first element is the scan's answer;
+// for b the only values that differ from D are those of a's neighbours, so b is the better of the
+// best neighbour and the first non-neighbour of the set.
 void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
   const int n = g.n;
-  const long long NEG = -(1LL << 60);
-  std::vector<long long> D(n), vb(n);
+  std::vector<long long> D(n);
   std::vector<char> locked(n);
+  using Key = std::pair<long long, int>;   // (-D, id)
   for (int pass = 0; pass < passes; ++pass) {
     for (int v = 0; v < n; ++v) {
       long long s = 0;
@@ -116,41 +122,62 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
       D[v] = s;
     }
     std::fill(locked.begin(), locked.end(), 0);
-    int nA = 0;
-    for (int v = 0; v < n; ++v) nA += side[v] == 0;
-    int steps = std::min(nA, n - nA);
+    std::set<Key> S[2];
+    for (int v = 0; v < n; ++v) S[side[v]].insert({-D[v], v});
+    const int nA = (int)S[0].size();
+    const int steps = std::min(nA, n - nA);
     std::vector<std::pair<int, int>> pairs;
     std::vector<long long> gains;
+    auto move_d = [&](int x, long long delta) {   // D[x] += delta for an unlocked x
+      S[side[x]].erase({-D[x], x});
+      D[x] += delta;
+      S[side[x]].insert({-D[x], x});
+    };
     for (int st = 0; st < steps; ++st) {
-      int a = -1;
-      long long best = NEG;
-      for (int v = 0; v < n; ++v) {
-        long long val = (side[v] == 0 && !locked[v]) ? D[v] : NEG;
-        if (a < 0 || val > best) { best = val; a = v; }
-      }
-      for (int v = 0; v < n; ++v) vb[v] = (side[v] == 1 && !locked[v]) ? D[v] : NEG;
-      long long wab = 0;
-      for (size_t k = 0; k < g.nbr[a].size(); ++k) {
-        int u = g.nbr[a][k];
-        if (side[u] == 1 && !locked[u]) vb[u] -= 2LL * g.wt[a][k];
-      }
+      const int a = S[0].begin()->second;
+      const std::vector<int>& na = g.nbr[a];
+      // best neighbour of a in unlocked B, by D - 2 w
+      bool have = false;
+      long long bv = 0;
       int b = -1;
-      best = NEG;
-      for (int v = 0; v < n; ++v)
-        if (b < 0 || vb[v] > best) { best = vb[v]; b = v; }
-      for (size_t k = 0; k < g.nbr[a].size(); ++k)
-        if (g.nbr[a][k] == b) wab = g.wt[a][k];
+      long long wab = 0;
+      for (size_t k = 0; k < na.size(); ++k) {
+        const int u = na[k];
+        if (side[u] != 1 || locked[u]) continue;
+        const long long val = D[u] - 2LL * g.wt[a][k];
+        if (!have || val > bv || (val == bv && u < b)) {
+          have = true;
+          bv = val;
+          b = u;
+          wab = g.wt[a][k];
+        }
+      }
+      // first unlocked B vertex that is not a neighbour of a
+      for (const Key& kk : S[1]) {
+        const int u = kk.second;
+        if (std::binary_search(na.begin(), na.end(), u)) continue;
+        const long long val = -kk.first;
+        if (!have || val > bv || (val == bv && u < b)) {
+          have = true;
+          bv = val;
+          b = u;
+          wab = 0;
+        }
+        break;
+      }
       gains.push_back(D[a] + D[b] - 2 * wab);
       pairs.emplace_back(a, b);
+      S[0].erase({-D[a], a});
+      S[1].erase({-D[b], b});
       locked[a] = 1;
       locked[b] = 1;
-      for (size_t k = 0; k < g.nbr[a].size(); ++k) {
-        int x = g.nbr[a][k];
-        if (!locked[x]) D[x] += (side[x] == 0) ? 2LL * g.wt[a][k] : -2LL * g.wt[a][k];
+      for (size_t k = 0; k < na.size(); ++k) {
+        const int x = na[k];
+        if (!locked[x]) move_d(x, (side[x] == 0) ? 2LL * g.wt[a][k] : -2LL * g.wt[a][k]);
       }
       for (size_t k = 0; k < g.nbr[b].size(); ++k) {
-        int y = g.nbr[b][k];
-        if (!locked[y]) D[y] += (side[y] == 1) ? 2LL * g.wt[b][k] : -2LL * g.wt[b][k];
+        const int y = g.nbr[b][k];
+        if (!locked[y]) move_d(y, (side[y] == 1) ? 2LL * g.wt[b][k] : -2LL * g.wt[b][k]);
       }
     }
     if (gains.empty()) break;
