@@ -188,6 +188,13 @@ def rel_err(got, ref):
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)
+def workload_name(cfg: int) -> str:
+    return (("1432-bus network (8 seeded 179-bus tiles), 3-level hierarchy, 20,000 time steps of 50 us, one line "
+             "trip at step 10,000, 16 monitored buses") if cfg == 2 else
+            ("179-bus tile, 2-level hierarchy (4 leaves), 2,000 time steps of 50 us, one line trip at step 1,000, "
+             "16 monitored buses"))
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -207,7 +214,7 @@ def reference_arm(args):
         "unit": "bus-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "1432-bus 8-tile network, 3-level hierarchy, dt=50us, trip at mid-run",
+        "config": {"workload": workload_name(2), "time_steps_per_step": 20000, "buses": net["n_bus"], "mode": "exact",
                    "sample_time_steps": sample},
         "cpu_baseline": {"value": v, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample} time steps of the 1,432-bus workload (trip at step {sample // 2}), "
@@ -370,10 +377,7 @@ def native_arm(args):
             "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
-            "config": {"workload": ("1432-bus network (8 seeded 179-bus tiles), 3-level hierarchy, 20,000 time steps "
-                                    "of 50 us, one line trip at step 10,000, 16 monitored buses") if args.config == 2 else
-                                   ("179-bus tile, 2-level hierarchy (4 leaves), 2,000 time steps of 50 us, one line "
-                                    "trip at step 1,000, 16 monitored buses"),
+            "config": {"workload": workload_name(args.config),
                        "time_steps_per_step": T, "buses": n, "mode": "exact", "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{world}"},
             "accuracy": {k: results[k]["err"] for k in names},
