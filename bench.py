@@ -42,10 +42,11 @@ def parse():
                     help="time steps per bench step (default: the workload's own; smaller values are for "
                          "profiling captures, not bench lines)")
     ap.add_argument("--variants", default="ff64,fp32,fp64")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 41],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7, 41],
                     help="2: single 1,432-bus simulation (default); 3: N-1 screening, 256 contingencies; "
                          "4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of 2,000 requests; "
                          "6: PAPER-mode d_th sweep (approximation error, build and modification cost); "
+                         "7: three-phase 1,432-bus network (4,296 nodes): apply, line trip vs rebuild; "
                          "41: single apply on the 11,456-bus store")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--tune", default="", help="rows_per_cta,kernels: fixed launch shape instead of the autotuner "
@@ -856,6 +857,100 @@ def dth_arm(args):
     }))
 
 
+# ---------------------------------------------------------------- config 7 (three-phase buses)
+def three_phase_arm(args):
+    """Three nodes per bus with mutually coupled RL branches: single-vector apply, and a
+    three-phase line trip as exact rank-1 node updates against rebuilding the store."""
+    import numpy as np
+    import torch
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+    from oracle import companion as ocm, dense as odense, modify as omod
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    net = netgen.three_phase(netgen.tiled(2, 4))
+    nn = 3 * net["n_bus"]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    x = torch.tensor(np.random.default_rng(5).standard_normal(nn), dtype=torch.float64, device=dev)
+
+    def sync_time(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    L.emt_build_hinv_from_network3(net, DT, levels=3)   # warm
+    h, build_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net, DT, levels=3))
+    v = torch.zeros(nn, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        L.emt_apply(h, x, v, stream=stream)
+    ts = []
+    for _ in range(max(args.steps, 10)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.emt_apply(h, x, v, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    apply_ms = float(np.median(ts))
+    # accuracy against a dense solve of the oracle's G (CPU)
+    gr = ocm.three_phase_graph(net, DT)
+    G = ocm.assemble_dense(gr)
+    t0 = time.perf_counter()
+    ref = odense.DenseSolver(G).solve(x.cpu().numpy())
+    cpu_ms = (time.perf_counter() - t0) * 1e3
+    err = rel_err(v.cpu().numpy(), ref)
+    # three-phase trip of the first RL branch: 15 exact rank-1 node updates, negative (cross-phase)
+    # branches first so every intermediate G stays positive definite
+    e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0)
+    a, b = int(net["br_a"][e]), int(net["br_b"][e])
+    Y = ocm.coupled_rl_admittance(float(net["R"][e]), float(net["L"][e]), float(net["L_mut"][e]), DT)
+    ups = ([(3 * a + p, 3 * b + q, Y[p, q]) for p in range(3) for q in range(3) if p != q]
+           + [(3 * z + p, 3 * z + q, -Y[p, q]) for z in (a, b) for p in range(3) for q in range(p + 1, 3)]
+           + [(3 * a + p, 3 * b + p, Y[p, p]) for p in range(3)])
+
+    v_before = v.cpu().numpy()
+
+    def trip():
+        for xx, yy, g in ups:
+            L.emt_modify_branch(h, xx, yy, -g, stream=stream)
+    _, trip_ms = sync_time(trip)
+    keep = [k for k in range(len(net["br_a"])) if k != e]
+    net_t = dict(net)
+    for k in ("br_a", "br_b", "kind", "R", "L", "C", "L_mut"):
+        net_t[k] = np.asarray(net[k])[keep]
+    _, rebuild_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net_t, DT, levels=3))
+    for xx, yy, g in ups:
+        G = omod.modified_G(G, xx, yy, -g)
+    L.emt_apply(h, x, v, stream=stream)
+    torch.cuda.synchronize()
+    err_trip = rel_err(v.cpu().numpy(), odense.DenseSolver(G).solve(x.cpu().numpy()))
+    change = rel_err(v.cpu().numpy(), v_before)
+    print(json.dumps({
+        "metric": "three-phase node solves per second (v = G^-1 i, one vector)", "value": nn / (apply_ms * 1e-3),
+        "unit": "node-solves/s", "n_gpus": 1, "steps": max(args.steps, 10), "warmup": args.warmup,
+        "ms_per_step": apply_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "1432-bus 8-tile network in three phases (4,296 nodes, mutual inductance U[0.2, 0.4] "
+                               "of self on every RL branch), 3-level hierarchy, EXACT FP64 store, L2 flushed before "
+                               "every apply", "nodes": nn},
+        "accuracy": {"apply": err, "after_three_phase_trip": err_trip, "solution_change_by_trip": change},
+        "build_ms": build_ms, "three_phase_trip": {"node_updates": len(ups), "ms": trip_ms, "rebuild_ms": rebuild_ms,
+                                                   "time_saved": 1.0 - trip_ms / rebuild_ms},
+        "cpu_baseline": {"value": nn / (cpu_ms * 1e-3), "unit": "node-solves/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": "dense Cholesky solve of the same G and vector (factorisation "
+                                                     "included)"},
+    }))
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -871,6 +966,8 @@ def main():
         apply_arm(args)
     elif args.config == 6:
         dth_arm(args)
+    elif args.config == 7:
+        three_phase_arm(args)
     else:
         native_arm(args)
 

@@ -57,8 +57,10 @@ typedef struct emt_hinv emt_hinv;
 typedef struct emt_sim emt_sim;
 
 /* Conductance graph (Sec. II): G = sum over branches of g_e u_e u_e^T with u_e = e_from - e_to,
- * or u_e = e_from for a branch to ground (to = -1). g_e > 0. Bus-to-bus branches are the edges
- * the partition sees; their index in this list is their branch id. */
+ * or u_e = e_from for a branch to ground (to = -1). g_e != 0: negative values carry mutual
+ * couplings (three-phase branches); G must be positive definite (EMT_ERR_SINGULAR otherwise).
+ * Bus-to-bus branches are the edges the partition sees; their index in this list is their
+ * branch id. */
 typedef struct {
   int32_t n_bus;
   int32_t n_branch;
@@ -119,7 +121,9 @@ emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nr
  * (Sherman-Morrison at every node on the paths from the touched leaves to the root, FP64
  * denominators); PAPER stores get Algorithm 2 (re-invert touched leaves, recompute the
  * factors on the paths to the lowest common ancestor). If a denominator is not positive the
- * store is left unchanged and EMT_ERR_SINGULAR is returned. Synchronises `stream`. */
+ * store is left unchanged and EMT_ERR_SINGULAR is returned. The packed copies the apply kernels
+ * read are refreshed by the next emt_apply, once for any number of modifications in between.
+ * Synchronises `stream`. */
 emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double delta_g,
                              void* stream);
 
@@ -180,6 +184,16 @@ typedef struct {
  * (Sec. II). Series branch ids are preserved. Synchronises `stream`. */
 emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const emt_hinv_opts* opts, void* stream,
                                        emt_hinv** out);
+/* The same for a three-phase network (the paper counts three nodes per bus): bus i carries nodes
+ * 3i, 3i + 1, 3i + 2. An RL series branch has R and self inductance L per phase and mutual
+ * inductance L_mut[e] (0 <= L_mut[e] < L[e]; host array of n_branch, ignored for RC branches)
+ * between any two phases; its coupled companion admittance Y = (R I + (2/dt) L3)^-1 enters G as
+ * Y (x) (e_a - e_b)(e_a - e_b)^T, written as node branches (phase-to-phase branches of negative
+ * conductance between the ends, positive ones within each end's three nodes). RC branches, shunt
+ * capacitors and sources act on each phase alone. The store and all calls on it work on the
+ * 3 n_bus nodes (node = 3 bus + phase); emt_modify_branch takes nodes. Synchronises `stream`. */
+emt_status emt_build_hinv_from_network3(const emt_network* net, const double* L_mut, double dt,
+                                        const emt_hinv_opts* opts, void* stream, emt_hinv** out);
 
 /* Event kinds for emt_sim_schedule. TRIP: target = branch id (opens before the step is
  * solved; current and history zeroed). FAULT_ON: target = bus, value = R_f (ohm). FAULT_OFF:

@@ -163,6 +163,18 @@ def add_loads(net: dict, frac: float = 0.3, seed: int = 13) -> dict:
     return out
 
 
+def three_phase(net: dict, frac_lo: float = 0.2, frac_hi: float = 0.4, seed: int = 23) -> dict:
+    """The same network with three phases per bus: every RL series branch gets a mutual
+    inductance between its phases of U[frac_lo, frac_hi] times its self inductance (RC branches:
+    none). Element data only; the store works on 3 nodes per bus."""
+    rng = np.random.default_rng(seed)
+    out = dict(net)
+    frac = rng.uniform(frac_lo, frac_hi, len(net["br_a"]))
+    out["L_mut"] = np.where(np.asarray(net["kind"]) == 0, frac * np.asarray(net["L"], float), 0.0)
+    out["phases"] = 3
+    return out
+
+
 def scenario_scales(net: dict, nrhs: int, sigma: float = 0.05, seed: int = 13) -> tuple:
     """Per-column multiplicative perturbations (1 + eps), eps ~ N(0, sigma),
     for every source amplitude and every load amplitude."""

@@ -71,6 +71,50 @@ def graph(net: dict, dt: float) -> dict:
                 n_series=el["n_series"])
 
 
+def coupled_rl_admittance(R: float, L: float, L_mut: float, dt: float) -> np.ndarray:
+    """Trapezoidal companion admittance of a three-phase RL branch with self inductance L and
+    mutual inductance L_mut between any two phases: i = Y v_e + I_h with
+    Y = (R I + (2/dt) L3)^-1, L3 = L I + L_mut (J - I) (the single-phase rule of Sec. II applied
+    to the coupled inductance matrix)."""
+    L3 = L * np.eye(3) + L_mut * (np.ones((3, 3)) - np.eye(3))
+    return np.linalg.inv(R * np.eye(3) + (2.0 / dt) * L3)
+
+
+def three_phase_graph(net: dict, dt: float) -> dict:
+    """Conductance graph of a three-phase network, node = 3 bus + phase. An RL branch's term
+    Y (x) (e_a - e_b)(e_a - e_b)^T is split into node branches: a_p-b_p with Y_pp, a_p-b_q
+    (p != q) with Y_pq, a_p-a_q and b_p-b_q (p < q) with -Y_pq (zero terms dropped). RC
+    branches, shunt capacitors and sources act on each phase alone."""
+    frm, to, g = [], [], []
+    n = net["n_bus"]
+    for e in range(len(net["br_a"])):
+        a, b = int(net["br_a"][e]), int(net["br_b"][e])
+        if net["kind"][e] == KIND_RL:
+            Y = coupled_rl_admittance(float(net["R"][e]), float(net["L"][e]), float(net["L_mut"][e]), dt)
+            for p in range(3):
+                frm.append(3 * a + p); to.append(3 * b + p); g.append(Y[p, p])
+            for p in range(3):
+                for q in range(3):
+                    if p != q and Y[p, q] != 0.0:
+                        frm.append(3 * a + p); to.append(3 * b + q); g.append(Y[p, q])
+            for p in range(3):
+                for q in range(p + 1, 3):
+                    if Y[p, q] != 0.0:
+                        frm.append(3 * a + p); to.append(3 * a + q); g.append(-Y[p, q])
+                        frm.append(3 * b + p); to.append(3 * b + q); g.append(-Y[p, q])
+        else:
+            gc = 1.0 / (float(net["R"][e]) + dt / (2.0 * float(net["C"][e])))
+            for p in range(3):
+                frm.append(3 * a + p); to.append(3 * b + p); g.append(gc)
+    for i in range(n):
+        for p in range(3):
+            frm.append(3 * i + p); to.append(-1); g.append(2.0 * float(net["shunt_C"][i]) / dt)
+    for k in range(len(net["src_bus"])):
+        for p in range(3):
+            frm.append(3 * int(net["src_bus"][k]) + p); to.append(-1); g.append(1.0 / float(net["src_Rs"][k]))
+    return dict(n_bus=3 * n, frm=np.asarray(frm, np.int64), to=np.asarray(to, np.int64), g=np.asarray(g, float))
+
+
 def assemble_dense(gr: dict) -> np.ndarray:
     """G = sum over branches of g u u^T, u = e_a - e_b (or e_a to ground)."""
     n = gr["n_bus"]

@@ -111,6 +111,8 @@ def _load():
         "emt_selftest_bounded_wait": (C.c_int, [C.c_int32, vp]),
         "emt_build_hinv_from_network": (C.c_int, [C.POINTER(EmtNetwork), C.c_double, C.POINTER(EmtHinvOpts), vp,
                                                   C.POINTER(vp)]),
+        "emt_build_hinv_from_network3": (C.c_int, [C.POINTER(EmtNetwork), _f64p, C.c_double, C.POINTER(EmtHinvOpts),
+                                                   vp, C.POINTER(vp)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -127,7 +129,8 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
             "emt_server_add_network", "emt_server_submit", "emt_server_submit_network", "emt_server_run",
             "emt_server_result", "emt_server_stats",
-            "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network")
+            "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network",
+            "emt_build_hinv_from_network3")
 
 
 def _check(code):
@@ -429,3 +432,15 @@ def emt_build_hinv_from_network(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_E
     h = C.c_void_p()
     _check(lib.emt_build_hinv_from_network(C.byref(nw), float(dt), C.byref(o), _stream(stream), C.byref(h)))
     return HInv(h.value, int(net["n_bus"]))
+
+
+def emt_build_hinv_from_network3(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64,
+                                 stream=None):
+    """Store of a three-phase network (3 nodes per bus; `net["L_mut"]` mutual inductances)."""
+    nw, keep = make_network(net)
+    lm = _f64(net["L_mut"])
+    o = make_opts(levels, d_th, mode, precision)
+    h = C.c_void_p()
+    _check(lib.emt_build_hinv_from_network3(C.byref(nw), _p(lm, _f64p), float(dt), C.byref(o), _stream(stream),
+                                            C.byref(h)))
+    return HInv(h.value, 3 * int(net["n_bus"]))

@@ -18,6 +18,8 @@ void apply_noalloc(const Store& st, const double* i_dev, double* v_dev, cudaStre
 int selftest_wait(int limit_us, cudaStream_t s);
 void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
                    std::vector<double>& gv);
+void network_graph3(const emt_network* net, const double* L_mut, double dt, std::vector<int32_t>& gf,
+                    std::vector<int32_t>& gt, std::vector<double>& gv);
 }  // namespace emt
 
 struct emt_tree {
@@ -28,6 +30,7 @@ struct emt_hinv {
   std::unique_ptr<emt::Store> st;
   emt::FusedPlan plan;
   bool has_plan = false;
+  bool plan_stale = false;   // the store changed since the plan's values were taken
   emt::DevBuf<double> vpos, rpos;
   emt_tree tree;
 };
@@ -147,6 +150,19 @@ emt_status emt_build_hinv(const emt_graph* graph, const emt_hinv_opts* opts, voi
   });
 }
 
+emt_status emt_build_hinv_from_network3(const emt_network* net, const double* L_mut, double dt,
+                                        const emt_hinv_opts* opts, void* stream, emt_hinv** out) {
+  std::vector<int32_t> gf, gt;
+  std::vector<double> gv;
+  emt_status r = guard([&] {
+    EMT_REQUIRE(net && net->n_bus <= (1 << 29), EMT_ERR_INVALID, "null or too large network");
+    emt::network_graph3(net, L_mut, dt, gf, gt, gv);
+  });
+  if (r != EMT_OK) return r;
+  emt_graph g{3 * net->n_bus, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
+  return emt_build_hinv(&g, opts, stream, out);
+}
+
 emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const emt_hinv_opts* opts, void* stream,
                                        emt_hinv** out) {
   std::vector<int32_t> gf, gt;
@@ -171,7 +187,10 @@ emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nr
     if (!h->has_plan) {
       emt::make_plan(*h->st, 0, h->plan, s);
       h->has_plan = true;
+    } else if (h->plan_stale) {
+      emt::refresh_plan_values(*h->st, h->plan, s);   // once for any number of modifications
     }
+    h->plan_stale = false;
     emt::apply_vectors(*h->st, h->plan, h->vpos, h->rpos, i_dev, v_dev, nrhs, ld, max_refine, s);
   });
 }
@@ -189,7 +208,7 @@ emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double d
     EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
     cudaStream_t s = as_stream(stream);
     h->st->modify(bus_a, bus_b, delta_g, s);
-    if (h->has_plan) emt::refresh_plan_values(*h->st, h->plan, s);
+    h->plan_stale = h->has_plan;   // the apply plan's copies of the values are refreshed by the next apply
     EMT_CUDA(cudaStreamSynchronize(s));
   });
 }

@@ -23,7 +23,8 @@ namespace emt {
 
 namespace {
 
-constexpr int kMaxCoreDim = 160;   // 2k limit for the in-shared-memory core inversion
+constexpr int kMaxCoreDim = 160;    // 2k limit for the in-shared-memory core inversion
+constexpr int kMaxCoreDimWs = 4096; // 2k limit with the global-memory workspace
 constexpr int kPanelCols = 32;     // column chunk of the level sweep
 
 __device__ __forceinline__ int anc_at_depth(const DStore& st, int q, int d) {
@@ -266,11 +267,16 @@ __global__ void k_leaf_dense(DStore st, const double* __restrict__ X, double* __
 }
 
 // ------------------------------------------------------------------ node cores
-__global__ void k_core(DStore st, const int* nodes, int mode) {
-  extern __shared__ double A[];
-  __shared__ int ipiv[kMaxCoreDim];
+// ws: null (the core is inverted in shared memory), or a workspace of ws_stride doubles and
+// ws_stride / m2max pivots per CTA in global memory for cores larger than kMaxCoreDim.
+__global__ void k_core(DStore st, const int* nodes, int mode, double* ws, int* ws_piv, int64_t ws_stride,
+                       int m2max) {
+  extern __shared__ double A_sh[];
+  __shared__ int ipiv_sh[kMaxCoreDim];
   __shared__ int prow;
   __shared__ double pval;
+  double* A = ws ? ws + blockIdx.x * ws_stride : A_sh;
+  int* ipiv = ws ? ws_piv + (int64_t)blockIdx.x * m2max : ipiv_sh;
   const int p = nodes[blockIdx.x];
   const int k = st.node_k[p];
   const int m2 = 2 * k;
@@ -533,7 +539,9 @@ Store::Store(const emt_graph* g, const emt_hinv_opts* o, cudaStream_t s) {
     EMT_REQUIRE(g->from[e] >= 0 && g->from[e] < g->n_bus && g->to[e] >= -1 && g->to[e] < g->n_bus,
                 EMT_ERR_INVALID, "branch endpoint out of range");
     EMT_REQUIRE(g->from[e] != g->to[e], EMT_ERR_INVALID, "self-loop branch");
-    EMT_REQUIRE(std::isfinite(g->g[e]) && g->g[e] > 0.0, EMT_ERR_INVALID, "branch conductance must be > 0");
+    // negative values carry mutual couplings (three-phase branches); G must stay positive definite,
+    // which the leaf factorisations check
+    EMT_REQUIRE(std::isfinite(g->g[e]) && g->g[e] != 0.0, EMT_ERR_INVALID, "branch conductance must be nonzero");
   }
   mode = o->mode;
   precision = o->precision;
@@ -618,8 +626,8 @@ void Store::setup_layout(cudaStream_t s) {
   for (int d = t.max_depth; d >= 0; --d) {     // deepest level first: each depth contiguous
     for (int p : by_depth[d]) {
       const int k = t.cut_ptr[p + 1] - t.cut_ptr[p];
-      EMT_REQUIRE(2 * k <= kMaxCoreDim, EMT_ERR_UNSUPPORTED,
-                  "a tree node cuts more than 80 branches; use more levels or a smaller d_th");
+      EMT_REQUIRE(2 * k <= kMaxCoreDimWs, EMT_ERR_UNSUPPORTED,
+                  "a tree node cuts more than 2048 branches; use more levels or a smaller d_th");
       node_k_h[p] = k;
       node_kld_h[p] = (k + 3) / 4 * 4;   // 16-byte rows in every precision
       node_foff_h[p] = foff;
@@ -840,9 +848,19 @@ void Store::form_cores(const std::vector<int>& nodes, cudaStream_t s) {
   for (int p : nodes) kb = std::max(kb, node_k_h[p]);
   if (kb == 0) return;
   const int nl = upload_list(nodes, s);
-  const size_t sh = (size_t)4 * kb * kb * sizeof(double);
-  if (sh > 48 * 1024) EMT_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-  k_core<<<nl, 256, sh, s>>>(view(), d_list.p, mode);
+  if (2 * kb <= kMaxCoreDim) {
+    const size_t sh = (size_t)4 * kb * kb * sizeof(double);
+    if (sh > 48 * 1024) EMT_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_core<<<nl, 256, sh, s>>>(view(), d_list.p, mode, nullptr, nullptr, 0, 0);
+  } else {
+    // larger cores (many cut branches, e.g. three-phase networks): the same inversion in a
+    // global-memory workspace
+    const int m2 = 2 * kb;
+    const int64_t stride = (int64_t)m2 * m2;
+    if (core_ws.n < (size_t)(nl * stride)) core_ws.alloc((size_t)nl * stride);
+    if (core_piv.n < (size_t)nl * m2) core_piv.alloc((size_t)nl * m2);
+    k_core<<<nl, 256, 0, s>>>(view(), d_list.p, mode, core_ws.p, core_piv.p, stride, m2);
+  }
   EMT_CUDA(cudaGetLastError());
 }
 

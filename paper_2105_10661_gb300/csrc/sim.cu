@@ -267,6 +267,66 @@ void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, 
   }
 }
 
+// Conductance graph of a three-phase network (the paper counts three nodes per bus): bus i
+// carries nodes 3i, 3i + 1, 3i + 2 (phases a, b, c). An RL series branch couples its phases:
+// resistance R and self inductance L per phase, mutual inductance L_mut between any two. Its
+// trapezoidal companion admittance is Y = (R I + (2/dt) L3)^-1 with L3 = L I + L_mut (J - I), a
+// matrix (alpha - beta) I + beta J (alpha = R + 2L/dt, beta = 2 L_mut/dt) whose inverse has
+// diagonal (alpha + beta) / ((alpha - beta)(alpha + 2 beta)) and off-diagonal
+// -beta / ((alpha - beta)(alpha + 2 beta)). The branch's term Y (x) (e_a - e_b)(e_a - e_b)^T is
+// written exactly as node branches: a_p-b_p with Y_pp, a_p-b_q (p != q) with Y_pq (negative),
+// a_p-a_q and b_p-b_q (p < q) with -Y_pq; none when L_mut = 0 (three decoupled phases). RC
+// branches, shunt capacitors and sources act on each phase alone.
+void network_graph3(const emt_network* net, const double* L_mut, double dt, std::vector<int32_t>& gf,
+                    std::vector<int32_t>& gt, std::vector<double>& gv) {
+  EMT_REQUIRE(net && L_mut && dt > 0, EMT_ERR_INVALID, "null network, null mutual inductances or bad dt");
+  gf.clear();
+  gt.clear();
+  gv.clear();
+  auto add = [&](int x, int y, double g) {
+    gf.push_back(x);
+    gt.push_back(y);
+    gv.push_back(g);
+  };
+  for (int e = 0; e < net->n_branch; ++e) {
+    const int a = net->from[e], b = net->to[e];
+    EMT_REQUIRE(a >= 0 && a < net->n_bus && b >= 0 && b < net->n_bus && a != b, EMT_ERR_INVALID,
+                "series branch endpoints");
+    if (net->kind[e] == EMT_KIND_RL) {
+      EMT_REQUIRE(L_mut[e] >= 0 && L_mut[e] < net->L[e], EMT_ERR_INVALID, "mutual inductance must be in [0, L)");
+      const double al = net->R[e] + 2.0 * net->L[e] / dt, be = 2.0 * L_mut[e] / dt;
+      const double den = (al - be) * (al + 2.0 * be);
+      const double yd = (al + be) / den, yo = -be / den;
+      EMT_REQUIRE(std::isfinite(yd) && yd > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
+      for (int p = 0; p < 3; ++p) add(3 * a + p, 3 * b + p, yd);
+      if (yo != 0.0) {
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q)
+            if (p != q) add(3 * a + p, 3 * b + q, yo);
+        for (int p = 0; p < 3; ++p)
+          for (int q = p + 1; q < 3; ++q) {
+            add(3 * a + p, 3 * a + q, -yo);
+            add(3 * b + p, 3 * b + q, -yo);
+          }
+      }
+    } else {
+      EMT_REQUIRE(net->kind[e] == EMT_KIND_RC && net->C[e] > 0, EMT_ERR_INVALID, "bad RC branch");
+      const double g = 1.0 / (net->R[e] + dt / (2.0 * net->C[e]));
+      EMT_REQUIRE(std::isfinite(g) && g > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
+      for (int p = 0; p < 3; ++p) add(3 * a + p, 3 * b + p, g);
+    }
+  }
+  if (net->shunt_C)
+    for (int i = 0; i < net->n_bus; ++i)
+      if (net->shunt_C[i] > 0)
+        for (int p = 0; p < 3; ++p) add(3 * i + p, -1, 2.0 * net->shunt_C[i] / dt);
+  for (int k = 0; k < net->n_src; ++k) {
+    EMT_REQUIRE(net->src_bus[k] >= 0 && net->src_bus[k] < net->n_bus && net->src_Rs[k] > 0, EMT_ERR_INVALID,
+                "bad source");
+    for (int p = 0; p < 3; ++p) add(3 * net->src_bus[k] + p, -1, 1.0 / net->src_Rs[k]);
+  }
+}
+
 SimD Sim::view() const {
   SimD d;
   d.n = n;

@@ -114,6 +114,8 @@ class Store {
   DevBuf<double> L64, F64, C64, W64;
   DevBuf<float2> Lff, Fff, Cff;
   DevBuf<float> L32, F32, C32;
+  DevBuf<double> core_ws;   // workspace of core inversions too large for shared memory
+  DevBuf<int> core_piv;
   DevBuf<int> d_csr_ptr, d_csr_col;
   DevBuf<double> d_csr_val;
   DevBuf<int> d_status;

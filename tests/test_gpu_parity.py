@@ -421,3 +421,56 @@ def test_multi_column_leaf_tile_widths_match_oracle(L, tile, R):
         ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
         ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
         assert rel_err(got[:, c, :], ref) <= 1e-8, (c, rel_err(got[:, c, :], ref))
+
+
+# ---------------------------------------------------------------- three-phase buses
+def _three_phase(levels=3):
+    from oracle import companion as ocm
+    net = netgen.three_phase(netgen.tiled(1, 2))
+    gr = ocm.three_phase_graph(net, DT)
+    return net, gr, ocm.assemble_dense(gr)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_three_phase_store_matches_dense_solve(L, prec):
+    # 358 buses, 1,074 nodes: mutual couplings enter as negative node branches
+    net, gr, G = _three_phase()
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, precision=prec)
+    _PREC[id(h)] = prec
+    X = np.random.default_rng(21).standard_normal((gr["n_bus"], 3))
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
+
+
+def test_three_phase_paper_store_matches_algorithm1(L):
+    from oracle import partition as op
+    net, gr, G = _three_phase()
+    ser = gr["to"] >= 0
+    tree = op.build_tree(gr["n_bus"], gr["frm"][ser], gr["to"][ser], 3)
+    H = ohinv.HInv(G, tree, gr["g"][ser], ohinv.PAPER)
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, mode=1)
+    X = np.random.default_rng(22).standard_normal((gr["n_bus"], 2))
+    assert rel_err(_apply(L, h, X), H.apply(X)) <= 1e-10
+
+
+def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L):
+    # a three-phase line trip removes Y (x) (e_a - e_b)(e_a - e_b)^T: fifteen exact rank-1 updates,
+    # negative (cross-phase) branches first so that every intermediate G stays positive definite;
+    # then a fault from one phase to ground
+    from oracle import companion as ocm
+    net, gr, G = _three_phase()
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3)
+    e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0)
+    a, b = int(net["br_a"][e]), int(net["br_b"][e])
+    Y = ocm.coupled_rl_admittance(float(net["R"][e]), float(net["L"][e]), float(net["L_mut"][e]), DT)
+    cross = [(3 * a + p, 3 * b + q, Y[p, q]) for p in range(3) for q in range(3) if p != q]
+    within = [(3 * x + p, 3 * x + q, -Y[p, q]) for x in (a, b) for p in range(3) for q in range(p + 1, 3)]
+    self_ = [(3 * a + p, 3 * b + p, Y[p, p]) for p in range(3)]
+    X = np.random.default_rng(23).standard_normal((gr["n_bus"], 2))
+    for x, y, g in cross + within + self_:
+        L.emt_modify_branch(h, x, y, -g)
+        G = omod.modified_G(G, x, y, -g)
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= 1e-10
+    node = 3 * int(net["br_a"][0]) + 1
+    L.emt_modify_branch(h, node, -1, 0.1)
+    G = omod.modified_G(G, node, -1, 0.1)
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= 1e-10

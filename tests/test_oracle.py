@@ -480,3 +480,69 @@ def test_stepping_solvers_agree_with_trip_and_fault():
     assert sd["cur"][e] == 0.0 and sd["Ih"][e] == 0.0
     p, _ = emt.simulate(nw, 80, ev, solver="paper")
     assert np.all(np.isfinite(p))
+
+
+# ---------------------------------------------------------------- three-phase buses (3 nodes per bus)
+def test_coupled_rl_admittance_closed_form():
+    # (R I + (2/dt)(L I + M (J - I)))^-1 = (alpha - beta)^-1 (I - beta / (alpha + 2 beta) J),
+    # alpha = R + 2L/dt, beta = 2M/dt (eigenvalues alpha + 2 beta on (1,1,1), alpha - beta twice);
+    # M = 0 gives the single-phase companion conductance on the diagonal
+    R, L, M, dt = 1.3, 0.021, 0.006, 50e-6
+    al, be = R + 2 * L / dt, 2 * M / dt
+    J = np.ones((3, 3))
+    closed = (np.eye(3) - be / (al + 2 * be) * J) / (al - be)
+    assert np.allclose(cm.coupled_rl_admittance(R, L, M, dt), closed, rtol=1e-13, atol=0)
+    assert np.allclose(cm.coupled_rl_admittance(R, L, 0.0, dt), np.eye(3) / al, rtol=1e-14, atol=0)
+    Y = cm.coupled_rl_admittance(R, L, M, dt)
+    assert np.all(np.linalg.eigvalsh(Y) > 0) and np.all(Y[~np.eye(3, dtype=bool)] < 0)
+
+
+def _block_assembly(net, dt):
+    # the same G from 3 x 3 blocks: Y at (a, a) and (b, b), -Y at (a, b) and (b, a)
+    n = net["n_bus"]
+    G = np.zeros((3 * n, 3 * n))
+    for e in range(len(net["br_a"])):
+        a, b = int(net["br_a"][e]), int(net["br_b"][e])
+        if net["kind"][e] == 0:
+            Y = cm.coupled_rl_admittance(float(net["R"][e]), float(net["L"][e]), float(net["L_mut"][e]), dt)
+        else:
+            Y = np.eye(3) / (float(net["R"][e]) + dt / (2 * float(net["C"][e])))
+        for (x, y, s) in ((a, a, 1.0), (b, b, 1.0), (a, b, -1.0), (b, a, -1.0)):
+            G[3 * x:3 * x + 3, 3 * y:3 * y + 3] += s * Y
+    for i in range(n):
+        G[3 * i:3 * i + 3, 3 * i:3 * i + 3] += np.eye(3) * 2 * float(net["shunt_C"][i]) / dt
+    for k in range(len(net["src_bus"])):
+        i = int(net["src_bus"][k])
+        G[3 * i:3 * i + 3, 3 * i:3 * i + 3] += np.eye(3) / float(net["src_Rs"][k])
+    return G
+
+
+def test_three_phase_node_branches_equal_block_assembly():
+    net = netgen.three_phase(netgen.small_network(13, 77))
+    gr = cm.three_phase_graph(net, DT)
+    G = cm.assemble_dense(gr)
+    Gb = _block_assembly(net, DT)
+    assert np.allclose(G, Gb, rtol=0, atol=1e-12 * np.abs(Gb).max())
+    assert np.allclose(G, G.T) and np.linalg.eigvalsh(G).min() > 0
+    assert (gr["g"] < 0).any()   # the mutual couplings appear as negative node branches
+
+
+def test_three_phase_without_mutual_is_three_decoupled_copies():
+    net = netgen.small_network(13, 77)
+    net3 = netgen.three_phase(net)
+    net3["L_mut"] = np.zeros(len(net["br_a"]))
+    G3 = cm.assemble_dense(cm.three_phase_graph(net3, DT))
+    G1 = cm.assemble_dense(cm.graph(net, DT))
+    assert np.allclose(G3, np.kron(G1, np.eye(3)), rtol=1e-14, atol=0)
+
+
+def test_three_phase_exact_store_equals_dense_inverse():
+    # the hierarchical store holds the node graph with its negative (mutual) branches exactly
+    net = netgen.three_phase(netgen.tile(1_000_000))
+    gr = cm.three_phase_graph(net, DT)
+    G = cm.assemble_dense(gr)
+    ser = gr["to"] >= 0
+    tree = pt.build_tree(gr["n_bus"], gr["frm"][ser], gr["to"][ser], levels=2)
+    H = hinv.HInv(G, tree, gr["g"][ser], hinv.EXACT)
+    X = np.random.default_rng(3).standard_normal((gr["n_bus"], 2))
+    assert np.allclose(H.apply(X), np.linalg.solve(G, X), rtol=0, atol=1e-12 * np.abs(np.linalg.solve(G, X)).max())
