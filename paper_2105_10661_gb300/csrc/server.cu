@@ -102,12 +102,12 @@ Server::~Server() {
 }
 
 int Server::add_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int max_slots, int n_mon,
-                        const int32_t* mon) {
+                        const int32_t* mon, bool fixed_slots) {
   EMT_REQUIRE(max_slots >= 4 && n_mon >= 1 && mon, EMT_ERR_INVALID, "need >= 4 slots and a monitor list");
   const int64_t n = net->n_bus;
   const int64_t per_slot = per_slot_bytes(net);
   int slots = max_slots;
-  if (budget > 0) {
+  if (budget > 0 && !fixed_slots) {
     const int64_t share = (int64_t)(budget - used) / 2;   // leave room for later networks
     slots = (int)std::min<int64_t>(max_slots, share / std::max<int64_t>(per_slot, 1));
     slots = slots / 4 * 4;
@@ -227,16 +227,7 @@ int Server::place_private(int req, double t, std::vector<int>& idle_since) {
     }
   }
   const auto b0 = std::chrono::steady_clock::now();
-  const size_t saved = budget;
-  budget = 0;   // exactly kPrivSlots slots; the check above already applied the budget
-  int ni;
-  try {
-    ni = add_network(&v, &d.opts, d.dt, kPrivSlots, (int)d.mon.size(), d.mon.data());
-  } catch (...) {
-    budget = saved;
-    throw;
-  }
-  budget = saved;
+  const int ni = add_network(&v, &d.opts, d.dt, kPrivSlots, (int)d.mon.size(), d.mon.data(), true);
   build_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - b0).count();
   ++builds;
   nets[ni].priv = true;

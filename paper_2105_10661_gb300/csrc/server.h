@@ -13,8 +13,10 @@ class Server {
  public:
   Server(int tick, size_t hbm_budget);
   ~Server();
+  // fixed_slots: exactly max_slots slots (the caller has applied the budget); otherwise the slots
+  // are the network's share of the remaining budget, at most max_slots
   int add_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int max_slots, int n_mon,
-                  const int32_t* mon);
+                  const int32_t* mon, bool fixed_slots = false);
   int submit(int net, double arrival, int n_steps, int kind, int target, double value, int ev_step, int len);
   // a request on its own network (copied now; built, or found resident, when it arrives)
   int submit_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int n_mon, const int32_t* mon,
