@@ -821,10 +821,17 @@ def dth_arm(args):
             # ancestors' factors: their gap
             Gm, Gf = inverse(h, n), inverse(hf, n)
             gap = float(torch.linalg.norm(Gm - Gf) / torch.linalg.norm(Gf))
+            # the EXACT store: the local update continued to the root, against its rebuild
+            hx = L.emt_build_hinv_from_network(net, DT, d_th=d)
+            _, xmod_ms = timed(lambda: L.emt_modify_branch(hx, bus, -1, 1.0 / fault_ohm, stream=stream))
+            hxf, xrebuild_ms = timed(lambda: L.emt_build_hinv_from_network(netf, DT, d_th=d))
+            xgap = float(torch.linalg.norm(inverse(hx, n) - inverse(hxf, n)) / torch.linalg.norm(Gi))
             rows.append({"n_bus": n, "d_th": d, "n_leaf": len(leaves), "max_leaf": bmax,
                          "paper_rel_err_vs_exact": err, "build_ms": build_ms, "modify_ms": mod_ms,
                          "rebuild_ms": rebuild_ms, "time_saved": 1.0 - mod_ms / rebuild_ms,
                          "algorithm2_vs_rebuild_rel_diff": gap,
+                         "exact_modify_ms": xmod_ms, "exact_rebuild_ms": xrebuild_ms,
+                         "exact_modify_vs_rebuild_rel_diff": xgap,
                          "element_saving": 1.0 - (bmax / n) ** 2})
     # scaling of the build time with N at each d_th (least-squares slope of log t vs log N)
     slopes = {}
