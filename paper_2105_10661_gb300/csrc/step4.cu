@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
     for (int base = 0; base < nv; base += ng_e) {
       if (base + wg_e >= nv) break;
       const int i = base + grp_e;
-      A a;
+      A a, a2;   // two accumulators: half-length dependent chains
       const int* vr = vrow + kVR * (i < nv ? i : 0);
       if (i < nv) {
         const int pos = vr[0], j = vr[2];
@@ -464,10 +464,15 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
           const int* an = anc + 5 * x;
           const int k = an[0];
           const int si = pos < an[2] ? an[3] : an[4];
-#pragma unroll 4
-          for (int e = gl_e; e < k; e += le) a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
+          int e = gl_e;
+          for (; e + le < k; e += 2 * le) {
+            a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
+            a2.fma(Fr[(int64_t)(e + le) * fs], neg(ssp[si + e + le]));
+          }
+          if (e < k) a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
           Fr += (int64_t)an[1] * fs;
         }
+        a.add(a2.getx());
       }
       const X w = group_sum<PREC>(a, le);
       if (i < nv && gl_e == 0) {
