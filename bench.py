@@ -331,11 +331,11 @@ def native_arm(args):
         byts = b_partial + b_sweep
         ach = byts / (kt[0] * 1e-6) / 1e9
         # DRAM traffic of this kernel from an ncu capture of one 1,000-step launch on this workload
-        # (dram__bytes_read.sum + dram__bytes_write.sum = 3,233,792 B: the store, read once),
+        # (dram__bytes_read.sum + dram__bytes_write.sum = 3,263,232 B: the store, read once),
         # per time step like `achieved`
         roofline = {"bound": "hbm", "kernel": "k_step4", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"],
-                    "traffic": 3233792 / 1000 if args.config == 2 and H["tuned"]["rows_per_cta"] == 16 else None,
+                    "traffic": 3263232 / 1000 if args.config == 2 and H["tuned"]["rows_per_cta"] == 16 else None,
                     "traffic_unit": "bytes per time step",
                     "us_per_step": kt[0],
                     "algorithmic_bytes_per_step": byts, "cluster_ctas": H["tuned"]["rows_per_cta"],
