@@ -81,6 +81,14 @@ emt_network Server::NetDesc::view() const {
   return v;
 }
 
+bool Server::NetDesc::same(const NetDesc& o) const {
+  return n_bus == o.n_bus && from == o.from && to == o.to && kind == o.kind && src_bus == o.src_bus &&
+         load_bus == o.load_bus && mon == o.mon && R == o.R && L == o.L && C == o.C && shunt_C == o.shunt_C &&
+         src_Vm == o.src_Vm && src_phi == o.src_phi && src_Rs == o.src_Rs && load_amp == o.load_amp &&
+         load_phi == o.load_phi && freq == o.freq && dt == o.dt && opts.levels == o.opts.levels &&
+         opts.d_th == o.opts.d_th && opts.mode == o.opts.mode && opts.precision == o.opts.precision;
+}
+
 int64_t Server::per_slot_bytes(const emt_network* net) {
   // V, X (float-float), Xf, Y (FP32), Z (float-float), two history buffers per element (series
   // branches and one shunt per bus), boundary vectors, source coefficients
@@ -167,10 +175,22 @@ int Server::submit_network(const emt_network* net, const emt_hinv_opts* opts, do
   const int32_t o[4] = {opts->levels, opts->d_th, opts->mode, opts->precision};
   fnv(h, o, sizeof o);
   d.key = h;
-  descs.push_back(std::move(d));
+  // requests bringing identical networks share one description
+  int di = -1;
+  auto range = desc_index.equal_range(h);
+  for (auto it = range.first; it != range.second; ++it)
+    if (descs[it->second].same(d)) {
+      di = it->second;
+      break;
+    }
+  if (di < 0) {
+    descs.push_back(std::move(d));
+    di = (int)descs.size() - 1;
+    desc_index.emplace(h, di);
+  }
   Req r;
   r.net = -1;
-  r.priv = (int)descs.size() - 1;
+  r.priv = di;
   r.n_mon = n_mon;
   r.arrival = arrival;
   r.n_steps = n_steps;
@@ -187,7 +207,8 @@ int Server::submit_network(const emt_network* net, const emt_hinv_opts* opts, do
 void Server::evict(int ni) {
   Net& nt = nets[ni];
   if (nt.stream) EMT_CUDA(cudaStreamSynchronize(nt.stream));
-  cache.erase(nt.key);
+  auto it = cache.find(nt.key);
+  if (it != cache.end() && it->second == ni) cache.erase(it);
   nt.sim.reset();
   nt.rec = DevBuf<double>();
   if (nt.host_rec) cudaFreeHost(nt.host_rec);
@@ -209,10 +230,11 @@ void Server::evict(int ni) {
 int Server::place_private(int req, double t, std::vector<int>& idle_since) {
   const NetDesc& d = descs[reqs[req].priv];
   auto it = cache.find(d.key);
-  if (it != cache.end()) {
+  if (it != cache.end() && (nets[it->second].desc == reqs[req].priv || descs[nets[it->second].desc].same(d))) {
     ++hits;
     return it->second;
   }
+  if (it != cache.end()) cache.erase(it);   // a different network with the same hash: no longer cached
   const emt_network v = d.view();
   const int64_t need = per_slot_bytes(&v) * kPrivSlots;
   if (budget > 0) {
@@ -232,6 +254,7 @@ int Server::place_private(int req, double t, std::vector<int>& idle_since) {
   ++builds;
   nets[ni].priv = true;
   nets[ni].key = d.key;
+  nets[ni].desc = reqs[req].priv;
   nets[ni].last_used = t;
   cache[d.key] = ni;
   idle_since.resize(nets.size(), -1);

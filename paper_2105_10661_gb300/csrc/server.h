@@ -33,6 +33,7 @@ class Server {
     emt_hinv_opts opts{};
     uint64_t key = 0;
     emt_network view() const;
+    bool same(const NetDesc& o) const;   // identical content (the key is a hash)
   };
   struct Req {
     int net = 0, n_steps = 0, kind = -1, target = 0, ev_step = 0, len = 0, slot = -1, done_steps = 0;
@@ -51,6 +52,7 @@ class Server {
     cudaEvent_t done = nullptr;
     bool priv = false;          // built for private-network requests (evictable)
     uint64_t key = 0;
+    int desc = -1;              // its description
     double last_used = 0;
   };
   static constexpr int kPrivSlots = 4;
@@ -60,6 +62,7 @@ class Server {
   std::vector<Req> reqs;
   std::vector<NetDesc> descs;
   std::unordered_map<uint64_t, int> cache;   // content key -> resident network
+  std::unordered_multimap<uint64_t, int> desc_index;   // content key -> descriptions (shared by requests)
   double wall = 0, bus_steps = 0, build_s = 0;
   int max_queue = 0, builds = 0, hits = 0, evictions = 0;
   int64_t ticks = 0;
