@@ -749,7 +749,7 @@ def apply_arm(args):
                                "L2 flushed before every apply", "store_bytes_fp64": (leaf + fac) * 8},
         "variants_ms": {k: v[0] for k, v in res.items()},
         "accuracy": {k: rel_err(v[1], ref) for k, v in res.items()},
-        "roofline": {"bound": "hbm", "kernel": "whole apply (leaf partials + sweep)", "achieved": ach,
+        "roofline": {"bound": "hbm", "kernel": "whole apply (k_leaf_stream + k_sweep_matrix + k_expand_stream)", "achieved": ach,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
                      "algorithmic_bytes": byts},
         "cpu_baseline": {"value": n / (t2 - t1), "unit": "bus-steps/s", "cores": 1, "kind": "oracle",

@@ -3,13 +3,13 @@
 // once:
 //   k_leaf_stream    y = blkdiag(L_j) x. One persistent CTA per SM owns a contiguous range of
 //                    leaf rows (the store keeps leaves one after another, rows in position order)
-//                    and streams them through a ring of shared-memory stages filled by
-//                    cp.async.bulk, one row per stage, with full/empty mbarriers; one warp per row
-//                    forms the row dot against its leaf's slice of x, held in shared memory.
+//                    and streams them through a ring of shared-memory stages (two rows of a
+//                    leaf each) filled by cp.async.bulk, with full/empty mbarriers; one warp per
+//                    stage forms the row dots against its leaf's slice of x, held in shared memory.
 //   k_sweep_matrix   s = K y_cut: the boundary sweep of every tree node is linear in the leaf-stage
 //                    values at the cut rows, so it is one dense product (K built on the device from
 //                    the sweep image, after every build or modification); one warp per row of K.
-//   k_expand_stream  v = y - sum over ancestors q of F_q[row] . s_q(half); 8 lanes per position.
+//   k_expand_stream  v = y - sum over ancestors q of F_q[row] . s_q(half); 16 lanes per position.
 // Every wait is bounded: a timeout sets the device status word and the CTA drains its own copies
 // before it returns.
 #include <algorithm>
