@@ -13,20 +13,25 @@
 //   2. leaf stage (Eq. 2 with the leaf blocks of Sec. III) in column form: by symmetry of the
 //      leaf inverse, the CTA's rows of L_j are its columns, so it forms the partial products
 //      p_c[r] = sum over its positions i of L_j[i, r] x_i for every row r of the leaf using only
-//      its own x; each partial is pushed (st.shared::cluster) to the CTAs that need y[r]: the
-//      owner of r, the CTAs for which r is a neighbour of one of their elements, and every CTA
-//      when r is a cut row
-//   3. cluster barrier; y = sum of the partials
+//      its own x; each partial is pushed (st.async to the peer's shared memory, completing on
+//      the peer's mbarrier) to the CTAs that need y[r]: the owner of r, the CTAs for which r is a
+//      neighbour of one of their elements, and the CTAs whose slice of s reads the cut row r
+//   3. wait on this step's partials mbarrier (the host counts the bytes each CTA receives per
+//      step); y = sum of the partials
 //   4. boundary sweep as one product: the sweep is linear in the cut-row values, s = K y_cut,
 //      with K built on the device from the sweep image after every build or modification; each
-//      CTA forms its slice of s and pushes it to every CTA
-//   5. cluster barrier; expansion v = y - sum over ancestors of (factor row . s) for the CTA's
-//      positions and for its halo positions (far ends of its elements), so that the next history
-//      update reads local voltages only.
-// Exchange is push-only: remote stores before a barrier, local reads after it. The partial
-// buffers of the expansion rows alternate between two copies by step parity (a fast CTA may push
-// step t+1 partials while a slow one still expands step t); every other buffer is written and
-// read in phases a barrier apart. A cluster of one CTA uses __syncthreads instead.
+//      CTA forms its slice of s and pushes it (st.async) to every CTA
+//   5. wait on this step's s mbarrier; expansion v = y - sum over ancestors of (factor row . s)
+//      for the CTA's positions and for its halo positions (far ends of its elements), so that the
+//      next history update reads local voltages only.
+// Exchange is push-only and has no cluster barrier inside the time loop: every pushed buffer
+// (expansion-row partials, s) and its two mbarriers alternate by step parity, so a fast CTA may
+// push step t+1 while a slow one still reads step t, and a CTA cannot be two steps ahead of a
+// peer because it waits for that peer's pushes of the step before. The cut-row partials need one
+// copy: a CTA pushes those of step t+1 only after it has received every CTA's s of step t, which
+// each CTA sends after it has summed its cut-row partials of step t. Every wait is bounded; one
+// cluster barrier at exit keeps each CTA's shared memory alive until no peer can write it. A
+// cluster of one CTA uses __syncthreads instead.
 #include <algorithm>
 #include <climits>
 #include <cstring>
