@@ -73,12 +73,6 @@ __device__ __forceinline__ uint32_t mapa4(uint32_t a, uint32_t rank) {
 __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void st_remote(uint32_t a, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
-__device__ __forceinline__ void st_remote(uint32_t a, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
-}
 // asynchronous remote store whose completion is counted (in bytes) on the destination CTA's
 // mbarrier `mbar` (a shared::cluster address in the destination CTA)
 __device__ __forceinline__ void st_async(uint32_t a, float2 v, uint32_t mbar) {
