@@ -2,16 +2,19 @@
 // share one stored inverse and step together.
 //
 // Per step, for all columns at once:
-//   inject    element histories and source/load injections (float-float arithmetic)
-//   apply     leaf stage Y = blkdiag(L_j) X as a GEMM over the R columns (FP32 operands, FP32
-//             accumulation), boundary sweep per column block, expansion V = Y - sum F_q S_q;
+//   inject    element histories and source/load injections (float-float values, compensated
+//             accumulation)
+//   apply     leaf stage Y = blkdiag(L_j) X as a GEMM over the R columns (tcgen05 BF16x3 with
+//             FP32 accumulation in tensor memory, or FP32 SIMT tiles), boundary sweep S = K Y_cut
+//             as a split-K product over the nonzero column pieces of K, expansion
+//             V = Y - sum F_q S_q (tcgen05 or SIMT, float-float update of V);
 //             a column whose branch has tripped adds the Sherman-Morrison term of its own
 //             change, v_c -= (delta_c / d_c) z_c u_c^T y_c with z_c = Ginv u_c and the FP64
 //             denominator d_c = 1 + delta_c u_c^T z_c
 //   refine    residual r = x - G' v in float-float arithmetic (G' includes each column's trip),
 //             a second apply of r, v += c
-// The result is float-float (about 48 significant bits); one refinement pass brings the FP32
-// apply to the accuracy of the FP64 oracle. Per-column trips switch on by step number inside
+// The result is float-float (about 48 significant bits); one refinement pass brings the
+// FP32-grade apply to within 1e-8 of the FP64 oracle. Per-column trips switch on by step number inside
 // the kernels, so a whole run is a chain of CUDA graphs with no host work between steps.
 #pragma once
 #include <map>
