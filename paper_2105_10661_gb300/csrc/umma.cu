@@ -12,10 +12,12 @@
 // (8 rows x 16 bytes per core matrix, no swizzle): A (leaf blocks or factor paths, split once per
 // store) per (leaf, 128-row tile, 32-deep K chunk), B (right-hand sides or gathered S rows, split
 // once per pass) per (leaf, TN-column tile, K chunk). One CTA computes a 128-row x TN-column tile
-// of one leaf as a pipeline of 2-4 stages (96 KB, two CTAs per SM): one thread issues one cp.async.bulk per operand and chunk
-// into a stage (full mbarrier), one thread issues tcgen05.mma (M = 128, N = TN, K = 16,
-// kind::f16 with BF16 inputs) three times per K step and commits them to the stage's empty
-// mbarrier, and the epilogue reads the accumulator with tcgen05.ld. Each mbarrier has a single
+// of one leaf as a pipeline of 2-4 stages (96 KB, two CTAs per SM): one thread issues one
+// cp.async.bulk per operand and chunk into a stage (full mbarrier), one thread issues
+// tcgen05.mma (M = 128, N = TN, K = 16, kind::f16 with BF16 inputs) three times per K step and
+// commits them to the stage's empty mbarrier, and the epilogue reads the accumulator with
+// tcgen05.ld (the expansion stages it through shared memory, 64 columns at a time, for the
+// float-float update of V). Each mbarrier has a single
 // waiter that waits for its phases in order; every wait is bounded by clock64 and reports a
 // timeout in the device status word; tensor memory is always released.
 #include <algorithm>
