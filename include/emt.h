@@ -109,9 +109,11 @@ const emt_tree* emt_hinv_tree(const emt_hinv* h);
 
 /* v = G^{-1} i (Eq. 2) for nrhs column vectors. i_dev, v_dev: device, column-major
  * n_bus x nrhs with leading dimension ld >= n_bus (doubles), bus order. For EMT_PREC_FP32 the
- * result is refined up to max_refine times against the FP64 residual r = i - G v until
- * ||c||_inf <= tol ||v||_inf. Asynchronous on `stream`. nrhs >= 1; nrhs == 1 takes the fused
- * single-vector kernels. */
+ * result is refined exactly max_refine times (0..16): r = i - G v with the FP64 matrix, then
+ * v += (stored inverse) r. The count is fixed, chosen per workload by calibration, so that the
+ * call stays asynchronous (a tolerance test would read the device back every pass); tol is not
+ * evaluated (reserved). FP64 and FF64 stores ignore both. Asynchronous on `stream`. nrhs >= 1;
+ * nrhs == 1 takes the fused single-vector kernels. */
 emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld,
                      int32_t max_refine, double tol, void* stream);
 

@@ -177,7 +177,7 @@ const emt_tree* emt_hinv_tree(const emt_hinv* h) { return h ? &h->tree : nullptr
 
 emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld, int32_t max_refine,
                      double tol, void* stream) {
-  (void)tol;
+  (void)tol;   // reserved: the refinement count is fixed (max_refine), see emt.h
   return guard([&] {
     EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
     EMT_REQUIRE(i_dev && v_dev, EMT_ERR_INVALID, "null vectors");
