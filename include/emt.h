@@ -106,6 +106,12 @@ emt_status emt_build_hinv(const emt_graph* graph, const emt_hinv_opts* opts, voi
                           emt_hinv** out);
 /* The handle's tree (owned by the handle). */
 const emt_tree* emt_hinv_tree(const emt_hinv* h);
+/* The handle's partition (Sec. III-B): perm [n_bus] (position -> bus, the nested ordering),
+ * node_lo, node_hi, parent [n_node] (node i holds positions [node_lo[i], node_hi[i]); parent -1
+ * at the root). n_node comes from emt_tree_sizes(emt_hinv_tree(h), ...). Any pointer may be
+ * NULL; the arrays are caller-owned host memory. Host only. EMT_ERR_INVALID for a null handle. */
+emt_status emt_hinv_get_partition(const emt_hinv* h, int32_t* perm, int32_t* node_lo, int32_t* node_hi,
+                                  int32_t* parent);
 
 /* v = G^{-1} i (Eq. 2) for nrhs column vectors. i_dev, v_dev: device, column-major
  * n_bus x nrhs with leading dimension ld >= n_bus (doubles), bus order. For EMT_PREC_FP32 the

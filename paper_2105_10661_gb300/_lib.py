@@ -78,6 +78,7 @@ def _load():
         "emt_tree_destroy": (None, [vp]),
         "emt_build_hinv": (C.c_int, [C.POINTER(EmtGraph), C.POINTER(EmtHinvOpts), vp, C.POINTER(vp)]),
         "emt_hinv_tree": (vp, [vp]),
+        "emt_hinv_get_partition": (C.c_int, [vp, _i32p, _i32p, _i32p, _i32p]),
         "emt_apply": (C.c_int, [vp, vp, vp, C.c_int32, C.c_int64, C.c_int32, C.c_double, vp]),
         "emt_modify_branch": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, vp]),
         "emt_hinv_sync": (C.c_int, [vp, vp]),
@@ -123,7 +124,8 @@ def _load():
 
 lib = _load()
 EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes", "emt_tree_arrays", "emt_tree_destroy",
-            "emt_build_hinv", "emt_hinv_tree", "emt_apply", "emt_modify_branch", "emt_hinv_sync", "emt_hinv_destroy",
+            "emt_build_hinv", "emt_hinv_tree", "emt_hinv_get_partition", "emt_apply", "emt_modify_branch",
+            "emt_hinv_sync", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
             "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
@@ -237,6 +239,16 @@ class HInv:
 
     def tree(self):
         return tree_arrays(lib.emt_hinv_tree(self.h), self.n)
+
+
+def emt_hinv_get_partition(h: HInv):
+    """(perm, node_lo, node_hi, parent) of the handle's partition tree."""
+    nn = C.c_int32()
+    _check(lib.emt_tree_sizes(lib.emt_hinv_tree(h.h), C.byref(nn), None, None))
+    perm = np.zeros(h.n, np.int32)
+    lo, hi, parent = (np.zeros(nn.value, np.int32) for _ in range(3))
+    _check(lib.emt_hinv_get_partition(h.h, *[_p(a, _i32p) for a in (perm, lo, hi, parent)]))
+    return perm, lo, hi, parent
 
 
 def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64, stream=None):

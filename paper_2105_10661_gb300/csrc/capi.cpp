@@ -175,6 +175,14 @@ emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const 
 
 const emt_tree* emt_hinv_tree(const emt_hinv* h) { return h ? &h->tree : nullptr; }
 
+emt_status emt_hinv_get_partition(const emt_hinv* h, int32_t* perm, int32_t* node_lo, int32_t* node_hi,
+                                  int32_t* parent) {
+  const emt_status r = guard([&] { EMT_REQUIRE(h, EMT_ERR_INVALID, "null handle"); });
+  if (r != EMT_OK) return r;
+  return emt_tree_arrays(&h->tree, perm, node_lo, node_hi, parent, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr);
+}
+
 emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld, int32_t max_refine,
                      double tol, void* stream) {
   (void)tol;   // reserved: the refinement count is fixed (max_refine), see emt.h

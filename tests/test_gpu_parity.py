@@ -56,6 +56,17 @@ def _build(L, net_nw, levels=0, d_th=0, mode=0, prec=0):
     return h
 
 
+def test_hinv_get_partition_matches_tree_arrays(L):
+    nw, gr = _store_inputs(netgen.tile(1_000_000))
+    h = _build(L, (nw, gr), levels=2)
+    perm, lo, hi, parent = L.emt_hinv_get_partition(h)
+    t = h.tree()
+    for k, a in (("perm", perm), ("lo", lo), ("hi", hi), ("parent", parent)):
+        assert np.array_equal(a, t[k]), k
+    assert np.array_equal(np.sort(perm), np.arange(gr["n_bus"]))
+    assert lo[0] == 0 and hi[0] == gr["n_bus"] and parent[0] == -1
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("which,levels,d_th", [("tile", 2, 0), ("tiles8", 3, 0), ("small5", 2, 0), ("small37", 0, 7),
                                                ("small2", 1, 0), ("tile", 0, 20)])

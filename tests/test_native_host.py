@@ -64,3 +64,8 @@ def test_partition_rejects_bad_input(L):
     assert e.value.code == L.EMT_ERR_INVALID
     with pytest.raises(L.EmtError):
         L.emt_tree_build(4, [0], [1], levels=0, d_th=0)
+
+
+def test_partition_accessor_rejects_null_handle(L):
+    assert L.lib.emt_hinv_get_partition(None, None, None, None, None) == L.EMT_ERR_INVALID
+    assert "null handle" in L.lib.emt_last_error().decode()
