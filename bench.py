@@ -135,37 +135,46 @@ class Clocks:
             self.p = None
 
     def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
         if self.p is None:
-            return out
+            os.unlink(self.f.name)
+            return summarize_clocks([])
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.f.name) as fh:
+            lines = fh.readlines()
         os.unlink(self.f.name)
-        if not rows:
-            return out
-        import numpy as np
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for k, name in enumerate(names):
-                if r[5 + k].lower().startswith("active"):
-                    reasons.add(name)
-        out["sm_mhz"] = float(np.median(sm)) if sm else None
-        out["sm_max_mhz"] = max(mx) if mx else None
-        out["reasons"] = sorted(reasons)
-        out["samples"] = len(rows)
+        return summarize_clocks(lines)
+
+
+def summarize_clocks(lines) -> dict:
+    """Median SM clock, maximum SM clock and the throttle reasons seen, from the CSV rows (no header,
+    no units) of `nvidia-smi --query-gpu=<Clocks.Q>`; rows that do not parse are skipped."""
+    import numpy as np
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
         return out
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for k, name in enumerate(names):
+            if r[5 + k].lower().startswith("active"):
+                reasons.add(name)
+    out["sm_mhz"] = float(np.median(sm)) if sm else None
+    out["sm_max_mhz"] = max(mx) if mx else None
+    out["reasons"] = sorted(reasons)
+    out["samples"] = len(rows)
+    return out
 
 
 def job_ms(ms: float, world: int, device=None) -> float:
