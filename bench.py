@@ -767,6 +767,68 @@ def apply_arm(args):
 
 
 # ---------------------------------------------------------------- config 6 (d_th sweep)
+def hier_solve_flops(tree: dict) -> int:
+    """Additions and multiplications of one solve with the hierarchical store in the recursive
+    order of Eq. 9: every leaf y_j = L_j x_j (b^2 products, b(b-1) additions); at every internal
+    node p with k cut columns, t_p (k products by -g, the other half is a gather), s_p = C_p t_p
+    (4k^2 products, 2k(2k-1) additions) and the correction of its n_p rows by P s_1 or Q s_2
+    (k products and k additions per row)."""
+    lo, hi, left, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "cut_ptr"))
+    total = 0
+    for p in range(len(lo)):
+        n_p = int(hi[p] - lo[p])
+        if left[p] < 0:
+            total += 2 * n_p * n_p - n_p
+        else:
+            k = int(cut_ptr[p + 1] - cut_ptr[p])
+            total += k + 8 * k * k - 2 * k + 2 * n_p * k
+    return total
+
+
+def lu_flops(n_bus: int, br_a, br_b) -> dict:
+    """Additions, multiplications and divisions of the sparse-LU alternative (SuperLU through SciPy,
+    minimum-degree ordering of A + A^T, no pivoting) on the pattern of G: a weighted Laplacian of the
+    branches plus a positive diagonal (fill depends on the pattern only). Factorisation: l_k divisions
+    and l_k u_k multiply-adds at pivot k (l_k, u_k: nonzeros below and right of it). Solve: one
+    multiply-add per off-diagonal nonzero of L and U, one division per row."""
+    import numpy as np
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    a, b = np.asarray(br_a), np.asarray(br_b)
+    ones = np.ones(len(a))
+    A = sp.coo_matrix((np.concatenate([-ones, -ones]), (np.concatenate([a, b]), np.concatenate([b, a]))),
+                      shape=(n_bus, n_bus)).tocsr()
+    deg = -np.asarray(A.sum(axis=1)).ravel()
+    A = (A + sp.diags(deg + 1.0)).tocsc()
+    lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0, options={"SymmetricMode": True})
+    Lm, Um = lu.L.tocsc(), lu.U.tocsr()
+    Lm.eliminate_zeros()
+    Um.eliminate_zeros()
+    l_k = np.diff(Lm.indptr) - 1            # below the unit diagonal, per column
+    u_k = np.diff(Um.indptr) - 1            # right of the diagonal, per row
+    factor = int(np.sum(l_k) + 2 * np.sum(l_k * u_k))
+    solve = int(2 * np.sum(l_k) + 2 * np.sum(u_k) + n_bus)
+    return {"factor": factor, "solve": solve, "nnz_L": int(Lm.nnz), "nnz_U": int(Um.nnz)}
+
+
+def e3_solve_flops(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 179)) -> list:
+    """Solve FLOPs per time step on the tiled arrays: the hierarchical store (partition from the
+    library's host-side tree build) against the sparse-LU solve and factorisation (Sec. V-B)."""
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+    rows = []
+    for (r, c) in shapes:
+        net = netgen.tile(1_000_000) if r * c == 1 else netgen.tiled(r, c)
+        n = int(net["n_bus"])
+        lu = lu_flops(n, net["br_a"], net["br_b"])
+        row = {"n_bus": n, "lu_solve": lu["solve"], "lu_factor": lu["factor"], "dense_matvec": 2 * n * n - n}
+        for d in dths:
+            tree = L.emt_tree_build(n, net["br_a"], net["br_b"], d_th=d)
+            row[f"hier_dth{d}"] = hier_solve_flops(tree)
+        rows.append(row)
+    return rows
+
+
 def dth_arm(args):
     """PAPER-mode store (Algorithm 1) on tiled arrays of 1..12 tiles, leaves of at most d_th buses.
 
@@ -866,7 +928,7 @@ def dth_arm(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "PAPER-mode d_th sweep on seeded tiled arrays (179..2148 buses), d_th in "
                                f"{dths}, 10-ohm fault at bus N/3", "headline": "2148 buses, d_th 45"},
-        "table": rows, "build_time_exponent_vs_N": slopes,
+        "table": rows, "build_time_exponent_vs_N": slopes, "e3_solve_flops": e3_solve_flops(),
         "cpu_baseline": {"value": cpu_ms, "unit": "ms per Algorithm 2", "cores": 1, "kind": "oracle",
                          "sample": "179-bus tile, d_th 45, the same fault"},
         "gpu_launches": None,

@@ -3,6 +3,7 @@ region, and the whole-job rate of independent replicas."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -39,3 +40,90 @@ def test_clock_summary_without_samples():
 def test_job_rate_counts_every_rank():
     # 4 replicas, 1,432 buses x 20,000 steps each, slowest rank 100 ms
     assert bench.job_rate(1432 * 20000, 4, 100.0) == pytest.approx(4 * 1432 * 20000 / 0.1)
+
+
+# ---- solve FLOP counts of Sec. V-B (hierarchical store against sparse LU)
+
+def test_lu_flops_closed_forms():
+    # path graph: tridiagonal, no fill; the Thomas algorithm's 3(n - 1) and 5n - 4
+    n = 50
+    c = bench.lu_flops(n, list(range(n - 1)), list(range(1, n)))
+    assert (c["factor"], c["solve"]) == (3 * (n - 1), 5 * n - 4)
+    # complete graph: dense LU, sum over pivots of j divisions and j^2 multiply-adds
+    m = 9
+    a, b = zip(*[(i, j) for i in range(m) for j in range(i + 1, m)])
+    c = bench.lu_flops(m, a, b)
+    assert c["factor"] == sum(j + 2 * j * j for j in range(m))
+    assert c["solve"] == 2 * m * m - m
+
+
+def _counting_apply(H, p, x, ops):
+    """The solve of the store, node by node in the recursive order of Eq. 9 with the cut-row
+    gather t_p = [h_l^T y_l; h_r^T y_r], counting every addition and multiplication."""
+    t = H.tree
+    if t["left"][p] < 0:
+        Lj = H.leaf_inv[p]
+        y = []
+        for i in range(len(x)):
+            acc = Lj[i, 0] * x[0]
+            ops[0] += 1
+            for j in range(1, len(x)):
+                acc += Lj[i, j] * x[j]
+                ops[0] += 2
+            y.append(acc)
+        return y
+    l, r = int(t["left"][p]), int(t["right"][p])
+    nl = int(t["hi"][l] - t["lo"][l])
+    yl = _counting_apply(H, l, x[:nl], ops)
+    yr = _counting_apply(H, r, x[nl:], ops)
+    hl, hr, P, Q, C = H.hl[p], H.hr[p], H.P[p], H.Q[p], H.C[p]
+    k = P.shape[1]
+    if k == 0:
+        return yl + yr
+    tv = []
+    for e in range(k):   # h_l column e = -g_e at row a_e: one product
+        a = int(np.nonzero(hl[:, e])[0][0])
+        tv.append(hl[a, e] * yl[a])
+        ops[0] += 1
+    for e in range(k):   # h_r column e = unit vector at row b_e: a gather
+        tv.append(yr[int(np.nonzero(hr[:, e])[0][0])])
+    s = []
+    for i in range(2 * k):
+        acc = C[i, 0] * tv[0]
+        ops[0] += 1
+        for j in range(1, 2 * k):
+            acc += C[i, j] * tv[j]
+            ops[0] += 2
+        s.append(acc)
+    out = []
+    for F, y, half in ((P, yl, s[:k]), (Q, yr, s[k:])):
+        for i in range(len(y)):
+            acc = F[i, 0] * half[0]
+            ops[0] += 1
+            for j in range(1, k):
+                acc += F[i, j] * half[j]
+                ops[0] += 2
+            out.append(y[i] - acc)
+            ops[0] += 1
+    return out
+
+
+@pytest.mark.parametrize("n_bus,levels", [(13, 2), (37, 3)])
+def test_hier_solve_flops_counts_a_real_solve(n_bus, levels):
+    import netgen
+    from oracle import emt as oemt
+    from oracle import hinv as ohinv
+    nw = oemt.Network(netgen.small_network(n_bus, 77), 50e-6, levels=levels)
+    H = ohinv.HInv(nw.G, nw.tree, nw.g_series, ohinv.EXACT)
+    x = np.random.default_rng(4).standard_normal(n_bus)
+    ops = [0]
+    perm = nw.tree["perm"]
+    y = np.array(_counting_apply(H, 0, list(x[perm]), ops))
+    assert np.allclose(y, np.linalg.solve(nw.G, x)[perm], rtol=1e-10, atol=1e-12)   # the counted loop solves
+    assert ops[0] == bench.hier_solve_flops(nw.tree)
+
+
+def test_hier_solve_flops_single_leaf_is_dense_matvec():
+    n = 20
+    tree = {"lo": [0], "hi": [n], "left": [-1], "cut_ptr": [0, 0]}
+    assert bench.hier_solve_flops(tree) == 2 * n * n - n
