@@ -767,21 +767,47 @@ def apply_arm(args):
 
 
 # ---------------------------------------------------------------- config 6 (d_th sweep)
-def hier_solve_flops(tree: dict) -> int:
-    """Additions and multiplications of one solve with the hierarchical store in the recursive
-    order of Eq. 9: every leaf y_j = L_j x_j (b^2 products, b(b-1) additions); at every internal
-    node p with k cut columns, t_p (k products by -g, the other half is a gather), s_p = C_p t_p
-    (4k^2 products, 2k(2k-1) additions) and the correction of its n_p rows by P s_1 or Q s_2
-    (k products and k additions per row)."""
-    lo, hi, left, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "cut_ptr"))
+def hier_solve_flops(tree: dict, p: int = 0, paper: bool = False) -> int:
+    """Additions and multiplications of one solve with the store of node p's subtree, in the
+    recursive order of Eq. 9: every leaf y_j = L_j x_j (b^2 products, b(b-1) additions); at every
+    internal node with k cut columns, t_p (k products by -g, the other half is a gather),
+    s_p = C_p t_p (EXACT: 4k^2 products and 2k(2k-1) additions; PAPER: C_p = [[0, I], [I, 0]] is a
+    swap) and the correction of its n_p rows by P s_1 or Q s_2 (k products, k additions a row)."""
+    lo, hi, left, right, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "right", "cut_ptr"))
+    total = 0
+    stack = [p]
+    while stack:
+        q = stack.pop()
+        n_q = int(hi[q] - lo[q])
+        if left[q] < 0:
+            total += 2 * n_q * n_q - n_q
+        else:
+            k = int(cut_ptr[q + 1] - cut_ptr[q])
+            total += k + (0 if paper else 8 * k * k - 2 * k) + 2 * n_q * k
+            stack += [int(left[q]), int(right[q])]
+    return total
+
+
+def leaf_inverse_flops(b: int) -> int:
+    """Direct inversion of an SPD leaf block (Cholesky L L^T, W = L^-1, then W^T W for one triangle;
+    divisions and square roots count one each)."""
+    chol = sum((b - j) * (2 * j + 1) for j in range(b))
+    trinv = b + sum((b - d) * 2 * d for d in range(1, b))
+    wtw = sum((j + 1) * (2 * (b - j) - 1) for j in range(b))
+    return chol + trinv + wtw
+
+
+def alg1_build_flops(tree: dict) -> int:
+    """Algorithm 1 (PAPER store): every leaf inverted directly, and at every internal node the k
+    cut columns of P and of Q, each one solve of -g e_a (resp. e_b) through the child's store."""
+    lo, hi, left, right, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "right", "cut_ptr"))
     total = 0
     for p in range(len(lo)):
-        n_p = int(hi[p] - lo[p])
         if left[p] < 0:
-            total += 2 * n_p * n_p - n_p
+            total += leaf_inverse_flops(int(hi[p] - lo[p]))
         else:
             k = int(cut_ptr[p + 1] - cut_ptr[p])
-            total += k + 8 * k * k - 2 * k + 2 * n_p * k
+            total += k * (hier_solve_flops(tree, int(left[p]), True) + hier_solve_flops(tree, int(right[p]), True))
     return total
 
 
@@ -811,9 +837,10 @@ def lu_flops(n_bus: int, br_a, br_b) -> dict:
     return {"factor": factor, "solve": solve, "nnz_L": int(Lm.nnz), "nnz_U": int(Um.nnz)}
 
 
-def e3_solve_flops(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 179)) -> list:
-    """Solve FLOPs per time step on the tiled arrays: the hierarchical store (partition from the
-    library's host-side tree build) against the sparse-LU solve and factorisation (Sec. V-B)."""
+def flop_table(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 179)) -> list:
+    """FLOPs on the tiled arrays (Sec. V-B): Algorithm 1's build (E2) and one solve per time step
+    with the PAPER and the EXACT store (E3), partitions from the library's host-side tree build,
+    against the sparse-LU solve and factorisation and the dense mat-vec."""
     import netgen
     import paper_2105_10661_gb300._lib as L
     rows = []
@@ -824,7 +851,9 @@ def e3_solve_flops(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 17
         row = {"n_bus": n, "lu_solve": lu["solve"], "lu_factor": lu["factor"], "dense_matvec": 2 * n * n - n}
         for d in dths:
             tree = L.emt_tree_build(n, net["br_a"], net["br_b"], d_th=d)
-            row[f"hier_dth{d}"] = hier_solve_flops(tree)
+            row[f"solve_paper_dth{d}"] = hier_solve_flops(tree, paper=True)
+            row[f"solve_exact_dth{d}"] = hier_solve_flops(tree)
+            row[f"alg1_build_dth{d}"] = alg1_build_flops(tree)
         rows.append(row)
     return rows
 
@@ -928,7 +957,7 @@ def dth_arm(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "PAPER-mode d_th sweep on seeded tiled arrays (179..2148 buses), d_th in "
                                f"{dths}, 10-ohm fault at bus N/3", "headline": "2148 buses, d_th 45"},
-        "table": rows, "build_time_exponent_vs_N": slopes, "e3_solve_flops": e3_solve_flops(),
+        "table": rows, "build_time_exponent_vs_N": slopes, "flops_e2_e3": flop_table(),
         "cpu_baseline": {"value": cpu_ms, "unit": "ms per Algorithm 2", "cores": 1, "kind": "oracle",
                          "sample": "179-bus tile, d_th 45, the same fault"},
         "gpu_launches": None,

@@ -57,9 +57,10 @@ def test_lu_flops_closed_forms():
     assert c["solve"] == 2 * m * m - m
 
 
-def _counting_apply(H, p, x, ops):
-    """The solve of the store, node by node in the recursive order of Eq. 9 with the cut-row
-    gather t_p = [h_l^T y_l; h_r^T y_r], counting every addition and multiplication."""
+def _counting_apply(H, p, x, ops, paper):
+    """The solve of the store of node p's subtree, node by node in the recursive order of Eq. 9
+    with the cut-row gather t_p = [h_l^T y_l; h_r^T y_r], counting every addition and
+    multiplication. PAPER cores [[0, I], [I, 0]] are applied as the swap they are."""
     t = H.tree
     if t["left"][p] < 0:
         Lj = H.leaf_inv[p]
@@ -74,8 +75,8 @@ def _counting_apply(H, p, x, ops):
         return y
     l, r = int(t["left"][p]), int(t["right"][p])
     nl = int(t["hi"][l] - t["lo"][l])
-    yl = _counting_apply(H, l, x[:nl], ops)
-    yr = _counting_apply(H, r, x[nl:], ops)
+    yl = _counting_apply(H, l, x[:nl], ops, paper)
+    yr = _counting_apply(H, r, x[nl:], ops, paper)
     hl, hr, P, Q, C = H.hl[p], H.hr[p], H.P[p], H.Q[p], H.C[p]
     k = P.shape[1]
     if k == 0:
@@ -87,14 +88,17 @@ def _counting_apply(H, p, x, ops):
         ops[0] += 1
     for e in range(k):   # h_r column e = unit vector at row b_e: a gather
         tv.append(yr[int(np.nonzero(hr[:, e])[0][0])])
-    s = []
-    for i in range(2 * k):
-        acc = C[i, 0] * tv[0]
-        ops[0] += 1
-        for j in range(1, 2 * k):
-            acc += C[i, j] * tv[j]
-            ops[0] += 2
-        s.append(acc)
+    if paper:
+        s = tv[k:] + tv[:k]
+    else:
+        s = []
+        for i in range(2 * k):
+            acc = C[i, 0] * tv[0]
+            ops[0] += 1
+            for j in range(1, 2 * k):
+                acc += C[i, j] * tv[j]
+                ops[0] += 2
+            s.append(acc)
     out = []
     for F, y, half in ((P, yl, s[:k]), (Q, yr, s[k:])):
         for i in range(len(y)):
@@ -108,22 +112,94 @@ def _counting_apply(H, p, x, ops):
     return out
 
 
-@pytest.mark.parametrize("n_bus,levels", [(13, 2), (37, 3)])
-def test_hier_solve_flops_counts_a_real_solve(n_bus, levels):
+def _counting_leaf_inverse(A, ops):
+    """Cholesky A = L L^T, W = L^-1, then A^-1 = W^T W (one triangle, mirrored), counting every
+    addition, multiplication, division and square root."""
+    b = A.shape[0]
+    Lc = np.zeros((b, b))
+    for j in range(b):
+        acc = A[j, j]
+        for k in range(j):
+            acc -= Lc[j, k] * Lc[j, k]
+            ops[0] += 2
+        Lc[j, j] = acc ** 0.5
+        ops[0] += 1
+        for i in range(j + 1, b):
+            acc = A[i, j]
+            for k in range(j):
+                acc -= Lc[i, k] * Lc[j, k]
+                ops[0] += 2
+            Lc[i, j] = acc / Lc[j, j]
+            ops[0] += 1
+    W = np.zeros((b, b))
+    for j in range(b):
+        W[j, j] = 1.0 / Lc[j, j]
+        ops[0] += 1
+        for i in range(j + 1, b):
+            acc = Lc[i, j] * W[j, j]
+            ops[0] += 1
+            for k in range(j + 1, i):
+                acc += Lc[i, k] * W[k, j]
+                ops[0] += 2
+            W[i, j] = -acc / Lc[i, i]
+            ops[0] += 1
+    out = np.zeros((b, b))
+    for j in range(b):
+        for i in range(j + 1):
+            acc = W[j, i] * W[j, j]
+            ops[0] += 1
+            for k in range(j + 1, b):
+                acc += W[k, i] * W[k, j]
+                ops[0] += 2
+            out[i, j] = out[j, i] = acc
+    return out
+
+
+def _network(n_bus, levels, mode):
     import netgen
     from oracle import emt as oemt
     from oracle import hinv as ohinv
     nw = oemt.Network(netgen.small_network(n_bus, 77), 50e-6, levels=levels)
-    H = ohinv.HInv(nw.G, nw.tree, nw.g_series, ohinv.EXACT)
+    return nw, ohinv.HInv(nw.G, nw.tree, nw.g_series, mode)
+
+
+@pytest.mark.parametrize("paper", [False, True])
+@pytest.mark.parametrize("n_bus,levels", [(13, 2), (37, 3)])
+def test_hier_solve_flops_counts_a_real_solve(n_bus, levels, paper):
+    from oracle import hinv as ohinv
+    nw, H = _network(n_bus, levels, ohinv.PAPER if paper else ohinv.EXACT)
     x = np.random.default_rng(4).standard_normal(n_bus)
     ops = [0]
     perm = nw.tree["perm"]
-    y = np.array(_counting_apply(H, 0, list(x[perm]), ops))
-    assert np.allclose(y, np.linalg.solve(nw.G, x)[perm], rtol=1e-10, atol=1e-12)   # the counted loop solves
-    assert ops[0] == bench.hier_solve_flops(nw.tree)
+    y = np.array(_counting_apply(H, 0, list(x[perm]), ops, paper))
+    ref = H.apply(x)[perm] if paper else np.linalg.solve(nw.G, x)[perm]   # Algorithm 1's inverse, or exact
+    assert np.allclose(y, ref, rtol=1e-10, atol=1e-12)   # the counted loop is the solve
+    assert ops[0] == bench.hier_solve_flops(nw.tree, paper=paper)
+
+
+@pytest.mark.parametrize("n_bus,levels", [(13, 2), (37, 3)])
+def test_alg1_build_flops_counts_a_real_build(n_bus, levels):
+    """Algorithm 1 with counted loops: direct leaf inverses, then every cut column of P and Q as a
+    counted solve through the child's store; each block equals the oracle's PAPER store."""
+    from oracle import hinv as ohinv
+    nw, H = _network(n_bus, levels, ohinv.PAPER)
+    t = nw.tree
+    ops = [0]
+    for p in range(len(t["lo"])):
+        lo, hi = int(t["lo"][p]), int(t["hi"][p])
+        if t["left"][p] < 0:
+            inv = _counting_leaf_inverse(H.Gp[lo:hi, lo:hi], ops)
+            assert np.allclose(inv, H.leaf_inv[p], rtol=1e-10, atol=1e-13)
+            continue
+        for child, h, F in ((int(t["left"][p]), H.hl[p], H.P[p]), (int(t["right"][p]), H.hr[p], H.Q[p])):
+            for e in range(h.shape[1]):
+                col = np.array(_counting_apply(H, child, list(h[:, e]), ops, True))
+                assert np.allclose(col, F[:, e], rtol=1e-10, atol=1e-13)
+    assert ops[0] == bench.alg1_build_flops(t)
 
 
 def test_hier_solve_flops_single_leaf_is_dense_matvec():
     n = 20
-    tree = {"lo": [0], "hi": [n], "left": [-1], "cut_ptr": [0, 0]}
+    tree = {"lo": [0], "hi": [n], "left": [-1], "right": [-1], "cut_ptr": [0, 0]}
     assert bench.hier_solve_flops(tree) == 2 * n * n - n
+    assert bench.leaf_inverse_flops(1) == 3   # sqrt, reciprocal, one product
