@@ -797,18 +797,51 @@ def leaf_inverse_flops(b: int) -> int:
     return chol + trinv + wtw
 
 
+def _alg1_node_flops(tree: dict, p: int) -> int:
+    """Algorithm 1's work at node p: a leaf's direct inverse, or the k cut columns of P and Q."""
+    lo, hi, left, right, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "right", "cut_ptr"))
+    if left[p] < 0:
+        return leaf_inverse_flops(int(hi[p] - lo[p]))
+    k = int(cut_ptr[p + 1] - cut_ptr[p])
+    return k * (hier_solve_flops(tree, int(left[p]), True) + hier_solve_flops(tree, int(right[p]), True))
+
+
 def alg1_build_flops(tree: dict) -> int:
     """Algorithm 1 (PAPER store): every leaf inverted directly, and at every internal node the k
     cut columns of P and of Q, each one solve of -g e_a (resp. e_b) through the child's store."""
-    lo, hi, left, right, cut_ptr = (tree[k] for k in ("lo", "hi", "left", "right", "cut_ptr"))
-    total = 0
-    for p in range(len(lo)):
-        if left[p] < 0:
-            total += leaf_inverse_flops(int(hi[p] - lo[p]))
-        else:
-            k = int(cut_ptr[p + 1] - cut_ptr[p])
-            total += k * (hier_solve_flops(tree, int(left[p]), True) + hier_solve_flops(tree, int(right[p]), True))
-    return total
+    return sum(_alg1_node_flops(tree, p) for p in range(len(tree["lo"])))
+
+
+def alg2_flops(tree: dict, a_pos: int, b_pos: int = -1) -> int:
+    """Algorithm 2 (Sec. IV) for a change at positions a_pos, b_pos (-1: to ground): the leaves
+    holding them re-inverted directly and Algorithm 1's cut columns recomputed at every internal
+    node on their paths up to the lowest common ancestor (Theorem 1), nothing above it."""
+    lo, hi, left, parent = (tree[k] for k in ("lo", "hi", "left", "parent"))
+
+    def leaf_of(x):
+        q = 0
+        while left[q] >= 0:
+            q = int(left[q]) if x < hi[int(left[q])] else int(tree["right"][q])
+        return q
+
+    la = leaf_of(a_pos)
+    lb = leaf_of(b_pos) if b_pos >= 0 else la
+    up, q = set(), la
+    while q >= 0:
+        up.add(q)
+        q = int(parent[q])
+    top = lb
+    while top not in up:
+        top = int(parent[top])
+    nodes = set()
+    for leaf in {la, lb}:
+        q = leaf
+        while True:
+            nodes.add(q)
+            if q == top:
+                break
+            q = int(parent[q])
+    return sum(_alg1_node_flops(tree, q) for q in nodes)
 
 
 def lu_flops(n_bus: int, br_a, br_b) -> dict:
@@ -838,9 +871,10 @@ def lu_flops(n_bus: int, br_a, br_b) -> dict:
 
 
 def flop_table(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 179)) -> list:
-    """FLOPs on the tiled arrays (Sec. V-B): Algorithm 1's build (E2) and one solve per time step
-    with the PAPER and the EXACT store (E3), partitions from the library's host-side tree build,
-    against the sparse-LU solve and factorisation and the dense mat-vec."""
+    """FLOPs on the tiled arrays (Sec. V-B): Algorithm 1's build (E2), Algorithm 2 for a fault and
+    for a trip of a root cut branch (Theorem 1), and one solve per time step with the PAPER and the
+    EXACT store (E3), partitions from the library's host-side tree build, against the sparse-LU
+    solve and factorisation and the dense mat-vec."""
     import netgen
     import paper_2105_10661_gb300._lib as L
     rows = []
@@ -854,6 +888,12 @@ def flop_table(shapes=((1, 1), (1, 2), (2, 2), (2, 4), (3, 4)), dths=(45, 179)) 
             row[f"solve_paper_dth{d}"] = hier_solve_flops(tree, paper=True)
             row[f"solve_exact_dth{d}"] = hier_solve_flops(tree)
             row[f"alg1_build_dth{d}"] = alg1_build_flops(tree)
+            # Algorithm 2: a fault at bus N/3 (one leaf), and a trip of the root's first cut branch
+            # (paths up to the root: Theorem 1's worst case)
+            pos = {int(bus): i for i, bus in enumerate(tree["perm"])}
+            row[f"alg2_fault_dth{d}"] = alg2_flops(tree, pos[n // 3])
+            if tree["left"][0] >= 0 and tree["cut_ptr"][1] > 0:
+                row[f"alg2_root_trip_dth{d}"] = alg2_flops(tree, int(tree["cut_a"][0]), int(tree["cut_b"][0]))
         rows.append(row)
     return rows
 

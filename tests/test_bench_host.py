@@ -198,6 +198,38 @@ def test_alg1_build_flops_counts_a_real_build(n_bus, levels):
     assert ops[0] == bench.alg1_build_flops(t)
 
 
+@pytest.mark.parametrize("to_ground", [False, True])
+def test_alg2_flops_counts_a_real_modification(to_ground):
+    """Algorithm 2 with counted loops on the touched leaves and path nodes (the oracle's own path
+    logic picks them): a trip of a root cut branch, or a fault to ground; the recomputed blocks
+    equal the oracle's Algorithm 2."""
+    from oracle import hinv as ohinv
+    from oracle import modify as omod
+    nw, H = _network(37, 3, ohinv.PAPER)
+    t = nw.tree
+    c0 = int(t["cut_ptr"][0])
+    a, b = int(t["cut_a"][c0]), int(t["cut_b"][c0])
+    if to_ground:
+        b, delta = -1, 0.1
+    else:
+        delta = -float(nw.g_series[int(t["cut_e"][c0])])
+    perm = t["perm"]
+    new = omod.algorithm2(H, nw.series_frm, nw.series_to, int(perm[a]), int(perm[b]) if b >= 0 else -1, delta)
+    leaves, order, _ = omod.touched_path(t, a, b, False)
+    ops = [0]
+    for j in leaves:
+        lo, hi = int(t["lo"][j]), int(t["hi"][j])
+        assert np.allclose(_counting_leaf_inverse(new.Gp[lo:hi, lo:hi], ops), new.leaf_inv[j], rtol=1e-10,
+                           atol=1e-13)
+    for q in order:
+        for child, h, F in ((int(t["left"][q]), new.hl[q], new.P[q]), (int(t["right"][q]), new.hr[q], new.Q[q])):
+            for e in range(h.shape[1]):
+                col = np.array(_counting_apply(new, child, list(h[:, e]), ops, True))
+                assert np.allclose(col, F[:, e], rtol=1e-10, atol=1e-13)
+    assert ops[0] == bench.alg2_flops(t, a, b)
+    assert (len(order) == 0) == to_ground
+
+
 def test_hier_solve_flops_single_leaf_is_dense_matvec():
     n = 20
     tree = {"lo": [0], "hi": [n], "left": [-1], "right": [-1], "cut_ptr": [0, 0]}
