@@ -152,6 +152,36 @@ def test_passivity_sources_off():
         E_prev = E
 
 
+def test_lossless_lc_network_conserves_energy_exactly():
+    # No resistance anywhere (R = 0, no Thevenin sources). For a linear system the trapezoidal rule
+    # is the implicit midpoint rule, which keeps every quadratic invariant: once the driving current
+    # sinks are zero at both ends of a step, the stored energy 1/2 C v^2 + 1/2 L i^2 stays the same
+    # at every step. A wrong sign or coefficient in any history update breaks this at O(dt).
+    base = _net(24, 5)
+    net = dict(base)
+    net["R"] = np.zeros_like(base["R"])
+    net.update(src_bus=np.zeros(0, np.int32), src_Vm=np.zeros(0), src_phi=np.zeros(0), src_Rs=np.zeros(0),
+               load_bus=np.array([0, 7, 13], np.int32), load_amp=np.array([0.1, 0.05, 0.08]),
+               load_phi=np.array([0.0, 1.0, 2.0]))
+    nw = emt.Network(net, DT, want_tree=False)
+    el, n = nw.el, net["n_bus"]
+    kinds = set(np.asarray(net["kind"]).tolist())
+    assert cm.KIND_RL in kinds and cm.KIND_RC in kinds   # both series histories are exercised
+    Ih = np.zeros(len(el["g"]))
+    active = np.ones(len(el["g"]), bool)
+    sol = dense.DenseSolver(nw.G)
+    for step in range(1, 102):   # driven for 100 steps, then one step whose start still carries the sinks
+        rhs = (cm.source_injection(net, step * DT) if step <= 100 else 0.0) + cm.history_injection(el, Ih, n)
+        v = sol.solve(rhs)
+        cur, Ih = cm.update_history(el, v, Ih, active)
+    E0 = _energy(nw, v, cur, active)
+    assert E0 > 0
+    for _ in range(400):
+        v = sol.solve(cm.history_injection(el, Ih, n))
+        cur, Ih = cm.update_history(el, v, Ih, active)
+        assert abs(_energy(nw, v, cur, active) - E0) <= 1e-11 * E0
+
+
 # ---------------------------------------------------------------- exact solve
 @pytest.mark.parametrize("n_bus", [2, 3, 5, 8, 13, 16])
 def test_dense_inverse_brute_force(n_bus):
