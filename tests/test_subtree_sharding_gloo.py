@@ -10,6 +10,11 @@ s_p = C_p t_p (Eq. 9 factors, exact cores); (4) each rank expands its own rows,
 v = Y_r - sum over its top ancestors of F row . s(half). The assembled result must equal the
 hierarchical apply of the whole network. No GPU is used: the store and the per-rank arithmetic are
 the oracle's.
+
+The second test runs whole time steps this way (injection, sharded apply, history update of the
+rank's elements). A branch joining two ranks' subtrees is cut at a top node, so both its end
+voltages follow from the values that one all-gather already brings: one exchange per step
+suffices for the whole time loop.
 """
 import os
 import socket
@@ -113,6 +118,97 @@ def _rank(rank, world, port, q):
         dist.destroy_process_group()
 
 
+def _rank_steps(rank, world, port, q, n_steps):
+    import torch.distributed as dist
+    from oracle import companion as cm
+    from oracle import emt as oemt
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nw, H = _store()
+        t, net, el = H.tree, nw.net, nw.el
+        n = nw.G.shape[0]
+        perm = np.asarray(t["perm"])
+        pos = np.empty(n, np.int64)
+        pos[perm] = np.arange(n)
+        d = int(np.log2(world))
+        owned = sorted((p for p in range(len(t["lo"])) if t["depth"][p] == d), key=lambda p: t["lo"][p])
+        me = owned[rank]
+        lo, hi = int(t["lo"][me]), int(t["hi"][me])
+        top = [p for p in range(len(t["lo"])) if t["depth"][p] < d and t["left"][p] >= 0]
+        ends = sorted({int(v) for p in top for c in range(t["cut_ptr"][p], t["cut_ptr"][p + 1])
+                       for v in (t["cut_a"][c], t["cut_b"][c])})
+        subtree_of = {}
+        for o in owned:
+            for x in range(int(t["lo"][o]), int(t["hi"][o])):
+                subtree_of[x] = o
+
+        def top_anc(x, below_depth):
+            out, p = [], int(t["parent"][subtree_of[x]])
+            while p >= 0:
+                if t["depth"][p] > below_depth:
+                    out.append(p)
+                p = int(t["parent"][p])
+            return out
+
+        # the rank's elements: every element with an end in its range; a cross-rank element is a
+        # top-node cut branch, so its far end is a gathered endpoint
+        ea, eb = pos[el["a"]], np.where(el["b"] >= 0, pos[np.maximum(el["b"], 0)], -1)
+        mine_el = ((ea >= lo) & (ea < hi)) | ((eb >= lo) & (eb < hi))
+        far = sorted({int(x) for x in np.concatenate([ea[mine_el], eb[mine_el]]) if x >= 0 and not lo <= x < hi})
+        assert set(far) <= set(ends)
+        Ih = np.zeros(len(el["g"]))
+        active = np.ones(len(el["g"]), bool)
+        rec = np.zeros((n_steps, hi - lo))
+        for step in range(1, n_steps + 1):
+            rhs = cm.source_injection(net, step * DT) + cm.history_injection(el, np.where(mine_el, Ih, 0.0), n)
+            Y = H.apply_node(me, rhs[perm][lo:hi])
+            gathered = [None] * world
+            dist.all_gather_object(gathered, {e: float(Y[e - lo]) for e in ends if lo <= e < hi})
+            yend = {}
+            for part in gathered:
+                yend.update(part)
+            s = {}
+
+            def value_below(x, depth):
+                # the solve of the subtree below depth `depth` at position x (-1: the whole network)
+                v = yend[x]
+                for a in top_anc(x, depth):
+                    row, half = _top_rows(H, a, x)
+                    v -= row @ s[a][half]
+                return v
+
+            for p in sorted(top, key=lambda p: -t["depth"][p]):
+                c0, c1 = int(t["cut_ptr"][p]), int(t["cut_ptr"][p + 1])
+                tl = [-H.g_branch[t["cut_e"][c]] * value_below(int(t["cut_a"][c]), t["depth"][p])
+                      for c in range(c0, c1)]
+                tr = [value_below(int(t["cut_b"][c]), t["depth"][p]) for c in range(c0, c1)]
+                s[p] = H.C[p] @ np.array(tl + tr)
+            v = Y.copy()
+            for i in range(hi - lo):
+                for a in top_anc(lo + i, -1):
+                    row, half = _top_rows(H, a, lo + i)
+                    v[i] -= row @ s[a][half]
+            vb = np.full(n, np.nan)   # bus voltages this rank knows: its own and the far ends
+            vb[perm[lo:hi]] = v
+            for x in far:
+                vb[perm[x]] = value_below(x, -1)
+            with np.errstate(invalid="ignore"):
+                _, Ih_new = cm.update_history(el, vb, Ih, active)
+            Ih = np.where(mine_el, Ih_new, Ih)
+            assert np.all(np.isfinite(Ih[mine_el]))
+            rec[step - 1] = v
+        ref, _ = oemt.simulate(nw, n_steps, (), solver="exact")
+        want = ref[:, perm[lo:hi]]
+        q.put((rank, float(np.max(np.abs(rec - want)) / np.max(np.abs(want))), len(far), len(ends)))
+    except Exception as e:   # report instead of leaving the parent waiting
+        q.put((rank, repr(e), -1, -1))
+        raise
+    finally:
+        dist.destroy_process_group()
+
+
 @pytest.mark.parametrize("world", [2, 4])
 def test_subtree_sharded_apply_equals_whole_apply(world):
     ctx = mp.get_context("spawn")
@@ -131,3 +227,22 @@ def test_subtree_sharded_apply_equals_whole_apply(world):
         assert err <= 1e-12, (rank, err)
         assert n_ends < 0.05 * n_bus   # the single exchange: a few hundred values, not a vector
     assert sum(o[2] for o in out) == out[0][3]   # every endpoint comes from exactly one rank
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_subtree_sharded_time_steps_equal_whole_network(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    n_steps = 40
+    procs = [ctx.Process(target=_rank_steps, args=(r, world, port, q, n_steps)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=600) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, err, n_far, n_ends in out:
+        assert not isinstance(err, str), (rank, err)
+        assert err <= 1e-11, (rank, err)
+        assert 0 < n_far <= n_ends   # cross-rank elements exist, and their far ends are gathered anyway
