@@ -30,8 +30,9 @@ KIND_RC = 1
 
 
 def elements(net: dict, dt: float) -> dict:
-    """History elements: series branches first (ids 0..nb-1), then one shunt
-    capacitor per bus. Returns endpoints, g, alpha, beta."""
+    """History elements of Eq. 1's i_his (Sec. II), with the trapezoidal companion models of the
+    module header: series branches first (ids 0..nb-1), then one shunt capacitor per bus.
+    Returns endpoints, g, alpha, beta."""
     nb = len(net["br_a"])
     n = net["n_bus"]
     a = np.concatenate([net["br_a"], np.arange(n)]).astype(np.int64)
@@ -60,8 +61,8 @@ def elements(net: dict, dt: float) -> dict:
 
 
 def graph(net: dict, dt: float) -> dict:
-    """The conductance graph: every element and every source conductance as a
-    branch (to = -1 for ground). This is the list G is assembled from."""
+    """The conductance graph of Eq. 1's G (Sec. II): every element and every source conductance
+    as a branch (to = -1 for ground). This is the list G is assembled from."""
     el = elements(net, dt)
     src_g = 1.0 / np.asarray(net["src_Rs"], float)
     return dict(n_bus=net["n_bus"],
@@ -81,7 +82,8 @@ def coupled_rl_admittance(R: float, L: float, L_mut: float, dt: float) -> np.nda
 
 
 def three_phase_graph(net: dict, dt: float) -> dict:
-    """Conductance graph of a three-phase network, node = 3 bus + phase. An RL branch's term
+    """Conductance graph of a three-phase network (three nodes per bus, Sec. III-A after Eq. 3),
+    node = 3 bus + phase. An RL branch's term
     Y (x) (e_a - e_b)(e_a - e_b)^T is split into node branches: a_p-b_p with Y_pp, a_p-b_q
     (p != q) with Y_pq, a_p-a_q and b_p-b_q (p < q) with -Y_pq (zero terms dropped). RC
     branches, shunt capacitors and sources act on each phase alone."""
@@ -116,7 +118,8 @@ def three_phase_graph(net: dict, dt: float) -> dict:
 
 
 def assemble_dense(gr: dict) -> np.ndarray:
-    """G = sum over branches of g u u^T, u = e_a - e_b (or e_a to ground)."""
+    """G of Eq. 1 (Sec. II) as a dense matrix: the sum over branches of g u u^T, u = e_a - e_b
+    (or e_a to ground)."""
     n = gr["n_bus"]
     G = np.zeros((n, n))
     for a, b, g in zip(gr["frm"], gr["to"], gr["g"]):
@@ -129,6 +132,7 @@ def assemble_dense(gr: dict) -> np.ndarray:
 
 
 def assemble_sparse(gr: dict) -> sp.csc_matrix:
+    """G of Eq. 1 (Sec. II) in CSC form, the same sum as assemble_dense."""
     n = gr["n_bus"]
     rows, cols, vals = [], [], []
     for a, b, g in zip(gr["frm"], gr["to"], gr["g"]):
@@ -139,7 +143,7 @@ def assemble_sparse(gr: dict) -> sp.csc_matrix:
 
 
 def source_injection(net: dict, t: float, src_scale=None, load_scale=None) -> np.ndarray:
-    """i_in(t): Norton currents e(t)/R_s of the sources minus the load sinks."""
+    """i_in(t) of Eq. 1 (Sec. II): Norton currents e(t)/R_s of the sources minus the load sinks."""
     n = net["n_bus"]
     w = 2.0 * np.pi * net["freq"]
     i = np.zeros(n)
@@ -152,7 +156,7 @@ def source_injection(net: dict, t: float, src_scale=None, load_scale=None) -> np
 
 
 def history_injection(el: dict, Ih: np.ndarray, n_bus: int) -> np.ndarray:
-    """i_his: -I_h at the from-bus and +I_h at the to-bus of every element."""
+    """i_his of Eq. 1 (Sec. II): -I_h at the from-bus and +I_h at the to-bus of every element."""
     i = np.zeros(n_bus)
     np.add.at(i, el["a"], -Ih)
     m = el["b"] >= 0
@@ -161,12 +165,14 @@ def history_injection(el: dict, Ih: np.ndarray, n_bus: int) -> np.ndarray:
 
 
 def branch_voltage(el: dict, v: np.ndarray) -> np.ndarray:
+    """v_e = v_a - v_b of every element (v_b = 0 for ground), the companion models' input."""
     vb = np.where(el["b"] >= 0, v[np.maximum(el["b"], 0)], 0.0)
     return v[el["a"]] - vb
 
 
 def update_history(el: dict, v: np.ndarray, Ih: np.ndarray, active: np.ndarray):
-    """Element currents at t and the history sources for t + dt."""
+    """Element currents at t and the history sources for t + dt: the trapezoidal update
+    I_h <- alpha v_e + beta i of the module header (Sec. II, Eq. 1's i_his)."""
     ve = branch_voltage(el, v)
     cur = np.where(active, el["g"] * ve + Ih, 0.0)
     Ih_new = np.where(active, el["alpha"] * ve + el["beta"] * cur, 0.0)

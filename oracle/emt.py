@@ -29,7 +29,8 @@ FAULT_OFF = 2
 
 
 class Network:
-    """Element data, conductance graph and tree of one network at a given dt."""
+    """Element data, conductance graph (Eq. 1's G, Sec. II) and partition tree (Sec. III-B) of
+    one network at a given dt."""
 
     def __init__(self, net: dict, dt: float, levels: int = 0, d_th: int = 0, want_tree: bool = True):
         self.net = net
@@ -47,6 +48,9 @@ class Network:
 
 
 class _Solver:
+    """Eq. 2's v = G^{-1} i with one of the three solvers of the module header, and the change
+    of G at an event: refactor, rebuild, or Algorithm 2 (Sec. IV)."""
+
     def __init__(self, nw: Network, kind: str):
         self.nw = nw
         self.kind = kind
@@ -59,9 +63,11 @@ class _Solver:
             self.s = _hinv.HInv(self.G, nw.tree, nw.g_series, mode)
 
     def solve(self, rhs):
+        """v = G^{-1} rhs (Eq. 2)."""
         return self.s.solve(rhs) if self.kind == "dense" else self.s.apply(rhs)
 
     def change(self, a, b, delta, key=None):
+        """G' = G + delta u u^T (Sec. IV) and the matching change of the solver."""
         self.G = _modify.modified_G(self.G, a, b, delta)
         if self.kind == "dense":
             self.s = _dense.DenseSolver(self.G)
@@ -71,16 +77,19 @@ class _Solver:
             self.s = _modify.algorithm2(self.s, self.nw.series_frm, self.nw.series_to, a, b, delta)
 
     def push(self, key):
+        """Save G and the solver before a fault is switched in (the fault reading above)."""
         self.saved[key] = (self.G.copy(), self.s)
 
     def pop(self, key):
+        """Restore the pre-fault G and solver when the fault is switched out."""
         self.G, self.s = self.saved.pop(key)
 
 
 def simulate(nw: Network, nsteps: int, events=(), solver: str = "dense", monitor=None,
              src_scale=None, load_scale=None, first_step: int = 1, init=None):
-    """Run nsteps steps; return v at the monitored buses per step [nsteps, n_mon]
-    (all buses when monitor is None) and the final state dict."""
+    """Run nsteps steps of Eq. 1 solved as Eq. 2 (Sec. II), with the events and readings of the
+    module header; return v at the monitored buses per step [nsteps, n_mon] (all buses when
+    monitor is None) and the final state dict."""
     net, el = nw.net, nw.el
     n = net["n_bus"]
     ne = len(el["g"])

@@ -35,12 +35,14 @@ PAPER = 1
 
 
 def _perm_matrix(G: np.ndarray, tree: dict) -> np.ndarray:
+    """G in the nested ordering of the partition (Sec. III-B), so every node is a range."""
     p = tree["perm"]
     return G[np.ix_(p, p)]
 
 
 class HInv:
-    """Factored store over the tree, in the nested ordering `tree['perm']`."""
+    """The hierarchical store of Sec. III (Algorithm 1 for PAPER, Woodbury cores for EXACT; see
+    the module header), over the tree in the nested ordering `tree['perm']`."""
 
     def __init__(self, G: np.ndarray, tree: dict, g_branch: np.ndarray, mode: int = EXACT):
         self.tree = tree
@@ -60,10 +62,12 @@ class HInv:
 
     # -- construction -----------------------------------------------------
     def node_range(self, p):
+        """Positions [lo, hi) of node p in the nested ordering (Sec. III-B)."""
         return int(self.tree["lo"][p]), int(self.tree["hi"][p])
 
     def cut_columns(self, p):
-        """h_l, h_r of node p (dense, n_l x k and n_r x k)."""
+        """h_l, h_r of node p (dense, n_l x k and n_r x k): H = h_l h_r^T of Eq. 3, one column per
+    cut branch (Sec. III-A, before Eq. 9)."""
         t = self.tree
         l, r = int(t["left"][p]), int(t["right"][p])
         ll, lh = self.node_range(l)
@@ -79,6 +83,8 @@ class HInv:
         return hl, hr
 
     def _build_node(self, p):
+        """Algorithm 1 at node p: a leaf's direct inverse, or P, Q of Eq. 9 from the children's
+        stores and the node's core (PAPER: [[0, I], [I, 0]]; EXACT: S^{-1})."""
         t = self.tree
         lo, hi = self.node_range(p)
         if t["left"][p] < 0:
@@ -100,8 +106,8 @@ class HInv:
 
     # -- application --------------------------------------------------------
     def apply_node(self, p, X: np.ndarray) -> np.ndarray:
-        """Ginv_p @ X by the recursive definition: children first, then the
-        correction -Y C Y^T X of node p."""
+        """Ginv_p @ X by the recursive definition (Eq. 4 with Eq. 9's factors): children first,
+        then the correction -Y C Y^T X of node p."""
         t = self.tree
         X = np.asarray(X, float)
         if t["left"][p] < 0:
@@ -118,7 +124,7 @@ class HInv:
         return np.concatenate([Yl - P @ s[:k], Yr - Q @ s[k:]], axis=0)
 
     def apply(self, x: np.ndarray) -> np.ndarray:
-        """v = Ginv i with x, v in the original bus order."""
+        """v = Ginv i (Eq. 2) with x, v in the original bus order."""
         perm = self.tree["perm"]
         x = np.asarray(x, float)
         y = self.apply_node(0, x[perm])
@@ -127,11 +133,13 @@ class HInv:
         return out
 
     def dense_node(self, p) -> np.ndarray:
+        """Ginv_p as a dense matrix (applied to the identity), nested order."""
         lo, hi = self.node_range(p)
         return self.apply_node(p, np.eye(hi - lo))
 
     def dense(self) -> np.ndarray:
-        """Ginv in the original bus order."""
+        """Ginv (Sec. III's approximation for PAPER, the exact inverse for EXACT) in the original
+    bus order; Fig. 5 compares the two."""
         perm = self.tree["perm"]
         D = self.dense_node(0)
         out = np.empty_like(D)

@@ -29,6 +29,8 @@ from .partition import leaf_of, lca
 
 
 def find_branch(frm, to, a: int, b: int) -> int:
+    """The lowest-id series branch joining a and b (-1 if none): the branch a change between two
+    buses is carried by (module header)."""
     for e, (x, y) in enumerate(zip(frm, to)):
         if (int(x) == a and int(y) == b) or (int(x) == b and int(y) == a):
             return e
@@ -36,6 +38,7 @@ def find_branch(frm, to, a: int, b: int) -> int:
 
 
 def modified_G(G: np.ndarray, a: int, b: int, delta: float) -> np.ndarray:
+    """G' = G + delta u u^T for a change between a and b, or at a alone when b < 0 (Sec. IV)."""
     G = np.array(G, float)
     G[a, a] += delta
     if b >= 0:
@@ -46,6 +49,7 @@ def modified_G(G: np.ndarray, a: int, b: int, delta: float) -> np.ndarray:
 
 
 def u_vector(n: int, a: int, b: int) -> np.ndarray:
+    """u = e_a - e_b, or e_a for a change to ground (Sec. IV)."""
     u = np.zeros(n)
     u[a] = 1.0
     if b >= 0:
@@ -54,7 +58,9 @@ def u_vector(n: int, a: int, b: int) -> np.ndarray:
 
 
 def touched_path(tree: dict, a_pos: int, b_pos: int, to_root: bool):
-    """Leaves re-inverted and internal nodes recomputed (children first)."""
+    """Algorithm 2's touched set (Sec. IV): the leaves holding a and b, re-inverted, and the
+    internal nodes on their paths up to the lowest common ancestor (to the root when to_root),
+    recomputed children first."""
     la = leaf_of(tree, a_pos)
     lb = leaf_of(tree, b_pos) if b_pos >= 0 else la
     top = lca(tree, la, lb)
@@ -105,7 +111,8 @@ def algorithm2(store: HInv, series_frm, series_to, a: int, b: int, delta: float,
 
 
 def rebuild(store: HInv, series_frm, series_to, a: int, b: int, delta: float) -> HInv:
-    """Explicit recomputation of the whole store on G'."""
+    """Explicit recomputation of the whole store on G' (Algorithm 1 again), the reference of
+    Sec. IV's local modification."""
     t = store.tree
     G = np.empty_like(store.Gp)
     perm = t["perm"]

@@ -41,7 +41,8 @@ _NEG = np.int64(-(1 << 60))
 
 def _local_graph(V: np.ndarray, frm: np.ndarray, to: np.ndarray):
     """Induced subgraph on V (sorted global ids): neighbour lists (ascending,
-    unique) and weights (branch multiplicities)."""
+    unique) and weights (branch multiplicities), the graph one bisection of
+    Sec. III-B works on."""
     n = len(V)
     loc = {int(g): i for i, g in enumerate(V)}
     w = [dict() for _ in range(n)]
@@ -60,6 +61,7 @@ def _local_graph(V: np.ndarray, frm: np.ndarray, to: np.ndarray):
 
 
 def _bfs(nbr, start, n):
+    """Breadth-first distances and visit order from `start` (step 1 of the module header)."""
     dist = np.full(n, -1, np.int64)
     dist[start] = 0
     q = deque([start])
@@ -75,6 +77,7 @@ def _bfs(nbr, start, n):
 
 
 def _start_vertex(nbr, n):
+    """Step 1: the pseudo-peripheral start vertex (two BFS sweeps, ties to the smallest id)."""
     s = 0
     for _ in range(2):
         dist, _ = _bfs(nbr, s, n)
@@ -84,6 +87,7 @@ def _start_vertex(nbr, n):
 
 
 def _growth_order(nbr, start, n):
+    """Step 2: BFS growth order from the start vertex, restarting at the smallest unvisited id."""
     seen = np.zeros(n, bool)
     order = []
     roots = [start] + list(range(n))
@@ -103,6 +107,8 @@ def _growth_order(nbr, start, n):
 
 
 def _kl(side: np.ndarray, nbr, wt, passes: int = 4) -> np.ndarray:
+    """Step 3: Kernighan-Lin refinement of the two sides, minimising the cut branches that
+    Sec. III-B asks the bisection to minimise."""
     n = len(side)
     side = side.copy()
     for _ in range(passes):
@@ -150,7 +156,8 @@ def _kl(side: np.ndarray, nbr, wt, passes: int = 4) -> np.ndarray:
 
 
 def bisect(V: np.ndarray, frm: np.ndarray, to: np.ndarray):
-    """Split sorted global id set V into (left, right), both sorted."""
+    """One bisection of Sec. III-B (steps 1-4 of the module header): split the sorted global id
+    set V into (left, right), both sorted."""
     n = len(V)
     nbr, wt = _local_graph(V, frm, to)
     start = _start_vertex(nbr, n)
@@ -167,6 +174,8 @@ def bisect(V: np.ndarray, frm: np.ndarray, to: np.ndarray):
 
 
 def cut_size(V_left, V_right, frm, to) -> int:
+    """Branches between the two halves: the quantity a bisection minimises (Sec. III-B) and the
+    rank k of H (Sec. III-A)."""
     L = set(int(x) for x in V_left)
     R = set(int(x) for x in V_right)
     c = 0
@@ -180,8 +189,9 @@ def cut_size(V_left, V_right, frm, to) -> int:
 
 
 def build_tree(n_bus: int, frm: np.ndarray, to: np.ndarray, levels: int = 0, d_th: int = 0) -> dict:
-    """Recursive bisection tree. `frm/to` are the bus-to-bus branches (series
-    branch ids are their positions in these arrays; to < 0 entries are ignored)."""
+    """The partition tree of Sec. III-B (Fig. 2-3) by recursive bisection, with step 5's stopping
+    rule. `frm/to` are the bus-to-bus branches (series branch ids are their positions in these
+    arrays; to < 0 entries are ignored)."""
     frm = np.asarray(frm, np.int64)
     to = np.asarray(to, np.int64)
     buses = [np.arange(n_bus, dtype=np.int64)]
@@ -212,6 +222,7 @@ def build_tree(n_bus: int, frm: np.ndarray, to: np.ndarray, levels: int = 0, d_t
     leaves = []
 
     def dfs(p):
+        # leaves left to right give the nested ordering; every node becomes a range
         lo[p] = len(perm)
         if left[p] < 0:
             perm.extend(int(x) for x in buses[p])
@@ -252,6 +263,7 @@ def build_tree(n_bus: int, frm: np.ndarray, to: np.ndarray, levels: int = 0, d_t
 
 
 def leaf_of(tree: dict, position: int) -> int:
+    """The leaf holding a position: where Algorithm 2 starts (Sec. IV)."""
     for j in tree["leaves"]:
         if tree["lo"][j] <= position < tree["hi"][j]:
             return int(j)
@@ -259,7 +271,8 @@ def leaf_of(tree: dict, position: int) -> int:
 
 
 def lca(tree: dict, u: int, v: int) -> int:
-    """Lowest common ancestor of two tree nodes by walking parent pointers."""
+    """Lowest common ancestor of two tree nodes by walking parent pointers (the LCA that
+    Algorithm 2 updates up to, Sec. IV)."""
     anc = set()
     x = u
     while x >= 0:
