@@ -9,6 +9,8 @@ namespace emt {
 
 namespace {
 
+// Leaf stage of v = G^{-1} i (Eq. 2 with the leaf blocks of Sec. III): CTA c forms the partial
+// products of its rows of the leaf inverse with its slice of x.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_apply_partial(DStore st, CtaMapD cm, const double* __restrict__ src,
                                                                  int src_pos, typename Acc<PREC>::X* __restrict__ part) {
@@ -29,6 +31,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_apply_partial(DStore st, CtaM
   leaf_partial_core<PREC>(st, j, r0, r1, xs, part + (int64_t)c * cm.pld, red);
 }
 
+// Boundary sweep (t_p = [h_l^T y_l; h_r^T y_r], s_p = C_p t_p with Eq. 9's factors) and the
+// expansion v = y - sum over ancestors of (factor row . s) for the CTA's rows.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_apply_sweep(DStore st, CtaMapD cm, CutRowsD cr,
                                                                const typename Acc<PREC>::X* __restrict__ part,
@@ -61,7 +65,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_apply_sweep(DStore st, CtaMap
   }
 }
 
-// r_pos = i - G v (FP64, position-ordered CSR), i bus-ordered or position-ordered
+// r_pos = i - G v with Eq. 1's G (FP64, position-ordered CSR), i bus-ordered or position-ordered:
+// the residual that refines an FP32 apply
 __global__ void k_residual(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                            const double* __restrict__ val, const int* __restrict__ perm, const double* __restrict__ src,
                            int src_pos, const double* __restrict__ v_pos, double* __restrict__ r_pos) {
@@ -72,11 +77,13 @@ __global__ void k_residual(int n, const int* __restrict__ ptr, const int* __rest
   r_pos[i] = acc;
 }
 
+// position order (the nested ordering of Sec. III-B) -> bus order
 __global__ void k_scatter(int n, const int* __restrict__ perm, const double* __restrict__ v_pos, double* __restrict__ v_bus) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v_bus[perm[i]] = v_pos[i];
 }
 
+// -g per cut column (h_l[:, e] = -g_e e_a, Sec. III-A) in the three precisions
 __global__ void k_neg_g(int n, const double* __restrict__ g, double* __restrict__ g64, float2* __restrict__ gff,
                         float* __restrict__ g32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -33,6 +33,8 @@ __device__ __forceinline__ int anc_at_depth(const DStore& st, int q, int d) {
 }
 
 // ------------------------------------------------------------------ leaf blocks
+// Leaf blocks G_jj of Algorithm 1's direct inversion (Sec. III-B): cleared, then assembled from
+// the CSR copy of G.
 __global__ void k_zero_leaf(DStore st, const int* leaves) {
   const int j = leaves[blockIdx.x];
   const int node = st.leaf_node[j];
@@ -57,7 +59,8 @@ __global__ void k_assemble_leaf(DStore st, const int* __restrict__ csr_ptr, cons
   }
 }
 
-// In-place lower Cholesky of one leaf block per CTA (right looking, column by column).
+// In-place lower Cholesky of one leaf block per CTA (right looking, column by column): the first
+// step of the direct leaf inversion of Algorithm 1 (Sec. III-B).
 __global__ void k_chol(DStore st, const int* leaves) {
   extern __shared__ double colk[];
   const int j = leaves[blockIdx.x];
@@ -101,7 +104,7 @@ __global__ void k_chol(DStore st, const int* leaves) {
   }
 }
 
-// W = L^{-1} column by column (thread per column).
+// W = L^{-1} column by column (thread per column), direct leaf inversion (Algorithm 1).
 __global__ void k_trinv(DStore st, double* __restrict__ W, const int* leaves) {
   const int j = leaves[blockIdx.x];
   const int node = st.leaf_node[j];
@@ -120,7 +123,8 @@ __global__ void k_trinv(DStore st, double* __restrict__ W, const int* leaves) {
   }
 }
 
-// G_jj^{-1} = W^T W (row i per CTA, j <= i by threads), written symmetric.
+// G_jj^{-1} = W^T W (row i per CTA, j <= i by threads), written symmetric: the leaf inverse of
+// Algorithm 1 (Sec. III-B).
 __global__ void k_wtw(DStore st, const double* __restrict__ W, const int* leaves) {
   const int j = leaves[blockIdx.x];
   const int node = st.leaf_node[j];
@@ -252,7 +256,8 @@ __global__ void k_level_expand(DStore st, int modeB, const int* flag, int d, int
   }
 }
 
-// Leaf stage of a dense multi-vector apply: Y[i] = L_j X[leaf rows] (row-major panels).
+// Leaf stage of a dense multi-vector apply (Eq. 2 with Sec. III's leaf blocks): Y[i] = L_j X[leaf
+// rows] (row-major panels).
 __global__ void k_leaf_dense(DStore st, const double* __restrict__ X, double* __restrict__ Y, int m, int ld) {
   const int i = blockIdx.x;
   const int j = st.pos_leaf[i];
@@ -267,6 +272,9 @@ __global__ void k_leaf_dense(DStore st, const double* __restrict__ X, double* __
 }
 
 // ------------------------------------------------------------------ node cores
+// Core of each node (Sec. III): PAPER mode C = [[0, I], [I, 0]] (Eq. 9's M = -P Q^T); EXACT mode
+// C = S^{-1}, S = [[h_l^T P, I], [I, h_r^T Q]] (the Woodbury form of Eq. 3's split), inverted by
+// Gauss-Jordan with partial pivoting in FP64.
 // ws: null (the core is inverted in shared memory), or a workspace of ws_stride doubles and
 // ws_stride / m2max pivots per CTA in global memory for cores larger than kMaxCoreDim.
 __global__ void k_core(DStore st, const int* nodes, int mode, double* ws, int* ws_piv, int64_t ws_stride,
@@ -355,6 +363,7 @@ __global__ void k_core(DStore st, const int* nodes, int mode, double* ws, int* w
 }
 
 // ------------------------------------------------------------------ precision copies
+// Float-float and FP32 copies of the FP64 store that the apply kernels read.
 __global__ void k_pack(const double* __restrict__ src, float2* __restrict__ ff, float* __restrict__ f32, int64_t n) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const double x = src[t];
@@ -366,7 +375,8 @@ __global__ void k_pack(const double* __restrict__ src, float2* __restrict__ ff, 
 }
 
 // ------------------------------------------------------------------ exact local modification
-// z of one path node q: leaf -> columns of the leaf inverse; internal ->
+// Sec. IV: G' = G + delta u u^T, applied exactly at every node on the paths from the touched leaves
+// to the root (Sherman-Morrison with the old store's z). z of one path node q: leaf -> columns of the leaf inverse; internal ->
 // z_q = [x_l; x_r] - Y S^{-1} [h_l^T x_l; h_r^T x_r] (old store), then d_q = 1 + delta u_q^T z_q.
 struct ModItem {
   int node, is_leaf;
@@ -435,6 +445,8 @@ __global__ void k_mod_z(DStore st, ModItem it, double* __restrict__ z, double* _
   }
 }
 
+// d_q = 1 + delta u_q^T z_q in FP64 (Sherman-Morrison, Sec. IV); a non-positive d would make G'
+// indefinite and is reported as DEV_SINGULAR.
 __global__ void k_mod_denominator(DStore st, ModItem it, const double* __restrict__ z, double* __restrict__ dv,
                                   double delta) {
   const int q = it.node;
@@ -447,6 +459,8 @@ __global__ void k_mod_denominator(DStore st, ModItem it, const double* __restric
   if (!(d > 1e-12)) atomicExch(st.status, DEV_SINGULAR);
 }
 
+// Rank-one update of a touched leaf inverse: L_j' = L_j - (delta/d) z z^T (Sherman-Morrison on the
+// leaf block, Sec. IV).
 __global__ void k_mod_leaf(DStore st, ModItem it, const double* __restrict__ z, const double* __restrict__ dv,
                            double delta) {
   if (*st.status != DEV_OK) return;
@@ -505,11 +519,13 @@ __global__ void k_mod_factor(DStore st, ModItem it, const double* __restrict__ z
   }
 }
 
+// New conductance of a cut column after a change of its branch (Sec. IV).
 __global__ void k_set_cut_g(DStore st, int idx, double g) {
   if (*st.status != DEV_OK) return;
   st.cut_g[idx] = g;
 }
 
+// G' = G + delta u u^T on the CSR copy (Sec. IV): up to four entries change.
 __global__ void k_csr_add(double* val, int i0, int i1, int i2, int i3, double d0, double d1, double d2, double d3,
                           const int* status) {
   if (*status != DEV_OK) return;
