@@ -81,11 +81,12 @@ __device__ __forceinline__ bool change_on(const MSimD& m, int c, int step) {
   return m.trip_step[c] > 0 && step >= m.trip_step[c] && step < m.trip_off[c];
 }
 
-// History update of every element and injection. A CTA takes `ipp` consecutive positions (1, 2,
-// 4 or 8) and 256 columns, one per thread. The element-end records and row pointers of its
-// positions are staged in shared memory first, so that each position then costs one round trip to
-// memory: its voltage, the other ends' voltages, the old histories (up to IKB ends) and the source
-// terms (up to ITB) are all loaded before any arithmetic.
+// History update of every element and injection: i = i_in(t) + i_his(t - dt) of Eq. 1 with the
+// trapezoidal companion sources (Sec. II), for every column. A CTA takes `ipp` consecutive
+// positions (1, 2, 4 or 8) and 256 columns, one per thread. The element-end records and row
+// pointers of its positions are staged in shared memory first, so that each position then costs
+// one round trip to memory: its voltage, the other ends' voltages, the old histories (up to IKB
+// ends) and the source terms (up to ITB) are all loaded before any arithmetic.
 constexpr int IPP_MAX = 8, ITH = 256, IKB = 6, ITB = 2;
 __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in_chunk, int* status) {
   extern __shared__ __align__(16) unsigned char ism[];
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
   }
 }
 
-// Leaf stage as a GEMM over the columns: Y[leaf rows] = L_j (FP32) * Xf[leaf rows].
+// Leaf stage as a GEMM over the columns (Eq. 2 with Sec. III's leaf blocks):
+// Y[leaf rows] = L_j (FP32) * Xf[leaf rows].
 // Tile 64 x 128, K step 16, 256 threads with an 8 x 4 register tile.
 constexpr int GBM = 64, GBN = 128, GBK = 16;
 __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restrict__ tiles,
@@ -249,17 +251,19 @@ __global__ void __launch_bounds__(256) k_mc_gemm(DStore st, const int4* __restri
   }
 }
 
-// Boundary sweep of all columns as one product: S = K Y_cut, K = the matrix of the sweep
-// (s_total x n_crow, FP32, built on the device from the sweep image and kept transposed so that a
-// chunk is read and staged without bank conflicts), Y_cut = the leaf-stage rows at the distinct
-// cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows inside its
-// subtree, so each 32-row tile of S runs over the column range of K holding its nonzeros, cut into
-// pieces of 32..128 columns (the longest giving about four CTAs per SM; work item = tile, piece). A CTA forms the 32 x 64 product of one
-// piece in 32-deep chunks (128 threads, a 4 x 4 block of outputs each, from 16-byte shared-memory
-// reads; the next chunk is loaded into registers while the current one is multiplied). A tile of a
-// single piece writes S; otherwise each piece writes its partial to global memory and the CTA that
-// completes the tile (an atomic count per tile) adds the partials in piece order, so the result
-// does not depend on timing, and resets the count.
+// Boundary sweep of all columns as one product (Sec. III: Eq. 9's t_p and s_p = C_p t_p of every
+// node are linear in the leaf-stage values at the cut rows): S = K Y_cut, K = the matrix of the
+// sweep (s_total x n_crow, FP32, built on the device from the sweep image and kept transposed so
+// that a chunk is read and staged without bank conflicts), Y_cut = the leaf-stage rows at the
+// distinct cut rows. K is block-sparse: the rows of S of a node depend only on the cut rows inside
+// its subtree, so each 32-row tile of S runs over the column range of K holding its nonzeros, cut
+// into pieces of 32..128 columns (the longest giving about four CTAs per SM; work item = tile,
+// piece). A CTA forms the 32 x 64 product of one piece in 32-deep chunks (128 threads, a 4 x 4
+// block of outputs each, from 16-byte shared-memory reads; the next chunk is loaded into registers
+// while the current one is multiplied). A tile of a single piece writes S; otherwise each piece
+// writes its partial to global memory and the CTA that completes the tile (an atomic count per
+// tile) adds the partials in piece order, so the result does not depend on timing, and resets the
+// count.
 constexpr int SBM = 32, SBN = 64, SBK = 32, SBT = 128, SPIECE = 128;
 __global__ void __launch_bounds__(SBT) k_mc_sweep_gemm(MSimD m, const float* __restrict__ Kt, int ldt,
                                                        const int4* __restrict__ items, float* part, int* count,
@@ -434,7 +438,8 @@ __global__ void k_mc_fcol(DStore st, MSimD m, int s_in_chunk, const int* status)
   m.fcol[c] = f;
 }
 
-// Expansion (+ N-1 correction) as a tiled product per leaf: for a tile of up to 32 positions of
+// Expansion with Eq. 9's factors (+ the N-1 Sherman-Morrison correction of Sec. IV) as a tiled
+// product per leaf: for a tile of up to 32 positions of
 // one leaf and 128 columns, V = Y - F_path S_path, where F_path holds the tile's factor rows of all
 // its ancestors (the same ancestors and halves for every position of a leaf) and S_path the
 // matching rows of S. Path elements are taken in chunks of 16: the S chunk (16 x 128) and the F
@@ -529,7 +534,8 @@ __global__ void __launch_bounds__(XT) k_mc_expand_tiled(DStore st, MSimD m, cons
   }
 }
 
-// r = x - G' v (float-float), stored as the FP32 input of the correction apply. Same shape as the
+// r = x - G' v (float-float; Eq. 1's G with each column's own change of Sec. IV), stored as the
+// FP32 input of the correction apply. Same shape as the
 // injection: `ipp` positions x 256 columns per CTA, the CSR rows of its positions staged in shared
 // memory, then one round trip per position (up to RKB entries per batch).
 constexpr int RKB = 8;
@@ -585,7 +591,7 @@ __global__ void __launch_bounds__(ITH) k_mc_residual(MSimD m, int ipp, int n1, i
   }
 }
 
-// d_c = 1 + delta_c u_c^T z_c (FP64) and the Sherman-Morrison factor delta_c / d_c
+// d_c = 1 + delta_c u_c^T z_c (FP64) and the Sherman-Morrison factor delta_c / d_c (Sec. IV)
 __global__ void k_mc_trip_coef(MSimD m, double* coef, int* status) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.R) return;
@@ -605,6 +611,7 @@ __global__ void k_mc_trip_coef(MSimD m, double* coef, int* status) {
   coef[c] = m.trip_delta[c] / d;
 }
 
+// Right-hand sides u_c = e_a - e_b (or e_a) of the columns' changes, for z_c = G^{-1} u_c (Sec. IV).
 __global__ void k_mc_unit(MSimD m, float2* X, float* Xf) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.R || m.trip_step[c] <= 0) return;
@@ -643,6 +650,7 @@ __global__ void k_mc_rotate_terms(MSimD m, const double* __restrict__ base, floa
   sn[(int64_t)t * m.R + c] = make_float2(yh, (float)(y - (double)yh));
 }
 
+// z_c of column c (its change's G^{-1} u_c, Sec. IV) as float-float.
 __global__ void k_mc_set_z(MSimD m, float2* Z, const double* __restrict__ zpos, int c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n) return;
@@ -651,6 +659,7 @@ __global__ void k_mc_set_z(MSimD m, float2* Z, const double* __restrict__ zpos, 
   Z[(int64_t)i * m.R + c] = make_float2(h, (float)(v - (double)h));
 }
 
+// d_c and delta_c / d_c of one column (Sec. IV), when a column starts afresh.
 __global__ void k_mc_one_coef(MSimD m, double* coef, int c, int* status) {
   const int64_t R = m.R;
   const float2 za = m.Z[(int64_t)m.trip_a[c] * R + c];
