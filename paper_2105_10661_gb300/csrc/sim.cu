@@ -35,6 +35,8 @@ __device__ __forceinline__ double element_history(double vi, double vo, int sgn,
   return sgn > 0 ? -Ihn : Ihn;   // contribution to i_his at this end
 }
 
+// First-generation partial kernel: history update and injection of the owned rows (Eq. 1), then
+// the leaf stage of Eq. 2 over them.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_step_partial(DStore st, CtaMapD cm, SimD sim, int s_in_chunk,
                                                                 int pass, typename Acc<PREC>::X* __restrict__ part) {
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_partial(DStore st, CtaMa
   leaf_partial_core<PREC>(st, j, r0, r1, xs, part + (int64_t)c * cm.pld, red);
 }
 
+// First-generation sweep kernel: boundary sweep with Eq. 9's factors and the expansion to v(t).
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_step_sweep(DStore st, CtaMapD cm, CutRowsD cr, SimD sim,
                                                               int s_in_chunk, int accumulate, int record,
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_step_sweep(DStore st, CtaMapD
   }
 }
 
+// Step counter of the captured graphs (the step number lives in device memory).
 __global__ void k_advance(SimDyn* dyn, int n) { dyn->step_base += n; }
 __global__ void k_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec) {
   dyn->step_base = step_base;
@@ -124,7 +128,8 @@ __global__ void k_set_dyn(SimDyn* dyn, int step_base, int rec_first, double* rec
   dyn->rec = rec;
   dyn->trig_first = rec_first;
 }
-// Trip: the element leaves G; its parameters and both history copies are zeroed.
+// Trip (Sec. IV's change G' = G - g u u^T): the element leaves G; its parameters and both history
+// copies are zeroed.
 __global__ void k_open_element(double* g, double* alpha, double* beta, double* Ih, int m0, int m1) {
   for (int m : {m0, m1})
     if (m >= 0) {

@@ -89,6 +89,7 @@ __global__ void k_img_refresh(DStore st, unsigned char* img, int off_g, int n_cu
   }
 }
 
+// sin and cos of w t per step for the source injections of Eq. 1's i_in (FP64 and float-float).
 __global__ void k_trig(double* trig, float4* trigff, int first_step, int n, double omega, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -106,6 +107,8 @@ constexpr int kMaxNnz = 16;     // CSR row length prefetched into registers (hos
 constexpr int kGatherUnroll = 8;
 constexpr int kGroup = 8;       // threads per dot product in the sweep
 
+// Second-generation partial kernel: history update and injection (Eq. 1), then the leaf stage of
+// Eq. 2 over the CTA's rows, with static loads issued before griddepcontrol.wait.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_step2_partial(DStore st, CtaMapD cm, SimD sim, Step2D q,
                                                                  int s_in_chunk, int pass,
@@ -231,6 +234,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_step2_partial(DStore st, CtaM
 }
 
 // ------------------------------------------------------------------ sweep kernel
+// Boundary sweep of every node from the shared-memory image (t_p and s_p = C_p t_p, Eq. 9's
+// factors) and the expansion of the CTA's rows to v(t).
 template <int PREC, bool FROMY = false>
 __global__ void __launch_bounds__(kFusedThreads) k_step2_sweep(DStore st, CtaMapD cm, SimD sim, Step2D q,
                                                                int s_in_chunk, int accumulate, int record,

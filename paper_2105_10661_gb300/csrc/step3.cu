@@ -61,6 +61,7 @@ __device__ __forceinline__ bool bar3_wait(uint64_t* bar) {
   }
 }
 
+// Cluster leaf stage of Eq. 2 with the history update and injection of Eq. 1 (header above).
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_step3_partial(DStore st, SimD sim, Step2D q, int cs, int s_in_chunk,
                                                                  int pass, int max_rows, double* __restrict__ ylf) {
