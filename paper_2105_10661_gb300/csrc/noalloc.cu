@@ -46,6 +46,7 @@ __device__ __forceinline__ bool cta_rows(const DStore& st, int cpl, int& j, int&
   return r0 < b;
 }
 
+// Leaf stage of v = G^{-1} i (Eq. 2, Sec. III's leaf blocks) into the fixed scratch array.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_na_partial(DStore st, const double* __restrict__ i_dev,
                                                               typename Acc<PREC>::X* __restrict__ part, int cpl,
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_na_partial(DStore st, const d
   leaf_partial_core<PREC>(st, j, r0, r1, xs, part + (int64_t)blockIdx.x * pld, red);
 }
 
+// Boundary sweep (Eq. 9's factors and the node cores) and expansion of the CTA's rows to v.
 template <int PREC>
 __global__ void __launch_bounds__(kFusedThreads) k_na_sweep(DStore st, const typename Acc<PREC>::X* __restrict__ part,
                                                             int cpl, int pld, const int* __restrict__ g_item_node,

@@ -116,7 +116,8 @@ __device__ __forceinline__ typename Acc<PREC>::X warp_sum(const Acc<PREC>& a, in
 __device__ __forceinline__ void pdl_wait_s() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_go_s() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Stages [st0[c], st0[c + 1]) of CTA c: a contiguous range of leaf rows (rows = positions), one or
+// Leaf stage of Eq. 2 (Sec. III's leaf blocks), streamed. Stages [st0[c], st0[c + 1]) of CTA c: a
+// contiguous range of leaf rows (rows = positions), one or
 // two rows of one leaf per stage; y in position order, vector type. y_cut (the distinct cut rows,
 // in their order) is written as well. The x window [win[c].x, win[c].y) is gathered before the
 // first copy is issued, so the gather does not queue behind the stream.
@@ -318,7 +319,8 @@ __global__ void __launch_bounds__(kLT, 1) k_leaf_ldg(DStore st, const int* __res
   }
 }
 
-// s = K y_cut: y_cut staged in shared memory, one warp per row of K
+// s = K y_cut, the boundary sweep of every node (Eq. 9's t_p and s_p = C_p t_p are linear in the
+// cut-row values): y_cut staged in shared memory, one warp per row of K
 template <int PREC>
 __global__ void __launch_bounds__(128) k_sweep_matrix(const typename Acc<PREC>::T* __restrict__ K, int s_total, int ldk,
                                                       int n_crow, const typename Acc<PREC>::X* ycut_g,
@@ -359,7 +361,8 @@ __global__ void __launch_bounds__(128) k_sweep_matrix(const typename Acc<PREC>::
   if (lane == 0) s[row] = v;
 }
 
-// v = y - sum over ancestors of F row . s(half); 16 lanes per position, two positions per warp.
+// v = y - sum over ancestors of F row . s(half) (the expansion with Eq. 9's factors); 16 lanes per
+// position, two positions per warp.
 // s and the ancestor records sit in shared memory. A lane takes elements lane + 16 m (m < 4) of
 // every ancestor's factor row (k <= 64 per pass; longer rows take further passes), and the loads
 // of up to kMaxAnc ancestors (deeper paths take further rounds) are all issued before the first
