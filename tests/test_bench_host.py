@@ -235,3 +235,15 @@ def test_hier_solve_flops_single_leaf_is_dense_matvec():
     tree = {"lo": [0], "hi": [n], "left": [-1], "right": [-1], "cut_ptr": [0, 0]}
     assert bench.hier_solve_flops(tree) == 2 * n * n - n
     assert bench.leaf_inverse_flops(1) == 3   # sqrt, reciprocal, one product
+
+
+def test_flop_table_row_on_one_tile():
+    rows = bench.flop_table(shapes=((1, 1),), dths=(45, 179))
+    r = rows[0]
+    assert r["n_bus"] == 179
+    assert r["solve_paper_dth179"] == r["dense_matvec"] == 2 * 179 * 179 - 179   # one leaf: the dense inverse
+    assert r["alg1_build_dth179"] == bench.leaf_inverse_flops(179)
+    assert r["alg2_fault_dth179"] == r["alg1_build_dth179"]                       # the only leaf is touched
+    assert "alg2_root_trip_dth179" not in r                                       # a single leaf has no cuts
+    assert r["solve_paper_dth45"] < r["solve_exact_dth45"] < r["dense_matvec"]
+    assert r["alg2_fault_dth45"] < r["alg2_root_trip_dth45"] < r["alg1_build_dth45"]
