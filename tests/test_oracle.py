@@ -576,3 +576,93 @@ def test_three_phase_exact_store_equals_dense_inverse():
     H = hinv.HInv(G, tree, gr["g"][ser], hinv.EXACT)
     X = np.random.default_rng(3).standard_normal((gr["n_bus"], 2))
     assert np.allclose(H.apply(X), np.linalg.solve(G, X), rtol=0, atol=1e-12 * np.abs(np.linalg.solve(G, X)).max())
+
+
+# ---------------------------------------------------------------- three-phase stepping
+def _with_loads(net):
+    out = dict(net)
+    out.update(load_bus=np.array([1, 4, 9], np.int32), load_amp=np.array([0.05, 0.08, 0.03]),
+               load_phi=np.array([0.3, -0.2, 1.1]))
+    return out
+
+
+def test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs():
+    # L_mut = 0 decouples the phases: phase p of every bus follows the single-phase stepping of the
+    # same network with its sources and loads shifted by -2 pi p / 3, trip included
+    from oracle import emt3
+    net = _with_loads(netgen.small_network(13, 77))
+    net3 = netgen.three_phase(net)
+    net3["L_mut"] = np.zeros(len(net["br_a"]))
+    trip = 5
+    got, _ = emt3.simulate3(net3, DT, 160, [(80, emt3.TRIP, trip, 0.0)])
+    for p in range(3):
+        netp = dict(net)
+        netp["src_phi"] = np.asarray(net["src_phi"]) + (-2 * np.pi * p / 3)
+        netp["load_phi"] = np.asarray(net["load_phi"]) + (-2 * np.pi * p / 3)
+        ref, _ = emt.simulate(emt.Network(netp, DT, want_tree=False), 160, [(80, emt.TRIP, trip, 0.0)])
+        assert np.max(np.abs(got[:, p::3] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_three_phase_balanced_steady_state_uses_positive_sequence_inductance():
+    # Balanced source (Rs) -> coupled RL branch -> bus 1 with a shunt C. Balanced currents sum to
+    # zero, so L3 i = (L - L_mut) i per phase; the trapezoidal steady state is the phasor solution
+    # with s = j (2/dt) tan(w dt / 2) (bilinear transform), each phase shifted by -2 pi p / 3.
+    from oracle import emt3
+    f, dt = 60.0, 50e-6
+    w = 2 * np.pi * f
+    Rs, R, L, M, C0, C1, V, phi = 1.0, 2.0, 10e-3, 3e-3, 20e-6, 100e-6, 1.3, 0.4
+    net = dict(n_bus=2, br_a=np.array([0], np.int32), br_b=np.array([1], np.int32), kind=np.array([0], np.int32),
+               R=np.array([R]), L=np.array([L]), C=np.zeros(1), L_mut=np.array([M]), shunt_C=np.array([C0, C1]),
+               src_bus=np.array([0], np.int32), src_Vm=np.array([V]), src_phi=np.array([phi]),
+               src_Rs=np.array([Rs]), load_bus=np.zeros(0, np.int32), load_amp=np.zeros(0), load_phi=np.zeros(0),
+               freq=f)
+    n = 8000
+    out, _ = emt3.simulate3(net, dt, n)
+    s = 1j * (2 / dt) * np.tan(w * dt / 2)
+    Zb = R + s * (L - M)
+    A = np.array([[1 / Rs + s * C0 + 1 / Zb, -1 / Zb], [-1 / Zb, s * C1 + 1 / Zb]])
+    k = np.arange(n - 400, n) + 1
+    for p in range(3):
+        E = V * np.exp(1j * (phi + (-2 * np.pi * p / 3) - np.pi / 2)) / Rs
+        Vp = np.linalg.solve(A, np.array([E, 0]))
+        ref = np.real(Vp[None, :] * np.exp(1j * w * k * dt)[:, None])
+        got = out[n - 400:, [p, 3 + p]]
+        assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_three_phase_lossless_network_conserves_energy_exactly():
+    # R = 0 and no source resistances: the trapezoidal rule keeps the quadratic invariant
+    # 1/2 sum C v^2 + 1/2 sum i^T L3 i (+ series capacitors) once the driving sinks stop
+    from oracle import emt3
+    net = _with_loads(netgen.small_network(24, 5))
+    net.update(src_bus=np.zeros(0, np.int32), src_Vm=np.zeros(0), src_phi=np.zeros(0), src_Rs=np.zeros(0))
+    net["R"] = np.zeros(len(net["br_a"]))
+    net3 = netgen.three_phase(net)
+    kind = np.asarray(net3["kind"])
+    assert (kind == cm.KIND_RL).any() and (kind == cm.KIND_RC).any()
+
+    def energy(st):
+        v = st["v"]
+        E = 0.5 * np.sum(np.repeat(net3["shunt_C"], 3) * v ** 2)
+        for e in range(len(kind)):
+            i = st["cur"][e]
+            if kind[e] == cm.KIND_RL:
+                L, M = float(net3["L"][e]), float(net3["L_mut"][e])
+                E += 0.5 * i @ ((L - M) * np.eye(3) + M * np.ones((3, 3))) @ i
+            else:
+                a, b = int(net3["br_a"][e]), int(net3["br_b"][e])
+                vc = v[3 * a:3 * a + 3] - v[3 * b:3 * b + 3]   # R = 0: the capacitor holds the branch voltage
+                E += 0.5 * float(net3["C"][e]) * vc @ vc
+        return E
+
+    # driven by the sinks for 100 steps; then free: the first free step still integrates the sinks at
+    # its start, every later one conserves the energy
+    _, state = emt3.simulate3(net3, DT, 100, monitor=[0])
+    free = dict(net3)
+    free.update(load_bus=np.zeros(0, np.int32), load_amp=np.zeros(0), load_phi=np.zeros(0))
+    _, state = emt3.simulate3(free, DT, 1, monitor=[0], init=state, first_step=101)
+    E0 = energy(state)
+    assert E0 > 0
+    for k in range(6):
+        _, state = emt3.simulate3(free, DT, 50, monitor=[0], init=state, first_step=102 + 50 * k)
+        assert abs(energy(state) - E0) <= 1e-11 * E0
