@@ -235,9 +235,23 @@ void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
 // ---------------------------------------------------------------- host side
 // Conductance graph of a network at time step dt: trapezoidal companion conductances of the
 // series branches (ids preserved) and shunt capacitors, then 1/Rs of the sources.
+// Sizes and the arrays they require (host side, before any device work): branch endpoints, kinds
+// and R for every branch, L for RL and C for RC branches, bus and resistance for every source.
+static void check_network_arrays(const emt_network* net) {
+  EMT_REQUIRE(net->n_bus >= 1 && net->n_branch >= 0 && net->n_src >= 0 && net->n_load >= 0, EMT_ERR_INVALID,
+              "bad network sizes");
+  EMT_REQUIRE(net->n_branch == 0 || (net->from && net->to && net->kind && net->R), EMT_ERR_INVALID,
+              "null branch arrays");
+  for (int e = 0; e < net->n_branch; ++e)
+    EMT_REQUIRE(net->kind[e] == EMT_KIND_RL ? net->L != nullptr : net->C != nullptr, EMT_ERR_INVALID,
+                "null L (RL branches) or C (RC branches)");
+  EMT_REQUIRE(net->n_src == 0 || (net->src_bus && net->src_Rs), EMT_ERR_INVALID, "null source arrays");
+}
+
 void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
                    std::vector<double>& gv) {
   EMT_REQUIRE(net && dt > 0, EMT_ERR_INVALID, "null network or bad dt");
+  check_network_arrays(net);
   gf.clear();
   gt.clear();
   gv.clear();
@@ -285,6 +299,7 @@ void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, 
 void network_graph3(const emt_network* net, const double* L_mut, double dt, std::vector<int32_t>& gf,
                     std::vector<int32_t>& gt, std::vector<double>& gv) {
   EMT_REQUIRE(net && L_mut && dt > 0, EMT_ERR_INVALID, "null network, null mutual inductances or bad dt");
+  check_network_arrays(net);
   gf.clear();
   gt.clear();
   gv.clear();

@@ -69,3 +69,30 @@ def test_partition_rejects_bad_input(L):
 def test_partition_accessor_rejects_null_handle(L):
     assert L.lib.emt_hinv_get_partition(None, None, None, None, None) == L.EMT_ERR_INVALID
     assert "null handle" in L.lib.emt_last_error().decode()
+
+
+def test_network_input_checks_run_before_any_device_work(L):
+    # bad element data is rejected on the host with EMT_ERR_INVALID (no GPU needed to see it)
+    import ctypes as C
+    net = netgen.small_network(5, 3)
+    nw, keep = L.make_network(net)
+    opts = L.make_opts(levels=1)
+
+    def build(n):
+        h = C.c_void_p()
+        return L.lib.emt_build_hinv_from_network(C.byref(n), 50e-6, C.byref(opts), None, C.byref(h))
+
+    bad = L.EmtNetwork.from_buffer_copy(nw)
+    bad.from_ = None
+    assert build(bad) == L.EMT_ERR_INVALID and b"null branch arrays" in L.lib.emt_last_error()
+    bad = L.EmtNetwork.from_buffer_copy(nw)
+    bad.n_bus = 0
+    assert build(bad) == L.EMT_ERR_INVALID and b"sizes" in L.lib.emt_last_error()
+    bad = L.EmtNetwork.from_buffer_copy(nw)
+    bad.src_Rs = None
+    assert build(bad) == L.EMT_ERR_INVALID and b"source" in L.lib.emt_last_error()
+    bad = L.EmtNetwork.from_buffer_copy(nw)
+    bad.L = None
+    assert build(bad) == L.EMT_ERR_INVALID and b"null L" in L.lib.emt_last_error()
+    h = C.c_void_p()
+    assert L.lib.emt_build_hinv_from_network(C.byref(nw), -1.0, C.byref(opts), None, C.byref(h)) == L.EMT_ERR_INVALID
