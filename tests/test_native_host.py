@@ -96,3 +96,18 @@ def test_network_input_checks_run_before_any_device_work(L):
     assert build(bad) == L.EMT_ERR_INVALID and b"null L" in L.lib.emt_last_error()
     h = C.c_void_p()
     assert L.lib.emt_build_hinv_from_network(C.byref(nw), -1.0, C.byref(opts), None, C.byref(h)) == L.EMT_ERR_INVALID
+
+
+@pytest.mark.parametrize("frm,to,g,mode,msg", [
+    ([0, 1, 2], [1, 2, 7], [1.0, 1.0, 1.0], 0, b"out of range"),
+    ([0, 1, 2], [1, 2, 3], [1.0, 0.0, 1.0], 0, b"nonzero"),
+    ([0, 1, 2], [1, 1, 3], [1.0, 1.0, 1.0], 0, b"self-loop"),
+    ([0, 1, 2], [1, 2, 3], [1.0, 1.0, 1.0], 5, b"bad mode")])
+def test_graph_input_checks_run_before_any_device_work(L, frm, to, g, mode, msg):
+    import ctypes as C
+    gr, keep = L.make_graph(4, frm, to, g)
+    o = L.make_opts(levels=1, mode=mode)
+    h = C.c_void_p()
+    assert L.lib.emt_build_hinv(C.byref(gr), C.byref(o), None, C.byref(h)) == L.EMT_ERR_INVALID
+    assert msg in L.lib.emt_last_error()
+    assert h.value is None
