@@ -740,6 +740,7 @@ MSimD MSim::view() const {
 MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_, const double* src_scale,
            const double* load_scale, cudaStream_t s) {
   EMT_REQUIRE(net && opts, EMT_ERR_INVALID, "null network or options");
+  check_network_arrays(net);
   EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
   EMT_REQUIRE(R_ >= 2 && R_ <= 65536, EMT_ERR_INVALID, "nrhs out of range");
   n = net->n_bus;

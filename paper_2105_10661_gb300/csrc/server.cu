@@ -111,6 +111,8 @@ Server::~Server() {
 
 int Server::add_network(const emt_network* net, const emt_hinv_opts* opts, double dt, int max_slots, int n_mon,
                         const int32_t* mon, bool fixed_slots) {
+  EMT_REQUIRE(net && opts, EMT_ERR_INVALID, "null network or options");
+  check_network_arrays(net);
   EMT_REQUIRE(max_slots >= 4 && n_mon >= 1 && mon, EMT_ERR_INVALID, "need >= 4 slots and a monitor list");
   const int64_t n = net->n_bus;
   const int64_t per_slot = per_slot_bytes(net);
@@ -145,6 +147,7 @@ int Server::submit_network(const emt_network* net, const emt_hinv_opts* opts, do
               EMT_ERR_INVALID, "incomplete network");
   EMT_REQUIRE(n_steps >= 1 && arrival >= 0, EMT_ERR_INVALID, "bad request");
   EMT_REQUIRE(kind >= -1 && kind <= 1, EMT_ERR_INVALID, "event kind must be -1, 0 (trip) or 1 (fault)");
+  check_network_arrays(net);
   NetDesc d;
   d.n_bus = net->n_bus;
   d.from = copy_of(net->from, net->n_branch);

@@ -236,8 +236,10 @@ void launch_bench_any(Sim& sm, int which, int reps, cudaStream_t s) {
 // Conductance graph of a network at time step dt: trapezoidal companion conductances of the
 // series branches (ids preserved) and shunt capacitors, then 1/Rs of the sources.
 // Sizes and the arrays they require (host side, before any device work): branch endpoints, kinds
-// and R for every branch, L for RL and C for RC branches, bus and resistance for every source.
-static void check_network_arrays(const emt_network* net) {
+// and R for every branch, L for RL and C for RC branches, all four arrays of every source and all
+// three of every load.
+void check_network_arrays(const emt_network* net) {
+  EMT_REQUIRE(net, EMT_ERR_INVALID, "null network");
   EMT_REQUIRE(net->n_bus >= 1 && net->n_branch >= 0 && net->n_src >= 0 && net->n_load >= 0, EMT_ERR_INVALID,
               "bad network sizes");
   EMT_REQUIRE(net->n_branch == 0 || (net->from && net->to && net->kind && net->R), EMT_ERR_INVALID,
@@ -245,7 +247,10 @@ static void check_network_arrays(const emt_network* net) {
   for (int e = 0; e < net->n_branch; ++e)
     EMT_REQUIRE(net->kind[e] == EMT_KIND_RL ? net->L != nullptr : net->C != nullptr, EMT_ERR_INVALID,
                 "null L (RL branches) or C (RC branches)");
-  EMT_REQUIRE(net->n_src == 0 || (net->src_bus && net->src_Rs), EMT_ERR_INVALID, "null source arrays");
+  EMT_REQUIRE(net->n_src == 0 || (net->src_bus && net->src_Rs && net->src_Vm && net->src_phi), EMT_ERR_INVALID,
+              "null source arrays");
+  EMT_REQUIRE(net->n_load == 0 || (net->load_bus && net->load_amp && net->load_phi), EMT_ERR_INVALID,
+              "null load arrays");
 }
 
 void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
@@ -376,6 +381,7 @@ SimD Sim::view() const {
 Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs_, const double* src_scale,
          const double* load_scale, cudaStream_t s) {
   EMT_REQUIRE(net && opts, EMT_ERR_INVALID, "null network or options");
+  check_network_arrays(net);
   EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
   EMT_REQUIRE(nrhs_ == 1, EMT_ERR_UNSUPPORTED, "this build steps one column per simulation");
   (void)src_scale;

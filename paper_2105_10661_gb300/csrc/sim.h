@@ -10,6 +10,10 @@
 
 namespace emt {
 
+// Sizes and required arrays of an element description, checked on the host before any device work
+// (EMT_ERR_INVALID otherwise).
+void check_network_arrays(const emt_network* net);
+
 struct SimDyn {
   int step_base;   // steps completed before the current launch sequence
   int rec_first;   // step number stored at record row 0

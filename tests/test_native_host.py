@@ -111,3 +111,29 @@ def test_graph_input_checks_run_before_any_device_work(L, frm, to, g, mode, msg)
     assert L.lib.emt_build_hinv(C.byref(gr), C.byref(o), None, C.byref(h)) == L.EMT_ERR_INVALID
     assert msg in L.lib.emt_last_error()
     assert h.value is None
+
+
+@pytest.mark.parametrize("field,msg", [("from_", b"null branch arrays"), ("R", b"null branch arrays"),
+                                       ("src_Vm", b"null source arrays"), ("load_bus", b"null load arrays")])
+@pytest.mark.parametrize("nrhs", [1, 8])
+def test_simulation_input_checks_run_before_any_device_work(L, field, msg, nrhs):
+    # single- and multi-column simulations reject incomplete element data with a status, not a crash
+    import ctypes as C
+    nw, keep = L.make_network(netgen.small_network(5, 3))
+    bad = L.EmtNetwork.from_buffer_copy(nw)
+    setattr(bad, field, None)
+    if field == "load_bus":
+        bad.n_load = 2
+    opts = L.make_opts(levels=1)
+    h = C.c_void_p()
+    assert L.lib.emt_sim_create(C.byref(bad), C.byref(opts), 50e-6, nrhs, None, None, None,
+                                C.byref(h)) == L.EMT_ERR_INVALID
+    assert msg in L.lib.emt_last_error()
+    assert L.lib.emt_sim_create(None, C.byref(opts), 50e-6, nrhs, None, None, None, C.byref(h)) == L.EMT_ERR_INVALID
+
+
+def test_server_create_checks_its_arguments(L):
+    import ctypes as C
+    s = C.c_void_p()
+    assert L.lib.emt_server_create(0, 0, C.byref(s)) == L.EMT_ERR_INVALID
+    assert b"tick" in L.lib.emt_last_error()
