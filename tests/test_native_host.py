@@ -137,3 +137,43 @@ def test_server_create_checks_its_arguments(L):
     s = C.c_void_p()
     assert L.lib.emt_server_create(0, 0, C.byref(s)) == L.EMT_ERR_INVALID
     assert b"tick" in L.lib.emt_last_error()
+
+
+NULL_HANDLE_CALLS = {
+    "emt_tree_sizes": (None, None, None, None),
+    "emt_tree_arrays": (None,) * 12,
+    "emt_hinv_get_partition": (None,) * 5,
+    "emt_apply": (None, None, None, 1, 1, 0, 0.0, None),
+    "emt_apply_noalloc": (None, None, None, None),
+    "emt_modify_branch": (None, 0, 1, -1.0, None),
+    "emt_hinv_sync": (None, None),
+    "emt_sim_schedule": (None, 1, 0, 0, 0.0, -1),
+    "emt_sim_monitor": (None, 0, None),
+    "emt_step": (None, 1, None, None),
+    "emt_sim_read": (None, 0, None),
+    "emt_sim_set_rows_per_cta": (None, 0),
+    "emt_sim_tune": (None, 0, 2),
+    "emt_sim_autotune": (None, 1, None, None, None),
+    "emt_sim_reset": (None, None),
+    "emt_sim_stats": (None, None, 0),
+    "emt_sim_bench_kernel": (None, 0, 1, None),
+    "emt_server_add_network": (None, None, None, 50e-6, 4, 1, None, None),
+    "emt_server_submit": (None, 0, 0.0, 1, -1, 0, 0.0, 0, 0, None),
+    "emt_server_submit_network": (None, None, None, 50e-6, 1, None, 0.0, 1, -1, 0, 0.0, 0, 0, None),
+    "emt_server_run": (None,),
+    "emt_server_result": (None, 0, None, None),
+    "emt_server_stats": (None, None, 0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(NULL_HANDLE_CALLS))
+def test_every_call_rejects_a_null_handle_with_a_status(L, name):
+    # the ABI never throws or aborts: a null handle is EMT_ERR_INVALID with a message
+    assert getattr(L.lib, name)(*NULL_HANDLE_CALLS[name]) == L.EMT_ERR_INVALID
+    assert L.lib.emt_last_error()
+
+
+def test_destroy_and_accessors_accept_null(L):
+    for name in ("emt_tree_destroy", "emt_hinv_destroy", "emt_sim_destroy", "emt_server_destroy"):
+        getattr(L.lib, name)(None)
+    assert L.lib.emt_hinv_tree(None) is None
