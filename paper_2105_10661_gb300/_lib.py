@@ -140,12 +140,23 @@ def _check(code):
         raise EmtError(code, lib.emt_last_error().decode())
 
 
-def _ptr(x):
+def _ptr(x, n_min=0, what="buffer"):
+    """Device address of a CUDA float64 tensor (contiguous, at least n_min elements), checked here so
+    that a host tensor or a short buffer is an error in Python, never an address the GPU reads; a raw
+    integer address is passed through as the caller's responsibility."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if not getattr(x, "is_cuda", False):
+            raise ValueError(f"{what}: expected a CUDA tensor, got one on {getattr(x, 'device', 'the host')}")
+        if str(getattr(x, "dtype", "")) != "torch.float64":
+            raise ValueError(f"{what}: expected float64, got {getattr(x, 'dtype', None)}")
+        if not x.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous tensor")
+        if x.numel() < n_min:
+            raise ValueError(f"{what}: {x.numel()} elements, the call writes or reads {n_min}")
         return x.data_ptr()
     raise TypeError("expected a device pointer or an object with data_ptr()")
 
@@ -260,13 +271,15 @@ def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, pre
 
 
 def emt_apply(h: HInv, i_dev, v_dev, nrhs=1, ld=None, max_refine=0, tol=0.0, stream=None):
-    _check(lib.emt_apply(h.h, _ptr(i_dev), _ptr(v_dev), int(nrhs), int(ld if ld is not None else h.n),
+    ld = int(ld if ld is not None else h.n)
+    need = ld * (int(nrhs) - 1) + h.n if int(nrhs) >= 1 else 0
+    _check(lib.emt_apply(h.h, _ptr(i_dev, need, "i_dev"), _ptr(v_dev, need, "v_dev"), int(nrhs), ld,
                          int(max_refine), float(tol), _stream(stream)))
 
 
 def emt_apply_noalloc(h: HInv, i_dev, v_dev, stream=None):
     """Single-vector apply that allocates nothing (scratch in a fixed device array)."""
-    _check(lib.emt_apply_noalloc(h.h, _ptr(i_dev), _ptr(v_dev), _stream(stream)))
+    _check(lib.emt_apply_noalloc(h.h, _ptr(i_dev, h.n, "i_dev"), _ptr(v_dev, h.n, "v_dev"), _stream(stream)))
 
 
 def emt_modify_branch(h: HInv, bus_a, bus_b, delta_g, stream=None):
@@ -315,7 +328,8 @@ def emt_sim_monitor(s: Sim, buses):
 
 
 def emt_step(s: Sim, n_steps, record_dev=None, stream=None):
-    _check(lib.emt_step(s.h, int(n_steps), _ptr(record_dev), _stream(stream)))
+    need = max(int(n_steps), 0) * s.nrhs * s.n_mon
+    _check(lib.emt_step(s.h, int(n_steps), _ptr(record_dev, need, "record_dev"), _stream(stream)))
 
 
 def emt_sim_read(s: Sim, what=0):

@@ -177,3 +177,47 @@ def test_destroy_and_accessors_accept_null(L):
     for name in ("emt_tree_destroy", "emt_hinv_destroy", "emt_sim_destroy", "emt_server_destroy"):
         getattr(L.lib, name)(None)
     assert L.lib.emt_hinv_tree(None) is None
+
+
+def test_binding_rejects_host_short_or_wrong_type_buffers(L):
+    # a host tensor, a float32 tensor, a strided view or a short buffer never reaches the library
+    # as a device address (checked without a GPU: the host-tensor check comes first)
+    import torch
+
+    class FakeHInv:
+        h, n = None, 8
+
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        L.emt_apply(FakeHInv(), torch.zeros(8, dtype=torch.float64), torch.zeros(8, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        L.emt_apply_noalloc(FakeHInv(), torch.zeros(8, dtype=torch.float64), None)
+
+    class FakeSim:
+        h, n, nrhs, n_mon = None, 8, 2, 3
+
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        L.emt_step(FakeSim(), 10, torch.zeros(10, 2, 3, dtype=torch.float64))
+    assert L._ptr(None) is None and L._ptr(1234) == 1234
+
+    class FakeCuda:   # stands in for a CUDA tensor's attributes
+        is_cuda = True
+
+        def __init__(self, dtype, n, contiguous=True):
+            self.dtype, self.n, self.c = dtype, n, contiguous
+
+        def numel(self):
+            return self.n
+
+        def is_contiguous(self):
+            return self.c
+
+        def data_ptr(self):
+            return 4096
+
+    assert L._ptr(FakeCuda(torch.float64, 10), 10) == 4096
+    with pytest.raises(ValueError, match="float64"):
+        L._ptr(FakeCuda(torch.float32, 10), 10)
+    with pytest.raises(ValueError, match="contiguous"):
+        L._ptr(FakeCuda(torch.float64, 10, contiguous=False), 10)
+    with pytest.raises(ValueError, match="elements"):
+        L._ptr(FakeCuda(torch.float64, 9), 10, "record_dev")
