@@ -116,7 +116,8 @@ def test_exact_core_without_the_swap_term_is_caught(monkeypatch):
 
     monkeypatch.setattr(hinv.HInv, "_build_node", mutated)
     nw = _tile()
-    assert _some_pin_fails([lambda: T.test_exact_store_equals_dense_inverse(nw), T.test_no_coupling_paper_equals_exact])
+    assert _some_pin_fails([lambda: T.test_exact_store_equals_dense_inverse(nw),
+                            T.test_no_coupling_paper_equals_exact])
 
 
 def test_sherman_morrison_with_the_wrong_denominator_is_caught(monkeypatch):
@@ -161,6 +162,21 @@ def test_coupled_admittance_with_the_wrong_mutual_sign_is_caught(monkeypatch):
                             T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
 
 
+def test_bisection_without_kernighan_lin_is_caught(monkeypatch):
+    monkeypatch.setattr(pt, "_kl", lambda side, nbr, wt, passes=4: side.copy())
+    pins = [lambda g=g: T.test_bisection_reaches_brute_force_minimum(*g) for g in (
+        ("path", T._graph_path(11), 11), ("cycle", T._graph_cycle(12), 12),
+        ("barbell", T._graph_barbell(6), 12), ("ladder", T._graph_ladder(6), 12))]
+    assert _some_pin_fails(pins + [T.test_kl_never_worse_than_growth_and_small_brute_force])
+
+
+def test_three_phase_sources_with_the_wrong_sequence_are_caught(monkeypatch):
+    from oracle import emt3
+    monkeypatch.setattr(emt3, "phase_shift", lambda p: 2.0 * np.pi * p / 3.0)   # a-c-b instead of a-b-c
+    assert _some_pin_fails([T.test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs,
+                            T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
+
+
 @pytest.mark.parametrize("case", ["none"])
 def test_the_pins_pass_without_a_mistake(case):
     # the control: with nothing planted, every pin used above passes
@@ -170,4 +186,8 @@ def test_the_pins_pass_without_a_mistake(case):
         T.test_kirchhoff_balance_every_step, T.test_two_bus_golden, T.test_lca_brute_force,
         lambda: T.test_eq5_offdiagonal_blocks_vanish(nw), lambda: T.test_exact_store_equals_dense_inverse(nw),
         lambda: T.test_sherman_morrison_and_woodbury_closed_forms(nw),
-        lambda: T.test_algorithm2_to_root_equals_rebuild(nw), T.test_coupled_rl_admittance_closed_form])
+        lambda: T.test_algorithm2_to_root_equals_rebuild(nw), T.test_coupled_rl_admittance_closed_form,
+        T.test_kl_never_worse_than_growth_and_small_brute_force,
+        lambda: T.test_bisection_reaches_brute_force_minimum("ladder", T._graph_ladder(6), 12),
+        T.test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs,
+        T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
