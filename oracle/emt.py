@@ -6,8 +6,12 @@ Readings where the paper is silent: all voltages, currents and history
 sources start at zero and the sources are first evaluated at t = dt; a line
 trip at step k opens the branch instantaneously before step k is solved (its
 conductance leaves G, its current and history are zeroed); a bus fault is a
-resistor R_f to ground switched in at step k_on and out at step k_off, and
-switching it out restores the pre-fault inverse.
+resistor R_f to ground switched in at step k_on and out at step k_off. Each
+switching is its own change of G (Sec. IV): switching in adds 1/R_f e_a e_a^T,
+switching out subtracts it again (delta = -1/R_f), so changes made while the
+fault is on (a trip, a fault at another bus, a second fault at the same bus)
+stay in G after it clears. Several faults on at one bus clear in the order
+they were switched in.
 
 The solver is one of: "dense" (Cholesky, refactored on every change),
 "exact" (the exact hierarchical store, rebuilt on every change), "paper"
@@ -55,7 +59,6 @@ class _Solver:
         self.nw = nw
         self.kind = kind
         self.G = nw.G.copy()
-        self.saved = {}
         if kind == "dense":
             self.s = _dense.DenseSolver(self.G)
         else:
@@ -66,7 +69,7 @@ class _Solver:
         """v = G^{-1} rhs (Eq. 2)."""
         return self.s.solve(rhs) if self.kind == "dense" else self.s.apply(rhs)
 
-    def change(self, a, b, delta, key=None):
+    def change(self, a, b, delta):
         """G' = G + delta u u^T (Sec. IV) and the matching change of the solver."""
         self.G = _modify.modified_G(self.G, a, b, delta)
         if self.kind == "dense":
@@ -75,14 +78,6 @@ class _Solver:
             self.s = _modify.rebuild(self.s, self.nw.series_frm, self.nw.series_to, a, b, delta)
         else:
             self.s = _modify.algorithm2(self.s, self.nw.series_frm, self.nw.series_to, a, b, delta)
-
-    def push(self, key):
-        """Save G and the solver before a fault is switched in (the fault reading above)."""
-        self.saved[key] = (self.G.copy(), self.s)
-
-    def pop(self, key):
-        """Restore the pre-fault G and solver when the fault is switched out."""
-        self.G, self.s = self.saved.pop(key)
 
 
 def simulate(nw: Network, nsteps: int, events=(), solver: str = "dense", monitor=None,
@@ -102,6 +97,7 @@ def simulate(nw: Network, nsteps: int, events=(), solver: str = "dense", monitor
     mon = np.arange(n) if monitor is None else np.asarray(monitor, np.int64)
     out = np.zeros((nsteps, len(mon)))
     ev = sorted(events, key=lambda x: x[0])
+    faults = {}          # bus -> R_f of the faults on there, in the order they were switched in
     ei = 0
     v = np.zeros(n)
     cur = np.zeros(ne)
@@ -117,10 +113,13 @@ def simulate(nw: Network, nsteps: int, events=(), solver: str = "dense", monitor
                     active[e] = False
                     Ih[e] = 0.0
             elif kind == FAULT_ON:
-                sol.push(("fault", int(target)))
+                faults.setdefault(int(target), []).append(float(value))
                 sol.change(int(target), -1, 1.0 / float(value))
             elif kind == FAULT_OFF:
-                sol.pop(("fault", int(target)))
+                on = faults.get(int(target), [])
+                if not on:
+                    raise ValueError(f"fault switched out at bus {int(target)} where none is on")
+                sol.change(int(target), -1, -1.0 / on.pop(0))
             ei += 1
         t = step * nw.dt
         rhs = cm.source_injection(net, t, src_scale, load_scale) + cm.history_injection(el, Ih, n)

@@ -512,6 +512,77 @@ def test_stepping_solvers_agree_with_trip_and_fault():
     assert np.all(np.isfinite(p))
 
 
+def _fault_event_sequences(net):
+    """Event orders in which one change happens while a fault is on (steps, kind, target, value)."""
+    e = netgen.pick_branch(net)
+    e17 = next(i for i in range(len(net["br_a"])) if 17 in (int(net["br_a"][i]), int(net["br_b"][i])))
+    return {
+        "trip inside a fault window": [(20, emt.FAULT_ON, 17, 10.0), (30, emt.TRIP, e, 0.0),
+                                       (40, emt.FAULT_OFF, 17, 0.0)],
+        "trip at the faulted bus inside its window": [(20, emt.FAULT_ON, 17, 10.0), (28, emt.TRIP, e17, 0.0),
+                                                      (41, emt.FAULT_OFF, 17, 0.0)],
+        "overlapping faults at two buses": [(20, emt.FAULT_ON, 17, 10.0), (25, emt.FAULT_ON, 60, 5.0),
+                                            (35, emt.FAULT_OFF, 17, 0.0), (45, emt.FAULT_OFF, 60, 0.0)],
+        "back-to-back and stacked faults at one bus": [
+            (20, emt.FAULT_ON, 17, 10.0), (30, emt.FAULT_OFF, 17, 0.0), (30, emt.FAULT_ON, 17, 4.0),
+            (33, emt.FAULT_ON, 17, 20.0), (38, emt.FAULT_OFF, 17, 0.0), (45, emt.FAULT_OFF, 17, 0.0)],
+    }
+
+
+def _kirchhoff_through_events(nw, nsteps, events, solver):
+    # Kirchhoff's current law at every bus and step, for the network the events describe: a
+    # tripped branch carries nothing from its trip on, and each fault that is on draws v_a / R_f
+    # (faults at one bus clear in the order they came on). The voltages come from the oracle's
+    # stepping; the element currents follow from them by the companion models.
+    out, _ = emt.simulate(nw, nsteps, events, solver=solver)
+    net, el = nw.net, nw.el
+    n = net["n_bus"]
+    w = 2 * np.pi * net["freq"]
+    Ih = np.zeros(len(el["g"]))
+    active = np.ones(len(el["g"]), bool)
+    on = {}
+    worst = 0.0
+    for s in range(nsteps):
+        step = s + 1
+        for (st, kind, tgt, val) in events:
+            if st != step:
+                continue
+            if kind == emt.TRIP:
+                active[tgt] = False
+                Ih[tgt] = 0.0
+            elif kind == emt.FAULT_ON:
+                on.setdefault(tgt, []).append(val)
+            else:
+                on[tgt].pop(0)
+        v = out[s]
+        cur, Ih = cm.update_history(el, v, Ih, active)
+        bal = np.zeros(n)
+        np.add.at(bal, el["a"], cur)
+        m = el["b"] >= 0
+        np.add.at(bal, el["b"][m], -cur[m])
+        e = net["src_Vm"] * np.sin(w * step * nw.dt + net["src_phi"])
+        np.add.at(bal, net["src_bus"], (v[net["src_bus"]] - e) / net["src_Rs"])
+        for bus, rs in on.items():
+            bal[bus] += sum(v[bus] / r for r in rs)
+        scale = max(np.max(np.abs(cur)), np.max(np.abs(net["src_Vm"] / net["src_Rs"])))
+        worst = max(worst, np.max(np.abs(bal)) / scale)
+    return worst
+
+
+@pytest.mark.parametrize("solver", ["dense", "exact"])
+def test_kirchhoff_balance_through_trips_and_overlapping_faults(solver):
+    net = netgen.tile(1_000_000)
+    nw = emt.Network(net, DT, levels=2)
+    for name, ev in _fault_event_sequences(net).items():
+        assert _kirchhoff_through_events(nw, 55, ev, solver) <= 1e-12, name
+
+
+def test_fault_cleared_where_none_is_on_is_rejected():
+    nw = emt.Network(netgen.tile(1_000_000), DT, want_tree=False)
+    with pytest.raises(ValueError):
+        emt.simulate(nw, 10, [(3, emt.FAULT_ON, 17, 10.0), (5, emt.FAULT_OFF, 18, 0.0)])
+
+
 # ---------------------------------------------------------------- three-phase buses (3 nodes per bus)
 def test_coupled_rl_admittance_closed_form():
     # (R I + (2/dt)(L I + M (J - I)))^-1 = (alpha - beta)^-1 (I - beta / (alpha + 2 beta) J),

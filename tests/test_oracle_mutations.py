@@ -177,6 +177,24 @@ def test_three_phase_sources_with_the_wrong_sequence_are_caught(monkeypatch):
                             T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
 
 
+def test_fault_clearing_by_restoring_the_pre_fault_solver_is_caught(monkeypatch):
+    # the reading that clearing a fault puts back G and the solver saved when it came on, which
+    # also undoes every change made in between
+    saved = {}
+    orig_change = emt._Solver.change
+
+    def change(self, a, b, delta):
+        if b < 0 and delta > 0:
+            saved.setdefault(id(self), {})[a] = (self.G.copy(), self.s)
+        if b < 0 and delta < 0 and a in saved.get(id(self), {}):
+            self.G, self.s = saved[id(self)].pop(a)
+            return
+        orig_change(self, a, b, delta)
+
+    monkeypatch.setattr(emt._Solver, "change", change)
+    assert _some_pin_fails([lambda: T.test_kirchhoff_balance_through_trips_and_overlapping_faults("dense")])
+
+
 @pytest.mark.parametrize("case", ["none"])
 def test_the_pins_pass_without_a_mistake(case):
     # the control: with nothing planted, every pin used above passes
@@ -184,6 +202,7 @@ def test_the_pins_pass_without_a_mistake(case):
     assert not _some_pin_fails([
         T.test_rc_series_sine_steady_state_bilinear, T.test_rl_sine_steady_state_bilinear,
         T.test_kirchhoff_balance_every_step, T.test_two_bus_golden, T.test_lca_brute_force,
+        lambda: T.test_kirchhoff_balance_through_trips_and_overlapping_faults("dense"),
         lambda: T.test_eq5_offdiagonal_blocks_vanish(nw), lambda: T.test_exact_store_equals_dense_inverse(nw),
         lambda: T.test_sherman_morrison_and_woodbury_closed_forms(nw),
         lambda: T.test_algorithm2_to_root_equals_rebuild(nw), T.test_coupled_rl_admittance_closed_form,
