@@ -117,9 +117,10 @@ emt_status emt_hinv_get_partition(const emt_hinv* h, int32_t* perm, int32_t* nod
  * n_bus x nrhs with leading dimension ld >= n_bus (doubles), bus order. For EMT_PREC_FP32 the
  * result is refined exactly max_refine times (0..16): r = i - G v with the FP64 matrix, then
  * v += (stored inverse) r. The count is fixed, chosen per workload by calibration, so that the
- * call stays asynchronous (a tolerance test would read the device back every pass); tol is not
- * evaluated (reserved). FP64 and FF64 stores ignore both. Asynchronous on `stream`. nrhs >= 1;
- * nrhs == 1 takes the fused single-vector kernels. */
+ * call stays asynchronous (a tolerance test would read the device back every pass). tol is not
+ * evaluated: tol > 0 (or NaN) returns EMT_ERR_UNSUPPORTED, so that no caller believes a
+ * tolerance was enforced; pass tol <= 0. FP64 and FF64 stores ignore max_refine. Asynchronous on
+ * `stream`. nrhs >= 1; nrhs == 1 takes the fused single-vector kernels. */
 emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld,
                      int32_t max_refine, double tol, void* stream);
 
@@ -203,9 +204,13 @@ emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const 
 emt_status emt_build_hinv_from_network3(const emt_network* net, const double* L_mut, double dt,
                                         const emt_hinv_opts* opts, void* stream, emt_hinv** out);
 
-/* Event kinds for emt_sim_schedule. TRIP: target = branch id (opens before the step is
- * solved; current and history zeroed). FAULT_ON: target = bus, value = R_f (ohm). FAULT_OFF:
- * target = bus (restores the pre-fault store). */
+/* Event kinds for emt_sim_schedule. Each event is one change of G, applied to the stored
+ * inverse as a local update (Sec. IV) before the step is solved. TRIP: target = branch id (the
+ * branch opens; its current and history are zeroed). FAULT_ON: target = bus, value = R_f (ohm):
+ * G + (1/R_f) e_a e_a^T. FAULT_OFF: target = bus: takes back exactly the conductance of the
+ * oldest fault still on at that bus (delta = -1/R_f), so changes made while it was on (trips,
+ * faults at other buses, further faults at the same bus) stay. emt_step returns EMT_ERR_STATE,
+ * before enqueuing any work, if a FAULT_OFF in its range finds no fault on at its bus. */
 enum { EMT_EVENT_TRIP = 0, EMT_EVENT_FAULT_ON = 1, EMT_EVENT_FAULT_OFF = 2 };
 
 /* Create a simulation of `net` at time step dt with nrhs independent columns (nrhs = 1 for

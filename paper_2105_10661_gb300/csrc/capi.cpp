@@ -185,12 +185,14 @@ emt_status emt_hinv_get_partition(const emt_hinv* h, int32_t* perm, int32_t* nod
 
 emt_status emt_apply(emt_hinv* h, const double* i_dev, double* v_dev, int32_t nrhs, int64_t ld, int32_t max_refine,
                      double tol, void* stream) {
-  (void)tol;   // reserved: the refinement count is fixed (max_refine), see emt.h
   return guard([&] {
     EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
     EMT_REQUIRE(i_dev && v_dev, EMT_ERR_INVALID, "null vectors");
     EMT_REQUIRE(nrhs >= 1 && ld >= h->st->n, EMT_ERR_INVALID, "bad nrhs or leading dimension");
     EMT_REQUIRE(max_refine >= 0 && max_refine <= 16, EMT_ERR_INVALID, "max_refine out of range");
+    // the refinement count is fixed (max_refine); a tolerance would need a device read-back per pass
+    EMT_REQUIRE(!(tol > 0.0) && !std::isnan(tol), EMT_ERR_UNSUPPORTED,
+                "tol is not evaluated: pass tol <= 0 and choose max_refine instead");
     cudaStream_t s = as_stream(stream);
     if (!h->has_plan) {
       emt::make_plan(*h->st, 0, h->plan, s);

@@ -567,6 +567,7 @@ Store::Store(const emt_graph* g, const emt_hinv_opts* o, cudaStream_t s) {
   g_val.assign(g->g, g->g + g->n_branch);
   tree = build_tree(n, g->n_branch, g->from, g->to, o->levels, o->d_th);
   build_csr();
+  EMT_CUDA(cudaGetDevice(&device));   // first device call: every host-side check has passed
   setup_layout(s);
 }
 

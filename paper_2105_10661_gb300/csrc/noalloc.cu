@@ -186,10 +186,14 @@ void set_smem_limits() {
 }
 
 // Once per device, with that device current: look up the array's device address (a host-side
-// use of the symbol itself would be a host stand-in, not a device address).
-void* device_scratch() {
+// use of the symbol itself would be a host stand-in, not a device address). The current device
+// must be the one the store was built on, or the kernels would pair its pointers with another
+// device's array.
+void* device_scratch(int store_device) {
   int dev = 0;
   EMT_CUDA(cudaGetDevice(&dev));
+  EMT_REQUIRE(dev == store_device, EMT_ERR_INVALID,
+              "emt_apply_noalloc: the current CUDA device is not the one the store was built on");
   EMT_REQUIRE(dev >= 0 && dev < kMaxDevices, EMT_ERR_UNSUPPORTED, "device ordinal too large");
   std::lock_guard<std::mutex> lk(g_setup_mutex);
   DeviceSetup& d = g_setup[dev];
@@ -220,7 +224,7 @@ void apply_noalloc(const Store& st, const double* i_dev, double* v_dev, cudaStre
   EMT_REQUIRE(need <= kScratchBytes, EMT_ERR_UNSUPPORTED,
               "emt_apply_noalloc: this store needs more scratch than EMT_APPLY_NOALLOC_SCRATCH_BYTES "
               "(n_leaf * ceil(max_leaf / 32) * max_leaf * 8 bytes); use emt_apply");
-  void* scratch = device_scratch();
+  void* scratch = device_scratch(st.device);
   // shared memory of the two kernels (same bounds as the fused apply)
   size_t red = 0;
   for (int ve : {2, 4}) {

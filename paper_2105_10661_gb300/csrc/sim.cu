@@ -513,7 +513,7 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
   launches_per_step = store->precision == EMT_PREC_FP32 ? 4 : 2;
   s2.build(*this, s);
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-  apply_cached_tuning(s);
+  if (!apply_cached_tuning(s)) choose_default_kernels(s);
   EMT_CUDA(cudaStreamSynchronize(s));
   EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
 }
@@ -623,15 +623,35 @@ void Sim::autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream
   if (best_kernels) *best_kernels = bk;
 }
 
-void Sim::apply_cached_tuning(cudaStream_t s) {
+bool Sim::apply_cached_tuning(cudaStream_t s) {
   std::pair<int, int> v;
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune_cache.find(tune_key(*this));
-    if (it == g_tune_cache.end()) return;
+    if (it == g_tune_cache.end()) return false;
     v = it->second;
   }
   tune(v.first, v.second, s);
+  return true;
+}
+
+// Launch shape of a simulation nobody has timed: the persistent cluster kernel (generation 4)
+// whenever its plan fits, with the largest cluster (at most 16 CTAs) that still gives every CTA
+// 16 positions or more (8 CTAs at 179 buses, 16 at 1,432; the sizes the autotuner picks there),
+// else the nearest sizes that fit; generation 2 when none does (FP32 stores, or stores too large
+// for one cluster's shared memory).
+void Sim::choose_default_kernels(cudaStream_t s) {
+  if (!s2.ready || (store->precision != EMT_PREC_FF64 && store->precision != EMT_PREC_FP64)) return;
+  int pref = 16;
+  while (pref > 1 && n / pref < 16) pref /= 2;
+  std::vector<int> order;
+  for (int c = pref; c >= 1; c /= 2) order.push_back(c);
+  for (int c = pref * 2; c <= 16; c *= 2) order.push_back(c);
+  for (int c : order) {
+    tune(c, 4, s);
+    if (use_v4()) return;
+  }
+  tune(0, 2, s);
 }
 
 void Sim::set_monitor(int nm, const int32_t* buses, cudaStream_t s) {
@@ -673,20 +693,40 @@ void Sim::apply_event(const Event& ev, cudaStream_t s) {
     if (s2.ready) s2.open_element(el_inc[e].first, el_inc[e].second, s);
     el_g[e] = 0.0;
   } else if (ev.kind == EMT_EVENT_FAULT_ON) {
-    Snapshot& sn = snapshots[ev.target];
-    sn.save(st, s);
+    // a fault is its own change G' = G + (1/R_f) e_a e_a^T (Sec. IV)
+    faults_on[ev.target].push_back(ev.value);
     st.modify_async(ev.target, -1, 1.0 / ev.value, s);
   } else {
-    auto it = snapshots.find(ev.target);
-    EMT_REQUIRE(it != snapshots.end(), EMT_ERR_STATE, "FAULT_OFF without FAULT_ON");
-    it->second.restore(st, s);
-    snapshots.erase(it);
+    // clearing takes back exactly that change (delta = -1/R_f, the oldest fault on at the bus),
+    // so changes made while the fault was on (trips, other faults) stay in G
+    auto it = faults_on.find(ev.target);
+    EMT_REQUIRE(it != faults_on.end() && !it->second.empty(), EMT_ERR_STATE, "FAULT_OFF without FAULT_ON");
+    const double r_f = it->second.front();
+    it->second.pop_front();
+    if (it->second.empty()) faults_on.erase(it);
+    st.modify_async(ev.target, -1, -1.0 / r_f, s);
   }
   refresh_plan_values(st, plan, s);
   if (s2.ready) s2.refresh(*this, s);
   if (s3.ready) s3.img.refresh(*this, s);
   if (s4.ready) s4.refresh(*this, s);
   EMT_CUDA(cudaGetLastError());
+}
+
+// Every FAULT_OFF up to last_step must find a fault on at its bus; checked before any work of an
+// emt_step call is enqueued, so a bad sequence fails without touching the simulation.
+void Sim::check_fault_sequence(int last_step) const {
+  std::map<int, size_t> on;
+  for (const auto& kv : faults_on) on[kv.first] = kv.second.size();
+  for (size_t i = ev_cursor; i < events.size() && events[i].step <= last_step; ++i) {
+    const Event& ev = events[i];
+    if (ev.step <= cur_step) continue;
+    if (ev.kind == EMT_EVENT_FAULT_ON) ++on[ev.target];
+    if (ev.kind == EMT_EVENT_FAULT_OFF) {
+      EMT_REQUIRE(on[ev.target] > 0, EMT_ERR_STATE, "FAULT_OFF at a bus where no fault is on at that step");
+      --on[ev.target];
+    }
+  }
 }
 
 void Snapshot::save(const Store& st, cudaStream_t s) {
@@ -763,6 +803,7 @@ void Sim::run(int n_steps, cudaStream_t s) {
 void Sim::step(int n_steps, double* record_dev, cudaStream_t s) {
   EMT_REQUIRE(n_steps >= 0, EMT_ERR_INVALID, "n_steps must be >= 0");
   if (n_steps == 0) return;
+  check_fault_sequence(cur_step + n_steps);
   k_set_dyn<<<1, 1, 0, s>>>(d_dyn.p, cur_step, cur_step + 1, record_dev);
   EMT_CUDA(cudaGetLastError());
   launches += 1;
@@ -792,7 +833,7 @@ void Sim::reset(cudaStream_t s) {
   }
   if (s3.ready) s3.img.refresh(*this, s);
   if (s4.ready) s4.refresh(*this, s);
-  snapshots.clear();
+  faults_on.clear();
   cur_step = 0;
   ev_cursor = 0;
   launches += 4;   // pack (3) + -g refresh

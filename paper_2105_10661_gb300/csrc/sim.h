@@ -1,5 +1,6 @@
 // EMT simulation object (host) and its device view.
 #pragma once
+#include <deque>
 #include <map>
 #include <memory>
 #include <utility>
@@ -51,7 +52,7 @@ struct Event {
   int column;
 };
 
-// Copy of the FP64 store taken when a fault switches in; switching it out restores it.
+// Copy of the FP64 store right after construction; emt_sim_reset puts it back.
 struct Snapshot {
   DevBuf<double> L, F, C, cg, cv;
   std::vector<double> g_val, csr_val, cut_g;
@@ -141,7 +142,8 @@ class Sim {
   void set_rows_per_cta(int rpc, cudaStream_t s);
   void tune(int rpc, int kernels, cudaStream_t s);
   void autotune(int probe_steps, int* best_rpc, int* best_kernels, cudaStream_t s);
-  void apply_cached_tuning(cudaStream_t s);
+  bool apply_cached_tuning(cudaStream_t s);
+  void choose_default_kernels(cudaStream_t s);
   void step(int n_steps, double* record_dev, cudaStream_t s);
   void read(int what, double* host_out, cudaStream_t s);
   void reset(cudaStream_t s);
@@ -163,7 +165,7 @@ class Sim {
   DevBuf<SimDyn> d_dyn;
   std::vector<Event> events;
   size_t ev_cursor = 0;
-  std::map<int, Snapshot> snapshots;
+  std::map<int, std::deque<double>> faults_on;   // bus -> R_f of the faults on there, oldest first
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraphExec_t> bench_graphs;
   cudaStream_t cap_stream = nullptr;
@@ -178,12 +180,14 @@ class Sim {
   Step3 s3;
   Step4 s4;
   int kernels = 2;                             // 1: first generation, 2: step2, 3: step3, 4: step4
+                                               // (creation picks 4 when it fits: choose_default_kernels)
   bool use_v2() const { return kernels == 2 && s2.ready; }
   bool use_v3() const { return kernels == 3 && s3.ready && s2.ready; }
   bool use_v4() const { return kernels == 4 && s4.ready && s2.ready; }
 
  private:
   void run(int n_steps, cudaStream_t s);
+  void check_fault_sequence(int last_step) const;
   void apply_event(const Event& ev, cudaStream_t s);
   void drop_graphs();
 };

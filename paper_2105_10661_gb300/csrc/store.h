@@ -89,6 +89,7 @@ class Store {
   void apply_rows_fp64(const double* Xin, double* Y, int m, int ld, cudaStream_t s);
 
   Tree tree;
+  int device = -1;                                   // CUDA device the store was built on
   int mode, precision;
   int n;
   int n_leaf, n_internal, kmax;

@@ -56,6 +56,20 @@ def _build(L, net_nw, levels=0, d_th=0, mode=0, prec=0):
     return h
 
 
+def test_apply_rejects_a_tolerance_it_would_not_evaluate(L):
+    nw, gr = _store_inputs(netgen.tile(1_000_000))
+    h = _build(L, (nw, gr), levels=2, prec=2)
+    i_dev = torch.ones(gr["n_bus"], dtype=torch.float64, device="cuda")
+    v_dev = torch.zeros_like(i_dev)
+    for tol in (1e-10, float("nan")):
+        with pytest.raises(L.EmtError) as ex:
+            L.emt_apply(h, i_dev, v_dev, max_refine=2, tol=tol)
+        assert ex.value.code == L.EMT_ERR_UNSUPPORTED
+    L.emt_apply(h, i_dev, v_dev, max_refine=2, tol=0.0)
+    torch.cuda.synchronize()
+    assert torch.isfinite(v_dev).all()
+
+
 def test_hinv_get_partition_matches_tree_arrays(L):
     nw, gr = _store_inputs(netgen.tile(1_000_000))
     h = _build(L, (nw, gr), levels=2)
@@ -188,14 +202,14 @@ def test_paper_modify_matches_algorithm2(L):
         assert rel_err(_apply(L, h, X), H.apply(X)) <= 1e-10
 
 
-def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rpc=0, kernels=2):
+def _sim_compare(L, net, levels, steps, events, prec, mode=0, solver="dense", rpc=0, kernels=None):
     nw = oemt.Network(net, DT, levels=levels)
     oev = []
     for (st, kind, tgt, val) in events:
         oev.append((st, kind, tgt, val))
     ref, _ = oemt.simulate(nw, steps, oev, solver=solver)
     sim = L.emt_sim_create(net, DT, levels=levels, mode=mode, precision=prec)
-    if rpc or kernels != 2:
+    if kernels is not None:      # None: the launch shape emt_sim_create chose
         L.emt_sim_tune(sim, rpc, kernels)
     L.emt_sim_monitor(sim, np.arange(net["n_bus"]))
     for (st, kind, tgt, val) in events:
@@ -228,6 +242,30 @@ def test_sim_fault_on_off_and_cta_shapes(L, rpc, kernels):
     ev = [(30, 1, 17, 10.0), (90, 2, 17, 0.0), (100, 0, netgen.pick_branch(net), 0.0)]
     err = _sim_compare(L, net, 2, 140, ev, 1, rpc=rpc, kernels=kernels)
     assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("kernels,rpc", [(1, 0), (2, 0), (3, 0), (4, 8), (4, 16)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sim_changes_inside_fault_windows_match_oracle(L, prec, kernels, rpc):
+    # a trip inside a fault window, overlapping faults at two buses, back-to-back and stacked
+    # faults at one bus: clearing a fault takes back its own conductance only (Sec. IV), and the
+    # oracle's trajectory for these orders is pinned by Kirchhoff's law at every bus and step
+    from tests.test_oracle import _fault_event_sequences
+    net = netgen.tile(1_000_000)
+    for name, ev in _fault_event_sequences(net).items():
+        err = _sim_compare(L, net, 2, 60, ev, prec, rpc=rpc, kernels=kernels)
+        assert err <= TOL[prec], (name, err)
+
+
+def test_sim_fault_cleared_where_none_is_on_is_rejected_before_stepping(L):
+    net = netgen.tile(1_000_000)
+    sim = L.emt_sim_create(net, DT, levels=2, precision=L.EMT_PREC_FF64)
+    L.emt_sim_schedule(sim, 5, 1, 17, 10.0)
+    L.emt_sim_schedule(sim, 8, 2, 18, 0.0)
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_step(sim, 10)
+    assert ex.value.code == L.EMT_ERR_STATE
+    assert L.emt_sim_read(sim, 1)[0] == 0.0   # nothing was stepped
 
 
 @pytest.mark.parametrize("cs", [1, 2, 4, 8, 16])
@@ -281,6 +319,23 @@ def test_sim_1432_bus_matches_oracle(L, prec, kernels):
     e = netgen.pick_branch(net)
     err = _sim_compare(L, net, 3, 200, [(100, 0, e, 0.0)], prec, kernels=kernels)
     assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("net_name,levels", [("tile", 2), ("tiled", 3), ("small", 3)])
+def test_sim_create_runs_the_persistent_kernel_by_default(L, net_name, levels):
+    # no autotune: a fresh simulation runs generation 4 with the cluster the rule picks, launches
+    # one kernel per stretch between events, and matches the oracle
+    net = {"tile": lambda: netgen.tile(1_000_000), "tiled": lambda: netgen.tiled(2, 4),
+           "small": lambda: netgen.small_network(37, 5)}[net_name]()
+    sim = L.emt_sim_create(net, DT, levels=levels, precision=L.EMT_PREC_FF64)
+    before = L.emt_sim_stats(sim)["launches"]
+    L.emt_step(sim, 50)
+    torch.cuda.synchronize()
+    per_call = L.emt_sim_stats(sim)["launches"] - before
+    assert per_call <= 4, per_call      # set-up, trig table, one persistent launch, advance
+    e = netgen.pick_branch(net) if net_name != "small" else 3
+    err = _sim_compare(L, net, levels, 80, [(40, 0, e, 0.0)], 1)
+    assert err <= 1e-10, err
 
 
 def test_sim_reset_reproduces_run_bit_for_bit(L):
