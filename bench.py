@@ -1,18 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the GPU EMT network solve (bus-steps per second).
 
-Workload (default): the 1,432-bus network (8 seeded 179-bus tiles, 3-level
-hierarchy, 8 leaves of 179 buses), dt = 50 us, 20,000 time steps, one line trip
-(branch chosen by seed 7) at step 10,000, 16 monitored buses. One bench "step"
-is one whole simulation: every time step injects the sources, updates all
-branch histories, applies the hierarchical inverse (leaf blocks, boundary
-sweep, expansion) and, at the trip, modifies the stored inverse locally.
-Variants: float-float (FF64), FP32 with one FP64-residual refinement pass per
-step, plain FP64. Accuracy of every variant is measured against the CPU oracle
-(FP64, exact hierarchical store, explicit recomputation at the trip) over the
-full trajectory; the headline is the fastest variant within 1e-8.
+Default workload: the 11,456-bus network (64 seeded 179-bus tiles, 4-level
+hierarchy, 16 leaves of 716 buses), dt = 50 us, 512 scenarios (source and load
+amplitudes scaled by 1 + N(0, 5%) per column), 1,000 time steps. One bench
+"step" is the whole run: every time step updates all branch histories, injects
+the sources, applies the hierarchical inverse to the 512 right-hand sides
+(split-BF16 tensor-core products with FP32 accumulation) and refines once
+against the float-float residual r = i - G v. Accuracy is measured against the
+CPU oracle (FP64, exact hierarchical store) on 8 columns over all 1,000 steps.
+The same JSON line carries, as secondary keys, the single 1,432-bus simulation
+(20,000 steps with a line trip; FF64, FP32 + refinement and FP64 variants) and
+the single-vector apply on the 11,456-bus store (the HBM-bound form).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+--config picks one workload alone (1: 179 buses; 2: 1,432 buses; 3: N-1
+screening; 4: scenarios; 5: serving; 6: d_th sweep; 7: three phases; 41: the
+single apply). --gpus N splits the columns (3, 4) or the request stream (5)
+over N ranks, one per GPU; without an outside launcher it starts the ranks
+itself under torch.distributed.run.
+
+  python bench.py [--gpus N --steps K --warmup W] [--config C] [--impl reference]
 """
 from __future__ import annotations
 
@@ -42,11 +49,12 @@ def parse():
                     help="time steps per bench step (default: the workload's own; smaller values are for "
                          "profiling captures, not bench lines)")
     ap.add_argument("--variants", default="ff64,fp32,fp64")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7, 41],
-                    help="2: single 1,432-bus simulation (default); 3: N-1 screening, 256 contingencies; "
-                         "4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of 2,000 requests; "
-                         "6: PAPER-mode d_th sweep (approximation error, build and modification cost); "
-                         "7: three-phase 1,432-bus network (4,296 nodes): apply, line trip vs rebuild; "
+    ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 41],
+                    help="0 (default): config 4 with configs 2 and 41 as secondary keys of the same line; "
+                         "1: single 179-bus simulation; 2: single 1,432-bus simulation; 3: N-1 screening, 256 "
+                         "contingencies; 4: 11,456-bus network, 512 scenarios; 5: serving, Poisson stream of "
+                         "2,000 requests; 6: PAPER-mode d_th sweep (approximation error, build and modification "
+                         "cost); 7: three-phase 1,432-bus network (4,296 nodes): apply, line trip vs rebuild; "
                          "41: single apply on the 11,456-bus store")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--tune", default="", help="rows_per_cta,kernels: fixed launch shape instead of the autotuner "
@@ -67,8 +75,9 @@ def workload(rank: int = 0, cfg: int = 2):
 
 
 # ---------------------------------------------------------------- CPU oracle (test infrastructure)
-def multi_workload(cfg: int):
-    """Configs 3 and 4: network, per-column trips, scales, monitored buses, steps, levels."""
+def multi_workload(cfg: int, world: int = 1, rank: int = 0) -> dict:
+    """Configs 3 and 4: network, monitored buses, steps, levels, and this rank's block [c0, c1) of
+    the R columns with its trips (keyed by local column) and source/load scales (rows of the block)."""
     import numpy as np
     import netgen
     if cfg == 3:
@@ -83,7 +92,30 @@ def multi_workload(cfg: int):
         trips = {}
         ss, ls = netgen.scenario_scales(net, R, seed=13)
     mon = np.sort(np.random.default_rng(17).choice(net["n_bus"], N_MON, replace=False))
-    return net, trips, ss, ls, mon, R, steps, levels
+    c0, c1 = rank_columns(R, world, rank)
+    return dict(net=net, mon=mon, R=R, steps=steps, levels=levels, c0=c0, c1=c1,
+                trips={c - c0: trips[c] for c in range(c0, c1) if c in trips},
+                ss=None if ss is None else np.ascontiguousarray(ss[c0:c1]),
+                ls=None if ls is None else np.ascontiguousarray(ls[c0:c1]),
+                global_trips=trips, global_ss=ss, global_ls=ls)
+
+
+def rank_columns(R: int, world: int, rank: int):
+    """Contiguous block [c0, c1) of the R columns that rank `rank` of `world` steps; the blocks of
+    all ranks cover every column exactly once."""
+    return R * rank // world, R * (rank + 1) // world
+
+
+def rank_share(items, world: int, rank: int):
+    """Round-robin share of a request stream: the (global index, item) pairs rank `rank` serves."""
+    return [(i, x) for i, x in enumerate(items) if i % world == rank]
+
+
+def accuracy_columns(n_cols: int):
+    """Local columns the oracle checks: first, last, both sides of the 192-column tensor-core tile
+    edge, the middle and the ragged last tile (8 distinct columns when there are that many)."""
+    want = [0, 1, 191, 192, n_cols // 2, n_cols - 65, n_cols - 2, n_cols - 1]
+    return sorted({c for c in want if 0 <= c < n_cols})
 
 
 def cpu_worker(out_prefix: str, n_steps: int, cfg: int = 2, col: int = -1):
@@ -98,10 +130,11 @@ def cpu_worker(out_prefix: str, n_steps: int, cfg: int = 2, col: int = -1):
         half = n_steps // 2
         traj, _ = oemt.simulate(nw, n_steps, [(half, oemt.TRIP, trip, 0.0)], solver="exact", monitor=mon)
     else:
-        net, trips, ss, ls, mon, R, steps, levels = multi_workload(cfg)
-        nw = oemt.Network(net, DT, levels=levels)
+        w = multi_workload(cfg)
+        trips, ss, ls = w["global_trips"], w["global_ss"], w["global_ls"]
+        nw = oemt.Network(w["net"], DT, levels=w["levels"])
         ev = [(trips[col][0], oemt.TRIP, trips[col][1], 0.0)] if col in trips else []
-        traj, _ = oemt.simulate(nw, n_steps, ev, solver="exact", monitor=mon,
+        traj, _ = oemt.simulate(nw, n_steps, ev, solver="exact", monitor=w["mon"],
                                 src_scale=None if ss is None else ss[col], load_scale=None if ls is None else ls[col])
     t1 = time.perf_counter()
     np.save(out_prefix + ".npy", traj)
@@ -109,15 +142,32 @@ def cpu_worker(out_prefix: str, n_steps: int, cfg: int = 2, col: int = -1):
 
 
 def run_cpu_oracle(n_steps: int, cfg: int = 2, col: int = -1):
+    trajs, secs = run_cpu_oracle_columns(n_steps, cfg, [col])
+    return trajs[0], secs[0]
+
+
+def run_cpu_oracle_columns(n_steps: int, cfg: int, cols):
+    """The oracle on several columns, each in its own single-threaded process, at most one process
+    per host core at a time; returns the trajectories and each process's own wall seconds."""
     import numpy as np
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cols = list(cols)
+    par = max(1, min(len(cols), os.cpu_count() or 1))
+    trajs, secs = [None] * len(cols), [0.0] * len(cols)
     with tempfile.TemporaryDirectory() as td:
-        pre = os.path.join(td, "oracle")
-        subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", pre, "--cpu-steps", str(n_steps),
-                        "--config", str(cfg), "--cpu-col", str(col)], check=True, env=env)
-        traj = np.load(pre + ".npy")
-        meta = json.load(open(pre + ".json"))
-    return traj, meta["seconds"]
+        for k0 in range(0, len(cols), par):
+            procs = []
+            for k in range(k0, min(len(cols), k0 + par)):
+                pre = os.path.join(td, f"oracle{k}")
+                procs.append((k, pre, subprocess.Popen(
+                    [sys.executable, os.path.abspath(__file__), "--cpu-worker", pre, "--cpu-steps", str(n_steps),
+                     "--config", str(cfg), "--cpu-col", str(cols[k])], env=env)))
+            for k, pre, p in procs:
+                if p.wait() != 0:
+                    raise RuntimeError(f"oracle worker for column {cols[k]} failed")
+                trajs[k] = np.load(pre + ".npy")
+                secs[k] = json.load(open(pre + ".json"))["seconds"]
+    return trajs, secs
 
 
 # ---------------------------------------------------------------- clocks
@@ -192,6 +242,31 @@ def job_rate(units_per_rank: float, world: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
+def job_units(local_units: float, world: int, device=None) -> float:
+    """Units processed by all ranks together, each rank counting only the distinct units it ran."""
+    import torch
+    t = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def launch_ranks(args):
+    """`--gpus N` with no launcher around this process: start N ranks, one per GPU, under
+    torch.distributed.run and return their exit status. None when this process is a rank already
+    (WORLD_SIZE set) or N is 1."""
+    if args.gpus <= 1 or "WORLD_SIZE" in os.environ:
+        return None
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def rel_err(got, ref):
     import numpy as np
     return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
@@ -205,52 +280,104 @@ def workload_name(cfg: int) -> str:
              "16 monitored buses"))
 
 
+def multi_name(cfg: int) -> str:
+    return ("N-1 screening: 256 contingencies on the 1432-bus network, each trips a different branch at step "
+            "1000, 5000 steps" if cfg == 3 else
+            "11456-bus network (64 tiles), 4-level hierarchy, 512 scenarios (+-5% source/load), 1000 steps")
+
+
 def reference_arm(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    """The oracle as it stands, single-threaded on the host cores, on a bounded sample of the
+    workload the native arm runs (same config, metric and unit). Rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    net, _, _ = workload()
-    sample = 2000
-    times = []
-    for i in range(args.warmup + args.steps):
-        _, sec = run_cpu_oracle(sample)
-        if i >= args.warmup:
-            times.append(sec)
     import numpy as np
-    t = float(np.mean(times))
-    v = net["n_bus"] * sample / t
+    cfg = 4 if args.config in (0, 4) else args.config
+    if cfg in (3, 4):
+        from oracle import emt as oemt
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        w = multi_workload(cfg)
+        net, R, T = w["net"], w["R"], w["steps"]
+        n = net["n_bus"]
+        nw = oemt.Network(net, DT, levels=w["levels"])    # partition and network set-up, once
+        trips, ss, ls = w["global_trips"], w["global_ss"], w["global_ls"]
+        sample = 20 if cfg == 4 else 200                   # time steps of one column per bench step
+        times = []
+        for i in range(args.warmup + args.steps):
+            col = (i * 97) % R
+            ev = [(trips[col][0], oemt.TRIP, trips[col][1], 0.0)] if col in trips else []
+            t0 = time.perf_counter()
+            oemt.simulate(nw, sample, ev, solver="exact", monitor=w["mon"],
+                          src_scale=None if ss is None else ss[col], load_scale=None if ls is None else ls[col])
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        t = float(np.mean(times))
+        v = n * sample / t
+        desc = (f"{sample} time steps of one column per step (columns 97 i mod {R}), FP64 exact hierarchical store "
+                "built once, single thread")
+        config = {"workload": multi_name(cfg), "buses": n, "columns": R, "time_steps_per_step": T,
+                  "sample_time_steps": sample}
+        ms = t * 1e3
+    else:
+        net, _, _ = workload(0, 2 if cfg not in (1, 2) else cfg)
+        sample = 2000
+        times = []
+        for i in range(args.warmup + args.steps):
+            _, sec = run_cpu_oracle(sample, 2 if cfg not in (1, 2) else cfg)
+            if i >= args.warmup:
+                times.append(sec)
+        t = float(np.mean(times))
+        v = net["n_bus"] * sample / t
+        desc = (f"{sample} time steps of the {net['n_bus']}-bus workload (trip at step {sample // 2}), FP64 exact "
+                "hierarchical store, single thread")
+        config = {"workload": workload_name(2 if cfg not in (1, 2) else cfg), "time_steps_per_step": 20000,
+                  "buses": net["n_bus"], "mode": "exact", "sample_time_steps": sample}
+        ms = t * 1e3
     print(json.dumps({
         "impl": "reference", "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": v,
         "unit": "bus-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": workload_name(2), "time_steps_per_step": 20000, "buses": net["n_bus"], "mode": "exact",
-                   "sample_time_steps": sample},
-        "cpu_baseline": {"value": v, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} time steps of the 1,432-bus workload (trip at step {sample // 2}), "
-                                   "FP64 exact hierarchical store, single thread"},
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": v, "unit": "bus-steps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "bus-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 # ---------------------------------------------------------------- native arm
-def native_arm(args):
-    import numpy as np
+def ranks():
+    """(rank, world size, local rank) of this process; the CUDA device is the local rank's."""
     import torch
-    import torch.distributed as dist
-    import paper_2105_10661_gb300._lib as L
-
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def step4_ceilings(n_cta: int, sm_mhz: float, store_bytes_per_step: float, ff_fma_per_step: float) -> dict:
+    """On-chip time bounds of one time step of the persistent cluster kernel, whose store lives in
+    the shared memory of its n_cta CTAs (one per SM): reading the store once from shared memory at
+    128 B per clock per SM, and its float-float FMAs at about 14 per clock per SM (measured at
+    full occupancy); in microseconds."""
+    hz = sm_mhz * 1e6
+    return {"smem_read_us": store_bytes_per_step / (n_cta * 128.0 * hz) * 1e6,
+            "ff_fma_us": ff_fma_per_step / (n_cta * 14.0 * hz) * 1e6,
+            "smem_peak_gbs": n_cta * 128.0 * hz / 1e9}
+
+
+def native_arm(args, cfg: int):
+    """Configs 1 and 2: one simulation per rank (replicas). Returns the JSON line on rank 0."""
+    import numpy as np
+    import torch
+    import paper_2105_10661_gb300._lib as L
+
+    rank, world, local = ranks()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    T = (args.time_steps or 20000) if args.config == 2 else (args.time_steps or 2000)
-    LV = 3 if args.config == 2 else 2
-    net, trip, mon = workload(rank, args.config)
+    T = (args.time_steps or 20000) if cfg == 2 else (args.time_steps or 2000)
+    LV = 3 if cfg == 2 else 2
+    net, trip, mon = workload(rank, cfg)
     n = net["n_bus"]
     prec = {"ff64": L.EMT_PREC_FF64, "fp32": L.EMT_PREC_FP32, "fp64": L.EMT_PREC_FP64}
     names = [v for v in args.variants.split(",") if v]
@@ -259,13 +386,38 @@ def native_arm(args):
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
+
+    # end to end through the C ABI from host buffers, with the launch shape emt_sim_create picks on
+    # its own (before this process autotunes anything, so no tuned shape is cached yet)
+    e2e = {}
+    rec_host = torch.empty(T, N_MON, dtype=torch.float64, pin_memory=True)
+    h2d = sum(int(np.asarray(net[k]).nbytes) for k in ("br_a", "br_b", "kind", "R", "L", "C", "shunt_C", "src_bus",
+                                                          "src_Vm", "src_phi", "src_Rs"))
+    for name in names:
+        e2e_times = []
+        for i in range(max(1, min(args.steps, 3)) + 1):
+            barrier()
+            t0 = time.perf_counter()
+            s2 = L.emt_sim_create(net, DT, levels=LV, mode=L.EMT_MODE_EXACT, precision=prec[name])
+            L.emt_sim_schedule(s2, T // 2, L.EMT_EVENT_TRIP, trip)
+            L.emt_sim_monitor(s2, mon)
+            rec2 = torch.empty(T, N_MON, dtype=torch.float64, device=dev)
+            L.emt_step(s2, T, rec2, stream)
+            rec_host.copy_(rec2, non_blocking=True)
+            torch.cuda.synchronize()
+            del s2
+            t1 = time.perf_counter()
+            if i > 0:
+                e2e_times.append(t1 - t0)
+        e2e[name] = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
 
     # oracle trajectory (accuracy reference and CPU baseline), rank 0 only, in a subprocess
     ref = None
     cpu_sec = None
     if rank == 0:
-        ref, cpu_sec = run_cpu_oracle(T, args.config)
+        ref, cpu_sec = run_cpu_oracle(T, cfg)
 
     results = {}
     clocks = Clocks(local)
@@ -312,7 +464,8 @@ def native_arm(args):
     st = L.emt_sim_stats(sim)
     value = job_rate(n * T, world, H["ms"])
 
-    # roofline of the dominant kernel (timed alone as a graph of back-to-back launches)
+    # roofline of the dominant kernel (timed alone: a graph of back-to-back launches, or one
+    # persistent launch running `reps` steps)
     reps = 2000
     kt = {}
     for which in (0, 1):
@@ -324,7 +477,7 @@ def native_arm(args):
         L.emt_sim_bench_kernel(sim, which, reps, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        kt[which] = e0.elapsed_time(e1) / reps * 1e3   # us per launch
+        kt[which] = e0.elapsed_time(e1) / reps * 1e3   # us per launch (per time step for generation 4)
     L.emt_sim_reset(sim, stream)
     gen4 = H["tuned"]["kernels"] == 4
     s_bytes = 4 if head == "fp32" else 8
@@ -334,22 +487,30 @@ def native_arm(args):
     dom = 0 if kt[0] >= kt[1] else 1
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    # per bus-step bytes of the method's own data (store rows and the state a step touches), the
+    # HBM-roofline accounting of the measurement plan: s (b + sum over the path of k) + 60 B
+    leaf_b = st["leaf_elems"] / max(n, 1)
+    path_k = st["factor_elems"] / max(n, 1)
+    plan_bytes = (s_bytes * (leaf_b + path_k) + 60.0) * n
     if gen4:
-        # one persistent launch runs every step: per-step bytes of the store it streams (from
-        # shared memory) over the per-step time of a launch running `reps` steps
+        # the store lives in the shared memory of one cluster: the step is bound on chip (shared-
+        # memory reads of the store and float-float FMAs on n_cta SMs) and by the latency of its
+        # phase chain, not by HBM
+        cs = H["tuned"]["rows_per_cta"]
         byts = b_partial + b_sweep
+        ff = st["leaf_elems"] + st["factor_elems"] + st["s_total"] * st["n_cut_rows"]   # leaf, expansion, s = K y_cut
+        ceil = step4_ceilings(cs, clk.get("sm_mhz") or 2070.0, byts, ff)
         ach = byts / (kt[0] * 1e-6) / 1e9
-        # DRAM traffic of this kernel from an ncu capture of one 1,000-step launch on this workload
-        # (dram__bytes_read.sum + dram__bytes_write.sum = 3,263,232 B: the store, read once),
-        # per time step like `achieved`
-        roofline = {"bound": "hbm", "kernel": "k_step4", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"],
-                    "traffic": 3263232 / 1000 if args.config == 2 and H["tuned"]["rows_per_cta"] == 16 else None,
-                    "traffic_unit": "bytes per time step",
-                    "us_per_step": kt[0],
-                    "algorithmic_bytes_per_step": byts, "cluster_ctas": H["tuned"]["rows_per_cta"],
-                    "peak_source": "measured" if "when" in peaks else "fallback",
-                    "note": "store resident in the shared memory of one cluster; per-step latency, not HBM, bounds it"}
+        roofline = {"bound": "smem", "kernel": "k_step4", "achieved": ach, "peak": ceil["smem_peak_gbs"],
+                    "unit": "GB/s", "frac": ach / ceil["smem_peak_gbs"], "traffic": None,
+                    "us_per_step": kt[0], "algorithmic_bytes_per_step": byts, "cluster_ctas": cs,
+                    "ceilings_us_per_step": {"smem_read": ceil["smem_read_us"], "ff_fma": ceil["ff_fma_us"]},
+                    "hbm_view": {"bytes_per_step": plan_bytes, "achieved_gbs": plan_bytes / (kt[0] * 1e-6) / 1e9,
+                                 "frac_of_hbm": plan_bytes / (kt[0] * 1e-6) / 1e9 / peaks["hbm_gbs"]},
+                    "peak_source": f"shared-memory read bandwidth of {cs} SMs (128 B/clock each) at the median "
+                                   "SM clock sampled in the timed region",
+                    "note": "store resident in the shared memory of one thread-block cluster; the per-step chain "
+                            "of dependent phases (latency) bounds it, far above both on-chip ceilings"}
     else:
         ach = (b_partial if dom == 0 else b_sweep) / (kt[dom] * 1e-6) / 1e9
         roofline = {"bound": "hbm", "kernel": "k_step_partial" if dom == 0 else "k_step_sweep", "achieved": ach,
@@ -358,90 +519,90 @@ def native_arm(args):
                     "algorithmic_bytes_per_launch": {"k_step_partial": b_partial, "k_step_sweep": b_sweep},
                     "peak_source": "measured" if "when" in peaks else "fallback"}
 
-    # end to end through the C ABI from host buffers
-    e2e_times = []
-    rec_host = torch.empty(T, N_MON, dtype=torch.float64, pin_memory=True)
-    h2d = sum(int(np.asarray(net[k]).nbytes) for k in ("br_a", "br_b", "kind", "R", "L", "C", "shunt_C", "src_bus",
-                                                          "src_Vm", "src_phi", "src_Rs"))
-    for i in range(max(1, min(args.steps, 3)) + 1):
-        barrier()
-        t0 = time.perf_counter()
-        s2 = L.emt_sim_create(net, DT, levels=LV, mode=L.EMT_MODE_EXACT, precision=prec[head])
-        if args.tune:
-            L.emt_sim_tune(s2, *H["tuned"].values())
-        L.emt_sim_schedule(s2, T // 2, L.EMT_EVENT_TRIP, trip)
-        L.emt_sim_monitor(s2, mon)
-        rec2 = torch.empty(T, N_MON, dtype=torch.float64, device=dev)
-        L.emt_step(s2, T, rec2, stream)
-        rec_host.copy_(rec2, non_blocking=True)
-        torch.cuda.synchronize()
-        del s2
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e_times.append(t1 - t0)
-    e2e_ms = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
-    e2e_val = job_rate(n * T, world, e2e_ms)
-
-    if rank == 0:
-        line = {
-            "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
-            "config": {"workload": workload_name(args.config),
-                       "time_steps_per_step": T, "buses": n, "mode": "exact", "l2": "flushed between timed steps",
-                       "parallelism": f"replicas x{world}"},
-            "accuracy": {k: results[k]["err"] for k in names},
-            "variants_ms_per_step": {k: results[k]["ms"] for k in names},
-            "autotuned": {k: results[k]["tuned"] for k in names},
-            "variants_bus_steps_per_s": {k: world * n * T / (results[k]["ms"] / 1e3) for k in names},
-            "roofline": roofline,
-            "cpu_baseline": {"value": n * T / cpu_sec, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"full workload ({T} time steps incl. the trip), FP64 exact hierarchical "
-                                       "store with explicit recomputation at the trip, single thread"},
-            "e2e": {"value": e2e_val, "unit": "bus-steps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": T * N_MON * 8,
-                    "includes": "emt_sim_create from host arrays (partition, GPU build), emt_step, D2H of the record"},
-            "gpu_launches": int(H["launches"]),
-            "clocks": clk,
-        }
-        print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {
+        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
+        "config": {"workload": workload_name(cfg),
+                   "time_steps_per_step": T, "buses": n, "mode": "exact", "l2": "flushed between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "accuracy": {k: results[k]["err"] for k in names},
+        "variants_ms_per_step": {k: results[k]["ms"] for k in names},
+        "autotuned": {k: results[k]["tuned"] for k in names},
+        "variants_bus_steps_per_s": {k: world * n * T / (results[k]["ms"] / 1e3) for k in names},
+        "roofline": roofline,
+        "cpu_baseline": {"value": n * T / cpu_sec, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full workload ({T} time steps incl. the trip), FP64 exact hierarchical "
+                                   "store with explicit recomputation at the trip, single thread"},
+        "e2e": {"value": job_rate(n * T, world, e2e[head]), "unit": "bus-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": T * N_MON * 8,
+                "variants": {k: job_rate(n * T, world, v) for k, v in e2e.items()},
+                "includes": "emt_sim_create from host arrays (partition, GPU build, the launch shape it picks "
+                            "itself), emt_step, D2H of the record; measured before any autotuning in this process"},
+        "gpu_launches": int(H["launches"]),
+        "clocks": clk,
+    }
 
 
 # ---------------------------------------------------------------- configs 3 and 4 (many columns)
-def multi_arm(args):
+def multi_arm(args, cfg: int):
+    """Configs 3 and 4: R columns stepped together, split into one contiguous block per rank (no
+    collective on the data path). Returns the JSON line on rank 0, None elsewhere."""
     import numpy as np
     import torch
-    import torch.distributed as dist
     import paper_2105_10661_gb300._lib as L
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    rank, world, local = ranks()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    net, trips, ss, ls, mon, R, T, levels = multi_workload(args.config)
-    T = args.time_steps or T
+    w = multi_workload(cfg, world, rank)
+    net, mon, R, levels = w["net"], w["mon"], w["R"], w["levels"]
+    T = args.time_steps or w["steps"]
+    Rl = w["c1"] - w["c0"]
+    trips, ss, ls = w["trips"], w["ss"], w["ls"]
     n = net["n_bus"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
 
     tune = [int(x) for x in args.tune.split(",")] if args.tune else None
-    sim = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=R, src_scale=ss, load_scale=ls)
-    if tune:
-        L.emt_sim_tune(sim, *tune)
-    for c, (st, e) in trips.items():
-        L.emt_sim_schedule(sim, st, L.EMT_EVENT_TRIP, e, 0.0, c)
-    L.emt_sim_monitor(sim, mon)
-    rec = torch.zeros(T, R, N_MON, dtype=torch.float64, device=dev)
+
+    def create():
+        sm = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=Rl, src_scale=ss, load_scale=ls)
+        if tune:
+            L.emt_sim_tune(sm, *tune)
+        for c, (st_, e) in trips.items():
+            L.emt_sim_schedule(sm, st_, L.EMT_EVENT_TRIP, e, 0.0, c)
+        L.emt_sim_monitor(sm, mon)
+        return sm
+
+    # end to end through the C ABI from host arrays, first, in a process that has timed nothing yet:
+    # build, schedule, step, record read back to pinned host memory
+    rec = torch.zeros(T, Rl, N_MON, dtype=torch.float64, device=dev)
+    rec_host = torch.empty(T, Rl, N_MON, dtype=torch.float64, pin_memory=True)
+    h2d = sum(int(np.asarray(net[k]).nbytes) for k in ("br_a", "br_b", "kind", "R", "L", "C", "shunt_C", "src_bus",
+                                                          "src_Vm", "src_phi", "src_Rs"))
+    h2d += (0 if ss is None else np.asarray(ss).nbytes) + (0 if ls is None else np.asarray(ls).nbytes)
+    e2e_times = []
+    for i in range(max(1, min(args.steps, 2)) + 1):
+        barrier()
+        t0 = time.perf_counter()
+        s2 = create()
+        L.emt_step(s2, T, rec, stream)
+        rec_host.copy_(rec, non_blocking=True)
+        torch.cuda.synchronize()
+        del s2
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_times.append(t1 - t0)
+
+    sim = create()
     for _ in range(args.warmup):
         L.emt_sim_reset(sim, stream)
         L.emt_step(sim, T, rec, stream)
@@ -463,7 +624,10 @@ def multi_arm(args):
     clk = clocks.stop()
     launches = (L.emt_sim_stats(sim)["launches"] - l0) // args.steps
     ms = job_ms(float(np.mean(times)), world, dev)
-    value = job_rate(n * R * T, world, ms)
+    units = job_units(n * Rl * T, world, dev)     # each column counted once, on the rank that ran it
+    value = units / (ms / 1e3)
+    e2e_ms = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
+    e2e_val = units / (e2e_ms / 1e3)
     traj = rec.cpu().numpy()
     st = L.emt_sim_stats(sim)
 
@@ -483,48 +647,21 @@ def multi_arm(args):
         torch.cuda.synchronize()
         kus[which] = e0.elapsed_time(e1) / reps * 1e3
     L.emt_sim_reset(sim, stream)
-    us_gemm = kus[0]
 
-    # end to end through the C ABI from host arrays: build, schedule, step, record read back
-    e2e_times = []
-    rec_host = torch.empty(T, R, N_MON, dtype=torch.float64, pin_memory=True)
-    h2d = sum(int(np.asarray(net[k]).nbytes) for k in ("br_a", "br_b", "kind", "R", "L", "C", "shunt_C", "src_bus",
-                                                          "src_Vm", "src_phi", "src_Rs"))
-    h2d += (0 if ss is None else np.asarray(ss).nbytes) + (0 if ls is None else np.asarray(ls).nbytes)
-    for i in range(max(1, min(args.steps, 2)) + 1):
-        barrier()
-        t0 = time.perf_counter()
-        s2 = L.emt_sim_create(net, DT, levels=levels, mode=L.EMT_MODE_EXACT, nrhs=R, src_scale=ss, load_scale=ls)
-        if tune:
-            L.emt_sim_tune(s2, *tune)
-        for c, (stp, e) in trips.items():
-            L.emt_sim_schedule(s2, stp, L.EMT_EVENT_TRIP, e, 0.0, c)
-        L.emt_sim_monitor(s2, mon)
-        L.emt_step(s2, T, rec, stream)
-        rec_host.copy_(rec, non_blocking=True)
-        torch.cuda.synchronize()
-        del s2
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e_times.append(t1 - t0)
-    e2e_ms = job_ms(float(np.mean(e2e_times)) * 1e3, world, dev)
-    e2e_val = job_rate(n * R * T, world, e2e_ms)
-    # accuracy on sampled columns over a bounded number of steps (oracle, single thread)
-    acc_cols = [0, R - 1] if args.config == 4 else [0, R // 2, R - 1]
-    acc_steps = T if args.config == 3 else min(100, T)
-    errs = {}
-    cpu_sec = 0.0
+    # accuracy: the oracle on 8 of this rank's columns over every time step (rank 0; one
+    # single-threaded process per column)
+    errs, cpu_rate, acc_cols = {}, None, []
     if rank == 0:
-        for c in acc_cols:
-            ref, sec = run_cpu_oracle(acc_steps, args.config, c)
-            cpu_sec += sec
-            errs[c] = rel_err(traj[:acc_steps, c, :], ref)
-    cpu_rate = n * acc_steps * len(acc_cols) / cpu_sec if cpu_sec else None
+        acc_cols = accuracy_columns(Rl)
+        refs, secs = run_cpu_oracle_columns(T, cfg, [w["c0"] + c for c in acc_cols])
+        for c, ref in zip(acc_cols, refs):
+            errs[w["c0"] + c] = rel_err(traj[:, c, :], ref)
+        cpu_rate = n * T * len(acc_cols) / sum(secs)
     # leaf GEMM: 2 sum(b_j^2) R algorithmic flops per launch (FP32-grade products, each formed as
     # three BF16 tensor-core products hi*hi + hi*lo + lo*hi)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
-    flops_gemm = 2 * st["leaf_elems"] * R
+    flops_gemm = 2 * st["leaf_elems"] * Rl
     peak_tf = peaks["bf16_tflops"] / 3.0
     hbm = peaks.get("hbm_gbs", 6800.0)
     fp32_peak = 69.4   # TFLOP/s FP32 FMA (2 flops per FMA), measured by the probe on this GB300
@@ -534,53 +671,53 @@ def multi_arm(args):
     # and neighbour voltages, source terms, X (float-float) and Xf written; residual: X and the
     # CSR neighbours' V read, Xf written (neighbour re-reads hit L2: counted once)
     n_el = st["n_elements"]
-    n_terms_b = (net["n_src"] if "n_src" in net else len(net["src_bus"])) + len(net.get("load_bus", []))
-    inj_bytes = (2 * n_el * 8 + n * 8 + n_terms_b * 16 + n * 12) * R
-    res_bytes = n * (8 + 8 + 4) * R
+    n_terms_b = len(net["src_bus"]) + len(net.get("load_bus", []))
+    inj_bytes = (2 * n_el * 8 + n * 8 + n_terms_b * 16 + n * 12) * Rl
+    res_bytes = n * (8 + 8 + 4) * Rl
     per = {
         "k_mc_umma<leaf> (tcgen05 BF16x3)": (kus[0], 2, "tensor", flops_gemm / 1e12, peak_tf, "TFLOP/s"),
-        "k_split_b (BF16 hi/lo split)": (kus[1], 2, "hbm", n * R * 8 / 1e9, hbm, "GB/s"),
+        "k_split_b (BF16 hi/lo split)": (kus[1], 2, "hbm", n * Rl * 8 / 1e9, hbm, "GB/s"),
         "k_mc_sweep_gemm (FP32 SIMT, split-K over nonzero column pieces)":
-            (kus[2], 2, "alu", 2 * st["s_total"] * st["n_cut_rows"] * R / 1e12, fp32_peak, "TFLOP/s"),
+            (kus[2], 2, "alu", 2 * st["s_total"] * st["n_cut_rows"] * Rl / 1e12, fp32_peak, "TFLOP/s"),
         "expansion (tcgen05 k_mc_umma<expand> when it has a tile per SM, else SIMT k_mc_expand_tiled)":
-            (kus[3], 2, "hbm", n * R * 20 / 1e9, hbm, "GB/s"),
+            (kus[3], 2, "hbm", n * Rl * 20 / 1e9, hbm, "GB/s"),
         "k_mc_inject (histories + injection, float-float)": (kus[4], 1, "hbm", inj_bytes / 1e9, hbm, "GB/s"),
         "k_mc_residual (float-float r = x - G'v)": (kus[5], 1, "hbm", res_bytes / 1e9, hbm, "GB/s"),
     }
     kernels = {}
+    my_ms = float(np.mean(times))
     for name, (us, per_step, bound, work, peak, unit) in per.items():
         ach = work / (us * 1e-6)
         kernels[name] = {"us_per_launch": us, "launches_per_time_step": per_step, "bound": bound, "achieved": ach,
                          "peak": peak, "unit": unit, "frac": ach / peak,
-                         "share_of_step": per_step * us * T / 1e3 / ms}
+                         "share_of_step": per_step * us * T / 1e3 / my_ms}
     dom = max(kernels, key=lambda k: kernels[k]["share_of_step"])
-    if rank == 0:
-        name = ("N-1 screening: 256 contingencies on the 1432-bus network, each trips a different branch at step "
-                "1000, 5000 steps" if args.config == 3 else
-                "11456-bus network (64 tiles), 4-level hierarchy, 512 scenarios (+-5% source/load), 1000 steps")
-        print(json.dumps({
-            "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff64-refine", "data": "synthetic",
-            "config": {"workload": name, "buses": n, "columns": R, "time_steps_per_step": T,
-                       "l2": "flushed between timed steps"},
-            "accuracy": {"sampled_columns": {str(k): v for k, v in errs.items()}, "sampled_steps": acc_steps,
-                         "max": max(errs.values()) if errs else None},
-            "roofline": dict(kernels[dom], kernel=dom, traffic=None,
-                             peak_source=("measured" if "when" in peaks else "fallback")
-                             + " (tensor: bf16 burst / 3, three BF16 products per FP32-grade product; hbm: copy; "
-                               "alu: FP32 FMA rate of the probe)",
-                             kernels=kernels),
-            "e2e": {"value": e2e_val, "unit": "bus-steps/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": T * R * N_MON * 8,
-                    "includes": "emt_sim_create from host arrays (partition, GPU build), trip scheduling, emt_step, "
-                                "D2H of the record"},
-            "cpu_baseline": {"value": cpu_rate, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"columns {acc_cols}, {acc_steps} steps each, exact hierarchical store"},
-            "gpu_launches": int(launches), "clocks": clk,
-        }))
-    if world > 1:
-        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    name = multi_name(cfg)
+    return {
+        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": value, "unit": "bus-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "bf16x3-f32acc+ff64-refine", "data": "synthetic",
+        "config": {"workload": name, "buses": n, "columns": R, "columns_per_rank": Rl, "time_steps_per_step": T,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"columns split over {world} rank(s), no collective on the data path"},
+        "accuracy": {"sampled_columns": {str(k): v for k, v in errs.items()}, "sampled_steps": T,
+                     "max": max(errs.values()) if errs else None, "tolerance": ERR_TOL},
+        "roofline": dict(kernels[dom], kernel=dom, traffic=None,
+                         peak_source=("measured" if "when" in peaks else "fallback")
+                         + " (tensor: bf16 burst / 3, three BF16 products per FP32-grade product; hbm: copy; "
+                           "alu: FP32 FMA rate of the probe)",
+                         kernels=kernels),
+        "e2e": {"value": e2e_val, "unit": "bus-steps/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": T * Rl * N_MON * 8,
+                "includes": "emt_sim_create from host arrays (partition, GPU build), trip scheduling, emt_step, "
+                            "D2H of the record; measured first, in a process that had run nothing else"},
+        "cpu_baseline": {"value": cpu_rate, "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"columns {[w['c0'] + c for c in acc_cols]}, {T} steps each, FP64 exact "
+                                   "hierarchical store, each column single-threaded in its own process"},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
 
 
 # ---------------------------------------------------------------- config 5 (serving)
@@ -611,15 +748,17 @@ def serve_requests(nets, n_req, seed, rate, steps_lo=1000, steps_hi=10000, priv=
 
 
 def serve_arm(args):
+    """Config 5. With N ranks the stream carries N times the requests at N times the rate, dealt
+    round-robin, so every rank (one server per GPU) sees the one-GPU load (weak scaling);
+    latencies of all ranks' requests are gathered for p50/p99. Returns the JSON line on rank 0."""
     import numpy as np
     import torch
     import netgen
     import paper_2105_10661_gb300._lib as L
     from oracle import emt as oemt
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rank, world, local = ranks()
+    dev = torch.device("cuda", local)
     nets = [(netgen.tile(1_000_000), 2, 256), (netgen.tiled(2, 4), 3, 256), (netgen.config_network(4), 4, 128)]
     mons = [np.sort(np.random.default_rng(17 + i).choice(n[0]["n_bus"], N_MON, replace=False)) for i, n in enumerate(nets)]
     # private networks: a pool of seeded 179-bus tiles that requests bring with them (10 % of the
@@ -646,17 +785,37 @@ def serve_arm(args):
         submit(srv, ids, r)
     L.emt_server_run(srv)
     cst = L.emt_server_stats(srv)
-    sat_rate = cst["finished"] / cst["wall_s"]
+    # one GPU's saturated rate, averaged over the ranks' calibrations
+    sat_rate = job_units(cst["finished"] / cst["wall_s"], world, dev) / world
     del srv
-    # the measured run: Poisson arrivals at 80% of the saturated rate
-    rate = 0.8 * sat_rate
-    reqs = serve_requests(nets, args.requests, 17, rate, priv=priv, priv_frac=priv_frac)
+    # the measured run: Poisson arrivals at 80% of the saturated rate per GPU
+    rate = 0.8 * sat_rate * world
+    reqs_all = serve_requests(nets, args.requests * world, 17, rate, priv=priv, priv_frac=priv_frac)
+    mine = rank_share(reqs_all, world, rank)
+    reqs = [r for _, r in mine]
     srv, ids = make_server()
     rids = [submit(srv, ids, r) for r in reqs]
-    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(local)
     L.emt_server_run(srv)
     clk = clocks.stop()
     st = L.emt_server_stats(srv)
+    lat = []
+    for rid in rids:
+        _, tm = L.emt_server_result(srv, rid)
+        lat.append(float(tm[2] - tm[0]))
+    wall = job_ms(st["wall_s"] * 1e3, world, dev) / 1e3
+    bus_steps = job_units(st["bus_steps"], world, dev)
+    if world > 1:
+        import torch.distributed as dist
+        gathered = [None] * world
+        dist.all_gather_object(gathered, lat)
+        lat = [x for part in gathered for x in part]
+    if rank != 0:
+        return None
+    lat_np = np.asarray(lat)
     # accuracy: oracle on sampled short requests of the two smaller networks
     errs = {}
     cpu_sec = 0.0
@@ -676,16 +835,20 @@ def serve_arm(args):
         cpu_bus_steps += steps * net["n_bus"]
         got, _ = L.emt_server_result(srv, rids[i])
         errs[str(i)] = rel_err(got, ref)
-    print(json.dumps({
-        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle; p50/p99 served latency", "value": st["bus_steps_per_s"],
-        "unit": "bus-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": st["wall_s"] * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff64-refine", "data": "synthetic",
-        "config": {"workload": f"serving: Poisson stream of {args.requests} requests over resident 179/1432/11456-bus "
-                               "networks (10% bring one of 16 private 179-bus networks, built on first arrival), "
-                               "1000-10000 steps each, a line trip or a 10-ohm 400-step bus fault per request",
-                   "arrival_rate_req_per_s": rate, "saturated_rate_req_per_s": sat_rate, "tick_steps": 100,
-                   "slots": [n[2] for n in nets]},
-        "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "max": st["max_s"]},
+    return {
+        "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle; p50/p99 served latency", "value": bus_steps / wall,
+        "unit": "bus-steps/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3-f32acc+ff64-refine",
+        "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {args.requests} requests per GPU over resident "
+                               "179/1432/11456-bus networks (10% bring one of 16 private 179-bus networks, built on "
+                               "first arrival), 1000-10000 steps each, a line trip or a 10-ohm 400-step bus fault per "
+                               "request",
+                   "arrival_rate_req_per_s": rate, "saturated_rate_req_per_s_per_gpu": sat_rate, "tick_steps": 100,
+                   "slots": [n[2] for n in nets],
+                   "parallelism": f"requests dealt round-robin over {world} rank(s), one server per GPU"},
+        "latency_s": {"p50": float(np.percentile(lat_np, 50)), "p99": float(np.percentile(lat_np, 99)),
+                      "max": float(lat_np.max()), "requests": len(lat)},
         "served": {k: st[k] for k in ("wall_s", "bus_steps", "max_queue", "ticks", "finished")},
         "private_networks": {"requests": sum(1 for r in reqs if r[0] >= PRIV_BASE), "pool": len(priv),
                              "builds": st["builds"], "cache_hits": st["cache_hits"], "build_s": st["build_s"],
@@ -694,7 +857,7 @@ def serve_arm(args):
         "cpu_baseline": {"value": cpu_bus_steps / cpu_sec if cpu_sec else None, "unit": "bus-steps/s", "cores": 1,
                          "kind": "oracle", "sample": f"{len(picks)} sampled requests, exact hierarchical store"},
         "clocks": clk,
-    }))
+    }
 
 
 # ---------------------------------------------------------------- config 4': single-vector apply, HBM bound
@@ -716,6 +879,7 @@ def apply_arm(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     x = torch.tensor(np.random.default_rng(5).standard_normal(n), dtype=torch.float64, device=dev)
     res = {}
+    clocks = Clocks(dev.index)
     for name, p in (("fp64", L.EMT_PREC_FP64), ("ff64", L.EMT_PREC_FF64)):
         h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=p)
         v = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -733,6 +897,7 @@ def apply_arm(args):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         res[name] = (float(np.median(ts)), v.cpu().numpy())
+    clk = clocks.stop()
     # oracle: exact hierarchical apply of the same vector (CPU, single thread)
     t0 = time.perf_counter()
     nw = oemt.Network(net, DT, levels=4)
@@ -750,7 +915,7 @@ def apply_arm(args):
     head = min(res, key=lambda k: res[k][0])
     ms = res[head][0]
     ach = byts / (ms * 1e-3) / 1e9
-    print(json.dumps({
+    return {
         "metric": "bus-steps/sec at rel err <=1e-8 vs FP64 oracle", "value": n / (ms * 1e-3), "unit": "bus-steps/s",
         "n_gpus": 1, "steps": max(args.steps, 10), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
@@ -763,7 +928,8 @@ def apply_arm(args):
                      "algorithmic_bytes": byts},
         "cpu_baseline": {"value": n / (t2 - t1), "unit": "bus-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "one exact hierarchical apply of the same vector (store build excluded)"},
-    }))
+        "clocks": clk,
+    }
 
 
 # ---------------------------------------------------------------- config 6 (d_th sweep)
@@ -935,6 +1101,7 @@ def dth_arm(args):
         torch.cuda.synchronize()
         return out
 
+    clocks = Clocks(dev.index)
     for (r, c) in shapes:
         net = netgen.tile(1_000_000) if r * c == 1 else netgen.tiled(r, c)
         n = net["n_bus"]
@@ -974,6 +1141,7 @@ def dth_arm(args):
                          "exact_modify_vs_rebuild_rel_diff": xgap,
                          "element_saving": 1.0 - (bmax / n) ** 2})
     # scaling of the build time with N at each d_th (least-squares slope of log t vs log N)
+    clk = clocks.stop()
     slopes = {}
     for d in dths:
         pts = [(x["n_bus"], x["build_ms"]) for x in rows if x["d_th"] == d]
@@ -990,7 +1158,7 @@ def dth_arm(args):
     t0 = time.perf_counter()
     omod.algorithm2(H, nw.series_frm, nw.series_to, t_net["n_bus"] // 3, -1, 1.0 / fault_ohm)
     cpu_ms = (time.perf_counter() - t0) * 1e3
-    print(json.dumps({
+    return {
         "metric": "share of rebuild time saved by Algorithm 2 (10-ohm bus fault, PAPER store)",
         "value": head["time_saved"], "unit": "fraction", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": head["modify_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1000,8 +1168,8 @@ def dth_arm(args):
         "table": rows, "build_time_exponent_vs_N": slopes, "flops_e2_e3": flop_table(),
         "cpu_baseline": {"value": cpu_ms, "unit": "ms per Algorithm 2", "cores": 1, "kind": "oracle",
                          "sample": "179-bus tile, d_th 45, the same fault"},
-        "gpu_launches": None,
-    }))
+        "gpu_launches": None, "clocks": clk,
+    }
 
 
 # ---------------------------------------------------------------- config 7 (three-phase buses)
@@ -1036,6 +1204,7 @@ def three_phase_arm(args):
     v = torch.zeros(nn, dtype=torch.float64, device=dev)
     for _ in range(args.warmup):
         L.emt_apply(h, x, v, stream=stream)
+    clocks = Clocks(dev.index)
     ts = []
     for _ in range(max(args.steps, 10)):
         flush.zero_()
@@ -1047,6 +1216,7 @@ def three_phase_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
     apply_ms = float(np.median(ts))
     # accuracy against a dense solve of the oracle's G (CPU)
     gr = ocm.three_phase_graph(net, DT)
@@ -1081,7 +1251,7 @@ def three_phase_arm(args):
     torch.cuda.synchronize()
     err_trip = rel_err(v.cpu().numpy(), odense.DenseSolver(G).solve(x.cpu().numpy()))
     change = rel_err(v.cpu().numpy(), v_before)
-    print(json.dumps({
+    return {
         "metric": "three-phase node solves per second (v = G^-1 i, one vector)", "value": nn / (apply_ms * 1e-3),
         "unit": "node-solves/s", "n_gpus": 1, "steps": max(args.steps, 10), "warmup": args.warmup,
         "ms_per_step": apply_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -1095,7 +1265,8 @@ def three_phase_arm(args):
         "cpu_baseline": {"value": nn / (cpu_ms * 1e-3), "unit": "node-solves/s", "cores": os.cpu_count(),
                          "kind": "oracle", "sample": "dense Cholesky solve of the same G and vector (factorisation "
                                                      "included)"},
-    }))
+        "clocks": clk,
+    }
 
 
 def main():
@@ -1103,6 +1274,9 @@ def main():
     if args.cpu_worker:
         cpu_worker(args.cpu_worker, args.cpu_steps, args.config, args.cpu_col)
         return
+    rc = launch_ranks(args)
+    if rc is not None:
+        sys.exit(rc)
     if args.impl != "reference" and args.config in (5, 6, 41):
         # these arms time the oracle in this process and report one core: pin the BLAS pools to one
         # thread before numpy is first imported
@@ -1110,18 +1284,41 @@ def main():
             os.environ[k] = "1"
     if args.impl == "reference":
         reference_arm(args)
-    elif args.config in (3, 4):
-        multi_arm(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.config in (0, 4):
+        line = multi_arm(args, 4)
+        if args.config == 0:
+            # secondary keys of the same line: the single 1,432-bus simulation and the single apply on
+            # the 11,456-bus store (rank 0 times the apply alone)
+            sec = {"single_1432bus_20000_steps": native_arm(args, 2)}
+            if int(os.environ.get("RANK", "0")) == 0:
+                sec["single_apply_11456bus"] = apply_arm(args)
+            if line is not None:
+                line["secondary"] = sec
+    elif args.config == 3:
+        line = multi_arm(args, 3)
     elif args.config == 5:
-        serve_arm(args)
+        line = serve_arm(args)
     elif args.config == 41:
-        apply_arm(args)
+        line = apply_arm(args)
     elif args.config == 6:
-        dth_arm(args)
+        line = dth_arm(args)
     elif args.config == 7:
-        three_phase_arm(args)
+        line = three_phase_arm(args)
     else:
-        native_arm(args)
+        line = native_arm(args, args.config)
+    if line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
