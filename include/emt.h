@@ -156,6 +156,20 @@ emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double d
  * Asynchronous on `stream`. */
 emt_status emt_apply_noalloc(const emt_hinv* h, const double* i_dev, double* v_dev, void* stream);
 
+/* Kernels of the single-vector emt_apply on stores whose leaf blocks do not stay in the caches
+ * (FP64 or FF64 stores with >= 48 MB of leaf blocks). kernels = 0 (default, automatic) or 1: three
+ * kernels (leaf stream, sweep product, expansion) chained with programmatic dependent launch, which
+ * also lets consecutive applies overlap. kernels = 2: one cooperative launch of one CTA per SM whose
+ * warps each stream their own leaf rows (asynchronous 16-byte copies, one row ahead), which then
+ * stages the factor rows and its part of the sweep matrix and meets the other CTAs at two grid-wide
+ * barriers (bounded waits: EMT_ERR_TIMEOUT at the next synchronising call if one ran out); it falls
+ * back to the three kernels when its plan does not fit (shared memory, co-residency). warps
+ * (0 = automatic, else 4..16) sets the warps per CTA of the single launch (a change re-plans on the
+ * next emt_apply). *used (may be NULL) receives what the next single-vector apply runs: 2 the
+ * single launch, 1 the three kernels, 0 the fused kernels of small stores or a plan not built yet
+ * (the first emt_apply builds it). Host only; takes effect on the next emt_apply. */
+emt_status emt_apply_tune(emt_hinv* h, int32_t kernels, int32_t warps, int32_t* used);
+
 /* Wait for the handle's work on `stream` and return its device status. */
 emt_status emt_hinv_sync(emt_hinv* h, void* stream);
 void emt_hinv_destroy(emt_hinv* h);

@@ -82,6 +82,7 @@ def _load():
         "emt_apply": (C.c_int, [vp, vp, vp, C.c_int32, C.c_int64, C.c_int32, C.c_double, vp]),
         "emt_modify_branch": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, vp]),
         "emt_hinv_sync": (C.c_int, [vp, vp]),
+        "emt_apply_tune": (C.c_int, [vp, C.c_int32, C.c_int32, _i32p]),
         "emt_hinv_destroy": (None, [vp]),
         "emt_sim_create": (C.c_int, [C.POINTER(EmtNetwork), C.POINTER(EmtHinvOpts), C.c_double, C.c_int32, _f64p,
                                      _f64p, vp, C.POINTER(vp)]),
@@ -125,7 +126,7 @@ def _load():
 lib = _load()
 EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes", "emt_tree_arrays", "emt_tree_destroy",
             "emt_build_hinv", "emt_hinv_tree", "emt_hinv_get_partition", "emt_apply", "emt_modify_branch",
-            "emt_hinv_sync", "emt_hinv_destroy",
+            "emt_hinv_sync", "emt_apply_tune", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
             "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
@@ -284,6 +285,14 @@ def emt_apply_noalloc(h: HInv, i_dev, v_dev, stream=None):
 
 def emt_modify_branch(h: HInv, bus_a, bus_b, delta_g, stream=None):
     _check(lib.emt_modify_branch(h.h, int(bus_a), int(bus_b), float(delta_g), _stream(stream)))
+
+
+def emt_apply_tune(h: HInv, kernels=0, warps=0):
+    """Kernels of the single-vector apply on large stores; returns what the next apply runs
+    (2 single launch, 1 three kernels, 0 small-store kernels or no plan yet)."""
+    used = C.c_int32(-1)
+    _check(lib.emt_apply_tune(h.h, int(kernels), int(warps), C.byref(used)))
+    return int(used.value)
 
 
 def emt_hinv_sync(h: HInv, stream=None):

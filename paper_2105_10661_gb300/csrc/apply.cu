@@ -251,6 +251,7 @@ void refresh_plan_values(const Store& st, FusedPlan& p, cudaStream_t s) {
 void fused_apply(const Store& st, FusedPlan& p, const double* src, bool src_pos, double* v_pos, double* v_bus,
                  bool accumulate, cudaStream_t s) {
   if (p.sa && p.sa->ready) {
+    p.sa->mode = p.stream_mode;
     stream_apply(st, *p.sa, src, src_pos, v_pos, v_bus, accumulate, s);
     return;
   }
@@ -271,8 +272,10 @@ void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>
                    double* v_dev, int nrhs, int64_t ld, int max_refine, cudaStream_t s) {
   if (vpos.n < (size_t)st.n) vpos.alloc(st.n);
   if (rpos.n < (size_t)st.n) rpos.alloc(st.n);
+  if (p.sa && p.sa->rps_req != p.stream_rps) p.sa.reset();   // re-plan for another stage depth
   if (!p.sa && stream_apply_wanted(st)) {
     auto sa = std::make_shared<StreamApply>();
+    sa->rps_req = p.stream_rps;
     if (sa->build(st, s)) p.sa = sa;
   }
   const bool refine = st.precision == EMT_PREC_FP32 && max_refine > 0;

@@ -223,6 +223,28 @@ emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double d
   });
 }
 
+emt_status emt_apply_tune(emt_hinv* h, int32_t kernels, int32_t warps, int32_t* used) {
+  return guard([&] {
+    EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle");
+    EMT_REQUIRE(kernels >= 0 && kernels <= 2, EMT_ERR_INVALID, "kernels must be 0, 1 or 2");
+    EMT_REQUIRE(warps == 0 || (warps >= 4 && warps <= 16), EMT_ERR_INVALID, "warps must be 0 or 4..16");
+    h->plan.stream_mode = kernels;
+    if (warps != h->plan.stream_rps) {
+      h->plan.stream_rps = warps;
+      if (h->plan.sa) {   // re-planned by the next emt_apply
+        EMT_CUDA(cudaDeviceSynchronize());
+        h->plan.sa.reset();
+      }
+    }
+    if (used) {
+      // what the next single-vector emt_apply runs: 2 single launch, 1 three kernels, 0 the fused
+      // kernels of stores that stay in the caches (the plan is built by the first emt_apply)
+      const auto& sa = h->plan.sa;
+      *used = (sa && sa->ready) ? ((sa->persist && kernels == 2) ? 2 : 1) : 0;
+    }
+  });
+}
+
 emt_status emt_hinv_sync(emt_hinv* h, void* stream) {
   emt_status r = guard([&] { EMT_REQUIRE(h && h->st, EMT_ERR_INVALID, "null handle"); });
   if (r != EMT_OK) return r;

@@ -22,11 +22,53 @@ namespace emt {
 // Error-free transformations: Knuth's TwoSum and the FMA-based TwoProd (Dekker 1971 splits a
 // product exactly; with an FMA the error term is fma(a, b, -a*b)). The __f*_rn intrinsics keep
 // the compiler from contracting or reassociating them.
-__device__ __forceinline__ float2 ff_from(double x) {
+//
+// The conversions between double and float-float avoid this GPU's FP64 pipe, which sustains about
+// one thread-operation per cycle per SM (a double<->float conversion pair with an add about 0.6),
+// against a few hundred for FP32 and integer operations: they work on the bit patterns. Values
+// outside the range where both parts are normal floats take the FP64 instructions.
+// The FP64 fallbacks are real calls, never inlined, so that the compiler cannot turn the rare
+// branch into predicated FP64 instructions that every call would issue.
+static __device__ __noinline__ float2 ff_from_fp64(double x) {
   const float h = __double2float_rn(x);
   return make_float2(h, __double2float_rn(x - (double)h));
 }
-__device__ __forceinline__ double ff_to(float2 a) { return (double)a.x + (double)a.y; }
+static __device__ __noinline__ double ff_to_fp64(float2 a) { return (double)a.x + (double)a.y; }
+// hi = x truncated to 24 significant bits (its top bits with the exponent rebiased), lo = the other
+// 29 bits rounded to a float and scaled by 2^(e - 1075); hi + lo = x to 2^-48 relative.
+__device__ __forceinline__ float2 ff_from(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  if ((b << 1) == 0ull) return make_float2(__uint_as_float(sign), 0.0f);
+  const int ef = (int)((b >> 52) & 0x7ffu) - 896;   // float-biased exponent of hi (1023 - 127)
+  if (ef < 53 || ef > 253) return ff_from_fp64(x);
+  const float hi = __uint_as_float(sign | ((unsigned int)ef << 23) | ((unsigned int)(b >> 29) & 0x7fffffu));
+  const float scale = __uint_as_float((unsigned int)(ef - 52) << 23);
+  const float lo = __fmul_rn(__uint2float_rn((unsigned int)b & 0x1fffffffu), scale);
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+// the double nearest below-or-at hi + lo: hi's significand on 53 bits, lo's added at its offset,
+// renormalised by the leading-zero count (truncation: within 2^-52 relative)
+__device__ __forceinline__ double ff_to(float2 a) {
+  const unsigned int bh = __float_as_uint(a.x), bl = __float_as_uint(a.y);
+  const bool lo_zero = (bl << 1) == 0u;
+  if ((bh << 1) == 0u && lo_zero) return __longlong_as_double((long long)(bh & 0x80000000u) << 32);
+  const int eh = (int)(bh >> 23) & 0xff, el = (int)(bl >> 23) & 0xff;
+  if (eh == 0 || eh == 255 || el == 255 || (el == 0 && !lo_zero)) return ff_to_fp64(a);
+  long long m = (long long)((bh & 0x7fffffu) | 0x800000u) << 29;
+  if (!lo_zero) {
+    const int sh = el - eh + 29;
+    if (sh >= 40) return ff_to_fp64(a);
+    long long ml = (long long)((bl & 0x7fffffu) | 0x800000u);
+    ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0ll);
+    m = ((bh ^ bl) & 0x80000000u) ? m - ml : m + ml;
+  }
+  if (m <= 0) return ff_to_fp64(a);
+  const int s = __clzll(m) - 11;
+  m = s >= 0 ? (m << s) : (m >> -s);
+  const long long e = (long long)(eh + 896 - s);
+  return __longlong_as_double(((long long)(bh & 0x80000000u) << 32) | (e << 52) | (m & ((1ll << 52) - 1)));
+}
 __device__ __forceinline__ float2 ff_norm(float hi, float lo) {
   const float s = __fadd_rn(hi, lo);
   return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));

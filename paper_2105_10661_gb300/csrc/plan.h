@@ -23,11 +23,40 @@ struct StreamStage {
   int ld, nr, xo, b, crow0, crow1, p, pad;
 };
 
+// Persistent single-launch apply (stream.cu, k_apply_persist): a CTA's rows within one leaf, and
+// the slices of the factor panels those rows need, staged into the CTA's shared memory.
+struct PersistSeg {
+  int p0, p1;     // positions [p0, p1) of one leaf
+  int f0, f1;     // factor slices [f0, f1) of the CTA's table, one per ancestor
+  int xo, b, ld;  // the leaf's offset in the CTA's x window, its size and row stride
+  int pad;
+  long long loff; // element offset of row p0 in the packed leaf store
+};
+struct PersistF {
+  long long src;  // element offset in the packed factor store of row p0
+  int dst;        // element offset in the CTA's factor region (shared memory)
+  int kld, k;     // row stride and width of the panel
+  int sidx;       // index in s of the half these rows use
+  int bytes, pad;
+};
+
 // Streaming apply for stores larger than the caches (stream.cu): row ranges of the persistent
 // leaf-stream CTAs, the sweep image and matrix K (s = K y_cut), ancestor records for the
 // expansion, and the intermediate vectors.
 struct StreamApply {
   bool ready = false;
+  // single-launch form: one cooperative launch of one CTA per SM (two grid-wide barriers)
+  bool persist = false;              // plan fits: shared memory, co-residency
+  int mode = 0;                      // 0 or 1: three kernels; 2: single launch when it fits
+  int warps = 0;                     // warps per CTA of the single launch (each streams its own rows)
+  int rps_req = 0;                   // requested warps per CTA (0: automatic)
+  int row_elems = 0, k_bytes = 0;
+  size_t smem_p = 0;
+  int o_bar = 0, o_ring = 0, o_y = 0, o_crow = 0, o_perm = 0, o_vec = 0, o_tab = 0;
+  DevBuf<PersistSeg> pseg;
+  DevBuf<int> pseg_ptr, krow0;
+  DevBuf<PersistF> pf;
+  DevBuf<unsigned int> bar;          // [0] arrivals at the grid barriers, [1] CTAs done (reset by the last)
   int prec = 0, n_cta = 0, stage_elems = 0, n_crow = 0, s_total = 0, ldk = 0, n_seg = 0, max_stages = 0, n_anc = 0;
   size_t smem = 0, smem_ldg = 0;
   bool ldg = false;                  // leaf stage: plain 16-byte loads instead of the TMA ring
@@ -57,6 +86,8 @@ struct FusedPlan {
   DevBuf<float2> cut_gnff;
   DevBuf<float> cut_gn32;
   std::shared_ptr<StreamApply> sa;   // built on first use for large stores (emt_apply)
+  int stream_mode = 0;               // large stores: 0 automatic (three kernels), 1 three kernels, 2 single launch
+  int stream_rps = 0;                // warps per CTA of the single launch (0: automatic)
   CtaMapD cmap() const;
   CutRowsD crows() const;
 };

@@ -486,12 +486,482 @@ void launch_stream(const Store& st, StreamApply& sa, const double* src, bool src
                (const int*)sa.anc_ptr.p, sa.n_anc, sa.s_total, (const X*)y, (const X*)sv, v_pos, v_bus, acc ? 1 : 0);
 }
 
+// ---------------------------------------------------------------- single-launch apply
+// The whole apply in one cooperative launch of one CTA per SM, for stores whose leaf blocks stream
+// from HBM. Three phases separated by two grid-wide barriers:
+//   A  leaf stage: the CTA streams its leaf rows through a ring of shared-memory slots (one
+//      consumer warp per slot, as in k_leaf_stream), keeps y of its own rows in shared memory and
+//      writes the cut-row values y_cut to global memory. After the last ring copy it issues the
+//      copies of everything phases B and C read from the store: its slice of K and the rows of
+//      the factor panels of its own positions (one slice per leaf segment and ancestor).
+//   B  s = K y_cut for the CTA's rows of K (one warp per row), written to global memory.
+//   C  expansion v = y - sum over ancestors of F row . s(half) of the CTA's own positions, from
+//      the staged factor rows; 16 lanes per position.
+// The copies of phase A's tail land while the CTAs wait at the barriers, so HBM stays busy up to
+// the end of the stream and the two later phases touch only on-chip data and L2.
+// Barriers count arrivals on one global word (release add, acquire polling, bounded); the last CTA
+// to finish puts both counters back to zero, so every launch starts from zero. Every wait gives up
+// after about 2 s, records DEV_TIMEOUT, skips the remaining work and still reaches the later
+// barriers and the exit, draining its own copies first.
+struct PersistD {
+  const int2* win;
+  const int* row0;
+  const PersistSeg* seg;
+  const int* seg_ptr;
+  const PersistF* fsl;
+  const int* krow0;
+  const int* crow_of;   // position -> distinct cut-row index, -1 if none
+  const void* K;
+  void* ycut;
+  void* sv;
+  unsigned int* bar;
+  int row_elems, ldk, n_crow, s_total, k_bytes;
+  int o_bar, o_ring, o_y, o_crow, o_perm, o_vec, o_tab;
+};
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier: every CTA arrives once per barrier (also after an abort), then waits until
+// `target` arrivals are counted. The CTA's writes before the barrier are made visible GPU-wide by
+// bar.sync + a fence of thread 0 before its release add. Returns false (and sets the abort flag
+// and the status word) when the wait ran out.
+__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int target, int* abort_flag,
+                                             int* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_gpu_add(count, 1u);
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(count) < target) {
+      if (clock64() - t0 > kWaitS) {
+        atomicExch(status, DEV_TIMEOUT);
+        *reinterpret_cast<volatile int*>(abort_flag) = 1;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Bounded wait of every thread of a warp-uniform caller on an mbarrier phase.
+__device__ __forceinline__ bool cta_wait(uint64_t* b, uint32_t parity, int* abort_flag, int* status) {
+  if (mb_wait(b, parity, kWaitS)) return true;
+  atomicExch(status, DEV_TIMEOUT);
+  *reinterpret_cast<volatile int*>(abort_flag) = 1;
+  return false;
+}
+
+
+// Rows of the leaf stage a warp keeps in flight ahead of the one it multiplies (its private ring
+// holds kAhead + 1 rows).
+constexpr int kAhead = 1;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sas(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int PREC>
+__global__ void __launch_bounds__(512, 1) k_apply_persist(DStore st, PersistD pd, const double* src, int src_pos,
+                                                           double* v_pos, double* v_bus, int accumulate) {
+  using A = Acc<PREC>;
+  using X = typename A::X;
+  using T = typename A::T;
+  extern __shared__ __align__(128) unsigned char smp[];
+  uint64_t* aux = reinterpret_cast<uint64_t*>(smp + pd.o_bar);
+  int* flags = reinterpret_cast<int*>(aux + 1);   // [0] abort, [1] copies of phases B and C issued
+  volatile int* vflags = flags;
+  T* ring = reinterpret_cast<T*>(smp + pd.o_ring);   // per-warp leaf rows (A); K rows and factor rows (B, C)
+  T* ksl = ring;
+  T* fsm = reinterpret_cast<T*>(smp + pd.o_ring + pd.k_bytes);
+  X* yown = reinterpret_cast<X*>(smp + pd.o_y);
+  int* crow_own = reinterpret_cast<int*>(smp + pd.o_crow);
+  int* perm_own = reinterpret_cast<int*>(smp + pd.o_perm);
+  X* vec = reinterpret_cast<X*>(smp + pd.o_vec);   // x window (A), y_cut (B), s (C)
+  X* ycut_g = reinterpret_cast<X*>(pd.ycut);
+  X* sv_g = reinterpret_cast<X*>(pd.sv);
+  const T* Kg = reinterpret_cast<const T*>(pd.K);
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  const int r0 = pd.row0[c], r1 = pd.row0[c + 1];
+  const int k0 = pd.krow0[c], k1 = pd.krow0[c + 1];
+  const int g0 = pd.seg_ptr[c], g1 = pd.seg_ptr[c + 1];
+  const int2 w = pd.win[c];
+  const unsigned int n_cta = gridDim.x;
+  const int nrow = r1 - r0;
+  const T* L = Elem<PREC>::L(st);
+  const T* F = Elem<PREC>::F(st);
+  // leaf rows of the warp, k-th = own row warp + k nwarp; slot k % (kAhead + 1) of its private ring
+  T* wring = ring + (size_t)warp * (kAhead + 1) * pd.row_elems;
+  const PersistSeg* sgt = pd.seg + g0;   // the CTA's leaf segments (in shared memory once staged)
+  auto row_seg = [&](int p) {
+    int g = 0;
+    while (g + 1 < g1 - g0 && p >= sgt[g].p1) ++g;
+    return g;
+  };
+  auto issue_row = [&](int k) {
+    const int i = warp + k * nwarp;
+    if (i < nrow) {
+      const int p = r0 + i;
+      const PersistSeg sg = sgt[row_seg(p)];
+      const T* Lr = L + sg.loff + (int64_t)(p - sg.p0) * sg.ld;
+      T* dst = wring + (size_t)(k % (kAhead + 1)) * pd.row_elems;
+      for (int col = 2 * lane; col < sg.b; col += 64) cp_async16(dst + col, Lr + col);
+    }
+    cp_async_commit();   // also when empty, so that every lane counts the same groups
+  };
+  // the first rows go out before anything else, then the bookkeeping while they travel
+  for (int k = 0; k <= kAhead; ++k) issue_row(k);
+  if (tid == 0) {
+    mb_init(aux, 1);
+    flags[0] = 0;
+    flags[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int f_first = g1 > g0 ? pd.seg[g0].f0 : 0;
+  const int n_f = g1 > g0 ? pd.seg[g1 - 1].f1 - f_first : 0;
+  PersistSeg* segs = reinterpret_cast<PersistSeg*>(smp + pd.o_tab);
+  PersistF* fsls = reinterpret_cast<PersistF*>(segs + (g1 - g0));
+  for (int u = tid; u < g1 - g0; u += blockDim.x) segs[u] = pd.seg[g0 + u];
+  for (int u = tid; u < n_f; u += blockDim.x) fsls[u] = pd.fsl[f_first + u];
+  for (int u = tid; u < nrow; u += blockDim.x) {
+    crow_own[u] = pd.crow_of[r0 + u];
+    perm_own[u] = st.perm[r0 + u];
+  }
+  // what phases B and C read from the store goes to L2 now: rows [k0, k1) of K and the factor rows
+  // of the CTA's positions (copied into the drained ring after phase A)
+  if (warp == nwarp - 1 && lane == 0) {
+    if (k1 > k0) bulk_prefetch_l2(Kg + (size_t)k0 * pd.ldk, (uint32_t)((k1 - k0) * pd.ldk * (int)sizeof(T)));
+    for (int f = f_first; f < f_first + n_f; ++f) bulk_prefetch_l2(F + pd.fsl[f].src, (uint32_t)pd.fsl[f].bytes);
+  }
+  // the x window: all index loads of a thread, then all value loads (two round trips)
+  {
+    constexpr int kG = 4;
+    for (int base = w.x + tid; base < w.y + 2; base += kG * blockDim.x) {
+      int idx[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int p = base + u * blockDim.x;
+        idx[u] = p < w.y ? (src_pos ? p : st.perm[p]) : -1;
+      }
+      double val[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) val[u] = idx[u] >= 0 ? ldcg(src + idx[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int p = base + u * blockDim.x;
+        if (p < w.y + 2) vec[p - w.x] = A::prep(val[u]);
+      }
+    }
+  }
+  __syncthreads();
+  sgt = segs;
+  // ---- phase A: leaf stage, one warp per row, kAhead rows in flight per warp
+  for (int k = 0; warp + k * nwarp < nrow; ++k) {
+    cp_async_wait<kAhead>();   // row k of this lane has landed
+    __syncwarp();              // ... and of every lane
+    const int i = warp + k * nwarp;
+    const PersistSeg sg = segs[row_seg(r0 + i)];
+    const T* Lr = wring + (size_t)(k % (kAhead + 1)) * pd.row_elems;
+    const X* xr = vec + sg.xo;
+    A a, a2;
+#pragma unroll 4
+    for (int col = 2 * lane; col < sg.b; col += 64) {
+      T l2[2];
+      ld2(Lr + col, l2);
+      a.fma(l2[0], xr[col]);
+      a2.fma(l2[1], xr[col + 1]);
+    }
+    a.add(a2.getx());
+    const X v = warp_sum<PREC>(a, 32);
+    if (lane == 0) {
+      yown[i] = v;
+      const int kc = crow_own[i];
+      if (kc >= 0) ycut_g[kc] = v;
+    }
+    __syncwarp();              // every lane is done with the slot before it is refilled
+    issue_row(k + kAhead + 1);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the ring is drained: copy K rows and factor rows (now in L2) into it, behind a proxy fence
+  // that orders the generic accesses to the ring before the async writes
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    uint32_t bytes = (uint32_t)((k1 - k0) * pd.ldk * (int)sizeof(T));
+    for (int f = 0; f < n_f; ++f) bytes += (uint32_t)fsls[f].bytes;
+    mb_expect(aux, bytes);
+    if (k1 > k0) bulk_row(ksl, Kg + (size_t)k0 * pd.ldk, (uint32_t)((k1 - k0) * pd.ldk * (int)sizeof(T)), aux);
+    for (int f = 0; f < n_f; ++f) bulk_row(fsm + fsls[f].dst, F + fsls[f].src, (uint32_t)fsls[f].bytes, aux);
+    flags[1] = 1;
+  }
+  // ---- barrier 1: every CTA's y_cut is written
+  grid_barrier(&pd.bar[0], n_cta, flags, st.status);
+  // ---- phase B: rows [k0, k1) of s = K y_cut
+  bool live = !vflags[0];
+  if (live) {
+    stage_vec(vec, ycut_g, pd.n_crow);
+    if (flags[1]) cta_wait(aux, 0u, flags, st.status);
+  }
+  __syncthreads();
+  live = !vflags[0];
+  if (live) {
+    for (int row = k0 + warp; row < k1; row += nwarp) {
+      const T* Kr = ksl + (size_t)(row - k0) * pd.ldk;
+      A a, a2;
+      for (int k = lane; k < pd.n_crow; k += 64) {
+        a.fma(Kr[k], vec[k]);
+        if (k + 32 < pd.n_crow) a2.fma(Kr[k + 32], vec[k + 32]);
+      }
+      a.add(a2.getx());
+      const X v = warp_sum<PREC>(a, 32);
+      if (lane == 0) sv_g[row] = v;
+    }
+  }
+  // ---- barrier 2: every row of s is written
+  grid_barrier(&pd.bar[0], 2 * n_cta, flags, st.status);
+  // ---- phase C: expansion of the CTA's own positions from the staged factor rows
+  live = !vflags[0];
+  if (live) stage_vec(vec, sv_g, pd.s_total);
+  __syncthreads();
+  if (live) {
+    const int npos = r1 - r0;
+    const int gl = tid & (kEL - 1);
+    // two positions per warp; the trip count is uniform across the warp (shuffles below)
+    for (int base = warp * 2; base < npos; base += nwarp * 2) {
+      const int i = base + ((tid >> 4) & 1);
+      const bool valid = i < npos;
+      const int p = r0 + (valid ? i : 0);
+      A a, a2;
+      if (valid) {
+        int g = 0;
+        while (g + 1 < g1 - g0 && p >= segs[g].p1) ++g;
+        const PersistSeg sg = segs[g];
+        for (int f = sg.f0 - f_first; f < sg.f1 - f_first; ++f) {
+          const PersistF r = fsls[f];
+          const T* Fr = fsm + r.dst + (size_t)(p - sg.p0) * r.kld;
+          for (int e = gl; e < r.k; e += 2 * kEL) {
+            a.fma(Fr[e], neg(vec[r.sidx + e]));
+            if (e + kEL < r.k) a2.fma(Fr[e + kEL], neg(vec[r.sidx + e + kEL]));
+          }
+        }
+      }
+      a.add(a2.getx());
+      const X wv = warp_sum<PREC>(a, kEL);
+      if (valid && gl == 0) {
+        A f;
+        f.add(yown[i]);
+        f.add(wv);
+        yown[i] = f.getx();   // v of the position, converted below
+      }
+    }
+  }
+  __syncthreads();
+  // one thread per position for the conversion to double and the stores (full warps)
+  if (live) {
+    for (int i = tid; i < r1 - r0; i += blockDim.x) {
+      double out = A::todbl(yown[i]);
+      if (accumulate) out += v_pos[r0 + i];
+      if (v_pos) v_pos[r0 + i] = out;
+      if (v_bus) v_bus[perm_own[i]] = out;
+    }
+  }
+  // ---- exit: own copies drained; the last CTA out puts the barrier counters back to zero
+  __syncthreads();
+  if (tid == 0) {
+    if (flags[1]) mb_wait(aux, 0u, kWaitS);
+    __threadfence();
+    const unsigned int done = atomicAdd(&pd.bar[1], 1u);
+    if (done == n_cta - 1) {
+      atomicExch(&pd.bar[0], 0u);
+      atomicExch(&pd.bar[1], 0u);
+    }
+  }
+}
+
+template <int PREC>
+void launch_persist(const Store& st, StreamApply& sa, const double* src, bool src_pos, double* v_pos, double* v_bus,
+                    bool acc, cudaStream_t s) {
+  PersistD pd{};
+  pd.win = sa.win.p;
+  pd.row0 = sa.row0.p;
+  pd.seg = sa.pseg.p;
+  pd.seg_ptr = sa.pseg_ptr.p;
+  pd.fsl = sa.pf.p;
+  pd.krow0 = sa.krow0.p;
+  pd.crow_of = sa.crow_of.p;
+  pd.K = sa.K.p;
+  pd.ycut = sa.ycut.p;
+  pd.sv = sa.sv.p;
+  pd.bar = sa.bar.p;
+  pd.row_elems = sa.row_elems;
+  pd.ldk = sa.ldk;
+  pd.n_crow = sa.n_crow;
+  pd.s_total = sa.s_total;
+  pd.k_bytes = sa.k_bytes;
+  pd.o_bar = sa.o_bar;
+  pd.o_ring = sa.o_ring;
+  pd.o_y = sa.o_y;
+  pd.o_crow = sa.o_crow;
+  pd.o_perm = sa.o_perm;
+  pd.o_vec = sa.o_vec;
+  pd.o_tab = sa.o_tab;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sa.n_cta);
+  cfg.blockDim = dim3(32 * sa.warps);
+  cfg.dynamicSmemBytes = sa.smem_p;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  EMT_CUDA(cudaLaunchKernelEx(&cfg, k_apply_persist<PREC>, st.view(), pd, src, src_pos ? 1 : 0, v_pos, v_bus,
+                              acc ? 1 : 0));
+}
+
 }  // namespace
 
 // Whether the streaming kernels serve this store: FP64 or float-float storage large enough that
 // the leaf blocks do not stay in L2 between applications.
 bool stream_apply_wanted(const Store& st) {
   return (st.precision == EMT_PREC_FF64 || st.precision == EMT_PREC_FP64) && st.L_elems * 8 >= (int64_t)48 << 20;
+}
+
+// Plan of the single-launch apply (k_apply_persist): rows of K per CTA, the leaf segments of each
+// CTA's positions with their factor-panel slices, the shared-memory layout and the number of warps
+// whose private rings of kAhead + 1 leaf rows fit. K rows and factor rows are copied into the
+// rings once they have drained, so the ring region must also hold them. False (three-kernel path)
+// when a CTA cannot hold its data, a copy would break the 16-byte rules, or one CTA per SM is not
+// resident.
+static bool persist_plan(const Store& st, StreamApply& sa, const std::vector<int>& r0,
+                         const std::vector<StreamAnc>& an, const std::vector<int>& ap, size_t max_win, int optin,
+                         cudaStream_t s) {
+  sa.persist = false;
+  const Tree& t = st.tree;
+  const int n_cta = sa.n_cta;
+  int dev = 0, coop = 0, sms = 0;
+  EMT_CUDA(cudaGetDevice(&dev));
+  EMT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  EMT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop || (sa.ldk & 1) != 0) return false;
+  int max_ld = 0;
+  for (int j = 0; j < st.n_leaf; ++j) {
+    max_ld = std::max(max_ld, st.leaf_ld_h[j]);
+    if ((st.leaf_ld_h[j] & 1) || (st.leaf_off_h[j] & 1)) return false;   // 16-byte row starts
+  }
+  // rows of K per CTA; leaf segments and factor slices
+  std::vector<int> k0(n_cta + 1);
+  for (int c = 0; c <= n_cta; ++c) k0[c] = (int)((int64_t)sa.s_total * c / n_cta);
+  std::vector<PersistSeg> seg;
+  std::vector<PersistF> fs;
+  std::vector<int> sp(n_cta + 1, 0);
+  int64_t f_max = 0;
+  int rows_max = 1, krows_max = 0, tab_max = 0;
+  for (int c = 0; c < n_cta; ++c) {
+    sp[c] = (int)seg.size();
+    const int fs0 = (int)fs.size();
+    int64_t fe = 0;
+    const int wlo = r0[c + 1] > r0[c] ? t.lo[st.leaf_nodes_h[leaf_index_of_pos(st, r0[c])]] : 0;
+    for (int p = r0[c]; p < r0[c + 1];) {
+      const int j = leaf_index_of_pos(st, p);
+      const int lo = t.lo[st.leaf_nodes_h[j]];
+      const int p1 = std::min(t.hi[st.leaf_nodes_h[j]], r0[c + 1]);
+      PersistSeg g{};
+      g.p0 = p;
+      g.p1 = p1;
+      g.f0 = (int)fs.size();
+      g.xo = lo - wlo;
+      g.b = t.hi[st.leaf_nodes_h[j]] - lo;
+      g.ld = st.leaf_ld_h[j];
+      g.loff = st.leaf_off_h[j] + (int64_t)(p - lo) * g.ld;
+      for (int x = ap[j]; x < ap[j + 1]; ++x) {
+        const StreamAnc& r = an[x];
+        PersistF f{};
+        f.src = r.foff + (int64_t)(p - lo) * r.kld;
+        f.dst = (int)fe;
+        f.kld = r.kld;
+        f.k = r.k;
+        f.sidx = r.sidx;
+        const int64_t bytes = (int64_t)(p1 - p) * r.kld * 8;
+        if ((f.src & 1) || (bytes & 15) || bytes >= (1 << 20)) return false;   // 16-byte rules of cp.async.bulk
+        f.bytes = (int)bytes;
+        fe += (int64_t)(p1 - p) * r.kld;
+        fs.push_back(f);
+      }
+      g.f1 = (int)fs.size();
+      seg.push_back(g);
+      p = p1;
+    }
+    f_max = std::max(f_max, fe);
+    tab_max = std::max(tab_max, (int)(((int)seg.size() - sp[c]) * sizeof(PersistSeg) +
+                                      ((int)fs.size() - fs0) * sizeof(PersistF)));
+    rows_max = std::max(rows_max, r0[c + 1] - r0[c]);
+    krows_max = std::max(krows_max, k0[c + 1] - k0[c]);
+  }
+  sp[n_cta] = (int)seg.size();
+  auto up = [](size_t x) { return (x + 127) / 128 * 128; };
+  sa.k_bytes = (int)up((size_t)krows_max * sa.ldk * 8);
+  const size_t bc_bytes = (size_t)sa.k_bytes + (size_t)f_max * 8;   // K rows + factor rows
+  if (bc_bytes >= (1u << 20)) return false;                         // one mbarrier transaction count
+  sa.row_elems = max_ld;
+  const size_t warp_ring = (size_t)(kAhead + 1) * max_ld * 8;
+  const size_t vec_elems = std::max({max_win + 2, (size_t)std::max(sa.n_crow, 1), (size_t)std::max(sa.s_total, 1)});
+  auto layout = [&](int W) {
+    sa.o_bar = 0;
+    size_t off = 128;   // the aux mbarrier and two flags
+    sa.o_ring = (int)off;
+    off = up(off + std::max((size_t)W * warp_ring, bc_bytes));
+    sa.o_y = (int)off;
+    off = up(off + (size_t)rows_max * 8);
+    sa.o_crow = (int)off;
+    off = up(off + (size_t)rows_max * 4);
+    sa.o_perm = (int)off;
+    off = up(off + (size_t)rows_max * 4);
+    sa.o_vec = (int)off;
+    off = up(off + vec_elems * 8);
+    sa.o_tab = (int)off;
+    off += (size_t)tab_max + 16;
+    return off;
+  };
+  int W = sa.rps_req > 0 ? std::min(sa.rps_req, 16) : 16;
+  while (W >= 4 && layout(W) > (size_t)optin - 1024) --W;
+  if (W < 4) return false;
+  sa.warps = W;
+  sa.smem_p = layout(W);
+  int nb = 0;
+  auto setup = [&](auto kernel) {
+    EMT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa.smem_p));
+    EMT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, 32 * W, sa.smem_p));
+  };
+  if (sa.prec == EMT_PREC_FF64) setup(k_apply_persist<EMT_PREC_FF64>);
+  else setup(k_apply_persist<EMT_PREC_FP64>);
+  if (nb < 1 || n_cta > nb * sms) return false;
+  if (seg.empty()) seg.push_back(PersistSeg{});
+  if (fs.empty()) fs.push_back(PersistF{});
+  sa.pseg.upload(seg, s);
+  sa.pseg_ptr.upload(sp, s);
+  sa.pf.upload(fs, s);
+  sa.krow0.upload(k0, s);
+  if (!sa.bar.p) {
+    sa.bar.alloc(2);
+    EMT_CUDA(cudaMemsetAsync(sa.bar.p, 0, 2 * sizeof(unsigned int), s));
+  }
+  sa.persist = true;
+  return true;
 }
 
 bool StreamApply::build(const Store& st, cudaStream_t s) {
@@ -625,6 +1095,7 @@ bool StreamApply::build(const Store& st, cudaStream_t s) {
   }
   ready = true;
   refresh(st, s);
+  persist_plan(st, *this, r0, an, ap, max_win, optin, s);
   EMT_CUDA(cudaStreamSynchronize(s));
   return true;
 }
@@ -640,6 +1111,11 @@ void StreamApply::refresh(const Store& st, cudaStream_t s) {
 
 void stream_apply(const Store& st, StreamApply& sa, const double* src, bool src_pos, double* v_pos, double* v_bus,
                   bool accumulate, cudaStream_t s) {
+  if (sa.persist && sa.mode == 2) {
+    if (sa.prec == EMT_PREC_FF64) launch_persist<EMT_PREC_FF64>(st, sa, src, src_pos, v_pos, v_bus, accumulate, s);
+    else launch_persist<EMT_PREC_FP64>(st, sa, src, src_pos, v_pos, v_bus, accumulate, s);
+    return;
+  }
   if (sa.prec == EMT_PREC_FF64) launch_stream<EMT_PREC_FF64>(st, sa, src, src_pos, v_pos, v_bus, accumulate, s);
   else launch_stream<EMT_PREC_FP64>(st, sa, src, src_pos, v_pos, v_bus, accumulate, s);
 }

@@ -41,14 +41,18 @@ def _apply(L, h, X, pos_in=False):
     return v_dev.cpu().numpy().T
 
 
+@pytest.mark.parametrize("mode", [2, 0])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_streaming_apply_matches_sparse_solve_and_tracks_trips(L, big, prec):
+def test_streaming_apply_matches_sparse_solve_and_tracks_trips(L, big, prec, mode):
+    # mode 2: the single cooperative launch; 0: the default, three chained kernels
     net, gr = big
     n = net["n_bus"]
     G = ocomp.assemble_sparse(gr).tocsc()
     h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=prec)
+    L.emt_apply_tune(h, mode)
     X = np.random.default_rng(21).standard_normal((n, 3))
     assert rel_err(_apply(L, h, X), spla.splu(G).solve(X)) <= 1e-10
+    assert L.emt_apply_tune(h, mode) == (2 if mode == 2 else 1)
     # two trips: one branch inside a leaf, one chosen by the seeded picker (may cross leaves)
     rng = np.random.default_rng(5)
     for e in [netgen.pick_branch(net), int(rng.integers(0, gr["n_series"]))]:
@@ -71,3 +75,41 @@ def test_streaming_apply_repeatable_bit_for_bit(L, big):
     a = _apply(L, h, X)
     b = _apply(L, h, X)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_launch_apply_repeats_bit_for_bit_and_agrees_with_three_kernels(L, big, prec):
+    # many launches in a row: the grid-barrier counters return to zero after every launch
+    net, _ = big
+    n = net["n_bus"]
+    h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=prec)
+    x = torch.tensor(np.random.default_rng(8).standard_normal(n), dtype=torch.float64, device="cuda")
+    first = torch.zeros_like(x)
+    L.emt_apply_tune(h, 2)
+    L.emt_apply(h, x, first)
+    assert L.emt_apply_tune(h, 2) == 2
+    outs = [torch.zeros_like(x) for _ in range(40)]
+    for o in outs:
+        L.emt_apply(h, x, o)
+    L.emt_hinv_sync(h)
+    for o in outs:
+        assert torch.equal(o, first)
+    L.emt_apply_tune(h, 1)
+    three = torch.zeros_like(x)
+    L.emt_apply(h, x, three)
+    torch.cuda.synchronize()
+    assert rel_err(first.cpu().numpy(), three.cpu().numpy()) <= 1e-13
+
+
+@pytest.mark.parametrize("warps", [4, 7, 12, 16])
+def test_single_launch_warp_counts_match_sparse_solve(L, big, warps):
+    # 4..16 warps per CTA, each streaming its own rows (ragged last rounds in every CTA)
+    net, gr = big
+    n = net["n_bus"]
+    G = ocomp.assemble_sparse(gr).tocsc()
+    h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=1)
+    L.emt_apply_tune(h, 2, warps)
+    X = np.random.default_rng(31).standard_normal((n, 2))
+    got = _apply(L, h, X)
+    assert L.emt_apply_tune(h, 2, warps) == 2
+    assert rel_err(got, spla.splu(G).solve(X)) <= 1e-10

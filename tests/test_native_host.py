@@ -147,6 +147,7 @@ NULL_HANDLE_CALLS = {
     "emt_apply_noalloc": (None, None, None, None),
     "emt_modify_branch": (None, 0, 1, -1.0, None),
     "emt_hinv_sync": (None, None),
+    "emt_apply_tune": (None, 0, 0, None),
     "emt_sim_schedule": (None, 1, 0, 0, 0.0, -1),
     "emt_sim_monitor": (None, 0, None),
     "emt_step": (None, 1, None, None),
