@@ -234,6 +234,20 @@ enum { EMT_EVENT_TRIP = 0, EMT_EVENT_FAULT_ON = 1, EMT_EVENT_FAULT_OFF = 2 };
 emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, double dt,
                           int32_t nrhs, const double* src_scale, const double* load_scale,
                           void* stream, emt_sim** out);
+/* A three-phase simulation (the paper counts three nodes per bus, Sec. III-A after Eq. 3; node =
+ * 3 bus + phase) on the store of emt_build_hinv_from_network3. Each step injects balanced sine
+ * sources and loads (phase p lags phase 0 by 2 pi p / 3), solves v = G^-1 i (Eq. 2) and updates
+ * every branch's three-phase history by the trapezoidal rule: for an RL branch with the coupled
+ * companion admittance Y = (R I + (2/dt) L3)^-1, i = Y v_e + I_h and
+ * I_h <- Y (v_e + ((2/dt) L3 - R I) i); RC branches, shunt capacitors and source resistances act on
+ * each phase alone. FP64 or FF64 stores (EMT_ERR_UNSUPPORTED otherwise). The handle works with
+ * emt_sim_schedule (EMT_EVENT_TRIP of a series branch opens its three phases: one exact local
+ * update of the store per node branch of the line; other events EMT_ERR_UNSUPPORTED),
+ * emt_sim_monitor (node indices), emt_step, emt_sim_read (3 n_bus node voltages), emt_sim_reset,
+ * emt_sim_stats and emt_sim_destroy. State starts at zero; sources are first evaluated at t = dt.
+ * Synchronises `stream`. */
+emt_status emt_sim3_create(const emt_network* net, const double* L_mut, const emt_hinv_opts* opts, double dt,
+                           void* stream, emt_sim** out);
 /* Schedule an event at a 1-based step (before that step is solved). column = -1: every
  * column (the shared store is modified); column >= 0: that column only (multi-column runs
  * apply it as a per-column Sherman-Morrison correction; TRIP only). */

@@ -115,6 +115,8 @@ def _load():
                                                   C.POINTER(vp)]),
         "emt_build_hinv_from_network3": (C.c_int, [C.POINTER(EmtNetwork), _f64p, C.c_double, C.POINTER(EmtHinvOpts),
                                                    vp, C.POINTER(vp)]),
+        "emt_sim3_create": (C.c_int, [C.POINTER(EmtNetwork), _f64p, C.POINTER(EmtHinvOpts), C.c_double, vp,
+                                      C.POINTER(vp)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -133,7 +135,7 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_server_add_network", "emt_server_submit", "emt_server_submit_network", "emt_server_run",
             "emt_server_result", "emt_server_stats",
             "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network",
-            "emt_build_hinv_from_network3")
+            "emt_build_hinv_from_network3", "emt_sim3_create")
 
 
 def _check(code):
@@ -479,3 +481,13 @@ def emt_build_hinv_from_network3(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_
     _check(lib.emt_build_hinv_from_network3(C.byref(nw), _p(lm, _f64p), float(dt), C.byref(o), _stream(stream),
                                             C.byref(h)))
     return HInv(h.value, 3 * int(net["n_bus"]))
+
+
+def emt_sim3_create(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FF64, stream=None):
+    """Three-phase simulation (3 nodes per bus; `net["L_mut"]` mutual inductances of the RL branches)."""
+    nw, keep = make_network(net)
+    lm = _f64(net["L_mut"])
+    o = make_opts(levels, d_th, mode, precision)
+    h = C.c_void_p()
+    _check(lib.emt_sim3_create(C.byref(nw), _p(lm, _f64p), C.byref(o), float(dt), _stream(stream), C.byref(h)))
+    return Sim(h.value, 3 * int(net["n_bus"]), 1)

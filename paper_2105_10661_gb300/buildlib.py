@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libemt_hinv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cpp", "capi.cpp", "hinv.cu", "apply.cu", "sim.cu", "step2.cu", "step3.cu", "step4.cu", "stream.cu", "multi.cu", "umma.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["tree.cpp", "capi.cpp", "hinv.cu", "apply.cu", "sim.cu", "step2.cu", "step3.cu", "step4.cu", "stream.cu", "multi.cu", "umma.cu", "server.cu", "noalloc.cu", "sim3.cu"]
 
 
 def _nvcc():

@@ -8,6 +8,7 @@
 #include "multi.h"
 #include "server.h"
 #include "sim.h"
+#include "sim3.h"
 
 namespace emt {
 thread_local std::string g_last_error;
@@ -19,7 +20,7 @@ int selftest_wait(int limit_us, cudaStream_t s);
 void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, std::vector<int32_t>& gt,
                    std::vector<double>& gv);
 void network_graph3(const emt_network* net, const double* L_mut, double dt, std::vector<int32_t>& gf,
-                    std::vector<int32_t>& gt, std::vector<double>& gv);
+                    std::vector<int32_t>& gt, std::vector<double>& gv, std::vector<int>* br_ptr);
 }  // namespace emt
 
 struct emt_tree {
@@ -42,7 +43,8 @@ struct emt_server {
 struct emt_sim {
   std::unique_ptr<emt::Sim> sim;     // one column
   std::unique_ptr<emt::MSim> msim;   // several columns
-  bool ok() const { return sim || msim; }
+  std::unique_ptr<emt::Sim3> sim3;   // three phases per bus
+  bool ok() const { return sim || msim || sim3; }
 };
 
 namespace {
@@ -156,7 +158,7 @@ emt_status emt_build_hinv_from_network3(const emt_network* net, const double* L_
   std::vector<double> gv;
   emt_status r = guard([&] {
     EMT_REQUIRE(net && net->n_bus <= (1 << 29), EMT_ERR_INVALID, "null or too large network");
-    emt::network_graph3(net, L_mut, dt, gf, gt, gv);
+    emt::network_graph3(net, L_mut, dt, gf, gt, gv, nullptr);
   });
   if (r != EMT_OK) return r;
   emt_graph g{3 * net->n_bus, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
@@ -268,10 +270,23 @@ emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, dou
   });
 }
 
+emt_status emt_sim3_create(const emt_network* net, const double* L_mut, const emt_hinv_opts* opts, double dt,
+                           void* stream, emt_sim** out) {
+  return guard([&] {
+    EMT_REQUIRE(out, EMT_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    EMT_REQUIRE(net && L_mut && opts, EMT_ERR_INVALID, "null network, mutual inductances or options");
+    std::unique_ptr<emt_sim> h(new emt_sim);
+    h->sim3.reset(new emt::Sim3(net, L_mut, opts, dt, as_stream(stream)));
+    *out = h.release();
+  });
+}
+
 emt_status emt_sim_schedule(emt_sim* s, int32_t step, int32_t kind, int32_t target, double value, int32_t column) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
-    if (s->msim) s->msim->schedule(step, kind, target, value, column);
+    if (s->sim3) s->sim3->schedule(step, kind, target, value, column);
+    else if (s->msim) s->msim->schedule(step, kind, target, value, column);
     else s->sim->schedule(step, kind, target, value, column);
   });
 }
@@ -279,7 +294,8 @@ emt_status emt_sim_schedule(emt_sim* s, int32_t step, int32_t kind, int32_t targ
 emt_status emt_sim_monitor(emt_sim* s, int32_t n_mon, const int32_t* buses) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
-    if (s->msim) s->msim->set_monitor(n_mon, buses);
+    if (s->sim3) s->sim3->set_monitor(n_mon, buses);
+    else if (s->msim) s->msim->set_monitor(n_mon, buses);
     else s->sim->set_monitor(n_mon, buses, nullptr);
   });
 }
@@ -287,7 +303,8 @@ emt_status emt_sim_monitor(emt_sim* s, int32_t n_mon, const int32_t* buses) {
 emt_status emt_step(emt_sim* s, int32_t n_steps, double* record_dev, void* stream) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
-    if (s->msim) s->msim->step(n_steps, record_dev, as_stream(stream));
+    if (s->sim3) s->sim3->step(n_steps, record_dev, as_stream(stream));
+    else if (s->msim) s->msim->step(n_steps, record_dev, as_stream(stream));
     else s->sim->step(n_steps, record_dev, as_stream(stream));
   });
 }
@@ -295,14 +312,16 @@ emt_status emt_step(emt_sim* s, int32_t n_steps, double* record_dev, void* strea
 emt_status emt_sim_read(emt_sim* s, int32_t what, double* host_out) {
   emt_status r = guard([&] {
     EMT_REQUIRE(s && s->ok() && host_out, EMT_ERR_INVALID, "null argument");
-    if (s->msim) s->msim->read(what, host_out);
+    if (s->sim3) s->sim3->read(what, host_out);
+    else if (s->msim) s->msim->read(what, host_out);
     else s->sim->read(what, host_out, nullptr);
   });
   if (r != EMT_OK) return r;
   int dev = 0;
   r = guard([&] {
     EMT_CUDA(cudaDeviceSynchronize());
-    dev = s->msim ? s->msim->store->device_status(nullptr) : s->sim->store->device_status(nullptr);
+    dev = s->sim3 ? s->sim3->store->device_status(nullptr)
+                  : (s->msim ? s->msim->store->device_status(nullptr) : s->sim->store->device_status(nullptr));
   });
   if (r != EMT_OK) return r;
   return status_from_device(dev);
@@ -319,6 +338,7 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(!s->sim3, EMT_ERR_UNSUPPORTED, "three-phase simulations have no launch-shape choices");
     EMT_REQUIRE(rows_per_cta >= 0 && rows_per_cta <= 256, EMT_ERR_INVALID, "rows_per_cta out of range");
     if (s->msim) {
       s->msim->set_gemm(kernels, rows_per_cta, nullptr);
@@ -347,7 +367,8 @@ emt_status emt_sim_autotune(emt_sim* s, int32_t probe_steps, int32_t* best_rpc, 
 emt_status emt_sim_reset(emt_sim* s, void* stream) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
-    if (s->msim) s->msim->reset(as_stream(stream));
+    if (s->sim3) s->sim3->reset(as_stream(stream));
+    else if (s->msim) s->msim->reset(as_stream(stream));
     else s->sim->reset(as_stream(stream));
   });
 }
@@ -355,7 +376,8 @@ emt_status emt_sim_reset(emt_sim* s, void* stream) {
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok() && out && n >= 0, EMT_ERR_INVALID, "null argument");
-    if (s->msim) s->msim->stats(out, n);
+    if (s->sim3) s->sim3->stats(out, n);
+    else if (s->msim) s->msim->stats(out, n);
     else s->sim->stats(out, n);
   });
 }
@@ -363,6 +385,7 @@ emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n) {
 emt_status emt_sim_bench_kernel(emt_sim* s, int32_t which, int32_t reps, void* stream) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(!s->sim3, EMT_ERR_UNSUPPORTED, "no kernel timing for three-phase simulations");
     if (s->msim) s->msim->bench_kernel(which, reps, as_stream(stream));
     else s->sim->bench_kernel(which, reps, as_stream(stream));
   });

@@ -302,12 +302,13 @@ void network_graph(const emt_network* net, double dt, std::vector<int32_t>& gf, 
 // a_p-a_q and b_p-b_q (p < q) with -Y_pq; none when L_mut = 0 (three decoupled phases). RC
 // branches, shunt capacitors and sources act on each phase alone.
 void network_graph3(const emt_network* net, const double* L_mut, double dt, std::vector<int32_t>& gf,
-                    std::vector<int32_t>& gt, std::vector<double>& gv) {
+                    std::vector<int32_t>& gt, std::vector<double>& gv, std::vector<int>* br_ptr) {
   EMT_REQUIRE(net && L_mut && dt > 0, EMT_ERR_INVALID, "null network, null mutual inductances or bad dt");
   check_network_arrays(net);
   gf.clear();
   gt.clear();
   gv.clear();
+  if (br_ptr) br_ptr->assign(1, 0);
   auto add = [&](int x, int y, double g) {
     gf.push_back(x);
     gt.push_back(y);
@@ -340,6 +341,7 @@ void network_graph3(const emt_network* net, const double* L_mut, double dt, std:
       EMT_REQUIRE(std::isfinite(g) && g > 0, EMT_ERR_INVALID, "branch companion conductance must be > 0");
       for (int p = 0; p < 3; ++p) add(3 * a + p, 3 * b + p, g);
     }
+    if (br_ptr) br_ptr->push_back((int)gf.size());
   }
   if (net->shunt_C)
     for (int i = 0; i < net->n_bus; ++i)

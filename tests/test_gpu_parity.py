@@ -540,3 +540,66 @@ def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L):
     L.emt_modify_branch(h, node, -1, 0.1)
     G = omod.modified_G(G, node, -1, 0.1)
     assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= 1e-10
+
+
+# ---------------------------------------------------------------- three-phase time stepping (NEXT-3)
+def _sim3_run(L, net, levels, steps, trips, prec, monitor=None, halves=True):
+    sim = L.emt_sim3_create(net, DT, levels=levels, precision=prec)
+    nn = 3 * net["n_bus"]
+    mon = np.arange(nn) if monitor is None else np.asarray(monitor)
+    L.emt_sim_monitor(sim, mon)
+    for st, e in trips:
+        L.emt_sim_schedule(sim, st, 0, e)
+    rec = torch.zeros(steps, len(mon), dtype=torch.float64, device="cuda")
+    h1 = steps // 2 if halves else steps
+    L.emt_step(sim, h1, rec[:h1])
+    if steps > h1:
+        L.emt_step(sim, steps - h1, rec[h1:])
+    torch.cuda.synchronize()
+    return sim, rec.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_three_phase_stepping_matches_oracle_with_a_coupled_line_trip(L, prec):
+    # one tile in three phases with loads: coupled RL histories (3 x 3), RC branches per phase,
+    # balanced sources and loads; the trip opens a coupled line at step 70 (15 exact node updates)
+    from oracle import emt3 as oemt3
+    net = netgen.three_phase(netgen.add_loads(netgen.tile(1_000_000), seed=3))
+    e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0 and net["L_mut"][k] > 0)
+    ref, state = oemt3.simulate3(net, DT, 140, [(70, oemt3.TRIP, e, 0.0)])
+    sim, got = _sim3_run(L, net, 2, 140, [(70, e)], prec)
+    assert rel_err(got, ref) <= 1e-10, rel_err(got, ref)
+    final = L.emt_sim_read(sim, 0)
+    assert np.array_equal(final, got[-1])
+    assert rel_err(final, state["v"]) <= 1e-10
+
+
+def test_three_phase_stepping_1432_buses_matches_oracle(L):
+    from oracle import emt3 as oemt3
+    net = netgen.three_phase(netgen.tiled(2, 4))
+    e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0 and net["L_mut"][k] > 0)
+    mon = np.sort(np.random.default_rng(17).choice(3 * net["n_bus"], 48, replace=False))
+    ref, _ = oemt3.simulate3(net, DT, 90, [(40, oemt3.TRIP, e, 0.0)], monitor=mon)
+    _, got = _sim3_run(L, net, 3, 90, [(40, e)], 1, monitor=mon)
+    assert rel_err(got, ref) <= 1e-10, rel_err(got, ref)
+
+
+def test_three_phase_reset_repeats_and_rejects_other_events(L):
+    net = netgen.three_phase(netgen.tile(1_000_000))
+    sim = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FF64)
+    L.emt_sim_monitor(sim, np.arange(0, 3 * net["n_bus"], 7))
+    L.emt_sim_schedule(sim, 30, 0, 3)
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_sim_schedule(sim, 40, 1, 5, 10.0)
+    assert ex.value.code == L.EMT_ERR_UNSUPPORTED
+    a = torch.zeros(80, sim.n_mon, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    L.emt_step(sim, 80, a)
+    L.emt_sim_reset(sim)
+    L.emt_step(sim, 80, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    sim32 = None
+    with pytest.raises(L.EmtError) as ex:
+        sim32 = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FP32)
+    assert ex.value.code == L.EMT_ERR_UNSUPPORTED and sim32 is None
