@@ -172,6 +172,117 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
   }
 }
 
+
+// The same injection with two columns per thread (column stride even): the element-end record,
+// the 32-bit index arithmetic and the loop control of an incidence serve both columns, and the
+// pair of float-float values of a row is one 16-byte access. A thread whose second column lies
+// beyond the active ones computes it but stores only the first.
+__device__ __forceinline__ void ld_pair(const float2* p, float2 (&o)[2]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = make_float2(v.x, v.y);
+  o[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void st_pair(float2* p, const float2 (&o)[2], bool both) {
+  if (both) *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+  else p[0] = o[0];
+}
+__global__ void __launch_bounds__(ITH, 2) k_mc_inject2(MSimD m, int ipp, int s_in_chunk, int* status) {
+  extern __shared__ __align__(16) unsigned char ism[];
+  MRec* srec = reinterpret_cast<MRec*>(ism);
+  __shared__ int sptr[IPP_MAX + 1], tptr[IPP_MAX + 1];
+  if (*status != DEV_OK) return;   // uniform, before any barrier
+  const int p0 = blockIdx.x * ipp, np = min(ipp, m.n - p0);
+  const int tid = threadIdx.x, c = 2 * (blockIdx.y * ITH + tid);
+  if (tid <= np) {
+    sptr[tid] = m.inc_ptr[p0 + tid];
+    tptr[tid] = m.term_ptr[p0 + tid];
+  }
+  __syncthreads();
+  const int r0 = sptr[0];
+  for (int i = tid; i < sptr[np] - r0; i += ITH) srec[i] = m.inc[r0 + i];
+  __syncthreads();
+  if (c >= m.R_act) return;
+  const bool both = c + 1 < m.R_act;
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  const int R = m.R;
+  const float2* Ih_rd = m.Ih + ((step - 1) & 1) * m.n_el * R;
+  float2* Ih_wr = m.Ih + (step & 1) * m.n_el * R;
+  int te[2];
+  te[0] = change_on(m, c, step) ? m.trip_elem[c] : -1;
+  te[1] = both && change_on(m, c + 1, step) ? m.trip_elem[c + 1] : -1;
+  const int ti = step - m.dyn->trig_first;
+  const float2 sw = m.trig[2 * ti], cw = m.trig[2 * ti + 1];
+  for (int pi = 0; pi < np; ++pi) {
+    const int pos = p0 + pi;
+    const int k1 = sptr[pi + 1] - r0, t1 = tptr[pi + 1];
+    int kb = sptr[pi] - r0, tb = tptr[pi];
+    float2 vi[2];
+    ld_pair(m.V + pos * R + c, vi);
+    Acc2 hist[2] = {{0.f, 0.f}, {0.f, 0.f}}, inj[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    do {
+      float2 vo[IKB][2], ih[IKB][2], tc[ITB][2], ts[ITB][2];
+#pragma unroll
+      for (int q = 0; q < IKB; ++q) {
+        if (kb + q < k1) {
+          const MRec& r = srec[kb + q];
+          if (r.other >= 0) ld_pair(m.V + r.other * R + c, vo[q]);
+          else vo[q][0] = vo[q][1] = ff_f(0.f);
+          ld_pair(Ih_rd + r.elem * R + c, ih[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < ITB; ++q) {
+        if (tb + q < t1) {
+          ld_pair(m.term_cs + (tb + q) * R + c, tc[q]);
+          ld_pair(m.term_sn + (tb + q) * R + c, ts[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < IKB; ++q) {
+        if (kb + q >= k1) break;
+        const MRec& r = srec[kb + q];
+        float2 ihn[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          // v_e = v_from - v_to (TwoSum of the leading parts), formed identically at both ends
+          const float2 vf = r.sgn > 0 ? vi[j] : vo[q][j], vt = r.sgn > 0 ? vo[q][j] : vi[j];
+          Acc2 de = acc2(vf);
+          de.add(-vt.x, -vt.y);
+          const float2 ve = make_float2(de.s, de.c);
+          // Ih' = a1 v_e + beta Ih, renormalised once (it is state)
+          Acc2 h{0.f, 0.f};
+          h.add_prod(r.a1, ve);
+          h.add_prod(r.beta, ih[q][j]);
+          ihn[j] = r.elem == te[j] ? ff_f(0.f) : h.get();   // the tripped element carries no current
+          if (r.sgn > 0) hist[j].add(-ihn[j].x, -ihn[j].y);
+          else hist[j].add(ihn[j].x, ihn[j].y);
+        }
+        if (r.sgn > 0) st_pair(Ih_wr + r.elem * R + c, ihn, both);
+      }
+#pragma unroll
+      for (int q = 0; q < ITB; ++q) {
+        if (tb + q >= t1) break;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          inj[j].add_prod(tc[q][j], sw);
+          inj[j].add_prod(ts[q][j], cw);
+        }
+      }
+      kb += IKB;
+      tb += ITB;
+    } while (kb < k1 || tb < t1);
+    float2 x[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      inj[j].add(hist[j].s, hist[j].c);
+      x[j] = inj[j].get();
+    }
+    st_pair(m.X + pos * R + c, x, both);
+    if (both) *reinterpret_cast<float2*>(m.Xf + pos * R + c) = make_float2(x[0].x, x[1].x);
+    else m.Xf[pos * R + c] = x[0].x;
+  }
+}
+
 // Leaf stage as a GEMM over the columns (Eq. 2 with Sec. III's leaf blocks):
 // Y[leaf rows] = L_j (FP32) * Xf[leaf rows].
 // Tile 64 x 128, K step 16, 256 threads with an 8 x 4 register tile.
@@ -837,8 +948,11 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
     res_smem = (size_t)mc * (sizeof(float2) + sizeof(int));
     EMT_REQUIRE(inj_smem <= 160 * 1024 && res_smem <= 160 * 1024, EMT_ERR_UNSUPPORTED,
                 "too many element ends on 8 consecutive buses");
-    if (inj_smem > 48 * 1024)
+    if (inj_smem > 48 * 1024) {
       EMT_CUDA(cudaFuncSetAttribute(k_mc_inject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+    }
+
     if (res_smem > 48 * 1024)
       EMT_CUDA(cudaFuncSetAttribute(k_mc_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
     int dev = 0;
@@ -890,6 +1004,11 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   }
   term_ptr.upload(tptr, s);
   term_cs.upload(tcs, s);
+  {
+    // the two-column injection indexes rows with 32-bit products (R even, every row * R < 2^31)
+    const int64_t rows = std::max<int64_t>({(int64_t)2 * n_el_h, (int64_t)n, (int64_t)(tcs.size() / std::max(R, 1))});
+    inj_pairs = (R % 2) == 0 && (rows + 1) * R < ((int64_t)1 << 31);
+  }
   term_sn.upload(tsn, s);
   std::vector<float2> cff(store->csr_val.size());
   for (size_t k = 0; k < cff.size(); ++k) cff[k] = host_ff(store->csr_val[k]);
@@ -1204,9 +1323,7 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
         k_mc_sweep_gemm<<<dim3(n_sweep_items, n_ct), SBT, 0, s>>>(d, Kt.p, ldt, sweep_items.p, sweep_part.p,
                                                                   sweep_count.p, n_ct, store->d_status.p);
     } else if (which == 4) {
-      const int ipp = positions_per_cta();
-      k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, 0,
-                                                                                          store->d_status.p);
+      launch_inject(0, s);
     } else if (which == 5) {
       launch_residual(1, 0, s);
     } else {
@@ -1222,9 +1339,22 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
   EMT_CUDA(cudaGetLastError());
 }
 
+void MSim::launch_inject(int s_in_chunk, cudaStream_t s) {
+  const MSimD d = view();
+  if (inj_pairs) {
+    const int ipp = positions_per_cta(2);
+    k_mc_inject2<<<dim3((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH)), ITH, inj_smem, s>>>(
+        d, ipp, s_in_chunk, store->d_status.p);
+  } else {
+    const int ipp = positions_per_cta();
+    k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, s_in_chunk,
+                                                                                        store->d_status.p);
+  }
+}
+
 // positions per CTA of the injection and residual kernels: enough CTAs for about four per SM
-int MSim::positions_per_cta() const {
-  const int64_t col_blocks = (R_act + ITH - 1) / ITH;
+int MSim::positions_per_cta(int cols_per_thread) const {
+  const int64_t col_blocks = (R_act + cols_per_thread * ITH - 1) / (cols_per_thread * ITH);
   int ipp = IPP_MAX;
   while (ipp > 1 && (int64_t)((n + ipp - 1) / ipp) * col_blocks < 4LL * n_sm) ipp /= 2;
   return ipp;
@@ -1239,10 +1369,8 @@ void MSim::launch_residual(int n1, int s_in_chunk, cudaStream_t s) {
 
 void MSim::launch_steps(int nst, cudaStream_t s) {
   const MSimD d = view();
-  const int ipp = positions_per_cta();
   for (int i = 0; i < nst; ++i) {
-    k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, i,
-                                                                                        store->d_status.p);
+    launch_inject(i, s);
     apply_pass(0, 1, 0, i, s);
     launch_residual(1, i, s);
     apply_pass(1, 1, 1, i, s);

@@ -159,7 +159,9 @@ class MSim {
   void launch_steps(int n, cudaStream_t s);
   void apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s);
   void launch_residual(int n1, int s_in_chunk, cudaStream_t s);
-  int positions_per_cta() const;
+  int positions_per_cta(int cols_per_thread = 1) const;
+  void launch_inject(int s_in_chunk, cudaStream_t s);
+  bool inj_pairs = false;   // two-column injection kernel (even column stride, 32-bit row indices)
   bool tensor_expand() const;
  public:
   void bench_kernel(int which, int reps, cudaStream_t s);
