@@ -57,6 +57,11 @@ def parse():
                          "cost); 7: three-phase 1,432-bus network (4,296 nodes): apply, line trip vs rebuild; "
                          "41: single apply on the 11,456-bus store")
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="for profiler captures: run only the stepping of configs 3/4 (this many time steps) or this "
+                         "many applies of config 41, with no oracle, no e2e and no JSON line")
+    ap.add_argument("--apply-kernels", type=int, default=0, help="config 41 with --profile: emt_apply_tune kernels")
+    ap.add_argument("--columns", type=int, default=0, help="configs 3/4 with --profile: columns (default: all)")
     ap.add_argument("--tune", default="", help="rows_per_cta,kernels: fixed launch shape instead of the autotuner "
                                                "(with kernels 4, rows_per_cta is the cluster size)")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
@@ -681,7 +686,7 @@ def multi_arm(args, cfg: int):
             (kus[2], 2, "alu", 2 * st["s_total"] * st["n_cut_rows"] * Rl / 1e12, fp32_peak, "TFLOP/s"),
         "expansion (tcgen05 k_mc_umma<expand> when it has a tile per SM, else SIMT k_mc_expand_tiled)":
             (kus[3], 2, "hbm", n * Rl * 20 / 1e9, hbm, "GB/s"),
-        "k_mc_inject (histories + injection, float-float)": (kus[4], 1, "hbm", inj_bytes / 1e9, hbm, "GB/s"),
+        inject_name(st): (kus[4], 1, "hbm", inj_bytes / 1e9, hbm, "GB/s"),
         "k_mc_residual (float-float r = x - G'v)": (kus[5], 1, "hbm", res_bytes / 1e9, hbm, "GB/s"),
     }
     kernels = {}
@@ -704,7 +709,7 @@ def multi_arm(args, cfg: int):
                    "parallelism": f"columns split over {world} rank(s), no collective on the data path"},
         "accuracy": {"sampled_columns": {str(k): v for k, v in errs.items()}, "sampled_steps": T,
                      "max": max(errs.values()) if errs else None, "tolerance": ERR_TOL},
-        "roofline": dict(kernels[dom], kernel=dom, traffic=None,
+        "roofline": dict(kernels[dom], kernel=dom, traffic=ncu_traffic(dom, n, Rl),
                          peak_source=("measured" if "when" in peaks else "fallback")
                          + " (tensor: bf16 burst / 3, three BF16 products per FP32-grade product; hbm: copy; "
                            "alu: FP32 FMA rate of the probe)",
@@ -718,6 +723,21 @@ def multi_arm(args, cfg: int):
                                    "hierarchical store, each column single-threaded in its own process"},
         "gpu_launches": int(launches), "clocks": clk,
     }
+
+
+def inject_name(st):
+    if st["inject_columns_per_thread"] == 2:
+        return "k_mc_inject2 (histories + injection, float-float, two columns per thread)"
+    return "k_mc_inject (histories + injection, float-float)"
+
+
+# DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu --set full
+# capture of the kernel as it stands (python bench.py --config 4 --profile 6, third launch)
+NCU_TRAFFIC = {("k_mc_inject2", 11456, 512): 212.828416e6 + 150.211584e6}
+
+
+def ncu_traffic(kernel, n, cols):
+    return NCU_TRAFFIC.get((kernel.split(" ")[0], n, cols))
 
 
 # ---------------------------------------------------------------- config 5 (serving)
@@ -1284,10 +1304,46 @@ def three_phase_arm(args):
     }
 
 
+def profile_run(args):
+    """The kernels of one workload and nothing else, for profiler captures (no timing, no line)."""
+    import numpy as np
+    import torch
+    import netgen
+    import paper_2105_10661_gb300._lib as L
+    if args.config in (3, 4):
+        w = multi_workload(args.config)
+        R = args.columns or w["R"]
+        ss = None if w["ss"] is None else np.ascontiguousarray(w["ss"][:R])
+        ls = None if w["ls"] is None else np.ascontiguousarray(w["ls"][:R])
+        sim = L.emt_sim_create(w["net"], DT, levels=w["levels"], nrhs=R, src_scale=ss, load_scale=ls)
+        for c, (st_, e) in w["trips"].items():
+            if c < R:
+                L.emt_sim_schedule(sim, st_, L.EMT_EVENT_TRIP, e, 0.0, c)
+        L.emt_sim_monitor(sim, w["mon"])
+        rec = torch.zeros(args.profile, R, N_MON, dtype=torch.float64, device="cuda")
+        L.emt_step(sim, args.profile, rec)
+    elif args.config == 41:
+        net = netgen.config_network(4)
+        h = L.emt_build_hinv_from_network(net, DT, levels=4, precision=L.EMT_PREC_FF64)
+        L.emt_apply_tune(h, args.apply_kernels)
+        x = torch.tensor(np.random.default_rng(5).standard_normal(net["n_bus"]), dtype=torch.float64, device="cuda")
+        v = torch.zeros_like(x)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(args.profile):
+            flush.zero_()
+            L.emt_apply(h, x, v)
+    else:
+        raise SystemExit("--profile serves configs 3, 4 and 41")
+    torch.cuda.synchronize()
+
+
 def main():
     args = parse()
     if args.cpu_worker:
         cpu_worker(args.cpu_worker, args.cpu_steps, args.config, args.cpu_col)
+        return
+    if args.profile:
+        profile_run(args)
         return
     rc = launch_ranks(args)
     if rc is not None:

@@ -293,7 +293,9 @@ emt_status emt_sim_reset(emt_sim* s, void* stream);
 /* Sizes of the simulation, for byte/FLOP accounting. out[0..n): n_bus, n_leaf, leaf elements
  * (sum b_j^2), factor elements (sum n_q k_q), core elements (sum (2k_q)^2), CTAs of the fused
  * kernels, element incidences, distinct cut rows, boundary-vector length (sum 2k_q), kernels
- * launched by emt_step/emt_sim_reset since creation, series branches, elements. */
+ * launched by emt_step/emt_sim_reset since creation, series branches, elements, columns per thread
+ * of the injection kernel of a several-column simulation (2 when the columns fill whole blocks of
+ * pairs, else 1; 0 for single-column simulations). */
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
 /* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
  * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the

@@ -1341,7 +1341,7 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
 
 void MSim::launch_inject(int s_in_chunk, cudaStream_t s) {
   const MSimD d = view();
-  if (inj_pairs) {
+  if (inj_pairs && R_act % (2 * ITH) == 0) {   // pairs only when they fill whole blocks
     const int ipp = positions_per_cta(2);
     k_mc_inject2<<<dim3((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH)), ITH, inj_smem, s>>>(
         d, ipp, s_in_chunk, store->d_status.p);
@@ -1536,7 +1536,7 @@ void MSim::stats(int64_t* out, int n_out) const {
     core += 4 * k * k;
   }
   const int64_t v[] = {n, st.n_leaf, leaf, fac, core, n_tiles, n_inc, n_crow, st.s_total, launches, n_series,
-                       (int64_t)el_a.size()};
+                       (int64_t)el_a.size(), (inj_pairs && R % (2 * ITH) == 0) ? 2 : 1};
   for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
 }
 
