@@ -608,6 +608,14 @@ def multi_arm(args, cfg: int):
             e2e_times.append(t1 - t0)
 
     sim = create()
+    tuned = None
+    if not tune:
+        # block tiles, product kinds and the injection kernel timed on this simulation
+        t0 = time.perf_counter()
+        tn, kind = L.emt_sim_autotune(sim, 64, stream)
+        tuned = {"leaf_tile_columns": tn, "kernels": kind,
+                 "inject_columns_per_thread": L.emt_sim_stats(sim)["inject_columns_per_thread"],
+                 "seconds": time.perf_counter() - t0, "probe_steps": 64}
     for _ in range(args.warmup):
         L.emt_sim_reset(sim, stream)
         L.emt_step(sim, T, rec, stream)
@@ -709,6 +717,7 @@ def multi_arm(args, cfg: int):
                    "parallelism": f"columns split over {world} rank(s), no collective on the data path"},
         "accuracy": {"sampled_columns": {str(k): v for k, v in errs.items()}, "sampled_steps": T,
                      "max": max(errs.values()) if errs else None, "tolerance": ERR_TOL},
+        "autotuned": tuned,
         "roofline": dict(kernels[dom], kernel=dom, traffic=ncu_traffic(dom, n, Rl),
                          peak_source=("measured" if "when" in peaks else "fallback")
                          + " (tensor: bf16 burst / 3, three BF16 products per FP32-grade product; hbm: copy; "

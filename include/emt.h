@@ -279,11 +279,16 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
  * a leaf-GEMM tile (0 = chosen from nrhs). Synchronises the device; takes effect on the next
  * emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
-/* Autotuner: time each candidate (cluster sizes 1..16 of generation 4, rows per CTA in {4..48}
- * of generations 3, 2 and 1) on
- * probe_steps steps of this simulation, keep the fastest and remember it for every later
- * simulation of the same network shape in this process (emt_sim_create applies it). Resets the
- * simulation. Synchronises `stream`. best_rpc / best_kernels (may be NULL) receive the choice. */
+/* Autotuner: time each candidate on probe_steps steps of this simulation (after 8 untimed
+ * steps), keep the fastest and remember it for every later simulation of the same shape in this
+ * process (emt_sim_create applies it). Single-column simulations: cluster sizes 1..16 of
+ * generation 4, rows per CTA in {4..48} of generations 3, 2 and 1; best_rpc / best_kernels
+ * receive rows_per_cta and the generation. Multi-column simulations: FP32 CUDA-core products, and
+ * tcgen05 products (kernels 2 and 3) with leaf-GEMM tiles 64, 128, 192 and 256 columns wide; then,
+ * with those, the injection kernel with one or two columns per thread (even nrhs); best_rpc /
+ * best_kernels receive the tile width and `kernels` of emt_sim_tune, emt_sim_stats the injection
+ * choice. Three-phase simulations: EMT_ERR_UNSUPPORTED. Resets the simulation. Synchronises the
+ * device. best_rpc / best_kernels may be NULL. */
 emt_status emt_sim_autotune(emt_sim* s, int32_t probe_steps, int32_t* best_rpc, int32_t* best_kernels,
                             void* stream);
 /* Return the simulation to its state right after emt_sim_create: stored inverse restored

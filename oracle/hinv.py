@@ -5,7 +5,11 @@ splits as G_p = [[G_l, H], [H^T, G_r]] (Eq. 3), and H = h_l h_r^T has rank k,
 the number of branches cut between l and r (Sec. III-A, before Eq. 9). The
 decomposition is not unique; the one used here gives one column per cut
 branch e = (a in l, b in r):  h_l[:, e] = -g_e e_a,  h_r[:, e] = e_b,
-so (h_l h_r^T)[a, b] = -g_e, the off-diagonal entry of G.
+so (h_l h_r^T)[a, b] = -g_e, the off-diagonal entry of G. Three-phase networks
+partitioned by bus (partition.build_block_tree) take block cuts instead: one
+column per (left bus, right node) pair of joined buses, h_l holding the three
+entries G[x, y] of the left bus's nodes x and h_r = e_y, so a coupled line is a
+rank-3 cut (b buses per leaf become 3b nodes).
 
 Two stores share one shape. With P = Ginv_l h_l and Q = Ginv_r h_r (the
 factors of Eq. 9) and Y = blkdiag(P, Q):
@@ -67,18 +71,27 @@ class HInv:
 
     def cut_columns(self, p):
         """h_l, h_r of node p (dense, n_l x k and n_r x k): H = h_l h_r^T of Eq. 3, one column per
-    cut branch (Sec. III-A, before Eq. 9)."""
+    cut branch (Sec. III-A, before Eq. 9). Block trees (partition.build_block_tree, key cut_w = B)
+    have B left entries per column, h_l[x, c] = G[x, y] for the B vertices x of the left group and
+    h_r = e_y."""
         t = self.tree
         l, r = int(t["left"][p]), int(t["right"][p])
         ll, lh = self.node_range(l)
         rl, rh = self.node_range(r)
         s, e = int(t["cut_ptr"][p]), int(t["cut_ptr"][p + 1])
         k = e - s
+        W = int(t.get("cut_w", 1))
         hl = np.zeros((lh - ll, k))
         hr = np.zeros((rh - rl, k))
         for c in range(k):
-            a = int(t["cut_a"][s + c]); b = int(t["cut_b"][s + c]); br = int(t["cut_e"][s + c])
-            hl[a - ll, c] = -self.g_branch[br]
+            b = int(t["cut_b"][s + c])
+            if W == 1:
+                a = int(t["cut_a"][s + c]); br = int(t["cut_e"][s + c])
+                hl[a - ll, c] = -self.g_branch[br]
+            else:
+                for w in range(W):
+                    a = int(t["cut_a"][W * (s + c) + w])
+                    hl[a - ll, c] = self.Gp[a, b]
             hr[b - rl, c] = 1.0
         return hl, hr
 

@@ -262,6 +262,66 @@ def build_tree(n_bus: int, frm: np.ndarray, to: np.ndarray, levels: int = 0, d_t
                 cut_b=np.array(cut_b, np.int64), cut_e=np.array(cut_e, np.int64))
 
 
+def build_block_tree(n_node: int, frm: np.ndarray, to: np.ndarray, B: int, levels: int = 0,
+                     d_th: int = 0) -> dict:
+    """Partition tree whose units are groups of B consecutive vertices (the three nodes of a
+    three-phase bus, so that a leaf of b buses holds 3b nodes), with block cuts.
+
+    The paper counts three nodes per bus (Sec. III-A, after Eq. 3) and bisects buses (Sec. III-B).
+    Here the group graph has one edge per distinct pair of groups joined by any vertex branch
+    (x // B != y // B, y >= 0), listed as (min, max) in ascending order; build_tree bisects it
+    (d_th counts vertices: a group leaf holds at most d_th // B groups). Positions expand group
+    by group: vertex B g + w sits at B pos_g[g] + w.
+
+    A node's cut columns factor the off-diagonal block of Eq. 3 exactly, H = G_lr = h_l h_r^T,
+    with one column per (left group A, right vertex y) pair whose groups are joined:
+    h_r = e_y and h_l holds G[x, y] at the B vertices x of A. A coupled three-phase line is then
+    one rank-3 cut (B columns) instead of one column per vertex branch. Columns are sorted by
+    (position of A's first vertex, position of y); cut_a holds B positions per column
+    (cut_a[B c + w]), cut_e is -1 (the coefficients come from G itself)."""
+    frm = np.asarray(frm, np.int64)
+    to = np.asarray(to, np.int64)
+    if B < 1 or n_node % B:
+        raise ValueError("n_node must be a multiple of B")
+    ng = n_node // B
+    pairs = sorted({(min(int(x) // B, int(y) // B), max(int(x) // B, int(y) // B))
+                    for x, y in zip(frm, to) if y >= 0 and int(x) // B != int(y) // B})
+    gf = np.array([a for a, _ in pairs], np.int64)
+    gt = np.array([b for _, b in pairs], np.int64)
+    tg = build_tree(ng, gf, gt, levels=levels, d_th=d_th // B if levels <= 0 else 0)
+    nn = len(tg["lo"])
+    perm = (B * tg["perm"][:, None] + np.arange(B)[None, :]).reshape(-1)
+    pos = np.empty(n_node, np.int64)
+    pos[perm] = np.arange(n_node)
+    lo, hi = B * tg["lo"], B * tg["hi"]
+    gpos = tg["pos"]
+    cut_ptr = [0]
+    cut_a, cut_b = [], []
+    for p in range(nn):
+        l, r = int(tg["left"][p]), int(tg["right"][p])
+        if l >= 0:
+            cols = []
+            for a, b in pairs:
+                pa, pb = int(gpos[a]), int(gpos[b])
+                if tg["lo"][l] <= pa < tg["hi"][l] and tg["lo"][r] <= pb < tg["hi"][r]:
+                    A, Bb = pa, pb
+                elif tg["lo"][l] <= pb < tg["hi"][l] and tg["lo"][r] <= pa < tg["hi"][r]:
+                    A, Bb = pb, pa
+                else:
+                    continue
+                for q in range(B):
+                    cols.append((B * A, B * Bb + q))
+            cols.sort()
+            for a0, y in cols:
+                cut_a.extend(a0 + w for w in range(B))
+                cut_b.append(y)
+        cut_ptr.append(len(cut_b))
+    return dict(n_bus=n_node, perm=perm, pos=pos, lo=lo, hi=hi, parent=tg["parent"], left=tg["left"],
+                right=tg["right"], depth=tg["depth"], leaves=tg["leaves"],
+                cut_ptr=np.array(cut_ptr, np.int64), cut_a=np.array(cut_a, np.int64),
+                cut_b=np.array(cut_b, np.int64), cut_e=np.full(len(cut_b), -1, np.int64), cut_w=B)
+
+
 def leaf_of(tree: dict, position: int) -> int:
     """The leaf holding a position: where Algorithm 2 starts (Sec. IV)."""
     for j in tree["leaves"]:

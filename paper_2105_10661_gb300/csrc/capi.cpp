@@ -356,9 +356,11 @@ emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
 emt_status emt_sim_autotune(emt_sim* s, int32_t probe_steps, int32_t* best_rpc, int32_t* best_kernels,
                             void* stream) {
   return guard([&] {
-    EMT_REQUIRE(s && s->sim, EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(!s->sim3, EMT_ERR_UNSUPPORTED, "three-phase simulations have no launch-shape choices");
     int r = 0, k = 0;
-    s->sim->autotune(probe_steps, &r, &k, as_stream(stream));
+    if (s->msim) s->msim->autotune(probe_steps, &r, &k, nullptr, as_stream(stream));
+    else s->sim->autotune(probe_steps, &r, &k, as_stream(stream));
     if (best_rpc) *best_rpc = r;
     if (best_kernels) *best_kernels = k;
   });

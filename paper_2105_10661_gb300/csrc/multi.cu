@@ -1,7 +1,10 @@
 // Multi-column EMT stepping (see multi.h).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <tuple>
 
 #include "multi.h"
@@ -1047,6 +1050,7 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   EMT_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   EMT_CUDA(cudaStreamSynchronize(s));
   EMT_REQUIRE(store->device_status(s) == DEV_OK, EMT_ERR_SINGULAR, "G is not positive definite");
+  apply_cached_tuning(s);
 }
 
 MSim::~MSim() {
@@ -1339,9 +1343,14 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
   EMT_CUDA(cudaGetLastError());
 }
 
+bool MSim::inject_pairs() const {
+  if (!inj_pairs || inj_mode == 1) return false;
+  return inj_mode == 2 || R_act % (2 * ITH) == 0;   // by default pairs only when they fill whole blocks
+}
+
 void MSim::launch_inject(int s_in_chunk, cudaStream_t s) {
   const MSimD d = view();
-  if (inj_pairs && R_act % (2 * ITH) == 0) {   // pairs only when they fill whole blocks
+  if (inject_pairs()) {
     const int ipp = positions_per_cta(2);
     k_mc_inject2<<<dim3((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH)), ITH, inj_smem, s>>>(
         d, ipp, s_in_chunk, store->d_status.p);
@@ -1484,6 +1493,100 @@ void MSim::set_gemm(int kind, int tn, cudaStream_t s) {
   EMT_CUDA(cudaStreamSynchronize(s));
 }
 
+void MSim::set_inject(int mode) {
+  EMT_REQUIRE(mode >= 0 && mode <= 2, EMT_ERR_INVALID, "injection mode must be 0, 1 or 2");
+  EMT_REQUIRE(mode != 2 || inj_pairs, EMT_ERR_UNSUPPORTED, "two columns per thread need an even column count");
+  EMT_CUDA(cudaDeviceSynchronize());
+  drop_graphs();
+  inj_mode = mode;
+}
+
+namespace {
+// tuning key: buses, leaves, depth, precision, columns, SMs
+using MTuneKey = std::array<int64_t, 6>;
+std::map<MTuneKey, std::array<int, 3>> g_mtune_cache;
+std::mutex g_mtune_mutex;
+MTuneKey mtune_key(const MSim& m, int sms) {
+  return {m.n, m.store->n_leaf, m.store->tree.max_depth, m.store->precision, m.R, sms};
+}
+}  // namespace
+
+void MSim::autotune(int probe_steps, int* best_tn, int* best_kind, int* best_inj, cudaStream_t s) {
+  EMT_REQUIRE(probe_steps >= 1 && probe_steps <= 100000, EMT_ERR_INVALID, "probe_steps out of range");
+  EMT_REQUIRE(R_act == R, EMT_ERR_STATE, "tune a simulation with every column active");
+  cudaEvent_t e0, e1;
+  EMT_CUDA(cudaEventCreate(&e0));
+  EMT_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&]() {
+    reset(s);
+    step(8, nullptr, s);
+    EMT_CUDA(cudaEventRecord(e0, s));
+    step(probe_steps, nullptr, s);
+    EMT_CUDA(cudaEventRecord(e1, s));
+    EMT_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    EMT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  // candidates of the products: FP32 CUDA cores, then tcgen05 (leaf tiles of every width, with
+  // the expansion on tcgen05 by the tile count or always)
+  std::vector<std::pair<int, int>> cands = {{1, 0}};
+  if (umma.ready)
+    for (int kind : {2, 3})
+      for (int tn : {64, 128, 192, 256}) cands.push_back({kind, tn});
+  float best = 1e30f;
+  int bkind = 1, btn = 0;
+  set_inject(0);
+  for (auto [kind, tn] : cands) {
+    set_gemm(kind, tn, s);
+    if (kind == 3 && umma.x_tiles >= n_sm) continue;   // the same kernels as kind 2
+    const float ms = time_it();
+    if (ms < best) {
+      best = ms;
+      bkind = kind;
+      btn = tn;
+    }
+  }
+  set_gemm(bkind, btn, s);
+  // then the injection kernel with those products
+  int binj = 0;
+  if (inj_pairs) {
+    for (int mode : {1, 2}) {
+      set_inject(mode);
+      const float ms = time_it();
+      if (ms < best) {
+        best = ms;
+        binj = mode;
+      }
+    }
+    set_inject(binj);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  reset(s);
+  EMT_CUDA(cudaStreamSynchronize(s));
+  {
+    std::lock_guard<std::mutex> lk(g_mtune_mutex);
+    g_mtune_cache[mtune_key(*this, n_sm)] = {bkind, btn, binj};
+  }
+  if (best_tn) *best_tn = btn;
+  if (best_kind) *best_kind = bkind;
+  if (best_inj) *best_inj = binj;
+}
+
+bool MSim::apply_cached_tuning(cudaStream_t s) {
+  std::array<int, 3> v;
+  {
+    std::lock_guard<std::mutex> lk(g_mtune_mutex);
+    auto it = g_mtune_cache.find(mtune_key(*this, n_sm));
+    if (it == g_mtune_cache.end()) return false;
+    v = it->second;
+  }
+  set_gemm(v[0], v[1], s);
+  set_inject(v[2]);
+  return true;
+}
+
 void MSim::reset(cudaStream_t s) {
   Ih.zero(s);
   V.zero(s);
@@ -1536,7 +1639,7 @@ void MSim::stats(int64_t* out, int n_out) const {
     core += 4 * k * k;
   }
   const int64_t v[] = {n, st.n_leaf, leaf, fac, core, n_tiles, n_inc, n_crow, st.s_total, launches, n_series,
-                       (int64_t)el_a.size(), (inj_pairs && R % (2 * ITH) == 0) ? 2 : 1};
+                       (int64_t)el_a.size(), inject_pairs() ? 2 : 1};
   for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
 }
 

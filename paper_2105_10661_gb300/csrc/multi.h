@@ -105,6 +105,14 @@ class MSim {
   // 1 SIMT FP32, 2 tcgen05 BF16x3 (expansion on tcgen05 when it fills the SMs), 3 tcgen05 for both
   // products; leaf-GEMM tiles tn columns wide (0: by the column count)
   void set_gemm(int kind, int tn, cudaStream_t s);
+  // injection kernel: 0 by the column count (two columns per thread when they fill whole blocks
+  // of pairs), 1 one column per thread, 2 two columns per thread (even column counts only)
+  void set_inject(int mode);
+  // time every candidate product kind, leaf-GEMM tile width and injection kernel on `probe_steps`
+  // steps and keep the fastest (cached per network and column-count shape for this process); the
+  // simulation is reset afterwards
+  void autotune(int probe_steps, int* best_tn, int* best_kind, int* best_inj, cudaStream_t s);
+  bool apply_cached_tuning(cudaStream_t s);
   // serving: (re)start column c as a new request at the current step, with an optional
   // per-column change (kind 0 trip of series branch `target`, kind 1 fault at bus `target` with
   // R_f = value ohm lasting `len` steps, kind -1 none) `ev_step` steps after the start
@@ -162,6 +170,8 @@ class MSim {
   int positions_per_cta(int cols_per_thread = 1) const;
   void launch_inject(int s_in_chunk, cudaStream_t s);
   bool inj_pairs = false;   // two-column injection kernel (even column stride, 32-bit row indices)
+  int inj_mode = 0;
+  bool inject_pairs() const;
   bool tensor_expand() const;
  public:
   void bench_kernel(int which, int reps, cudaStream_t s);

@@ -489,6 +489,44 @@ def test_multi_column_leaf_tile_widths_match_oracle(L, tile, R):
         assert rel_err(got[:, c, :], ref) <= 1e-8, (c, rel_err(got[:, c, :], ref))
 
 
+def test_multi_column_autotune_times_the_shapes_and_matches_oracle(L):
+    # the autotuner times FP32 products and tcgen05 leaf tiles of every width, then the injection
+    # kernel; the shape it keeps still matches the oracle, and a later simulation of the same shape
+    # starts with it (bit-for-bit the same trajectory)
+    net = netgen.tiled(2, 4)
+    R, steps = 96, 30
+    branches = netgen.pick_branches(net, 2, seed=21)
+    trips = {3: (11, int(branches[0])), R - 2: (17, int(branches[1]))}
+    mon = np.arange(0, net["n_bus"], 11)
+
+    def make():
+        sim = L.emt_sim_create(net, DT, levels=3, nrhs=R)
+        for c, (st, e) in trips.items():
+            L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+        L.emt_sim_monitor(sim, mon)
+        return sim
+
+    def run(sim):
+        rec = torch.zeros(steps, R, len(mon), dtype=torch.float64, device="cuda")
+        L.emt_step(sim, steps, rec)
+        torch.cuda.synchronize()
+        return rec.cpu().numpy()
+
+    sim = make()
+    tn, kind = L.emt_sim_autotune(sim, 8)
+    assert kind in (1, 2, 3) and tn in (0, 64, 128, 192, 256), (tn, kind)
+    assert L.emt_sim_stats(sim)["inject_columns_per_thread"] in (1, 2)
+    got = run(sim)
+    nw = oemt.Network(net, DT, levels=3)
+    for c in (0, 3, R // 2, R - 2):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
+        assert rel_err(got[:, c, :], ref) <= 1e-8, (c, rel_err(got[:, c, :], ref))
+    again = make()
+    assert L.emt_sim_stats(again)["inject_columns_per_thread"] == L.emt_sim_stats(sim)["inject_columns_per_thread"]
+    assert np.array_equal(run(again), got)
+
+
 # ---------------------------------------------------------------- three-phase buses
 def _three_phase(levels=3):
     from oracle import companion as ocm

@@ -649,6 +649,74 @@ def test_three_phase_exact_store_equals_dense_inverse():
     assert np.allclose(H.apply(X), np.linalg.solve(G, X), rtol=0, atol=1e-12 * np.abs(np.linalg.solve(G, X)).max())
 
 
+def _block_case(levels=2):
+    net = netgen.three_phase(netgen.tile(1_000_000))
+    gr = cm.three_phase_graph(net, DT)
+    return net, gr, cm.assemble_dense(gr), pt.build_block_tree(gr["n_bus"], gr["frm"], gr["to"], 3, levels=levels)
+
+
+def test_block_tree_keeps_buses_together_and_factors_each_h_exactly():
+    # Eq. 3: H is the off-diagonal block G_lr; with block cuts h_l h_r^T must equal it entry for
+    # entry, every node must hold whole buses (b buses -> 3b nodes), and a coupled line costs one
+    # rank-3 cut instead of one column per node branch
+    net, gr, G, tb = _block_case()
+    n = gr["n_bus"]
+    perm = tb["perm"]
+    assert np.array_equal(perm % 3, np.tile(np.arange(3), n // 3))
+    assert np.array_equal(perm[0::3] // 3, perm[1::3] // 3) and np.array_equal(perm[0::3] // 3, perm[2::3] // 3)
+    assert np.all(tb["lo"] % 3 == 0) and np.all(tb["hi"] % 3 == 0)
+    st = hinv.HInv(G, tb, np.zeros(0), hinv.EXACT)
+    Gp = G[np.ix_(perm, perm)]
+    pairs_total = 0
+    for p in range(len(tb["lo"])):
+        l, r = int(tb["left"][p]), int(tb["right"][p])
+        if l < 0:
+            continue
+        hl, hr = st.cut_columns(p)
+        H = Gp[tb["lo"][l]:tb["hi"][l], tb["lo"][r]:tb["hi"][r]]
+        assert np.array_equal(hl @ hr.T, H)
+        # bus pairs joined across this cut, counted by brute force from the series branches
+        lb = set(int(x) for x in perm[tb["lo"][l]:tb["hi"][l]] // 3)
+        rb = set(int(x) for x in perm[tb["lo"][r]:tb["hi"][r]] // 3)
+        pairs = {(min(a, b), max(a, b)) for a, b in zip(net["br_a"], net["br_b"])
+                 if (a in lb and b in rb) or (a in rb and b in lb)}
+        assert tb["cut_ptr"][p + 1] - tb["cut_ptr"][p] == 3 * len(pairs)
+        pairs_total += len(pairs)
+    ser = gr["to"] >= 0
+    tn = pt.build_tree(n, gr["frm"][ser], gr["to"][ser], levels=2)
+    assert len(tb["cut_b"]) == 3 * pairs_total < len(tn["cut_b"])
+
+
+def test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1():
+    net, gr, G, tb = _block_case(levels=3)
+    perm = tb["perm"]
+    ex = hinv.HInv(G, tb, np.zeros(0), hinv.EXACT)
+    Ginv = np.linalg.inv(G)
+    assert hinv.relative_error(ex.dense(), Ginv) <= 1e-12
+    pa = hinv.HInv(G, tb, np.zeros(0), hinv.PAPER)
+    ref = hinv.algorithm1_dense(G[np.ix_(perm, perm)], tb)
+    got = pa.dense()[np.ix_(perm, perm)]
+    assert hinv.relative_error(got, ref) <= 1e-12
+
+
+def test_block_store_local_update_equals_rebuild():
+    # Sec. IV on a block store: a cross-phase node branch of a cut line changes its column's
+    # coefficient (read from G), and Algorithm 2 carried to the root equals a rebuild
+    net, gr, G, tb = _block_case()
+    st = hinv.HInv(G, tb, gr["g"], hinv.EXACT)
+    p = 0
+    a = int(tb["cut_a"][3 * tb["cut_ptr"][p] + 1])
+    y = int(tb["cut_b"][tb["cut_ptr"][p]])
+    xa, xb = int(tb["perm"][a]), int(tb["perm"][y])
+    frm = np.asarray(gr["frm"])
+    to = np.asarray(gr["to"])
+    assert modify.find_branch(frm, to, xa, xb) >= 0
+    delta = -0.25 * abs(float(G[xa, xb]))
+    new = modify.algorithm2(st, frm, to, xa, xb, delta, to_root=True)
+    G2 = modify.modified_G(G, xa, xb, delta)
+    assert hinv.relative_error(new.dense(), np.linalg.inv(G2)) <= 1e-12
+
+
 # ---------------------------------------------------------------- three-phase stepping
 def _with_loads(net):
     out = dict(net)

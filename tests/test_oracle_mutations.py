@@ -195,6 +195,46 @@ def test_fault_clearing_by_restoring_the_pre_fault_solver_is_caught(monkeypatch)
     assert _some_pin_fails([lambda: T.test_kirchhoff_balance_through_trips_and_overlapping_faults("dense")])
 
 
+def test_block_cut_columns_without_the_cross_phase_entries_are_caught(monkeypatch):
+    # the node-level reading carried into block cuts: only the same-phase vertex of the left bus
+    orig = hinv.HInv.cut_columns
+
+    def mutated(self, p):
+        hl, hr = orig(self, p)
+        if int(self.tree.get("cut_w", 1)) == 3:
+            lo = int(self.tree["lo"][int(self.tree["left"][p])])
+            ro = int(self.tree["lo"][int(self.tree["right"][p])])
+            rows = np.arange(hl.shape[0])[:, None] + lo
+            cols = (np.argmax(hr, axis=0) + ro)[None, :]
+            hl = np.where(rows % 3 == cols % 3, hl, 0.0)
+        return hl, hr
+
+    monkeypatch.setattr(hinv.HInv, "cut_columns", mutated)
+    assert _some_pin_fails([T.test_block_tree_keeps_buses_together_and_factors_each_h_exactly,
+                            T.test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1])
+
+
+def test_block_tree_with_a_dropped_bus_pair_is_caught(monkeypatch):
+    orig = pt.build_block_tree
+
+    def mutated(*a, **k):
+        t = dict(orig(*a, **k))
+        B = int(t["cut_w"])
+        e0, e1 = int(t["cut_ptr"][0]), int(t["cut_ptr"][1])
+        keep = np.ones(len(t["cut_b"]), bool)
+        keep[e1 - B:e1] = False   # the root's last joined bus pair is lost
+        t["cut_b"] = t["cut_b"][keep]
+        t["cut_e"] = t["cut_e"][keep]
+        t["cut_a"] = t["cut_a"].reshape(-1, B)[keep].reshape(-1)
+        t["cut_ptr"] = np.concatenate([t["cut_ptr"][:1], t["cut_ptr"][1:] - B])
+        assert e1 - e0 >= B
+        return t
+
+    monkeypatch.setattr(pt, "build_block_tree", mutated)
+    assert _some_pin_fails([T.test_block_tree_keeps_buses_together_and_factors_each_h_exactly,
+                            T.test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1])
+
+
 @pytest.mark.parametrize("case", ["none"])
 def test_the_pins_pass_without_a_mistake(case):
     # the control: with nothing planted, every pin used above passes
@@ -209,4 +249,6 @@ def test_the_pins_pass_without_a_mistake(case):
         T.test_kl_never_worse_than_growth_and_small_brute_force,
         lambda: T.test_bisection_reaches_brute_force_minimum("ladder", T._graph_ladder(6), 12),
         T.test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs,
+        T.test_block_tree_keeps_buses_together_and_factors_each_h_exactly,
+        T.test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1,
         T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
