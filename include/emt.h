@@ -71,12 +71,20 @@ typedef struct {
 
 /* Build options. levels > 0: bisect to depth `levels` (2^levels leaves when sizes allow);
  * levels == 0: bisect while a set has more than d_th buses (a leaf holds at most d_th buses,
- * the node threshold of Sec. III-B). */
+ * the node threshold of Sec. III-B).
+ * nodes_per_bus = B >= 2: the graph's vertices come in groups of B consecutive indices (the three
+ * nodes of a three-phase bus, Sec. III-A after Eq. 3; n_bus a multiple of B). The partition bisects
+ * groups, so a leaf of b buses holds B b vertices, and cuts are block cuts: one column per (left
+ * group, right vertex) of joined groups, with the B entries G[x, y] of the left group's vertices,
+ * so a coupled three-phase line is one rank-3 cut (B = 3) instead of one column per vertex
+ * branch; d_th counts vertices. 0 or 1: every vertex is its own unit (0 means 3 for the
+ * three-phase builders emt_build_hinv_from_network3 and emt_sim3_create). */
 typedef struct {
   int32_t levels;
   int32_t d_th;
   int32_t mode;            /* EMT_MODE_*  */
   int32_t precision;       /* EMT_PREC_*  */
+  int32_t nodes_per_bus;   /* 0 or 1: none; B >= 2: groups of B vertices, block cuts */
 } emt_hinv_opts;
 
 const char* emt_last_error(void);
@@ -92,7 +100,9 @@ emt_status emt_tree_build(const emt_graph* graph, const emt_hinv_opts* opts, emt
 emt_status emt_tree_sizes(const emt_tree* t, int32_t* n_node, int32_t* n_leaf, int32_t* n_cut);
 /* Copy the tree out. perm: [n_bus]; lo, hi, parent (-1 at the root), left, right (-1 at
  * leaves), depth: [n_node]; cut_ptr: [n_node + 1]; cut_a, cut_b (positions in perm, a in the
- * left child, b in the right), cut_branch (branch id): [n_cut]. Any pointer may be NULL. */
+ * left child, b in the right), cut_branch (branch id): [n_cut]. Trees with nodes_per_bus B >= 2
+ * have one cut per block column: cut_a is the first position of the left group (its B vertices
+ * follow it), cut_b the right vertex, cut_branch -1. Any pointer may be NULL. */
 emt_status emt_tree_arrays(const emt_tree* t, int32_t* perm, int32_t* lo, int32_t* hi,
                            int32_t* parent, int32_t* left, int32_t* right, int32_t* depth,
                            int32_t* cut_ptr, int32_t* cut_a, int32_t* cut_b, int32_t* cut_branch);
@@ -157,9 +167,11 @@ emt_status emt_modify_branch(emt_hinv* h, int32_t bus_a, int32_t bus_b, double d
 emt_status emt_apply_noalloc(const emt_hinv* h, const double* i_dev, double* v_dev, void* stream);
 
 /* Kernels of the single-vector emt_apply on stores whose leaf blocks do not stay in the caches
- * (FP64 or FF64 stores with >= 48 MB of leaf blocks). kernels = 0 (default, automatic) or 1: three
- * kernels (leaf stream, sweep product, expansion) chained with programmatic dependent launch, which
- * also lets consecutive applies overlap. kernels = 2: one cooperative launch of one CTA per SM whose
+ * (FP64 or FF64 stores with >= 48 MB of leaf blocks). kernels = 0 (default, automatic): the
+ * streaming kernels for such stores, the fused kernels of small stores otherwise. kernels = 1:
+ * three kernels (leaf stream, sweep product, expansion) chained with programmatic dependent launch,
+ * which also lets consecutive applies overlap, for any FP64 or FF64 store whose leaf rows fit their
+ * stages (small stores included). kernels = 2: one cooperative launch of one CTA per SM whose
  * warps each stream their own leaf rows (asynchronous 16-byte copies, one row ahead), which then
  * stages the factor rows and its part of the sweep matrix and meets the other CTAs at two grid-wide
  * barriers (bounded waits: EMT_ERR_TIMEOUT at the next synchronising call if one ran out); it falls

@@ -47,7 +47,8 @@ class EmtGraph(C.Structure):
 
 
 class EmtHinvOpts(C.Structure):
-    _fields_ = [("levels", C.c_int32), ("d_th", C.c_int32), ("mode", C.c_int32), ("precision", C.c_int32)]
+    _fields_ = [("levels", C.c_int32), ("d_th", C.c_int32), ("mode", C.c_int32), ("precision", C.c_int32),
+                ("nodes_per_bus", C.c_int32)]
 
 
 class EmtNetwork(C.Structure):
@@ -190,8 +191,8 @@ def make_graph(n_bus, frm, to, g):
     return gr, keep
 
 
-def make_opts(levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64):
-    return EmtHinvOpts(int(levels), int(d_th), int(mode), int(precision))
+def make_opts(levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64, nodes_per_bus=0):
+    return EmtHinvOpts(int(levels), int(d_th), int(mode), int(precision), int(nodes_per_bus))
 
 
 def make_network(net: dict):
@@ -213,11 +214,11 @@ def emt_version():
     return lib.emt_version().decode()
 
 
-def emt_tree_build(n_bus, frm, to, g=None, levels=0, d_th=0):
+def emt_tree_build(n_bus, frm, to, g=None, levels=0, d_th=0, nodes_per_bus=0):
     if g is None:
         g = np.ones(len(frm))
     gr, keep = make_graph(n_bus, frm, to, g)
-    o = make_opts(levels, d_th)
+    o = make_opts(levels, d_th, nodes_per_bus=nodes_per_bus)
     h = C.c_void_p()
     _check(lib.emt_tree_build(C.byref(gr), C.byref(o), C.byref(h)))
     try:
@@ -265,9 +266,10 @@ def emt_hinv_get_partition(h: HInv):
     return perm, lo, hi, parent
 
 
-def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64, stream=None):
+def emt_build_hinv(n_bus, frm, to, g, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64, stream=None,
+                   nodes_per_bus=0):
     gr, keep = make_graph(n_bus, frm, to, g)
-    o = make_opts(levels, d_th, mode, precision)
+    o = make_opts(levels, d_th, mode, precision, nodes_per_bus)
     h = C.c_void_p()
     _check(lib.emt_build_hinv(C.byref(gr), C.byref(o), _stream(stream), C.byref(h)))
     return HInv(h.value, n_bus)
@@ -472,22 +474,25 @@ def emt_build_hinv_from_network(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_E
 
 
 def emt_build_hinv_from_network3(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FP64,
-                                 stream=None):
-    """Store of a three-phase network (3 nodes per bus; `net["L_mut"]` mutual inductances)."""
+                                 stream=None, nodes_per_bus=0):
+    """Store of a three-phase network (3 nodes per bus; `net["L_mut"]` mutual inductances); block cuts
+    unless nodes_per_bus == 1."""
     nw, keep = make_network(net)
     lm = _f64(net["L_mut"])
-    o = make_opts(levels, d_th, mode, precision)
+    o = make_opts(levels, d_th, mode, precision, nodes_per_bus)
     h = C.c_void_p()
     _check(lib.emt_build_hinv_from_network3(C.byref(nw), _p(lm, _f64p), float(dt), C.byref(o), _stream(stream),
                                             C.byref(h)))
     return HInv(h.value, 3 * int(net["n_bus"]))
 
 
-def emt_sim3_create(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FF64, stream=None):
-    """Three-phase simulation (3 nodes per bus; `net["L_mut"]` mutual inductances of the RL branches)."""
+def emt_sim3_create(net: dict, dt, levels=0, d_th=0, mode=EMT_MODE_EXACT, precision=EMT_PREC_FF64, stream=None,
+                    nodes_per_bus=0):
+    """Three-phase simulation (3 nodes per bus; `net["L_mut"]` mutual inductances of the RL branches);
+    block cuts unless nodes_per_bus == 1."""
     nw, keep = make_network(net)
     lm = _f64(net["L_mut"])
-    o = make_opts(levels, d_th, mode, precision)
+    o = make_opts(levels, d_th, mode, precision, nodes_per_bus)
     h = C.c_void_p()
     _check(lib.emt_sim3_create(C.byref(nw), _p(lm, _f64p), C.byref(o), float(dt), _stream(stream), C.byref(h)))
     return Sim(h.value, 3 * int(net["n_bus"]), 1)

@@ -273,7 +273,7 @@ void apply_vectors(Store& st, FusedPlan& p, DevBuf<double>& vpos, DevBuf<double>
   if (vpos.n < (size_t)st.n) vpos.alloc(st.n);
   if (rpos.n < (size_t)st.n) rpos.alloc(st.n);
   if (p.sa && p.sa->rps_req != p.stream_rps) p.sa.reset();   // re-plan for another stage depth
-  if (!p.sa && stream_apply_wanted(st)) {
+  if (!p.sa && (stream_apply_wanted(st) || (p.stream_mode >= 1 && st.precision != EMT_PREC_FP32))) {
     auto sa = std::make_shared<StreamApply>();
     sa->rps_req = p.stream_rps;
     if (sa->build(st, s)) p.sa = sa;

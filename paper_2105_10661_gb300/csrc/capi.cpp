@@ -86,6 +86,13 @@ emt_status status_from_device(int dev) {
   return EMT_ERR_CUDA;
 }
 
+// three-phase builders: block cuts (three nodes per bus) unless the caller asks otherwise
+emt_hinv_opts three_phase_opts(const emt_hinv_opts& o) {
+  emt_hinv_opts c = o;
+  if (c.nodes_per_bus == 0) c.nodes_per_bus = 3;
+  return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -97,8 +104,12 @@ emt_status emt_tree_build(const emt_graph* graph, const emt_hinv_opts* opts, emt
   return guard([&] {
     EMT_REQUIRE(graph && opts && out, EMT_ERR_INVALID, "null argument");
     EMT_REQUIRE(graph->n_branch == 0 || (graph->from && graph->to), EMT_ERR_INVALID, "null branch arrays");
+    EMT_REQUIRE(opts->nodes_per_bus >= 0, EMT_ERR_INVALID, "nodes_per_bus must be >= 0");
     std::unique_ptr<emt_tree> t(new emt_tree);
-    t->t = emt::build_tree(graph->n_bus, graph->n_branch, graph->from, graph->to, opts->levels, opts->d_th);
+    t->t = opts->nodes_per_bus >= 2
+               ? emt::build_block_tree(graph->n_bus, graph->n_branch, graph->from, graph->to, opts->nodes_per_bus,
+                                       opts->levels, opts->d_th)
+               : emt::build_tree(graph->n_bus, graph->n_branch, graph->from, graph->to, opts->levels, opts->d_th);
     *out = t.release();
   });
 }
@@ -162,7 +173,9 @@ emt_status emt_build_hinv_from_network3(const emt_network* net, const double* L_
   });
   if (r != EMT_OK) return r;
   emt_graph g{3 * net->n_bus, (int32_t)gf.size(), gf.data(), gt.data(), gv.data()};
-  return emt_build_hinv(&g, opts, stream, out);
+  if (!opts) return emt_build_hinv(&g, opts, stream, out);
+  const emt_hinv_opts o3 = three_phase_opts(*opts);
+  return emt_build_hinv(&g, &o3, stream, out);
 }
 
 emt_status emt_build_hinv_from_network(const emt_network* net, double dt, const emt_hinv_opts* opts, void* stream,
@@ -277,7 +290,8 @@ emt_status emt_sim3_create(const emt_network* net, const double* L_mut, const em
     *out = nullptr;
     EMT_REQUIRE(net && L_mut && opts, EMT_ERR_INVALID, "null network, mutual inductances or options");
     std::unique_ptr<emt_sim> h(new emt_sim);
-    h->sim3.reset(new emt::Sim3(net, L_mut, opts, dt, as_stream(stream)));
+    const emt_hinv_opts o3 = three_phase_opts(*opts);
+    h->sim3.reset(new emt::Sim3(net, L_mut, &o3, dt, as_stream(stream)));
     *out = h.release();
   });
 }

@@ -296,27 +296,30 @@ __device__ void boundary_sweep(const DStore& st, const CtaMapD& cm, const CutRow
   for (int d = st.max_depth - 1; d >= 0; --d) {
     const int i0 = cr.item_lvl[d], i1 = cr.item_lvl[d + 1];
     for (int it = i0 + tid; it < i1; it += kFusedThreads) {
-      const int pos = cr.item_pos[it];
-      // value of the child's full result at pos: leaf value minus the corrections of every
-      // internal ancestor strictly below depth d on pos's path (already in sm_s)
-      A acc;
-      acc.add(sm_ycut[cr.item_crow[it]]);
-      int q = st.parent[st.leaf_node[st.pos_leaf[pos]]];
-      while (q >= 0 && st.depth[q] > d) {
-        const int kq = st.node_k[q];
-        const int half = pos < st.hi[st.left[q]] ? 0 : kq;
-        const T* Fi = F + st.node_foff[q] + (int64_t)(pos - st.lo[q]) * st.node_kld[q];
-        const typename A::X* sq = sm_s + st.node_soff[q] + half;
-        for (int e = 0; e < kq; ++e) acc.fma(Fi[e], neg(sq[e]));
-        q = st.parent[q];
-      }
       const int cut = cr.item_cut[it];
-      typename A::X val = acc.getx();
-      if (cut >= 0) {   // a side: t = -g_e * value
-        A m;
-        m.fma(reinterpret_cast<const T*>(cut_gx)[cut], val);
-        val = m.getx();
+      // a side of a block column: the W vertices cut_a .. cut_a + W - 1, rows crow .. crow + W - 1
+      const int W = cut >= 0 ? st.cut_w : 1;
+      A m;
+      typename A::X val;
+      for (int w = 0; w < W; ++w) {
+        const int pos = cr.item_pos[it] + w;
+        // value of the child's full result at pos: leaf value minus the corrections of every
+        // internal ancestor strictly below depth d on pos's path (already in sm_s)
+        A acc;
+        acc.add(sm_ycut[cr.item_crow[it] + w]);
+        int q = st.parent[st.leaf_node[st.pos_leaf[pos]]];
+        while (q >= 0 && st.depth[q] > d) {
+          const int kq = st.node_k[q];
+          const int half = pos < st.hi[st.left[q]] ? 0 : kq;
+          const T* Fi = F + st.node_foff[q] + (int64_t)(pos - st.lo[q]) * st.node_kld[q];
+          const typename A::X* sq = sm_s + st.node_soff[q] + half;
+          for (int e = 0; e < kq; ++e) acc.fma(Fi[e], neg(sq[e]));
+          q = st.parent[q];
+        }
+        val = acc.getx();
+        if (cut >= 0) m.fma(reinterpret_cast<const T*>(cut_gx)[(int64_t)cut * W + w], val);   // t = -g * value
       }
+      if (cut >= 0) val = m.getx();
       sm_t[cr.item_sidx[it]] = val;
     }
     __syncthreads();

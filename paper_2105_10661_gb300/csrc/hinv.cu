@@ -152,7 +152,8 @@ __global__ void k_zero_factor(DStore st, const int* nodes) {
 }
 
 // Leaf stage of [P; Q] = blkdiag(Ginv_l, Ginv_r)[h_l; h_r]: column e of h_l is -g_e e_a, so its
-// leaf-stage image is -g_e times column a of the leaf inverse holding a (rows of that leaf only).
+// leaf-stage image is -g_e times column a of the leaf inverse holding a (rows of that leaf only);
+// a block column sums its W entries (the W vertices of one group share a leaf).
 __global__ void k_factor_init(DStore st, const int* nodes) {
   const int p = nodes[blockIdx.x];
   const int e = blockIdx.y;
@@ -161,7 +162,7 @@ __global__ void k_factor_init(DStore st, const int* nodes) {
   const int side = blockIdx.z;
   const int c0 = st.cut_ptr[p];
   const int pos = side == 0 ? st.cut_a[c0 + e] : st.cut_b[c0 + e];
-  const double coef = side == 0 ? -st.cut_g[c0 + e] : 1.0;
+  const int W = side == 0 ? st.cut_w : 1;
   const int jl = st.pos_leaf[pos];
   const int ln = st.leaf_node[jl];
   const int llo = st.lo[ln], b = st.hi[ln] - llo, ld = st.leaf_ld[jl];
@@ -169,8 +170,16 @@ __global__ void k_factor_init(DStore st, const int* nodes) {
   double* F = st.F64 + st.node_foff[p];
   const int kld = st.node_kld[p];
   const int plo = st.lo[p];
-  for (int r = threadIdx.x; r < b; r += blockDim.x)
-    F[(int64_t)(llo - plo + r) * kld + e] = coef * Lrow[r];
+  for (int r = threadIdx.x; r < b; r += blockDim.x) {
+    double v;
+    if (side == 0) {
+      v = 0.0;
+      for (int w = 0; w < W; ++w) v += -st.cut_g[(int64_t)(c0 + e) * W + w] * Lrow[(int64_t)w * ld + r];
+    } else {
+      v = Lrow[r];
+    }
+    F[(int64_t)(llo - plo + r) * kld + e] = v;
+  }
 }
 
 struct Panel {
@@ -214,8 +223,14 @@ __global__ void k_level_sweep(DStore st, int modeB, const int* flag, int d, int 
   for (int t = threadIdx.x; t < m2 * nc; t += blockDim.x) {
     const int r = t / nc, c = t % nc;
     double v;
-    if (r < kq) v = -st.cut_g[cp + r] * pn.ptr[(int64_t)(st.cut_a[cp + r] - pn.lo) * pn.ld + c0 + c];
-    else v = pn.ptr[(int64_t)(st.cut_b[cp + r - kq] - pn.lo) * pn.ld + c0 + c];
+    if (r < kq) {
+      const int W = st.cut_w;
+      const double* row = pn.ptr + (int64_t)(st.cut_a[cp + r] - pn.lo) * pn.ld + c0 + c;
+      v = 0.0;
+      for (int w = 0; w < W; ++w) v += -st.cut_g[(int64_t)(cp + r) * W + w] * row[(int64_t)w * pn.ld];
+    } else {
+      v = pn.ptr[(int64_t)(st.cut_b[cp + r - kq] - pn.lo) * pn.ld + c0 + c];
+    }
     tsh[r * kPanelCols + c] = v;
   }
   __syncthreads();
@@ -304,8 +319,11 @@ __global__ void k_core(DStore st, const int* nodes, int mode, double* ws, int* w
   for (int t = threadIdx.x; t < m2 * m2; t += blockDim.x) {
     const int r = t / m2, c = t % m2;
     double v = 0.0;
-    if (r < k && c < k) v = -st.cut_g[cp + r] * F[(int64_t)(st.cut_a[cp + r] - plo) * kld + c];
-    else if (r >= k && c >= k) v = F[(int64_t)(st.cut_b[cp + r - k] - plo) * kld + (c - k)];
+    if (r < k && c < k) {
+      const int W = st.cut_w;
+      for (int w = 0; w < W; ++w)
+        v += -st.cut_g[(int64_t)(cp + r) * W + w] * F[(int64_t)(st.cut_a[cp + r] + w - plo) * kld + c];
+    } else if (r >= k && c >= k) v = F[(int64_t)(st.cut_b[cp + r - k] - plo) * kld + (c - k)];
     else if (c == r + k || r == c + k) v = 1.0;
     A[t] = v;
   }
@@ -412,7 +430,9 @@ __global__ void k_mod_z(DStore st, ModItem it, double* __restrict__ z, double* _
   for (int e = threadIdx.x; e < m2; e += blockDim.x) {
     double v = 0.0;
     if (e < k) {
-      if (it.zl >= 0) v = -st.cut_g[cp + e] * z[it.zl + st.cut_a[cp + e] - llo];
+      if (it.zl >= 0)
+        for (int w = 0; w < st.cut_w; ++w)
+          v += -st.cut_g[(int64_t)(cp + e) * st.cut_w + w] * z[it.zl + st.cut_a[cp + e] + w - llo];
     } else {
       if (it.zr >= 0) v = z[it.zr + st.cut_b[cp + e - k] - rlo];
     }
@@ -491,7 +511,9 @@ __global__ void k_mod_factor(DStore st, ModItem it, const double* __restrict__ z
   for (int e = threadIdx.x; e < 2 * k; e += blockDim.x) {
     double v = 0.0;
     if (e < k) {
-      if (it.zl >= 0) v = -st.cut_g[cp + e] * z[it.zl + st.cut_a[cp + e] - llo];
+      if (it.zl >= 0)
+        for (int w = 0; w < st.cut_w; ++w)
+          v += -st.cut_g[(int64_t)(cp + e) * st.cut_w + w] * z[it.zl + st.cut_a[cp + e] + w - llo];
     } else {
       if (it.zr >= 0) v = z[it.zr + st.cut_b[cp + e - k] - rlo];
     }
@@ -509,8 +531,14 @@ __global__ void k_mod_factor(DStore st, ModItem it, const double* __restrict__ z
     if (i < split) {
       if (it.zl < 0) continue;
       const double xi = z[it.zl + i];
-      if (e == ec) Fi[e] = -g_new * xi / dv[it.dl];
-      else Fi[e] -= fl * xi * w[e];
+      if (e == ec) {
+        // h_l' = h_l - delta e_a e_ec^T: with Ginv_l' = Ginv_l - (delta/d_l) x x^T the column becomes
+        // P e_ec - (delta/d_l) x (w_ec + 1); a one-entry column (cut_w 1) is set directly
+        if (st.cut_w == 1) Fi[e] = -g_new * xi / dv[it.dl];
+        else Fi[e] -= fl * xi * (w[e] + 1.0);
+      } else {
+        Fi[e] -= fl * xi * w[e];
+      }
     } else {
       if (it.zr < 0) continue;
       const double xi = z[it.zr + i - split];
@@ -565,7 +593,9 @@ Store::Store(const emt_graph* g, const emt_hinv_opts* o, cudaStream_t s) {
   g_from.assign(g->from, g->from + g->n_branch);
   g_to.assign(g->to, g->to + g->n_branch);
   g_val.assign(g->g, g->g + g->n_branch);
-  tree = build_tree(n, g->n_branch, g->from, g->to, o->levels, o->d_th);
+  EMT_REQUIRE(o->nodes_per_bus >= 0, EMT_ERR_INVALID, "nodes_per_bus must be >= 0");
+  tree = o->nodes_per_bus >= 2 ? build_block_tree(n, g->n_branch, g->from, g->to, o->nodes_per_bus, o->levels, o->d_th)
+                               : build_tree(n, g->n_branch, g->from, g->to, o->levels, o->d_th);
   build_csr();
   EMT_CUDA(cudaGetDevice(&device));   // first device call: every host-side check has passed
   setup_layout(s);
@@ -659,10 +689,30 @@ void Store::setup_layout(cudaStream_t s) {
   F_elems = foff;
   C_elems = coff;
   s_total = soff;
-  cut_g_h.resize(t.cut_e.size());
-  for (size_t c = 0; c < t.cut_e.size(); ++c) cut_g_h[c] = g_val[t.cut_e[c]];
+  if (t.cut_w == 1) {
+    cut_g_h.resize(t.cut_e.size());
+    for (size_t c = 0; c < t.cut_e.size(); ++c) cut_g_h[c] = g_val[t.cut_e[c]];
+  } else {
+    // block cuts: entry (c, w) is -G[cut_a + w, cut_b], the conductance of the branches joining
+    // the two vertices (each joined pair is cut at exactly one tree node, its LCA)
+    const int W = t.cut_w;
+    cut_g_h.assign(t.cut_b.size() * W, 0.0);
+    std::map<std::pair<int, int>, int64_t> at;
+    for (size_t c = 0; c < t.cut_b.size(); ++c)
+      for (int w = 0; w < W; ++w) at[{t.cut_a[c] + w, t.cut_b[c]}] = (int64_t)c * W + w;
+    for (size_t e = 0; e < g_from.size(); ++e) {
+      if (g_to[e] < 0) continue;
+      const int x = t.pos[g_from[e]], y = t.pos[g_to[e]];
+      auto it = at.find({x, y});
+      if (it == at.end()) it = at.find({y, x});
+      if (it != at.end()) cut_g_h[it->second] += g_val[e];
+    }
+  }
   // distinct cut endpoints for the fused sweep
   {
+    // block cuts (cut_w = W > 1): a group's W positions (aligned to W) get W consecutive rows, so
+    // the row of cut_a + w is the row of cut_a plus w
+    const int W = t.cut_w;
     std::map<int, int> crow;
     CutRows cr;
     for (int d = t.max_depth; d >= 0; --d)
@@ -671,15 +721,17 @@ void Store::setup_layout(cudaStream_t s) {
         for (int side = 0; side < 2; ++side)
           for (int e = 0; e < k; ++e) {
             const int pos_ = side == 0 ? t.cut_a[t.cut_ptr[p] + e] : t.cut_b[t.cut_ptr[p] + e];
-            auto it = crow.find(pos_);
+            const int g0 = pos_ - pos_ % W;
+            auto it = crow.find(g0);
             int ci;
             if (it == crow.end()) {
               ci = (int)cr.crow_pos.size();
-              crow[pos_] = ci;
-              cr.crow_pos.push_back(pos_);
+              crow[g0] = ci;
+              for (int w = 0; w < W; ++w) cr.crow_pos.push_back(g0 + w);
             } else {
               ci = it->second;
             }
+            ci += pos_ - g0;
             cr.item_node.push_back(p);
             cr.item_pos.push_back(pos_);
             cr.item_crow.push_back(ci);
@@ -776,6 +828,7 @@ DStore Store::view() const {
   v.cut_b = d_cut_b.p;
   v.cut_e = d_cut_e.p;
   v.cut_g = d_cut_g.p;
+  v.cut_w = tree.cut_w;
   v.L64 = L64.p;
   v.Lff = Lff.p;
   v.L32 = L32.p;
@@ -1007,6 +1060,25 @@ PathInfo find_paths(const Tree& t, int leaf_a_node, int leaf_b_node) {
 }
 }  // namespace
 
+// Index into cut_g_h of the coefficient a change between positions pa and pb moves, at tree node
+// c (their LCA): the column of the cut branch (one entry per column), or of a block column the
+// entry of the left-side vertex in the column of the right-side vertex; -1 if none.
+int Store::cut_entry(int c, int pa, int pb, int branch) const {
+  const Tree& t = tree;
+  const int W = t.cut_w;
+  if (W == 1) {
+    for (int i = t.cut_ptr[c]; i < t.cut_ptr[c + 1]; ++i)
+      if (t.cut_e[i] == branch) return i;
+    return -1;
+  }
+  const int l = t.left[c];
+  const bool a_left = t.lo[l] <= pa && pa < t.hi[l];
+  const int x = a_left ? pa : pb, y = a_left ? pb : pa;
+  for (int i = t.cut_ptr[c]; i < t.cut_ptr[c + 1]; ++i)
+    if (t.cut_b[i] == y && x >= t.cut_a[i] && x < t.cut_a[i] + W) return i * W + (x - t.cut_a[i]);
+  return -1;
+}
+
 void Store::modify_exact(int pa, int pb, int branch, double delta, cudaStream_t s) {
   const Tree& t = tree;
   const int la = leaf_nodes_h[leaf_index_of_pos(*this, pa)];
@@ -1016,14 +1088,10 @@ void Store::modify_exact(int pa, int pb, int branch, double delta, cudaStream_t 
   int ec = -1, ec_global = -1;
   double g_new = 0.0;
   if (pb >= 0 && la != lb) {
-    const int c = pi.lca;
-    for (int i = t.cut_ptr[c]; i < t.cut_ptr[c + 1]; ++i)
-      if (t.cut_e[i] == branch) {
-        ec = i - t.cut_ptr[c];
-        ec_global = i;
-        break;
-      }
-    EMT_REQUIRE(ec >= 0, EMT_ERR_INVALID, "modified branch is not in the cut list of its LCA");
+    const int i = cut_entry(pi.lca, pa, pb, branch);
+    EMT_REQUIRE(i >= 0, EMT_ERR_INVALID, "modified branch is not in the cut list of its LCA");
+    ec = i / t.cut_w - t.cut_ptr[pi.lca];
+    ec_global = i;
     g_new = cut_g_h[ec_global] + delta;
   }
   // build items bottom-up with z slots
@@ -1100,13 +1168,10 @@ void Store::modify_paper(int pa, int pb, int branch, double delta, cudaStream_t 
   PathInfo pi = find_paths(t, leaf_nodes_h[ja], leaf_nodes_h[jb]);
   update_graph(t.perm[pa], pb >= 0 ? t.perm[pb] : -1, branch, delta, s);
   if (pb >= 0 && ja != jb) {
-    const int c = pi.lca;
-    for (int i = t.cut_ptr[c]; i < t.cut_ptr[c + 1]; ++i)
-      if (t.cut_e[i] == branch) {
-        cut_g_h[i] += delta;
-        k_set_cut_g<<<1, 1, 0, s>>>(view(), i, cut_g_h[i]);
-        break;
-      }
+    const int i = cut_entry(pi.lca, pa, pb, branch);
+    EMT_REQUIRE(i >= 0, EMT_ERR_INVALID, "modified branch is not in the cut list of its LCA");
+    cut_g_h[i] += delta;
+    k_set_cut_g<<<1, 1, 0, s>>>(view(), i, cut_g_h[i]);
   }
   std::vector<int> leaves{ja};
   if (jb != ja) leaves.push_back(jb);

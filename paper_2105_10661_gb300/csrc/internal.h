@@ -41,10 +41,18 @@ struct Tree {
   std::vector<int32_t> lo, hi, parent, left, right, depth;
   std::vector<int32_t> leaves;                           // node ids, left to right
   std::vector<int32_t> cut_ptr, cut_a, cut_b, cut_e;     // cut endpoints as positions
+  // cut_w = 1: one column per cut branch (h_l = -g e_a). cut_w = B > 1 (block cuts): one column
+  // per (left group, right vertex) of joined groups of B vertices; cut_a is the group's first
+  // position, its B vertices sit at cut_a .. cut_a + B - 1, cut_e is -1
+  int cut_w = 1;
   int n_node() const { return (int)lo.size(); }
 };
 Tree build_tree(int n_bus, int n_branch, const int32_t* from, const int32_t* to, int levels,
                 int d_th);
+// Partition by groups of B consecutive vertices (the three nodes of a three-phase bus) with block
+// cuts; d_th counts vertices.
+Tree build_block_tree(int n_vertex, int n_branch, const int32_t* from, const int32_t* to, int B, int levels,
+                      int d_th);
 
 // ---------------------------------------------------------------- device buffers
 template <typename T>

@@ -857,6 +857,8 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   check_network_arrays(net);
   EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
   EMT_REQUIRE(R_ >= 2 && R_ <= 65536, EMT_ERR_INVALID, "nrhs out of range");
+  EMT_REQUIRE(opts->nodes_per_bus <= 1, EMT_ERR_UNSUPPORTED,
+              "single-phase simulations partition buses one by one (nodes_per_bus 0 or 1)");
   n = net->n_bus;
   R = R_;
   dt = dt_;

@@ -386,6 +386,8 @@ Sim::Sim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int nrhs
   check_network_arrays(net);
   EMT_REQUIRE(dt_ > 0 && std::isfinite(dt_), EMT_ERR_INVALID, "dt must be > 0");
   EMT_REQUIRE(nrhs_ == 1, EMT_ERR_UNSUPPORTED, "this build steps one column per simulation");
+  EMT_REQUIRE(opts->nodes_per_bus <= 1, EMT_ERR_UNSUPPORTED,
+              "single-phase simulations partition buses one by one (nodes_per_bus 0 or 1)");
   (void)src_scale;
   (void)load_scale;
   n = net->n_bus;

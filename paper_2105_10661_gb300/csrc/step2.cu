@@ -66,7 +66,17 @@ struct TT<EMT_PREC_FP32> {
 };
 
 // ------------------------------------------------------------------ image refresh (after build/modify)
-// -g per cut and the factor rows every sweep item needs, gathered from the store.
+template <int PREC>
+__device__ __forceinline__ typename TT<PREC>::T img_value(double g) {
+  if constexpr (PREC == EMT_PREC_FF64) return make_float2((float)g, (float)(g - (double)(float)g));
+  else if constexpr (PREC == EMT_PREC_FP32) return (float)g;
+  else return g;
+}
+
+// -g per cut entry and the factor rows every sweep item needs, gathered from the store. seg_src
+// holds (source element, coefficient base, row stride) per segment: base -1 copies one factor row;
+// base >= 0 (a side of a block column) writes sum over w of -g[base + w] times the rows of the
+// column's W consecutive positions (FP64 sums of the FP64 factor rows).
 template <int PREC>
 __global__ void k_img_refresh(DStore st, unsigned char* img, int off_g, int n_cut, int off_r,
                               const int* __restrict__ seg_src, const int* __restrict__ seg_dst,
@@ -77,15 +87,19 @@ __global__ void k_img_refresh(DStore st, unsigned char* img, int off_g, int n_cu
   const T* F = Elem<PREC>::F(st);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  for (int c = tid; c < n_cut; c += nth) {
-    const double g = -st.cut_g[c];
-    if constexpr (PREC == EMT_PREC_FF64) G[c] = make_float2((float)g, (float)(g - (double)(float)g));
-    else if constexpr (PREC == EMT_PREC_FP32) G[c] = (float)g;
-    else G[c] = g;
-  }
+  for (int c = tid; c < n_cut; c += nth) G[c] = img_value<PREC>(-st.cut_g[c]);
   for (int sgi = tid; sgi < n_seg; sgi += nth) {
-    const int src = seg_src[sgi], dst = seg_dst[sgi], len = seg_len[sgi];
-    for (int e = 0; e < len; ++e) R[dst + e] = F[src + e];
+    const int src = seg_src[3 * sgi], base = seg_src[3 * sgi + 1], ld = seg_src[3 * sgi + 2];
+    const int dst = seg_dst[sgi], len = seg_len[sgi];
+    if (base < 0) {
+      for (int e = 0; e < len; ++e) R[dst + e] = F[src + e];
+    } else {
+      for (int e = 0; e < len; ++e) {
+        double v = 0.0;
+        for (int w = 0; w < st.cut_w; ++w) v += -st.cut_g[base + w] * st.F64[src + (int64_t)w * ld + e];
+        R[dst + e] = img_value<PREC>(v);
+      }
+    }
   }
 }
 
@@ -445,6 +459,7 @@ void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader&
   Hh.max_depth = t.max_depth;
   Hh.n_leaf = st.n_leaf;
   Hh.n_cut = (int)st.cut_g_h.size();
+  Hh.cut_w = t.cut_w;
   Hh.off_crow = (int)ints.size();
   for (int k = 0; k < Hh.n_crow; ++k) {
     const int ps = cr.crow_pos[k];
@@ -502,6 +517,8 @@ void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader&
     rec[3] = r_elems;
     rec[4] = (int)segs.size() / 2;
     int nseg = 0;
+    // a side of a block column (cut_w > 1) gets its W factor rows combined with the coefficients
+    const int comb = (t.cut_w > 1 && rec[2] >= 0) ? rec[2] * t.cut_w : -1;
     for (int a = t.parent[st.leaf_nodes_h[leaf_index_of_pos(st, ps)]]; a >= 0 && t.depth[a] > d; a = t.parent[a]) {
       const int ka = st.node_k_h[a];
       if (ka == 0) continue;
@@ -509,6 +526,8 @@ void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader&
       segs.push_back(st.node_soff_h[a] + half);
       segs.push_back(ka);
       seg_src_h.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * st.node_kld_h[a]));
+      seg_src_h.push_back(comb);
+      seg_src_h.push_back(st.node_kld_h[a]);
       seg_dst_h.push_back(r_elems);
       seg_len_h.push_back(ka);
       r_elems += ka;
@@ -572,7 +591,7 @@ void build_sweep_image(const Store& st, const FusedPlan* p, int prec, ImgHeader&
   seg_src.upload(seg_src_h.empty() ? std::vector<int>{0} : seg_src_h, s);
   seg_dst.upload(seg_dst_h.empty() ? std::vector<int>{0} : seg_dst_h, s);
   seg_len.upload(seg_len_h.empty() ? std::vector<int>{0} : seg_len_h, s);
-  n_seg = (int)seg_src_h.size();
+  n_seg = (int)seg_dst_h.size();
   refresh_sweep_image(st, prec, hdr, img, seg_src, seg_dst, seg_len, n_seg, s);
 }
 

@@ -52,6 +52,7 @@ struct ImgHeader {
   int off_g_bytes;   // byte offset of -g per cut (T)
   int off_r_bytes;   // byte offset of the cut-row factor segments (T)
   int img_bytes;     // bytes of the image (without cores)
+  int cut_w;         // left entries per cut column (block cuts: rows crow .. crow + cut_w - 1)
 };
 
 // Per-CTA copy list for its own factor rows: up to kMaxAnc ancestors.
@@ -131,8 +132,15 @@ __device__ __forceinline__ void sweep_levels(const unsigned char* img, const uns
       const int it = base + grp;
       A a;
       const int* rec = item + 6 * (it < i1 ? it : i0);
+      const int W = H->cut_w;
       if (it < i1) {
-        if (gl == 0) a.add(ycut[rec[0]]);
+        // a side of a block column: its rows are pre-combined with the coefficients in the image
+        if (gl == 0) {
+          if (W > 1 && rec[2] >= 0)
+            for (int w = 0; w < W; ++w) a.fma(Gn[rec[2] * W + w], ycut[rec[0] + w]);
+          else
+            a.add(ycut[rec[0]]);
+        }
         const T* rv = R + rec[3];
         for (int sg = rec[4]; sg < rec[4] + rec[5]; ++sg) {
           const int si = seg[2 * sg], k = seg[2 * sg + 1];
@@ -149,7 +157,7 @@ __device__ __forceinline__ void sweep_levels(const unsigned char* img, const uns
         val = tt.getx();
       }
       if (it < i1 && gl == 0) {
-        if (rec[2] >= 0) {
+        if (rec[2] >= 0 && W == 1) {
           A m;
           m.fma(Gn[rec[2]], val);
           val = m.getx();

@@ -22,6 +22,7 @@ namespace emt {
 
 struct DStore {
   int n, n_node, n_leaf, max_depth, kmax;
+  int cut_w;               // left entries per cut column (1, or B for block cuts: cut_a .. cut_a + B - 1)
   const int* lo;
   const int* hi;
   const int* parent;
@@ -46,7 +47,7 @@ struct DStore {
   const int* cut_a;
   const int* cut_b;
   const int* cut_e;
-  double* cut_g;
+  double* cut_g;           // [n_cut][cut_w]: h_l[cut_a + w, c] = -cut_g[c cut_w + w]
   double* L64;
   float2* Lff;
   float* L32;
@@ -78,6 +79,7 @@ class Store {
   // Enqueue the modification without synchronising; a singular change raises the device
   // status word and leaves the store unchanged. Returns false if the request is invalid.
   void modify_async(int bus_a, int bus_b, double delta, cudaStream_t s);
+  int cut_entry(int c, int pa, int pb, int branch) const;
   void pack(cudaStream_t s);                       // refresh FF64 / FP32 copies
   int device_status(cudaStream_t s);               // sync + read status word
   void clear_status(cudaStream_t s);

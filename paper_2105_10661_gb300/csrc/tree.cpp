@@ -305,4 +305,82 @@ Tree build_tree(int n_bus, int n_branch, const int32_t* from, const int32_t* to,
   return t;
 }
 
+// Sec. III-B bisects buses; a three-phase bus has three nodes (Sec. III-A, after Eq. 3). The group
+// graph has one edge per distinct pair of groups joined by a vertex branch, listed in ascending
+// (min, max) order; its tree is expanded group by group (vertex B g + w at B pos(g) + w). Each
+// tree node's cut columns factor the off-diagonal block of Eq. 3 exactly, H = G_lr = h_l h_r^T:
+// one column per (left group A, right vertex y) of joined groups, h_r = e_y, h_l holding G[x, y]
+// at A's B vertices, sorted by (position of A, position of y).
+Tree build_block_tree(int n_vertex, int n_branch, const int32_t* from, const int32_t* to, int B, int levels,
+                      int d_th) {
+  EMT_REQUIRE(B >= 2 && n_vertex >= B && n_vertex % B == 0, EMT_ERR_INVALID,
+              "block partition: the vertex count must be a positive multiple of nodes_per_bus");
+  const int ng = n_vertex / B;
+  std::vector<std::pair<int, int>> pairs;
+  for (int e = 0; e < n_branch; ++e) {
+    const int a = from[e], b = to[e];
+    EMT_REQUIRE(a >= 0 && a < n_vertex && b >= -1 && b < n_vertex, EMT_ERR_INVALID, "branch endpoint out of range");
+    if (b < 0 || a / B == b / B) continue;
+    pairs.emplace_back(std::min(a / B, b / B), std::max(a / B, b / B));
+  }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  std::vector<int32_t> gf(pairs.size()), gt(pairs.size());
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    gf[i] = pairs[i].first;
+    gt[i] = pairs[i].second;
+  }
+  const Tree tg = build_tree(ng, (int)pairs.size(), gf.data(), gt.data(), levels, levels > 0 ? 0 : d_th / B);
+  Tree t;
+  t.n_bus = n_vertex;
+  t.max_depth = tg.max_depth;
+  t.parent = tg.parent;
+  t.left = tg.left;
+  t.right = tg.right;
+  t.depth = tg.depth;
+  t.leaves = tg.leaves;
+  t.cut_w = B;
+  t.perm.resize(n_vertex);
+  t.pos.resize(n_vertex);
+  for (int i = 0; i < ng; ++i)
+    for (int w = 0; w < B; ++w) t.perm[B * i + w] = B * tg.perm[i] + w;
+  for (int i = 0; i < n_vertex; ++i) t.pos[t.perm[i]] = i;
+  const int nn = tg.n_node();
+  t.lo.resize(nn);
+  t.hi.resize(nn);
+  for (int p = 0; p < nn; ++p) {
+    t.lo[p] = B * tg.lo[p];
+    t.hi[p] = B * tg.hi[p];
+  }
+  t.cut_ptr.push_back(0);
+  for (int p = 0; p < nn; ++p) {
+    if (tg.left[p] >= 0) {
+      const int l = tg.left[p], r = tg.right[p];
+      std::vector<std::pair<int, int>> cols;
+      for (auto& pr : pairs) {
+        const int pa = tg.pos[pr.first], pb = tg.pos[pr.second];
+        int A, Bg;
+        if (tg.lo[l] <= pa && pa < tg.hi[l] && tg.lo[r] <= pb && pb < tg.hi[r]) {
+          A = pa;
+          Bg = pb;
+        } else if (tg.lo[l] <= pb && pb < tg.hi[l] && tg.lo[r] <= pa && pa < tg.hi[r]) {
+          A = pb;
+          Bg = pa;
+        } else {
+          continue;
+        }
+        for (int q = 0; q < B; ++q) cols.emplace_back(B * A, B * Bg + q);
+      }
+      std::sort(cols.begin(), cols.end());
+      for (auto& c : cols) {
+        t.cut_a.push_back(c.first);
+        t.cut_b.push_back(c.second);
+        t.cut_e.push_back(-1);
+      }
+    }
+    t.cut_ptr.push_back((int)t.cut_a.size());
+  }
+  return t;
+}
+
 }  // namespace emt

@@ -535,35 +535,53 @@ def _three_phase(levels=3):
     return net, gr, ocm.assemble_dense(gr)
 
 
+@pytest.mark.parametrize("npb", [1, 3])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_three_phase_store_matches_dense_solve(L, prec):
-    # 358 buses, 1,074 nodes: mutual couplings enter as negative node branches
+def test_three_phase_store_matches_dense_solve(L, prec, npb):
+    # 358 buses, 1,074 nodes: mutual couplings enter as negative node branches; npb 3 partitions
+    # by bus with block cuts (the default), npb 1 node by node
     net, gr, G = _three_phase()
-    h = L.emt_build_hinv_from_network3(net, DT, levels=3, precision=prec)
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, precision=prec, nodes_per_bus=npb)
     _PREC[id(h)] = prec
     X = np.random.default_rng(21).standard_normal((gr["n_bus"], 3))
     assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
 
 
-def test_three_phase_paper_store_matches_algorithm1(L):
+@pytest.mark.parametrize("npb", [1, 3])
+def test_three_phase_paper_store_matches_algorithm1(L, npb):
+    # Algorithm 1's store is an approximation that depends on the tree and its cut columns: the
+    # node-level tree, or the bus-level tree with block cuts
     from oracle import partition as op
     net, gr, G = _three_phase()
     ser = gr["to"] >= 0
-    tree = op.build_tree(gr["n_bus"], gr["frm"][ser], gr["to"][ser], 3)
-    H = ohinv.HInv(G, tree, gr["g"][ser], ohinv.PAPER)
-    h = L.emt_build_hinv_from_network3(net, DT, levels=3, mode=1)
+    if npb == 1:
+        tree = op.build_tree(gr["n_bus"], gr["frm"][ser], gr["to"][ser], 3)
+        H = ohinv.HInv(G, tree, gr["g"][ser], ohinv.PAPER)
+    else:
+        tree = op.build_block_tree(gr["n_bus"], gr["frm"], gr["to"], 3, levels=3)
+        H = ohinv.HInv(G, tree, gr["g"], ohinv.PAPER)
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, mode=1, nodes_per_bus=npb)
     X = np.random.default_rng(22).standard_normal((gr["n_bus"], 2))
     assert rel_err(_apply(L, h, X), H.apply(X)) <= 1e-10
 
 
-def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L):
+@pytest.mark.parametrize("npb,cut_line", [(1, False), (3, False), (3, True)])
+def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L, npb, cut_line):
     # a three-phase line trip removes Y (x) (e_a - e_b)(e_a - e_b)^T: fifteen exact rank-1 updates,
     # negative (cross-phase) branches first so that every intermediate G stays positive definite;
-    # then a fault from one phase to ground
+    # then a fault from one phase to ground. cut_line: a coupled line cut at the root, whose nine
+    # phase-to-phase branches are the entries of one rank-3 block cut
     from oracle import companion as ocm
     net, gr, G = _three_phase()
-    h = L.emt_build_hinv_from_network3(net, DT, levels=3)
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, nodes_per_bus=npb)
     e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0)
+    if cut_line:
+        t = h.tree()
+        cut_buses = {(int(t["perm"][a]) // 3, int(t["perm"][b]) // 3)
+                     for a, b in zip(t["cut_a"][t["cut_ptr"][0]:t["cut_ptr"][1]], t["cut_b"][t["cut_ptr"][0]:t["cut_ptr"][1]])}
+        e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0 and net["L_mut"][k] > 0 and
+                 ((int(net["br_a"][k]), int(net["br_b"][k])) in cut_buses or
+                  (int(net["br_b"][k]), int(net["br_a"][k])) in cut_buses))
     a, b = int(net["br_a"][e]), int(net["br_b"][e])
     Y = ocm.coupled_rl_admittance(float(net["R"][e]), float(net["L"][e]), float(net["L_mut"][e]), DT)
     cross = [(3 * a + p, 3 * b + q, Y[p, q]) for p in range(3) for q in range(3) if p != q]
@@ -580,9 +598,50 @@ def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L):
     assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= 1e-10
 
 
+def test_block_cuts_keep_buses_together_and_shrink_the_cut(L):
+    # b buses per leaf become 3b nodes; a coupled line is one rank-3 cut instead of nine columns
+    net, gr, G = _three_phase()
+    hb = L.emt_build_hinv_from_network3(net, DT, levels=3)
+    hn = L.emt_build_hinv_from_network3(net, DT, levels=3, nodes_per_bus=1)
+    tb, tn = hb.tree(), hn.tree()
+    assert np.array_equal(tb["perm"] % 3, np.tile(np.arange(3), len(tb["perm"]) // 3))
+    assert np.all(tb["lo"] % 3 == 0) and np.all(tb["hi"] % 3 == 0)
+    assert 3 * len(tb["cut_b"]) <= len(tn["cut_b"]) * 2
+    X = np.random.default_rng(24).standard_normal((gr["n_bus"], 1))
+    ref = odense.DenseSolver(G).solve(X)
+    assert rel_err(_apply(L, hb, X), ref) <= 1e-10
+    v = torch.zeros(gr["n_bus"], dtype=torch.float64, device="cuda")
+    L.emt_apply_noalloc(hb, torch.tensor(X[:, 0], dtype=torch.float64, device="cuda"), v)
+    torch.cuda.synchronize()
+    assert rel_err(v.cpu().numpy(), ref[:, 0]) <= 1e-10
+
+
+@pytest.mark.parametrize("prec,kernels", [(0, 1), (1, 1), (1, 2)])
+def test_block_store_streaming_apply_matches_dense_solve(L, prec, kernels):
+    # the streaming kernels (three, or the single launch) asked for on a small three-phase store:
+    # the sweep matrix holds the block columns' factor rows combined with their coefficients
+    net, gr, G = _three_phase()
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, precision=prec)
+    _PREC[id(h)] = prec
+    assert L.emt_apply_tune(h, kernels) == 0   # planned by the first apply
+    X = np.random.default_rng(25).standard_normal((gr["n_bus"], 2))
+    ref = odense.DenseSolver(G).solve(X)
+    assert rel_err(_apply(L, h, X), ref) <= TOL[prec]
+    assert L.emt_apply_tune(h, kernels) == kernels
+    # after an exact update of a cut entry the refreshed image still matches
+    t = h.tree()
+    a = int(t["perm"][t["cut_a"][0] + 1])
+    b = int(t["perm"][t["cut_b"][0]])
+    g = float(G[a, b])
+    if g != 0.0:
+        L.emt_modify_branch(h, a, b, 0.5 * g)
+        G = omod.modified_G(G, a, b, 0.5 * g)
+        assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
+
+
 # ---------------------------------------------------------------- three-phase time stepping (NEXT-3)
-def _sim3_run(L, net, levels, steps, trips, prec, monitor=None, halves=True):
-    sim = L.emt_sim3_create(net, DT, levels=levels, precision=prec)
+def _sim3_run(L, net, levels, steps, trips, prec, monitor=None, halves=True, npb=0):
+    sim = L.emt_sim3_create(net, DT, levels=levels, precision=prec, nodes_per_bus=npb)
     nn = 3 * net["n_bus"]
     mon = np.arange(nn) if monitor is None else np.asarray(monitor)
     L.emt_sim_monitor(sim, mon)
@@ -597,15 +656,16 @@ def _sim3_run(L, net, levels, steps, trips, prec, monitor=None, halves=True):
     return sim, rec.cpu().numpy()
 
 
+@pytest.mark.parametrize("npb", [1, 3])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_three_phase_stepping_matches_oracle_with_a_coupled_line_trip(L, prec):
+def test_three_phase_stepping_matches_oracle_with_a_coupled_line_trip(L, prec, npb):
     # one tile in three phases with loads: coupled RL histories (3 x 3), RC branches per phase,
     # balanced sources and loads; the trip opens a coupled line at step 70 (15 exact node updates)
     from oracle import emt3 as oemt3
     net = netgen.three_phase(netgen.add_loads(netgen.tile(1_000_000), seed=3))
     e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0 and net["L_mut"][k] > 0)
     ref, state = oemt3.simulate3(net, DT, 140, [(70, oemt3.TRIP, e, 0.0)])
-    sim, got = _sim3_run(L, net, 2, 140, [(70, e)], prec)
+    sim, got = _sim3_run(L, net, 2, 140, [(70, e)], prec, npb=npb)
     assert rel_err(got, ref) <= 1e-10, rel_err(got, ref)
     final = L.emt_sim_read(sim, 0)
     assert np.array_equal(final, got[-1])

@@ -58,6 +58,31 @@ def test_partition_bit_exact_64_tiles(L):
         assert np.array_equal(got[k], np.asarray(ref[k])), k
 
 
+@pytest.mark.parametrize("which,levels,d_th", [("tile", 2, 0), ("tiles8", 3, 0), ("small40", 0, 24), ("tiles8", 0, 300)])
+def test_block_partition_bit_exact_with_oracle(L, which, levels, d_th):
+    # three nodes per bus: the partition bisects buses and cuts in rank-3 blocks
+    from oracle import companion as ocm
+    base = (netgen.tile(1_000_000) if which == "tile" else netgen.tiled(2, 4) if which == "tiles8"
+            else netgen.small_network(int(which[5:]), 77))
+    gr = ocm.three_phase_graph(netgen.three_phase(base), 50e-6)
+    got = L.emt_tree_build(gr["n_bus"], gr["frm"], gr["to"], levels=levels, d_th=d_th, nodes_per_bus=3)
+    ref = opart.build_block_tree(gr["n_bus"], gr["frm"], gr["to"], 3, levels=levels, d_th=d_th)
+    for k in KEYS:
+        if k == "cut_a":
+            a = np.asarray(ref["cut_a"]).reshape(-1, 3)
+            assert np.array_equal(a - a[:, :1], np.tile(np.arange(3), (len(a), 1)))
+            assert np.array_equal(got["cut_a"], a[:, 0])
+        else:
+            assert np.array_equal(got[k], np.asarray(ref[k])), k
+    assert len(got["cut_b"]) > 0
+
+
+def test_block_partition_rejects_a_vertex_count_off_the_group_size(L):
+    with pytest.raises(L.EmtError) as e:
+        L.emt_tree_build(7, [0, 3], [3, 6], levels=1, nodes_per_bus=3)
+    assert e.value.code == L.EMT_ERR_INVALID
+
+
 def test_partition_rejects_bad_input(L):
     with pytest.raises(L.EmtError) as e:
         L.emt_tree_build(4, [0, 1], [1, 7], levels=1)
