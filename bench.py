@@ -1219,7 +1219,8 @@ def dth_arm(args):
 # ---------------------------------------------------------------- config 7 (three-phase buses)
 def three_phase_arm(args):
     """Three nodes per bus with mutually coupled RL branches: single-vector apply, and a
-    three-phase line trip as exact rank-1 node updates against rebuilding the store."""
+    three-phase line trip as exact rank-1 node updates against rebuilding the store; the bus-level
+    partition with block cuts (the default) beside the node-level one."""
     import numpy as np
     import torch
     import netgen
@@ -1243,32 +1244,12 @@ def three_phase_arm(args):
         torch.cuda.synchronize()
         return out, (time.perf_counter() - t0) * 1e3
 
-    L.emt_build_hinv_from_network3(net, DT, levels=3)   # warm
-    h, build_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net, DT, levels=3))
-    v = torch.zeros(nn, dtype=torch.float64, device=dev)
-    for _ in range(args.warmup):
-        L.emt_apply(h, x, v, stream=stream)
-    clocks = Clocks(dev.index)
-    ts = []
-    for _ in range(max(args.steps, 10)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        L.emt_apply(h, x, v, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    clk = clocks.stop()
-    apply_ms = float(np.median(ts))
-    # accuracy against a dense solve of the oracle's G (CPU)
+    # reference solution of the oracle's G (CPU), also the timed CPU baseline
     gr = ocm.three_phase_graph(net, DT)
-    G = ocm.assemble_dense(gr)
+    G0 = ocm.assemble_dense(gr)
     t0 = time.perf_counter()
-    ref = odense.DenseSolver(G).solve(x.cpu().numpy())
+    ref = odense.DenseSolver(G0).solve(x.cpu().numpy())
     cpu_ms = (time.perf_counter() - t0) * 1e3
-    err = rel_err(v.cpu().numpy(), ref)
     # three-phase trip of the first RL branch: 15 exact rank-1 node updates, negative (cross-phase)
     # branches first so every intermediate G stays positive definite
     e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0)
@@ -1277,35 +1258,66 @@ def three_phase_arm(args):
     ups = ([(3 * a + p, 3 * b + q, Y[p, q]) for p in range(3) for q in range(3) if p != q]
            + [(3 * z + p, 3 * z + q, -Y[p, q]) for z in (a, b) for p in range(3) for q in range(p + 1, 3)]
            + [(3 * a + p, 3 * b + p, Y[p, p]) for p in range(3)])
-
-    v_before = v.cpu().numpy()
-
-    def trip():
-        for xx, yy, g in ups:
-            L.emt_modify_branch(h, xx, yy, -g, stream=stream)
-    _, trip_ms = sync_time(trip)
+    Gt = G0
+    for xx, yy, g in ups:
+        Gt = omod.modified_G(Gt, xx, yy, -g)
+    ref_trip = odense.DenseSolver(Gt).solve(x.cpu().numpy())
     keep = [k for k in range(len(net["br_a"])) if k != e]
     net_t = dict(net)
     for k in ("br_a", "br_b", "kind", "R", "L", "C", "L_mut"):
         net_t[k] = np.asarray(net[k])[keep]
-    _, rebuild_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net_t, DT, levels=3))
-    for xx, yy, g in ups:
-        G = omod.modified_G(G, xx, yy, -g)
-    L.emt_apply(h, x, v, stream=stream)
-    torch.cuda.synchronize()
-    err_trip = rel_err(v.cpu().numpy(), odense.DenseSolver(G).solve(x.cpu().numpy()))
-    change = rel_err(v.cpu().numpy(), v_before)
+
+    def measure(npb, clocks=None):
+        L.emt_build_hinv_from_network3(net, DT, levels=3, nodes_per_bus=npb)   # warm
+        h, build_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net, DT, levels=3, nodes_per_bus=npb))
+        v = torch.zeros(nn, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            L.emt_apply(h, x, v, stream=stream)
+        clk = Clocks(dev.index) if clocks else None
+        ts = []
+        t_end = time.perf_counter() + (0.8 if clocks else 0.0)   # long enough for clock samples
+        while len(ts) < max(args.steps, 10) or time.perf_counter() < t_end:
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.emt_apply(h, x, v, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        clk = clk.stop() if clk else None
+        v_before = v.cpu().numpy()
+        err = rel_err(v_before, ref)
+        cuts = int(len(h.tree()["cut_b"]))
+
+        def trip():
+            for xx, yy, g in ups:
+                L.emt_modify_branch(h, xx, yy, -g, stream=stream)
+        _, trip_ms = sync_time(trip)
+        _, rebuild_ms = sync_time(lambda: L.emt_build_hinv_from_network3(net_t, DT, levels=3, nodes_per_bus=npb))
+        L.emt_apply(h, x, v, stream=stream)
+        torch.cuda.synchronize()
+        return {"apply_ms": float(np.median(ts)), "applies_timed": len(ts), "build_ms": build_ms, "cut_columns": cuts,
+                "accuracy": {"apply": err, "after_three_phase_trip": rel_err(v.cpu().numpy(), ref_trip),
+                             "solution_change_by_trip": rel_err(v.cpu().numpy(), v_before)},
+                "three_phase_trip": {"node_updates": len(ups), "ms": trip_ms, "rebuild_ms": rebuild_ms,
+                                     "time_saved": 1.0 - trip_ms / rebuild_ms}}, clk
+
+    blk, clk = measure(3, clocks=True)
+    node, _ = measure(1)
+    apply_ms = blk["apply_ms"]
     return {
         "metric": "three-phase node solves per second (v = G^-1 i, one vector)", "value": nn / (apply_ms * 1e-3),
-        "unit": "node-solves/s", "n_gpus": 1, "steps": max(args.steps, 10), "warmup": args.warmup,
+        "unit": "node-solves/s", "n_gpus": 1, "steps": blk["applies_timed"], "warmup": args.warmup,
         "ms_per_step": apply_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "1432-bus 8-tile network in three phases (4,296 nodes, mutual inductance U[0.2, 0.4] "
                                "of self on every RL branch), 3-level hierarchy, EXACT FP64 store, L2 flushed before "
-                               "every apply", "nodes": nn},
-        "accuracy": {"apply": err, "after_three_phase_trip": err_trip, "solution_change_by_trip": change},
-        "build_ms": build_ms, "three_phase_trip": {"node_updates": len(ups), "ms": trip_ms, "rebuild_ms": rebuild_ms,
-                                                   "time_saved": 1.0 - trip_ms / rebuild_ms},
+                               "every apply", "nodes": nn,
+                   "partition": "by bus (three nodes kept together), one rank-3 block cut per joined bus pair"},
+        "accuracy": blk["accuracy"], "build_ms": blk["build_ms"], "three_phase_trip": blk["three_phase_trip"],
+        "partitions": {"block_cuts": blk, "node_level": node},
         "cpu_baseline": {"value": nn / (cpu_ms * 1e-3), "unit": "node-solves/s", "cores": os.cpu_count(),
                          "kind": "oracle", "sample": "dense Cholesky solve of the same G and vector (factorisation "
                                                      "included)"},
