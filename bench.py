@@ -735,14 +735,17 @@ def multi_arm(args, cfg: int):
 
 
 def inject_name(st):
-    if st["inject_columns_per_thread"] == 2:
-        return "k_mc_inject2 (histories + injection, float-float, two columns per thread)"
+    v = st["inject_variant"]
+    if v >= 2:
+        kb, mb = {2: (6, 2), 3: (3, 3), 4: (2, 4)}[v]
+        return (f"k_mc_inject2<{kb},{mb}> (histories + injection, float-float, two columns per thread, "
+                f"{kb} element ends per round trip, {mb} CTAs per SM)")
     return "k_mc_inject (histories + injection, float-float)"
 
 
 # DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu --set full
 # capture of the kernel as it stands (python bench.py --config 4 --profile 6, third launch)
-NCU_TRAFFIC = {("k_mc_inject2", 11456, 512): 212.828416e6 + 150.211584e6}
+NCU_TRAFFIC = {("k_mc_inject2<6,2>", 11456, 512): 212.828416e6 + 150.211584e6}
 
 
 def ncu_traffic(kernel, n, cols):

@@ -291,13 +291,23 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta);
  * a leaf-GEMM tile (0 = chosen from nrhs). Synchronises the device; takes effect on the next
  * emt_step. */
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels);
+/* Injection kernel of a multi-column simulation (the history update and right-hand side of Eq. 1,
+ * Sec. II): mode 0 chosen from nrhs (the default), 1 one column per thread, 2, 3, 4 two columns
+ * per thread with 6, 3 or 2 element ends per memory round trip and 2, 3 or 4 CTAs per SM (nrhs
+ * even; EMT_ERR_UNSUPPORTED otherwise; mode 0 takes 4 when nrhs is a multiple of 512, else 1);
+ * positions_per_cta 1, 2, 4 or 8 bus positions per CTA, 0 chosen from the sizes (enough CTAs for
+ * about sixteen per SM in mode 4, four otherwise). The two-column modes give the same
+ * results bit for bit. Single-column and three-phase simulations: EMT_ERR_UNSUPPORTED.
+ * Synchronises the device; takes effect on the next emt_step. */
+emt_status emt_sim_set_inject(emt_sim* s, int32_t mode, int32_t positions_per_cta);
 /* Autotuner: time each candidate on probe_steps steps of this simulation (after 8 untimed
  * steps), keep the fastest and remember it for every later simulation of the same shape in this
  * process (emt_sim_create applies it). Single-column simulations: cluster sizes 1..16 of
  * generation 4, rows per CTA in {4..48} of generations 3, 2 and 1; best_rpc / best_kernels
  * receive rows_per_cta and the generation. Multi-column simulations: FP32 CUDA-core products, and
  * tcgen05 products (kernels 2 and 3) with leaf-GEMM tiles 64, 128, 192 and 256 columns wide; then,
- * with those, the injection kernel with one or two columns per thread (even nrhs); best_rpc /
+ * with those, the injection kernel with one column per thread and its three two-column variants
+ * (even nrhs); best_rpc /
  * best_kernels receive the tile width and `kernels` of emt_sim_tune, emt_sim_stats the injection
  * choice. Three-phase simulations: EMT_ERR_UNSUPPORTED. Resets the simulation. Synchronises the
  * device. best_rpc / best_kernels may be NULL. */
@@ -312,7 +322,9 @@ emt_status emt_sim_reset(emt_sim* s, void* stream);
  * kernels, element incidences, distinct cut rows, boundary-vector length (sum 2k_q), kernels
  * launched by emt_step/emt_sim_reset since creation, series branches, elements, columns per thread
  * of the injection kernel of a several-column simulation (2 when the columns fill whole blocks of
- * pairs, else 1; 0 for single-column simulations). */
+ * pairs, else 1; 0 for single-column simulations), and its variant (1 one column per thread; 2, 3,
+ * 4 two columns per thread with 6, 3 or 2 element ends per memory round trip, 2, 3 or 4 CTAs per
+ * SM; 0 for single-column simulations). */
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
 /* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
  * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the

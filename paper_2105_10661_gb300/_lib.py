@@ -98,6 +98,7 @@ def _load():
         "emt_sim_bench_kernel": (C.c_int, [vp, C.c_int32, C.c_int32, vp]),
         "emt_apply_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "emt_sim_tune": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "emt_sim_set_inject": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "emt_sim_autotune": (C.c_int, [vp, C.c_int32, _i32p, _i32p, vp]),
         "emt_server_create": (C.c_int, [C.c_int32, C.c_uint64, C.POINTER(vp)]),
         "emt_server_add_network": (C.c_int, [vp, C.POINTER(EmtNetwork), C.POINTER(EmtHinvOpts), C.c_double, C.c_int32,
@@ -132,7 +133,7 @@ EXPORTED = ("emt_last_error", "emt_version", "emt_tree_build", "emt_tree_sizes",
             "emt_hinv_sync", "emt_apply_tune", "emt_hinv_destroy",
             "emt_sim_create", "emt_sim_schedule", "emt_sim_monitor", "emt_step", "emt_sim_read",
             "emt_sim_set_rows_per_cta", "emt_sim_destroy", "emt_sim_reset", "emt_sim_stats",
-            "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_autotune", "emt_server_create",
+            "emt_sim_bench_kernel", "emt_apply_noalloc", "emt_sim_tune", "emt_sim_set_inject", "emt_sim_autotune", "emt_server_create",
             "emt_server_add_network", "emt_server_submit", "emt_server_submit_network", "emt_server_run",
             "emt_server_result", "emt_server_stats",
             "emt_server_destroy", "emt_selftest_bounded_wait", "emt_build_hinv_from_network",
@@ -360,7 +361,7 @@ def emt_sim_reset(s: Sim, stream=None):
 
 
 STAT_KEYS = ("n_bus", "n_leaf", "leaf_elems", "factor_elems", "core_elems", "n_cta", "n_incidence", "n_cut_rows",
-             "s_total", "launches", "n_series", "n_elements", "inject_columns_per_thread")
+             "s_total", "launches", "n_series", "n_elements", "inject_columns_per_thread", "inject_variant")
 
 
 def emt_sim_stats(s: Sim):
@@ -375,6 +376,10 @@ def emt_sim_bench_kernel(s: Sim, which, reps, stream=None):
 
 def emt_sim_tune(s: Sim, rows_per_cta=0, kernels=2):
     _check(lib.emt_sim_tune(s.h, int(rows_per_cta), int(kernels)))
+
+
+def emt_sim_set_inject(s: Sim, mode=0, positions_per_cta=0):
+    _check(lib.emt_sim_set_inject(s.h, int(mode), int(positions_per_cta)))
 
 
 def emt_sim_autotune(s: Sim, probe_steps=256, stream=None):

@@ -349,6 +349,14 @@ emt_status emt_sim_set_rows_per_cta(emt_sim* s, int32_t rows_per_cta) {
   });
 }
 
+emt_status emt_sim_set_inject(emt_sim* s, int32_t mode, int32_t positions_per_cta) {
+  return guard([&] {
+    EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");
+    EMT_REQUIRE(s->msim, EMT_ERR_UNSUPPORTED, "only multi-column simulations have injection variants");
+    s->msim->set_inject(mode, positions_per_cta);
+  });
+}
+
 emt_status emt_sim_tune(emt_sim* s, int32_t rows_per_cta, int32_t kernels) {
   return guard([&] {
     EMT_REQUIRE(s && s->ok(), EMT_ERR_INVALID, "null simulation");

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
 // The same injection with two columns per thread (column stride even): the element-end record,
 // the 32-bit index arithmetic and the loop control of an incidence serve both columns, and the
 // pair of float-float values of a row is one 16-byte access. A thread whose second column lies
-// beyond the active ones computes it but stores only the first.
+// beyond the active ones computes it but stores only the first. KB element ends per memory round
+// trip; MINB CTAs per SM (the registers that allows: 6 ends with 2 CTAs, 3 with 3, 2 with 4).
 __device__ __forceinline__ void ld_pair(const float2* p, float2 (&o)[2]) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = make_float2(v.x, v.y);
@@ -189,7 +190,8 @@ __device__ __forceinline__ void st_pair(float2* p, const float2 (&o)[2], bool bo
   if (both) *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
   else p[0] = o[0];
 }
-__global__ void __launch_bounds__(ITH, 2) k_mc_inject2(MSimD m, int ipp, int s_in_chunk, int* status) {
+template <int KB, int MINB>
+__global__ void __launch_bounds__(ITH, MINB) k_mc_inject2(MSimD m, int ipp, int s_in_chunk, int* status) {
   extern __shared__ __align__(16) unsigned char ism[];
   MRec* srec = reinterpret_cast<MRec*>(ism);
   __shared__ int sptr[IPP_MAX + 1], tptr[IPP_MAX + 1];
@@ -223,9 +225,9 @@ __global__ void __launch_bounds__(ITH, 2) k_mc_inject2(MSimD m, int ipp, int s_i
     ld_pair(m.V + pos * R + c, vi);
     Acc2 hist[2] = {{0.f, 0.f}, {0.f, 0.f}}, inj[2] = {{0.f, 0.f}, {0.f, 0.f}};
     do {
-      float2 vo[IKB][2], ih[IKB][2], tc[ITB][2], ts[ITB][2];
+      float2 vo[KB][2], ih[KB][2], tc[ITB][2], ts[ITB][2];
 #pragma unroll
-      for (int q = 0; q < IKB; ++q) {
+      for (int q = 0; q < KB; ++q) {
         if (kb + q < k1) {
           const MRec& r = srec[kb + q];
           if (r.other >= 0) ld_pair(m.V + r.other * R + c, vo[q]);
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(ITH, 2) k_mc_inject2(MSimD m, int ipp, int s_i
         }
       }
 #pragma unroll
-      for (int q = 0; q < IKB; ++q) {
+      for (int q = 0; q < KB; ++q) {
         if (kb + q >= k1) break;
         const MRec& r = srec[kb + q];
         float2 ihn[2];
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(ITH, 2) k_mc_inject2(MSimD m, int ipp, int s_i
           inj[j].add_prod(ts[q][j], cw);
         }
       }
-      kb += IKB;
+      kb += KB;
       tb += ITB;
     } while (kb < k1 || tb < t1);
     float2 x[2];
@@ -955,7 +957,9 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
                 "too many element ends on 8 consecutive buses");
     if (inj_smem > 48 * 1024) {
       EMT_CUDA(cudaFuncSetAttribute(k_mc_inject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
-      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2<6, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2<3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
     }
 
     if (res_smem > 48 * 1024)
@@ -1345,29 +1349,40 @@ void MSim::bench_kernel(int which, int reps, cudaStream_t s) {
   EMT_CUDA(cudaGetLastError());
 }
 
-bool MSim::inject_pairs() const {
-  if (!inj_pairs || inj_mode == 1) return false;
-  return inj_mode == 2 || R_act % (2 * ITH) == 0;   // by default pairs only when they fill whole blocks
+bool MSim::inject_pairs() const { return inject_variant() >= 2; }
+
+// 1: one column per thread; 2, 3, 4: two columns per thread with 6, 3 or 2 element ends per round
+// trip (2, 3 or 4 CTAs per SM)
+int MSim::inject_variant() const {
+  if (!inj_pairs || inj_mode == 1) return 1;
+  if (inj_mode >= 2) return inj_mode;
+  // by default pairs only when they fill whole blocks, with 2 ends per round trip and 4 CTAs per
+  // SM (measured fastest on 11,456 buses x 512 columns: 94.5 us against 108.8 for 6 ends, 2 CTAs)
+  return R_act % (2 * ITH) == 0 ? 4 : 1;
 }
 
 void MSim::launch_inject(int s_in_chunk, cudaStream_t s) {
   const MSimD d = view();
-  if (inject_pairs()) {
-    const int ipp = positions_per_cta(2);
-    k_mc_inject2<<<dim3((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH)), ITH, inj_smem, s>>>(
-        d, ipp, s_in_chunk, store->d_status.p);
+  const int var = inject_variant();
+  if (var >= 2) {
+    // about 16 CTAs per SM over the launch (4 resident): the last wave stays short
+    const int ipp = inj_ipp > 0 ? inj_ipp : positions_per_cta(2, var == 4 ? 16 : 4);
+    const dim3 grid((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH));
+    if (var == 2) k_mc_inject2<6, 2><<<grid, ITH, inj_smem, s>>>(d, ipp, s_in_chunk, store->d_status.p);
+    else if (var == 3) k_mc_inject2<3, 3><<<grid, ITH, inj_smem, s>>>(d, ipp, s_in_chunk, store->d_status.p);
+    else k_mc_inject2<2, 4><<<grid, ITH, inj_smem, s>>>(d, ipp, s_in_chunk, store->d_status.p);
   } else {
-    const int ipp = positions_per_cta();
+    const int ipp = inj_ipp > 0 ? inj_ipp : positions_per_cta();
     k_mc_inject<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, inj_smem, s>>>(d, ipp, s_in_chunk,
                                                                                         store->d_status.p);
   }
 }
 
 // positions per CTA of the injection and residual kernels: enough CTAs for about four per SM
-int MSim::positions_per_cta(int cols_per_thread) const {
+int MSim::positions_per_cta(int cols_per_thread, int ctas_per_sm) const {
   const int64_t col_blocks = (R_act + cols_per_thread * ITH - 1) / (cols_per_thread * ITH);
   int ipp = IPP_MAX;
-  while (ipp > 1 && (int64_t)((n + ipp - 1) / ipp) * col_blocks < 4LL * n_sm) ipp /= 2;
+  while (ipp > 1 && (int64_t)((n + ipp - 1) / ipp) * col_blocks < (int64_t)ctas_per_sm * n_sm) ipp /= 2;
   return ipp;
 }
 
@@ -1495,18 +1510,21 @@ void MSim::set_gemm(int kind, int tn, cudaStream_t s) {
   EMT_CUDA(cudaStreamSynchronize(s));
 }
 
-void MSim::set_inject(int mode) {
-  EMT_REQUIRE(mode >= 0 && mode <= 2, EMT_ERR_INVALID, "injection mode must be 0, 1 or 2");
-  EMT_REQUIRE(mode != 2 || inj_pairs, EMT_ERR_UNSUPPORTED, "two columns per thread need an even column count");
+void MSim::set_inject(int mode, int ipp) {
+  EMT_REQUIRE(mode >= 0 && mode <= 4, EMT_ERR_INVALID, "injection mode must be 0..4");
+  EMT_REQUIRE(ipp == 0 || ipp == 1 || ipp == 2 || ipp == 4 || ipp == 8, EMT_ERR_INVALID,
+              "positions per CTA must be 0, 1, 2, 4 or 8");
+  EMT_REQUIRE(mode < 2 || inj_pairs, EMT_ERR_UNSUPPORTED, "two columns per thread need an even column count");
   EMT_CUDA(cudaDeviceSynchronize());
   drop_graphs();
   inj_mode = mode;
+  inj_ipp = ipp;
 }
 
 namespace {
 // tuning key: buses, leaves, depth, precision, columns, SMs
 using MTuneKey = std::array<int64_t, 6>;
-std::map<MTuneKey, std::array<int, 3>> g_mtune_cache;
+std::map<MTuneKey, std::array<int, 4>> g_mtune_cache;
 std::mutex g_mtune_mutex;
 MTuneKey mtune_key(const MSim& m, int sms) {
   return {m.n, m.store->n_leaf, m.store->tree.max_depth, m.store->precision, m.R, sms};
@@ -1538,7 +1556,7 @@ void MSim::autotune(int probe_steps, int* best_tn, int* best_kind, int* best_inj
       for (int tn : {64, 128, 192, 256}) cands.push_back({kind, tn});
   float best = 1e30f;
   int bkind = 1, btn = 0;
-  set_inject(0);
+  set_inject(0, 0);
   for (auto [kind, tn] : cands) {
     set_gemm(kind, tn, s);
     if (kind == 3 && umma.x_tiles >= n_sm) continue;   // the same kernels as kind 2
@@ -1551,25 +1569,27 @@ void MSim::autotune(int probe_steps, int* best_tn, int* best_kind, int* best_inj
   }
   set_gemm(bkind, btn, s);
   // then the injection kernel with those products
-  int binj = 0;
-  if (inj_pairs) {
-    for (int mode : {1, 2}) {
-      set_inject(mode);
+  int binj = 0, bipp = 0;
+  for (int mode : {1, 2, 3, 4}) {
+    if (mode >= 2 && !inj_pairs) break;
+    for (int ipp : {0, 4, 2, 1}) {
+      set_inject(mode, ipp);
       const float ms = time_it();
       if (ms < best) {
         best = ms;
         binj = mode;
+        bipp = ipp;
       }
     }
-    set_inject(binj);
   }
+  set_inject(binj, bipp);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   reset(s);
   EMT_CUDA(cudaStreamSynchronize(s));
   {
     std::lock_guard<std::mutex> lk(g_mtune_mutex);
-    g_mtune_cache[mtune_key(*this, n_sm)] = {bkind, btn, binj};
+    g_mtune_cache[mtune_key(*this, n_sm)] = {bkind, btn, binj, bipp};
   }
   if (best_tn) *best_tn = btn;
   if (best_kind) *best_kind = bkind;
@@ -1577,7 +1597,7 @@ void MSim::autotune(int probe_steps, int* best_tn, int* best_kind, int* best_inj
 }
 
 bool MSim::apply_cached_tuning(cudaStream_t s) {
-  std::array<int, 3> v;
+  std::array<int, 4> v;
   {
     std::lock_guard<std::mutex> lk(g_mtune_mutex);
     auto it = g_mtune_cache.find(mtune_key(*this, n_sm));
@@ -1585,7 +1605,7 @@ bool MSim::apply_cached_tuning(cudaStream_t s) {
     v = it->second;
   }
   set_gemm(v[0], v[1], s);
-  set_inject(v[2]);
+  set_inject(v[2], v[3]);
   return true;
 }
 
@@ -1641,7 +1661,7 @@ void MSim::stats(int64_t* out, int n_out) const {
     core += 4 * k * k;
   }
   const int64_t v[] = {n, st.n_leaf, leaf, fac, core, n_tiles, n_inc, n_crow, st.s_total, launches, n_series,
-                       (int64_t)el_a.size(), inject_pairs() ? 2 : 1};
+                       (int64_t)el_a.size(), inject_pairs() ? 2 : 1, inject_variant()};
   for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
 }
 

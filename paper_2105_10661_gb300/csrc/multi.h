@@ -106,8 +106,10 @@ class MSim {
   // products; leaf-GEMM tiles tn columns wide (0: by the column count)
   void set_gemm(int kind, int tn, cudaStream_t s);
   // injection kernel: 0 by the column count (two columns per thread when they fill whole blocks
-  // of pairs), 1 one column per thread, 2 two columns per thread (even column counts only)
-  void set_inject(int mode);
+  // of pairs), 1 one column per thread, 2, 3, 4 two columns per thread (even column counts only)
+  // with 6, 3 or 2 element ends per memory round trip and 2, 3 or 4 CTAs per SM
+  // ipp: positions per CTA (0: enough CTAs for about four per SM)
+  void set_inject(int mode, int ipp);
   // time every candidate product kind, leaf-GEMM tile width and injection kernel on `probe_steps`
   // steps and keep the fastest (cached per network and column-count shape for this process); the
   // simulation is reset afterwards
@@ -167,11 +169,12 @@ class MSim {
   void launch_steps(int n, cudaStream_t s);
   void apply_pass(int pass, int n1, int record, int s_in_chunk, cudaStream_t s);
   void launch_residual(int n1, int s_in_chunk, cudaStream_t s);
-  int positions_per_cta(int cols_per_thread = 1) const;
+  int positions_per_cta(int cols_per_thread = 1, int ctas_per_sm = 4) const;
   void launch_inject(int s_in_chunk, cudaStream_t s);
   bool inj_pairs = false;   // two-column injection kernel (even column stride, 32-bit row indices)
-  int inj_mode = 0;
+  int inj_mode = 0, inj_ipp = 0;
   bool inject_pairs() const;
+  int inject_variant() const;
   bool tensor_expand() const;
  public:
   void bench_kernel(int which, int reps, cudaStream_t s);

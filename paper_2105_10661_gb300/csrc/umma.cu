@@ -299,8 +299,10 @@ __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs
   }
 }
 
+// Two CTAs per SM for the leaf products (2-4 stages in 96 KB); four for the expansion, whose short
+// K (the ancestor path) needs only two stages and whose epilogue is bound by its loads.
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
+__global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 4 : 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
   // tensor-memory columns: a power of two >= 32 holding the TN accumulator columns
@@ -482,9 +484,11 @@ int umma_stages(int TN) {
   return std::max(2, std::min(4, (int)(kStageBudget / stage)));
 }
 // stages + barriers (2 ns + 1) + tensor-memory slot + flag
-size_t umma_smem_bytes(int TN) {
-  return (size_t)umma_stages(TN) * (2 * (size_t)A_CHUNK + 2 * (size_t)TN * UKC * 2) + 128;
+size_t umma_smem_bytes(int TN, int stages) {
+  return (size_t)stages * (2 * (size_t)A_CHUNK + 2 * (size_t)TN * UKC * 2) + 128;
 }
+size_t umma_smem_bytes(int TN) { return umma_smem_bytes(TN, umma_stages(TN)); }
+constexpr int kExpandStages = 2;
 
 void Umma::build(const Store& st, int R_, cudaStream_t s, int tn) {
   R = R_;
@@ -604,7 +608,7 @@ void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* 
   x_tile_b.upload(tb, s);
   x_tiles_d.upload(tiles, s);
   EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)umma_smem_bytes(xTN)));
+                                (int)umma_smem_bytes(xTN, kExpandStages)));
   EMT_CUDA(cudaStreamSynchronize(s));
   exp_ready = true;
 }
@@ -648,7 +652,7 @@ void Umma::expand(const Store& st, const MSimD& m, const int* path_ptr, const in
   a.Y = m.Y;
   a.R = R;
   a.TN = xTN;
-  a.ns = umma_stages(xTN);
+  a.ns = kExpandStages;
   a.r_act = m.R_act;
   ExpArgs x;
   x.m = m;
@@ -656,7 +660,7 @@ void Umma::expand(const Store& st, const MSimD& m, const int* path_ptr, const in
   x.n1 = n1;
   x.record = record;
   x.s_in_chunk = s_in_chunk;
-  k_mc_umma<UMMA_EXPAND><<<x_tiles, 256, umma_smem_bytes(xTN), s>>>(st.view(), a, x, st.d_status.p);
+  k_mc_umma<UMMA_EXPAND><<<x_tiles, 256, umma_smem_bytes(xTN, kExpandStages), s>>>(st.view(), a, x, st.d_status.p);
   EMT_CUDA(cudaGetLastError());
 }
 

@@ -489,6 +489,43 @@ def test_multi_column_leaf_tile_widths_match_oracle(L, tile, R):
         assert rel_err(got[:, c, :], ref) <= 1e-8, (c, rel_err(got[:, c, :], ref))
 
 
+def test_multi_column_injection_variants_agree_and_match_oracle(L):
+    # one column per thread, and two per thread with 6, 3 or 2 element ends per round trip (2, 3,
+    # 4 CTAs per SM): the two-column variants batch the same arithmetic differently, bit for bit
+    net = netgen.add_loads(netgen.tiled(2, 2), seed=13)
+    R, steps = 64, 30
+    ss, ls = netgen.scenario_scales(net, R, seed=13)
+    branches = netgen.pick_branches(net, 2, seed=41)
+    trips = {1: (10, int(branches[0])), R - 1: (18, int(branches[1]))}
+    mon = np.arange(0, net["n_bus"], 9)
+    out = {}
+    for mode, ipp in ((1, 0), (2, 0), (3, 0), (4, 0), (4, 1), (2, 4), (1, 2)):
+        sim = L.emt_sim_create(net, DT, levels=2, nrhs=R, src_scale=ss, load_scale=ls)
+        L.emt_sim_set_inject(sim, mode, ipp)
+        assert L.emt_sim_stats(sim)["inject_variant"] == mode
+        for c, (st, e) in trips.items():
+            L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+        L.emt_sim_monitor(sim, mon)
+        rec = torch.zeros(steps, R, len(mon), dtype=torch.float64, device="cuda")
+        L.emt_step(sim, steps, rec)
+        torch.cuda.synchronize()
+        out[mode, ipp] = rec.cpu().numpy()
+    for key in ((3, 0), (4, 0), (4, 1), (2, 4)):
+        assert np.array_equal(out[2, 0], out[key]), key
+    assert np.array_equal(out[1, 0], out[1, 2])
+    out = {m: out[m, 0] for m in (1, 2)}
+    nw = oemt.Network(net, DT, levels=2)
+    for c in (0, 1, R - 1):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon, src_scale=ss[c], load_scale=ls[c])
+        for mode in (1, 2):
+            assert rel_err(out[mode][:, c, :], ref) <= 1e-8, (mode, c)
+    odd = L.emt_sim_create(net, DT, levels=2, nrhs=5)
+    with pytest.raises(L.EmtError) as e:
+        L.emt_sim_set_inject(odd, 3)
+    assert e.value.code == L.EMT_ERR_UNSUPPORTED
+
+
 def test_multi_column_autotune_times_the_shapes_and_matches_oracle(L):
     # the autotuner times FP32 products and tcgen05 leaf tiles of every width, then the injection
     # kernel; the shape it keeps still matches the oracle, and a later simulation of the same shape

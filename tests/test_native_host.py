@@ -180,6 +180,7 @@ NULL_HANDLE_CALLS = {
     "emt_sim_set_rows_per_cta": (None, 0),
     "emt_sim_tune": (None, 0, 2),
     "emt_sim_autotune": (None, 1, None, None, None),
+    "emt_sim_set_inject": (None, 0, 0),
     "emt_sim_reset": (None, None),
     "emt_sim_stats": (None, None, 0),
     "emt_sim_bench_kernel": (None, 0, 1, None),
