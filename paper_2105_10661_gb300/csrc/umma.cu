@@ -607,6 +607,10 @@ void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* 
   x_bdesc.upload(bdesc, s);
   x_tile_b.upload(tb, s);
   x_tiles_d.upload(tiles, s);
+  // the epilogue stages the 128 x xTN accumulator (row stride xTN + 1 words) in the pipeline
+  // stages: they must hold it
+  EMT_REQUIRE((size_t)UM * (xTN + 1) * sizeof(float) <= umma_smem_bytes(xTN, kExpandStages) - 128,
+              EMT_ERR_UNSUPPORTED, "expansion tile too wide for its pipeline stages");
   EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)umma_smem_bytes(xTN, kExpandStages)));
   EMT_CUDA(cudaStreamSynchronize(s));
