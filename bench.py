@@ -746,8 +746,7 @@ def inject_name(st):
 # DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu --set full
 # capture of the kernel as it stands (python bench.py --config 4 --profile 6, third launch of each)
 NCU_TRAFFIC = {("k_mc_inject2<2,4>", 11456, 512): 212.473856e6 + 148.755968e6,
-               ("k_mc_residual", 11456, 512): 94.541056e6 + 10.648576e6,
-               ("expansion", 11456, 512): 81.736448e6 + 2.981376e6}
+               ("k_mc_residual", 11456, 512): 94.541056e6 + 10.648576e6}
 
 
 def ncu_traffic(kernel, n, cols):

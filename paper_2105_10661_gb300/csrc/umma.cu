@@ -184,61 +184,60 @@ __device__ __forceinline__ void bulk_g2s_u(unsigned char* dst, const void* src, 
                : "memory");
 }
 
-// Expansion epilogue: the accumulator (128 x TN, FP32) goes through shared memory (row stride
-// TN + 1 words: conflict-free both ways) so that each warp then handles one position's TN columns
-// with coalesced accesses: v = Y - acc (- f_c z for a column whose change is on), V = v (pass 0) or
-// V + v in float-float (pass 1), and the monitored record. The pipeline stages are free here (every
-// MMA reading them has completed).
+// Expansion epilogue, per group of 64 columns: the accumulator's 128 x 64 block goes through shared
+// memory (row stride 65 words: conflict-free both ways; it lives in the pipeline stages, which are
+// free here since every MMA reading them has completed) so that each warp then handles rows of
+// the group with coalesced accesses: v = Y - acc (- f_c z for a column whose change is on), V = v
+// (pass 0) or V + v in float-float (pass 1), and the monitored record.
 __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs& x, uint32_t tmem, unsigned char* sm,
                                                 int lo, int b, int m0, int n0) {
   const int TN = a.TN, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* T = reinterpret_cast<float*>(sm);
-  const int ldt = TN + 1;
-  {
-    const int lane_base = 32 * (warp & 3);
-    const int nchunks = TN / 32;
-    const int half = nchunks / 2 > 0 ? nchunks / 2 : 1;
-    const int c_begin = (warp >> 2) * half, c_end = min(nchunks, c_begin + half);
-    for (int ch = c_begin; ch < c_end; ++ch) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float* trow = T + (lane_base + lane) * ldt + ch * 32;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) trow[q] = __uint_as_float(r[q]);
-    }
-  }
-  __syncthreads();
+  constexpr int ldt = 65;
   const MSimD& m = x.m;
   const int64_t R = m.R;
   const int step = m.dyn->step_base + x.s_in_chunk + 1;
   double* rec = x.record ? m.dyn->rec : nullptr;
   const int rec_first = m.dyn->rec_first;
-  // per 64-column group, lane: columns c, c + 1 of every row of this warp; four rows' loads in
-  // flight at once
+  const int rows = min(UM, b - m0);
   for (int cg = 0; cg < TN; cg += 64) {
-    const int cc = cg + 2 * lane, c = n0 + cc;
+    if (cg > 0) __syncthreads();   // the previous group's rows are done with T
+    {
+      // warps 0-3 read columns cg .. cg + 31, warps 4-7 cg + 32 .. cg + 63 of their 32 lanes
+      const int lane_base = 32 * (warp & 3);
+      const int ch = cg / 32 + (warp >> 2);
+      if (ch * 32 < TN) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float* trow = T + (lane_base + lane) * ldt + (warp >> 2) * 32;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) trow[q] = __uint_as_float(r[q]);
+      }
+    }
+    __syncthreads();
+    // lane: columns c, c + 1 of every row of this warp; four rows' loads in flight at once
+    const int cl = 2 * lane, cc = cg + cl, c = n0 + cc;
     const int nv = cc < TN ? max(0, min(2, m.R_act - c)) : 0;   // valid columns of this lane
     float fc0 = 0.f, fc1 = 0.f;
     if (x.n1 && nv > 0) {
       fc0 = m.fcol[c];
       if (nv > 1) fc1 = m.fcol[c + 1];
     }
-    const int rows = min(UM, b - m0);
     constexpr int RB = 4;
     for (int r0 = warp; r0 < rows; r0 += 8 * RB) {
       float2 y[RB];
       float4 vo[RB];
       int mi[RB];
-  #pragma unroll
+#pragma unroll
       for (int u = 0; u < RB; ++u) {
         const int rr = r0 + 8 * u;
         const int64_t at = (int64_t)(lo + m0 + rr) * R + c;
@@ -260,18 +259,18 @@ __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs
           if (rec) mi[u] = m.mon_idx[lo + m0 + rr];
         }
       }
-  #pragma unroll
+#pragma unroll
       for (int u = 0; u < RB; ++u) {
         const int rr = r0 + 8 * u;
         if (rr >= rows || nv == 0) continue;
         const int pos = lo + m0 + rr;
         const int64_t at = (int64_t)pos * R + c;
-        float v[2] = {y[u].x - T[rr * ldt + cc], y[u].y - T[rr * ldt + cc + 1]};
+        float v[2] = {y[u].x - T[rr * ldt + cl], y[u].y - T[rr * ldt + cl + 1]};
         if (fc0 != 0.f) v[0] = fmaf(-fc0, m.Z[at].x, v[0]);
         if (fc1 != 0.f) v[1] = fmaf(-fc1, m.Z[at + 1].x, v[1]);
         const float ox[2] = {vo[u].x, vo[u].z}, oy[2] = {vo[u].y, vo[u].w};
         float2 out[2];
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < 2; ++q) {
           if (x.pass == 0) {
             out[q] = make_float2(v[q], 0.f);
@@ -299,10 +298,11 @@ __device__ __forceinline__ void expand_epilogue(const UmmaArgs& a, const ExpArgs
   }
 }
 
-// Two CTAs per SM for the leaf products (2-4 stages in 96 KB); four for the expansion, whose short
-// K (the ancestor path) needs only two stages and whose epilogue is bound by its loads.
+// Two CTAs per SM for the leaf products (2-4 stages in 96 KB); three for the expansion (128-column
+// tiles), whose short K (the ancestor path) needs only two stages and whose epilogue is bound by
+// its loads.
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 4 : 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
+__global__ void __launch_bounds__(256, MODE == UMMA_EXPAND ? 3 : 2) k_mc_umma(DStore st, UmmaArgs a, ExpArgs x, int* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int TN = a.TN;
   // tensor-memory columns: a power of two >= 32 holding the TN accumulator columns
@@ -563,9 +563,9 @@ void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* 
   const Tree& t = st.tree;
   for (int j = 0; j < st.n_leaf; ++j)
     if (pp[j + 1] == pp[j]) return;   // a leaf without ancestor rows: the SIMT expansion serves it
-  // 64-column tiles: the epilogue is bound by its loads and needs the CTAs (128-column tiles, a
-  // quarter of the CTAs fewer setups, measured slower on the 11,456-bus network: 49 against 39 us)
-  xTN = 64;
+  // 128-column tiles at three CTAs per SM (the accumulator staged per 64-column group): 37.4 us on
+  // the 11,456-bus network x 512 columns, against 38.9 for 64-column tiles at four CTAs per SM
+  xTN = 128;
   std::vector<int> bl, bm, bk;
   std::vector<int4> tiles, bdesc;
   std::vector<int2> tb;
@@ -607,9 +607,9 @@ void Umma::build_expand(const Store& st, const std::vector<int>& pp, const int* 
   x_bdesc.upload(bdesc, s);
   x_tile_b.upload(tb, s);
   x_tiles_d.upload(tiles, s);
-  // the epilogue stages the 128 x xTN accumulator (row stride xTN + 1 words) in the pipeline
-  // stages: they must hold it
-  EMT_REQUIRE((size_t)UM * (xTN + 1) * sizeof(float) <= umma_smem_bytes(xTN, kExpandStages) - 128,
+  // the epilogue stages 128 x 64 blocks of the accumulator (row stride 65 words) in the pipeline
+  // stages: they must hold one; tiles are whole 64-column groups
+  EMT_REQUIRE((size_t)UM * 65 * sizeof(float) <= umma_smem_bytes(xTN, kExpandStages) - 128 && xTN % 64 == 0,
               EMT_ERR_UNSUPPORTED, "expansion tile too wide for its pipeline stages");
   EMT_CUDA(cudaFuncSetAttribute(k_mc_umma<UMMA_EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)umma_smem_bytes(xTN, kExpandStages)));
