@@ -989,14 +989,17 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   }
   std::vector<int> tptr(n + 1, 0);
   std::vector<float2> tcs, tsn;
+  tcs.reserve((size_t)(net->n_src + net->n_load) * R);
+  tsn.reserve((size_t)(net->n_src + net->n_load) * R);
   for (int p = 0; p < n; ++p) {
     for (auto& tm : terms[p]) {
+      const double cph = std::cos(tm.phi), sph = std::sin(tm.phi);
       for (int c = 0; c < R; ++c) {
         double sc = 1.0;
         if (tm.kind == 0 && src_scale) sc = src_scale[(size_t)c * net->n_src + tm.idx];
         if (tm.kind == 1 && load_scale) sc = load_scale[(size_t)c * net->n_load + tm.idx];
-        tcs.push_back(host_ff(tm.coef * sc * std::cos(tm.phi)));
-        tsn.push_back(host_ff(tm.coef * sc * std::sin(tm.phi)));
+        tcs.push_back(host_ff(tm.coef * sc * cph));
+        tsn.push_back(host_ff(tm.coef * sc * sph));
       }
     }
     tptr[p + 1] = tptr[p] + (int)terms[p].size();

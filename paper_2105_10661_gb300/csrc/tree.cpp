@@ -13,9 +13,11 @@
 //   5. leaves at depth `levels`, or (levels == 0) once a set has at most d_th buses.
 // Nodes are numbered breadth first; the left-to-right leaves give the nested ordering.
 #include <algorithm>
+#include <atomic>
 #include <deque>
-#include <map>
-#include <set>
+#include <exception>
+#include <mutex>
+#include <thread>
 #include <tuple>
 
 #include "internal.h"
@@ -29,22 +31,26 @@ struct Local {
   std::vector<std::vector<int>> wt;    // multiplicities
 };
 
-Local local_graph(const std::vector<int>& V, const std::vector<int>& gl2lo,
+// Induced subgraph on the set V (owner[v] == set, loc[v] its local index): ascending unique
+// neighbours with their multiplicities.
+Local local_graph(const std::vector<int>& V, int set, const std::vector<int>& owner, const std::vector<int>& loc,
                   const std::vector<std::vector<int>>& adj_global) {
   Local g;
   g.n = (int)V.size();
   g.nbr.resize(g.n);
   g.wt.resize(g.n);
+  std::vector<int> tmp;
   for (int i = 0; i < g.n; ++i) {
-    std::map<int, int> m;
-    for (int u : adj_global[V[i]]) {
-      int lu = gl2lo[u];
-      if (lu < 0 || lu == i) continue;
-      m[lu] += 1;
-    }
-    for (auto& kv : m) {
-      g.nbr[i].push_back(kv.first);
-      g.wt[i].push_back(kv.second);
+    tmp.clear();
+    for (int u : adj_global[V[i]])
+      if (owner[u] == set && loc[u] != i) tmp.push_back(loc[u]);
+    std::sort(tmp.begin(), tmp.end());
+    for (size_t k = 0; k < tmp.size();) {
+      size_t e = k;
+      while (e < tmp.size() && tmp[e] == tmp[k]) ++e;
+      g.nbr[i].push_back(tmp[k]);
+      g.wt[i].push_back((int)(e - k));
+      k = e;
     }
   }
   return g;
@@ -104,37 +110,66 @@ std::vector<int> growth_order(const Local& g, int start) {
   return order;
 }
 
+// Argmax of (D[v], -v) over the active vertices: an array segment tree whose nodes hold the
+// winning vertex of their range (-1 if none); a change of D or of activity re-plays one path.
+struct MaxTree {
+  int P = 1;
+  std::vector<int> t;
+  const long long* D = nullptr;
+  bool better(int x, int y) const {
+    if (y < 0) return x >= 0;
+    if (x < 0) return false;
+    return D[x] > D[y] || (D[x] == D[y] && x < y);
+  }
+  void build(int n, const long long* d, const std::vector<char>& active) {
+    D = d;
+    P = 1;
+    while (P < n) P <<= 1;
+    t.assign(2 * P, -1);
+    for (int v = 0; v < n; ++v) t[P + v] = active[v] ? v : -1;
+    for (int i = P - 1; i >= 1; --i) t[i] = better(t[2 * i], t[2 * i + 1]) ? t[2 * i] : t[2 * i + 1];
+  }
+  void replay(int v) {
+    for (int i = (P + v) >> 1; i >= 1; i >>= 1) t[i] = better(t[2 * i], t[2 * i + 1]) ? t[2 * i] : t[2 * i + 1];
+  }
+  void set(int v, bool on) {
+    t[P + v] = on ? v : -1;
+    replay(v);
+  }
+  int top() const { return t[1]; }
+};
+
 // The choices are those of the plain O(n) scans (a = largest D over unlocked A, b = largest
-// D(b) - 2 w(a, b) over unlocked B, smallest id on ties), found in O(log n): the unlocked vertices
-// of each side sit in an ordered set keyed by (-D, id), whose first element is the scan's answer;
-// for b the only values that differ from D are those of a's neighbours, so b is the better of the
-// best neighbour and the first non-neighbour of the set.
+// D(b) - 2 w(a, b) over unlocked B, smallest id on ties), found in O(deg log n): each side's
+// unlocked vertices sit in a MaxTree; for b the only values that differ from D are those of a's
+// neighbours, so b is the better of the best neighbour and the best of the tree with a's
+// neighbours masked out.
 void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
   const int n = g.n;
   std::vector<long long> D(n);
-  std::vector<char> locked(n);
-  using Key = std::pair<long long, int>;   // (-D, id)
+  std::vector<char> locked(n), act(n);
+  MaxTree T[2];
   for (int pass = 0; pass < passes; ++pass) {
+    int nA = 0;
     for (int v = 0; v < n; ++v) {
       long long s = 0;
       for (size_t k = 0; k < g.nbr[v].size(); ++k)
         s += (side[g.nbr[v][k]] != side[v]) ? g.wt[v][k] : -g.wt[v][k];
       D[v] = s;
+      nA += side[v] == 0;
     }
     std::fill(locked.begin(), locked.end(), 0);
-    std::set<Key> S[2];
-    for (int v = 0; v < n; ++v) S[side[v]].insert({-D[v], v});
-    const int nA = (int)S[0].size();
+    for (int sd = 0; sd < 2; ++sd) {
+      for (int v = 0; v < n; ++v) act[v] = side[v] == sd;
+      T[sd].build(n, D.data(), act);
+    }
     const int steps = std::min(nA, n - nA);
     std::vector<std::pair<int, int>> pairs;
     std::vector<long long> gains;
-    auto move_d = [&](int x, long long delta) {   // D[x] += delta for an unlocked x
-      S[side[x]].erase({-D[x], x});
-      D[x] += delta;
-      S[side[x]].insert({-D[x], x});
-    };
+    pairs.reserve(steps);
+    gains.reserve(steps);
     for (int st = 0; st < steps; ++st) {
-      const int a = S[0].begin()->second;
+      const int a = T[0].top();
       const std::vector<int>& na = g.nbr[a];
       // best neighbour of a in unlocked B, by D - 2 w
       bool have = false;
@@ -152,32 +187,38 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
           wab = g.wt[a][k];
         }
       }
-      // first unlocked B vertex that is not a neighbour of a
-      for (const Key& kk : S[1]) {
-        const int u = kk.second;
-        if (std::binary_search(na.begin(), na.end(), u)) continue;
-        const long long val = -kk.first;
-        if (!have || val > bv || (val == bv && u < b)) {
+      // best unlocked B vertex that is not a neighbour of a
+      for (int u : na)
+        if (side[u] == 1 && !locked[u]) T[1].set(u, false);
+      const int c = T[1].top();
+      for (int u : na)
+        if (side[u] == 1 && !locked[u]) T[1].set(u, true);
+      if (c >= 0) {
+        const long long val = D[c];
+        if (!have || val > bv || (val == bv && c < b)) {
           have = true;
           bv = val;
-          b = u;
+          b = c;
           wab = 0;
         }
-        break;
       }
       gains.push_back(D[a] + D[b] - 2 * wab);
       pairs.emplace_back(a, b);
-      S[0].erase({-D[a], a});
-      S[1].erase({-D[b], b});
       locked[a] = 1;
       locked[b] = 1;
+      T[0].set(a, false);
+      T[1].set(b, false);
       for (size_t k = 0; k < na.size(); ++k) {
         const int x = na[k];
-        if (!locked[x]) move_d(x, (side[x] == 0) ? 2LL * g.wt[a][k] : -2LL * g.wt[a][k]);
+        if (locked[x]) continue;
+        D[x] += (side[x] == 0) ? 2LL * g.wt[a][k] : -2LL * g.wt[a][k];
+        T[side[x]].replay(x);
       }
       for (size_t k = 0; k < g.nbr[b].size(); ++k) {
         const int y = g.nbr[b][k];
-        if (!locked[y]) move_d(y, (side[y] == 1) ? 2LL * g.wt[b][k] : -2LL * g.wt[b][k]);
+        if (locked[y]) continue;
+        D[y] += (side[y] == 1) ? 2LL * g.wt[b][k] : -2LL * g.wt[b][k];
+        T[side[y]].replay(y);
       }
     }
     if (gains.empty()) break;
@@ -217,35 +258,79 @@ Tree build_tree(int n_bus, int n_branch, const int32_t* from, const int32_t* to,
   parent.push_back(-1);
   left.push_back(-1);
   right.push_back(-1);
-  std::vector<int> gl2lo(n_bus, -1);
-  for (size_t i = 0; i < sets.size(); ++i) {
-    const int n = (int)sets[i].size();
-    bool split = n >= 2 && ((levels > 0 && depth[i] < levels) || (levels <= 0 && n > d_th));
-    if (!split) continue;
-    std::vector<int> V = sets[i];
-    for (int k = 0; k < n; ++k) gl2lo[V[k]] = k;
-    Local g = local_graph(V, gl2lo, adj);
-    for (int k = 0; k < n; ++k) gl2lo[V[k]] = -1;
-    int s = start_vertex(g);
-    std::vector<int> order = growth_order(g, s);
-    std::vector<int> side(n, 1);
-    int nA = (n + 1) / 2;
-    for (int k = 0; k < nA; ++k) side[order[k]] = 0;
-    kernighan_lin(g, side, 4);
-    std::vector<int> A, B;
-    for (int k = 0; k < n; ++k) (side[k] == 0 ? A : B).push_back(V[k]);
-    if (!(A.front() < B.front())) std::swap(A, B);
-    int li = (int)sets.size();
-    sets.push_back(A);
-    sets.push_back(B);
-    for (int c = 0; c < 2; ++c) {
-      depth.push_back(depth[i] + 1);
-      parent.push_back((int)i);
-      left.push_back(-1);
-      right.push_back(-1);
+  // Level by level: the sets of one depth are disjoint, so their bisections run concurrently (each
+  // is deterministic), and their children are appended in the parents' order, which keeps the
+  // breadth-first numbering of a one-at-a-time loop.
+  std::vector<int> owner(n_bus, -1), loc(n_bus, -1);
+  size_t lvl_begin = 0;
+  while (lvl_begin < sets.size()) {
+    const size_t lvl_end = sets.size();
+    std::vector<size_t> todo;
+    for (size_t i = lvl_begin; i < lvl_end; ++i) {
+      const int n = (int)sets[i].size();
+      if (n >= 2 && ((levels > 0 && depth[i] < levels) || (levels <= 0 && n > d_th))) todo.push_back(i);
     }
-    left[i] = li;
-    right[i] = li + 1;
+    for (size_t q = 0; q < todo.size(); ++q) {
+      const std::vector<int>& V = sets[todo[q]];
+      for (int k = 0; k < (int)V.size(); ++k) {
+        owner[V[k]] = (int)q;
+        loc[V[k]] = k;
+      }
+    }
+    std::vector<std::pair<std::vector<int>, std::vector<int>>> halves(todo.size());
+    auto bisect = [&](size_t q) {
+      const std::vector<int>& V = sets[todo[q]];
+      const int n = (int)V.size();
+      Local g = local_graph(V, (int)q, owner, loc, adj);
+      const int s = start_vertex(g);
+      std::vector<int> order = growth_order(g, s);
+      std::vector<int> side(n, 1);
+      const int nA = (n + 1) / 2;
+      for (int k = 0; k < nA; ++k) side[order[k]] = 0;
+      kernighan_lin(g, side, 4);
+      std::vector<int> A, B;
+      for (int k = 0; k < n; ++k) (side[k] == 0 ? A : B).push_back(V[k]);
+      if (!(A.front() < B.front())) std::swap(A, B);
+      halves[q] = {std::move(A), std::move(B)};
+    };
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t nth = std::min<size_t>(todo.size(), hw);
+    if (nth <= 1) {
+      for (size_t q = 0; q < todo.size(); ++q) bisect(q);
+    } else {
+      std::atomic<size_t> next{0};
+      std::vector<std::thread> pool;
+      std::exception_ptr err;
+      std::mutex err_mu;
+      for (size_t w = 0; w < nth; ++w)
+        pool.emplace_back([&] {
+          for (size_t q; (q = next.fetch_add(1)) < todo.size();) {
+            try {
+              bisect(q);
+            } catch (...) {
+              std::lock_guard<std::mutex> lk(err_mu);
+              if (!err) err = std::current_exception();
+            }
+          }
+        });
+      for (auto& th : pool) th.join();
+      if (err) std::rethrow_exception(err);
+    }
+    for (size_t q = 0; q < todo.size(); ++q) {
+      const size_t i = todo[q];
+      const int li = (int)sets.size();
+      sets.push_back(std::move(halves[q].first));
+      sets.push_back(std::move(halves[q].second));
+      for (int c = 0; c < 2; ++c) {
+        depth.push_back(depth[i] + 1);
+        parent.push_back((int)i);
+        left.push_back(-1);
+        right.push_back(-1);
+      }
+      left[i] = li;
+      right[i] = li + 1;
+    }
+    lvl_begin = lvl_end;
   }
   Tree t;
   t.n_bus = n_bus;
