@@ -59,67 +59,178 @@ __global__ void k_assemble_leaf(DStore st, const int* __restrict__ csr_ptr, cons
   }
 }
 
-// In-place lower Cholesky of one leaf block per CTA (right looking, column by column): the first
-// step of the direct leaf inversion of Algorithm 1 (Sec. III-B).
-__global__ void k_chol(DStore st, const int* leaves) {
-  extern __shared__ double colk[];
+// Blocked right-looking Cholesky of the leaf blocks (in place, lower), panel width kCholNb: per
+// panel, the diagonal block is factored in shared memory (one CTA per leaf), the rows below it
+// solved against it (CTAs of kCholRows rows per leaf), and the trailing lower triangle updated in
+// 64 x 64 tiles (as many CTAs as tiles), so a leaf's FP64 work is spread over the SMs instead of
+// one CTA walking its b columns.
+constexpr int kCholNb = 64, kCholRows = 128;
+
+__global__ void __launch_bounds__(256) k_chol_diag(DStore st, const int* leaves, int kb) {
+  __shared__ double D[kCholNb][kCholNb + 1];
+  __shared__ int bad;
+  if (*st.status != DEV_OK) return;
   const int j = leaves[blockIdx.x];
   const int node = st.leaf_node[j];
   const int b = st.hi[node] - st.lo[node];
+  if (kb >= b) return;
+  const int nb = min(kCholNb, b - kb);
   const int ld = st.leaf_ld[j];
-  double* A = st.L64 + st.leaf_off[j];
-  __shared__ double piv;
-  __shared__ int bad;
+  double* A = st.L64 + st.leaf_off[j] + (int64_t)kb * ld + kb;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) D[t / nb][t % nb] = A[(int64_t)(t / nb) * ld + t % nb];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  for (int k = 0; k < b; ++k) {
+  for (int k = 0; k < nb; ++k) {
     if (threadIdx.x == 0) {
-      const double d = A[(int64_t)k * ld + k];
-      if (!(d > 0.0)) {
-        bad = 1;
-        piv = 1.0;
-      } else {
-        piv = sqrt(d);
-      }
-      A[(int64_t)k * ld + k] = piv;
+      const double d = D[k][k];
+      if (!(d > 0.0)) bad = 1;
+      D[k][k] = d > 0.0 ? sqrt(d) : 1.0;
     }
     __syncthreads();
-    if (bad) {
-      if (threadIdx.x == 0) atomicExch(st.status, DEV_SINGULAR);
-      return;
-    }
-    const double inv = 1.0 / piv;
-    for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) {
-      const double v = A[(int64_t)i * ld + k] * inv;
-      A[(int64_t)i * ld + k] = v;
-      colk[i] = v;
-    }
+    if (bad) break;
+    const double inv = 1.0 / D[k][k];
+    for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i][k] *= inv;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = k + 1 + warp; i < b; i += nw) {
-      const double aik = colk[i];
-      for (int c = k + 1 + lane; c <= i; c += 32) A[(int64_t)i * ld + c] -= aik * colk[c];
+    for (int t = threadIdx.x; t < (nb - k - 1) * (nb - k - 1); t += blockDim.x) {
+      const int i = k + 1 + t / (nb - k - 1), c = k + 1 + t % (nb - k - 1);
+      if (c <= i) D[i][c] -= D[i][k] * D[c][k];
     }
     __syncthreads();
   }
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(st.status, DEV_SINGULAR);
+    return;
+  }
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, c = t % nb;
+    if (c <= i) A[(int64_t)i * ld + c] = D[i][c];
+  }
 }
 
-// W = L^{-1} column by column (thread per column), direct leaf inversion (Algorithm 1).
-__global__ void k_trinv(DStore st, double* __restrict__ W, const int* leaves) {
+// rows r >= kb + nb of the panel: L[r, kb:kb+nb] = A[r, kb:kb+nb] L_kk^-T (forward substitution,
+// one row per thread, the panel rows staged in shared memory)
+__global__ void __launch_bounds__(kCholRows) k_chol_panel(DStore st, const int* leaves, int kb) {
+  __shared__ double Lk[kCholNb][kCholNb + 1];
+  extern __shared__ double P[];   // [kCholRows][kCholNb + 1]
+  if (*st.status != DEV_OK) return;
+  const int j = leaves[blockIdx.x];
+  const int node = st.leaf_node[j];
+  const int b = st.hi[node] - st.lo[node];
+  if (kb >= b) return;
+  const int nb = min(kCholNb, b - kb);
+  const int r0 = kb + nb + blockIdx.y * kCholRows;
+  if (r0 >= b) return;
+  const int nr = min(kCholRows, b - r0);
+  const int ld = st.leaf_ld[j];
+  double* A = st.L64 + st.leaf_off[j];
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, c = t % nb;
+    Lk[i][c] = c <= i ? A[(int64_t)(kb + i) * ld + kb + c] : 0.0;
+  }
+  for (int t = threadIdx.x; t < nr * nb; t += blockDim.x)
+    P[(t / nb) * (kCholNb + 1) + t % nb] = A[(int64_t)(r0 + t / nb) * ld + kb + t % nb];
+  __syncthreads();
+  if ((int)threadIdx.x < nr) {
+    double* x = P + threadIdx.x * (kCholNb + 1);
+    for (int c = 0; c < nb; ++c) {
+      double v = x[c];
+      for (int m = 0; m < c; ++m) v -= x[m] * Lk[c][m];
+      x[c] = v / Lk[c][c];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * nb; t += blockDim.x)
+    A[(int64_t)(r0 + t / nb) * ld + kb + t % nb] = P[(t / nb) * (kCholNb + 1) + t % nb];
+}
+
+// trailing update A[r, c] -= L[r, panel] . L[c, panel] for kb + nb <= c <= r, tile (ti, tj) of 64
+// x 64 with ti >= tj (blockIdx.y enumerates the lower-triangle tiles)
+__global__ void __launch_bounds__(256) k_chol_update(DStore st, const int* leaves, int kb) {
+  extern __shared__ double upd_sm[];   // Lr, Lc: [64][kCholNb + 1] each
+  double (*Lr)[kCholNb + 1] = reinterpret_cast<double (*)[kCholNb + 1]>(upd_sm);
+  double (*Lc)[kCholNb + 1] = reinterpret_cast<double (*)[kCholNb + 1]>(upd_sm + 64 * (kCholNb + 1));
+  if (*st.status != DEV_OK) return;
+  const int j = leaves[blockIdx.x];
+  const int node = st.leaf_node[j];
+  const int b = st.hi[node] - st.lo[node];
+  const int t0 = kb + kCholNb;
+  if (t0 >= b) return;
+  const int nt = (b - t0 + 63) / 64;
+  int ti = 0, rem = blockIdx.y;
+  while (rem > ti) {
+    rem -= ti + 1;
+    ++ti;
+  }
+  const int tj = rem;
+  if (ti >= nt) return;
+  const int ld = st.leaf_ld[j];
+  double* A = st.L64 + st.leaf_off[j];
+  const int r0 = t0 + 64 * ti, c0 = t0 + 64 * tj;
+  const int nr = min(64, b - r0), nc = min(64, b - c0);
+  for (int t = threadIdx.x; t < 64 * kCholNb; t += blockDim.x) {
+    const int i = t / kCholNb, m = t % kCholNb;
+    Lr[i][m] = i < nr ? A[(int64_t)(r0 + i) * ld + kb + m] : 0.0;
+    Lc[i][m] = i < nc ? A[(int64_t)(c0 + i) * ld + kb + m] : 0.0;
+  }
+  __syncthreads();
+  // thread: 4 x 4 outputs (rows ty + 16 u, columns tx + 16 v)
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int m = 0; m < kCholNb; ++m) {
+    double a[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Lr[ty + 16 * u][m];
+      c[u] = Lc[tx + 16 * u][m];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * c[v];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = ty + 16 * u, c = tx + 16 * v;
+      if (r < nr && c < nc && r0 + r >= c0 + c) A[(int64_t)(r0 + r) * ld + c0 + c] -= acc[u][v];
+    }
+}
+
+// W = L^{-1} by forward substitution, one CTA per (leaf, COLS columns): the block's columns of W
+// stay in shared memory while the rows are swept in order. Each column has 256 / COLS lanes of one
+// warp, which split the dot product L[i, col:i] . W[col:i, col] and add the parts by shuffles, so a
+// warp needs no barrier but its own. The inverse's FP64 work is spread over ceil(b / COLS) CTAs
+// per leaf instead of one thread per column walking global memory.
+template <int COLS>
+__global__ void __launch_bounds__(256) k_trinv_block(DStore st, double* __restrict__ W, const int* leaves) {
+  constexpr int LPC = 256 / COLS;   // lanes per column (16 or 32)
+  static_assert(LPC == 16 || LPC == 32, "columns per CTA: 16 or 8");
+  extern __shared__ double xs[];   // [b][COLS]
   const int j = leaves[blockIdx.x];
   const int node = st.leaf_node[j];
   const int b = st.hi[node] - st.lo[node];
   const int ld = st.leaf_ld[j];
+  const int c0 = blockIdx.y * COLS;
+  if (c0 >= b) return;
   const double* A = st.L64 + st.leaf_off[j];
   double* X = W + st.leaf_off[j];
-  const int col = blockIdx.y * blockDim.x + threadIdx.x;
-  if (col >= b) return;
-  for (int i = 0; i < col; ++i) X[(int64_t)i * ld + col] = 0.0;
-  for (int i = col; i < b; ++i) {
-    double s = (i == col) ? 1.0 : 0.0;
+  const int cl = threadIdx.x / LPC, part = threadIdx.x % LPC;   // local column, part of the dot product
+  const int col = c0 + cl;
+  for (int i = c0; i < b; ++i) {
     const double* Ai = A + (int64_t)i * ld;
-    for (int k = col; k < i; ++k) s -= Ai[k] * X[(int64_t)k * ld + col];
-    X[(int64_t)i * ld + col] = s / Ai[i];
+    double s = 0.0;
+    if (col < b && i > col)
+      for (int k = col + part; k < i; k += LPC) s += Ai[k] * xs[k * COLS + cl];
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (col < b && part == 0) xs[i * COLS + cl] = i < col ? 0.0 : ((i == col ? 1.0 : 0.0) - s) / Ai[i];
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < b * COLS; t += blockDim.x) {
+    const int i = t / COLS, c = c0 + t % COLS;
+    if (c < b) X[(int64_t)i * ld + c] = i < c0 ? 0.0 : xs[t];
   }
 }
 
@@ -866,10 +977,35 @@ void Store::invert_leaves(const std::vector<int>& leaves, cudaStream_t s) {
   DStore v = view();
   int bmax = 0;
   for (int j : leaves) bmax = std::max(bmax, tree.hi[leaf_nodes_h[j]] - tree.lo[leaf_nodes_h[j]]);
-  const size_t sh = (size_t)bmax * sizeof(double);
-  if (sh > 48 * 1024) EMT_CUDA(cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-  k_chol<<<nl, 1024, sh, s>>>(v, d_list.p);
-  k_trinv<<<dim3(nl, (bmax + 127) / 128), 128, 0, s>>>(v, W64.p, d_list.p);
+  // blocked Cholesky: panels of kCholNb columns (every launch sees the leaf list and skips leaves
+  // already done)
+  {
+    const size_t shp = (size_t)kCholRows * (kCholNb + 1) * sizeof(double);
+    if (shp > 48 * 1024)
+      EMT_CUDA(cudaFuncSetAttribute(k_chol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shp));
+    const size_t shu = (size_t)2 * 64 * (kCholNb + 1) * sizeof(double);
+    EMT_CUDA(cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu));
+    for (int kb = 0; kb < bmax; kb += kCholNb) {
+      k_chol_diag<<<nl, 256, 0, s>>>(v, d_list.p, kb);
+      const int rest = bmax - kb - kCholNb;
+      if (rest <= 0) continue;
+      k_chol_panel<<<dim3(nl, (rest + kCholRows - 1) / kCholRows), kCholRows, shp, s>>>(v, d_list.p, kb);
+      const int nt = (rest + 63) / 64;
+      k_chol_update<<<dim3(nl, nt * (nt + 1) / 2), 256, shu, s>>>(v, d_list.p, kb);
+    }
+  }
+  // 16 columns per CTA while their rows fit 200 KB of shared memory (leaves up to 1,600), else 8
+  EMT_REQUIRE(bmax <= 3200, EMT_ERR_UNSUPPORTED, "leaf larger than 3200 nodes");
+  if (bmax <= 1600) {
+    const size_t shx = (size_t)bmax * 16 * sizeof(double);
+    if (shx > 48 * 1024)
+      EMT_CUDA(cudaFuncSetAttribute(k_trinv_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shx));
+    k_trinv_block<16><<<dim3(nl, (bmax + 15) / 16), 256, shx, s>>>(v, W64.p, d_list.p);
+  } else {
+    const size_t shx = (size_t)bmax * 8 * sizeof(double);
+    EMT_CUDA(cudaFuncSetAttribute(k_trinv_block<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shx));
+    k_trinv_block<8><<<dim3(nl, (bmax + 7) / 8), 256, shx, s>>>(v, W64.p, d_list.p);
+  }
   k_wtw<<<dim3(nl, bmax), 256, 0, s>>>(v, W64.p, d_list.p);
   EMT_CUDA(cudaGetLastError());
 }
