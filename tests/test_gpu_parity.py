@@ -573,7 +573,7 @@ def _three_phase(levels=3):
 
 
 @pytest.mark.parametrize("npb", [1, 3])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_three_phase_store_matches_dense_solve(L, prec, npb):
     # 358 buses, 1,074 nodes: mutual couplings enter as negative node branches; npb 3 partitions
     # by bus with block cuts (the default), npb 1 node by node
@@ -633,6 +633,28 @@ def test_three_phase_line_trip_and_phase_fault_by_exact_node_updates(L, npb, cut
     L.emt_modify_branch(h, node, -1, 0.1)
     G = omod.modified_G(G, node, -1, 0.1)
     assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= 1e-10
+
+
+def test_block_paper_store_local_update_matches_algorithm2(L):
+    # Algorithm 2 on a block store: a cross-phase branch of a line cut at the root changes one
+    # entry of a block column; the GPU's literal Algorithm 2 equals the oracle's on the same tree
+    from oracle import partition as op
+    net, gr, G = _three_phase()
+    tree = op.build_block_tree(gr["n_bus"], gr["frm"], gr["to"], 3, levels=3)
+    H = ohinv.HInv(G, tree, gr["g"], ohinv.PAPER)
+    h = L.emt_build_hinv_from_network3(net, DT, levels=3, mode=1)
+    t = h.tree()
+    assert np.array_equal(t["perm"], tree["perm"])
+    # a cross-phase entry of a root block column that a coupled line fills
+    a, b = next((int(t["perm"][t["cut_a"][c] + w]), int(t["perm"][t["cut_b"][c]]))
+                for c in range(t["cut_ptr"][0], t["cut_ptr"][1]) for w in range(3)
+                if (t["cut_a"][c] + w) % 3 != t["cut_b"][c] % 3
+                and G[int(t["perm"][t["cut_a"][c] + w]), int(t["perm"][t["cut_b"][c]])] != 0.0)
+    delta = 0.5 * float(G[a, b])
+    L.emt_modify_branch(h, a, b, delta)
+    H2 = omod.algorithm2(H, gr["frm"], gr["to"], a, b, delta)
+    X = np.random.default_rng(26).standard_normal((gr["n_bus"], 2))
+    assert rel_err(_apply(L, h, X), H2.apply(X)) <= 1e-10
 
 
 def test_block_cuts_keep_buses_together_and_shrink_the_cut(L):
