@@ -160,6 +160,7 @@ class MSim {
   DevBuf<long long> path_fbase;
   std::vector<int> h_trip_step, h_trip_elem;
   bool z_ready = false;
+  bool any_change = false;   // some column has a change scheduled or admitted
   std::map<int, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;
 
