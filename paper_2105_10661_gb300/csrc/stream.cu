@@ -334,18 +334,26 @@ __global__ void __launch_bounds__(128) k_sweep_matrix(const typename Acc<PREC>::
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const T* Kr = K + (int64_t)(row < s_total ? row : 0) * ldk;
+  constexpr int kU = 18;   // loads in flight per lane (one pass for up to 576 cut rows)
+  // K does not depend on the kernels before this one: its first chunk is loaded while they finish
+  T kv[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int k = lane + 32 * u;
+    kv[u] = k < n_crow ? Kr[k] : T{};
+  }
   pdl_wait_s();
   stage_vec(yc, ycut_g, n_crow);
   __syncthreads();
   if (row >= s_total) return;
   A a, a2;
-  constexpr int kU = 18;   // loads in flight per lane (one pass for up to 576 cut rows)
   for (int base = 0; base < n_crow; base += 32 * kU) {
-    T kv[kU];
+    if (base > 0) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int k = base + lane + 32 * u;
-      kv[u] = k < n_crow ? Kr[k] : T{};
+      for (int u = 0; u < kU; ++u) {
+        const int k = base + lane + 32 * u;
+        kv[u] = k < n_crow ? Kr[k] : T{};
+      }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -390,29 +398,36 @@ __global__ void __launch_bounds__(256, 4) k_expand_stream(DStore st, const Strea
   const int j = st.pos_leaf[pp];
   const int lo = st.lo[st.leaf_node[j]];
   const int x0 = anc_ptr[j], x1 = valid ? anc_ptr[j + 1] : anc_ptr[j];
+  __syncthreads();
+  const T* F = Elem<PREC>::F(st);
+  // the factor rows do not depend on the kernels before this one: the first round of them is
+  // loaded while those finish
+  auto load_round = [&](int base, int xb, T (&f)[kMaxAnc][4]) {
+#pragma unroll
+    for (int u = 0; u < kMaxAnc; ++u) {
+      const int x = xb + u;
+      const bool ax = x < x1;
+      const StreamAnc r = an[ax ? x : x0];
+      const T* Fr = F + r.foff + (int64_t)(pp - lo) * r.kld;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int e = base + gl + kEL * m;
+        f[u][m] = (ax && e < r.k) ? Fr[e] : T{};
+      }
+    }
+  };
+  T f[kMaxAnc][4];
+  load_round(0, x0, f);
   pdl_wait_s();
   const X yp = ldcg(y + pp);   // in flight with the loads below
   stage_vec(ss, s_g, s_total);
   __syncthreads();
-  const T* F = Elem<PREC>::F(st);
   A a, a2;
   int kmax = 0;
   for (int x = x0; x < x1; ++x) kmax = max(kmax, an[x].k);
   for (int base = 0; base < kmax; base += 4 * kEL) {
     for (int xb = x0; xb < x1; xb += kMaxAnc) {
-      T f[kMaxAnc][4];
-#pragma unroll
-      for (int u = 0; u < kMaxAnc; ++u) {
-        const int x = xb + u;
-        const bool ax = x < x1;
-        const StreamAnc r = an[ax ? x : x0];
-        const T* Fr = F + r.foff + (int64_t)(pp - lo) * r.kld;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int e = base + gl + kEL * m;
-          f[u][m] = (ax && e < r.k) ? Fr[e] : T{};
-        }
-      }
+      if (base > 0 || xb > x0) load_round(base, xb, f);
 #pragma unroll
       for (int u = 0; u < kMaxAnc; ++u) {
         const int x = xb + u;
