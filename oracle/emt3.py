@@ -12,7 +12,11 @@ model. The readings here, with node = 3 bus + phase:
   * sources and loads are balanced: phase p lags phase 0 by 2 pi p / 3.
 
 A trip opens all three phases of a branch before the step is solved: its terms leave G, and its
-currents and histories are zeroed. G is the node-branch graph of companion.three_phase_graph.
+currents and histories are zeroed. A fault connects one node (a phase of a bus) to ground through
+R_f: FAULT_ON adds (1/R_f) e_x e_x^T to G before its step is solved, FAULT_OFF takes the oldest
+fault still on at that node back out (the single-phase semantics of emt.py, node by node; a
+three-phase fault is three node faults). G is the node-branch graph of
+companion.three_phase_graph.
 """
 from __future__ import annotations
 
@@ -22,6 +26,13 @@ from . import companion as cm
 from . import dense as _dense
 
 TRIP = 0
+FAULT_ON = 1
+FAULT_OFF = 2
+
+
+def fault_conductance(r_f: float) -> float:
+    """The conductance a fault through R_f adds to its node's diagonal of G (Sec. IV's change)."""
+    return 1.0 / r_f
 
 
 def phase_shift(p: int) -> float:
@@ -100,10 +111,16 @@ def simulate3(net: dict, dt: float, nsteps: int, events=(), monitor=None, init=N
     ev = sorted(events, key=lambda x: x[0])
     ei = 0
     v = np.zeros(3 * n)
+    faults = {} if init is None else {int(k): list(x) for k, x in init.get("faults", {}).items()}
+    for x, rs in faults.items():
+        for r in rs:
+            G[x, x] += fault_conductance(r)
+    if faults:
+        sol = _dense.DenseSolver(G)
     for s in range(nsteps):
         step = first_step + s
         while ei < len(ev) and ev[ei][0] == step:
-            _, kind, target, _ = ev[ei]
+            _, kind, target, value = ev[ei]
             if kind == TRIP and active[int(target)]:
                 e = int(target)
                 open_branch(e)
@@ -111,6 +128,17 @@ def simulate3(net: dict, dt: float, nsteps: int, events=(), monitor=None, init=N
                 active[e] = False
                 Ih[e] = 0.0
                 cur[e] = 0.0
+            elif kind == FAULT_ON:
+                x = int(target)
+                faults.setdefault(x, []).append(float(value))
+                G[x, x] += fault_conductance(float(value))
+                sol = _dense.DenseSolver(G)
+            elif kind == FAULT_OFF:
+                x = int(target)
+                if not faults.get(x):
+                    raise ValueError(f"FAULT_OFF at node {x} with no fault on")
+                G[x, x] -= fault_conductance(faults[x].pop(0))
+                sol = _dense.DenseSolver(G)
             ei += 1
         rhs = source_injection3(net, step * dt) - Ih_sh
         for e in np.flatnonzero(active):
@@ -129,4 +157,4 @@ def simulate3(net: dict, dt: float, nsteps: int, events=(), monitor=None, init=N
         i_sh = gsh * v + Ih_sh
         Ih_sh = -gsh * v - i_sh
         out[s] = v[mon]
-    return out, dict(v=v, cur=cur, Ih=Ih, Ih_sh=Ih_sh, active=active)
+    return out, dict(v=v, cur=cur, Ih=Ih, Ih_sh=Ih_sh, active=active, faults=faults)

@@ -742,6 +742,38 @@ def test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs(
         assert np.max(np.abs(got[:, p::3] - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+def test_three_phase_faults_without_mutual_are_single_phase_faults_on_one_copy():
+    # L_mut = 0 decouples the phases: a fault on phase p of a bus acts on the single-phase copy of
+    # phase p alone (emt.py's fault semantics, pinned by Kirchhoff balance); the other phases run
+    # as if there were no fault. Overlapping windows and a trip inside them included.
+    from oracle import emt3
+    net = _with_loads(netgen.small_network(13, 77))
+    net3 = netgen.three_phase(net)
+    net3["L_mut"] = np.zeros(len(net["br_a"]))
+    trip = 5
+    ev3 = [(40, emt3.FAULT_ON, 3 * 4 + 1, 10.0), (60, emt3.FAULT_ON, 3 * 9 + 1, 5.0), (70, emt3.TRIP, trip, 0.0),
+           (90, emt3.FAULT_OFF, 3 * 4 + 1, 0.0), (120, emt3.FAULT_OFF, 3 * 9 + 1, 0.0), (100, emt3.FAULT_ON, 3 * 2 + 2, 20.0)]
+    got, state = emt3.simulate3(net3, DT, 160, ev3)
+    assert state["faults"] == {13: [], 28: [], 8: [20.0]}
+    for p in range(3):
+        netp = dict(net)
+        netp["src_phi"] = np.asarray(net["src_phi"]) + (-2 * np.pi * p / 3)
+        netp["load_phi"] = np.asarray(net["load_phi"]) + (-2 * np.pi * p / 3)
+        ev1 = [(70, emt.TRIP, trip, 0.0)]
+        for st, kind, x, val in ev3:
+            if kind != emt3.TRIP and x % 3 == p:
+                ev1.append((st, emt.FAULT_ON if kind == emt3.FAULT_ON else emt.FAULT_OFF, x // 3, val))
+        ref, _ = emt.simulate(emt.Network(netp, DT, want_tree=False), 160, ev1)
+        assert np.max(np.abs(got[:, p::3] - ref)) <= 1e-12 * np.max(np.abs(ref)), p
+
+
+def test_three_phase_fault_cleared_where_none_is_on_is_rejected():
+    from oracle import emt3
+    net = netgen.three_phase(netgen.small_network(13, 77))
+    with pytest.raises(ValueError):
+        emt3.simulate3(net, DT, 20, [(5, emt3.FAULT_ON, 4, 10.0), (8, emt3.FAULT_OFF, 5, 0.0)])
+
+
 def test_three_phase_balanced_steady_state_uses_positive_sequence_inductance():
     # Balanced source (Rs) -> coupled RL branch -> bus 1 with a shunt C. Balanced currents sum to
     # zero, so L3 i = (L - L_mut) i per phase; the trapezoidal steady state is the phasor solution

@@ -235,6 +235,12 @@ def test_block_tree_with_a_dropped_bus_pair_is_caught(monkeypatch):
                             T.test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1])
 
 
+def test_three_phase_fault_with_r_f_as_its_conductance_is_caught(monkeypatch):
+    from oracle import emt3
+    monkeypatch.setattr(emt3, "fault_conductance", lambda r_f: r_f)
+    assert _some_pin_fails([T.test_three_phase_faults_without_mutual_are_single_phase_faults_on_one_copy])
+
+
 @pytest.mark.parametrize("case", ["none"])
 def test_the_pins_pass_without_a_mistake(case):
     # the control: with nothing planted, every pin used above passes
@@ -250,5 +256,6 @@ def test_the_pins_pass_without_a_mistake(case):
         lambda: T.test_bisection_reaches_brute_force_minimum("ladder", T._graph_ladder(6), 12),
         T.test_three_phase_stepping_without_mutual_is_three_shifted_single_phase_runs,
         T.test_block_tree_keeps_buses_together_and_factors_each_h_exactly,
+        T.test_three_phase_faults_without_mutual_are_single_phase_faults_on_one_copy,
         T.test_block_store_is_the_exact_inverse_and_paper_store_is_algorithm1,
         T.test_three_phase_balanced_steady_state_uses_positive_sequence_inductance])
