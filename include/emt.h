@@ -254,7 +254,10 @@ emt_status emt_sim_create(const emt_network* net, const emt_hinv_opts* opts, dou
  * I_h <- Y (v_e + ((2/dt) L3 - R I) i); RC branches, shunt capacitors and source resistances act on
  * each phase alone. FP64 or FF64 stores (EMT_ERR_UNSUPPORTED otherwise). The handle works with
  * emt_sim_schedule (EMT_EVENT_TRIP of a series branch opens its three phases: one exact local
- * update of the store per node branch of the line; other events EMT_ERR_UNSUPPORTED),
+ * update of the store per node branch of the line; EMT_EVENT_FAULT_ON / FAULT_OFF with target a
+ * node (3 bus + phase) connects it to ground through value = R_f ohm / takes the oldest fault still
+ * on at that node back out, each one exact local update; a three-phase fault is three node faults;
+ * a FAULT_OFF with no fault on at its node makes emt_step return EMT_ERR_STATE before any work),
  * emt_sim_monitor (node indices), emt_step, emt_sim_read (3 n_bus node voltages), emt_sim_reset,
  * emt_sim_stats and emt_sim_destroy. State starts at zero; sources are first evaluated at t = dt.
  * Synchronises `stream`. */

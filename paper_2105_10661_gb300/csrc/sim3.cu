@@ -11,6 +11,8 @@
 // FP64 (a few operations per node and branch per step); the apply runs in the store's precision.
 #include <algorithm>
 #include <cmath>
+#include <deque>
+#include <map>
 
 #include "sim3.h"
 
@@ -212,14 +214,58 @@ void Sim3::drop_graphs() {
 }
 
 void Sim3::schedule(int step, int kind, int target, double value, int column) {
-  (void)value;
   EMT_REQUIRE(step >= 1, EMT_ERR_INVALID, "event step must be >= 1");
   EMT_REQUIRE(step > cur_step, EMT_ERR_STATE, "event step already simulated");
   EMT_REQUIRE(column == -1, EMT_ERR_UNSUPPORTED, "three-phase simulations have one column");
-  EMT_REQUIRE(kind == EMT_EVENT_TRIP, EMT_ERR_UNSUPPORTED, "three-phase simulations take line trips only");
-  EMT_REQUIRE(target >= 0 && target < n_br, EMT_ERR_INVALID, "trip target must be a series branch");
-  events_.push_back({step, kind, target, 0.0, -1});
+  if (kind == EMT_EVENT_TRIP) {
+    EMT_REQUIRE(target >= 0 && target < n_br, EMT_ERR_INVALID, "trip target must be a series branch");
+  } else if (kind == EMT_EVENT_FAULT_ON) {
+    EMT_REQUIRE(target >= 0 && target < nn, EMT_ERR_INVALID, "fault target must be a node (3 bus + phase)");
+    EMT_REQUIRE(std::isfinite(value) && value > 0, EMT_ERR_INVALID, "fault resistance must be > 0");
+  } else {
+    EMT_REQUIRE(kind == EMT_EVENT_FAULT_OFF, EMT_ERR_INVALID, "unknown event kind");
+    EMT_REQUIRE(target >= 0 && target < nn, EMT_ERR_INVALID, "fault target must be a node (3 bus + phase)");
+  }
+  events_.push_back({step, kind, target, kind == EMT_EVENT_FAULT_ON ? value : 0.0, -1});
   std::stable_sort(events_.begin(), events_.end(), [](const Event& x, const Event& y) { return x.step < y.step; });
+}
+
+// A fault at a node connects it to ground through R_f: FAULT_ON adds 1/R_f to G's diagonal as
+// one exact local update (Sec. IV); FAULT_OFF takes the oldest fault still on at the node back
+// out with the opposite update (changes made while it was on stay in G).
+void Sim3::apply_event(const Event& ev, cudaStream_t s) {
+  if (ev.kind == EMT_EVENT_TRIP) {
+    apply_trip(ev.target, s);
+    return;
+  }
+  double delta;
+  if (ev.kind == EMT_EVENT_FAULT_ON) {
+    faults_on_[ev.target].push_back(ev.value);
+    delta = 1.0 / ev.value;
+  } else {
+    auto it = faults_on_.find(ev.target);
+    EMT_REQUIRE(it != faults_on_.end() && !it->second.empty(), EMT_ERR_STATE, "fault cleared where none is on");
+    delta = -1.0 / it->second.front();
+    it->second.pop_front();
+  }
+  store->modify_async(ev.target, -1, delta, s);
+  refresh_plan_values(*store, plan, s);
+  launches += 2;
+}
+
+// Every FAULT_OFF up to `last_step` must find a fault on at its node (checked before any work).
+void Sim3::check_fault_sequence(int last_step) const {
+  std::map<int, int> on;
+  for (const auto& kv : faults_on_) on[kv.first] = (int)kv.second.size();
+  for (size_t i = ev_cursor_; i < events_.size() && events_[i].step <= last_step; ++i) {
+    const Event& ev = events_[i];
+    if (ev.step <= cur_step) continue;
+    if (ev.kind == EMT_EVENT_FAULT_ON) ++on[ev.target];
+    if (ev.kind == EMT_EVENT_FAULT_OFF) {
+      EMT_REQUIRE(on[ev.target] > 0, EMT_ERR_STATE, "fault cleared where none is on");
+      --on[ev.target];
+    }
+  }
 }
 
 void Sim3::set_monitor(int nm, const int32_t* nodes) {
@@ -274,7 +320,7 @@ void Sim3::run(int n_steps, cudaStream_t s) {
   while (done < n_steps) {
     const int next = cur_step + 1;
     while (ev_cursor_ < events_.size() && events_[ev_cursor_].step < next) ++ev_cursor_;
-    while (ev_cursor_ < events_.size() && events_[ev_cursor_].step == next) apply_trip(events_[ev_cursor_++].target, s);
+    while (ev_cursor_ < events_.size() && events_[ev_cursor_].step == next) apply_event(events_[ev_cursor_++], s);
     int stretch = n_steps - done;
     if (ev_cursor_ < events_.size()) stretch = std::min(stretch, events_[ev_cursor_].step - next);
     stretch = std::max(stretch, 1);
@@ -303,6 +349,7 @@ void Sim3::run(int n_steps, cudaStream_t s) {
 void Sim3::step(int n_steps, double* record_dev, cudaStream_t s) {
   EMT_REQUIRE(n_steps >= 0, EMT_ERR_INVALID, "n_steps must be >= 0");
   if (n_steps == 0) return;
+  check_fault_sequence(cur_step + n_steps);
   std::vector<double> tr((size_t)2 * n_steps);
   for (int k = 0; k < n_steps; ++k) {
     const double t = (double)(cur_step + 1 + k) * dt;
@@ -342,6 +389,7 @@ void Sim3::reset(cudaStream_t s) {
   EMT_CUDA(cudaMemsetAsync(dyn_.p, 0, sizeof(Sim3Dyn), s));
   cur_step = 0;
   ev_cursor_ = 0;
+  faults_on_.clear();
   launches += 4;
 }
 

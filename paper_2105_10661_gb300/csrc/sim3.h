@@ -5,6 +5,8 @@
 // update. A line trip opens all three phases: exact local updates of the store (Sec. IV), one per
 // node branch of the line.
 #pragma once
+#include <deque>
+#include <map>
 #include <memory>
 #include <vector>
 
@@ -46,12 +48,15 @@ class Sim3 {
   void run(int n_steps, cudaStream_t s);
   void launch_step(cudaStream_t s);
   void apply_trip(int e, cudaStream_t s);
+  void apply_event(const Event& ev, cudaStream_t s);
+  void check_fault_sequence(int last_step) const;
   void drop_graphs();
 
   std::vector<int32_t> gf_, gt_;
   std::vector<double> gv_;
   std::vector<int> br_ptr_, active_h_;
   std::vector<Event> events_;
+  std::map<int, std::deque<double>> faults_on_;   // node -> R_f of the faults on, oldest first
   size_t ev_cursor_ = 0;
   Snapshot base_;
   DevBuf<int> br_a_, br_b_, br_sgn_, active_, inc_ptr_, inc_br_, inc_sgn_, term_ptr_, mon_;

@@ -741,14 +741,44 @@ def test_three_phase_stepping_1432_buses_matches_oracle(L):
     assert rel_err(got, ref) <= 1e-10, rel_err(got, ref)
 
 
+@pytest.mark.parametrize("npb", [1, 3])
+def test_three_phase_faults_and_a_trip_match_oracle(L, npb):
+    # a phase-a fault at one bus, a three-phase fault (three node faults) at another overlapping it,
+    # a coupled-line trip inside both windows; each clearing takes only its own fault back out
+    from oracle import emt3 as oemt3
+    net = netgen.three_phase(netgen.add_loads(netgen.tile(1_000_000), seed=3))
+    e = next(k for k in range(len(net["br_a"])) if net["kind"][k] == 0 and net["L_mut"][k] > 0)
+    ev = ([(30, oemt3.FAULT_ON, 3 * 17 + 0, 10.0)] + [(45, oemt3.FAULT_ON, 3 * 60 + p, 5.0) for p in range(3)]
+          + [(55, oemt3.TRIP, e, 0.0), (70, oemt3.FAULT_OFF, 3 * 17 + 0, 0.0)]
+          + [(90, oemt3.FAULT_OFF, 3 * 60 + p, 0.0) for p in range(3)])
+    ref, _ = oemt3.simulate3(net, DT, 120, ev)
+    sim = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FF64, nodes_per_bus=npb)
+    L.emt_sim_monitor(sim, np.arange(3 * net["n_bus"]))
+    for st, kind, target, value in ev:
+        L.emt_sim_schedule(sim, st, kind, target, value)
+    rec = torch.zeros(120, 3 * net["n_bus"], dtype=torch.float64, device="cuda")
+    L.emt_step(sim, 50, rec[:50])
+    L.emt_step(sim, 70, rec[50:])
+    torch.cuda.synchronize()
+    assert rel_err(rec.cpu().numpy(), ref) <= 1e-10
+
+
 def test_three_phase_reset_repeats_and_rejects_other_events(L):
     net = netgen.three_phase(netgen.tile(1_000_000))
     sim = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FF64)
     L.emt_sim_monitor(sim, np.arange(0, 3 * net["n_bus"], 7))
     L.emt_sim_schedule(sim, 30, 0, 3)
     with pytest.raises(L.EmtError) as ex:
-        L.emt_sim_schedule(sim, 40, 1, 5, 10.0)
+        L.emt_sim_schedule(sim, 40, 1, 5, 10.0, column=3)
     assert ex.value.code == L.EMT_ERR_UNSUPPORTED
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_sim_schedule(sim, 40, 1, 3 * net["n_bus"], 10.0)
+    assert ex.value.code == L.EMT_ERR_INVALID
+    bad = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FF64)
+    L.emt_sim_schedule(bad, 10, 2, 4)   # a clearing with no fault on: refused before any work
+    with pytest.raises(L.EmtError) as ex:
+        L.emt_step(bad, 20, None)
+    assert ex.value.code == L.EMT_ERR_STATE
     a = torch.zeros(80, sim.n_mon, dtype=torch.float64, device="cuda")
     b = torch.zeros_like(a)
     L.emt_step(sim, 80, a)
