@@ -107,8 +107,8 @@ void step3_launch_any(Sim& sm, int n, cudaStream_t s);
 // Kernel generation 4 (step4.cu): the whole time loop in one persistent thread-block cluster.
 struct Step4D {
   int C, P;         // CTAs in the cluster; most CTAs sharing one leaf
-  int o_x, o_part, o_ycp, o_ycut, o_yvp, o_s, o_v, o_contrib, o_row, o_vrow, o_out, o_push, o_img, o_K, o_L, o_F;
-  int max_vrows, img_int_bytes, ldk, n_crow, fstride, s_total;
+  int o_x, o_part, o_ycp, o_ycut, o_yvp, o_s, o_v, o_contrib, o_row, o_vrow, o_out, o_push, o_sx, o_K, o_L, o_F;
+  int max_vrows, e_max, ldk, n_crow, fstride, s_total;
   const int* hdr;   // [C][24] per-CTA header
   const int* tab;   // per-CTA tables
   const double* K;  // [s_total][ldk] matrix of the boundary sweep (8-byte elements)
@@ -119,8 +119,8 @@ struct Step4 {
   int C = 0, P = 1;
   size_t smem = 0;
   size_t o_x = 0, o_part = 0, o_ycp = 0, o_ycut = 0, o_yvp = 0, o_s = 0, o_v = 0, o_contrib = 0, o_row = 0,
-         o_vrow = 0, o_out = 0, o_push = 0, o_img = 0, o_K = 0, o_L = 0, o_F = 0;
-  int max_vrows = 0, img_int_bytes = 0, ldk = 0, n_crow = 0, s_total = 0, fstride = 0;
+         o_vrow = 0, o_out = 0, o_push = 0, o_sx = 0, o_K = 0, o_L = 0, o_F = 0;
+  int max_vrows = 0, e_max = 0, ldk = 0, n_crow = 0, s_total = 0, fstride = 0;
   DevBuf<int> hdr, tab;
   DevBuf<double> K;        // s = K y_cut (FP64 or float-float pairs)
   DevBuf<float2> rec_ff;   // float-float record of one launch, converted to FP64 afterwards

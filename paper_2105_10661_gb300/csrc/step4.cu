@@ -53,7 +53,8 @@ constexpr long long kWait4 = 4000000000LL;   // ~2 s of SM clock
 
 // header fields
 enum { H_P0, H_P1, H_NHALO, H_M0, H_M1, H_LBYTES, H_OLROW, H_NFC, H_OFC, H_OROW, H_OVROW, H_NOUT, H_OOUT, H_NPUSH,
-       H_OPUSH, H_OENDL, H_S0, H_S1, H_LP, H_YIN };   // H_YIN: partials this CTA receives per step
+       H_OPUSH, H_OENDL, H_S0, H_S1, H_LP, H_YIN, H_OSX, H_NSX };   // H_YIN: partials this CTA receives per step;
+                                                                    // H_OSX, H_NSX: its s-index lists
 // own-row record fields (injection)
 enum { R_ELO, R_EHI, R_MON };
 // push kinds: partial of an expansion row (double-buffered by step parity) or of a cut row
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   int* vrow = reinterpret_cast<int*>(sm4 + d.o_vrow);
   int* outi = reinterpret_cast<int*>(sm4 + d.o_out);
   int* push = reinterpret_cast<int*>(sm4 + d.o_push);
-  const int* II = reinterpret_cast<const int*>(sm4 + d.o_img);
+  int* sxs = reinterpret_cast<int*>(sm4 + d.o_sx);       // s index of every factor-row element, per leaf
   T* Ks = reinterpret_cast<T*>(sm4 + d.o_K);
   T* Ls = reinterpret_cast<T*>(sm4 + d.o_L);
   T* Fs = reinterpret_cast<T*>(sm4 + d.o_F);
@@ -209,8 +210,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   const T* Kg = reinterpret_cast<const T*>(d.K);
   const int* tab = d.tab;
 
-  // ---- prologue: bulk copies of the leaf rows (one per row) and of the integer part of the
-  //      sweep image (ancestor lists) ...
+  // ---- prologue: bulk copies of the leaf rows (one per row) ...
   if (tid < 32) {
     if (tid == 0) {
       mbar_init4(sbar);
@@ -218,15 +218,18 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       mbar_init4(ybar);
       mbar_init4(ybar + 1);
       mbar_init4(bar);
-      mbar_expect4(bar, (uint32_t)hd[H_LBYTES] + (uint32_t)d.img_int_bytes);
-      bulk4(sm4 + d.o_img, q.img, (uint32_t)d.img_int_bytes, bar);
+      mbar_expect4(bar, (uint32_t)hd[H_LBYTES]);
     }
     __syncwarp();
     const int* lr = tab + hd[H_OLROW];
     for (int r = tid; r < nrow; r += 32)
       bulk4(Ls + lr[3 * r + 1], Lg + lr[3 * r], (uint32_t)lr[3 * r + 2] * (uint32_t)sizeof(T), bar);
   }
-  // ... plain loads of the tables, the factor rows, this CTA's rows of K and the state
+  // ... plain loads of the tables, the factor rows (negated, each row's elements of all its
+  // ancestors packed back to back and zero up to the longest such row), this CTA's rows of K and
+  // the state
+  for (int i = tid; i < d.e_max * d.fstride; i += kT4) Fs[i] = T{};
+  __syncthreads();
   {
     const int* src = tab + hd[H_OROW];
     for (int i = tid; i < nrow * kRI; i += kT4) {
@@ -244,8 +247,10 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
     const int warp = tid >> 5, lane = tid & 31;
     for (int u = warp; u < hd[H_NFC]; u += kT4 / 32) {
       const int so = fc[3 * u], dst = fc[3 * u + 1], len = fc[3 * u + 2];
-      for (int e = lane; e < len; e += 32) Fs[dst + (int64_t)e * d.fstride] = Fg[so + e];
+      for (int e = lane; e < len; e += 32) Fs[dst + (int64_t)e * d.fstride] = neg(Fg[so + e]);
     }
+    src = tab + hd[H_OSX];
+    for (int i = tid; i < hd[H_NSX]; i += kT4) sxs[i] = src[i];
     for (int i = tid; i < ns * ldk; i += kT4) Ks[i] = Kg[(int64_t)s0 * ldk + i];
     // partial slots a CTA never receives (leaves split into fewer than P parts) stay zero
     for (int i = tid; i < n_crow * P; i += kT4) ycp[i] = A::zero();
@@ -312,9 +317,6 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   const int rec_first = sim.dyn->rec_first;
   double* rec = sim.dyn->rec;
   const int n_mon = sim.n_mon;
-  const ImgHeader* IH = reinterpret_cast<const ImgHeader*>(II);
-  const int* anc_ptr = II + IH->off_anc_ptr;
-  const int* anc = II + IH->off_anc;
   X sx = A::zero(), cx = A::zero();
   if (tid < nrow && n_steps > 0) trig_x(q, step0 + 1 - trig_first, sx, cx);
 
@@ -446,31 +448,28 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       flag[2] = 1;
     }
     __syncthreads();
-    // 4. expansion of own and halo rows: v = y - sum over ancestors of F row . s(half)
+    // 4. expansion of own and halo rows: v = y - sum over ancestors of F row . s(half), as one
+    //    dot of the row's packed (negated) factor elements with the entries of s its leaf's list
+    //    names; every row has e_max elements (zero past its own), so the lanes of a warp run
+    //    loops of one length
     const X* yv = yvp + par * yv_half;
+    const int e_max = d.e_max, fs = d.fstride;
     for (int base = 0; base < nv; base += ng_e) {
       if (base + wg_e >= nv) break;
       const int i = base + grp_e;
       A a, a2;   // two accumulators: half-length dependent chains
-      const int* vr = vrow + kVR * (i < nv ? i : 0);
       if (i < nv) {
-        const int pos = vr[0], j = vr[2];
         // factor rows are stored element-major (element e of row i at e * fstride + i), so the
         // lanes of a warp, which take consecutive rows, read consecutive words
         const T* Fr = Fs + i;
-        const int fs = d.fstride;
-        for (int x = anc_ptr[j]; x < anc_ptr[j + 1]; ++x) {
-          const int* an = anc + 5 * x;
-          const int k = an[0];
-          const int si = pos < an[2] ? an[3] : an[4];
-          int e = gl_e;
-          for (; e + le < k; e += 2 * le) {
-            a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
-            a2.fma(Fr[(int64_t)(e + le) * fs], neg(ssp[si + e + le]));
-          }
-          if (e < k) a.fma(Fr[(int64_t)e * fs], neg(ssp[si + e]));
-          Fr += (int64_t)an[1] * fs;
+        const int* sx = sxs + vrow[kVR * i + 2];
+        int e = gl_e;
+#pragma unroll 2
+        for (; e + le < e_max; e += 2 * le) {
+          a.fma(Fr[e * fs], ssp[sx[e]]);
+          a2.fma(Fr[(e + le) * fs], ssp[sx[e + le]]);
         }
+        if (e < e_max) a.fma(Fr[e * fs], ssp[sx[e]]);
         a.add(a2.getx());
       }
       const X w = group_sum<PREC>(a, le);
@@ -594,13 +593,13 @@ Step4D Step4::view() const {
   v.o_vrow = (int)o_vrow;
   v.o_out = (int)o_out;
   v.o_push = (int)o_push;
-  v.o_img = (int)o_img;
+  v.o_sx = (int)o_sx;
   v.o_K = (int)o_K;
   v.o_L = (int)o_L;
   v.o_F = (int)o_F;
   v.fstride = fstride;
   v.max_vrows = max_vrows;
-  v.img_int_bytes = img_int_bytes;
+  v.e_max = e_max;
   v.ldk = ldk;
   v.n_crow = n_crow;
   v.hdr = hdr.p;
@@ -735,15 +734,17 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     return false;
   };
   // ---- sizes
+  // elements of a position's packed factor row: k of every ancestor (the P or Q row of Eq. 9)
   auto frow = [&](int ps) {
     int64_t e = 0;
-    for (int a = t.parent[st.leaf_nodes_h[leaf_of(ps)]]; a >= 0; a = t.parent[a]) e += st.node_kld_h[a];
+    for (int a = t.parent[st.leaf_nodes_h[leaf_of(ps)]]; a >= 0; a = t.parent[a]) e += st.node_k_h[a];
     return e;
   };
   std::vector<int> n_out(n_cta, 0), lpv(n_cta, 1), n_push(n_cta, 0);
   int max_rows = 0, max_ends = 0, max_out = 0, max_push = 0, max_part = 0;
   int64_t maxL = 0, maxF = 0;
-  int max_packed = 0;   // longest packed factor row (sum of kld over a path)
+  int max_packed = 0;   // longest packed factor row (sum of k over a path)
+  int max_sx = 0;       // longest s-index table of a CTA (one list of max_packed per leaf it expands rows of)
   max_vrows = 0;
   for (int c = 0; c < n_cta; ++c) {
     const int nr = cp1[c] - cp0[c];
@@ -760,6 +761,13 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
     maxF = std::max(maxF, Fe);
     for (int ps = cp0[c]; ps < cp1[c]; ++ps) max_packed = std::max(max_packed, (int)frow(ps));
     for (int ps : halo[c]) max_packed = std::max(max_packed, (int)frow(ps));
+    {
+      std::vector<int> lv;
+      for (int ps = cp0[c]; ps < cp1[c]; ++ps) lv.push_back(leaf_of(ps));
+      for (int ps : halo[c]) lv.push_back(leaf_of(ps));
+      std::sort(lv.begin(), lv.end());
+      max_sx = std::max(max_sx, (int)(std::unique(lv.begin(), lv.end()) - lv.begin()));
+    }
     for (int j = cj0[c]; j < cj1[c]; ++j) {
       n_out[c] += lb[j];
       for (int r = 0; r < lb[j]; ++r) {
@@ -778,8 +786,8 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
   if (max_ends > kEPT * kT4 || max_rows > kT4) return false;
   // ---- shared-memory layout (identical in every CTA, so a remote address is the local one)
   const size_t tb = 8;   // FP64 or float-float element
-  const ImgHeader& Hh = s2.header;
-  img_int_bytes = Hh.int_words * 4;
+  e_max = max_packed;
+  max_sx *= max_packed;
   size_t off = 64;   // mbarriers (prologue, s x 2, partials x 2) and flags
   o_x = off;         off = align16(off + (size_t)std::max(max_rows, 1) * tb);
   o_part = off;      off = align16(off + (size_t)max_part * tb);
@@ -793,7 +801,7 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
   o_vrow = off;      off = align16(off + (size_t)max_vrows * kVR * 4);
   o_out = off;       off = align16(off + (size_t)std::max(max_out, 1) * kOR * 4);
   o_push = off;      off = align16(off + (size_t)std::max(max_push, 1) * kPR * 4);
-  o_img = off;       off = align16(off + (size_t)img_int_bytes);
+  o_sx = off;        off = align16(off + (size_t)std::max(max_sx, 1) * 4);
   o_K = off;         off = align16(off + (size_t)max_slice * ldk * tb);
   o_L = off;         off = align16(off + (size_t)maxL * tb);
   // element-major factor rows: stride = 8 (mod 16) elements, so two 8-byte columns of one warp
@@ -834,29 +842,46 @@ bool Step4::build(Sim& sm, int n_cta, cudaStream_t s) {
       dst += lld[j];
     }
     h[H_LBYTES] = (int)lbytes;
-    // expansion rows (own, then halo) and their packed factor rows
+    // expansion rows (own, then halo) and their packed factor rows: the k elements of the
+    // position's row of P (left child) or Q (right child) at every ancestor, back to back; all
+    // rows of one leaf sit in the same child of each ancestor, so they share one list of the
+    // entries of s that those elements multiply (padded with entry 0 up to e_max)
     std::vector<int> vpos;
     for (int ps = cp0[c]; ps < cp1[c]; ++ps) vpos.push_back(ps);
     for (int ps : halo[c]) vpos.push_back(ps);
-    std::vector<int> vr, fc;
+    std::vector<int> vr, fc, sxl, sx_at(nl, -1);
     for (size_t i = 0; i < vpos.size(); ++i) {
       const int ps = vpos[i];
       int64_t fdst = 0;   // element offset within the row's packed sequence
       const int j = leaf_of(ps);
+      if (sx_at[j] < 0) {
+        sx_at[j] = (int)sxl.size();
+        const int leaf_lo = t.lo[st.leaf_nodes_h[j]];
+        for (int a = t.parent[st.leaf_nodes_h[j]]; a >= 0; a = t.parent[a]) {
+          const int k = st.node_k_h[a];
+          const int si = leaf_lo < t.hi[t.left[a]] ? st.node_soff_h[a] : st.node_soff_h[a] + k;
+          for (int e = 0; e < k; ++e) sxl.push_back(si + e);
+        }
+        sxl.resize((size_t)sx_at[j] + e_max, 0);
+      }
       vr.push_back(ps);
       vr.push_back((int)i);
-      vr.push_back(j);
+      vr.push_back(sx_at[j]);
       vr.push_back(i < (size_t)nr ? (int)i : -1);
       for (int a = t.parent[st.leaf_nodes_h[j]]; a >= 0; a = t.parent[a]) {
-        const int kld = st.node_kld_h[a];
-        if (kld > 0) {
+        const int k = st.node_k_h[a], kld = st.node_kld_h[a];
+        if (k > 0) {
           fc.push_back((int)(st.node_foff_h[a] + (int64_t)(ps - t.lo[a]) * kld));
           fc.push_back((int)(fdst * fstride + (int64_t)i));
-          fc.push_back(kld);
+          fc.push_back(k);
         }
-        fdst += kld;
+        fdst += k;
       }
     }
+    if ((int)sxl.size() > max_sx) return false;   // cannot happen: one list per distinct leaf
+    h[H_OSX] = (int)TB.size();
+    h[H_NSX] = (int)sxl.size();
+    TB.insert(TB.end(), sxl.begin(), sxl.end());
     h[H_NFC] = (int)fc.size() / 3;
     h[H_OFC] = (int)TB.size();
     TB.insert(TB.end(), fc.begin(), fc.end());
