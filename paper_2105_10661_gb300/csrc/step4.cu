@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm4);        // prologue copies
   uint64_t* sbar = reinterpret_cast<uint64_t*>(sm4 + 8);    // [2] by step parity: slices of s from the other CTAs
   uint64_t* ybar = reinterpret_cast<uint64_t*>(sm4 + 24);   // [2] by step parity: leaf-stage partials pushed here
-  int* flag = reinterpret_cast<int*>(sm4 + 40);             // [0] own ok, [1] cluster ok, [2] a data wait failed
+  int* flag = reinterpret_cast<int*>(sm4 + 40);             // [0] own ok, [1] cluster ok
   const int tid = threadIdx.x;
   const int C = d.C, P = d.P;
   const int rank = C > 1 ? (int)cta_rank4() : 0;
@@ -293,7 +293,6 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       mbar_wait4(bar, kWait4);   // give copies in flight a second bounded chance
     }
     flag[0] = (ok && *reinterpret_cast<volatile int*>(st.status) == DEV_OK) ? 1 : 0;
-    flag[2] = 0;
   }
   if (C > 1) cluster_barrier(); else __syncthreads();
   if (tid == 0) {
@@ -326,6 +325,7 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
   // because every CTA sends its slice of s to every CTA: a CTA that holds all slices of step t
   // knows every CTA has finished step t - 1's expansion (the double-buffered partials and s of
   // that parity) and step t's cut-row reads, and the phases of one parity never overlap.
+  bool dead = false;   // thread 0: a data wait ran out
   const uint32_t y_bytes = (uint32_t)hd[H_YIN] * (uint32_t)sizeof(X);
   const uint32_t s_bytes = (uint32_t)((d.s_total - ns) * (int)sizeof(X));
   for (int it = 0; it < n_steps; ++it) {
@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
       if (pr[1] == rank) *reinterpret_cast<X*>(sm4 + off) = y;
       else st_async(mapa4(sa4(sm4) + off, (uint32_t)pr[1]), y, mapa4(sa4(ybar + par), (uint32_t)pr[1]));
     }
-    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(ybar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
+    if (C > 1 && tid == 0 && !dead && !mbar_wait4(ybar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
       atomicExch(st.status, DEV_TIMEOUT);   // partials never arrived: report and stop waiting
-      flag[2] = 1;
+      dead = true;
     }
     __syncthreads();
     // 3. cut-row values, then this CTA's slice of s = K y_cut, sent to every other CTA
@@ -442,10 +442,10 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
           else st_async(mapa4(sa4(&ssp[s0 + i]), (uint32_t)c), sv, mapa4(sa4(sbar + par), (uint32_t)c));
         }
     }
-    if (C > 1 && tid == 0 && !flag[2] && !mbar_wait4(sbar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
+    if (C > 1 && tid == 0 && !dead && !mbar_wait4(sbar + par, kWait4, (uint32_t)((it >> 1) & 1))) {
       // a slice never arrived: report it and stop waiting (the results are void)
       atomicExch(st.status, DEV_TIMEOUT);
-      flag[2] = 1;
+      dead = true;
     }
     __syncthreads();
     // 4. expansion of own and halo rows: v = y - sum over ancestors of F row . s(half), as one
@@ -485,7 +485,11 @@ __global__ void __launch_bounds__(kT4, 1) k_step4(DStore st, SimD sim, Step2D q,
         }
       }
     }
-    __syncthreads();
+    // After a wait ran out (thread 0 only waits) the CTA leaves the step loop at the end of that
+    // step: it arms no mbarrier again (a second arrival on a phase that never completed is
+    // undefined) and pushes nothing more, so its peers' waits run out too and every CTA meets at
+    // the exit barrier.
+    if (__syncthreads_or(dead)) break;
   }
   // no CTA leaves while another may still write into its shared memory
   if (C > 1) cluster_barrier();
