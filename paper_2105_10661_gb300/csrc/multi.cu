@@ -56,6 +56,11 @@ struct Acc2 {
   __device__ __forceinline__ float2 get() const { return ff_n(s, c); }
 };
 __device__ __forceinline__ Acc2 acc2(float2 x) { return Acc2{x.x, x.y}; }
+// a b as an (unnormalised) pair: what add_prod gives on a zero accumulator, without its TwoSum
+__device__ __forceinline__ Acc2 acc2_prod(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  return Acc2{p, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)))};
+}
 
 float2 host_ff(double x) {
   const float h = (float)x;
@@ -147,8 +152,7 @@ __global__ void __launch_bounds__(ITH, 4) k_mc_inject(MSimD m, int ipp, int s_in
         de.add(-vt.x, -vt.y);
         const float2 ve = make_float2(de.s, de.c);
         // Ih' = a1 v_e + beta Ih, renormalised once (it is state)
-        Acc2 h{0.f, 0.f};
-        h.add_prod(r.a1, ve);
+        Acc2 h = acc2_prod(r.a1, ve);
         h.add_prod(r.beta, ih[q]);
         float2 ihn = h.get();
         if (r.elem == te) ihn = ff_f(0.f);   // the tripped element carries no current
@@ -255,8 +259,7 @@ __global__ void __launch_bounds__(ITH, MINB) k_mc_inject2(MSimD m, int ipp, int 
           de.add(-vt.x, -vt.y);
           const float2 ve = make_float2(de.s, de.c);
           // Ih' = a1 v_e + beta Ih, renormalised once (it is state)
-          Acc2 h{0.f, 0.f};
-          h.add_prod(r.a1, ve);
+          Acc2 h = acc2_prod(r.a1, ve);
           h.add_prod(r.beta, ih[q][j]);
           ihn[j] = r.elem == te[j] ? ff_f(0.f) : h.get();   // the tripped element carries no current
           if (r.sgn > 0) hist[j].add(-ihn[j].x, -ihn[j].y);
