@@ -712,6 +712,71 @@ __global__ void __launch_bounds__(ITH) k_mc_residual(MSimD m, int ipp, int n1, i
   }
 }
 
+// The residual with two adjacent columns per thread (even column stride, 32-bit offsets): each
+// CSR entry is read from shared memory once for both columns and the two columns' voltages come in
+// one 16-byte load. Same arithmetic per column as k_mc_residual, so the results agree bit for bit.
+__global__ void __launch_bounds__(ITH) k_mc_residual2(MSimD m, int ipp, int n1, int s_in_chunk, const int* status) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  __shared__ int sptr[IPP_MAX + 1];
+  if (*status != DEV_OK) return;   // uniform, before any barrier
+  const int p0 = blockIdx.x * ipp, np = min(ipp, m.n - p0);
+  const int tid = threadIdx.x, c = 2 * (blockIdx.y * ITH + tid);
+  if (tid <= np) sptr[tid] = m.csr_ptr[p0 + tid];
+  __syncthreads();
+  const int r0 = sptr[0], nnz = sptr[np] - r0;
+  float2* sval = reinterpret_cast<float2*>(rsm);
+  int* scol = reinterpret_cast<int*>(rsm + (size_t)nnz * sizeof(float2));
+  for (int i = tid; i < nnz; i += ITH) {
+    sval[i] = m.csr_ff[r0 + i];
+    scol[i] = m.csr_col[r0 + i];
+  }
+  __syncthreads();
+  if (c >= m.R_act) return;
+  const bool both = c + 1 < m.R_act;   // column c + 1 < R exists (R even) even when it is not in use
+  const int R32 = m.R;
+  const int step = m.dyn->step_base + s_in_chunk + 1;
+  const bool on[2] = {n1 && change_on(m, c, step), both && n1 && change_on(m, c + 1, step)};
+  const float2* Vc = m.V + c;
+  for (int pi = 0; pi < np; ++pi) {
+    const int pos = p0 + pi;
+    const int k1 = sptr[pi + 1] - r0;
+    int kb = sptr[pi] - r0;
+    float2 xv[2];
+    ld_pair(m.X + pos * R32 + c, xv);
+    Acc2 ra[2] = {acc2(xv[0]), acc2(xv[1])};
+    while (kb < k1) {
+      float2 v[RKB][2];
+#pragma unroll
+      for (int q = 0; q < RKB; ++q)
+        if (kb + q < k1) ld_pair(Vc + scol[kb + q] * R32, v[q]);
+#pragma unroll
+      for (int q = 0; q < RKB; ++q) {
+        if (kb + q >= k1) break;
+        const float2 g = ff_negx(sval[kb + q]);
+        ra[0].add_prod(g, v[q][0]);
+        ra[1].add_prod(g, v[q][1]);
+      }
+      kb += RKB;
+    }
+    float2 r[2] = {ra[0].get(), ra[1].get()};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (!on[j]) continue;
+      const int cj = c + j;
+      const int a = m.trip_a[cj], b = m.trip_b[cj];
+      if (pos == a || pos == b) {
+        // (G' v)_i = (G v)_i + delta u_i (v_a - v_b)
+        float2 du = m.V[(int64_t)a * R32 + cj];
+        if (b >= 0) du = ff_subx(du, m.V[(int64_t)b * R32 + cj]);
+        const float2 dl = ff_mulx(m.trip_delta_ff[cj], du);
+        r[j] = pos == a ? ff_subx(r[j], dl) : ff_addx(r[j], dl);
+      }
+    }
+    if (both) *reinterpret_cast<float2*>(m.Xf + pos * R32 + c) = make_float2(r[0].x, r[1].x);
+    else m.Xf[pos * R32 + c] = r[0].x;
+  }
+}
+
 // d_c = 1 + delta_c u_c^T z_c (FP64) and the Sherman-Morrison factor delta_c / d_c (Sec. IV)
 __global__ void k_mc_trip_coef(MSimD m, double* coef, int* status) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -969,8 +1034,10 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
       EMT_CUDA(cudaFuncSetAttribute(k_mc_inject2<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inj_smem));
     }
 
-    if (res_smem > 48 * 1024)
+    if (res_smem > 48 * 1024) {
       EMT_CUDA(cudaFuncSetAttribute(k_mc_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
+      EMT_CUDA(cudaFuncSetAttribute(k_mc_residual2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
+    }
     int dev = 0;
     EMT_CUDA(cudaGetDevice(&dev));
     EMT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -1399,6 +1466,12 @@ int MSim::positions_per_cta(int cols_per_thread, int ctas_per_sm) const {
 
 void MSim::launch_residual(int n1, int s_in_chunk, cudaStream_t s) {
   const MSimD d = view();
+  if (inj_pairs) {
+    const int ipp = positions_per_cta(2, 4);
+    k_mc_residual2<<<dim3((n + ipp - 1) / ipp, (R_act + 2 * ITH - 1) / (2 * ITH)), ITH, res_smem, s>>>(
+        d, ipp, n1, s_in_chunk, store->d_status.p);
+    return;
+  }
   const int ipp = positions_per_cta();
   k_mc_residual<<<dim3((n + ipp - 1) / ipp, (R_act + ITH - 1) / ITH), ITH, res_smem, s>>>(d, ipp, n1, s_in_chunk,
                                                                                         store->d_status.p);
