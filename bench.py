@@ -695,7 +695,7 @@ def multi_arm(args, cfg: int):
         "expansion (tcgen05 k_mc_umma<expand> when it has a tile per SM, else SIMT k_mc_expand_tiled)":
             (kus[3], 2, "hbm", n * Rl * 20 / 1e9, hbm, "GB/s"),
         inject_name(st): (kus[4], 1, "hbm", inj_bytes / 1e9, hbm, "GB/s"),
-        "k_mc_residual (float-float r = x - G'v)": (kus[5], 1, "hbm", res_bytes / 1e9, hbm, "GB/s"),
+        residual_name(st): (kus[5], 1, "hbm", res_bytes / 1e9, hbm, "GB/s"),
     }
     kernels = {}
     my_ms = float(np.mean(times))
@@ -743,10 +743,17 @@ def inject_name(st):
     return "k_mc_inject (histories + injection, float-float)"
 
 
-# DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu --set full
-# capture of the kernel as it stands (python bench.py --config 4 --profile 6, third launch of each)
-NCU_TRAFFIC = {("k_mc_inject2<2,4>", 11456, 512): 212.473856e6 + 148.755968e6,
-               ("k_mc_residual", 11456, 512): 94.541056e6 + 10.648576e6}
+def residual_name(st):
+    if st["residual_columns_per_thread"] == 2:
+        return "k_mc_residual2 (float-float r = x - G'v, two columns per thread)"
+    return "k_mc_residual (float-float r = x - G'v)"
+
+
+# DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu capture of
+# dram__bytes_read.sum and dram__bytes_write.sum of the kernel as it stands (python bench.py
+# --config 4 --profile 6, third launch of each; profiles/multi_column_11456bus_512col_*_ncu_*.md)
+NCU_TRAFFIC = {("k_mc_inject2<2,4>", 11456, 512): 212.550400e6 + 148.302080e6,
+               ("k_mc_residual2", 11456, 512): 94.539264e6 + 9.608960e6}
 
 
 def ncu_traffic(kernel, n, cols):

@@ -361,7 +361,8 @@ def emt_sim_reset(s: Sim, stream=None):
 
 
 STAT_KEYS = ("n_bus", "n_leaf", "leaf_elems", "factor_elems", "core_elems", "n_cta", "n_incidence", "n_cut_rows",
-             "s_total", "launches", "n_series", "n_elements", "inject_columns_per_thread", "inject_variant")
+             "s_total", "launches", "n_series", "n_elements", "inject_columns_per_thread", "inject_variant",
+             "residual_columns_per_thread")
 
 
 def emt_sim_stats(s: Sim):

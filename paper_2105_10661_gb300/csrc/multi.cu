@@ -1754,7 +1754,7 @@ void MSim::stats(int64_t* out, int n_out) const {
     core += 4 * k * k;
   }
   const int64_t v[] = {n, st.n_leaf, leaf, fac, core, n_tiles, n_inc, n_crow, st.s_total, launches, n_series,
-                       (int64_t)el_a.size(), inject_pairs() ? 2 : 1, inject_variant()};
+                       (int64_t)el_a.size(), inject_pairs() ? 2 : 1, inject_variant(), inj_pairs ? 2 : 1};
   for (int i = 0; i < n_out && i < (int)(sizeof(v) / sizeof(v[0])); ++i) out[i] = v[i];
 }
 
