@@ -836,6 +836,31 @@ __global__ void k_mc_rotate_terms(MSimD m, const double* __restrict__ base, floa
   sn[(int64_t)t * m.R + c] = make_float2(yh, (float)(y - (double)yh));
 }
 
+// Source and load coefficient tables [term][column]: (coef * scale) * cos phi and (coef * scale) *
+// sin phi as float-float pairs (leading part the FP32 rounding, then the rounded remainder), with
+// scale = src_scale[c][idx] or load_scale[c][idx] (1 without scales); ki >= 0 names a source,
+// ki < 0 the load -(ki + 1).
+__global__ void k_mc_terms(const double* __restrict__ coef, const double* __restrict__ cph,
+                           const double* __restrict__ sph, const int* __restrict__ ki,
+                           const double* __restrict__ src_scale, const double* __restrict__ load_scale, int n_src,
+                           int n_load, int n_terms, int R, float2* __restrict__ cs, float2* __restrict__ sn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n_terms * R) return;
+  const int t = (int)(i / R), c = (int)(i % R);
+  const int k = ki[t];
+  double sc = 1.0;
+  if (k >= 0) {
+    if (src_scale) sc = src_scale[(size_t)c * n_src + k];
+  } else if (load_scale) {
+    sc = load_scale[(size_t)c * n_load + (-k - 1)];
+  }
+  const double a = coef[t] * sc;
+  const double x = a * cph[t], y = a * sph[t];
+  const float xh = __double2float_rn(x), yh = __double2float_rn(y);
+  cs[i] = make_float2(xh, __double2float_rn(x - (double)xh));
+  sn[i] = make_float2(yh, __double2float_rn(y - (double)yh));
+}
+
 // z_c of column c (its change's G^{-1} u_c, Sec. IV) as float-float.
 __global__ void k_mc_set_z(MSimD m, float2* Z, const double* __restrict__ zpos, int c) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1057,45 +1082,57 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
     EMT_REQUIRE(net->load_bus[k] >= 0 && net->load_bus[k] < n, EMT_ERR_INVALID, "bad load bus");
     terms[t.pos[net->load_bus[k]]].push_back({0, -net->load_amp[k], net->load_phi[k], 1, k});
   }
-  std::vector<int> tptr(n + 1, 0);
-  std::vector<float2> tcs, tsn;
-  tcs.reserve((size_t)(net->n_src + net->n_load) * R);
-  tsn.reserve((size_t)(net->n_src + net->n_load) * R);
+  // per-term constants on the host; the [term][column] coefficient tables (coef * scale * cos phi,
+  // coef * scale * sin phi as float-float pairs) are formed on the device from the scale arrays
+  std::vector<int> tptr(n + 1, 0), t_ki;   // t_ki: source index, or -(load index + 1)
+  std::vector<double> t_coef, t_cph, t_sph, tb;
   for (int p = 0; p < n; ++p) {
     for (auto& tm : terms[p]) {
-      const double cph = std::cos(tm.phi), sph = std::sin(tm.phi);
-      for (int c = 0; c < R; ++c) {
-        double sc = 1.0;
-        if (tm.kind == 0 && src_scale) sc = src_scale[(size_t)c * net->n_src + tm.idx];
-        if (tm.kind == 1 && load_scale) sc = load_scale[(size_t)c * net->n_load + tm.idx];
-        tcs.push_back(host_ff(tm.coef * sc * cph));
-        tsn.push_back(host_ff(tm.coef * sc * sph));
-      }
+      t_coef.push_back(tm.coef);
+      t_cph.push_back(std::cos(tm.phi));
+      t_sph.push_back(std::sin(tm.phi));
+      t_ki.push_back(tm.kind == 0 ? tm.idx : -(tm.idx + 1));
+      tb.push_back(tm.coef * std::cos(tm.phi));
+      tb.push_back(tm.coef * std::sin(tm.phi));
     }
     tptr[p + 1] = tptr[p] + (int)terms[p].size();
   }
-  if (tcs.empty()) {
-    tcs.push_back(make_float2(0, 0));
-    tsn.push_back(make_float2(0, 0));
-  }
-  {
-    std::vector<double> tb;
-    for (int p = 0; p < n; ++p)
-      for (auto& tm : terms[p]) {
-        tb.push_back(tm.coef * std::cos(tm.phi));
-        tb.push_back(tm.coef * std::sin(tm.phi));
-      }
-    if (tb.empty()) tb.assign(2, 0.0);
-    term_base.upload(tb, s);
-  }
+  const int n_terms = (int)t_coef.size();
+  if (tb.empty()) tb.assign(2, 0.0);
+  term_base.upload(tb, s);
   term_ptr.upload(tptr, s);
-  term_cs.upload(tcs, s);
+  term_cs.alloc(std::max<size_t>((size_t)n_terms * R, 1));
+  term_sn.alloc(std::max<size_t>((size_t)n_terms * R, 1));
+  if (n_terms > 0) {
+    DevBuf<double> d_coef, d_cph, d_sph, d_ss, d_ls;
+    DevBuf<int> d_ki;
+    d_coef.upload(t_coef, s);
+    d_cph.upload(t_cph, s);
+    d_sph.upload(t_sph, s);
+    d_ki.upload(t_ki, s);
+    if (src_scale && net->n_src > 0) {
+      d_ss.alloc((size_t)R * net->n_src);
+      EMT_CUDA(cudaMemcpyAsync(d_ss.p, src_scale, d_ss.n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    if (load_scale && net->n_load > 0) {
+      d_ls.alloc((size_t)R * net->n_load);
+      EMT_CUDA(cudaMemcpyAsync(d_ls.p, load_scale, d_ls.n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    const int64_t tot = (int64_t)n_terms * R;
+    k_mc_terms<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_coef.p, d_cph.p, d_sph.p, d_ki.p, d_ss.p, d_ls.p,
+                                                             net->n_src, net->n_load, n_terms, R, term_cs.p,
+                                                             term_sn.p);
+    EMT_CUDA(cudaGetLastError());
+    EMT_CUDA(cudaStreamSynchronize(s));   // the temporaries are freed on return
+  } else {
+    EMT_CUDA(cudaMemsetAsync(term_cs.p, 0, sizeof(float2), s));
+    EMT_CUDA(cudaMemsetAsync(term_sn.p, 0, sizeof(float2), s));
+  }
   {
     // the two-column injection indexes rows with 32-bit products (R even, every row * R < 2^31)
-    const int64_t rows = std::max<int64_t>({(int64_t)2 * n_el_h, (int64_t)n, (int64_t)(tcs.size() / std::max(R, 1))});
+    const int64_t rows = std::max<int64_t>({(int64_t)2 * n_el_h, (int64_t)n, (int64_t)n_terms});
     inj_pairs = (R % 2) == 0 && (rows + 1) * R < ((int64_t)1 << 31);
   }
-  term_sn.upload(tsn, s);
   std::vector<float2> cff(store->csr_val.size());
   for (size_t k = 0; k < cff.size(); ++k) cff[k] = host_ff(store->csr_val[k]);
   csr_ff.upload(cff, s);
