@@ -715,27 +715,54 @@ Store::Store(const emt_graph* g, const emt_hinv_opts* o, cudaStream_t s) {
 Store::~Store() {}
 
 void Store::build_csr() {
-  // position-ordered CSR of G; entries accumulated in branch order (deterministic)
-  std::vector<std::map<int, double>> rows(n);
-  for (int i = 0; i < n; ++i) rows[i][i] = 0.0;
-  for (size_t e = 0; e < g_from.size(); ++e) {
+  // position-ordered CSR of G; each entry is the sum of its contributions in branch order
+  // (deterministic): contributions are bucketed by row in that order, sorted by column with a
+  // stable insertion sort (rows hold a handful of entries) and summed from 0 per (row, column)
+  struct Contrib {
+    int col;
+    double v;
+  };
+  const size_t m = g_from.size();
+  std::vector<int> cnt(n + 1, 0);
+  for (int i = 0; i < n; ++i) cnt[i + 1] += 1;   // the diagonal exists even without branches
+  for (size_t e = 0; e < m; ++e) {
+    cnt[tree.pos[g_from[e]] + 1] += g_to[e] >= 0 ? 2 : 1;
+    if (g_to[e] >= 0) cnt[tree.pos[g_to[e]] + 1] += 2;
+  }
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<Contrib> all(cnt[n]);
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int i = 0; i < n; ++i) all[fill[i]++] = {i, 0.0};
+  for (size_t e = 0; e < m; ++e) {
     const int a = tree.pos[g_from[e]];
     const double gv = g_val[e];
-    rows[a][a] += gv;
+    all[fill[a]++] = {a, gv};
     if (g_to[e] >= 0) {
       const int b = tree.pos[g_to[e]];
-      rows[b][b] += gv;
-      rows[a][b] -= gv;
-      rows[b][a] -= gv;
+      all[fill[b]++] = {b, gv};
+      all[fill[a]++] = {b, -gv};
+      all[fill[b]++] = {a, -gv};
     }
   }
   csr_ptr.assign(n + 1, 0);
   csr_col.clear();
   csr_val.clear();
   for (int i = 0; i < n; ++i) {
-    for (auto& kv : rows[i]) {
-      csr_col.push_back(kv.first);
-      csr_val.push_back(kv.second);
+    Contrib* r = all.data() + cnt[i];
+    const int len = cnt[i + 1] - cnt[i];
+    for (int x = 1; x < len; ++x) {   // stable: equal columns keep their branch order
+      const Contrib c = r[x];
+      int y = x - 1;
+      for (; y >= 0 && r[y].col > c.col; --y) r[y + 1] = r[y];
+      r[y + 1] = c;
+    }
+    for (int x = 0; x < len;) {
+      double sum = 0.0;
+      int y = x;
+      for (; y < len && r[y].col == r[x].col; ++y) sum += r[y].v;
+      csr_col.push_back(r[x].col);
+      csr_val.push_back(sum);
+      x = y;
     }
     csr_ptr[i + 1] = (int)csr_col.size();
   }
