@@ -1146,6 +1146,10 @@ MSim::MSim(const emt_network* net, const emt_hinv_opts* opts, double dt_, int R_
   Z.alloc(nR);
   S.alloc((size_t)std::max(store->s_total, 1) * R);
   fcol.alloc(R);
+  // no column has a change yet: zero factors (read by the change terms of a pass with n1 = 1,
+  // e.g. the expansion timed alone) must not pick up stale device memory
+  Z.zero(s);
+  fcol.zero(s);
   h_trip_step.assign(R, 0);
   h_trip_elem.assign(R, -1);
   trip_step.upload(h_trip_step, s);
