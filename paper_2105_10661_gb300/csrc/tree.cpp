@@ -13,6 +13,7 @@
 //   5. leaves at depth `levels`, or (levels == 0) once a set has at most d_th buses.
 // Nodes are numbered breadth first; the left-to-right leaves give the nested ordering.
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <deque>
 #include <exception>
@@ -110,66 +111,108 @@ std::vector<int> growth_order(const Local& g, int start) {
   return order;
 }
 
-// Argmax of (D[v], -v) over the active vertices: an array segment tree whose nodes hold the
-// winning vertex of their range (-1 if none); a change of D or of activity re-plays one path.
-struct MaxTree {
-  int P = 1;
-  std::vector<int> t;
-  const long long* D = nullptr;
-  bool better(int x, int y) const {
-    if (y < 0) return x >= 0;
-    if (x < 0) return false;
-    return D[x] > D[y] || (D[x] == D[y] && x < y);
+// Unlocked vertices of one side bucketed by gain D (Fiduccia-Mattheyses style): per gain value a
+// two-level bitset over vertex ids, so the argmax of (D[v], -v) is the lowest id of the highest
+// non-empty bucket, and the next candidates in that order follow with a few word scans. Gains are
+// branch counts, |D| <= the vertex's weighted degree.
+struct GainBuckets {
+  int W = 0, S = 0, off = 0, nb = 0;
+  std::vector<uint64_t> b1, b2;   // [nb][W] vertex bits, [nb][S] non-empty words of b1
+  std::vector<int> cnt;           // vertices per bucket
+  int top = -1;                   // no bucket above is non-empty
+  void init(int n, int max_abs) {
+    W = (n + 63) / 64;
+    S = (W + 63) / 64;
+    off = max_abs;
+    nb = 2 * max_abs + 1;
+    b1.assign((size_t)nb * W, 0);
+    b2.assign((size_t)nb * S, 0);
+    cnt.assign(nb, 0);
+    top = -1;
   }
-  void build(int n, const long long* d, const std::vector<char>& active) {
-    D = d;
-    P = 1;
-    while (P < n) P <<= 1;
-    t.assign(2 * P, -1);
-    for (int v = 0; v < n; ++v) t[P + v] = active[v] ? v : -1;
-    for (int i = P - 1; i >= 1; --i) t[i] = better(t[2 * i], t[2 * i + 1]) ? t[2 * i] : t[2 * i + 1];
+  void insert(int v, int d) {
+    const int k = d + off;
+    uint64_t& w = b1[(size_t)k * W + (v >> 6)];
+    if (!w) b2[(size_t)k * S + (v >> 12)] |= 1ull << ((v >> 6) & 63);
+    w |= 1ull << (v & 63);
+    ++cnt[k];
+    top = std::max(top, k);
   }
-  void replay(int v) {
-    for (int i = (P + v) >> 1; i >= 1; i >>= 1) t[i] = better(t[2 * i], t[2 * i + 1]) ? t[2 * i] : t[2 * i + 1];
+  void erase(int v, int d) {
+    const int k = d + off;
+    uint64_t& w = b1[(size_t)k * W + (v >> 6)];
+    w &= ~(1ull << (v & 63));
+    if (!w) b2[(size_t)k * S + (v >> 12)] &= ~(1ull << ((v >> 6) & 63));
+    --cnt[k];
   }
-  void set(int v, bool on) {
-    t[P + v] = on ? v : -1;
-    replay(v);
+  // lowest id >= v in bucket k, or -1
+  int next(int k, int v) const {
+    const uint64_t* w1 = &b1[(size_t)k * W];
+    const uint64_t* w2 = &b2[(size_t)k * S];
+    int wi = v >> 6;
+    if (wi >= W) return -1;
+    const uint64_t m = w1[wi] & (~0ull << (v & 63));
+    if (m) return (wi << 6) + __builtin_ctzll(m);
+    int si = (wi + 1) >> 6;
+    if (si >= S) return -1;
+    uint64_t sm = ((wi + 1) & 63) ? (w2[si] & (~0ull << ((wi + 1) & 63))) : w2[si];
+    while (true) {
+      if (sm) {
+        const int wj = (si << 6) + __builtin_ctzll(sm);
+        return (wj << 6) + __builtin_ctzll(w1[wj]);
+      }
+      if (++si >= S) return -1;
+      sm = w2[si];
+    }
   }
-  int top() const { return t[1]; }
+  // argmax of (D, -id) over the bucketed vertices for which skip(v) is false; -1 if none
+  template <class F>
+  int best(F skip) {
+    while (top >= 0 && cnt[top] == 0) --top;
+    for (int k = top; k >= 0; --k) {
+      if (!cnt[k]) continue;
+      for (int v = next(k, 0); v >= 0; v = next(k, v + 1))
+        if (!skip(v)) return v;
+    }
+    return -1;
+  }
 };
 
 // The choices are those of the plain O(n) scans (a = largest D over unlocked A, b = largest
-// D(b) - 2 w(a, b) over unlocked B, smallest id on ties), found in O(deg log n): each side's
-// unlocked vertices sit in a MaxTree; for b the only values that differ from D are those of a's
-// neighbours, so b is the better of the best neighbour and the best of the tree with a's
-// neighbours masked out.
+// D(b) - 2 w(a, b) over unlocked B, smallest id on ties): each side's unlocked vertices sit in
+// gain buckets; for b the only values that differ from D are those of a's neighbours, so b is the
+// better of the best neighbour and the best non-neighbour of the buckets.
 void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
   const int n = g.n;
-  std::vector<long long> D(n);
-  std::vector<char> locked(n), act(n);
-  MaxTree T[2];
+  std::vector<int> D(n), nbr_of(n, -1);   // nbr_of[u] == a: u is a neighbour of the current a
+  std::vector<char> locked(n);
+  int max_abs = 0;
+  for (int v = 0; v < n; ++v) {
+    int s = 0;
+    for (int w : g.wt[v]) s += w;
+    max_abs = std::max(max_abs, s);
+  }
+  GainBuckets T[2];
   for (int pass = 0; pass < passes; ++pass) {
     int nA = 0;
     for (int v = 0; v < n; ++v) {
-      long long s = 0;
+      int s = 0;
       for (size_t k = 0; k < g.nbr[v].size(); ++k)
         s += (side[g.nbr[v][k]] != side[v]) ? g.wt[v][k] : -g.wt[v][k];
       D[v] = s;
       nA += side[v] == 0;
     }
     std::fill(locked.begin(), locked.end(), 0);
-    for (int sd = 0; sd < 2; ++sd) {
-      for (int v = 0; v < n; ++v) act[v] = side[v] == sd;
-      T[sd].build(n, D.data(), act);
-    }
+    T[0].init(n, max_abs);
+    T[1].init(n, max_abs);
+    for (int v = 0; v < n; ++v) T[side[v]].insert(v, D[v]);
     const int steps = std::min(nA, n - nA);
     std::vector<std::pair<int, int>> pairs;
     std::vector<long long> gains;
     pairs.reserve(steps);
     gains.reserve(steps);
     for (int st = 0; st < steps; ++st) {
-      const int a = T[0].top();
+      const int a = T[0].best([](int) { return false; });
       const std::vector<int>& na = g.nbr[a];
       // best neighbour of a in unlocked B, by D - 2 w
       bool have = false;
@@ -178,8 +221,9 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
       long long wab = 0;
       for (size_t k = 0; k < na.size(); ++k) {
         const int u = na[k];
+        nbr_of[u] = a;
         if (side[u] != 1 || locked[u]) continue;
-        const long long val = D[u] - 2LL * g.wt[a][k];
+        const long long val = (long long)D[u] - 2LL * g.wt[a][k];
         if (!have || val > bv || (val == bv && u < b)) {
           have = true;
           bv = val;
@@ -188,11 +232,7 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
         }
       }
       // best unlocked B vertex that is not a neighbour of a
-      for (int u : na)
-        if (side[u] == 1 && !locked[u]) T[1].set(u, false);
-      const int c = T[1].top();
-      for (int u : na)
-        if (side[u] == 1 && !locked[u]) T[1].set(u, true);
+      const int c = T[1].best([&](int v) { return nbr_of[v] == a; });
       if (c >= 0) {
         const long long val = D[c];
         if (!have || val > bv || (val == bv && c < b)) {
@@ -202,23 +242,25 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
           wab = 0;
         }
       }
-      gains.push_back(D[a] + D[b] - 2 * wab);
+      gains.push_back((long long)D[a] + D[b] - 2 * wab);
       pairs.emplace_back(a, b);
       locked[a] = 1;
       locked[b] = 1;
-      T[0].set(a, false);
-      T[1].set(b, false);
+      T[0].erase(a, D[a]);
+      T[1].erase(b, D[b]);
       for (size_t k = 0; k < na.size(); ++k) {
         const int x = na[k];
         if (locked[x]) continue;
-        D[x] += (side[x] == 0) ? 2LL * g.wt[a][k] : -2LL * g.wt[a][k];
-        T[side[x]].replay(x);
+        T[side[x]].erase(x, D[x]);
+        D[x] += (side[x] == 0) ? 2 * g.wt[a][k] : -2 * g.wt[a][k];
+        T[side[x]].insert(x, D[x]);
       }
       for (size_t k = 0; k < g.nbr[b].size(); ++k) {
         const int y = g.nbr[b][k];
         if (locked[y]) continue;
-        D[y] += (side[y] == 1) ? 2LL * g.wt[b][k] : -2LL * g.wt[b][k];
-        T[side[y]].replay(y);
+        T[side[y]].erase(y, D[y]);
+        D[y] += (side[y] == 1) ? 2 * g.wt[b][k] : -2 * g.wt[b][k];
+        T[side[y]].insert(y, D[y]);
       }
     }
     if (gains.empty()) break;
