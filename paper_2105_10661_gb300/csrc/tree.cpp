@@ -15,7 +15,6 @@
 #include <algorithm>
 #include <cstdint>
 #include <atomic>
-#include <deque>
 #include <exception>
 #include <mutex>
 #include <thread>
@@ -28,8 +27,9 @@ namespace {
 
 struct Local {
   int n = 0;
-  std::vector<std::vector<int>> nbr;   // ascending unique neighbours
-  std::vector<std::vector<int>> wt;    // multiplicities
+  std::vector<int> ptr;   // [n + 1]: vertex v's neighbours are adj[ptr[v] .. ptr[v + 1])
+  std::vector<int> adj;   // ascending unique neighbours
+  std::vector<int> wt;    // their multiplicities
 };
 
 // Induced subgraph on the set V (owner[v] == set, loc[v] its local index): ascending unique
@@ -38,8 +38,7 @@ Local local_graph(const std::vector<int>& V, int set, const std::vector<int>& ow
                   const std::vector<std::vector<int>>& adj_global) {
   Local g;
   g.n = (int)V.size();
-  g.nbr.resize(g.n);
-  g.wt.resize(g.n);
+  g.ptr.assign(g.n + 1, 0);
   std::vector<int> tmp;
   for (int i = 0; i < g.n; ++i) {
     tmp.clear();
@@ -49,27 +48,29 @@ Local local_graph(const std::vector<int>& V, int set, const std::vector<int>& ow
     for (size_t k = 0; k < tmp.size();) {
       size_t e = k;
       while (e < tmp.size() && tmp[e] == tmp[k]) ++e;
-      g.nbr[i].push_back(tmp[k]);
-      g.wt[i].push_back((int)(e - k));
+      g.adj.push_back(tmp[k]);
+      g.wt.push_back((int)(e - k));
       k = e;
     }
+    g.ptr[i + 1] = (int)g.adj.size();
   }
   return g;
 }
 
 std::vector<int> bfs_dist(const Local& g, int s) {
-  std::vector<int> d(g.n, -1);
-  std::deque<int> q;
+  std::vector<int> d(g.n, -1), q(g.n);
+  int head = 0, tail = 0;
   d[s] = 0;
-  q.push_back(s);
-  while (!q.empty()) {
-    int u = q.front();
-    q.pop_front();
-    for (int v : g.nbr[u])
+  q[tail++] = s;
+  while (head < tail) {
+    const int u = q[head++];
+    for (int k = g.ptr[u]; k < g.ptr[u + 1]; ++k) {
+      const int v = g.adj[k];
       if (d[v] < 0) {
         d[v] = d[u] + 1;
-        q.push_back(v);
+        q[tail++] = v;
       }
+    }
   }
   return d;
 }
@@ -88,22 +89,22 @@ int start_vertex(const Local& g) {
 
 std::vector<int> growth_order(const Local& g, int start) {
   std::vector<char> seen(g.n, 0);
-  std::vector<int> order;
+  std::vector<int> order;   // doubles as the BFS queue: a vertex is appended when first seen
   order.reserve(g.n);
   auto run = [&](int r) {
     if (seen[r]) return;
     seen[r] = 1;
-    std::deque<int> q;
-    q.push_back(r);
-    while (!q.empty()) {
-      int u = q.front();
-      q.pop_front();
-      order.push_back(u);
-      for (int v : g.nbr[u])
+    size_t head = order.size();
+    order.push_back(r);
+    while (head < order.size()) {
+      const int u = order[head++];
+      for (int k = g.ptr[u]; k < g.ptr[u + 1]; ++k) {
+        const int v = g.adj[k];
         if (!seen[v]) {
           seen[v] = 1;
-          q.push_back(v);
+          order.push_back(v);
         }
+      }
     }
   };
   run(start);
@@ -189,7 +190,7 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
   int max_abs = 0;
   for (int v = 0; v < n; ++v) {
     int s = 0;
-    for (int w : g.wt[v]) s += w;
+    for (int k = g.ptr[v]; k < g.ptr[v + 1]; ++k) s += g.wt[k];
     max_abs = std::max(max_abs, s);
   }
   GainBuckets T[2];
@@ -197,8 +198,7 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
     int nA = 0;
     for (int v = 0; v < n; ++v) {
       int s = 0;
-      for (size_t k = 0; k < g.nbr[v].size(); ++k)
-        s += (side[g.nbr[v][k]] != side[v]) ? g.wt[v][k] : -g.wt[v][k];
+      for (int k = g.ptr[v]; k < g.ptr[v + 1]; ++k) s += (side[g.adj[k]] != side[v]) ? g.wt[k] : -g.wt[k];
       D[v] = s;
       nA += side[v] == 0;
     }
@@ -213,22 +213,24 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
     gains.reserve(steps);
     for (int st = 0; st < steps; ++st) {
       const int a = T[0].best([](int) { return false; });
-      const std::vector<int>& na = g.nbr[a];
+      const int* na = g.adj.data() + g.ptr[a];
+      const int* wa = g.wt.data() + g.ptr[a];
+      const int da = g.ptr[a + 1] - g.ptr[a];
       // best neighbour of a in unlocked B, by D - 2 w
       bool have = false;
       long long bv = 0;
       int b = -1;
       long long wab = 0;
-      for (size_t k = 0; k < na.size(); ++k) {
+      for (int k = 0; k < da; ++k) {
         const int u = na[k];
         nbr_of[u] = a;
         if (side[u] != 1 || locked[u]) continue;
-        const long long val = (long long)D[u] - 2LL * g.wt[a][k];
+        const long long val = (long long)D[u] - 2LL * wa[k];
         if (!have || val > bv || (val == bv && u < b)) {
           have = true;
           bv = val;
           b = u;
-          wab = g.wt[a][k];
+          wab = wa[k];
         }
       }
       // best unlocked B vertex that is not a neighbour of a
@@ -248,18 +250,18 @@ void kernighan_lin(const Local& g, std::vector<int>& side, int passes) {
       locked[b] = 1;
       T[0].erase(a, D[a]);
       T[1].erase(b, D[b]);
-      for (size_t k = 0; k < na.size(); ++k) {
+      for (int k = 0; k < da; ++k) {
         const int x = na[k];
         if (locked[x]) continue;
         T[side[x]].erase(x, D[x]);
-        D[x] += (side[x] == 0) ? 2 * g.wt[a][k] : -2 * g.wt[a][k];
+        D[x] += (side[x] == 0) ? 2 * wa[k] : -2 * wa[k];
         T[side[x]].insert(x, D[x]);
       }
-      for (size_t k = 0; k < g.nbr[b].size(); ++k) {
-        const int y = g.nbr[b][k];
+      for (int k = g.ptr[b]; k < g.ptr[b + 1]; ++k) {
+        const int y = g.adj[k];
         if (locked[y]) continue;
         T[side[y]].erase(y, D[y]);
-        D[y] += (side[y] == 1) ? 2 * g.wt[b][k] : -2 * g.wt[b][k];
+        D[y] += (side[y] == 1) ? 2 * g.wt[k] : -2 * g.wt[k];
         T[side[y]].insert(y, D[y]);
       }
     }
