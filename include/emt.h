@@ -327,8 +327,8 @@ emt_status emt_sim_reset(emt_sim* s, void* stream);
  * of the injection kernel of a several-column simulation (2 when the columns fill whole blocks of
  * pairs, else 1; 0 for single-column simulations), and its variant (1 one column per thread; 2, 3,
  * 4 two columns per thread with 6, 3 or 2 element ends per memory round trip, 2, 3 or 4 CTAs per
- * SM; 0 for single-column simulations), and columns per thread of the residual kernel (2 when
- * nrhs is even, else 1; 0 for single-column simulations). */
+ * SM; 0 for single-column simulations), and columns per thread of the residual kernel (as for
+ * the injection; 0 for single-column simulations). */
 emt_status emt_sim_stats(const emt_sim* s, int64_t* out, int32_t n);
 /* Measurement aid: enqueue `reps` back-to-back launches (as one CUDA graph) of one fused
  * step kernel with the current arguments: which = 0 the leaf-partial kernel, 1 the
