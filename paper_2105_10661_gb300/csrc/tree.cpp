@@ -314,6 +314,10 @@ Tree build_tree(int n_bus, int n_branch, const int32_t* from, const int32_t* to,
       const int n = (int)sets[i].size();
       if (n >= 2 && ((levels > 0 && depth[i] < levels) || (levels <= 0 && n > d_th))) todo.push_back(i);
     }
+    // owner[v] = index in `todo` of the set v belongs to at this depth, -1 for a vertex of a set
+    // that is not bisected here (a leaf already): an index left from an earlier depth would make
+    // it look like a member of whichever set now has that index
+    std::fill(owner.begin(), owner.end(), -1);
     for (size_t q = 0; q < todo.size(); ++q) {
       const std::vector<int>& V = sets[todo[q]];
       for (int k = 0; k < (int)V.size(); ++k) {
