@@ -111,6 +111,24 @@ def test_block_partition_bit_exact_with_oracle(L, which, levels, d_th):
     assert len(got["cut_b"]) > 0
 
 
+@pytest.mark.parametrize("seed", [11, 12, 13])
+@pytest.mark.parametrize("levels,d_th", [(2, 0), (0, 8)])
+def test_block_partition_bit_exact_on_random_multigraphs(L, seed, levels, d_th):
+    # vertices grouped in threes: the random multigraph's buses become groups, and each of its
+    # branches joins a random vertex of one group to a random vertex of the other
+    n, a, b = _random_multigraph(seed)
+    rng = np.random.default_rng(seed)
+    fa = 3 * a + rng.integers(0, 3, len(a))
+    fb = 3 * b + rng.integers(0, 3, len(b))
+    got = L.emt_tree_build(3 * n, fa, fb, levels=levels, d_th=d_th, nodes_per_bus=3)
+    ref = opart.build_block_tree(3 * n, fa, fb, 3, levels=levels, d_th=d_th)
+    for k in KEYS:
+        if k == "cut_a":
+            assert np.array_equal(got["cut_a"], np.asarray(ref["cut_a"]).reshape(-1, 3)[:, 0])
+        else:
+            assert np.array_equal(got[k], np.asarray(ref[k])), k
+
+
 def test_block_partition_rejects_a_vertex_count_off_the_group_size(L):
     with pytest.raises(L.EmtError) as e:
         L.emt_tree_build(7, [0, 3], [3, 6], levels=1, nodes_per_bus=3)
