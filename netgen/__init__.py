@@ -224,3 +224,27 @@ def config_network(cfg: int) -> dict:
     if cfg == 4:
         return add_loads(tiled(8, 8))
     raise ValueError(cfg)
+
+
+def random_multigraph(seed: int):
+    """Random branch lists (n_bus, from, to) that stress the partition's and the store's
+    bookkeeping: parallel branches, a hub joined to a third of the buses (a wide gain range and
+    wide cuts), two isolated buses and a second component. Branch endpoints only, no parameters."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(60, 340))
+    m = int(n * rng.uniform(1.2, 2.2))
+    a = rng.integers(0, n - 5, m)
+    b = rng.integers(0, n - 5, m)
+    keep = a != b
+    a, b = list(a[keep]), list(b[keep])
+    for k in range(0, m // 4):          # parallel copies of a quarter of the branches
+        a.append(a[k])
+        b.append(b[k])
+    hub = int(rng.integers(0, n - 5))
+    for v in rng.choice(n - 5, n // 3, replace=False):
+        if int(v) != hub:
+            a.append(hub)
+            b.append(int(v))
+    a += [n - 4, n - 3]                 # a second component; buses n - 2, n - 1 stay isolated
+    b += [n - 3, n - 5]
+    return n, np.asarray(a, np.int32), np.asarray(b, np.int32)

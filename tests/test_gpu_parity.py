@@ -70,6 +70,50 @@ def test_apply_rejects_a_tolerance_it_would_not_evaluate(L):
     assert torch.isfinite(v_dev).all()
 
 
+def _random_conductance_graph(seed):
+    """A random multigraph with conductances and a shunt on every bus (so G is positive definite
+    whatever is tripped): irregular trees, wide cuts at the hub, parallel branches."""
+    n, a, b = netgen.random_multigraph(seed)
+    rng = np.random.default_rng(seed + 100)
+    g = rng.uniform(0.5, 20.0, len(a))
+    frm = np.concatenate([a, np.arange(n, dtype=np.int32)])
+    to = np.concatenate([b, np.full(n, -1, np.int32)])
+    gv = np.concatenate([g, rng.uniform(0.01, 0.1, n)])
+    G = np.zeros((n, n))
+    for x, y, c in zip(frm, to, gv):
+        G[x, x] += c
+        if y >= 0:
+            G[y, y] += c
+            G[x, y] -= c
+            G[y, x] -= c
+    return n, frm, to, gv, G
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+@pytest.mark.parametrize("levels,d_th,prec", [(3, 0, 0), (0, 12, 0), (0, 12, 1), (4, 0, 2)])
+def test_store_on_random_multigraph_matches_dense_solve_also_after_a_trip(L, seed, levels, d_th, prec):
+    n, frm, to, gv, G = _random_conductance_graph(seed)
+    h = L.emt_build_hinv(n, frm, to, gv, levels=levels, d_th=d_th, precision=prec)
+    _PREC[id(h)] = prec
+    X = np.random.default_rng(seed).standard_normal((n, 6))
+    assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec]
+    # trip the first of a parallel pair, then a hub branch whose pair of buses no earlier branch
+    # joins (the store updates the first branch between two buses)
+    first = {}
+    for e in range(len(frm) - n):
+        first.setdefault((min(frm[e], to[e]), max(frm[e], to[e])), e)
+    hub_branches = [e for e in range(len(frm) - n - 12, len(frm) - n - 2)
+                    if first[(min(frm[e], to[e]), max(frm[e], to[e]))] == e]
+    for e in (0, hub_branches[0]):
+        a, b, c = int(frm[e]), int(to[e]), float(gv[e])
+        L.emt_modify_branch(h, a, b, -c)
+        u = np.zeros(n)
+        u[a] = 1.0
+        u[b] -= 1.0
+        G = G - c * np.outer(u, u)
+        assert rel_err(_apply(L, h, X), odense.DenseSolver(G).solve(X)) <= TOL[prec], e
+
+
 def test_hinv_get_partition_matches_tree_arrays(L):
     nw, gr = _store_inputs(netgen.tile(1_000_000))
     h = _build(L, (nw, gr), levels=2)

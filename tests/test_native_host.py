@@ -50,34 +50,10 @@ def test_partition_bit_exact_with_oracle(L, which, levels, d_th):
         assert np.array_equal(got[k], np.asarray(ref[k])), k
 
 
-def _random_multigraph(seed):
-    """Random branch lists that stress the partition's bookkeeping: parallel branches (gains count
-    multiplicities), a hub joined to a third of the buses (a wide gain range), isolated buses and
-    a second component."""
-    rng = np.random.default_rng(seed)
-    n = int(rng.integers(60, 340))
-    m = int(n * rng.uniform(1.2, 2.2))
-    a = rng.integers(0, n - 5, m)
-    b = rng.integers(0, n - 5, m)
-    keep = a != b
-    a, b = list(a[keep]), list(b[keep])
-    for k in range(0, m // 4):          # parallel copies of a quarter of the branches
-        a.append(a[k])
-        b.append(b[k])
-    hub = int(rng.integers(0, n - 5))
-    for v in rng.choice(n - 5, n // 3, replace=False):
-        if int(v) != hub:
-            a.append(hub)
-            b.append(int(v))
-    a += [n - 4, n - 3]                 # a second component; buses n-2, n-1 stay isolated
-    b += [n - 3, n - 5 + 0 * n]
-    return n, np.asarray(a, np.int32), np.asarray(b, np.int32)
-
-
 @pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("levels,d_th", [(3, 0), (0, 9)])
 def test_partition_bit_exact_on_random_multigraphs(L, seed, levels, d_th):
-    n, a, b = _random_multigraph(seed)
+    n, a, b = netgen.random_multigraph(seed)
     got = L.emt_tree_build(n, a, b, levels=levels, d_th=d_th)
     ref = opart.build_tree(n, a, b, levels=levels, d_th=d_th)
     for k in KEYS:
@@ -116,7 +92,7 @@ def test_block_partition_bit_exact_with_oracle(L, which, levels, d_th):
 def test_block_partition_bit_exact_on_random_multigraphs(L, seed, levels, d_th):
     # vertices grouped in threes: the random multigraph's buses become groups, and each of its
     # branches joins a random vertex of one group to a random vertex of the other
-    n, a, b = _random_multigraph(seed)
+    n, a, b = netgen.random_multigraph(seed)
     rng = np.random.default_rng(seed)
     fa = 3 * a + rng.integers(0, 3, len(a))
     fb = 3 * b + rng.integers(0, 3, len(b))
