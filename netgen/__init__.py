@@ -248,3 +248,30 @@ def random_multigraph(seed: int):
     a += [n - 4, n - 3]                 # a second component; buses n - 2, n - 1 stay isolated
     b += [n - 3, n - 5]
     return n, np.asarray(a, np.int32), np.asarray(b, np.int32)
+
+
+def random_network(seed: int, src_frac: float = 0.1, load_frac: float = 0.2) -> dict:
+    """A simulation network on random_multigraph(seed): RL (90 %) and RC series branches with
+    the tile's parameter ranges, a shunt capacitor on every bus (so every bus, the isolated ones
+    included, has a path to ground), Thevenin sources and constant-current loads on random buses."""
+    n, a, b = random_multigraph(seed)
+    rng = np.random.default_rng(seed + 1000)
+    nb = len(a)
+    kind = np.where(rng.random(nb) < 0.9, KIND_RL, KIND_RC).astype(np.int32)
+    R = rng.uniform(0.5, 5.0, nb)
+    L = rng.uniform(1e-3, 50e-3, nb)
+    C = rng.uniform(0.1e-6, 2e-6, nb)
+    L[kind == KIND_RC] = 0.0
+    C[kind == KIND_RL] = 0.0
+    n_src = max(1, int(src_frac * n))
+    n_load = int(load_frac * n)
+    src_bus = np.sort(rng.choice(n, size=n_src, replace=False)).astype(np.int32)
+    load_bus = np.sort(rng.choice(n, size=n_load, replace=False)).astype(np.int32)
+    return dict(
+        n_bus=n, br_a=a, br_b=b, kind=kind, R=R, L=L, C=C,
+        shunt_C=rng.uniform(0.1e-6, 2e-6, n),
+        src_bus=src_bus, src_Vm=rng.uniform(0.95, 1.05, n_src), src_phi=rng.uniform(-np.pi / 6, np.pi / 6, n_src),
+        src_Rs=rng.uniform(0.5, 2.0, n_src),
+        load_bus=load_bus, load_amp=rng.uniform(0.01, 0.1, n_load), load_phi=rng.uniform(-np.pi / 3, 0.0, n_load),
+        freq=FREQ_HZ,
+    )

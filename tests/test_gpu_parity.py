@@ -403,6 +403,29 @@ def test_sim_ragged_small_network(L):
     assert err <= 1e-10, err
 
 
+def _random_network_trips(net):
+    """Branches of a random network to trip: the second of the first parallel pair, and a hub
+    branch whose buses no other branch joins."""
+    a, b = np.asarray(net["br_a"]), np.asarray(net["br_b"])
+    key = [(min(x, y), max(x, y)) for x, y in zip(a, b)]
+    second = next(e for e in range(1, len(a)) if key[e] == key[0])
+    count = {}
+    for k in key:
+        count[k] = count.get(k, 0) + 1
+    hub = next(e for e in range(len(a) - 3, 0, -1) if count[key[e]] == 1)
+    return second, hub
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+@pytest.mark.parametrize("prec,kernels", [(1, None), (1, 2), (0, 2), (2, 2)])
+def test_sim_on_random_network_with_parallel_and_hub_trips_matches_oracle(L, seed, prec, kernels):
+    net = netgen.random_network(seed)
+    second, hub = _random_network_trips(net)
+    events = [(40, 0, second, 0.0), (70, 0, hub, 0.0)]
+    err = _sim_compare(L, net, 3, 110, events, prec, rpc=0, kernels=kernels)
+    assert err <= TOL[prec], err
+
+
 # ---------------------------------------------------------------- multi-column (N-1, scenarios)
 def _msim_run(L, net, levels, steps, R, trips=None, src_scale=None, load_scale=None):
     sim = L.emt_sim_create(net, DT, levels=levels, nrhs=R, src_scale=src_scale, load_scale=load_scale)
@@ -426,6 +449,22 @@ def test_multi_column_n1_trips_match_oracle(L, which, levels, R, steps):
     net = netgen.tile(1_000_000) if which == "tile" else netgen.tiled(2, 4)
     branches = netgen.pick_branches(net, R - 1, seed=11)
     trips = {c: (steps // 2 + (c % 3), int(branches[c])) for c in range(R - 1)}   # last column: no trip
+    got = _msim_run(L, net, levels, steps, R, trips=trips)
+    nw = oemt.Network(net, DT, levels=levels)
+    worst = 0.0
+    for c in range(R):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense")
+        worst = max(worst, rel_err(got[:, c, :], ref))
+    assert worst <= 1e-8, worst
+
+
+@pytest.mark.parametrize("seed", [31, 33])
+def test_multi_column_on_random_network_with_parallel_and_hub_trips_matches_oracle(L, seed):
+    net = netgen.random_network(seed)
+    second, hub = _random_network_trips(net)
+    R, steps, levels = 6, 80, 3
+    trips = {0: (30, second), 1: (45, hub), 3: (30, hub)}   # columns 2, 4, 5: no trip
     got = _msim_run(L, net, levels, steps, R, trips=trips)
     nw = oemt.Network(net, DT, levels=levels)
     worst = 0.0
