@@ -316,19 +316,30 @@ __device__ __forceinline__ bool panel_of(const DStore& st, int q, int modeB, con
   return true;
 }
 
+// Panel columns per CTA of the level sweep for a level whose widest cut has kq columns: kPanelCols
+// while the 2 kq x columns staging block fits the opt-in shared memory, fewer for wide cuts
+int level_sweep_cols(int kq) {
+  int dev = 0, optin = 0;
+  EMT_CUDA(cudaGetDevice(&dev));
+  EMT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int fit = (int)((size_t)optin / ((size_t)2 * std::max(kq, 1) * sizeof(double)));
+  EMT_REQUIRE(fit >= 1, EMT_ERR_UNSUPPORTED, "cut too wide for the level sweep's shared memory");
+  return std::min(kPanelCols, fit);
+}
+
 // Boundary projections of one internal node q on a panel: t = [h_l^T y_l; h_r^T y_r] is a
 // gather of the (already corrected) panel rows at q's cut endpoints; s = C_q t.
 __global__ void k_level_sweep(DStore st, int modeB, const int* flag, int d, int dq, double* Ybase, int m, int ldY,
-                              double* __restrict__ scratch, int mcols) {
+                              double* __restrict__ scratch, int mcols, int pc) {
   extern __shared__ double tsh[];
   const int q = st.lvl_nodes[st.lvl_ptr[dq] + blockIdx.x];
   Panel pn;
   if (!panel_of(st, q, modeB, flag, d, Ybase, m, ldY, pn)) return;
   const int kq = st.node_k[q];
   if (kq == 0) return;
-  const int c0 = blockIdx.y * kPanelCols;
+  const int c0 = blockIdx.y * pc;   // pc panel columns per CTA (kPanelCols, fewer for wide cuts)
   if (c0 >= pn.ncols) return;
-  const int nc = min(kPanelCols, pn.ncols - c0);
+  const int nc = min(pc, pn.ncols - c0);
   const int m2 = 2 * kq;
   const int cp = st.cut_ptr[q];
   for (int t = threadIdx.x; t < m2 * nc; t += blockDim.x) {
@@ -342,7 +353,7 @@ __global__ void k_level_sweep(DStore st, int modeB, const int* flag, int d, int 
     } else {
       v = pn.ptr[(int64_t)(st.cut_b[cp + r - kq] - pn.lo) * pn.ld + c0 + c];
     }
-    tsh[r * kPanelCols + c] = v;
+    tsh[r * pc + c] = v;
   }
   __syncthreads();
   const double* C = st.C64 + st.node_coff[q];
@@ -350,7 +361,7 @@ __global__ void k_level_sweep(DStore st, int modeB, const int* flag, int d, int 
   for (int t = threadIdx.x; t < m2 * nc; t += blockDim.x) {
     const int r = t / nc, c = t % nc;
     double s = 0.0;
-    for (int e2 = 0; e2 < m2; ++e2) s += C[r * m2 + e2] * tsh[e2 * kPanelCols + c];
+    for (int e2 = 0; e2 < m2; ++e2) s += C[r * m2 + e2] * tsh[e2 * pc + c];
     S[(int64_t)r * mcols + c0 + c] = s;
   }
 }
@@ -1063,11 +1074,12 @@ void Store::form_factors(const std::vector<int>& nodes, int d, cudaStream_t s) {
       nq = std::max(nq, tree.hi[lvl_nodes_h[i]] - tree.lo[lvl_nodes_h[i]]);
     }
     if (kq == 0) continue;
-    const size_t sh = (size_t)2 * kq * kPanelCols * sizeof(double);
+    const int pc = level_sweep_cols(kq);
+    const size_t sh = (size_t)2 * kq * pc * sizeof(double);
     if (sh > 48 * 1024)
       EMT_CUDA(cudaFuncSetAttribute(k_level_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    k_level_sweep<<<dim3(cnt, (kb + kPanelCols - 1) / kPanelCols), 256, sh, s>>>(v, 0, d_flag.p, d, dq, nullptr, 0,
-                                                                                 0, scratch.p, mcols);
+    k_level_sweep<<<dim3(cnt, (kb + pc - 1) / pc), 256, sh, s>>>(v, 0, d_flag.p, d, dq, nullptr, 0, 0, scratch.p,
+                                                                 mcols, pc);
     const int rpb = 64;
     k_level_expand<<<dim3(cnt, (nq + rpb - 1) / rpb), 256, 0, s>>>(v, 0, d_flag.p, d, dq, nullptr, 0, 0, scratch.p,
                                                                    mcols, rpb);
@@ -1372,11 +1384,12 @@ void Store::apply_rows_fp64(const double* Xin, double* Y, int m, int ld, cudaStr
       nq = std::max(nq, tree.hi[lvl_nodes_h[i]] - tree.lo[lvl_nodes_h[i]]);
     }
     if (kq == 0) continue;
-    const size_t sh = (size_t)2 * kq * kPanelCols * sizeof(double);
+    const int pc = level_sweep_cols(kq);
+    const size_t sh = (size_t)2 * kq * pc * sizeof(double);
     if (sh > 48 * 1024)
       EMT_CUDA(cudaFuncSetAttribute(k_level_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    k_level_sweep<<<dim3(cnt, (m + kPanelCols - 1) / kPanelCols), 256, sh, s>>>(v, 1, d_flag.p, 0, dq, Y, m, ld,
-                                                                                scratch.p, mcols);
+    k_level_sweep<<<dim3(cnt, (m + pc - 1) / pc), 256, sh, s>>>(v, 1, d_flag.p, 0, dq, Y, m, ld, scratch.p, mcols,
+                                                                pc);
     const int rpb = 16;
     k_level_expand<<<dim3(cnt, (nq + rpb - 1) / rpb), 256, 0, s>>>(v, 1, d_flag.p, 0, dq, Y, m, ld, scratch.p, mcols,
                                                                    rpb);

@@ -17,11 +17,19 @@ struct Error : std::runtime_error {
   Error(emt_status c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
-#define EMT_CUDA(x)                                                                        \
-  do {                                                                                     \
-    cudaError_t e_ = (x);                                                                  \
-    if (e_ != cudaSuccess)                                                                 \
-      throw ::emt::Error(EMT_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));   \
+// source file name without its directories, for error messages
+inline const char* src_name(const char* path) {
+  const char* b = path;
+  for (const char* p = path; *p; ++p)
+    if (*p == '/') b = p + 1;
+  return b;
+}
+#define EMT_CUDA(x)                                                                                    \
+  do {                                                                                                 \
+    cudaError_t e_ = (x);                                                                              \
+    if (e_ != cudaSuccess)                                                                             \
+      throw ::emt::Error(EMT_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_) + " (" +        \
+                                           ::emt::src_name(__FILE__) + ":" + std::to_string(__LINE__) + ")"); \
   } while (0)
 #define EMT_REQUIRE(c, code, msg)              \
   do {                                         \

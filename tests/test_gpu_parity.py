@@ -846,6 +846,54 @@ def test_three_phase_faults_and_a_trip_match_oracle(L, npb):
     assert rel_err(rec.cpu().numpy(), ref) <= 1e-10
 
 
+@pytest.mark.parametrize("seed,npb", [(31, 3), (33, 3)])
+def test_three_phase_on_random_network_with_parallel_trip_and_faults_matches_oracle(L, seed, npb):
+    # the random multigraph in three phases: wide cuts at the hub, parallel coupled lines (the
+    # second of a pair trips), a second component and isolated buses, faults at the hub. Block cuts
+    # only: node-level cuts at a hub of a third of the buses give cores of 2k in the thousands,
+    # whose exact updates run for minutes in FP64 on one SM each
+    from oracle import emt3 as oemt3
+    net = netgen.three_phase(netgen.random_network(seed))
+    second, _ = _random_network_trips(net)
+    hub = int(np.bincount(np.concatenate([net["br_a"], net["br_b"]])).argmax())
+    ev = ([(25, oemt3.FAULT_ON, 3 * hub + 1, 8.0), (40, oemt3.TRIP, second, 0.0),
+           (60, oemt3.FAULT_OFF, 3 * hub + 1, 0.0)])
+    ref, _ = oemt3.simulate3(net, DT, 90, ev)
+    sim = L.emt_sim3_create(net, DT, levels=3, precision=L.EMT_PREC_FF64, nodes_per_bus=npb)
+    L.emt_sim_monitor(sim, np.arange(3 * net["n_bus"]))
+    for st, kind, target, value in ev:
+        L.emt_sim_schedule(sim, st, kind, target, value)
+    rec = torch.zeros(90, 3 * net["n_bus"], dtype=torch.float64, device="cuda")
+    L.emt_step(sim, 90, rec)
+    torch.cuda.synchronize()
+    assert rel_err(rec.cpu().numpy(), ref) <= 1e-10, rel_err(rec.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("gemm", [1, 3])
+def test_multi_column_gemm_kinds_on_random_network_match_oracle(L, gemm):
+    net = netgen.random_network(32)
+    second, hub = _random_network_trips(net)
+    R, steps, levels = 36, 60, 4
+    trips = {0: (20, second), 17: (30, hub), 35: (5, hub)}
+    sim = L.emt_sim_create(net, DT, levels=levels, nrhs=R)
+    L.emt_sim_tune(sim, 0, gemm)
+    for c, (st, e) in trips.items():
+        L.emt_sim_schedule(sim, st, 0, e, 0.0, c)
+    mon = np.arange(0, net["n_bus"], 5)
+    L.emt_sim_monitor(sim, mon)
+    rec = torch.zeros(steps, R, len(mon), dtype=torch.float64, device="cuda")
+    L.emt_step(sim, steps, rec)
+    torch.cuda.synchronize()
+    got = rec.cpu().numpy()
+    nw = oemt.Network(net, DT, levels=levels)
+    worst = 0.0
+    for c in (0, 1, 17, 35):
+        ev = [(trips[c][0], oemt.TRIP, trips[c][1], 0.0)] if c in trips else []
+        ref, _ = oemt.simulate(nw, steps, ev, solver="dense", monitor=mon)
+        worst = max(worst, rel_err(got[:, c, :], ref))
+    assert worst <= 1e-8, worst
+
+
 def test_three_phase_reset_repeats_and_rejects_other_events(L):
     net = netgen.three_phase(netgen.tile(1_000_000))
     sim = L.emt_sim3_create(net, DT, levels=2, precision=L.EMT_PREC_FF64)
