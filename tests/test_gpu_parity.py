@@ -421,7 +421,10 @@ def _random_network_trips(net):
 def test_sim_on_random_network_with_parallel_and_hub_trips_matches_oracle(L, seed, prec, kernels):
     net = netgen.random_network(seed)
     second, hub = _random_network_trips(net)
-    events = [(40, 0, second, 0.0), (70, 0, hub, 0.0)]
+    hub_bus = int(np.bincount(np.concatenate([net["br_a"], net["br_b"]])).argmax())
+    # a fault at the hub bus whose window holds both trips; a second fault at an isolated bus
+    events = [(30, 1, hub_bus, 5.0), (35, 1, net["n_bus"] - 1, 2.0), (40, 0, second, 0.0), (70, 0, hub, 0.0),
+              (85, 2, hub_bus, 0.0)]
     err = _sim_compare(L, net, 3, 110, events, prec, rpc=0, kernels=kernels)
     assert err <= TOL[prec], err
 
