@@ -154,3 +154,28 @@ def test_server_evicts_idle_private_networks_under_the_budget(L):
     assert rel_err(L.emt_server_result(srv, r[0])[0], ref1) <= 1e-8
     assert rel_err(L.emt_server_result(srv, r[2])[0], ref1) <= 1e-8
     assert rel_err(L.emt_server_result(srv, r[1])[0], _oracle_run(p2, 2, 60, -1, 0, 0.0, 0, 0, mon2)) <= 1e-8
+
+
+def test_server_random_private_networks_with_trips_and_faults_match_oracle(L):
+    # private networks of irregular shape (hub, parallel branches, isolated buses): a trip of the
+    # second of a parallel pair, a hub fault window, and a plain run, mixed on one server
+    cases = []
+    for seed in (31, 33):
+        net = netgen.random_network(seed)
+        a, b = np.asarray(net["br_a"]), np.asarray(net["br_b"])
+        key = [(min(x, y), max(x, y)) for x, y in zip(a, b)]
+        second = next(e for e in range(1, len(a)) if key[e] == key[0])
+        hub = int(np.bincount(np.concatenate([a, b])).argmax())
+        mon = np.arange(0, net["n_bus"], 9)
+        cases += [(net, mon, (0.00, 110, 0, second, 0.0, 40, 0)),
+                  (net, mon, (0.01, 90, 1, hub, 5.0, 20, 35)),
+                  (net, mon, (0.02, 70, -1, 0, 0.0, 0, 0))]
+    srv = L.emt_server_create(30, 0)
+    rids = [L.emt_server_submit_network(srv, net, DT, *args, levels=3, monitor=mon) for net, mon, args in cases]
+    L.emt_server_run(srv)
+    st = L.emt_server_stats(srv)
+    assert st["finished"] == len(cases) and st["builds"] == 2
+    for (net, mon, args), rid in zip(cases, rids):
+        got, _ = L.emt_server_result(srv, rid)
+        ref = _oracle_run(net, 3, args[1], *args[2:], mon)
+        assert rel_err(got, ref) <= 1e-8, rel_err(got, ref)
