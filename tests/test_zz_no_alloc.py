@@ -145,3 +145,30 @@ def test_noalloc_rejects_a_store_beyond_its_fixed_scratch(L):
     L.emt_apply(h, x, v)
     torch.cuda.synchronize()
     assert torch.isfinite(v).all()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("levels,d_th", [(3, 0), (0, 12)])
+def test_noalloc_on_a_random_multigraph_store_matches_the_dense_solve(L, prec, levels, d_th):
+    # an irregular tree (hub cuts, parallel branches, isolated buses with only a shunt), then a
+    # trip of one branch of a parallel pair
+    n, a, b = netgen.random_multigraph(41)
+    rng = np.random.default_rng(141)
+    g = rng.uniform(0.5, 20.0, len(a))
+    frm = np.concatenate([a, np.arange(n, dtype=np.int32)])
+    to = np.concatenate([b, np.full(n, -1, np.int32)])
+    gv = np.concatenate([g, rng.uniform(0.01, 0.1, n)])
+    G = np.zeros((n, n))
+    for x, y, c in zip(frm, to, gv):
+        G[x, x] += c
+        if y >= 0:
+            G[y, y] += c
+            G[x, y] -= c
+            G[y, x] -= c
+    h = L.emt_build_hinv(n, frm, to, gv, levels=levels, d_th=d_th, precision=prec)
+    _calls(L, h, n, 1, G, prec, 0)
+    L.emt_modify_branch(h, int(frm[0]), int(to[0]), -float(gv[0]))
+    u = np.zeros(n)
+    u[frm[0]] = 1.0
+    u[to[0]] = -1.0
+    _calls(L, h, n, 2, G - gv[0] * np.outer(u, u), prec, 0)
