@@ -194,6 +194,17 @@ __device__ __forceinline__ void st_pair(float2* p, const float2 (&o)[2], bool bo
   if (both) *reinterpret_cast<float4*>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
   else p[0] = o[0];
 }
+// One element end's new history Ih' = a1 v_e + beta Ih (trapezoidal companion source, Sec. II),
+// v_e = v_from - v_to as a TwoSum of the leading parts, renormalised once (it is state). Both ends
+// of an element call it with the same operands in the same roles, so they form the same value.
+__device__ __forceinline__ float2 hist_next(const MRec& r, float2 vf, float2 vt, float2 ih, int te) {
+  Acc2 de = acc2(vf);
+  de.add(-vt.x, -vt.y);
+  Acc2 h = acc2_prod(r.a1, make_float2(de.s, de.c));
+  h.add_prod(r.beta, ih);
+  return r.elem == te ? ff_f(0.f) : h.get();   // the tripped element carries no current
+}
+
 template <int KB, int MINB>
 __global__ void __launch_bounds__(ITH, MINB) k_mc_inject2(MSimD m, int ipp, int s_in_chunk, int* status) {
   extern __shared__ __align__(16) unsigned char ism[];
@@ -251,21 +262,21 @@ __global__ void __launch_bounds__(ITH, MINB) k_mc_inject2(MSimD m, int ipp, int 
         if (kb + q >= k1) break;
         const MRec& r = srec[kb + q];
         float2 ihn[2];
+        // the record, hence the branch, is the same for every thread of the CTA
+        if (r.sgn > 0) {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          // v_e = v_from - v_to (TwoSum of the leading parts), formed identically at both ends
-          const float2 vf = r.sgn > 0 ? vi[j] : vo[q][j], vt = r.sgn > 0 ? vo[q][j] : vi[j];
-          Acc2 de = acc2(vf);
-          de.add(-vt.x, -vt.y);
-          const float2 ve = make_float2(de.s, de.c);
-          // Ih' = a1 v_e + beta Ih, renormalised once (it is state)
-          Acc2 h = acc2_prod(r.a1, ve);
-          h.add_prod(r.beta, ih[q][j]);
-          ihn[j] = r.elem == te[j] ? ff_f(0.f) : h.get();   // the tripped element carries no current
-          if (r.sgn > 0) hist[j].add(-ihn[j].x, -ihn[j].y);
-          else hist[j].add(ihn[j].x, ihn[j].y);
+          for (int j = 0; j < 2; ++j) {
+            ihn[j] = hist_next(r, vi[j], vo[q][j], ih[q][j], te[j]);
+            hist[j].add(-ihn[j].x, -ihn[j].y);
+          }
+          st_pair(Ih_wr + r.elem * R + c, ihn, both);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            ihn[j] = hist_next(r, vo[q][j], vi[j], ih[q][j], te[j]);
+            hist[j].add(ihn[j].x, ihn[j].y);
+          }
         }
-        if (r.sgn > 0) st_pair(Ih_wr + r.elem * R + c, ihn, both);
       }
 #pragma unroll
       for (int q = 0; q < ITB; ++q) {
