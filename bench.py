@@ -752,7 +752,7 @@ def residual_name(st):
 # DRAM bytes (read + write) per launch, keyed by (kernel, buses, columns), from one ncu capture of
 # dram__bytes_read.sum and dram__bytes_write.sum of the kernel as it stands (python bench.py
 # --config 4 --profile 6, third launch of each; profiles/multi_column_11456bus_512col_*_ncu_*.md)
-NCU_TRAFFIC = {("k_mc_inject2<2,4>", 11456, 512): 212.550400e6 + 148.302080e6,
+NCU_TRAFFIC = {("k_mc_inject2<2,4>", 11456, 512): 211.768832e6 + 148.137472e6,
                ("k_mc_residual2", 11456, 512): 94.539264e6 + 9.608960e6}
 
 
